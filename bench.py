@@ -1,0 +1,388 @@
+#!/usr/bin/env python
+"""Benchmark of the Pointing SelfCal hot path on GB300 (one JSON line).
+
+Workload: "vla27_l64ch" -- 27 antennas (351 baselines) in a Y layout with
+1 km arms, 25 m uniform-disk apertures, 64 channels over 1-2 GHz, 600 x 2 s
+split into 4 solution intervals, a 2048^2 model image (8") with 2000
+power-law sources; 13,478,400 visibilities, observed data simulated by the
+GPU predictor at seeded true offsets (sigma 20") plus 1 mJy noise.
+
+One step = one Levenberg-Marquardt iteration over all four intervals: per
+interval a solver restart to the zero start (one tiny kernel), one fused
+launch (degrid with the pointing-modified kernel, the four pointing
+derivatives, residuals, per-baseline chi^2 / gradient / normal sums), the
+deterministic per-antenna reduction and the FP64 LM update (damped full
+Cholesky solve).  value = visibilities evaluated with derivatives per second
+(Gvis/s).  Every step is the first iteration of a solve from zero offsets,
+so no step can be skipped by a stopped solver.  The model-grid DFT and the aperture tables are
+pre-computes outside the iteration loop (Algorithm 1); their time is reported
+under "precompute_ms".
+
+``--impl reference`` times the FP64 CPU oracle on the host cores instead
+(rank 0 only), on a bounded sample of the same workload per step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gvis/s predict+∂/∂pointing; solves/s to 1″ RMS offset, learned vs plain LM"
+FLOPS_PER_TAP = 15      # s = dx^2+dy^2 (2), sqrt (1), t = rho ov (1), A° lerp (2), P += A G (4), A dx (1), Q += (A dx) G (4)
+SMS_GB300 = 152
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=300)
+    p.add_argument("--warmup", type=int, default=10)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="vla27_l64ch")
+    p.add_argument("--seed", type=int, default=0)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
+    return p.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+    NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.samples = []
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(gpu_index), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                self.samples.append((time.time(), float(parts[0]), float(parts[1]), parts[3:7]))
+            except ValueError:
+                pass
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self, t0, t1):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        win = [s for s in self.samples if t0 <= s[0] <= t1]
+        if not win:
+            mid = 0.5 * (t0 + t1)
+            win = sorted(self.samples, key=lambda s: abs(s[0] - mid))[:3]
+        reasons = set()
+        for s in win:
+            for name, v in zip(self.NAMES, s[3]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median([s[1] for s in win])), "sm_max_mhz": float(win[0][2]),
+                "reasons": sorted(reasons), "samples": len(win)}
+
+
+# ---------------------------------------------------------------- workload helpers
+
+def taps_per_channel(wl):
+    """Expected non-zero taps per visibility per channel: pi rho_max^2 cells^2
+    with rho_max the radial table's support (disk), clipped to the window."""
+    du = 1.0 / (wl.n_grid * wl.cell_rad)
+    out = []
+    for f in wl.freq_hz:
+        dl = wl.diam_m * f / 299_792_458.0
+        rho = dl / du if wl.ap_kind == "disk" else 0.5 * wl.support * math.sqrt(2)
+        L = math.floor(wl.oversample * rho) + 2
+        r = (L - 1) / wl.oversample
+        out.append(min(math.pi * r * r, wl.support * wl.support))
+    return np.asarray(out)
+
+
+def cpu_sample_oracle(wl, vis_host, w_host, target_s, interval=0, min_t=1):
+    """Times the FP64 oracle (predict + derivatives + reductions) on the first
+    timesteps of one interval, enough to take about ``target_s`` seconds."""
+    from oracle import model_grid, psc
+    grid = model_grid.grid_from_image(wl.image, wl.n_grid)
+    t0, nt = wl.intervals[interval]
+
+    def run(n_t):
+        m = psc.Model(uvw_m=wl.uvw_m[t0:t0 + n_t], freq_hz=wl.freq_hz, n_ant=wl.n_ant, grid=grid,
+                      cell_rad=wl.cell_rad, support=wl.support, oversample=wl.oversample, ap_kind=wl.ap_kind,
+                      diam_m=wl.diam_m, alpha_per_dlambda=wl.alpha_per_dlambda, decorrelation=wl.decorrelation)
+        lm = np.zeros((wl.n_ant, 2))
+        t = time.perf_counter()
+        psc.chi2_grad_normal(m, lm, vis_host[t0:t0 + n_t], w_host[t0:t0 + n_t])
+        return time.perf_counter() - t
+
+    dt1 = run(min_t)
+    n_t = int(max(min_t, min(nt, round(min_t * target_s / max(dt1, 1e-3)))))
+    dt = run(n_t) if n_t != min_t else dt1
+    n_vis = n_t * wl.n_bl * wl.n_chan
+    return n_vis, dt, n_t, grid
+
+
+def omp_threads():
+    v = os.environ.get("OMP_NUM_THREADS")
+    return int(v) if v else (os.cpu_count() or 1)
+
+
+# ---------------------------------------------------------------- reference arm
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_1709_08681_gb300 import inputs as I
+    from oracle import model_grid, psc
+    wl = I.make_workload(args.workload, seed=args.seed)
+    # observed data for the sample: the oracle's own prediction at the true offsets plus noise
+    grid = model_grid.grid_from_image(wl.image, wl.n_grid)
+    t0, nt = wl.intervals[0]
+    n_t = 1
+    m = psc.Model(uvw_m=wl.uvw_m[t0:t0 + n_t], freq_hz=wl.freq_hz, n_ant=wl.n_ant, grid=grid, cell_rad=wl.cell_rad,
+                  support=wl.support, oversample=wl.oversample, ap_kind=wl.ap_kind, diam_m=wl.diam_m,
+                  alpha_per_dlambda=wl.alpha_per_dlambda, decorrelation=wl.decorrelation)
+    V, _ = psc.predict(m, wl.lm_true[0], False)
+    vis = V + wl.noise()[t0:t0 + n_t]
+    w = np.full(vis.shape, 1.0 / wl.sigma_noise ** 2)
+    lm = np.zeros((wl.n_ant, 2))
+    for _ in range(args.warmup):
+        psc.chi2_grad_normal(m, lm, vis, w)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        psc.chi2_grad_normal(m, lm, vis, w)
+    dt = time.perf_counter() - t
+    n_vis = vis.size
+    value = n_vis * args.steps / dt / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "Gvis/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "sample": "interval 0, first timestep: %d visibilities per step" % n_vis},
+        "cpu_baseline": {"value": value, "unit": "Gvis/s", "cores": omp_threads(), "kind": "oracle",
+                         "sample": "interval 0, 1 timestep x 351 baselines x 64 channels per step"},
+        "e2e": {"value": value, "unit": "Gvis/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- our arm
+
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device (the CUDA library is the only implementation)")
+    torch.cuda.set_device(local)
+    from paper_1709_08681_gb300 import _abi, inputs as I
+    from paper_1709_08681_gb300.session import Session
+
+    # weak scaling: every rank solves its own batch of four intervals (own seed)
+    wl = I.make_workload(args.workload, seed=args.seed + rank)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sess = Session(wl, stream=stream)
+        e1.record(stream)
+        stream.synchronize()
+        precompute_ms = e0.elapsed_time(e1)
+        vis = sess.simulate()
+        w = torch.full(vis.shape, 1.0 / wl.sigma_noise ** 2, dtype=torch.float32, device=vis.device)
+        stream.synchronize()
+
+        lm0 = np.zeros((wl.n_ant, 2))
+        opts = _abi.psc_solve_opts_default()
+        for c in sess.ctxs:
+            c.psc_lm_begin(lm0, opts)
+        vk = [sess.vis_slice(vis, k) for k in range(len(sess.ctxs))]
+        wk = [sess.vis_slice(w, k) for k in range(len(sess.ctxs))]
+
+        def step():
+            for k, c in enumerate(sess.ctxs):
+                c.psc_lm_restart()
+                c.psc_lm_iterate(vk[k], wk[k], 1.0, 1)
+
+        for _ in range(max(3, args.warmup)):
+            step()
+        stream.synchronize()
+
+        gpu_index = local
+        vis_dev = os.environ.get("CUDA_VISIBLE_DEVICES")
+        if vis_dev:
+            try:
+                gpu_index = int(vis_dev.split(",")[local])
+            except ValueError:
+                gpu_index = local
+        sampler = ClockSampler(gpu_index)
+        time.sleep(0.3)
+        for c in sess.ctxs:
+            c.psc_profile(True)
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        t_wall0 = time.time()
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_wall1 = time.time()
+        if ws > 1:
+            torch.distributed.barrier()
+        ms = e0.elapsed_time(e1)
+        kern_ms, kern_n = 0.0, 0
+        for c in sess.ctxs:
+            c.psc_profile(False)
+            a, b = c.psc_profile_read()
+            kern_ms += a
+            kern_n += b
+        time.sleep(0.2)
+        sampler.stop()
+        clocks = sampler.summary(t_wall0, t_wall1)
+        if ws > 1:
+            t = torch.tensor([ms], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms = float(t.item())
+
+        n_vis = wl.n_vis
+        value = ws * n_vis * args.steps / (ms * 1e-3) / 1e9
+        launches_per_step = 4 * len(sess.ctxs)
+
+        # roofline of the fused kernel (FP32 ALU bound)
+        taps = taps_per_channel(wl)
+        flops_per_step = 0.0
+        for (t0, nt) in wl.intervals:
+            flops_per_step += nt * wl.n_bl * float(np.sum(taps)) * FLOPS_PER_TAP
+        flops_per_launch = flops_per_step / len(wl.intervals)
+        avg_launch_ms = kern_ms / max(kern_n, 1)
+        achieved = flops_per_launch / (avg_launch_ms * 1e-3) / 1e12
+        props = torch.cuda.get_device_properties(local)
+        n_sm = props.multi_processor_count
+        peak = n_sm * FP32_LANES_PER_SM * 2 * 2.070e9 / 1e12
+
+        # end to end: pinned host buffers, copies inside the timed region
+        vis_h = vis.cpu().pin_memory()
+        w_h = w.cpu().pin_memory()
+        vis_d = torch.empty_like(vis)
+        w_d = torch.empty_like(w)
+        k_e2e = max(3, min(args.steps, 50))
+        vdk = [sess.vis_slice(vis_d, k) for k in range(len(sess.ctxs))]
+        wdk = [sess.vis_slice(w_d, k) for k in range(len(sess.ctxs))]
+        vhk = [sess.vis_slice(vis_h, k) for k in range(len(sess.ctxs))]
+        whk = [sess.vis_slice(w_h, k) for k in range(len(sess.ctxs))]
+        d2h = 0
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for _ in range(k_e2e):
+            for k, c in enumerate(sess.ctxs):
+                vdk[k].copy_(vhk[k], non_blocking=True)
+                wdk[k].copy_(whk[k], non_blocking=True)
+                c.psc_lm_restart()
+                c.psc_lm_iterate(vdk[k], wdk[k], 1.0, 1)
+            d2h = 0
+            for c in sess.ctxs:
+                lm_out, rep = c.psc_lm_end()       # synchronises; offsets + chi^2 to the host
+                d2h += lm_out.nbytes + 8 * 5
+        e2e_s = time.perf_counter() - t
+        e2e_value = ws * n_vis * k_e2e / e2e_s / 1e9
+        h2d = vis.numel() * 8 + w.numel() * 4
+
+        # full solves (plain LM from zero) of the four intervals
+        solve = None
+        if rank == 0:
+            t = time.perf_counter()
+            iters, errs = [], []
+            n_rep = 3
+            for _ in range(n_rep):
+                for k, c in enumerate(sess.ctxs):
+                    sol, rep = c.psc_solve_offsets(vk[k], wk[k], 1.0)
+                    iters.append(rep.n_iter)
+                    errs.append(np.sqrt(np.mean((sol - wl.lm_true[k]) ** 2)) / I.ARCSEC)
+            dt = time.perf_counter() - t
+            solve = {"intervals_per_s": n_rep * len(sess.ctxs) / dt, "mean_lm_iters": float(np.mean(iters)),
+                     "rms_err_arcsec": float(np.mean(errs)), "init": "zero (plain LM)"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "Gvis/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "n_ant": wl.n_ant, "n_bl": wl.n_bl, "n_time": wl.n_time,
+                   "n_chan": wl.n_chan, "n_interval": len(wl.intervals), "n_vis": n_vis,
+                   "image": wl.image.shape[0], "grid": wl.n_grid, "support": wl.support,
+                   "oversample": wl.oversample, "aperture": wl.ap_kind,
+                   "l2": "inputs larger than L2 (vis 108 MB + weights 54 MB + grid 32 MB per step)",
+                   "step": "one LM iteration of all intervals", "precompute_ms": precompute_ms},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "eval_kernel<false> (fused degrid + derivatives + residual + sums)",
+                     "avg_launch_ms": avg_launch_ms, "flops_per_launch": flops_per_launch,
+                     "peak_basis": "%d SMs x 128 FP32 lanes x 2 x 2070 MHz" % n_sm},
+        "e2e": {"value": e2e_value, "unit": "Gvis/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "clocks": clocks,
+        "gpu_launches": launches_per_step * args.steps,
+    }
+    if solve:
+        line["solve"] = solve
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        vis_host = vis.cpu().numpy()
+        w_host = w.cpu().numpy()
+        n_s, dt, n_t, _ = cpu_sample_oracle(wl, vis_host, w_host, args.cpu_seconds)
+        line["cpu_baseline"] = {"value": n_s / dt / 1e9, "unit": "Gvis/s", "cores": omp_threads(), "kind": "oracle",
+                                "sample": "interval 0, first %d timesteps x %d baselines x %d channels (%d vis, %.1f s)"
+                                          % (n_t, wl.n_bl, wl.n_chan, n_s, dt)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    sess.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,223 @@
+/*
+ * psc.h -- Pointing SelfCal hot path on one NVIDIA GB300 (sm_103a): the C ABI.
+ *
+ * The library solves for antenna pointing offsets (l_i, m_i) of an aperture
+ * synthesis array, following Bhatnagar & Cornwell 2017, "The Pointing Self
+ * Calibration algorithm for aperture synthesis radio telescopes":
+ *
+ *   Algorithm 1      pre-compute V° = F[I^M] and A°, then iterate: degrid
+ *                    V^M = A_ij * V° and grad V^M = grad A_ij * V°, form the
+ *                    residuals, accumulate chi^2 and its gradient, update l_i.
+ *   Eq. AIJPOINTING  A_ij = A° exp(-(l_i-l_j)^2 alpha^2/2) exp(i pi u (l_i+l_j))
+ *   Eq. DAIJPOINTING dA_ij/dl_i = A_ij [(l_j - l_i) alpha^2 + i pi u]
+ *                    (both extended to m the same way, Sec. 3)
+ *   Eq. DCHIDD       d chi^2/d a_i = -2 sum_j Re(R_ij^dag W_ij grad_i V^M_ij)
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Units: offsets in radians, uvw in metres, frequencies in Hz.
+ * Baselines: antenna pairs i < j in lexicographic order (0,1),(0,2),...,(1,2),...;
+ *   n_bl = n_ant (n_ant - 1) / 2.  uvw of baseline (i, j) is x_j - x_i.
+ * Visibilities: complex64 (interleaved float re, im), layout [n_time][n_bl][n_chan].
+ * Image / grid: image pixel (row, col) is at l = (col - N/2) cell,
+ *   m = (row - N/2) cell; grid cell (gy, gx) at u = (gx - Ng/2) du,
+ *   v = (gy - Ng/2) du, du = 1 / (Ng cell).  Fourier sign exp(+2 pi i), Eq. ME.
+ * Parameter vectors: lm[n_ant][2] = (l_a, m_a); gradient grad[n_ant][2];
+ *   normal blocks normal[n_ant][3] = (H_ll, H_lm, H_mm) of antenna a;
+ *   cross blocks cross[n_bl][4] = (H_{l_i l_j}, H_{l_i m_j}, H_{m_i l_j}, H_{m_i m_j}).
+ *   H_pq = 2 sum w Re(conj(dV/dp) dV/dq) (Gauss-Newton); chi^2 = sum w |R|^2
+ *   over the measured baselines i < j.
+ * Memory: "device" pointers are CUDA global memory of the current device and
+ *   "host" pointers are ordinary host memory; the caller owns every buffer it
+ *   passes.  A psc_ctx owns its internal workspace and frees it in psc_destroy.
+ * Streams: work is enqueued on the stream given to psc_create (a cudaStream_t
+ *   passed as void*, NULL = legacy default stream).  Calls that return host
+ *   results synchronise that stream before returning; psc_lm_iterate does not.
+ * Errors: every call returns a psc_status and never throws or aborts; the
+ *   message of the last failure is available from psc_last_error().  Device
+ *   side checks (a tap outside the staged tile, a non-finite LM state) are
+ *   reported as PSC_ERR_DEVICE or PSC_ERR_NUMERIC by the next synchronising call.
+ * Threads: a psc_ctx must not be used by two host threads at once.
+ */
+#ifndef PSC_H
+#define PSC_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PSC_OK = 0,
+    PSC_ERR_ARG = 1,            /* an argument is NULL, out of range or inconsistent */
+    PSC_ERR_CUDA = 2,           /* a CUDA runtime call failed */
+    PSC_ERR_OOM = 3,            /* device allocation failed */
+    PSC_ERR_NOT_CONVERGED = 4,  /* reserved: a solve hit max_iter (reported in psc_solve_report) */
+    PSC_ERR_TIMEOUT = 5,        /* reserved for bounded device waits */
+    PSC_ERR_NUMERIC = 6,        /* non-finite chi^2 / normals in the solver */
+    PSC_ERR_DEVICE = 7          /* a device-side consistency check failed */
+} psc_status;
+
+enum { PSC_AP_DISK = 0, PSC_AP_GAUSS = 1 };
+enum { PSC_LM_FULL = 0, PSC_LM_BLOCK = 1 };
+enum { PSC_STOP_NONE = 0, PSC_STOP_STEP = 1, PSC_STOP_CHI2 = 2, PSC_STOP_LAMBDA = 3,
+       PSC_STOP_MAX_ITER = 4, PSC_STOP_NUMERIC = 5 };
+
+typedef struct psc_ctx psc_ctx;
+
+/* Model grid and tap geometry (Algorithm 1 pre-computes; Eq. MEDD).
+ * Tap window of a visibility at grid coordinate x = u/du + Ng/2:
+ * x0 = floor(x) - S/2 + 1, taps x0 .. x0 + S - 1 (same for y); cells outside
+ * [0, Ng) contribute nothing. */
+typedef struct {
+    int    n_img;        /* N: the model image is N x N (N even, 2..8192) */
+    int    n_grid;       /* Ng: padded grid size (even, N <= Ng <= 16384) */
+    double cell_rad;     /* image pixel size (rad) */
+    int    support;      /* S: taps per axis (even, 2..64) */
+    int    oversample;   /* radial table samples per grid cell (1..64; 20 is the usual) */
+} psc_grid_desc;
+
+/* A-priori aperture kernel A° (Sec. 3: the pre-computed, pointing-free part
+ * of A_ij) for a homogeneous array of circularly symmetric antennas.
+ *   PSC_AP_DISK : uniform disk of diameter diam_m; A° is the disk's
+ *                 autocorrelation over its area squared (transform of the
+ *                 Airy power beam, integral 1).
+ *   PSC_AP_GAUSS: Gaussian voltage pattern exp(-alpha^2 rho^2) (Sec. 3);
+ *                 A°(q) = (pi / 2 alpha^2) exp(-pi^2 q^2 / (2 alpha^2)).
+ * alpha = alpha_per_dlambda * diam_m * nu / c at every channel.  For the disk,
+ * alpha only enters the decorrelation factor (1.1442341... matches the Airy
+ * half-power width).  A° is applied through a radial table at `oversample`
+ * samples per cell, linearly interpolated:
+ *   t = rho*ov, n = floor(t), f = t - n, A° = (1-f) tab[n] + f tab[n+1]
+ *   if n + 1 < len, else 0;  tab[n] = A°(n du / ov) du^2,
+ *   len = floor(ov * rho_max) + 2, rho_max = D_lambda/du (disk), (S/2)sqrt(2) (Gaussian). */
+typedef struct {
+    int    kind;               /* PSC_AP_DISK or PSC_AP_GAUSS */
+    double diam_m;             /* aperture diameter (m), > 0 */
+    double alpha_per_dlambda;  /* alpha / D_lambda, > 0 */
+    int    decorrelation;      /* 1: keep exp(-alpha^2 |p_i - p_j|^2 / 2) of Eq. AIJPOINTING; 0: drop it */
+} psc_aperture;
+
+/* One block of observation (normally one solution interval, Algorithm 1's
+ * (tau_sol, dnu_sol)).  uvw_dev is borrowed for the lifetime of the ctx. */
+typedef struct {
+    int           n_ant;     /* 2..512 */
+    int           n_time;    /* >= 1 */
+    int           n_chan;    /* 1..4096 */
+    const double *uvw_dev;   /* device [n_time][n_bl][3] (m) */
+    const double *freq_hz;   /* host [n_chan] (Hz), > 0 */
+} psc_obs;
+
+/* Levenberg-Marquardt options: f() and Terminate() of Algorithm 1, left to
+ * the minimiser by the paper (Sec. 2.2).  Damped system
+ * (H + lam diag(H)) delta = -g over all 2 n_ant parameters (PSC_LM_FULL) or
+ * per antenna with step scaled by block_gain (PSC_LM_BLOCK).  A trial that
+ * lowers chi^2 is accepted (lam /= 10, floored at lam_min), else rejected
+ * (lam *= 10).  Stops: max |delta| < step_tol_rad; an accepted relative chi^2
+ * decrease < chi2_rtol; lam > lam_max; max_iter iterations. */
+typedef struct {
+    int    max_iter;       /* 50 */
+    int    mode;           /* PSC_LM_FULL */
+    double lam0;           /* 1e-3 */
+    double lam_max;        /* 1e10 */
+    double lam_min;        /* 1e-12 */
+    double step_tol_rad;   /* 1e-4 arcsec */
+    double chi2_rtol;      /* 1e-10 */
+    double block_gain;     /* 0.5 */
+} psc_solve_opts;
+
+typedef struct {
+    int    n_iter;         /* iterations taken */
+    int    n_eval;         /* fused evaluations (= n_iter + 1 unless stopped on a step) */
+    int    reason;         /* PSC_STOP_* */
+    double chi2;           /* chi^2 at the returned offsets */
+    double lam;            /* final damping */
+} psc_solve_report;
+
+/* Fills *opts with the defaults listed above. */
+void psc_solve_opts_default(psc_solve_opts *opts);
+
+/* V° = F[I^M] (Algorithm 1, first pre-compute): the unnormalised DFT of the
+ * image zero-padded to Ng x Ng, G[gy][gx] = sum I[row][col]
+ * exp(+2 pi i ((gx-Ng/2)(col-N/2) + (gy-Ng/2)(row-N/2)) / Ng).
+ * image_dev: device float [N][N]; grid_out: device complex64 [Ng][Ng];
+ * stream: cudaStream_t or NULL.  Allocates a temporary complex64 [N][Ng]
+ * buffer and synchronises the stream before freeing it and returning. */
+psc_status psc_model_grid(const psc_grid_desc *gd, const float *image_dev, void *grid_out,
+                          void *stream);
+
+/* Creates a context for one observation block: copies the channel list,
+ * builds the A° tables on the device (Algorithm 1, second pre-compute) and
+ * allocates the workspace.  grid_dev (complex64 [Ng][Ng], from
+ * psc_model_grid or the caller) is borrowed, like obs->uvw_dev; several
+ * contexts may share one grid.  On failure *out is NULL. */
+psc_status psc_create(psc_ctx **out, const psc_obs *obs, const psc_aperture *ap,
+                      const psc_grid_desc *gd, const void *grid_dev, void *stream);
+
+/* Frees the context's workspace.  NULL is ignored. */
+void psc_destroy(psc_ctx *ctx);
+
+/* Message of the last failure on ctx (or of the last failed psc_create /
+ * psc_model_grid when ctx is NULL).  Valid until the next call on ctx. */
+const char *psc_last_error(const psc_ctx *ctx);
+
+/* Model visibilities at offsets lm (host [n_ant][2]) -- Algorithm 1's
+ * V^M_ij = A_ij * V° and grad_i V^M_ij = grad_i A_ij * V°.
+ * vis_out: device complex64 [n_time][n_bl][n_chan].
+ * dvis_out: NULL, or device complex64 [4][n_time][n_bl][n_chan] holding
+ * dV/dl_i, dV/dm_i, dV/dl_j, dV/dm_j of each baseline (i, j).  Synchronises. */
+psc_status psc_predict(psc_ctx *ctx, const double *lm, void *vis_out, void *dvis_out);
+
+/* One fused evaluation at offsets lm (host [n_ant][2]) of the residuals
+ * R = V^Obs - V^M, chi^2 (Eq. Chisq), the gradient (Eq. DCHIDD) and the
+ * Gauss-Newton normal blocks.  vis_obs: device complex64 [n_time][n_bl][n_chan];
+ * w: device float weights of the same shape, or NULL for all ones; each
+ * weight is multiplied by w_scale (> 0).  Outputs are host buffers: chi2 (1),
+ * grad [n_ant][2], normal [n_ant][3], cross [n_bl][4] (NULL to skip).
+ * Synchronises. */
+psc_status psc_residual_grad(psc_ctx *ctx, const double *lm, const void *vis_obs, const float *w,
+                             double w_scale, double *chi2, double *grad, double *normal,
+                             double *cross);
+
+/* Solves for the offsets (Algorithm 1's iteration loop, LM as described at
+ * psc_solve_opts), starting from lm_inout (host [n_ant][2]) and writing the
+ * solution back there.  opts NULL = defaults; rep may be NULL.  All
+ * iterations run on the device; synchronises once at the end. */
+psc_status psc_solve_offsets(psc_ctx *ctx, const void *vis_obs, const float *w, double w_scale,
+                             const psc_solve_opts *opts, double *lm_inout, psc_solve_report *rep);
+
+/* The solve split into device-resident steps, for callers that pipeline or
+ * time the loop: psc_lm_begin uploads lm0 (host [n_ant][2]) and resets the
+ * solver state (no synchronisation); psc_lm_iterate enqueues n_iter
+ * iterations -- one fused evaluation and one LM update each; iterations after
+ * a stop are skipped on the device -- without synchronising; psc_lm_end
+ * synchronises and copies out the current offsets (host [n_ant][2]) and report
+ * (either may be NULL). */
+psc_status psc_lm_begin(psc_ctx *ctx, const double *lm0, const psc_solve_opts *opts);
+psc_status psc_lm_iterate(psc_ctx *ctx, const void *vis_obs, const float *w, double w_scale,
+                          int n_iter);
+psc_status psc_lm_end(psc_ctx *ctx, double *lm_out, psc_solve_report *rep);
+
+/* Resets the solver to the start given by the last psc_lm_begin (offsets,
+ * options, damping) with one device kernel, no host transfer and no
+ * synchronisation, so that a pipelined caller can run many solves from the
+ * same start.  Fails with PSC_ERR_ARG if psc_lm_begin was never called. */
+psc_status psc_lm_restart(psc_ctx *ctx);
+
+/* Launch-shape knobs of the fused kernel (time steps and channels per
+ * thread block); 0 keeps the current value.  t_tile in {8,16,32},
+ * c_group in {1,2,4,8}, t_tile * c_group in {32, 64, 128, 256}. */
+psc_status psc_set_tiling(psc_ctx *ctx, int t_tile, int c_group);
+
+/* Timing of the fused evaluation kernel (the dominant launch of every
+ * iteration).  psc_profile(ctx, 1) makes every later fused launch on ctx's
+ * stream record a pair of CUDA events around it; psc_profile(ctx, 0) stops
+ * recording.  psc_profile_read synchronises the stream, returns the summed
+ * duration (ms) and count of the recorded launches, and clears the record.
+ * This is instrumentation only; it does not change any result. */
+psc_status psc_profile(psc_ctx *ctx, int enable);
+psc_status psc_profile_read(psc_ctx *ctx, double *total_ms, int *n_launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PSC_H */

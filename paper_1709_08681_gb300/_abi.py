@@ -1,0 +1,225 @@
+"""ctypes binding of ``libpsc.so`` (declared in ``include/psc.h``).
+
+Argument marshalling only: every step of the Pointing SelfCal path runs in
+the CUDA library.  Device buffers are passed as torch CUDA tensors (or raw
+integer device addresses); host buffers as numpy arrays.  Functions carry the
+C names and raise ``PscError`` on any status other than ``PSC_OK``.  There is
+no CPU fallback: if the library cannot be loaded the import-time ``lib()``
+call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+PSC_OK, PSC_ERR_ARG, PSC_ERR_CUDA, PSC_ERR_OOM = 0, 1, 2, 3
+PSC_ERR_NOT_CONVERGED, PSC_ERR_TIMEOUT, PSC_ERR_NUMERIC, PSC_ERR_DEVICE = 4, 5, 6, 7
+PSC_AP_DISK, PSC_AP_GAUSS = 0, 1
+PSC_LM_FULL, PSC_LM_BLOCK = 0, 1
+STOP_REASONS = {0: "none", 1: "step", 2: "chi2", 3: "lambda", 4: "max_iter", 5: "numeric"}
+
+EXPORTS = ("psc_solve_opts_default", "psc_model_grid", "psc_create", "psc_destroy", "psc_last_error",
+           "psc_predict", "psc_residual_grad", "psc_solve_offsets", "psc_lm_begin", "psc_lm_iterate",
+           "psc_lm_end", "psc_lm_restart", "psc_set_tiling", "psc_profile", "psc_profile_read")
+
+
+class PscError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("psc status %d: %s" % (status, msg))
+        self.status = status
+
+
+class psc_grid_desc(ctypes.Structure):
+    _fields_ = [("n_img", ctypes.c_int), ("n_grid", ctypes.c_int), ("cell_rad", ctypes.c_double),
+                ("support", ctypes.c_int), ("oversample", ctypes.c_int)]
+
+
+class psc_aperture(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("diam_m", ctypes.c_double), ("alpha_per_dlambda", ctypes.c_double),
+                ("decorrelation", ctypes.c_int)]
+
+
+class psc_obs(ctypes.Structure):
+    _fields_ = [("n_ant", ctypes.c_int), ("n_time", ctypes.c_int), ("n_chan", ctypes.c_int),
+                ("uvw_dev", ctypes.c_void_p), ("freq_hz", ctypes.POINTER(ctypes.c_double))]
+
+
+class psc_solve_opts(ctypes.Structure):
+    _fields_ = [("max_iter", ctypes.c_int), ("mode", ctypes.c_int), ("lam0", ctypes.c_double),
+                ("lam_max", ctypes.c_double), ("lam_min", ctypes.c_double), ("step_tol_rad", ctypes.c_double),
+                ("chi2_rtol", ctypes.c_double), ("block_gain", ctypes.c_double)]
+
+
+class psc_solve_report(ctypes.Structure):
+    _fields_ = [("n_iter", ctypes.c_int), ("n_eval", ctypes.c_int), ("reason", ctypes.c_int),
+                ("chi2", ctypes.c_double), ("lam", ctypes.c_double)]
+
+
+_lib = None
+_D = ctypes.POINTER(ctypes.c_double)
+_V = ctypes.c_void_p
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Loads (building first if the sources are newer) the CUDA library."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        sig = {
+            "psc_solve_opts_default": (None, [ctypes.POINTER(psc_solve_opts)]),
+            "psc_model_grid": (ctypes.c_int, [ctypes.POINTER(psc_grid_desc), _V, _V, _V]),
+            "psc_create": (ctypes.c_int, [ctypes.POINTER(_V), ctypes.POINTER(psc_obs), ctypes.POINTER(psc_aperture),
+                                          ctypes.POINTER(psc_grid_desc), _V, _V]),
+            "psc_destroy": (None, [_V]),
+            "psc_last_error": (ctypes.c_char_p, [_V]),
+            "psc_predict": (ctypes.c_int, [_V, _D, _V, _V]),
+            "psc_residual_grad": (ctypes.c_int, [_V, _D, _V, _V, ctypes.c_double, _D, _D, _D, _D]),
+            "psc_solve_offsets": (ctypes.c_int, [_V, _V, _V, ctypes.c_double, ctypes.POINTER(psc_solve_opts), _D,
+                                                 ctypes.POINTER(psc_solve_report)]),
+            "psc_lm_begin": (ctypes.c_int, [_V, _D, ctypes.POINTER(psc_solve_opts)]),
+            "psc_lm_iterate": (ctypes.c_int, [_V, _V, _V, ctypes.c_double, ctypes.c_int]),
+            "psc_lm_end": (ctypes.c_int, [_V, _D, ctypes.POINTER(psc_solve_report)]),
+            "psc_lm_restart": (ctypes.c_int, [_V]),
+            "psc_set_tiling": (ctypes.c_int, [_V, ctypes.c_int, ctypes.c_int]),
+            "psc_profile": (ctypes.c_int, [_V, ctypes.c_int]),
+            "psc_profile_read": (ctypes.c_int, [_V, _D, ctypes.POINTER(ctypes.c_int)]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _ptr(x):
+    """Device address of a torch tensor (or an int address, or None)."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def _dp(a):
+    return a.ctypes.data_as(_D)
+
+
+def _check(st, ctx=None):
+    if st != PSC_OK:
+        msg = lib().psc_last_error(ctx)
+        raise PscError(st, msg.decode() if msg else "")
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def psc_solve_opts_default() -> psc_solve_opts:
+    o = psc_solve_opts()
+    lib().psc_solve_opts_default(ctypes.byref(o))
+    return o
+
+
+def psc_model_grid(n_img, n_grid, cell_rad, support, oversample, image_dev, grid_out, stream=None):
+    gd = psc_grid_desc(n_img, n_grid, cell_rad, support, oversample)
+    _check(lib().psc_model_grid(ctypes.byref(gd), _ptr(image_dev), _ptr(grid_out), _stream(stream)))
+
+
+class Context:
+    """Owns one ``psc_ctx``; ``uvw_dev`` and ``grid_dev`` must outlive it."""
+
+    def __init__(self, n_ant, n_time, n_chan, uvw_dev, freq_hz, ap_kind, diam_m, alpha_per_dlambda,
+                 decorrelation, n_img, n_grid, cell_rad, support, oversample, grid_dev, stream=None):
+        self._keep = (uvw_dev, grid_dev)
+        self.n_ant, self.n_time, self.n_chan = int(n_ant), int(n_time), int(n_chan)
+        self.n_bl = self.n_ant * (self.n_ant - 1) // 2
+        self._freq = np.ascontiguousarray(freq_hz, dtype=np.float64)
+        obs = psc_obs(self.n_ant, self.n_time, self.n_chan, _ptr(uvw_dev), _dp(self._freq))
+        kind = {"disk": PSC_AP_DISK, "gauss": PSC_AP_GAUSS}.get(ap_kind, ap_kind)
+        ap = psc_aperture(int(kind), float(diam_m), float(alpha_per_dlambda), int(decorrelation))
+        gd = psc_grid_desc(int(n_img), int(n_grid), float(cell_rad), int(support), int(oversample))
+        h = _V()
+        _check(lib().psc_create(ctypes.byref(h), ctypes.byref(obs), ctypes.byref(ap), ctypes.byref(gd),
+                                _ptr(grid_dev), _stream(stream)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().psc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _lm(self, lm):
+        lm = np.ascontiguousarray(lm, dtype=np.float64)
+        if lm.shape != (self.n_ant, 2):
+            raise ValueError("lm must be [n_ant][2]")
+        return lm
+
+    def psc_set_tiling(self, t_tile=0, c_group=0):
+        _check(lib().psc_set_tiling(self.h, int(t_tile), int(c_group)), self.h)
+
+    def psc_predict(self, lm, vis_out, dvis_out=None):
+        lm = self._lm(lm)
+        _check(lib().psc_predict(self.h, _dp(lm), _ptr(vis_out), _ptr(dvis_out)), self.h)
+
+    def psc_residual_grad(self, lm, vis_obs, w=None, w_scale=1.0, cross=False):
+        lm = self._lm(lm)
+        chi2 = np.zeros(1)
+        g = np.zeros((self.n_ant, 2))
+        H = np.zeros((self.n_ant, 3))
+        X = np.zeros((self.n_bl, 4)) if cross else None
+        _check(lib().psc_residual_grad(self.h, _dp(lm), _ptr(vis_obs), _ptr(w), float(w_scale), _dp(chi2), _dp(g),
+                                       _dp(H), _dp(X) if cross else None), self.h)
+        return (float(chi2[0]), g, H, X) if cross else (float(chi2[0]), g, H)
+
+    def psc_solve_offsets(self, vis_obs, w=None, w_scale=1.0, lm0=None, opts=None):
+        lm = self._lm(np.zeros((self.n_ant, 2)) if lm0 is None else lm0).copy()
+        rep = psc_solve_report()
+        _check(lib().psc_solve_offsets(self.h, _ptr(vis_obs), _ptr(w), float(w_scale),
+                                       ctypes.byref(opts) if opts is not None else None, _dp(lm),
+                                       ctypes.byref(rep)), self.h)
+        return lm, rep
+
+    def psc_lm_begin(self, lm0, opts=None):
+        self._lm0 = self._lm(lm0)
+        _check(lib().psc_lm_begin(self.h, _dp(self._lm0), ctypes.byref(opts) if opts is not None else None), self.h)
+
+    def psc_lm_iterate(self, vis_obs, w=None, w_scale=1.0, n_iter=1):
+        _check(lib().psc_lm_iterate(self.h, _ptr(vis_obs), _ptr(w), float(w_scale), int(n_iter)), self.h)
+
+    def psc_lm_restart(self):
+        _check(lib().psc_lm_restart(self.h), self.h)
+
+    def psc_profile(self, enable=True):
+        _check(lib().psc_profile(self.h, int(bool(enable))), self.h)
+
+    def psc_profile_read(self):
+        ms = np.zeros(1)
+        n = ctypes.c_int(0)
+        _check(lib().psc_profile_read(self.h, _dp(ms), ctypes.byref(n)), self.h)
+        return float(ms[0]), int(n.value)
+
+    def psc_lm_end(self):
+        lm = np.zeros((self.n_ant, 2))
+        rep = psc_solve_report()
+        _check(lib().psc_lm_end(self.h, _dp(lm), ctypes.byref(rep)), self.h)
+        return lm, rep

@@ -1,0 +1,361 @@
+// Fused evaluation kernel of the Pointing SelfCal hot path (sm_103a):
+// degridding with the pointing-modified aperture kernel, the four pointing
+// derivatives, the residual against the observed visibilities and the
+// per-baseline sums of chi^2, gradient and Gauss-Newton normals.
+//
+// Paper basis (Bhatnagar & Cornwell 2017): Algorithm 1's inner loop; the
+// kernel A_ij of Eq. AIJPOINTING and its derivative of Eq. DAIJPOINTING
+// (extended to m, Sec. 3); chi^2 of Eq. Chisq and its gradient, Eq. DCHIDD.
+//
+// Work decomposition.  One thread block handles one "brick": a baseline
+// (i, j), a group of c_group channels and a tile of t_tile time steps, one
+// visibility per thread (warps are single-channel, consecutive times).  The
+// block stages the grid cells its visibilities touch in shared memory.  The
+// kernel's ramp factorises, exp(i pi (u_k - u_g) L) =
+// exp(i pi (u_k - u_o) L) exp(-i pi (u_g - u_o) L) for any origin u_o, so the
+// staged cells are pre-multiplied by the second factor (per cell, once per
+// block) and each visibility applies the first factor once; the inner loop
+// over taps then only needs the real radial A° and five FMAs per tap.  Taps
+// outside the disk's support are not visited (their A° is zero by the table
+// rule).  If a brick's footprint does not fit the staging tile, the block
+// falls back to reading the grid from global memory with the ramp applied
+// per tap (same arithmetic, slower).
+#include <climits>
+
+#include "psc_internal.cuh"
+
+namespace psc {
+namespace {
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// A°(rho) for t = rho * ov >= 0 from a table of (A°(n), A°(n+1) - A°(n)) pairs
+// whose last entry is (0, 0).  floor(t) is taken exactly by adding 2^23 with
+// round-toward-zero (valid for 0 <= t < 2^23): the sum lands on the integer
+// floor(t) + 2^23, whose low mantissa bits are floor(t).
+__device__ __forceinline__ float tab_lookup(const float2 *tab, int len, float t) {
+    const float tf = __fadd_rz(t, 8388608.0f);
+    int n = __float_as_int(tf) - 0x4B000000;
+    const float f = t - (tf - 8388608.0f);
+    n = min(n, len - 1);
+    const float2 e = tab[n];
+    return fmaf(f, e.y, e.x);
+}
+
+template <bool kPredict>
+__global__ void __launch_bounds__(kMaxThreads) eval_kernel(const EvalArgs a) {
+    if (a.skip != nullptr && *a.skip) return;
+    extern __shared__ float2 s_tab[];                 // c_group * max_tab_len
+    __shared__ float2 s_tile[kTile * kTile];
+    __shared__ float2 s_phx[kTile], s_phy[kTile];
+    __shared__ int s_box[4];
+    __shared__ double s_red[kMaxThreads / 32][kRed];
+
+    const int tid = threadIdx.x;
+    const int brick = blockIdx.x;
+    const int tt = brick % a.n_tt;
+    const int cgi = (brick / a.n_tt) % a.n_cg;
+    const int bl = brick / (a.n_tt * a.n_cg);
+    const int lt = tid % a.t_tile;
+    const int lc = tid / a.t_tile;
+    const int t = tt * a.t_tile + lt;
+    const int c = cgi * a.c_group + lc;
+    const bool valid = lc < a.c_group && t < a.nt && c < a.nc;
+
+    const int2 ij = a.pairs[bl];
+    const double li = a.lm[2 * ij.x], mi = a.lm[2 * ij.x + 1];
+    const double lj = a.lm[2 * ij.y], mj = a.lm[2 * ij.y + 1];
+    const float L = (float)(li + lj), M = (float)(mi + mj);     // ramp: l_i + l_j, m_i + m_j
+    const float dL = (float)(li - lj), dM = (float)(mi - mj);   // l_i - l_j, m_i - m_j
+
+    if (tid == 0) {
+        s_box[0] = INT_MAX; s_box[1] = INT_MIN; s_box[2] = INT_MAX; s_box[3] = INT_MIN;
+    }
+    __syncthreads();
+
+    // Grid position of this visibility: x = u / du + Ng/2 (cells), window
+    // origin floor(x) - S/2 + 1.
+    int ix0 = 0, iy0 = 0;
+    float fx = 0.f, fy = 0.f;
+    if (valid) {
+        const double *p = a.uvw + ((size_t)t * a.n_bl + bl) * 3;
+        const double sc = a.chan[c].uv_scale;
+        const double x = p[0] * sc + 0.5 * a.ng;
+        const double y = p[1] * sc + 0.5 * a.ng;
+        const double flx = floor(x), fly = floor(y);
+        fx = (float)(x - flx);
+        fy = (float)(y - fly);
+        ix0 = (int)flx - a.support / 2 + 1;
+        iy0 = (int)fly - a.support / 2 + 1;
+        atomicMin(&s_box[0], ix0); atomicMax(&s_box[1], ix0);
+        atomicMin(&s_box[2], iy0); atomicMax(&s_box[3], iy0);
+    }
+    // radial tables of this block's channels
+    for (int k = tid; k < a.c_group * a.max_tab_len; k += blockDim.x) {
+        const int cc = cgi * a.c_group + k / a.max_tab_len;
+        const int n = k % a.max_tab_len;
+        float2 v = make_float2(0.f, 0.f);
+        if (cc < a.nc) {
+            const ChanConst ch = a.chan[cc];
+            if (n < ch.tab_len) v = a.tabs[ch.tab_off + n];
+        }
+        s_tab[k] = v;
+    }
+    __syncthreads();
+    const int bx0 = s_box[0], by0 = s_box[2];
+    const int ex = s_box[1] - bx0 + a.support, ey = s_box[3] - by0 + a.support;
+    const bool staged = ex <= kTile && ey <= kTile;      // uniform over the block
+
+    if (staged) {
+        // per-cell half of the ramp, relative to the tile origin
+        for (int k = tid; k < ex; k += blockDim.x) {
+            float s, co;
+            sincospif(-(float)k * a.du * L, &s, &co);
+            s_phx[k] = make_float2(co, s);
+        }
+        for (int k = tid; k < ey; k += blockDim.x) {
+            float s, co;
+            sincospif(-(float)k * a.du * M, &s, &co);
+            s_phy[k] = make_float2(co, s);
+        }
+        __syncthreads();
+        for (int k = tid; k < ex * ey; k += blockDim.x) {
+            const int yy = k / ex, xx = k - yy * ex;
+            const int gx = bx0 + xx, gy = by0 + yy;
+            float2 g = make_float2(0.f, 0.f);
+            if (gx >= 0 && gx < a.ng && gy >= 0 && gy < a.ng) g = __ldg(&a.grid[(size_t)gy * a.ng + gx]);
+            s_tile[yy * kTile + xx] = cmul(g, cmul(s_phx[xx], s_phy[yy]));
+        }
+        __syncthreads();
+    }
+
+    // ---- per-visibility tap sums (relative to origin (ox, oy)) ----
+    const int ox = staged ? bx0 : ix0;
+    const int oy = staged ? by0 : iy0;
+    float2 S0 = make_float2(0.f, 0.f), Su = S0, Sv = S0;
+    const float hx = fx + (float)(a.support / 2 - 1);   // dx of tap 0 (cells)
+    const float hy = fy + (float)(a.support / 2 - 1);
+    if (valid) {
+        const ChanConst ch = a.chan[c];
+        const float2 *tab = s_tab + lc * a.max_tab_len;
+        const int len = ch.tab_len;
+        const float ov = (float)a.ov;
+        const float rmax = ch.rho_max;
+        const int b_lo = max(0, (int)ceilf(hy - rmax) - 1);
+        const int b_hi = min(a.support - 1, (int)floorf(hy + rmax) + 1);
+        float sdx = 0.f, cdx = 0.f;
+        if (!staged) sincospif(-a.du * L, &sdx, &cdx);     // per-column ramp step
+        for (int b = b_lo; b <= b_hi; ++b) {
+            const float dy = hy - (float)b;
+            if (fabsf(dy) >= rmax) continue;
+            const float r = sqrtf(fmaf(-dy, dy, rmax * rmax));
+            const int a_lo = max(0, (int)ceilf(hx - r) - 1);
+            const int a_hi = min(a.support - 1, (int)floorf(hx + r) + 1);
+            const float dy2 = dy * dy;
+            float pr = 0.f, pi = 0.f, qr = 0.f, qi = 0.f;
+            float dx = hx - (float)a_lo;
+            if (staged) {
+                const float2 *row = s_tile + (iy0 - oy + b) * kTile + (ix0 - ox);
+                for (int aa = a_lo; aa <= a_hi; ++aa, dx -= 1.f) {
+                    const float s = fmaxf(fmaf(dx, dx, dy2), 1e-30f);
+                    const float A = tab_lookup(tab, len, s * rsqrtf(s) * ov);
+                    const float2 g = row[aa];
+                    pr = fmaf(A, g.x, pr);
+                    pi = fmaf(A, g.y, pi);
+                    const float Ad = A * dx;
+                    qr = fmaf(Ad, g.x, qr);
+                    qi = fmaf(Ad, g.y, qi);
+                }
+            } else {
+                // ramp exp(-i pi du (a L + b M)) relative to this visibility's window origin
+                float sz, cz;
+                sincospif(-a.du * ((float)a_lo * L + (float)b * M), &sz, &cz);
+                float2 z = make_float2(cz, sz);
+                const float2 step = make_float2(cdx, sdx);
+                const int gy = iy0 + b;
+                for (int aa = a_lo; aa <= a_hi; ++aa, dx -= 1.f) {
+                    const int gx = ix0 + aa;
+                    float2 g = make_float2(0.f, 0.f);
+                    if (gx >= 0 && gx < a.ng && gy >= 0 && gy < a.ng) g = __ldg(&a.grid[(size_t)gy * a.ng + gx]);
+                    g = cmul(g, z);
+                    z = cmul(z, step);
+                    const float s = fmaxf(fmaf(dx, dx, dy2), 1e-30f);
+                    const float A = tab_lookup(tab, len, s * rsqrtf(s) * ov);
+                    pr = fmaf(A, g.x, pr);
+                    pi = fmaf(A, g.y, pi);
+                    const float Ad = A * dx;
+                    qr = fmaf(Ad, g.x, qr);
+                    qi = fmaf(Ad, g.y, qi);
+                }
+            }
+            S0.x += pr; S0.y += pi;
+            Su.x += qr; Su.y += qi;
+            Sv.x = fmaf(dy, pr, Sv.x);
+            Sv.y = fmaf(dy, pi, Sv.y);
+        }
+    }
+
+    // ---- epilogue: visibility half of the ramp, decorrelation, derivatives ----
+    float acc[kRed];
+#pragma unroll
+    for (int k = 0; k < kRed; ++k) acc[k] = 0.f;
+    if (valid) {
+        const float ph_arg = a.du * (((float)(ix0 - ox) + hx) * L + ((float)(iy0 - oy) + hy) * M);
+        float s, co;
+        sincospif(ph_arg, &s, &co);
+        const float2 ph = make_float2(co, s);
+        const float2 T0 = cmul(ph, S0);
+        float2 Tu = cmul(ph, Su), Tv = cmul(ph, Sv);
+        Tu.x *= a.du; Tu.y *= a.du;          // tap offsets in wavelengths
+        Tv.x *= a.du; Tv.y *= a.du;
+        const float al2 = a.chan[c].alpha2;
+        float D = 1.f, el = 0.f, em = 0.f;
+        if (a.decorrelation) {
+            D = expf(-0.5f * al2 * (dL * dL + dM * dM));
+            el = -dL * al2;                  // (l_j - l_i) alpha^2
+            em = -dM * al2;
+        }
+        const float pi_f = 3.14159265358979f;
+        const float2 V = make_float2(D * T0.x, D * T0.y);
+        // d/dl_i = D [(l_j - l_i) a^2 T0 + i pi Tu]; d/dl_j flips the first term; m likewise
+        const float2 dli = make_float2(D * (el * T0.x - pi_f * Tu.y), D * (el * T0.y + pi_f * Tu.x));
+        const float2 dmi = make_float2(D * (em * T0.x - pi_f * Tv.y), D * (em * T0.y + pi_f * Tv.x));
+        const float2 dlj = make_float2(D * (-el * T0.x - pi_f * Tu.y), D * (-el * T0.y + pi_f * Tu.x));
+        const float2 dmj = make_float2(D * (-em * T0.x - pi_f * Tv.y), D * (-em * T0.y + pi_f * Tv.x));
+        const size_t k = ((size_t)t * a.n_bl + bl) * a.nc + c;
+        if (kPredict) {
+            a.vis_out[k] = V;
+            if (a.dvis_out != nullptr) {
+                const size_t plane = (size_t)a.nt * a.n_bl * a.nc;
+                a.dvis_out[k] = dli;
+                a.dvis_out[plane + k] = dmi;
+                a.dvis_out[2 * plane + k] = dlj;
+                a.dvis_out[3 * plane + k] = dmj;
+            }
+        } else {
+            const float2 vo = a.vis_obs[k];
+            const float w = a.w_scale * (a.w != nullptr ? a.w[k] : 1.f);
+            const float2 R = make_float2(vo.x - V.x, vo.y - V.y);
+            const float w2 = 2.f * w;
+            acc[0] = w * (R.x * R.x + R.y * R.y);
+            acc[1] = -w2 * (R.x * dli.x + R.y * dli.y);
+            acc[2] = -w2 * (R.x * dmi.x + R.y * dmi.y);
+            acc[3] = -w2 * (R.x * dlj.x + R.y * dlj.y);
+            acc[4] = -w2 * (R.x * dmj.x + R.y * dmj.y);
+            acc[5] = w2 * (dli.x * dli.x + dli.y * dli.y);
+            acc[6] = w2 * (dli.x * dmi.x + dli.y * dmi.y);
+            acc[7] = w2 * (dmi.x * dmi.x + dmi.y * dmi.y);
+            acc[8] = w2 * (dlj.x * dlj.x + dlj.y * dlj.y);
+            acc[9] = w2 * (dlj.x * dmj.x + dlj.y * dmj.y);
+            acc[10] = w2 * (dmj.x * dmj.x + dmj.y * dmj.y);
+            acc[11] = w2 * (dli.x * dlj.x + dli.y * dlj.y);
+            acc[12] = w2 * (dli.x * dmj.x + dli.y * dmj.y);
+            acc[13] = w2 * (dmi.x * dlj.x + dmi.y * dlj.y);
+            acc[14] = w2 * (dmi.x * dmj.x + dmi.y * dmj.y);
+        }
+    }
+    if constexpr (!kPredict) {
+    // ---- block reduction: FP32 within a warp, FP64 across warps ----
+#pragma unroll
+    for (int k = 0; k < kRed; ++k) {
+        float v = acc[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        acc[k] = v;
+    }
+    const int warp = tid >> 5, lane = tid & 31;
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < kRed; ++k) s_red[warp][k] = (double)acc[k];
+    }
+    __syncthreads();
+    if (tid < kRed) {
+        double s = 0.0;
+        const int nw = (blockDim.x + 31) >> 5;
+        for (int wi = 0; wi < nw; ++wi) s += s_red[wi][tid];
+        a.partials[(size_t)brick * kRed + tid] = s;
+    }
+    }
+}
+
+// Second stage: per-baseline sums over bricks, then per-antenna sums, all in
+// a fixed order (deterministic).  ev = chi2 | g[2n] | H[3n] | X[4 nbl].
+__global__ void reduce_kernel(const double *__restrict__ partials, int n_bl, int bpb,
+                              const int2 *__restrict__ pairs, int n_ant, double *__restrict__ blsum,
+                              double *__restrict__ ev, const int *skip) {
+    if (skip != nullptr && *skip) return;
+    __shared__ double s_chi[kMaxThreads];
+    const int tid = threadIdx.x;
+    double chi = 0.0;
+    for (int bl = tid; bl < n_bl; bl += blockDim.x) {
+        double s[kRed];
+#pragma unroll
+        for (int k = 0; k < kRed; ++k) s[k] = 0.0;
+        const double *p = partials + (size_t)bl * bpb * kRed;
+        for (int b = 0; b < bpb; ++b) {
+#pragma unroll
+            for (int k = 0; k < kRed; ++k) s[k] += p[(size_t)b * kRed + k];
+        }
+#pragma unroll
+        for (int k = 0; k < kRed; ++k) blsum[(size_t)bl * kRed + k] = s[k];
+        chi += s[0];
+        double *x = ev + 1 + 5 * (size_t)n_ant + 4 * (size_t)bl;
+        x[0] = s[11]; x[1] = s[12]; x[2] = s[13]; x[3] = s[14];
+    }
+    s_chi[tid] = chi;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (tid < o) s_chi[tid] += s_chi[tid + o];
+        __syncthreads();
+    }
+    if (tid == 0) ev[0] = s_chi[0];
+    for (int an = tid; an < n_ant; an += blockDim.x) {
+        double g0 = 0, g1 = 0, h0 = 0, h1 = 0, h2 = 0;
+        for (int o = 0; o < n_ant; ++o) {
+            if (o == an) continue;
+            const int i = min(an, o), j = max(an, o);
+            const int bl = i * (2 * n_ant - i - 1) / 2 + (j - i - 1);
+            const double *s = blsum + (size_t)bl * kRed;
+            if (an == i) {
+                g0 += s[1]; g1 += s[2]; h0 += s[5]; h1 += s[6]; h2 += s[7];
+            } else {
+                g0 += s[3]; g1 += s[4]; h0 += s[8]; h1 += s[9]; h2 += s[10];
+            }
+        }
+        ev[1 + 2 * an] = g0;
+        ev[2 + 2 * an] = g1;
+        double *h = ev + 1 + 2 * (size_t)n_ant + 3 * (size_t)an;
+        h[0] = h0; h[1] = h1; h[2] = h2;
+    }
+    (void)pairs;
+}
+
+}  // namespace
+
+cudaError_t launch_eval(const EvalArgs &a, bool predict, cudaStream_t s) {
+    const int threads = a.t_tile * a.c_group;
+    const int blocks = a.n_bl * a.n_cg * a.n_tt;
+    const size_t dyn = sizeof(float2) * (size_t)a.c_group * a.max_tab_len;
+    if (predict) {
+        eval_kernel<true><<<blocks, threads, dyn, s>>>(a);
+    } else {
+        eval_kernel<false><<<blocks, threads, dyn, s>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t set_eval_smem(size_t dyn) {
+    cudaError_t e = cudaFuncSetAttribute(eval_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(eval_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+}
+
+cudaError_t launch_reduce(const double *partials, int n_bl, int bricks_per_bl, const int2 *pairs,
+                          int n_ant, double *blsum, double *ev, const int *skip, cudaStream_t s) {
+    reduce_kernel<<<1, kMaxThreads, 0, s>>>(partials, n_bl, bricks_per_bl, pairs, n_ant, blsum, ev, skip);
+    return cudaGetLastError();
+}
+
+}  // namespace psc

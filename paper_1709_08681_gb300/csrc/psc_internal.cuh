@@ -1,0 +1,83 @@
+// Internal declarations of the Pointing SelfCal CUDA library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "psc.h"
+
+namespace psc {
+
+constexpr double kC = 299792458.0;
+constexpr int kTile = 64;          // staged grid tile: kTile x kTile complex64 cells
+constexpr int kRed = 15;           // per-baseline sums: chi2, g_i(2), g_j(2), H_ii(3), H_jj(3), H_ij(4)
+constexpr int kMaxThreads = 256;   // fused-kernel block size upper bound
+
+// Per-channel constants, built once per context.
+struct ChanConst {
+    double uv_scale;   // nu / (c du): metres of baseline -> grid cells
+    float alpha2;      // alpha(nu)^2 (rad^-2)
+    float rho_max;     // (len - 1) / ov: taps at rho >= rho_max (cells) get A° = 0
+    int tab_off;       // first table entry (float2 units)
+    int tab_len;       // len
+};
+
+// Arguments of the fused evaluation kernel (one launch covers one context).
+struct EvalArgs {
+    const double *uvw;         // [nt][nbl][3] metres
+    const float2 *grid;        // [ng][ng] V° (complex64)
+    const ChanConst *chan;     // [nc]
+    const float2 *tabs;        // radial tables: (A°(n), A°(n+1) - A°(n)) pairs
+    const int2 *pairs;         // [nbl] antenna (i, j)
+    const double *lm;          // [n_ant][2] offsets of this evaluation
+    const float2 *vis_obs;     // reduce mode: [nt][nbl][nc]
+    const float *w;            // reduce mode: weights or nullptr (= 1)
+    float w_scale;
+    float2 *vis_out;           // predict mode: [nt][nbl][nc]
+    float2 *dvis_out;          // predict mode: nullptr or [4][nt][nbl][nc]
+    double *partials;          // reduce mode: [n_bricks][kRed]
+    const int *skip;           // nullptr or device flag: nonzero = solver stopped, do nothing
+    int n_bl, nt, nc, ng, support, ov;
+    float du;                  // grid cell (wavelengths)
+    int t_tile, c_group, n_tt, n_cg;
+    int decorrelation;
+    int max_tab_len;           // longest table among the channels (for shared staging)
+};
+
+// Solver state kept on the device between iterations.
+struct LMState {
+    int n_iter, n_eval, reason, done;
+    double lam, chi2;
+    // options
+    int max_iter, mode;
+    double lam_max, lam_min, step_tol, chi2_rtol, block_gain;
+};
+
+// Workspace pointers of the solver (device).
+struct LMArgs {
+    LMState *st;
+    double *lm_cur;            // [n_ant][2] accepted offsets
+    double *lm_trial;          // [n_ant][2] offsets of the next evaluation (EvalArgs::lm)
+    const double *ev;          // evaluation at lm_trial: chi2 | g[2n] | H[3n] | X[4 nbl]
+    double *cur;               // same layout, accepted evaluation
+    double *mat;               // [2n][2n] scratch for the damped full system
+    double *rhs;               // [2n] scratch
+    const int2 *pairs;
+    int n_ant, n_bl;
+};
+
+__host__ __device__ inline size_t ev_len(int n_ant, int n_bl) { return 1 + 2 * (size_t)n_ant + 3 * (size_t)n_ant + 4 * (size_t)n_bl; }
+
+// Launchers (defined in the .cu files).
+cudaError_t launch_eval(const EvalArgs &a, bool predict, cudaStream_t s);
+cudaError_t launch_reduce(const double *partials, int n_bl, int bricks_per_bl, const int2 *pairs,
+                          int n_ant, double *blsum, double *ev, const int *skip, cudaStream_t s);
+cudaError_t launch_tables(const psc_aperture &ap, const double *freq_dev, int nc, double du, int ov,
+                          int support, const int *tab_off_dev, const int *tab_len_dev, float2 *tabs,
+                          cudaStream_t s);
+cudaError_t launch_lm_update(const LMArgs &a, cudaStream_t s);
+cudaError_t launch_lm_restart(const LMArgs &a, const LMState *st0, const double *lm0, cudaStream_t s);
+cudaError_t launch_model_grid(int n_img, int n_grid, const float *image, float2 *tmp, float2 *twiddle,
+                              float2 *grid_out, cudaStream_t s);
+
+}  // namespace psc

@@ -1,0 +1,69 @@
+"""Device-resident setup of a workload for the C ABI.
+
+Uploads the inputs of a ``inputs.Workload`` with torch (device memory and
+streams only), builds the model grid with ``psc_model_grid`` and creates one
+``psc_ctx`` per solution interval (each borrows a time slice of the shared
+uvw array and the shared grid).  ``simulate`` predicts observed visibilities
+with the GPU predictor at the workload's true offsets and adds the seeded
+thermal noise drawn by ``inputs`` -- the way the paper simulates data
+(Sec. 4.1), with the predictor standing in for its direct Fourier transform.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import _abi
+from .inputs import Workload
+
+
+class Session:
+    def __init__(self, wl: Workload, device: str = "cuda:0", stream=None, grid=None):
+        self.wl = wl
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.uvw = torch.from_numpy(np.ascontiguousarray(wl.uvw_m)).to(self.device)
+        n_img = wl.image.shape[0]
+        self.grid_args = dict(n_img=n_img, n_grid=wl.n_grid, cell_rad=wl.cell_rad, support=wl.support,
+                              oversample=wl.oversample)
+        if grid is None:
+            img = torch.from_numpy(np.ascontiguousarray(wl.image, dtype=np.float32)).to(self.device)
+            self.grid = torch.empty((wl.n_grid, wl.n_grid), dtype=torch.complex64, device=self.device)
+            _abi.psc_model_grid(n_img, wl.n_grid, wl.cell_rad, wl.support, wl.oversample, img, self.grid,
+                                self.stream)
+            del img
+        else:
+            self.grid = grid
+        self.ctxs = []
+        row = wl.n_bl * 3 * 8
+        for (t0, nt) in wl.intervals:
+            self.ctxs.append(_abi.Context(
+                wl.n_ant, nt, wl.n_chan, self.uvw.data_ptr() + t0 * row, wl.freq_hz, wl.ap_kind, wl.diam_m,
+                wl.alpha_per_dlambda, wl.decorrelation, n_img, wl.n_grid, wl.cell_rad, wl.support,
+                wl.oversample, self.grid.data_ptr(), self.stream))
+
+    def vis_slice(self, vis: torch.Tensor, k: int) -> torch.Tensor:
+        t0, nt = self.wl.intervals[k]
+        return vis[t0:t0 + nt]
+
+    def empty_vis(self) -> torch.Tensor:
+        return torch.empty((self.wl.n_time, self.wl.n_bl, self.wl.n_chan), dtype=torch.complex64, device=self.device)
+
+    def predict(self, lm_per_interval) -> torch.Tensor:
+        out = self.empty_vis()
+        for k, ctx in enumerate(self.ctxs):
+            ctx.psc_predict(lm_per_interval[k], self.vis_slice(out, k))
+        return out
+
+    def simulate(self, noise: bool = True, noise_stream: int = 5) -> torch.Tensor:
+        """Observed visibilities at the true offsets plus thermal noise."""
+        v = self.predict(self.wl.lm_true)
+        if noise and self.wl.sigma_noise > 0:
+            n = torch.from_numpy(self.wl.noise(noise_stream)).to(self.device)
+            v += n
+        return v
+
+    def close(self):
+        for c in self.ctxs:
+            c.close()
+        self.ctxs = []

@@ -1,0 +1,231 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances: visibilities and their derivatives within a relative L2 error of
+1e-5 (FP32 complex against FP64); chi^2 and the normal blocks to the same
+relative level; the gradient, which is a sum of terms of both signs, to 1e-5
+of the sum of the magnitudes of its terms; solved offsets within 0.1 arcsec
+of the oracle's solution.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1709_08681_gb300 import _abi, inputs as I
+from oracle import lm as LM, psc
+
+import cases
+from gpu_cases import GpuProblem
+
+TOL_V = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _need_gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _rel(a, b):
+    return cases.rel_l2(a, b)
+
+
+@pytest.mark.parametrize("spec", [cases.GAUSS_SMALL, cases.DISK_SMALL])
+def test_model_grid_matches_oracle(spec):
+    m, _, _, img = cases.problem(spec)
+    gp = GpuProblem(m, img)
+    G = gp.grid.cpu().numpy()
+    assert _rel(G, m.grid) < 1e-6
+
+
+def test_model_grid_dense_random_image():
+    """A dense image with both signs, ragged against the 64-wide GEMM tiles."""
+    from oracle import model_grid
+    rng = np.random.default_rng(5)
+    N, Ng = 72, 200
+    img = rng.normal(size=(N, N)).astype(np.float32)
+    ref = model_grid.grid_from_image(img.astype(np.float64), Ng)
+    out = torch.empty((Ng, Ng), dtype=torch.complex64, device="cuda:0")
+    _abi.psc_model_grid(N, Ng, 1e-4, 32, 20, torch.from_numpy(img).cuda(), out)
+    assert _rel(out.cpu().numpy(), ref) < 1e-6
+
+
+# (spec, n_ant, n_time, freqs, t_tile, c_group): several tiles and ragged tails
+PREDICT_CASES = [
+    (cases.DISK_SMALL, 7, 40, (1.2e9, 1.3e9, 1.4e9, 1.5e9, 1.6e9), 32, 4),
+    (cases.DISK_SMALL, 5, 9, (1.4e9,), 8, 4),
+    (cases.GAUSS_SMALL, 6, 20, (1.3e9, 1.4e9, 1.45e9), 16, 2),
+    (cases.DISK_SMALL, 2, 1, (1.4e9,), 32, 4),
+]
+
+
+@pytest.mark.parametrize("case", PREDICT_CASES)
+def test_predict_matches_oracle(case):
+    spec, n_ant, nt, freqs, tt, cg = case
+    m, _, lm, img = cases.problem(spec, n_ant=n_ant, n_time=nt, freqs=freqs, sigma_arcsec=30.0)
+    V, dV = psc.predict(m, lm)
+    gp = GpuProblem(m, img, t_tile=tt, c_group=cg)
+    Vg, dVg = gp.predict(lm)
+    assert _rel(Vg, V) < TOL_V
+    for p in range(4):
+        assert _rel(dVg[p], dV[p]) < TOL_V, p
+
+
+def test_predict_with_the_oracle_grid():
+    """Isolates the degridder: same grid values on both sides (rounded to complex64)."""
+    m, _, lm, img = cases.problem(cases.DISK_SMALL, n_ant=6, n_time=12, freqs=(1.3e9, 1.4e9))
+    gp = GpuProblem(m, img, use_oracle_grid=True)
+    V, dV = psc.predict(m, lm)
+    Vg, dVg = gp.predict(lm)
+    assert _rel(Vg, V) < TOL_V
+    assert max(_rel(dVg[p], dV[p]) for p in range(4)) < TOL_V
+
+
+def test_unstaged_fallback_matches_oracle():
+    """Channels far apart in one block overflow the staging tile, so the
+    block reads the grid from global memory; results must not change."""
+    m, _, lm, img = cases.problem(cases.DISK_SMALL, n_ant=6, n_time=8, freqs=(1.0e9, 1.3e9, 1.6e9, 1.9e9),
+                                  sigma_arcsec=30.0, extent_m=600.0)
+    V, dV = psc.predict(m, lm)
+    gp = GpuProblem(m, img, t_tile=8, c_group=4)
+    Vg, dVg = gp.predict(lm)
+    assert _rel(Vg, V) < TOL_V
+    assert max(_rel(dVg[p], dV[p]) for p in range(4)) < TOL_V
+
+
+def test_zero_offset_invariant_bitwise():
+    """At zero offsets the decorrelation factor is one: both settings agree bit for bit."""
+    m, _, _, img = cases.problem(cases.DISK_SMALL, n_ant=6, n_time=12)
+    z = np.zeros((m.n_ant, 2))
+    a = GpuProblem(m, img).predict(z)
+    m0 = psc.Model(**{**m.__dict__, "decorrelation": 0})
+    b = GpuProblem(m0, img).predict(z)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def _obs(m, lmt, sigma=1e-3, seed=7):
+    V, _ = psc.predict(m, lmt, False)
+    vobs = (V + I.complex_noise(V.shape, sigma, seed)).astype(np.complex64)
+    w = np.full(V.shape, 1.0 / sigma ** 2, dtype=np.float32)
+    return vobs, w
+
+
+@pytest.mark.parametrize("case", PREDICT_CASES[:3])
+def test_residual_grad_matches_oracle(case):
+    spec, n_ant, nt, freqs, tt, cg = case
+    m, _, lmt, img = cases.problem(spec, n_ant=n_ant, n_time=nt, freqs=freqs, sigma_arcsec=30.0)
+    vobs, w = _obs(m, lmt)
+    lm = 0.5 * lmt
+    chi2, g, H, X = psc.chi2_grad_normal(m, lm, vobs, w)
+    gp = GpuProblem(m, img, t_tile=tt, c_group=cg)
+    chi2g, gg, Hg, Xg = gp.ctx.psc_residual_grad(lm, gp.upload(vobs), gp.upload(w, torch.float32), 1.0, cross=True)
+    assert abs(chi2g - chi2) < TOL_V * chi2
+    # gradient scale: sum over visibilities of |2 w R dV|
+    V, dV = psc.predict(m, lm)
+    gscale = 2.0 * np.sum(w[None] * np.abs(vobs - V)[None] * np.abs(dV))
+    assert np.max(np.abs(gg - g)) < TOL_V * gscale
+    assert np.max(np.abs(Hg - H)) < TOL_V * np.max(np.abs(H))
+    assert np.max(np.abs(Xg - X)) < TOL_V * np.max(np.abs(H))
+
+
+def test_weight_scale_and_null_weights():
+    m, _, lmt, img = cases.problem(cases.DISK_SMALL, n_ant=5, n_time=10)
+    vobs, _ = _obs(m, lmt)
+    gp = GpuProblem(m, img)
+    a = gp.ctx.psc_residual_grad(0 * lmt, gp.upload(vobs), None, 4.0)
+    b = gp.ctx.psc_residual_grad(0 * lmt, gp.upload(vobs), gp.upload(np.ones(vobs.shape), torch.float32), 1.0)
+    assert abs(a[0] - 4.0 * b[0]) < 1e-6 * a[0]
+    assert np.allclose(a[1], 4.0 * b[1], rtol=1e-6, atol=0)
+
+
+def _oracle_solve(m, vobs, w, mode="full"):
+    def ev(p):
+        c, g, H, X = psc.chi2_grad_normal(m, p, vobs, w)
+        if mode == "block":
+            return c, g, H
+        G, A = psc.assemble_full(m.n_ant, g, H, X)
+        return c, G, A
+    if mode == "block":
+        return LM.solve_block(ev, np.zeros((m.n_ant, 2)), LM.Options(max_iter=200))
+    return LM.solve_full(ev, np.zeros((m.n_ant, 2)))
+
+
+@pytest.mark.parametrize("spec", [cases.DISK_SMALL, cases.GAUSS_SMALL])
+def test_solve_matches_oracle(spec):
+    m, _, lmt, img = cases.problem(spec, n_ant=7, n_time=12, freqs=(1.3e9, 1.4e9), n_src=8)
+    vobs, w = _obs(m, lmt)
+    sol_o, rep_o = _oracle_solve(m, vobs, w)
+    gp = GpuProblem(m, img)
+    sol_g, rep_g = gp.ctx.psc_solve_offsets(gp.upload(vobs), gp.upload(w, torch.float32), 1.0)
+    assert _abi.STOP_REASONS[rep_g.reason] in ("step", "chi2")
+    assert np.max(np.abs(sol_g - sol_o)) < 0.1 * I.ARCSEC
+    assert abs(rep_g.chi2 - rep_o.chi2) < 1e-4 * rep_o.chi2
+
+
+def test_noiseless_recovery_on_gpu():
+    m, _, lmt, img = cases.problem(cases.DISK_SMALL, n_ant=6, n_time=10, n_src=8)
+    V, _ = psc.predict(m, lmt, False)
+    gp = GpuProblem(m, img)
+    sol, rep = gp.ctx.psc_solve_offsets(gp.upload(V.astype(np.complex64)), None, 1e6)
+    assert np.max(np.abs(sol - lmt)) < 0.1 * I.ARCSEC
+
+
+def test_block_mode_matches_oracle():
+    m, _, lmt, img = cases.problem(cases.DISK_SMALL, n_ant=6, n_time=10, n_src=8)
+    vobs, w = _obs(m, lmt)
+    sol_o, rep_o = _oracle_solve(m, vobs, w, "block")
+    gp = GpuProblem(m, img)
+    o = _abi.psc_solve_opts_default()
+    o.mode = _abi.PSC_LM_BLOCK
+    o.max_iter = 200
+    sol_g, rep_g = gp.ctx.psc_solve_offsets(gp.upload(vobs), gp.upload(w, torch.float32), 1.0, opts=o)
+    assert np.max(np.abs(sol_g - sol_o)) < 0.1 * I.ARCSEC
+
+
+def test_lm_split_calls_equal_solve():
+    m, _, lmt, img = cases.problem(cases.DISK_SMALL, n_ant=6, n_time=10, n_src=8)
+    vobs, w = _obs(m, lmt)
+    gp = GpuProblem(m, img)
+    dv, dw = gp.upload(vobs), gp.upload(w, torch.float32)
+    sol_a, rep_a = gp.ctx.psc_solve_offsets(dv, dw, 1.0)
+    gp.ctx.psc_lm_begin(np.zeros((m.n_ant, 2)))
+    gp.ctx.psc_lm_iterate(dv, dw, 1.0, 60)
+    sol_b, rep_b = gp.ctx.psc_lm_end()
+    assert np.array_equal(sol_a, sol_b)
+    assert rep_a.n_iter == rep_b.n_iter and rep_a.reason == rep_b.reason
+
+
+def test_argument_errors_are_reported():
+    m, _, lmt, img = cases.problem(cases.DISK_SMALL, n_ant=4, n_time=4)
+    gp = GpuProblem(m, img)
+    with pytest.raises(_abi.PscError) as e:
+        gp.ctx.psc_set_tiling(12, 4)
+    with pytest.raises(_abi.PscError):
+        gp.ctx.psc_set_tiling(8, 1)
+    assert e.value.status == _abi.PSC_ERR_ARG
+    with pytest.raises(_abi.PscError):
+        gp.ctx.psc_residual_grad(lmt, gp.upload(np.zeros(gp.shape, np.complex64)), None, -1.0)
+
+
+def test_visibilities_on_and_near_grid_nodes():
+    """Taps at tiny radius (a visibility within 1e-4..0.5 cells of a grid
+    node) exercise the table lookup at t = rho * ov < 0.5."""
+    m, _, lm, img = cases.problem(cases.DISK_SMALL, n_ant=4, n_time=8)
+    ng, du = m.grid.shape[0], m.du
+    f = m.freq_hz[0]
+    fr = np.array([0.0, 1e-4, 0.004, 0.02, 0.4999, 0.5, 0.9996, 0.99999])
+    uvw = np.array(m.uvw_m)
+    for t in range(uvw.shape[0]):
+        for b in range(uvw.shape[1]):
+            for ax in (0, 1):
+                x = uvw[t, b, ax] * f / 299_792_458.0 / du
+                xs = np.floor(x) + fr[(t + b + ax) % len(fr)]
+                uvw[t, b, ax] = xs * du * 299_792_458.0 / f
+    m2 = psc.Model(**{**m.__dict__, "uvw_m": uvw})
+    V, dV = psc.predict(m2, lm)
+    Vg, dVg = GpuProblem(m2, img).predict(lm)
+    assert _rel(Vg, V) < TOL_V
+    assert max(_rel(dVg[p], dV[p]) for p in range(4)) < TOL_V
