@@ -24,7 +24,8 @@ STOP_REASONS = {0: "none", 1: "step", 2: "chi2", 3: "lambda", 4: "max_iter", 5: 
 
 EXPORTS = ("psc_solve_opts_default", "psc_model_grid", "psc_create", "psc_destroy", "psc_last_error",
            "psc_predict", "psc_residual_grad", "psc_solve_offsets", "psc_lm_begin", "psc_lm_iterate",
-           "psc_lm_end", "psc_lm_restart", "psc_set_tiling", "psc_profile", "psc_profile_read")
+           "psc_lm_end", "psc_lm_restart", "psc_set_tiling", "psc_profile", "psc_profile_read",
+           "psc_residual_grad_noalloc")
 
 
 class PscError(RuntimeError):
@@ -92,6 +93,9 @@ def lib():
             "psc_set_tiling": (ctypes.c_int, [_V, ctypes.c_int, ctypes.c_int]),
             "psc_profile": (ctypes.c_int, [_V, ctypes.c_int]),
             "psc_profile_read": (ctypes.c_int, [_V, _D, ctypes.POINTER(ctypes.c_int)]),
+            "psc_residual_grad_noalloc": (ctypes.c_int, [ctypes.POINTER(psc_obs), ctypes.POINTER(psc_aperture),
+                                                         ctypes.POINTER(psc_grid_desc), _V, _D, _V, _V, ctypes.c_double,
+                                                         _D, _D, _D, _D, _V]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -137,6 +141,28 @@ def psc_solve_opts_default() -> psc_solve_opts:
 def psc_model_grid(n_img, n_grid, cell_rad, support, oversample, image_dev, grid_out, stream=None):
     gd = psc_grid_desc(n_img, n_grid, cell_rad, support, oversample)
     _check(lib().psc_model_grid(ctypes.byref(gd), _ptr(image_dev), _ptr(grid_out), _stream(stream)))
+
+
+def psc_residual_grad_noalloc(n_ant, n_time, n_chan, uvw_dev, freq_hz, ap_kind, diam_m, alpha_per_dlambda,
+                              decorrelation, n_img, n_grid, cell_rad, support, oversample, grid_dev, lm, vis_obs,
+                              w=None, w_scale=1.0, cross=False, stream=None):
+    """Allocation-free fused evaluation (no psc_ctx; scratch in the
+    library's static device array).  Returns (chi2, g, H[, X])."""
+    freq = np.ascontiguousarray(freq_hz, dtype=np.float64)
+    obs = psc_obs(int(n_ant), int(n_time), int(n_chan), _ptr(uvw_dev), _dp(freq))
+    kind = {"disk": PSC_AP_DISK, "gauss": PSC_AP_GAUSS}.get(ap_kind, ap_kind)
+    ap = psc_aperture(int(kind), float(diam_m), float(alpha_per_dlambda), int(decorrelation))
+    gd = psc_grid_desc(int(n_img), int(n_grid), float(cell_rad), int(support), int(oversample))
+    lm = np.ascontiguousarray(lm, dtype=np.float64)
+    n_bl = int(n_ant) * (int(n_ant) - 1) // 2
+    chi2 = np.zeros(1)
+    g = np.zeros((int(n_ant), 2))
+    H = np.zeros((int(n_ant), 3))
+    X = np.zeros((n_bl, 4)) if cross else None
+    _check(lib().psc_residual_grad_noalloc(ctypes.byref(obs), ctypes.byref(ap), ctypes.byref(gd), _ptr(grid_dev),
+                                           _dp(lm), _ptr(vis_obs), _ptr(w), float(w_scale), _dp(chi2), _dp(g),
+                                           _dp(H), _dp(X) if cross else None, _stream(stream)))
+    return (float(chi2[0]), g, H, X) if cross else (float(chi2[0]), g, H)
 
 
 class Context:

@@ -10,10 +10,6 @@
 
 #include "psc_internal.cuh"
 
-namespace psc {
-cudaError_t set_eval_smem(size_t dyn);
-}
-
 using namespace psc;
 
 struct psc_ctx {
@@ -62,6 +58,15 @@ psc_status fail(psc_ctx *ctx, psc_status st, const std::string &msg) {
     else g_err = msg;
     return st;
 }
+
+}  // namespace
+
+psc_status psc::set_global_error(psc_status st, const char *msg) {
+    g_err = msg;
+    return st;
+}
+
+namespace {
 
 psc_status cuda_fail(psc_ctx *ctx, cudaError_t e, const char *what) {
     std::string m = std::string(what) + ": " + cudaGetErrorString(e);

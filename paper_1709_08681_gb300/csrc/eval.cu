@@ -346,10 +346,24 @@ cudaError_t launch_eval(const EvalArgs &a, bool predict, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// Raises the fused kernel's dynamic shared-memory limit to everything the
+// device allows beyond its static shared memory (never lowers it, so contexts
+// with different channel groups can share the kernel), after checking that
+// `dyn` bytes fit.
 cudaError_t set_eval_smem(size_t dyn) {
-    cudaError_t e = cudaFuncSetAttribute(eval_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(eval_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    cudaFuncAttributes fa{};
+    e = cudaFuncGetAttributes(&fa, eval_kernel<false>);
+    if (e != cudaSuccess) return e;
+    const size_t allowed = (size_t)optin > fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes : 0;
+    if (dyn > allowed) return cudaErrorInvalidValue;
+    e = cudaFuncSetAttribute(eval_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)allowed);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(eval_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)allowed);
 }
 
 cudaError_t launch_reduce(const double *partials, int n_bl, int bricks_per_bl, const int2 *pairs,

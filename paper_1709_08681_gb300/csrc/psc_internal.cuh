@@ -77,6 +77,9 @@ cudaError_t launch_tables(const psc_aperture &ap, const double *freq_dev, int nc
                           cudaStream_t s);
 cudaError_t launch_lm_update(const LMArgs &a, cudaStream_t s);
 cudaError_t launch_lm_restart(const LMArgs &a, const LMState *st0, const double *lm0, cudaStream_t s);
+cudaError_t set_eval_smem(size_t dyn);
+// Records msg as the context-free last error (psc_last_error(NULL)); returns st.
+psc_status set_global_error(psc_status st, const char *msg);
 cudaError_t launch_model_grid(int n_img, int n_grid, const float *image, float2 *tmp, float2 *twiddle,
                               float2 *grid_out, cudaStream_t s);
 
