@@ -32,6 +32,7 @@ struct psc_ctx {
     double *d_lm_trial = nullptr;
     double *d_lm_cur = nullptr;
     double *d_mat = nullptr;
+    float *d_mat32 = nullptr;
     double *d_rhs = nullptr;
     LMState *d_state = nullptr;
     LMState *d_state0 = nullptr; // state written by psc_lm_begin (for psc_lm_restart)
@@ -89,7 +90,7 @@ void free_ctx(psc_ctx *c) {
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     cudaFree(c->d_chan); cudaFree(c->d_tabs); cudaFree(c->d_pairs); cudaFree(c->d_partials);
     cudaFree(c->d_blsum); cudaFree(c->d_ev); cudaFree(c->d_cur); cudaFree(c->d_lm_trial);
-    cudaFree(c->d_lm_cur); cudaFree(c->d_mat); cudaFree(c->d_rhs); cudaFree(c->d_state);
+    cudaFree(c->d_lm_cur); cudaFree(c->d_mat); cudaFree(c->d_mat32); cudaFree(c->d_rhs); cudaFree(c->d_state);
     cudaFree(c->d_state0); cudaFree(c->d_lm0);
     delete c;
 }
@@ -142,6 +143,7 @@ LMArgs lm_args(const psc_ctx *c) {
     a.ev = c->d_ev;
     a.cur = c->d_cur;
     a.mat = c->d_mat;
+    a.mat32 = c->d_mat32;
     a.rhs = c->d_rhs;
     a.pairs = c->d_pairs;
     a.n_ant = c->n_ant;
@@ -290,6 +292,7 @@ psc_status psc_create(psc_ctx **out, const psc_obs *obs, const psc_aperture *ap,
     if (e == cudaSuccess) e = dalloc(&c->d_lm_trial, n2);
     if (e == cudaSuccess) e = dalloc(&c->d_lm_cur, n2);
     if (e == cudaSuccess) e = dalloc(&c->d_mat, (size_t)n2 * n2);
+    if (e == cudaSuccess) e = dalloc(&c->d_mat32, (size_t)n2 * n2);
     if (e == cudaSuccess) e = dalloc(&c->d_rhs, n2);
     if (e == cudaSuccess) e = dalloc(&c->d_state, 1);
     if (e == cudaSuccess) e = dalloc(&c->d_state0, 1);
@@ -315,8 +318,9 @@ psc_status psc_create(psc_ctx **out, const psc_obs *obs, const psc_aperture *ap,
     }
     c->d_done = &c->d_state->done;
     c->h_ev.resize(evn);
-    // room for the tables of the widest channel group
-    e = set_eval_smem(sizeof(float2) * (size_t)8 * c->max_tab_len);
+    // room for the tables of the widest channel group, and the LM layouts
+    e = set_eval_smem(eval_dyn_smem(8, c->max_tab_len));
+    if (e == cudaSuccess) e = lm_prepare(c->n_ant);
     if (e != cudaSuccess) { psc_status st = cuda_fail(nullptr, e, "psc_create: shared memory"); free_ctx(c); return st; }
     *out = c;
     return PSC_OK;

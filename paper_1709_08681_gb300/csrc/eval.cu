@@ -15,11 +15,18 @@
 // exp(i pi (u_k - u_o) L) exp(-i pi (u_g - u_o) L) for any origin u_o, so the
 // staged cells are pre-multiplied by the second factor (per cell, once per
 // block) and each visibility applies the first factor once; the inner loop
-// over taps then only needs the real radial A° and five FMAs per tap.  Taps
-// outside the disk's support are not visited (their A° is zero by the table
-// rule).  If a brick's footprint does not fit the staging tile, the block
-// falls back to reading the grid from global memory with the ramp applied
-// per tap (same arithmetic, slower).
+// over taps then needs only the real radial A° and five FMAs per tap.  Taps
+// outside the aperture's support are not visited (their A° is zero by the
+// table rule).  If a brick's footprint does not fit the staging tile, the
+// block falls back to reading the grid from global memory with the ramp
+// applied per tap (same arithmetic, slower).
+//
+// Inner loop per tap (rho in units of table samples, t = rho * ov):
+//   s2 = dxo^2 + dyo^2 (dxo = dx ov, dyo^2 carries a 1e-20 floor so s2 > 0),
+//   t = s2 * rsqrt(s2), n = floor(t) by a round-toward-zero add of 2^23 whose
+//   bit pattern also gives the table address, A° = value + f * slope, then
+//   P += A° G', Q += (A° dxo) G'.  Tables are padded with zero entries so no
+//   index clamp is needed (taps are limited to rho < rho_max).
 #include <climits>
 
 #include "psc_internal.cuh"
@@ -27,27 +34,51 @@
 namespace psc {
 namespace {
 
+constexpr int kTabPad = 2;     // zero entries after each staged table
+
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
-// A°(rho) for t = rho * ov >= 0 from a table of (A°(n), A°(n+1) - A°(n)) pairs
-// whose last entry is (0, 0).  floor(t) is taken exactly by adding 2^23 with
-// round-toward-zero (valid for 0 <= t < 2^23): the sum lands on the integer
-// floor(t) + 2^23, whose low mantissa bits are floor(t).
-__device__ __forceinline__ float tab_lookup(const float2 *tab, int len, float t) {
-    const float tf = __fadd_rz(t, 8388608.0f);
-    int n = __float_as_int(tf) - 0x4B000000;
-    const float f = t - (tf - 8388608.0f);
-    n = min(n, len - 1);
-    const float2 e = tab[n];
-    return fmaf(f, e.y, e.x);
+__device__ __forceinline__ float rsqrt_fast(float x) {
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ float2 lds_f2(unsigned addr) {
+    float2 v;
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(addr));
+    return v;
+}
+
+// One row of taps: a_n consecutive staged cells starting at `row`, first tap
+// at dxo (= dx * ov), table at shared address tab_adj + (0x4B000000 << 3).
+// Accumulates P = sum A G' and Q = sum A dxo G'.
+__device__ __forceinline__ void row_taps(const float2 *__restrict__ row, int a_n, float dxo, float dyo2, float ov,
+                                         unsigned tab_adj, float &pr, float &pi, float &qr, float &qi) {
+#pragma unroll 4
+    for (int k = 0; k < a_n; ++k) {
+        const float s2 = fmaf(dxo, dxo, dyo2);
+        const float t = s2 * rsqrt_fast(s2);
+        const float tf = __fadd_rz(t, 8388608.0f);             // floor(t) + 2^23
+        const float2 e = lds_f2(tab_adj + ((unsigned)__float_as_int(tf) << 3));
+        const float f = t - (tf - 8388608.0f);
+        const float A = fmaf(f, e.y, e.x);
+        const float2 g = row[k];
+        pr = fmaf(A, g.x, pr);
+        pi = fmaf(A, g.y, pi);
+        const float Ad = A * dxo;
+        qr = fmaf(Ad, g.x, qr);
+        qi = fmaf(Ad, g.y, qi);
+        dxo -= ov;
+    }
 }
 
 template <bool kPredict>
 __global__ void __launch_bounds__(kMaxThreads) eval_kernel(const EvalArgs a) {
     if (a.skip != nullptr && *a.skip) return;
-    extern __shared__ float2 s_tab[];                 // c_group * max_tab_len
+    extern __shared__ float2 s_tab[];                 // c_group * (max_tab_len + kTabPad)
     __shared__ float2 s_tile[kTile * kTile];
     __shared__ float2 s_phx[kTile], s_phy[kTile];
     __shared__ int s_box[4];
@@ -63,17 +94,22 @@ __global__ void __launch_bounds__(kMaxThreads) eval_kernel(const EvalArgs a) {
     const int t = tt * a.t_tile + lt;
     const int c = cgi * a.c_group + lc;
     const bool valid = lc < a.c_group && t < a.nt && c < a.nc;
+    const int tab_stride = a.max_tab_len + kTabPad;
 
-    const int2 ij = a.pairs[bl];
-    const double li = a.lm[2 * ij.x], mi = a.lm[2 * ij.x + 1];
-    const double lj = a.lm[2 * ij.y], mj = a.lm[2 * ij.y + 1];
-    const float L = (float)(li + lj), M = (float)(mi + mj);     // ramp: l_i + l_j, m_i + m_j
-    const float dL = (float)(li - lj), dM = (float)(mi - mj);   // l_i - l_j, m_i - m_j
-
+    // per-baseline constants, computed once per block in FP64
+    __shared__ float s_bl[4];
     if (tid == 0) {
+        const int2 ij = a.pairs[bl];
+        const double li = a.lm[2 * ij.x], mi = a.lm[2 * ij.x + 1];
+        const double lj = a.lm[2 * ij.y], mj = a.lm[2 * ij.y + 1];
+        s_bl[0] = (float)(li + lj);   // ramp: l_i + l_j
+        s_bl[1] = (float)(mi + mj);
+        s_bl[2] = (float)(li - lj);   // decorrelation: l_i - l_j
+        s_bl[3] = (float)(mi - mj);
         s_box[0] = INT_MAX; s_box[1] = INT_MIN; s_box[2] = INT_MAX; s_box[3] = INT_MIN;
     }
     __syncthreads();
+    const float L = s_bl[0], M = s_bl[1], dL = s_bl[2], dM = s_bl[3];
 
     // Grid position of this visibility: x = u / du + Ng/2 (cells), window
     // origin floor(x) - S/2 + 1.
@@ -92,10 +128,10 @@ __global__ void __launch_bounds__(kMaxThreads) eval_kernel(const EvalArgs a) {
         atomicMin(&s_box[0], ix0); atomicMax(&s_box[1], ix0);
         atomicMin(&s_box[2], iy0); atomicMax(&s_box[3], iy0);
     }
-    // radial tables of this block's channels
-    for (int k = tid; k < a.c_group * a.max_tab_len; k += blockDim.x) {
-        const int cc = cgi * a.c_group + k / a.max_tab_len;
-        const int n = k % a.max_tab_len;
+    // radial tables of this block's channels, zero-padded
+    for (int k = tid; k < a.c_group * tab_stride; k += blockDim.x) {
+        const int cc = cgi * a.c_group + k / tab_stride;
+        const int n = k % tab_stride;
         float2 v = make_float2(0.f, 0.f);
         if (cc < a.nc) {
             const ChanConst ch = a.chan[cc];
@@ -121,12 +157,22 @@ __global__ void __launch_bounds__(kMaxThreads) eval_kernel(const EvalArgs a) {
             s_phy[k] = make_float2(co, s);
         }
         __syncthreads();
-        for (int k = tid; k < ex * ey; k += blockDim.x) {
-            const int yy = k / ex, xx = k - yy * ex;
-            const int gx = bx0 + xx, gy = by0 + yy;
-            float2 g = make_float2(0.f, 0.f);
-            if (gx >= 0 && gx < a.ng && gy >= 0 && gy < a.ng) g = __ldg(&a.grid[(size_t)gy * a.ng + gx]);
-            s_tile[yy * kTile + xx] = cmul(g, cmul(s_phx[xx], s_phy[yy]));
+        // threads -> (column, row group) with shifts: 64 columns per pass for
+        // blocks of >= 64 threads, 32 for a 32-thread block (two passes);
+        // the row step blockDim >> cshift is >= 1 for every allowed block size
+        const int cshift = blockDim.x >= kTile ? 6 : 5;
+        const int cols = 1 << cshift;
+        const int rstep = blockDim.x >> cshift;
+        for (int xx = tid & (cols - 1); xx < kTile; xx += cols) {
+            const int gx = bx0 + xx;
+            const bool xin = xx < ex && gx >= 0 && gx < a.ng;
+            const float2 px = xin ? s_phx[xx] : make_float2(0.f, 0.f);
+            for (int yy = tid >> cshift; yy < ey; yy += rstep) {
+                const int gy = by0 + yy;
+                float2 g = make_float2(0.f, 0.f);
+                if (xin && gy >= 0 && gy < a.ng) g = __ldg(&a.grid[(size_t)gy * a.ng + gx]);
+                s_tile[yy * kTile + xx] = cmul(g, cmul(px, s_phy[yy]));
+            }
         }
         __syncthreads();
     }
@@ -139,35 +185,29 @@ __global__ void __launch_bounds__(kMaxThreads) eval_kernel(const EvalArgs a) {
     const float hy = fy + (float)(a.support / 2 - 1);
     if (valid) {
         const ChanConst ch = a.chan[c];
-        const float2 *tab = s_tab + lc * a.max_tab_len;
-        const int len = ch.tab_len;
+        const float2 *tab = s_tab + lc * tab_stride;
+        const unsigned tab_adj = (unsigned)__cvta_generic_to_shared(tab) - (0x4B000000u << 3);
         const float ov = (float)a.ov;
         const float rmax = ch.rho_max;
-        const int b_lo = max(0, (int)ceilf(hy - rmax) - 1);
-        const int b_hi = min(a.support - 1, (int)floorf(hy + rmax) + 1);
+        const float rmax2 = rmax * rmax;
+        const int b_lo = max(0, (int)floorf(hy - rmax) + 1);
+        const int b_hi = min(a.support - 1, (int)ceilf(hy + rmax) - 1);
         float sdx = 0.f, cdx = 0.f;
         if (!staged) sincospif(-a.du * L, &sdx, &cdx);     // per-column ramp step
         for (int b = b_lo; b <= b_hi; ++b) {
             const float dy = hy - (float)b;
-            if (fabsf(dy) >= rmax) continue;
-            const float r = sqrtf(fmaf(-dy, dy, rmax * rmax));
-            const int a_lo = max(0, (int)ceilf(hx - r) - 1);
-            const int a_hi = min(a.support - 1, (int)floorf(hx + r) + 1);
-            const float dy2 = dy * dy;
+            const float rem = rmax2 - dy * dy;
+            if (!(rem > 0.f)) continue;
+            const float r = rem * rsqrt_fast(rem);
+            const int a_lo = max(0, (int)floorf(hx - r) + 1);
+            const int a_hi = min(a.support - 1, (int)ceilf(hx + r) - 1);
+            const float dyo = dy * ov;
+            const float dyo2 = fmaf(dyo, dyo, 1e-20f);
             float pr = 0.f, pi = 0.f, qr = 0.f, qi = 0.f;
-            float dx = hx - (float)a_lo;
+            const float dxo = (hx - (float)a_lo) * ov;
             if (staged) {
-                const float2 *row = s_tile + (iy0 - oy + b) * kTile + (ix0 - ox);
-                for (int aa = a_lo; aa <= a_hi; ++aa, dx -= 1.f) {
-                    const float s = fmaxf(fmaf(dx, dx, dy2), 1e-30f);
-                    const float A = tab_lookup(tab, len, s * rsqrtf(s) * ov);
-                    const float2 g = row[aa];
-                    pr = fmaf(A, g.x, pr);
-                    pi = fmaf(A, g.y, pi);
-                    const float Ad = A * dx;
-                    qr = fmaf(Ad, g.x, qr);
-                    qi = fmaf(Ad, g.y, qi);
-                }
+                const float2 *row = s_tile + (iy0 - oy + b) * kTile + (ix0 - ox) + a_lo;
+                row_taps(row, a_hi - a_lo + 1, dxo, dyo2, ov, tab_adj, pr, pi, qr, qi);
             } else {
                 // ramp exp(-i pi du (a L + b M)) relative to this visibility's window origin
                 float sz, cz;
@@ -175,17 +215,21 @@ __global__ void __launch_bounds__(kMaxThreads) eval_kernel(const EvalArgs a) {
                 float2 z = make_float2(cz, sz);
                 const float2 step = make_float2(cdx, sdx);
                 const int gy = iy0 + b;
-                for (int aa = a_lo; aa <= a_hi; ++aa, dx -= 1.f) {
+                float dd = dxo;
+                for (int aa = a_lo; aa <= a_hi; ++aa, dd -= ov) {
                     const int gx = ix0 + aa;
                     float2 g = make_float2(0.f, 0.f);
                     if (gx >= 0 && gx < a.ng && gy >= 0 && gy < a.ng) g = __ldg(&a.grid[(size_t)gy * a.ng + gx]);
                     g = cmul(g, z);
                     z = cmul(z, step);
-                    const float s = fmaxf(fmaf(dx, dx, dy2), 1e-30f);
-                    const float A = tab_lookup(tab, len, s * rsqrtf(s) * ov);
+                    const float s2 = fmaf(dd, dd, dyo2);
+                    const float tv = s2 * rsqrt_fast(s2);
+                    const float tf = __fadd_rz(tv, 8388608.0f);
+                    const float2 e = lds_f2(tab_adj + ((unsigned)__float_as_int(tf) << 3));
+                    const float A = fmaf(tv - (tf - 8388608.0f), e.y, e.x);
                     pr = fmaf(A, g.x, pr);
                     pi = fmaf(A, g.y, pi);
-                    const float Ad = A * dx;
+                    const float Ad = A * dd;
                     qr = fmaf(Ad, g.x, qr);
                     qi = fmaf(Ad, g.y, qi);
                 }
@@ -195,6 +239,8 @@ __global__ void __launch_bounds__(kMaxThreads) eval_kernel(const EvalArgs a) {
             Sv.x = fmaf(dy, pr, Sv.x);
             Sv.y = fmaf(dy, pi, Sv.y);
         }
+        const float inv_ov = 1.0f / ov;
+        Su.x *= inv_ov; Su.y *= inv_ov;                  // Q was accumulated with dx * ov
     }
 
     // ---- epilogue: visibility half of the ramp, decorrelation, derivatives ----
@@ -257,49 +303,59 @@ __global__ void __launch_bounds__(kMaxThreads) eval_kernel(const EvalArgs a) {
         }
     }
     if constexpr (!kPredict) {
-    // ---- block reduction: FP32 within a warp, FP64 across warps ----
+        // ---- block reduction: FP32 within a warp, FP64 across warps ----
 #pragma unroll
-    for (int k = 0; k < kRed; ++k) {
-        float v = acc[k];
+        for (int k = 0; k < kRed; ++k) {
+            float v = acc[k];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        acc[k] = v;
-    }
-    const int warp = tid >> 5, lane = tid & 31;
-    if (lane == 0) {
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            acc[k] = v;
+        }
+        const int warp = tid >> 5, lane = tid & 31;
+        if (lane == 0) {
 #pragma unroll
-        for (int k = 0; k < kRed; ++k) s_red[warp][k] = (double)acc[k];
-    }
-    __syncthreads();
-    if (tid < kRed) {
-        double s = 0.0;
-        const int nw = (blockDim.x + 31) >> 5;
-        for (int wi = 0; wi < nw; ++wi) s += s_red[wi][tid];
-        a.partials[(size_t)brick * kRed + tid] = s;
-    }
+            for (int k = 0; k < kRed; ++k) s_red[warp][k] = (double)acc[k];
+        }
+        __syncthreads();
+        if (tid < kRed) {
+            double s = 0.0;
+            const int nw = (blockDim.x + 31) >> 5;
+            for (int wi = 0; wi < nw; ++wi) s += s_red[wi][tid];
+            a.partials[(size_t)tid * gridDim.x + brick] = s;      // [kRed][n_bricks]
+        }
     }
 }
 
-// Second stage: per-baseline sums over bricks, then per-antenna sums, all in
-// a fixed order (deterministic).  ev = chi2 | g[2n] | H[3n] | X[4 nbl].
-__global__ void reduce_kernel(const double *__restrict__ partials, int n_bl, int bpb,
-                              const int2 *__restrict__ pairs, int n_ant, double *__restrict__ blsum,
-                              double *__restrict__ ev, const int *skip) {
+// Second stage (a): per-baseline sums over its bricks, one warp per baseline,
+// a fixed butterfly order (deterministic).  partials is [kRed][n_bricks] with
+// the bricks of baseline bl at [bl * bpb, (bl + 1) * bpb).
+__global__ void bl_reduce_kernel(const double *__restrict__ partials, int n_bl, int bpb,
+                                 double *__restrict__ blsum, const int *skip) {
+    if (skip != nullptr && *skip) return;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp >= n_bl) return;
+    const size_t nb = (size_t)n_bl * bpb;
+    for (int k = 0; k < kRed; ++k) {
+        const double *p = partials + (size_t)k * nb + (size_t)warp * bpb;
+        double s = 0.0;
+        for (int b = lane; b < bpb; b += 32) s += p[b];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) blsum[(size_t)warp * kRed + k] = s;
+    }
+}
+
+// Second stage (b): chi^2, per-antenna gradient and diagonal blocks, cross
+// blocks; ev = chi2 | g[2n] | H[3n] | X[4 nbl].  One block, fixed order.
+__global__ void ev_kernel(const double *__restrict__ blsum, int n_bl, int n_ant, double *__restrict__ ev,
+                          const int *skip) {
     if (skip != nullptr && *skip) return;
     __shared__ double s_chi[kMaxThreads];
     const int tid = threadIdx.x;
     double chi = 0.0;
     for (int bl = tid; bl < n_bl; bl += blockDim.x) {
-        double s[kRed];
-#pragma unroll
-        for (int k = 0; k < kRed; ++k) s[k] = 0.0;
-        const double *p = partials + (size_t)bl * bpb * kRed;
-        for (int b = 0; b < bpb; ++b) {
-#pragma unroll
-            for (int k = 0; k < kRed; ++k) s[k] += p[(size_t)b * kRed + k];
-        }
-#pragma unroll
-        for (int k = 0; k < kRed; ++k) blsum[(size_t)bl * kRed + k] = s[k];
+        const double *s = blsum + (size_t)bl * kRed;
         chi += s[0];
         double *x = ev + 1 + 5 * (size_t)n_ant + 4 * (size_t)bl;
         x[0] = s[11]; x[1] = s[12]; x[2] = s[13]; x[3] = s[14];
@@ -329,15 +385,18 @@ __global__ void reduce_kernel(const double *__restrict__ partials, int n_bl, int
         double *h = ev + 1 + 2 * (size_t)n_ant + 3 * (size_t)an;
         h[0] = h0; h[1] = h1; h[2] = h2;
     }
-    (void)pairs;
 }
 
 }  // namespace
 
+size_t eval_dyn_smem(int c_group, int max_tab_len) {
+    return sizeof(float2) * (size_t)c_group * (max_tab_len + kTabPad);
+}
+
 cudaError_t launch_eval(const EvalArgs &a, bool predict, cudaStream_t s) {
     const int threads = a.t_tile * a.c_group;
     const int blocks = a.n_bl * a.n_cg * a.n_tt;
-    const size_t dyn = sizeof(float2) * (size_t)a.c_group * a.max_tab_len;
+    const size_t dyn = eval_dyn_smem(a.c_group, a.max_tab_len);
     if (predict) {
         eval_kernel<true><<<blocks, threads, dyn, s>>>(a);
     } else {
@@ -368,7 +427,13 @@ cudaError_t set_eval_smem(size_t dyn) {
 
 cudaError_t launch_reduce(const double *partials, int n_bl, int bricks_per_bl, const int2 *pairs,
                           int n_ant, double *blsum, double *ev, const int *skip, cudaStream_t s) {
-    reduce_kernel<<<1, kMaxThreads, 0, s>>>(partials, n_bl, bricks_per_bl, pairs, n_ant, blsum, ev, skip);
+    (void)pairs;
+    const int warps_per_block = 8;
+    bl_reduce_kernel<<<(n_bl + warps_per_block - 1) / warps_per_block, 32 * warps_per_block, 0, s>>>(
+        partials, n_bl, bricks_per_bl, blsum, skip);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    ev_kernel<<<1, kMaxThreads, 0, s>>>(blsum, n_bl, n_ant, ev, skip);
     return cudaGetLastError();
 }
 

@@ -1,15 +1,24 @@
-// Levenberg-Marquardt update on the device, FP64 (Algorithm 1's Terminate()
-// and f(), left to the minimiser by the paper, Sec. 2.2).
+// Levenberg-Marquardt update on the device (Algorithm 1's Terminate() and
+// f(), left to the minimiser by the paper, Sec. 2.2).
 //
 // One thread block per context.  After each fused evaluation at the trial
 // offsets it (1) accepts the trial if chi^2 went down (lam /= 10, floored at
 // lam_min) or rejects it (lam *= 10), (2) applies the stop rules, and (3) solves
 // the damped system (H + lam diag(H)) delta = -g for the next trial, either
-// over all 2 n_ant parameters (Cholesky of the full Gauss-Newton matrix:
-// per-antenna 2x2 diagonal blocks and one 2x2 cross block per baseline) or
-// per antenna from the diagonal block alone with the step scaled by the loop
-// gain block_gain.  Parameters whose diagonal is not positive (antennas with
-// no data) are held fixed.
+// over all 2 n_ant parameters (the full Gauss-Newton matrix: per-antenna 2x2
+// diagonal blocks and one 2x2 cross block per baseline) or per antenna from
+// the diagonal block alone with the step scaled by the loop gain block_gain.
+// Parameters whose diagonal is not positive (antennas with no data) are held
+// fixed.
+//
+// Precision.  The damped matrix and right-hand side are assembled in FP64.
+// GB300 runs FP64 at a small fraction of its FP32 rate, so the full system is
+// factored in FP32 (Cholesky) and the solution is refined in FP64: the
+// residual b - A x is formed in FP64 and the correction solved with the FP32
+// factor, until max|r| <= 1e-12 max|b| (at most 6 rounds).  That gives the
+// FP64 solution for any matrix whose condition number is well below 1e7.  If
+// the FP32 factorisation meets a non-positive pivot or the refinement does
+// not converge, the system is factored in FP64 instead.
 #include <math.h>
 
 #include "psc_internal.cuh"
@@ -18,6 +27,9 @@ namespace psc {
 namespace {
 
 constexpr int kLmThreads = 256;
+constexpr int kSmallN2 = 90;            // 2 n_ant up to this: matrices in shared memory
+constexpr int kRefineMax = 6;
+constexpr double kRefineTol = 1e-12;
 
 __device__ double block_max(double v, double *s) {
     const int tid = threadIdx.x;
@@ -32,7 +44,91 @@ __device__ double block_max(double v, double *s) {
     return r;
 }
 
-__global__ void __launch_bounds__(kLmThreads) lm_update_kernel(const LMArgs a) {
+// FP32 Cholesky A = L L^T in place (row-major, lower triangle), all threads
+// of the block.  Returns nonzero (uniformly) if a pivot is not positive.
+__device__ int chol32(float *A, int n) {
+    const int tid = threadIdx.x;
+    const int tx = tid & 15, ty = tid >> 4;            // 16 x 16 thread grid
+    int bad = 0;
+    for (int k = 0; k < n; ++k) {
+        const float d = A[(size_t)k * n + k];
+        const bool nonpos = !(d > 0.f);
+        bad |= nonpos;
+        const float inv = nonpos ? 1.f : rsqrtf(d);
+        for (int i = k + 1 + tid; i < n; i += blockDim.x) A[(size_t)i * n + k] *= inv;
+        __syncthreads();
+        for (int i = k + 1 + ty; i < n; i += 16) {
+            const float lik = A[(size_t)i * n + k];
+            for (int j = k + 1 + tx; j <= i; j += 16) A[(size_t)i * n + j] -= lik * A[(size_t)j * n + k];
+        }
+        __syncthreads();
+        if (tid == 0) A[(size_t)k * n + k] = nonpos ? 1.f : d * inv;
+    }
+    __syncthreads();
+    return bad;
+}
+
+// Solves L L^T y = y in place with the FP32 factor, warp 0 only.
+__device__ void solve32_warp(const float *L, int n, float *y) {
+    const int lane = threadIdx.x & 31;
+    for (int k = 0; k < n; ++k) {
+        const float yk = y[k] / L[(size_t)k * n + k];
+        __syncwarp();
+        if (lane == 0) y[k] = yk;
+        for (int i = k + 1 + lane; i < n; i += 32) y[i] -= L[(size_t)i * n + k] * yk;
+        __syncwarp();
+    }
+    for (int k = n - 1; k >= 0; --k) {
+        const float xk = y[k] / L[(size_t)k * n + k];
+        __syncwarp();
+        if (lane == 0) y[k] = xk;
+        for (int i = lane; i < k; i += 32) y[i] -= L[(size_t)k * n + i] * xk;
+        __syncwarp();
+    }
+}
+
+// FP64 Cholesky + solve of A x = b in place (x overwrites b), all threads.
+__device__ int chol64_solve(double *A, int n2, double *b) {
+    __shared__ int s_bad;
+    const int tid = threadIdx.x;
+    if (tid == 0) s_bad = 0;
+    __syncthreads();
+    for (int k = 0; k < n2; ++k) {
+        if (tid == 0) {
+            const double d = A[(size_t)k * n2 + k];
+            if (!(d > 0.0)) { s_bad = 1; A[(size_t)k * n2 + k] = 1.0; }
+            else A[(size_t)k * n2 + k] = sqrt(d);
+        }
+        __syncthreads();
+        const double lkk = A[(size_t)k * n2 + k];
+        for (int i = k + 1 + tid; i < n2; i += blockDim.x) A[(size_t)i * n2 + k] /= lkk;
+        __syncthreads();
+        const int tx = tid & 15, ty = tid >> 4;
+        for (int i = k + 1 + ty; i < n2; i += 16) {
+            const double lik = A[(size_t)i * n2 + k];
+            for (int j = k + 1 + tx; j <= i; j += 16) A[(size_t)i * n2 + j] -= lik * A[(size_t)j * n2 + k];
+        }
+        __syncthreads();
+    }
+    for (int k = 0; k < n2; ++k) {
+        if (tid == 0) b[k] /= A[(size_t)k * n2 + k];
+        __syncthreads();
+        const double yk = b[k];
+        for (int i = k + 1 + tid; i < n2; i += blockDim.x) b[i] -= A[(size_t)i * n2 + k] * yk;
+        __syncthreads();
+    }
+    for (int k = n2 - 1; k >= 0; --k) {
+        if (tid == 0) b[k] /= A[(size_t)k * n2 + k];
+        __syncthreads();
+        const double xk = b[k];
+        for (int i = tid; i < k; i += blockDim.x) b[i] -= A[(size_t)k * n2 + i] * xk;
+        __syncthreads();
+    }
+    return s_bad;
+}
+
+__global__ void __launch_bounds__(kLmThreads) lm_update_kernel(const LMArgs a, int small) {
+    extern __shared__ double s_dyn[];
     LMState *st = a.st;
     if (st->done) return;
     __shared__ int s_accept, s_stop;
@@ -100,8 +196,14 @@ __global__ void __launch_bounds__(kLmThreads) lm_update_kernel(const LMArgs a) {
         }
         __syncthreads();
     } else {
-        double *A = a.mat;                       // row-major [n2][n2]
-        // assemble H + lam diag(H)
+        // dynamic shared memory: [A64 | A32] (small systems only) then b, r (FP64), y32
+        double *A = small ? s_dyn : a.mat;
+        float *A32 = small ? (float *)(s_dyn + (size_t)n2 * n2) : a.mat32;
+        double *vb = small ? s_dyn + (size_t)n2 * n2 + ((size_t)n2 * n2 + 1) / 2 : s_dyn;
+        double *vr = vb + n2;
+        float *y32 = (float *)(vr + n2);
+
+        // assemble H + lam diag(H) (FP64, both triangles) and b = -g
         for (size_t k = tid; k < (size_t)n2 * n2; k += blockDim.x) A[k] = 0.0;
         __syncthreads();
         for (int an = tid; an < n; an += blockDim.x) {
@@ -111,8 +213,8 @@ __global__ void __launch_bounds__(kLmThreads) lm_update_kernel(const LMArgs a) {
             A[(size_t)p * n2 + p + 1] = hlm;
             A[(size_t)(p + 1) * n2 + p] = hlm;
             A[(size_t)(p + 1) * n2 + p + 1] = hmm * (1.0 + lam);
-            delta[p] = -g[p];
-            delta[p + 1] = -g[p + 1];
+            vb[p] = -g[p];
+            vb[p + 1] = -g[p + 1];
         }
         for (int bl = tid; bl < a.n_bl; bl += blockDim.x) {
             const int2 ij = a.pairs[bl];
@@ -132,41 +234,42 @@ __global__ void __launch_bounds__(kLmThreads) lm_update_kernel(const LMArgs a) {
         }
         __syncthreads();
         for (int p = tid; p < n2; p += blockDim.x) {
-            if (A[(size_t)p * n2 + p] == 0.0) { A[(size_t)p * n2 + p] = 1.0; delta[p] = 0.0; }
+            if (A[(size_t)p * n2 + p] == 0.0) { A[(size_t)p * n2 + p] = 1.0; vb[p] = 0.0; }
+            delta[p] = 0.0;
         }
         __syncthreads();
-        // Cholesky A = L L^T in place (lower triangle), right-looking
-        for (int k = 0; k < n2; ++k) {
-            if (tid == 0) {
-                const double d = A[(size_t)k * n2 + k];
-                if (!(d > 0.0)) { s_fail = 1; A[(size_t)k * n2 + k] = 1.0; }
-                else A[(size_t)k * n2 + k] = sqrt(d);
+        for (size_t k = tid; k < (size_t)n2 * n2; k += blockDim.x) A32[k] = (float)A[k];
+        __syncthreads();
+
+        const int bad = chol32(A32, n2);
+        double bmax = 0.0;
+        for (int p = tid; p < n2; p += blockDim.x) { bmax = fmax(bmax, fabs(vb[p])); vr[p] = vb[p]; }
+        bmax = block_max(bmax, s_tmp);
+        bool converged = false;
+        for (int it = 0; it < kRefineMax && !bad && !converged; ++it) {
+            for (int p = tid; p < n2; p += blockDim.x) y32[p] = (float)vr[p];
+            __syncthreads();
+            if (tid < 32) solve32_warp(A32, n2, y32);
+            __syncthreads();
+            for (int p = tid; p < n2; p += blockDim.x) delta[p] += (double)y32[p];
+            __syncthreads();
+            double rmax = 0.0;
+            for (int p = tid; p < n2; p += blockDim.x) {         // r = b - A x in FP64
+                double acc = vb[p];
+                const double *row = A + (size_t)p * n2;
+                for (int q = 0; q < n2; ++q) acc = fma(-row[q], delta[q], acc);
+                vr[p] = acc;
+                rmax = fmax(rmax, fabs(acc));
             }
-            __syncthreads();
-            const double lkk = A[(size_t)k * n2 + k];
-            for (int i = k + 1 + tid; i < n2; i += blockDim.x) A[(size_t)i * n2 + k] /= lkk;
-            __syncthreads();
-            const int m = n2 - k - 1;
-            for (int idx = tid; idx < m * m; idx += blockDim.x) {
-                const int i = k + 1 + idx / m, j = k + 1 + idx % m;
-                if (j <= i) A[(size_t)i * n2 + j] -= A[(size_t)i * n2 + k] * A[(size_t)j * n2 + k];
-            }
-            __syncthreads();
+            rmax = block_max(rmax, s_tmp);
+            converged = rmax <= kRefineTol * bmax;
         }
-        // forward: L y = -g
-        for (int k = 0; k < n2; ++k) {
-            if (tid == 0) delta[k] /= A[(size_t)k * n2 + k];
+        if (bad || !converged) {
+            // FP64 fallback: factor the FP64 matrix itself
+            for (int p = tid; p < n2; p += blockDim.x) delta[p] = vb[p];
             __syncthreads();
-            const double yk = delta[k];
-            for (int i = k + 1 + tid; i < n2; i += blockDim.x) delta[i] -= A[(size_t)i * n2 + k] * yk;
-            __syncthreads();
-        }
-        // backward: L^T x = y
-        for (int k = n2 - 1; k >= 0; --k) {
-            if (tid == 0) delta[k] /= A[(size_t)k * n2 + k];
-            __syncthreads();
-            const double xk = delta[k];
-            for (int i = tid; i < k; i += blockDim.x) delta[i] -= A[(size_t)k * n2 + i] * xk;
+            const int bad64 = chol64_solve(A, n2, delta);
+            if (bad64 && tid == 0) s_fail = 1;
             __syncthreads();
         }
     }
@@ -195,7 +298,22 @@ __global__ void lm_restart_kernel(const LMArgs a, const LMState *st0, const doub
     }
 }
 
+// Dynamic shared memory of the LM kernel: the FP64 matrix and its FP32 copy
+// for small systems, then b, r (FP64) and y (FP32), 2 n_ant each.
+size_t lm_dyn_smem(int n_ant) {
+    const size_t n2 = 2 * (size_t)n_ant;
+    const size_t vec = sizeof(double) * 2 * n2 + sizeof(float) * n2;
+    if ((int)n2 <= kSmallN2) return sizeof(double) * (n2 * n2 + (n2 * n2 + 1) / 2) + vec;
+    return vec;
+}
+
 }  // namespace
+
+cudaError_t lm_prepare(int n_ant) {
+    (void)n_ant;
+    const size_t most = lm_dyn_smem(kSmallN2 / 2) > lm_dyn_smem(512) ? lm_dyn_smem(kSmallN2 / 2) : lm_dyn_smem(512);
+    return cudaFuncSetAttribute(lm_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most);
+}
 
 cudaError_t launch_lm_restart(const LMArgs &a, const LMState *st0, const double *lm0, cudaStream_t s) {
     lm_restart_kernel<<<1, 128, 0, s>>>(a, st0, lm0);
@@ -203,7 +321,8 @@ cudaError_t launch_lm_restart(const LMArgs &a, const LMState *st0, const double 
 }
 
 cudaError_t launch_lm_update(const LMArgs &a, cudaStream_t s) {
-    lm_update_kernel<<<1, kLmThreads, 0, s>>>(a);
+    const int small = 2 * a.n_ant <= kSmallN2;
+    lm_update_kernel<<<1, kLmThreads, lm_dyn_smem(a.n_ant), s>>>(a, small);
     return cudaGetLastError();
 }
 

@@ -178,7 +178,7 @@ extern "C" psc_status psc_residual_grad_noalloc(const psc_obs *obs, const psc_ap
                                            gd->support, d_chan, d_toff, d_tlen, n_ant, d_pairs);
     NA_CUDA(cudaGetLastError());
     NA_CUDA(launch_tables(*ap, d_freq, nc, du, ov, gd->support, d_toff, d_tlen, d_tabs, s));
-    NA_CUDA(set_eval_smem(sizeof(float2) * (size_t)c_group * max_tab));
+    NA_CUDA(set_eval_smem(eval_dyn_smem(c_group, max_tab)));
 
     EvalArgs a{};
     a.uvw = obs->uvw_dev;

@@ -60,7 +60,8 @@ struct LMArgs {
     double *lm_trial;          // [n_ant][2] offsets of the next evaluation (EvalArgs::lm)
     const double *ev;          // evaluation at lm_trial: chi2 | g[2n] | H[3n] | X[4 nbl]
     double *cur;               // same layout, accepted evaluation
-    double *mat;               // [2n][2n] scratch for the damped full system
+    double *mat;               // [2n][2n] scratch for the damped full system (large systems)
+    float *mat32;              // [2n][2n] FP32 factor (large systems)
     double *rhs;               // [2n] scratch
     const int2 *pairs;
     int n_ant, n_bl;
@@ -76,8 +77,12 @@ cudaError_t launch_tables(const psc_aperture &ap, const double *freq_dev, int nc
                           int support, const int *tab_off_dev, const int *tab_len_dev, float2 *tabs,
                           cudaStream_t s);
 cudaError_t launch_lm_update(const LMArgs &a, cudaStream_t s);
+// Sets the LM kernel's shared-memory limit (once per device, before launches).
+cudaError_t lm_prepare(int n_ant);
 cudaError_t launch_lm_restart(const LMArgs &a, const LMState *st0, const double *lm0, cudaStream_t s);
 cudaError_t set_eval_smem(size_t dyn);
+// Dynamic shared memory of one fused-kernel block (zero-padded tables).
+size_t eval_dyn_smem(int c_group, int max_tab_len);
 // Records msg as the context-free last error (psc_last_error(NULL)); returns st.
 psc_status set_global_error(psc_status st, const char *msg);
 cudaError_t launch_model_grid(int n_img, int n_grid, const float *image, float2 *tmp, float2 *twiddle,

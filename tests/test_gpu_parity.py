@@ -153,9 +153,15 @@ def _oracle_solve(m, vobs, w, mode="full"):
     return LM.solve_full(ev, np.zeros((m.n_ant, 2)))
 
 
-@pytest.mark.parametrize("spec", [cases.DISK_SMALL, cases.GAUSS_SMALL])
-def test_solve_matches_oracle(spec):
-    m, _, lmt, img = cases.problem(spec, n_ant=7, n_time=12, freqs=(1.3e9, 1.4e9), n_src=8)
+# the 40-antenna case factors its 80 x 80 system in global memory (block-wide
+# Cholesky); the smaller ones in shared memory (one warp)
+@pytest.mark.parametrize("spec,n_ant,n_time,freqs", [
+    (cases.DISK_SMALL, 7, 12, (1.3e9, 1.4e9)),
+    (cases.GAUSS_SMALL, 7, 12, (1.3e9, 1.4e9)),
+    (cases.DISK_SMALL, 40, 3, (1.4e9,)),
+])
+def test_solve_matches_oracle(spec, n_ant, n_time, freqs):
+    m, _, lmt, img = cases.problem(spec, n_ant=n_ant, n_time=n_time, freqs=freqs, n_src=8)
     vobs, w = _obs(m, lmt)
     sol_o, rep_o = _oracle_solve(m, vobs, w)
     gp = GpuProblem(m, img)
