@@ -204,9 +204,61 @@ psc_status psc_lm_end(psc_ctx *ctx, double *lm_out, psc_solve_report *rep);
 psc_status psc_lm_restart(psc_ctx *ctx);
 
 /* Launch-shape knobs of the fused kernel (time steps and channels per
- * thread block); 0 keeps the current value.  t_tile in {8,16,32},
+ * thread block); 0 keeps the current value.  t_tile in {8,16,32,64,128},
  * c_group in {1,2,4,8}, t_tile * c_group in {32, 64, 128, 256}. */
 psc_status psc_set_tiling(psc_ctx *ctx, int t_tile, int c_group);
+
+/* ---- Batches of solution intervals (Algorithm 1's loop over all data) ----
+ * A batch groups contexts -- normally one per solution interval, of any
+ * array, length and channel set -- with their observed data, so that one LM
+ * iteration of all of them is one persistent fused launch: thread blocks pull
+ * (baseline, channel group, time tile) bricks of every context from one
+ * device work queue, so intervals of uneven size share the GPU.  The
+ * reductions and the LM updates of all contexts follow as one launch each,
+ * and the iteration is captured once in a CUDA graph and replayed (unless the
+ * batch runs on the legacy NULL stream).  Contexts whose solver stopped skip
+ * their bricks.  Every context in a batch uses 128 threads per block
+ * (t_tile * c_group = 128; other tilings are reset to 32 x 4).
+ * vis_obs[k], w[k] (NULL = ones) and w_scale[k] (NULL = all 1) are the data
+ * of ctxs[k], borrowed like the contexts for the batch's lifetime.  The
+ * offsets of all contexts are concatenated in the order of ctxs: lm0,
+ * lm_out, lm_inout are host [sum n_ant_k][2]; reps is [n_ctx]. */
+typedef struct psc_batch psc_batch;
+
+psc_status psc_batch_create(psc_batch **out, psc_ctx *const *ctxs, int n_ctx, const void *const *vis_obs,
+                            const float *const *w, const double *w_scale, void *stream);
+void psc_batch_destroy(psc_batch *b);
+const char *psc_batch_last_error(const psc_batch *b);
+
+/* Times the fused kernel of each context at the tile shapes (t_tile,
+ * c_group) = (32, 4), (16, 8) and (64, 2) on its own data and keeps the
+ * fastest; contexts of the same shape reuse the first one's choice.  Writes
+ * the chosen t_tile of each context to t_tile_out (NULL to skip).
+ * Synchronises. */
+psc_status psc_batch_autotune(psc_batch *b, int *t_tile_out);
+
+/* Start (host offsets, options as for psc_lm_begin), restart on the device,
+ * n_iter device-resident iterations (graph replays, no synchronisation) and
+ * the synchronising read-out, mirroring psc_lm_begin / psc_lm_restart /
+ * psc_lm_iterate / psc_lm_end. */
+psc_status psc_batch_begin(psc_batch *b, const double *lm0, const psc_solve_opts *opts);
+psc_status psc_batch_restart(psc_batch *b);
+psc_status psc_batch_iterate(psc_batch *b, int n_iter);
+psc_status psc_batch_end(psc_batch *b, double *lm_out, psc_solve_report *reps);
+
+/* Timing of the batch's persistent fused launch: while enabled,
+ * psc_batch_iterate launches each iteration directly (not through the graph)
+ * with a pair of CUDA events around the fused launch; psc_batch_profile_read
+ * synchronises, returns the summed duration (ms) and count, and clears them. */
+psc_status psc_batch_profile(psc_batch *b, int enable);
+psc_status psc_batch_profile_read(psc_batch *b, double *total_ms, int *n_launches);
+
+/* Solves every context in one batch (created and destroyed inside, on the
+ * first context's stream) from lm_inout, writing the solutions back; stops
+ * when every solver has stopped or after max_iter + 1 evaluations. */
+psc_status psc_solve_batch(psc_ctx *const *ctxs, int n_ctx, const void *const *vis_obs, const float *const *w,
+                           const double *w_scale, const psc_solve_opts *opts, double *lm_inout,
+                           psc_solve_report *reps);
 
 /* Allocation-free variant of psc_residual_grad.  The paper has no
  * counterpart: this entry point exists for callers that cannot call

@@ -25,7 +25,9 @@ STOP_REASONS = {0: "none", 1: "step", 2: "chi2", 3: "lambda", 4: "max_iter", 5: 
 EXPORTS = ("psc_solve_opts_default", "psc_model_grid", "psc_create", "psc_destroy", "psc_last_error",
            "psc_predict", "psc_residual_grad", "psc_solve_offsets", "psc_lm_begin", "psc_lm_iterate",
            "psc_lm_end", "psc_lm_restart", "psc_set_tiling", "psc_profile", "psc_profile_read",
-           "psc_residual_grad_noalloc")
+           "psc_residual_grad_noalloc", "psc_batch_create", "psc_batch_destroy", "psc_batch_last_error",
+           "psc_batch_autotune", "psc_batch_begin", "psc_batch_restart", "psc_batch_iterate", "psc_batch_end",
+           "psc_solve_batch", "psc_batch_profile", "psc_batch_profile_read")
 
 
 class PscError(RuntimeError):
@@ -96,6 +98,20 @@ def lib():
             "psc_residual_grad_noalloc": (ctypes.c_int, [ctypes.POINTER(psc_obs), ctypes.POINTER(psc_aperture),
                                                          ctypes.POINTER(psc_grid_desc), _V, _D, _V, _V, ctypes.c_double,
                                                          _D, _D, _D, _D, _V]),
+            "psc_batch_create": (ctypes.c_int, [ctypes.POINTER(_V), ctypes.POINTER(_V), ctypes.c_int,
+                                                ctypes.POINTER(_V), ctypes.POINTER(_V), _D, _V]),
+            "psc_batch_destroy": (None, [_V]),
+            "psc_batch_last_error": (ctypes.c_char_p, [_V]),
+            "psc_batch_autotune": (ctypes.c_int, [_V, ctypes.POINTER(ctypes.c_int)]),
+            "psc_batch_begin": (ctypes.c_int, [_V, _D, ctypes.POINTER(psc_solve_opts)]),
+            "psc_batch_restart": (ctypes.c_int, [_V]),
+            "psc_batch_iterate": (ctypes.c_int, [_V, ctypes.c_int]),
+            "psc_batch_end": (ctypes.c_int, [_V, _D, ctypes.POINTER(psc_solve_report)]),
+            "psc_batch_profile": (ctypes.c_int, [_V, ctypes.c_int]),
+            "psc_batch_profile_read": (ctypes.c_int, [_V, _D, ctypes.POINTER(ctypes.c_int)]),
+            "psc_solve_batch": (ctypes.c_int, [ctypes.POINTER(_V), ctypes.c_int, ctypes.POINTER(_V),
+                                               ctypes.POINTER(_V), _D, ctypes.POINTER(psc_solve_opts), _D,
+                                               ctypes.POINTER(psc_solve_report)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -249,3 +265,106 @@ class Context:
         rep = psc_solve_report()
         _check(lib().psc_lm_end(self.h, _dp(lm), ctypes.byref(rep)), self.h)
         return lm, rep
+
+
+def _ptr_array(items):
+    arr = (_V * len(items))()
+    for k, x in enumerate(items):
+        arr[k] = _ptr(x)
+    return arr
+
+
+def _bcheck(st, b):
+    if st != PSC_OK:
+        msg = lib().psc_batch_last_error(b)
+        raise PscError(st, msg.decode() if msg else "")
+
+
+class Batch:
+    """Owns one ``psc_batch`` over ``contexts`` (``Context`` objects) and their
+    per-context observed data; all of them must outlive the batch."""
+
+    def __init__(self, contexts, vis_obs, w=None, w_scale=None, stream=None):
+        self.contexts = list(contexts)
+        n = len(self.contexts)
+        self._keep = (list(vis_obs), list(w) if w is not None else None)
+        hs = (_V * n)(*[c.h.value for c in self.contexts])
+        self._hs = hs
+        ws = np.ascontiguousarray(np.ones(n) if w_scale is None else w_scale, dtype=np.float64)
+        self._ws = ws
+        h = _V()
+        _bcheck(lib().psc_batch_create(ctypes.byref(h), hs, n, _ptr_array(vis_obs),
+                                       _ptr_array(w) if w is not None else None, _dp(ws), _stream(stream)), None)
+        self.h = h
+        self.n_ant = [c.n_ant for c in self.contexts]
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().psc_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _concat(self, lm_list):
+        return np.ascontiguousarray(np.concatenate([np.asarray(x, dtype=np.float64).reshape(-1) for x in lm_list]))
+
+    def _split(self, flat):
+        out, off = [], 0
+        for n in self.n_ant:
+            out.append(flat[off:off + 2 * n].reshape(n, 2))
+            off += 2 * n
+        return out
+
+    def psc_batch_autotune(self):
+        t = (ctypes.c_int * len(self.contexts))()
+        _bcheck(lib().psc_batch_autotune(self.h, t), self.h)
+        return list(t)
+
+    def psc_batch_begin(self, lm0_list, opts=None):
+        self._lm0 = self._concat(lm0_list)
+        _bcheck(lib().psc_batch_begin(self.h, _dp(self._lm0), ctypes.byref(opts) if opts is not None else None),
+                self.h)
+
+    def psc_batch_restart(self):
+        _bcheck(lib().psc_batch_restart(self.h), self.h)
+
+    def psc_batch_iterate(self, n_iter=1):
+        _bcheck(lib().psc_batch_iterate(self.h, int(n_iter)), self.h)
+
+    def psc_batch_profile(self, enable=True):
+        _bcheck(lib().psc_batch_profile(self.h, int(bool(enable))), self.h)
+
+    def psc_batch_profile_read(self):
+        ms = np.zeros(1)
+        n = ctypes.c_int(0)
+        _bcheck(lib().psc_batch_profile_read(self.h, _dp(ms), ctypes.byref(n)), self.h)
+        return float(ms[0]), int(n.value)
+
+    def psc_batch_end(self):
+        flat = np.zeros(2 * sum(self.n_ant))
+        reps = (psc_solve_report * len(self.contexts))()
+        _bcheck(lib().psc_batch_end(self.h, _dp(flat), reps), self.h)
+        return self._split(flat), list(reps)
+
+
+def psc_solve_batch(contexts, vis_obs, w=None, w_scale=None, lm0_list=None, opts=None):
+    """Solves all contexts in one batch; returns (list of lm, list of reports)."""
+    n = len(contexts)
+    hs = (_V * n)(*[c.h.value for c in contexts])
+    n_ant = [c.n_ant for c in contexts]
+    if lm0_list is None:
+        lm0_list = [np.zeros((a, 2)) for a in n_ant]
+    flat = np.ascontiguousarray(np.concatenate([np.asarray(x, dtype=np.float64).reshape(-1) for x in lm0_list]))
+    ws = np.ascontiguousarray(np.ones(n) if w_scale is None else w_scale, dtype=np.float64)
+    reps = (psc_solve_report * n)()
+    _check(lib().psc_solve_batch(hs, n, _ptr_array(vis_obs), _ptr_array(w) if w is not None else None, _dp(ws),
+                                 ctypes.byref(opts) if opts is not None else None, _dp(flat), reps))
+    out, off = [], 0
+    for a in n_ant:
+        out.append(flat[off:off + 2 * a].reshape(a, 2))
+        off += 2 * a
+    return out, list(reps)

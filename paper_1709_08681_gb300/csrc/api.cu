@@ -1,6 +1,7 @@
 // C ABI of the Pointing SelfCal library (declared in include/psc.h): argument
 // checks, context workspace, and the launch sequences of Algorithm 1's
 // pre-computes and iteration loop.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -132,7 +133,20 @@ EvalArgs eval_args(const psc_ctx *c, const double *lm_dev) {
     a.n_cg = n_cg(c);
     a.decorrelation = c->ap.decorrelation;
     a.max_tab_len = c->max_tab_len;
+    a.n_bricks = (long long)c->n_bl * n_cg(c) * n_tt(c);
     return a;
+}
+
+RedArgs red_args(const psc_ctx *c, double *ev_out, const int *skip) {
+    RedArgs r{};
+    r.partials = c->d_partials;
+    r.blsum = c->d_blsum;
+    r.ev = ev_out;
+    r.skip = skip;
+    r.n_bl = c->n_bl;
+    r.bpb = n_cg(c) * n_tt(c);
+    r.n_ant = c->n_ant;
+    return r;
 }
 
 LMArgs lm_args(const psc_ctx *c) {
@@ -183,8 +197,7 @@ psc_status eval_reduce(psc_ctx *c, const double *lm_dev, const void *vis_obs, co
         PSC_CUDA(c, cudaEventRecord(c->ev_pool[c->ev_used + 1], c->stream));
         c->ev_used += 2;
     }
-    PSC_CUDA(c, launch_reduce(c->d_partials, c->n_bl, n_cg(c) * n_tt(c), c->d_pairs, c->n_ant, c->d_blsum,
-                              ev_out, skip, c->stream));
+    PSC_CUDA(c, launch_reduce(red_args(c, ev_out, skip), c->stream));
     return PSC_OK;
 }
 
@@ -332,7 +345,8 @@ psc_status psc_set_tiling(psc_ctx *ctx, int t_tile, int c_group) {
     if (!ctx) return fail(nullptr, PSC_ERR_ARG, "ctx is NULL");
     const int tt = t_tile ? t_tile : ctx->t_tile;
     const int cg = c_group ? c_group : ctx->c_group;
-    if (!(tt == 8 || tt == 16 || tt == 32)) return fail(ctx, PSC_ERR_ARG, "t_tile must be 8, 16 or 32");
+    if (!(tt == 8 || tt == 16 || tt == 32 || tt == 64 || tt == 128))
+        return fail(ctx, PSC_ERR_ARG, "t_tile must be 8, 16, 32, 64 or 128");
     if (!(cg == 1 || cg == 2 || cg == 4 || cg == 8)) return fail(ctx, PSC_ERR_ARG, "c_group must be 1, 2, 4 or 8");
     if (tt * cg < 32 || tt * cg > kMaxThreads) return fail(ctx, PSC_ERR_ARG, "t_tile * c_group must be in [32, 256]");
     ctx->t_tile = tt;
@@ -371,34 +385,73 @@ psc_status psc_residual_grad(psc_ctx *ctx, const double *lm, const void *vis_obs
     return PSC_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+psc_status check_opts(psc_ctx *ctx, const psc_solve_opts &o) {
+    if (o.max_iter < 0 || (o.mode != PSC_LM_FULL && o.mode != PSC_LM_BLOCK) || !(o.lam0 > 0.0) ||
+        !(o.lam_max >= o.lam0) || !(o.lam_min >= 0.0) || !(o.step_tol_rad >= 0.0) || !(o.chi2_rtol >= 0.0) ||
+        !(o.block_gain > 0.0 && o.block_gain <= 1.0))
+        return fail(ctx, PSC_ERR_ARG, "invalid solver options");
+    return PSC_OK;
+}
+
+// Uploads the start offsets and the initial solver state of ctx on `s`.
+psc_status lm_begin_on(psc_ctx *ctx, const double *lm0, const psc_solve_opts &o, cudaStream_t s) {
+    LMState st{};
+    st.lam = o.lam0;
+    st.chi2 = INFINITY;
+    st.max_iter = o.max_iter;
+    st.mode = o.mode;
+    st.lam_max = o.lam_max;
+    st.lam_min = o.lam_min;
+    st.step_tol = o.step_tol_rad;
+    st.chi2_rtol = o.chi2_rtol;
+    st.block_gain = o.block_gain;
+    ctx->h_state = st;
+    const size_t lmb = sizeof(double) * 2 * ctx->n_ant;
+    PSC_CUDA(ctx, cudaMemcpyAsync(ctx->d_state, &ctx->h_state, sizeof(LMState), cudaMemcpyHostToDevice, s));
+    PSC_CUDA(ctx, cudaMemcpyAsync(ctx->d_lm_trial, lm0, lmb, cudaMemcpyHostToDevice, s));
+    PSC_CUDA(ctx, cudaMemcpyAsync(ctx->d_lm_cur, lm0, lmb, cudaMemcpyHostToDevice, s));
+    PSC_CUDA(ctx, cudaMemcpyAsync(ctx->d_state0, &ctx->h_state, sizeof(LMState), cudaMemcpyHostToDevice, s));
+    PSC_CUDA(ctx, cudaMemcpyAsync(ctx->d_lm0, lm0, lmb, cudaMemcpyHostToDevice, s));
+    ctx->begun = true;
+    return PSC_OK;
+}
+
+// Copies the accepted offsets and the solver state of ctx to the host
+// (after the caller synchronised `s`).
+psc_status lm_fetch(psc_ctx *ctx, double *lm_out, psc_solve_report *rep, cudaStream_t s) {
+    if (lm_out)
+        PSC_CUDA(ctx, cudaMemcpyAsync(lm_out, ctx->d_lm_cur, sizeof(double) * 2 * ctx->n_ant, cudaMemcpyDeviceToHost, s));
+    PSC_CUDA(ctx, cudaMemcpyAsync(&ctx->h_state, ctx->d_state, sizeof(LMState), cudaMemcpyDeviceToHost, s));
+    PSC_CUDA(ctx, cudaStreamSynchronize(s));
+    if (rep) {
+        rep->n_iter = ctx->h_state.n_iter;
+        rep->n_eval = ctx->h_state.n_eval;
+        rep->reason = ctx->h_state.done ? ctx->h_state.reason : PSC_STOP_NONE;
+        rep->chi2 = ctx->h_state.chi2;
+        rep->lam = ctx->h_state.lam;
+    }
+    if (ctx->h_state.done && ctx->h_state.reason == PSC_STOP_NUMERIC)
+        return fail(ctx, PSC_ERR_NUMERIC, "solver stopped on a non-finite chi^2 or step");
+    return PSC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 psc_status psc_lm_begin(psc_ctx *ctx, const double *lm0, const psc_solve_opts *opts) {
     if (!ctx) return fail(nullptr, PSC_ERR_ARG, "ctx is NULL");
     if (!lm0) return fail(ctx, PSC_ERR_ARG, "lm0 is NULL");
     psc_solve_opts o;
     if (opts) o = *opts;
     else psc_solve_opts_default(&o);
-    if (o.max_iter < 0 || (o.mode != PSC_LM_FULL && o.mode != PSC_LM_BLOCK) || !(o.lam0 > 0.0) ||
-        !(o.lam_max >= o.lam0) || !(o.lam_min >= 0.0) || !(o.step_tol_rad >= 0.0) || !(o.chi2_rtol >= 0.0) ||
-        !(o.block_gain > 0.0 && o.block_gain <= 1.0))
-        return fail(ctx, PSC_ERR_ARG, "invalid solver options");
-    LMState s{};
-    s.lam = o.lam0;
-    s.chi2 = INFINITY;
-    s.max_iter = o.max_iter;
-    s.mode = o.mode;
-    s.lam_max = o.lam_max;
-    s.lam_min = o.lam_min;
-    s.step_tol = o.step_tol_rad;
-    s.chi2_rtol = o.chi2_rtol;
-    s.block_gain = o.block_gain;
-    ctx->h_state = s;
-    PSC_CUDA(ctx, cudaMemcpyAsync(ctx->d_state, &ctx->h_state, sizeof(LMState), cudaMemcpyHostToDevice, ctx->stream));
-    PSC_CUDA(ctx, cudaMemcpyAsync(ctx->d_lm_trial, lm0, sizeof(double) * 2 * ctx->n_ant, cudaMemcpyHostToDevice, ctx->stream));
-    PSC_CUDA(ctx, cudaMemcpyAsync(ctx->d_lm_cur, lm0, sizeof(double) * 2 * ctx->n_ant, cudaMemcpyHostToDevice, ctx->stream));
-    PSC_CUDA(ctx, cudaMemcpyAsync(ctx->d_state0, &ctx->h_state, sizeof(LMState), cudaMemcpyHostToDevice, ctx->stream));
-    PSC_CUDA(ctx, cudaMemcpyAsync(ctx->d_lm0, lm0, sizeof(double) * 2 * ctx->n_ant, cudaMemcpyHostToDevice, ctx->stream));
-    ctx->begun = true;
-    return PSC_OK;
+    psc_status st = check_opts(ctx, o);
+    if (st != PSC_OK) return st;
+    return lm_begin_on(ctx, lm0, o, ctx->stream);
 }
 
 psc_status psc_lm_restart(psc_ctx *ctx) {
@@ -423,20 +476,7 @@ psc_status psc_lm_iterate(psc_ctx *ctx, const void *vis_obs, const float *w, dou
 
 psc_status psc_lm_end(psc_ctx *ctx, double *lm_out, psc_solve_report *rep) {
     if (!ctx) return fail(nullptr, PSC_ERR_ARG, "ctx is NULL");
-    if (lm_out)
-        PSC_CUDA(ctx, cudaMemcpyAsync(lm_out, ctx->d_lm_cur, sizeof(double) * 2 * ctx->n_ant, cudaMemcpyDeviceToHost, ctx->stream));
-    PSC_CUDA(ctx, cudaMemcpyAsync(&ctx->h_state, ctx->d_state, sizeof(LMState), cudaMemcpyDeviceToHost, ctx->stream));
-    PSC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    if (rep) {
-        rep->n_iter = ctx->h_state.n_iter;
-        rep->n_eval = ctx->h_state.n_eval;
-        rep->reason = ctx->h_state.done ? ctx->h_state.reason : PSC_STOP_NONE;
-        rep->chi2 = ctx->h_state.chi2;
-        rep->lam = ctx->h_state.lam;
-    }
-    if (ctx->h_state.done && ctx->h_state.reason == PSC_STOP_NUMERIC)
-        return fail(ctx, PSC_ERR_NUMERIC, "solver stopped on a non-finite chi^2 or step");
-    return PSC_OK;
+    return lm_fetch(ctx, lm_out, rep, ctx->stream);
 }
 
 psc_status psc_solve_offsets(psc_ctx *ctx, const void *vis_obs, const float *w, double w_scale,
@@ -483,6 +523,378 @@ psc_status psc_profile_read(psc_ctx *ctx, double *total_ms, int *n_launches) {
     *total_ms = tot;
     *n_launches = (int)(ctx->ev_used / 2);
     ctx->ev_used = 0;
+    return PSC_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batches of contexts: one persistent fused launch per LM iteration.
+
+struct psc_batch {
+    cudaStream_t stream = nullptr;
+    std::vector<psc_ctx *> ctxs;
+    std::vector<const void *> vis;
+    std::vector<const float *> w;
+    std::vector<double> w_scale;
+    // device tables (rebuilt by build_tables)
+    EvalArgs *d_eval = nullptr;
+    long long *d_prefix = nullptr;
+    RedArgs *d_red = nullptr;
+    int *d_bl_prefix = nullptr;
+    LMArgs *d_lm = nullptr;
+    const LMState **d_st0 = nullptr;
+    const double **d_lm0 = nullptr;
+    unsigned long long *d_queue = nullptr;
+    int *d_active = nullptr;
+    int total_bl = 0;
+    int grid = 0;
+    size_t eval_dyn = 0, lm_dyn = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    // fused-kernel timing (psc_batch_profile): direct launches with event pairs
+    bool prof = false;
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;
+    std::string err;
+};
+
+namespace {
+
+psc_status bfail(psc_batch *b, psc_status st, const std::string &msg) {
+    if (b) b->err = msg;
+    return fail(nullptr, st, msg);
+}
+
+#define PSC_BCUDA(b, call)                                                        \
+    do {                                                                          \
+        cudaError_t e_ = (call);                                                  \
+        if (e_ != cudaSuccess)                                                    \
+            return bfail((b), e_ == cudaErrorMemoryAllocation ? PSC_ERR_OOM : PSC_ERR_CUDA, \
+                         std::string(#call) + ": " + cudaGetErrorString(e_));     \
+    } while (0)
+
+void drop_graph(psc_batch *b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+}
+
+void free_batch(psc_batch *b) {
+    if (!b) return;
+    drop_graph(b);
+    for (cudaEvent_t e : b->ev_pool) cudaEventDestroy(e);
+    cudaFree(b->d_eval); cudaFree(b->d_prefix); cudaFree(b->d_red); cudaFree(b->d_bl_prefix);
+    cudaFree(b->d_lm); cudaFree(b->d_st0); cudaFree(b->d_lm0); cudaFree(b->d_queue); cudaFree(b->d_active);
+    delete b;
+}
+
+// (Re)builds the device argument tables from the contexts' current tiling.
+psc_status build_tables(psc_batch *b) {
+    const int n = (int)b->ctxs.size();
+    std::vector<EvalArgs> ev(n);
+    std::vector<long long> prefix(n + 1, 0);
+    std::vector<RedArgs> red(n);
+    std::vector<int> blp(n + 1, 0);
+    std::vector<LMArgs> lm(n);
+    std::vector<const LMState *> st0(n);
+    std::vector<const double *> lm0(n);
+    size_t dyn = 0, lmd = 0;
+    for (int k = 0; k < n; ++k) {
+        psc_ctx *c = b->ctxs[k];
+        if (c->t_tile * c->c_group != 128) {
+            c->t_tile = 32;
+            c->c_group = 4;
+        }
+        psc_status st = ensure_partials(c);
+        if (st != PSC_OK) return bfail(b, st, c->err);
+        ev[k] = eval_args(c, c->d_lm_trial);
+        ev[k].vis_obs = (const float2 *)b->vis[k];
+        ev[k].w = b->w[k];
+        ev[k].w_scale = (float)b->w_scale[k];
+        ev[k].skip = c->d_done;
+        prefix[k + 1] = prefix[k] + ev[k].n_bricks;
+        red[k] = red_args(c, c->d_ev, c->d_done);
+        blp[k + 1] = blp[k] + c->n_bl;
+        lm[k] = lm_args(c);
+        st0[k] = c->d_state0;
+        lm0[k] = c->d_lm0;
+        dyn = std::max(dyn, eval_dyn_smem(c->c_group, c->max_tab_len));
+        lmd = std::max(lmd, lm_smem_bytes(c->n_ant));
+    }
+    b->total_bl = blp[n];
+    b->eval_dyn = dyn;
+    b->lm_dyn = lmd;
+    PSC_BCUDA(b, set_eval_smem(dyn));
+    int per_sm = 0, dev = 0, n_sm = 0;
+    PSC_BCUDA(b, eval_batch_occupancy(128, dyn, &per_sm));
+    PSC_BCUDA(b, cudaGetDevice(&dev));
+    PSC_BCUDA(b, cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+    b->grid = std::max(1, per_sm) * n_sm;
+    if (!b->d_eval) {
+        PSC_BCUDA(b, dalloc(&b->d_eval, n));
+        PSC_BCUDA(b, dalloc(&b->d_prefix, n + 1));
+        PSC_BCUDA(b, dalloc(&b->d_red, n));
+        PSC_BCUDA(b, dalloc(&b->d_bl_prefix, n + 1));
+        PSC_BCUDA(b, dalloc(&b->d_lm, n));
+        PSC_BCUDA(b, dalloc(&b->d_st0, n));
+        PSC_BCUDA(b, dalloc(&b->d_lm0, n));
+        PSC_BCUDA(b, dalloc(&b->d_queue, 1));
+        PSC_BCUDA(b, dalloc(&b->d_active, 1));
+    }
+    cudaStream_t s = b->stream;
+    PSC_BCUDA(b, cudaMemcpyAsync(b->d_eval, ev.data(), sizeof(EvalArgs) * n, cudaMemcpyHostToDevice, s));
+    PSC_BCUDA(b, cudaMemcpyAsync(b->d_prefix, prefix.data(), sizeof(long long) * (n + 1), cudaMemcpyHostToDevice, s));
+    PSC_BCUDA(b, cudaMemcpyAsync(b->d_red, red.data(), sizeof(RedArgs) * n, cudaMemcpyHostToDevice, s));
+    PSC_BCUDA(b, cudaMemcpyAsync(b->d_bl_prefix, blp.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, s));
+    PSC_BCUDA(b, cudaMemcpyAsync(b->d_lm, lm.data(), sizeof(LMArgs) * n, cudaMemcpyHostToDevice, s));
+    PSC_BCUDA(b, cudaMemcpyAsync(b->d_st0, st0.data(), sizeof(void *) * n, cudaMemcpyHostToDevice, s));
+    PSC_BCUDA(b, cudaMemcpyAsync(b->d_lm0, lm0.data(), sizeof(void *) * n, cudaMemcpyHostToDevice, s));
+    PSC_BCUDA(b, cudaStreamSynchronize(s));
+    drop_graph(b);
+    return PSC_OK;
+}
+
+// One LM iteration of every context: fused persistent launch, reductions, update.
+psc_status enqueue_iteration(psc_batch *b) {
+    const int n = (int)b->ctxs.size();
+    cudaStream_t s = b->stream;
+    PSC_BCUDA(b, cudaMemsetAsync(b->d_queue, 0, sizeof(unsigned long long), s));
+    if (b->prof) {
+        while (b->ev_pool.size() < b->ev_used + 2) {
+            cudaEvent_t e;
+            PSC_BCUDA(b, cudaEventCreate(&e));
+            b->ev_pool.push_back(e);
+        }
+        PSC_BCUDA(b, cudaEventRecord(b->ev_pool[b->ev_used], s));
+    }
+    PSC_BCUDA(b, launch_eval_batch(b->d_eval, b->d_prefix, n, b->d_queue, 128, b->eval_dyn, b->grid, s));
+    if (b->prof) {
+        PSC_BCUDA(b, cudaEventRecord(b->ev_pool[b->ev_used + 1], s));
+        b->ev_used += 2;
+    }
+    PSC_BCUDA(b, launch_reduce_batch(b->d_red, b->d_bl_prefix, n, b->total_bl, s));
+    PSC_BCUDA(b, launch_lm_update_batch(b->d_lm, n, b->lm_dyn, s));
+    return PSC_OK;
+}
+
+psc_status ensure_graph(psc_batch *b) {
+    if (b->exec) return PSC_OK;
+    cudaStream_t s = b->stream;
+    if (s == nullptr) return PSC_OK;                 // the legacy stream cannot be captured: launch directly
+    PSC_BCUDA(b, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    psc_status st = enqueue_iteration(b);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(s, &g);
+    if (st != PSC_OK) { if (g) cudaGraphDestroy(g); return st; }
+    if (e != cudaSuccess) return bfail(b, PSC_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    b->graph = g;
+    e = cudaGraphInstantiate(&b->exec, g, 0);
+    if (e != cudaSuccess) {
+        drop_graph(b);
+        return bfail(b, PSC_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    }
+    return PSC_OK;
+}
+
+__global__ void count_active_kernel(const LMArgs *la, int n, int *out) {
+    int c = 0;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) c += la[k].st->done ? 0 : 1;
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if (threadIdx.x == 0) *out = c;
+}
+
+}  // namespace
+
+extern "C" {
+
+psc_status psc_batch_create(psc_batch **out, psc_ctx *const *ctxs, int n_ctx, const void *const *vis_obs,
+                            const float *const *w, const double *w_scale, void *stream) {
+    if (!out) return fail(nullptr, PSC_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!ctxs || n_ctx < 1 || !vis_obs) return fail(nullptr, PSC_ERR_ARG, "ctxs and vis_obs must be non-NULL, n_ctx >= 1");
+    psc_batch *b = new psc_batch();
+    b->stream = (cudaStream_t)stream;
+    for (int k = 0; k < n_ctx; ++k) {
+        if (!ctxs[k] || !vis_obs[k]) { free_batch(b); return fail(nullptr, PSC_ERR_ARG, "a context or its vis_obs is NULL"); }
+        const double ws = w_scale ? w_scale[k] : 1.0;
+        if (!(ws > 0.0) || !std::isfinite(ws)) { free_batch(b); return fail(nullptr, PSC_ERR_ARG, "w_scale must be > 0"); }
+        for (int j = 0; j < k; ++j)
+            if (ctxs[j] == ctxs[k]) { free_batch(b); return fail(nullptr, PSC_ERR_ARG, "a context appears twice in the batch"); }
+        b->ctxs.push_back(ctxs[k]);
+        b->vis.push_back(vis_obs[k]);
+        b->w.push_back(w ? w[k] : nullptr);
+        b->w_scale.push_back(ws);
+    }
+    psc_status st = build_tables(b);
+    if (st != PSC_OK) { free_batch(b); return st; }
+    st = lm_prepare(0) == cudaSuccess ? PSC_OK : fail(nullptr, PSC_ERR_CUDA, "LM shared memory");
+    if (st != PSC_OK) { free_batch(b); return st; }
+    *out = b;
+    return PSC_OK;
+}
+
+void psc_batch_destroy(psc_batch *b) { free_batch(b); }
+
+psc_status psc_batch_autotune(psc_batch *b, int *t_tile_out) {
+    if (!b) return fail(nullptr, PSC_ERR_ARG, "batch is NULL");
+    static const int cand[3][2] = {{32, 4}, {16, 8}, {64, 2}};
+    cudaEvent_t e0, e1;
+    PSC_BCUDA(b, cudaEventCreate(&e0));
+    PSC_BCUDA(b, cudaEventCreate(&e1));
+    const int n = (int)b->ctxs.size();
+    std::vector<double> zeros;
+    for (int k = 0; k < n; ++k) {
+        psc_ctx *c = b->ctxs[k];
+        // reuse the choice of an earlier context with the same shape
+        int reuse = -1;
+        for (int j = 0; j < k && reuse < 0; ++j) {
+            psc_ctx *o = b->ctxs[j];
+            if (o->n_ant == c->n_ant && o->nc == c->nc && o->nt == c->nt && o->gd.n_grid == c->gd.n_grid &&
+                o->du == c->du && o->max_tab_len == c->max_tab_len)
+                reuse = j;
+        }
+        if (reuse >= 0) {
+            c->t_tile = b->ctxs[reuse]->t_tile;
+            c->c_group = b->ctxs[reuse]->c_group;
+        } else {
+            zeros.assign(2 * c->n_ant, 0.0);
+            PSC_BCUDA(b, cudaMemcpyAsync(c->d_lm_trial, zeros.data(), sizeof(double) * zeros.size(),
+                                         cudaMemcpyHostToDevice, b->stream));
+            float best = 1e30f;
+            int bt = 32, bc = 4;
+            for (const auto &cd : cand) {
+                c->t_tile = cd[0];
+                c->c_group = cd[1];
+                psc_status st = ensure_partials(c);
+                if (st != PSC_OK) return bfail(b, st, c->err);
+                EvalArgs a = eval_args(c, c->d_lm_trial);
+                a.vis_obs = (const float2 *)b->vis[k];
+                a.w = b->w[k];
+                a.w_scale = (float)b->w_scale[k];
+                PSC_BCUDA(b, launch_eval(a, false, b->stream));          // warm
+                PSC_BCUDA(b, cudaEventRecord(e0, b->stream));
+                for (int r = 0; r < 3; ++r) PSC_BCUDA(b, launch_eval(a, false, b->stream));
+                PSC_BCUDA(b, cudaEventRecord(e1, b->stream));
+                PSC_BCUDA(b, cudaEventSynchronize(e1));
+                float ms = 0.f;
+                PSC_BCUDA(b, cudaEventElapsedTime(&ms, e0, e1));
+                if (ms < best) { best = ms; bt = cd[0]; bc = cd[1]; }
+            }
+            c->t_tile = bt;
+            c->c_group = bc;
+        }
+        if (t_tile_out) t_tile_out[k] = c->t_tile;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return build_tables(b);
+}
+
+psc_status psc_batch_begin(psc_batch *b, const double *lm0, const psc_solve_opts *opts) {
+    if (!b) return fail(nullptr, PSC_ERR_ARG, "batch is NULL");
+    if (!lm0) return bfail(b, PSC_ERR_ARG, "lm0 is NULL");
+    psc_solve_opts o;
+    if (opts) o = *opts;
+    else psc_solve_opts_default(&o);
+    size_t off = 0;
+    for (psc_ctx *c : b->ctxs) {
+        psc_status st = check_opts(c, o);
+        if (st == PSC_OK) st = lm_begin_on(c, lm0 + off, o, b->stream);
+        if (st != PSC_OK) return bfail(b, st, c->err);
+        off += 2 * (size_t)c->n_ant;
+    }
+    PSC_BCUDA(b, cudaStreamSynchronize(b->stream));      // the staged host state must not change under the copies
+    return PSC_OK;
+}
+
+psc_status psc_batch_restart(psc_batch *b) {
+    if (!b) return fail(nullptr, PSC_ERR_ARG, "batch is NULL");
+    for (psc_ctx *c : b->ctxs)
+        if (!c->begun) return bfail(b, PSC_ERR_ARG, "psc_batch_restart before psc_batch_begin");
+    PSC_BCUDA(b, launch_lm_restart_batch(b->d_lm, b->d_st0, b->d_lm0, (int)b->ctxs.size(), b->stream));
+    return PSC_OK;
+}
+
+psc_status psc_batch_iterate(psc_batch *b, int n_iter) {
+    if (!b) return fail(nullptr, PSC_ERR_ARG, "batch is NULL");
+    if (n_iter < 0) return bfail(b, PSC_ERR_ARG, "n_iter must be >= 0");
+    psc_status st = b->prof ? PSC_OK : ensure_graph(b);
+    if (st != PSC_OK) return st;
+    for (int it = 0; it < n_iter; ++it) {
+        if (b->exec && !b->prof) PSC_BCUDA(b, cudaGraphLaunch(b->exec, b->stream));
+        else {
+            st = enqueue_iteration(b);
+            if (st != PSC_OK) return st;
+        }
+    }
+    return PSC_OK;
+}
+
+psc_status psc_batch_end(psc_batch *b, double *lm_out, psc_solve_report *reps) {
+    if (!b) return fail(nullptr, PSC_ERR_ARG, "batch is NULL");
+    size_t off = 0;
+    psc_status worst = PSC_OK;
+    for (size_t k = 0; k < b->ctxs.size(); ++k) {
+        psc_ctx *c = b->ctxs[k];
+        psc_status st = lm_fetch(c, lm_out ? lm_out + off : nullptr, reps ? reps + k : nullptr, b->stream);
+        if (st != PSC_OK && worst == PSC_OK) { worst = st; b->err = c->err; fail(nullptr, st, c->err); }
+        off += 2 * (size_t)c->n_ant;
+    }
+    return worst;
+}
+
+psc_status psc_solve_batch(psc_ctx *const *ctxs, int n_ctx, const void *const *vis_obs, const float *const *w,
+                           const double *w_scale, const psc_solve_opts *opts, double *lm_inout,
+                           psc_solve_report *reps) {
+    if (!lm_inout) return fail(nullptr, PSC_ERR_ARG, "lm_inout is NULL");
+    if (!ctxs || n_ctx < 1 || !ctxs[0]) return fail(nullptr, PSC_ERR_ARG, "ctxs must be non-NULL, n_ctx >= 1");
+    psc_batch *b = nullptr;
+    psc_status st = psc_batch_create(&b, ctxs, n_ctx, vis_obs, w, w_scale, ctxs[0]->stream);
+    if (st != PSC_OK) return st;
+    psc_solve_opts o;
+    if (opts) o = *opts;
+    else psc_solve_opts_default(&o);
+    st = psc_batch_begin(b, lm_inout, &o);
+    int active = n_ctx, done_evals = 0;
+    const int total = o.max_iter + 1;
+    while (st == PSC_OK && active > 0 && done_evals < total) {
+        const int chunk = std::min(4, total - done_evals);
+        st = psc_batch_iterate(b, chunk);
+        done_evals += chunk;
+        if (st != PSC_OK) break;
+        count_active_kernel<<<1, 32, 0, b->stream>>>(b->d_lm, n_ctx, b->d_active);
+        cudaError_t e = cudaMemcpyAsync(&active, b->d_active, sizeof(int), cudaMemcpyDeviceToHost, b->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+        if (e != cudaSuccess) st = bfail(b, PSC_ERR_CUDA, cudaGetErrorString(e));
+    }
+    if (st == PSC_OK) st = psc_batch_end(b, lm_inout, reps);
+    free_batch(b);
+    return st;
+}
+
+const char *psc_batch_last_error(const psc_batch *b) { return b ? b->err.c_str() : g_err.c_str(); }
+
+psc_status psc_batch_profile(psc_batch *b, int enable) {
+    if (!b) return fail(nullptr, PSC_ERR_ARG, "batch is NULL");
+    b->prof = enable != 0;
+    return PSC_OK;
+}
+
+psc_status psc_batch_profile_read(psc_batch *b, double *total_ms, int *n_launches) {
+    if (!b) return fail(nullptr, PSC_ERR_ARG, "batch is NULL");
+    if (!total_ms || !n_launches) return bfail(b, PSC_ERR_ARG, "outputs must be non-NULL");
+    PSC_BCUDA(b, cudaStreamSynchronize(b->stream));
+    double tot = 0.0;
+    for (size_t k = 0; k + 1 < b->ev_used; k += 2) {
+        float ms = 0.f;
+        PSC_BCUDA(b, cudaEventElapsedTime(&ms, b->ev_pool[k], b->ev_pool[k + 1]));
+        tot += ms;
+    }
+    *total_ms = tot;
+    *n_launches = (int)(b->ev_used / 2);
+    b->ev_used = 0;
     return PSC_OK;
 }
 

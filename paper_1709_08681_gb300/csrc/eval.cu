@@ -75,17 +75,51 @@ __device__ __forceinline__ void row_taps(const float2 *__restrict__ row, int a_n
     }
 }
 
+// One launch covers either one context (queue == nullptr: block b handles
+// brick b of a0) or a batch of contexts (persistent: each block pulls global
+// brick numbers from an atomic queue until all sum(bricks) are taken; prefix
+// holds the first global brick of each context).  Every brick writes its own
+// partial record, so the result does not depend on which block ran it.
 template <bool kPredict>
-__global__ void __launch_bounds__(kMaxThreads) eval_kernel(const EvalArgs a) {
-    if (a.skip != nullptr && *a.skip) return;
+__global__ void __launch_bounds__(kMaxThreads) eval_kernel(const EvalArgs a0, const EvalArgs *__restrict__ args,
+                                                           const long long *__restrict__ prefix, int n_ctx,
+                                                           unsigned long long *queue) {
     extern __shared__ float2 s_tab[];                 // c_group * (max_tab_len + kTabPad)
     __shared__ float2 s_tile[kTile * kTile];
     __shared__ float2 s_phx[kTile], s_phy[kTile];
     __shared__ int s_box[4];
     __shared__ double s_red[kMaxThreads / 32][kRed];
-
+    __shared__ EvalArgs s_a;
+    __shared__ long long s_work, s_first;
+    __shared__ int s_ctx;
+    const bool persistent = queue != nullptr;
+    long long next = -1;                              // thread 0: prefetched queue entry
+    for (;;) {
+    if (persistent) {
+        __syncthreads();                              // the previous brick is done with shared memory
+        if (threadIdx.x == 0) {
+            const long long gb = next >= 0 ? next : (long long)atomicAdd(queue, 1ull);
+            next = (long long)atomicAdd(queue, 1ull);  // consumed next round: its latency overlaps this brick
+            int lo = 0, hi = n_ctx - 1;               // last context with prefix[k] <= gb
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (prefix[mid] <= gb) lo = mid; else hi = mid - 1;
+            }
+            s_work = gb;
+            s_ctx = lo;
+            s_first = prefix[lo];
+            if (gb < prefix[n_ctx]) s_a = args[lo];
+        }
+        __syncthreads();
+        if (s_work >= prefix[n_ctx]) return;
+    } else {
+        if (threadIdx.x == 0) s_a = a0;
+        __syncthreads();
+    }
+    const EvalArgs &a = s_a;
+    if (!(a.skip != nullptr && *a.skip)) {
     const int tid = threadIdx.x;
-    const int brick = blockIdx.x;
+    const int brick = persistent ? (int)(s_work - s_first) : (int)blockIdx.x;
     const int tt = brick % a.n_tt;
     const int cgi = (brick / a.n_tt) % a.n_cg;
     const int bl = brick / (a.n_tt * a.n_cg);
@@ -321,44 +355,62 @@ __global__ void __launch_bounds__(kMaxThreads) eval_kernel(const EvalArgs a) {
             double s = 0.0;
             const int nw = (blockDim.x + 31) >> 5;
             for (int wi = 0; wi < nw; ++wi) s += s_red[wi][tid];
-            a.partials[(size_t)tid * gridDim.x + brick] = s;      // [kRed][n_bricks]
+            a.partials[(size_t)tid * a.n_bricks + brick] = s;      // [kRed][n_bricks]
         }
     }
+    }                                                 // not skipped
+    if (!persistent) return;
+    }                                                 // brick loop
 }
 
 // Second stage (a): per-baseline sums over its bricks, one warp per baseline,
 // a fixed butterfly order (deterministic).  partials is [kRed][n_bricks] with
-// the bricks of baseline bl at [bl * bpb, (bl + 1) * bpb).
-__global__ void bl_reduce_kernel(const double *__restrict__ partials, int n_bl, int bpb,
-                                 double *__restrict__ blsum, const int *skip) {
-    if (skip != nullptr && *skip) return;
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+// the bricks of baseline bl at [bl * bpb, (bl + 1) * bpb).  Batched form: the
+// global warp number runs over the baselines of all contexts (bl_prefix).
+__global__ void bl_reduce_kernel(const RedArgs r0, const RedArgs *__restrict__ ra,
+                                 const int *__restrict__ bl_prefix, int n_ctx) {
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (warp >= n_bl) return;
-    const size_t nb = (size_t)n_bl * bpb;
+    RedArgs r = r0;
+    int bl = gw;
+    if (ra != nullptr) {
+        if (gw >= bl_prefix[n_ctx]) return;
+        int lo = 0, hi = n_ctx - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (bl_prefix[mid] <= gw) lo = mid; else hi = mid - 1;
+        }
+        r = ra[lo];
+        bl = gw - bl_prefix[lo];
+    }
+    if (bl >= r.n_bl) return;
+    if (r.skip != nullptr && *r.skip) return;
+    const size_t nb = (size_t)r.n_bl * r.bpb;
     for (int k = 0; k < kRed; ++k) {
-        const double *p = partials + (size_t)k * nb + (size_t)warp * bpb;
-        double s = 0.0;
-        for (int b = lane; b < bpb; b += 32) s += p[b];
+        const double *p = r.partials + (size_t)k * nb + (size_t)bl * r.bpb;
+        double sum = 0.0;
+        for (int b = lane; b < r.bpb; b += 32) sum += p[b];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) blsum[(size_t)warp * kRed + k] = s;
+        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        if (lane == 0) r.blsum[(size_t)bl * kRed + k] = sum;
     }
 }
 
 // Second stage (b): chi^2, per-antenna gradient and diagonal blocks, cross
-// blocks; ev = chi2 | g[2n] | H[3n] | X[4 nbl].  One block, fixed order.
-__global__ void ev_kernel(const double *__restrict__ blsum, int n_bl, int n_ant, double *__restrict__ ev,
-                          const int *skip) {
-    if (skip != nullptr && *skip) return;
+// blocks; ev = chi2 | g[2n] | H[3n] | X[4 nbl].  One block per context
+// (blockIdx.x indexes ra when batched), fixed order.
+__global__ void ev_kernel(const RedArgs r0, const RedArgs *__restrict__ ra) {
+    const RedArgs r = ra != nullptr ? ra[blockIdx.x] : r0;
+    if (r.skip != nullptr && *r.skip) return;
     __shared__ double s_chi[kMaxThreads];
     const int tid = threadIdx.x;
+    const int n_ant = r.n_ant, n_bl = r.n_bl;
     double chi = 0.0;
     for (int bl = tid; bl < n_bl; bl += blockDim.x) {
-        const double *s = blsum + (size_t)bl * kRed;
-        chi += s[0];
-        double *x = ev + 1 + 5 * (size_t)n_ant + 4 * (size_t)bl;
-        x[0] = s[11]; x[1] = s[12]; x[2] = s[13]; x[3] = s[14];
+        const double *sb = r.blsum + (size_t)bl * kRed;
+        chi += sb[0];
+        double *x = r.ev + 1 + 5 * (size_t)n_ant + 4 * (size_t)bl;
+        x[0] = sb[11]; x[1] = sb[12]; x[2] = sb[13]; x[3] = sb[14];
     }
     s_chi[tid] = chi;
     __syncthreads();
@@ -366,23 +418,23 @@ __global__ void ev_kernel(const double *__restrict__ blsum, int n_bl, int n_ant,
         if (tid < o) s_chi[tid] += s_chi[tid + o];
         __syncthreads();
     }
-    if (tid == 0) ev[0] = s_chi[0];
+    if (tid == 0) r.ev[0] = s_chi[0];
     for (int an = tid; an < n_ant; an += blockDim.x) {
         double g0 = 0, g1 = 0, h0 = 0, h1 = 0, h2 = 0;
         for (int o = 0; o < n_ant; ++o) {
             if (o == an) continue;
             const int i = min(an, o), j = max(an, o);
             const int bl = i * (2 * n_ant - i - 1) / 2 + (j - i - 1);
-            const double *s = blsum + (size_t)bl * kRed;
+            const double *sb = r.blsum + (size_t)bl * kRed;
             if (an == i) {
-                g0 += s[1]; g1 += s[2]; h0 += s[5]; h1 += s[6]; h2 += s[7];
+                g0 += sb[1]; g1 += sb[2]; h0 += sb[5]; h1 += sb[6]; h2 += sb[7];
             } else {
-                g0 += s[3]; g1 += s[4]; h0 += s[8]; h1 += s[9]; h2 += s[10];
+                g0 += sb[3]; g1 += sb[4]; h0 += sb[8]; h1 += sb[9]; h2 += sb[10];
             }
         }
-        ev[1 + 2 * an] = g0;
-        ev[2 + 2 * an] = g1;
-        double *h = ev + 1 + 2 * (size_t)n_ant + 3 * (size_t)an;
+        r.ev[1 + 2 * an] = g0;
+        r.ev[2 + 2 * an] = g1;
+        double *h = r.ev + 1 + 2 * (size_t)n_ant + 3 * (size_t)an;
         h[0] = h0; h[1] = h1; h[2] = h2;
     }
 }
@@ -395,14 +447,25 @@ size_t eval_dyn_smem(int c_group, int max_tab_len) {
 
 cudaError_t launch_eval(const EvalArgs &a, bool predict, cudaStream_t s) {
     const int threads = a.t_tile * a.c_group;
-    const int blocks = a.n_bl * a.n_cg * a.n_tt;
+    const int blocks = (int)a.n_bricks;
     const size_t dyn = eval_dyn_smem(a.c_group, a.max_tab_len);
     if (predict) {
-        eval_kernel<true><<<blocks, threads, dyn, s>>>(a);
+        eval_kernel<true><<<blocks, threads, dyn, s>>>(a, nullptr, nullptr, 0, nullptr);
     } else {
-        eval_kernel<false><<<blocks, threads, dyn, s>>>(a);
+        eval_kernel<false><<<blocks, threads, dyn, s>>>(a, nullptr, nullptr, 0, nullptr);
     }
     return cudaGetLastError();
+}
+
+cudaError_t launch_eval_batch(const EvalArgs *args_dev, const long long *prefix_dev, int n_ctx,
+                              unsigned long long *queue, int threads, size_t dyn, int grid, cudaStream_t s) {
+    EvalArgs none{};
+    eval_kernel<false><<<grid, threads, dyn, s>>>(none, args_dev, prefix_dev, n_ctx, queue);
+    return cudaGetLastError();
+}
+
+cudaError_t eval_batch_occupancy(int threads, size_t dyn, int *blocks_per_sm) {
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, eval_kernel<false>, threads, dyn);
 }
 
 // Raises the fused kernel's dynamic shared-memory limit to everything the
@@ -425,15 +488,25 @@ cudaError_t set_eval_smem(size_t dyn) {
     return cudaFuncSetAttribute(eval_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)allowed);
 }
 
-cudaError_t launch_reduce(const double *partials, int n_bl, int bricks_per_bl, const int2 *pairs,
-                          int n_ant, double *blsum, double *ev, const int *skip, cudaStream_t s) {
-    (void)pairs;
+cudaError_t launch_reduce(const RedArgs &r, cudaStream_t s) {
     const int warps_per_block = 8;
-    bl_reduce_kernel<<<(n_bl + warps_per_block - 1) / warps_per_block, 32 * warps_per_block, 0, s>>>(
-        partials, n_bl, bricks_per_bl, blsum, skip);
+    bl_reduce_kernel<<<(r.n_bl + warps_per_block - 1) / warps_per_block, 32 * warps_per_block, 0, s>>>(
+        r, nullptr, nullptr, 0);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    ev_kernel<<<1, kMaxThreads, 0, s>>>(blsum, n_bl, n_ant, ev, skip);
+    ev_kernel<<<1, kMaxThreads, 0, s>>>(r, nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_batch(const RedArgs *ra_dev, const int *bl_prefix_dev, int n_ctx, int total_bl,
+                                cudaStream_t s) {
+    const int warps_per_block = 8;
+    RedArgs none{};
+    bl_reduce_kernel<<<(total_bl + warps_per_block - 1) / warps_per_block, 32 * warps_per_block, 0, s>>>(
+        none, ra_dev, bl_prefix_dev, n_ctx);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    ev_kernel<<<n_ctx, kMaxThreads, 0, s>>>(none, ra_dev);
     return cudaGetLastError();
 }
 

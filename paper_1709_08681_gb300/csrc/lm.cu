@@ -127,8 +127,10 @@ __device__ int chol64_solve(double *A, int n2, double *b) {
     return s_bad;
 }
 
-__global__ void __launch_bounds__(kLmThreads) lm_update_kernel(const LMArgs a, int small) {
+__global__ void __launch_bounds__(kLmThreads) lm_update_kernel(const LMArgs a0, const LMArgs *__restrict__ la) {
     extern __shared__ double s_dyn[];
+    const LMArgs a = la != nullptr ? la[blockIdx.x] : a0;     // batched: one block per context
+    const int small = 2 * a.n_ant <= kSmallN2;
     LMState *st = a.st;
     if (st->done) return;
     __shared__ int s_accept, s_stop;
@@ -290,7 +292,13 @@ __global__ void __launch_bounds__(kLmThreads) lm_update_kernel(const LMArgs a, i
     for (int p = tid; p < n2; p += blockDim.x) a.lm_trial[p] = a.lm_cur[p] + delta[p];
 }
 
-__global__ void lm_restart_kernel(const LMArgs a, const LMState *st0, const double *lm0) {
+__global__ void lm_restart_kernel(const LMArgs a0, const LMState *st00, const double *lm00,
+                                  const LMArgs *__restrict__ la, const LMState *const *st0s,
+                                  const double *const *lm0s) {
+    const bool batched = la != nullptr;
+    const LMArgs a = batched ? la[blockIdx.x] : a0;
+    const LMState *st0 = batched ? st0s[blockIdx.x] : st00;
+    const double *lm0 = batched ? lm0s[blockIdx.x] : lm00;
     if (threadIdx.x == 0) *a.st = *st0;
     for (int p = threadIdx.x; p < 2 * a.n_ant; p += blockDim.x) {
         a.lm_trial[p] = lm0[p];
@@ -315,14 +323,28 @@ cudaError_t lm_prepare(int n_ant) {
     return cudaFuncSetAttribute(lm_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most);
 }
 
+size_t lm_smem_bytes(int n_ant) { return lm_dyn_smem(n_ant); }
+
 cudaError_t launch_lm_restart(const LMArgs &a, const LMState *st0, const double *lm0, cudaStream_t s) {
-    lm_restart_kernel<<<1, 128, 0, s>>>(a, st0, lm0);
+    lm_restart_kernel<<<1, 128, 0, s>>>(a, st0, lm0, nullptr, nullptr, nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lm_restart_batch(const LMArgs *la_dev, const LMState *const *st0_dev,
+                                    const double *const *lm0_dev, int n_ctx, cudaStream_t s) {
+    LMArgs none{};
+    lm_restart_kernel<<<n_ctx, 128, 0, s>>>(none, nullptr, nullptr, la_dev, st0_dev, lm0_dev);
     return cudaGetLastError();
 }
 
 cudaError_t launch_lm_update(const LMArgs &a, cudaStream_t s) {
-    const int small = 2 * a.n_ant <= kSmallN2;
-    lm_update_kernel<<<1, kLmThreads, lm_dyn_smem(a.n_ant), s>>>(a, small);
+    lm_update_kernel<<<1, kLmThreads, lm_dyn_smem(a.n_ant), s>>>(a, nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lm_update_batch(const LMArgs *la_dev, int n_ctx, size_t dyn, cudaStream_t s) {
+    LMArgs none{};
+    lm_update_kernel<<<n_ctx, kLmThreads, dyn, s>>>(none, la_dev);
     return cudaGetLastError();
 }
 

@@ -204,8 +204,17 @@ extern "C" psc_status psc_residual_grad_noalloc(const psc_obs *obs, const psc_ap
     a.n_cg = n_cg;
     a.decorrelation = ap->decorrelation;
     a.max_tab_len = max_tab;
+    a.n_bricks = (long long)n_bricks;
+    RedArgs r{};
+    r.partials = d_part;
+    r.blsum = d_blsum;
+    r.ev = d_ev;
+    r.skip = nullptr;
+    r.n_bl = n_bl;
+    r.bpb = n_cg * n_tt;
+    r.n_ant = n_ant;
     NA_CUDA(launch_eval(a, false, s));
-    NA_CUDA(launch_reduce(d_part, n_bl, n_cg * n_tt, d_pairs, n_ant, d_blsum, d_ev, nullptr, s));
+    NA_CUDA(launch_reduce(r, s));
     NA_CUDA(cudaMemcpyAsync(chi2, d_ev, sizeof(double), cudaMemcpyDeviceToHost, s));
     NA_CUDA(cudaMemcpyAsync(grad, d_ev + 1, sizeof(double) * 2 * n_ant, cudaMemcpyDeviceToHost, s));
     NA_CUDA(cudaMemcpyAsync(normal, d_ev + 1 + 2 * n_ant, sizeof(double) * 3 * n_ant, cudaMemcpyDeviceToHost, s));

@@ -42,6 +42,16 @@ struct EvalArgs {
     int t_tile, c_group, n_tt, n_cg;
     int decorrelation;
     int max_tab_len;           // longest table among the channels (for shared staging)
+    long long n_bricks;        // n_bl * n_cg * n_tt (partials are [kRed][n_bricks])
+};
+
+// Arguments of the second-stage reductions of one context.
+struct RedArgs {
+    const double *partials;    // [kRed][n_bl * bpb]
+    double *blsum;             // [n_bl][kRed]
+    double *ev;                // chi2 | g[2n] | H[3n] | X[4 nbl]
+    const int *skip;           // nullptr or the solver's stop flag
+    int n_bl, bpb, n_ant;
 };
 
 // Solver state kept on the device between iterations.
@@ -71,12 +81,23 @@ __host__ __device__ inline size_t ev_len(int n_ant, int n_bl) { return 1 + 2 * (
 
 // Launchers (defined in the .cu files).
 cudaError_t launch_eval(const EvalArgs &a, bool predict, cudaStream_t s);
-cudaError_t launch_reduce(const double *partials, int n_bl, int bricks_per_bl, const int2 *pairs,
-                          int n_ant, double *blsum, double *ev, const int *skip, cudaStream_t s);
+// Persistent fused launch over several contexts (device arrays of EvalArgs and
+// first-brick prefixes [n_ctx + 1]; *queue must be zero at launch).
+cudaError_t launch_eval_batch(const EvalArgs *args_dev, const long long *prefix_dev, int n_ctx,
+                              unsigned long long *queue, int threads, size_t dyn, int grid, cudaStream_t s);
+cudaError_t eval_batch_occupancy(int threads, size_t dyn, int *blocks_per_sm);
+cudaError_t launch_reduce(const RedArgs &r, cudaStream_t s);
+cudaError_t launch_reduce_batch(const RedArgs *ra_dev, const int *bl_prefix_dev, int n_ctx, int total_bl,
+                                cudaStream_t s);
 cudaError_t launch_tables(const psc_aperture &ap, const double *freq_dev, int nc, double du, int ov,
                           int support, const int *tab_off_dev, const int *tab_len_dev, float2 *tabs,
                           cudaStream_t s);
 cudaError_t launch_lm_update(const LMArgs &a, cudaStream_t s);
+// Batched forms: one block per context (device arrays of LMArgs).
+cudaError_t launch_lm_update_batch(const LMArgs *la_dev, int n_ctx, size_t dyn, cudaStream_t s);
+cudaError_t launch_lm_restart_batch(const LMArgs *la_dev, const LMState *const *st0_dev,
+                                    const double *const *lm0_dev, int n_ctx, cudaStream_t s);
+size_t lm_smem_bytes(int n_ant);
 // Sets the LM kernel's shared-memory limit (once per device, before launches).
 cudaError_t lm_prepare(int n_ant);
 cudaError_t launch_lm_restart(const LMArgs &a, const LMState *st0, const double *lm0, cudaStream_t s);
