@@ -138,7 +138,7 @@ def cpu_sample_oracle(wl, vis_host, w_host, target_s, interval=0, min_t=1):
     timesteps of one interval, enough to take about ``target_s`` seconds."""
     from oracle import model_grid, psc
     grid = model_grid.grid_from_image(wl.image, wl.n_grid)
-    t0, nt = wl.intervals[interval]
+    t0, nt = 0, wl.n_time          # the sample may run over every interval's time steps
 
     def run(n_t):
         m = psc.Model(uvw_m=wl.uvw_m[t0:t0 + n_t], freq_hz=wl.freq_hz, n_ant=wl.n_ant, grid=grid,
@@ -154,6 +154,24 @@ def cpu_sample_oracle(wl, vis_host, w_host, target_s, interval=0, min_t=1):
     dt = run(n_t) if n_t != min_t else dt1
     n_vis = n_t * wl.n_bl * wl.n_chan
     return n_vis, dt, n_t, grid
+
+
+def profiled_traffic():
+    """DRAM bytes per fused launch from the committed ncu summary, or None
+    when eval.cu changed since the counters were taken (sha256 prefix)."""
+    import hashlib
+    import re
+    path = os.path.join(ROOT, "profiles", "eval_kernel_vla27_l64ch.md")
+    src = os.path.join(ROOT, "paper_1709_08681_gb300", "csrc", "eval.cu")
+    try:
+        text = open(path).read()
+        want = re.search(r"eval.cu sha256 prefix: ([0-9a-f]+)", text).group(1)
+        have = hashlib.sha256(open(src, "rb").read()).hexdigest()[:len(want)]
+        if want != have:
+            return None
+        return float(re.search(r"traffic per launch \(read \+ write\) \| ([0-9.]+) MB", text).group(1)) * 1e6
+    except (OSError, AttributeError, ValueError):
+        return None
 
 
 def omp_threads():
@@ -359,7 +377,7 @@ def run_ours(args):
                    "step": "one LM iteration of all intervals (one persistent fused launch, graph replay)",
                    "tiles_t": tiles, "precompute_ms": precompute_ms},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak, "traffic": profiled_traffic() if args.workload == "vla27_l64ch" else None,
                      "kernel": "eval_kernel<false>, persistent over all intervals (fused degrid + derivatives + residual + sums)",
                      "avg_launch_ms": avg_launch_ms, "flops_per_launch": flops_per_launch,
                      "peak_basis": "%d SMs x 128 FP32 lanes x 2 x 2070 MHz" % n_sm},
@@ -374,7 +392,8 @@ def run_ours(args):
         w_host = w.cpu().numpy()
         n_s, dt, n_t, _ = cpu_sample_oracle(wl, vis_host, w_host, args.cpu_seconds)
         line["cpu_baseline"] = {"value": n_s / dt / 1e9, "unit": "Gvis/s", "cores": omp_threads(), "kind": "oracle",
-                                "sample": "interval 0, first %d timesteps x %d baselines x %d channels (%d vis, %.1f s)"
+                                "sample": "first %d timesteps x %d baselines x %d channels (%d vis, %.1f s): FP64 "
+                                          "predict + derivatives + chi^2/gradient/normal sums at zero offsets"
                                           % (n_t, wl.n_bl, wl.n_chan, n_s, dt)}
     if rank == 0:
         print(json.dumps(line), flush=True)
