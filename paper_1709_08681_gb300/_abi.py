@@ -27,7 +27,7 @@ EXPORTS = ("psc_solve_opts_default", "psc_model_grid", "psc_create", "psc_destro
            "psc_lm_end", "psc_lm_restart", "psc_set_tiling", "psc_profile", "psc_profile_read",
            "psc_residual_grad_noalloc", "psc_batch_create", "psc_batch_destroy", "psc_batch_last_error",
            "psc_batch_autotune", "psc_batch_begin", "psc_batch_restart", "psc_batch_iterate", "psc_batch_end",
-           "psc_solve_batch", "psc_batch_profile", "psc_batch_profile_read")
+           "psc_solve_batch", "psc_batch_profile", "psc_batch_profile_read", "psc_features")
 
 
 class PscError(RuntimeError):
@@ -107,6 +107,7 @@ def lib():
             "psc_batch_restart": (ctypes.c_int, [_V]),
             "psc_batch_iterate": (ctypes.c_int, [_V, ctypes.c_int]),
             "psc_batch_end": (ctypes.c_int, [_V, _D, ctypes.POINTER(psc_solve_report)]),
+            "psc_features": (ctypes.c_int, [_V, _V, _V, ctypes.c_double, ctypes.c_double, ctypes.c_int, _V]),
             "psc_batch_profile": (ctypes.c_int, [_V, ctypes.c_int]),
             "psc_batch_profile_read": (ctypes.c_int, [_V, _D, ctypes.POINTER(ctypes.c_int)]),
             "psc_solve_batch": (ctypes.c_int, [ctypes.POINTER(_V), ctypes.c_int, ctypes.POINTER(_V),
@@ -247,6 +248,16 @@ class Context:
 
     def psc_lm_iterate(self, vis_obs, w=None, w_scale=1.0, n_iter=1):
         _check(lib().psc_lm_iterate(self.h, _ptr(vis_obs), _ptr(w), float(w_scale), int(n_iter)), self.h)
+
+    def psc_features(self, vis_obs, w=None, w_scale=1.0, sigma_prior=30.0 * 4.84813681109536e-06, time_stride=1,
+                     out=None):
+        """Features [n_ant][52] (torch float32 on the device of vis_obs)."""
+        import torch
+        if out is None:
+            out = torch.empty((self.n_ant, 52), dtype=torch.float32, device=vis_obs.device)
+        _check(lib().psc_features(self.h, _ptr(vis_obs), _ptr(w), float(w_scale), float(sigma_prior),
+                                  int(time_stride), _ptr(out)), self.h)
+        return out
 
     def psc_lm_restart(self):
         _check(lib().psc_lm_restart(self.h), self.h)

@@ -45,6 +45,10 @@ struct psc_ctx {
     LMState h_state{};
     std::vector<double> h_ev;
     std::string err;
+    // stencil features (psc_features)
+    double *d_spart = nullptr;
+    size_t spart_cap = 0;
+    double *d_sblsum = nullptr;
     // fused-kernel timing (psc_profile)
     bool prof = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -89,6 +93,8 @@ cudaError_t dalloc(T **p, size_t n) {
 void free_ctx(psc_ctx *c) {
     if (!c) return;
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    cudaFree(c->d_spart);
+    cudaFree(c->d_sblsum);
     cudaFree(c->d_chan); cudaFree(c->d_tabs); cudaFree(c->d_pairs); cudaFree(c->d_partials);
     cudaFree(c->d_blsum); cudaFree(c->d_ev); cudaFree(c->d_cur); cudaFree(c->d_lm_trial);
     cudaFree(c->d_lm_cur); cudaFree(c->d_mat); cudaFree(c->d_mat32); cudaFree(c->d_rhs); cudaFree(c->d_state);
@@ -502,6 +508,60 @@ psc_status psc_solve_offsets(psc_ctx *ctx, const void *vis_obs, const float *w, 
         if (done) break;
     }
     return psc_lm_end(ctx, lm_inout, rep);
+}
+
+psc_status psc_features(psc_ctx *ctx, const void *vis_obs, const float *w, double w_scale, double sigma_prior_rad,
+                        int time_stride, float *feat_dev) {
+    if (!ctx) return fail(nullptr, PSC_ERR_ARG, "ctx is NULL");
+    if (!vis_obs || !feat_dev) return fail(ctx, PSC_ERR_ARG, "vis_obs and feat must be non-NULL");
+    if (!(w_scale > 0.0) || !std::isfinite(w_scale)) return fail(ctx, PSC_ERR_ARG, "w_scale must be > 0");
+    if (!(sigma_prior_rad > 0.0) || !std::isfinite(sigma_prior_rad)) return fail(ctx, PSC_ERR_ARG, "sigma_prior must be > 0");
+    if (time_stride < 1) return fail(ctx, PSC_ERR_ARG, "time_stride must be >= 1");
+    // zero-offset evaluation: gradient and diagonal normal blocks
+    std::vector<double> zeros(2 * ctx->n_ant, 0.0);
+    PSC_CUDA(ctx, cudaMemcpyAsync(ctx->d_lm_trial, zeros.data(), sizeof(double) * zeros.size(),
+                                  cudaMemcpyHostToDevice, ctx->stream));
+    psc_status st = eval_reduce(ctx, ctx->d_lm_trial, vis_obs, w, w_scale, ctx->d_ev, nullptr);
+    if (st != PSC_OK) return st;
+    const int t_tile = 32, c_group = 4;
+    const int nts = (ctx->nt + time_stride - 1) / time_stride;
+    StencilArgs a{};
+    a.uvw = ctx->uvw;
+    a.grid = ctx->grid;
+    a.chan = ctx->d_chan;
+    a.tabs = ctx->d_tabs;
+    a.vis_obs = (const float2 *)vis_obs;
+    a.w = w;
+    a.w_scale = (float)w_scale;
+    a.n_bl = ctx->n_bl;
+    a.nt = ctx->nt;
+    a.nc = ctx->nc;
+    a.ng = ctx->gd.n_grid;
+    a.support = ctx->gd.support;
+    a.ov = ctx->gd.oversample;
+    a.du = (float)ctx->du;
+    a.t_tile = t_tile;
+    a.c_group = c_group;
+    a.n_tt = (nts + t_tile - 1) / t_tile;
+    a.n_cg = (ctx->nc + c_group - 1) / c_group;
+    a.time_stride = time_stride;
+    a.decorrelation = ctx->ap.decorrelation;
+    a.max_tab_len = ctx->max_tab_len;
+    a.n_bricks = (long long)ctx->n_bl * a.n_cg * a.n_tt;
+    a.sigma = (float)sigma_prior_rad;
+    const size_t need = (size_t)a.n_bricks * 51;
+    if (need > ctx->spart_cap) {
+        cudaFree(ctx->d_spart);
+        ctx->d_spart = nullptr;
+        ctx->spart_cap = 0;
+        PSC_CUDA(ctx, dalloc(&ctx->d_spart, need));
+        ctx->spart_cap = need;
+    }
+    if (!ctx->d_sblsum) PSC_CUDA(ctx, dalloc(&ctx->d_sblsum, (size_t)ctx->n_bl * 51));
+    a.partials = ctx->d_spart;
+    PSC_CUDA(ctx, launch_features(a, ctx->d_sblsum, ctx->d_ev, ctx->n_ant, feat_dev, ctx->stream));
+    PSC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));     // zeros[] is pageable host memory
+    return PSC_OK;
 }
 
 psc_status psc_profile(psc_ctx *ctx, int enable) {

@@ -1,0 +1,299 @@
+// Input features of the learned initial estimate (not part of the paper; an
+// addition to the method): per antenna i, the block Newton step at zero
+// offsets and a 5 x 5 trial-offset stencil.  For trial offset
+// delta_s = sigma (a, b), a, b in -2..2, on antenna i alone:
+//   A_i(s) = sum w Re(conj(V_obs) V_s) / sum w |V_s|^2
+//   C_i(s) = (chi2_i(delta_s) - chi2_i(0)) / sum w |V_0|^2,
+// sums over the baselines of i and over time steps t with t % stride == 0.
+// V_s is the model of Eq. AIJPOINTING with l_i + l_j = delta and
+// |l_i - l_j| = |delta|, which is the same whichever end of a baseline carries
+// delta, so one stencil evaluation per baseline serves both antennas.
+//
+// Stencil kernel: bricks as in the fused evaluation, but the staged grid tile
+// is not rotated.  All 25 ramps exp(i pi du sigma (dx a + dy b)) are built
+// from per-tap and per-row phasors z_x, z_y and their squares, so one A° table
+// lookup per tap serves the 25 trial offsets: per row R_a = sum A G z_x^a
+// (a = -2..2), then V[b][a] += R_a z_y^b.  Per visibility it returns
+// X_s = w Re(conj(V_obs) D_s V_s), Y_s = w |D_s V_s|^2 and Z = w |V_obs|^2.
+#include <climits>
+
+#include "psc_internal.cuh"
+
+namespace psc {
+namespace {
+
+constexpr int kTabPad = 2;
+constexpr int kSRed = 51;                 // X[25], Y[25], Z
+
+__device__ __forceinline__ float rsqrt_fast(float x) {
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ float2 lds_f2(unsigned addr) {
+    float2 v;
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(addr));
+    return v;
+}
+
+__global__ void __launch_bounds__(128) stencil_kernel(const StencilArgs a) {
+    extern __shared__ float2 s_tab[];
+    __shared__ float2 s_tile[kTile * kTile];
+    __shared__ int s_box[4];
+    __shared__ double s_red[4][kSRed];
+
+    const int tid = threadIdx.x;
+    const int brick = blockIdx.x;
+    const int tt = brick % a.n_tt;
+    const int cgi = (brick / a.n_tt) % a.n_cg;
+    const int bl = brick / (a.n_tt * a.n_cg);
+    const int lt = tid % a.t_tile;
+    const int lc = tid / a.t_tile;
+    const int t = (tt * a.t_tile + lt) * a.time_stride;
+    const int c = cgi * a.c_group + lc;
+    const bool valid = lc < a.c_group && t < a.nt && c < a.nc;
+    const int tab_stride = a.max_tab_len + kTabPad;
+
+    if (tid == 0) { s_box[0] = INT_MAX; s_box[1] = INT_MIN; s_box[2] = INT_MAX; s_box[3] = INT_MIN; }
+    __syncthreads();
+    int ix0 = 0, iy0 = 0;
+    float fx = 0.f, fy = 0.f;
+    if (valid) {
+        const double *p = a.uvw + ((size_t)t * a.n_bl + bl) * 3;
+        const double sc = a.chan[c].uv_scale;
+        const double x = p[0] * sc + 0.5 * a.ng;
+        const double y = p[1] * sc + 0.5 * a.ng;
+        const double flx = floor(x), fly = floor(y);
+        fx = (float)(x - flx);
+        fy = (float)(y - fly);
+        ix0 = (int)flx - a.support / 2 + 1;
+        iy0 = (int)fly - a.support / 2 + 1;
+        atomicMin(&s_box[0], ix0); atomicMax(&s_box[1], ix0);
+        atomicMin(&s_box[2], iy0); atomicMax(&s_box[3], iy0);
+    }
+    for (int k = tid; k < a.c_group * tab_stride; k += blockDim.x) {
+        const int cc = cgi * a.c_group + k / tab_stride;
+        const int n = k % tab_stride;
+        float2 v = make_float2(0.f, 0.f);
+        if (cc < a.nc) {
+            const ChanConst ch = a.chan[cc];
+            if (n < ch.tab_len) v = a.tabs[ch.tab_off + n];
+        }
+        s_tab[k] = v;
+    }
+    __syncthreads();
+    const int bx0 = s_box[0], by0 = s_box[2];
+    const int ex = s_box[1] - bx0 + a.support, ey = s_box[3] - by0 + a.support;
+    const bool staged = ex <= kTile && ey <= kTile;
+    if (staged) {
+        const int cshift = blockDim.x >= kTile ? 6 : 5;
+        const int cols = 1 << cshift;
+        const int rstep = blockDim.x >> cshift;
+        for (int xx = tid & (cols - 1); xx < kTile; xx += cols) {
+            const int gx = bx0 + xx;
+            const bool xin = xx < ex && gx >= 0 && gx < a.ng;
+            for (int yy = tid >> cshift; yy < ey; yy += rstep) {
+                const int gy = by0 + yy;
+                float2 g = make_float2(0.f, 0.f);
+                if (xin && gy >= 0 && gy < a.ng) g = __ldg(&a.grid[(size_t)gy * a.ng + gx]);
+                s_tile[yy * kTile + xx] = g;
+            }
+        }
+    }
+    __syncthreads();
+
+    float vr[25], vi[25];
+#pragma unroll
+    for (int s = 0; s < 25; ++s) { vr[s] = 0.f; vi[s] = 0.f; }
+    const float hx = fx + (float)(a.support / 2 - 1);
+    const float hy = fy + (float)(a.support / 2 - 1);
+    const float ph = a.du * a.sigma;                     // phase per cell per unit of a (units of pi)
+    if (valid) {
+        const ChanConst ch = a.chan[c];
+        const float2 *tab = s_tab + lc * tab_stride;
+        const unsigned tab_adj = (unsigned)__cvta_generic_to_shared(tab) - (0x4B000000u << 3);
+        const float ov = (float)a.ov;
+        const float rmax = ch.rho_max;
+        const float rmax2 = rmax * rmax;
+        const int b_lo = max(0, (int)floorf(hy - rmax) + 1);
+        const int b_hi = min(a.support - 1, (int)ceilf(hy + rmax) - 1);
+        float stp_s, stp_c;
+        sincospif(-ph, &stp_s, &stp_c);                  // z_x step per tap
+        for (int b = b_lo; b <= b_hi; ++b) {
+            const float dy = hy - (float)b;
+            const float rem = rmax2 - dy * dy;
+            if (!(rem > 0.f)) continue;
+            const float r = rem * rsqrt_fast(rem);
+            const int a_lo = max(0, (int)floorf(hx - r) + 1);
+            const int a_hi = min(a.support - 1, (int)ceilf(hx + r) - 1);
+            const float dyo = dy * ov;
+            const float dyo2 = fmaf(dyo, dyo, 1e-20f);
+            float dxo = (hx - (float)a_lo) * ov;
+            float zr, zi;
+            sincospif(ph * (hx - (float)a_lo), &zi, &zr);
+            float Rr[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, Ri[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+            for (int aa = a_lo; aa <= a_hi; ++aa) {
+                float2 g;
+                if (staged) {
+                    g = s_tile[(iy0 - by0 + b) * kTile + (ix0 - bx0 + aa)];
+                } else {
+                    const int gx = ix0 + aa, gy = iy0 + b;
+                    g = make_float2(0.f, 0.f);
+                    if (gx >= 0 && gx < a.ng && gy >= 0 && gy < a.ng) g = __ldg(&a.grid[(size_t)gy * a.ng + gx]);
+                }
+                const float s2 = fmaf(dxo, dxo, dyo2);
+                const float tv = s2 * rsqrt_fast(s2);
+                const float tf = __fadd_rz(tv, 8388608.0f);
+                const float2 e = lds_f2(tab_adj + ((unsigned)__float_as_int(tf) << 3));
+                const float A = fmaf(tv - (tf - 8388608.0f), e.y, e.x);
+                const float pr = A * g.x, pim = A * g.y;
+                const float z2r = zr * zr - zi * zi, z2i = 2.f * zr * zi;
+                Rr[2] += pr; Ri[2] += pim;
+                // p z and p conj(z), p z^2 and p conj(z^2)
+                const float a1 = pr * zr, a2 = pim * zi, a3 = pr * zi, a4 = pim * zr;
+                Rr[3] += a1 - a2; Ri[3] += a3 + a4;
+                Rr[1] += a1 + a2; Ri[1] += a4 - a3;
+                const float c1 = pr * z2r, c2 = pim * z2i, c3 = pr * z2i, c4 = pim * z2r;
+                Rr[4] += c1 - c2; Ri[4] += c3 + c4;
+                Rr[0] += c1 + c2; Ri[0] += c4 - c3;
+                const float nzr = zr * stp_c - zi * stp_s;
+                zi = zr * stp_s + zi * stp_c;
+                zr = nzr;
+                dxo -= ov;
+            }
+            float yr, yi;
+            sincospif(ph * dy, &yi, &yr);
+            const float y2r = yr * yr - yi * yi, y2i = 2.f * yr * yi;
+            // z_y^b for b = -2..2: conj(z^2), conj(z), 1, z, z^2
+            const float pbr[5] = {y2r, yr, 1.f, yr, y2r};
+            const float pbi[5] = {-y2i, -yi, 0.f, yi, y2i};
+#pragma unroll
+            for (int bb = 0; bb < 5; ++bb) {
+#pragma unroll
+                for (int aa = 0; aa < 5; ++aa) {
+                    const int sidx = bb * 5 + aa;
+                    vr[sidx] += Rr[aa] * pbr[bb] - Ri[aa] * pbi[bb];
+                    vi[sidx] += Rr[aa] * pbi[bb] + Ri[aa] * pbr[bb];
+                }
+            }
+        }
+    }
+
+    float acc[kSRed];
+#pragma unroll
+    for (int k = 0; k < kSRed; ++k) acc[k] = 0.f;
+    if (valid) {
+        const size_t k = ((size_t)t * a.n_bl + bl) * a.nc + c;
+        const float2 vo = a.vis_obs[k];
+        const float w = a.w_scale * (a.w != nullptr ? a.w[k] : 1.f);
+        const float al2s2 = a.chan[c].alpha2 * a.sigma * a.sigma;
+#pragma unroll
+        for (int bb = 0; bb < 5; ++bb) {
+#pragma unroll
+            for (int aa = 0; aa < 5; ++aa) {
+                const int sidx = bb * 5 + aa;
+                const float ia = (float)(aa - 2), ib = (float)(bb - 2);
+                const float D = a.decorrelation ? expf(-0.5f * al2s2 * (ia * ia + ib * ib)) : 1.f;
+                const float xr = D * vr[sidx], xi = D * vi[sidx];
+                acc[sidx] = w * (vo.x * xr + vo.y * xi);
+                acc[25 + sidx] = w * (xr * xr + xi * xi);
+            }
+        }
+        acc[50] = w * (vo.x * vo.x + vo.y * vo.y);
+    }
+#pragma unroll
+    for (int k = 0; k < kSRed; ++k) {
+        float v = acc[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        acc[k] = v;
+    }
+    const int warp = tid >> 5, lane = tid & 31;
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < kSRed; ++k) s_red[warp][k] = (double)acc[k];
+    }
+    __syncthreads();
+    if (tid < kSRed) {
+        double sum = 0.0;
+        const int nw = (blockDim.x + 31) >> 5;
+        for (int wi = 0; wi < nw; ++wi) sum += s_red[wi][tid];
+        a.partials[(size_t)tid * a.n_bricks + brick] = sum;
+    }
+}
+
+// Per-baseline sums of the stencil partials, one warp per baseline.
+__global__ void stencil_bl_kernel(const double *__restrict__ partials, int n_bl, int bpb, double *__restrict__ blsum) {
+    const int bl = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (bl >= n_bl) return;
+    const size_t nb = (size_t)n_bl * bpb;
+    for (int k = 0; k < kSRed; ++k) {
+        const double *p = partials + (size_t)k * nb + (size_t)bl * bpb;
+        double s = 0.0;
+        for (int b = lane; b < bpb; b += 32) s += p[b];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) blsum[(size_t)bl * kSRed + k] = s;
+    }
+}
+
+// Features per antenna (thread per antenna): block Newton step from the
+// zero-offset evaluation ev (chi2 | g | H | X) and the stencil sums.
+__global__ void features_kernel(const double *__restrict__ blsum, const double *__restrict__ ev, int n_ant,
+                                float sigma, float *__restrict__ feat) {
+    for (int an = blockIdx.x * blockDim.x + threadIdx.x; an < n_ant; an += gridDim.x * blockDim.x) {
+        const double g0 = ev[1 + 2 * an], g1 = ev[2 + 2 * an];
+        const double *H = ev + 1 + 2 * (size_t)n_ant + 3 * (size_t)an;
+        const double det = H[0] * H[2] - H[1] * H[1];
+        float s0 = 0.f, s1 = 0.f;
+        if (det > 0.0 && H[0] > 0.0) {
+            s0 = (float)(-(H[2] * g0 - H[1] * g1) / det / sigma);
+            s1 = (float)(-(-H[1] * g0 + H[0] * g1) / det / sigma);
+        }
+        double X[25], Y[25], Z = 0.0;
+        for (int s = 0; s < 25; ++s) { X[s] = 0.0; Y[s] = 0.0; }
+        for (int o = 0; o < n_ant; ++o) {
+            if (o == an) continue;
+            const int i = min(an, o), j = max(an, o);
+            const int bl = i * (2 * n_ant - i - 1) / 2 + (j - i - 1);
+            const double *b = blsum + (size_t)bl * kSRed;
+            for (int s = 0; s < 25; ++s) { X[s] += b[s]; Y[s] += b[25 + s]; }
+            Z += b[50];
+        }
+        float *f = feat + (size_t)an * 52;
+        f[0] = s0;
+        f[1] = s1;
+        const double chi0 = Z - 2.0 * X[12] + Y[12];
+        for (int s = 0; s < 25; ++s) {
+            f[2 + s] = Y[s] > 0.0 ? (float)(X[s] / Y[s]) : 0.f;
+            f[27 + s] = Y[12] > 0.0 ? (float)((Z - 2.0 * X[s] + Y[s] - chi0) / Y[12]) : 0.f;
+        }
+    }
+}
+
+}  // namespace
+
+size_t stencil_dyn_smem(int c_group, int max_tab_len) {
+    return sizeof(float2) * (size_t)c_group * (max_tab_len + kTabPad);
+}
+
+cudaError_t launch_features(const StencilArgs &a, double *blsum, const double *ev, int n_ant, float *feat,
+                            cudaStream_t s) {
+    const size_t dyn = stencil_dyn_smem(a.c_group, a.max_tab_len);
+    cudaError_t e = cudaFuncSetAttribute(stencil_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(dyn > 48 * 1024 ? dyn : 48 * 1024));
+    if (e != cudaSuccess) return e;
+    stencil_kernel<<<(int)a.n_bricks, a.t_tile * a.c_group, dyn, s>>>(a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int wpb = 8;
+    stencil_bl_kernel<<<(a.n_bl + wpb - 1) / wpb, 32 * wpb, 0, s>>>(a.partials, a.n_bl, a.n_cg * a.n_tt, blsum);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    features_kernel<<<(n_ant + 127) / 128, 128, 0, s>>>(blsum, ev, n_ant, a.sigma, feat);
+    return cudaGetLastError();
+}
+
+}  // namespace psc
