@@ -224,6 +224,43 @@ psc_status psc_set_tiling(psc_ctx *ctx, int t_tile, int c_group);
 psc_status psc_features(psc_ctx *ctx, const void *vis_obs, const float *w, double w_scale, double sigma_prior_rad,
                         int time_stride, float *feat_dev);
 
+/* ---- The learned initial estimate's network (an addition to the method) ----
+ * MLP 52 -> 256 -> 256 -> 256 -> 2 with GELU after the hidden layers, input
+ * standardised by fixed (mu, s), output the offsets in units of sigma_prior.
+ * Flat FP32 parameter vector of psc_mlp_n_params() floats:
+ *   W1 [52][256], b1 [256], W2 [256][256], b2 [256], W3 [256][256], b3 [256],
+ *   W4 [256][2], b4 [2], mu [52], s [52]   (y = x W + b; W stored [in][out]).
+ * GEMM operands are bfloat16 on the tensor cores with FP32 accumulation;
+ * master weights, biases and AdamW state are FP32.  The caller draws the
+ * initial weights and sets them with psc_mlp_set_params (which also clears
+ * the AdamW state).  Loss: (1/B) sum_b sum_o (y_bo - t_bo)^2.
+ * x_dev [batch][52], t_dev and y_dev [batch][2] are device FP32; batch is
+ * 1..max_batch.  All calls enqueue on the stream given to psc_mlp_create;
+ * those with host outputs synchronise it.  Errors: psc_last_error(NULL). */
+typedef struct psc_mlp psc_mlp;
+int psc_mlp_n_params(void);
+psc_status psc_mlp_create(psc_mlp **out, int max_batch, void *stream);
+void psc_mlp_destroy(psc_mlp *m);
+psc_status psc_mlp_set_params(psc_mlp *m, const float *params);     /* host [n_params] */
+psc_status psc_mlp_get_params(psc_mlp *m, float *params);           /* host [n_params] */
+psc_status psc_mlp_forward(psc_mlp *m, const float *x_dev, int batch, float *y_dev);
+/* Gradient of the loss at the current parameters (no update): grad_host
+ * [n_params] (zero for mu and s) and loss, either NULL to skip. */
+psc_status psc_mlp_grad(psc_mlp *m, const float *x_dev, const float *t_dev, int batch, float *grad_host,
+                        double *loss);
+/* One AdamW step (beta 0.9 / 0.999, eps 1e-8, weight decay 1e-4, learning
+ * rate lr) on the trained parameters; loss (before the step) if non-NULL. */
+psc_status psc_mlp_train_step(psc_mlp *m, const float *x_dev, const float *t_dev, int batch, double lr,
+                              double *loss);
+/* Offsets (rad, host [n_ant][2]) from features feat_dev [n_ant][52]:
+ * network output times sigma_prior_rad. */
+psc_status psc_mlp_infer_offsets(psc_mlp *m, const float *feat_dev, int n_ant, double sigma_prior_rad,
+                                 double *lm_out);
+/* The learned initial estimate of a context: psc_features then
+ * psc_mlp_infer_offsets (max_batch >= n_ant).  lm_out host [n_ant][2]. */
+psc_status psc_learned_init(psc_ctx *ctx, psc_mlp *m, const void *vis_obs, const float *w, double w_scale,
+                            double sigma_prior_rad, int time_stride, double *lm_out);
+
 /* ---- Batches of solution intervals (Algorithm 1's loop over all data) ----
  * A batch groups contexts -- normally one per solution interval, of any
  * array, length and channel set -- with their observed data, so that one LM

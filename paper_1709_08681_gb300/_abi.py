@@ -27,7 +27,9 @@ EXPORTS = ("psc_solve_opts_default", "psc_model_grid", "psc_create", "psc_destro
            "psc_lm_end", "psc_lm_restart", "psc_set_tiling", "psc_profile", "psc_profile_read",
            "psc_residual_grad_noalloc", "psc_batch_create", "psc_batch_destroy", "psc_batch_last_error",
            "psc_batch_autotune", "psc_batch_begin", "psc_batch_restart", "psc_batch_iterate", "psc_batch_end",
-           "psc_solve_batch", "psc_batch_profile", "psc_batch_profile_read", "psc_features")
+           "psc_solve_batch", "psc_batch_profile", "psc_batch_profile_read", "psc_features",
+           "psc_mlp_n_params", "psc_mlp_create", "psc_mlp_destroy", "psc_mlp_set_params", "psc_mlp_get_params",
+           "psc_mlp_forward", "psc_mlp_grad", "psc_mlp_train_step", "psc_mlp_infer_offsets", "psc_learned_init")
 
 
 class PscError(RuntimeError):
@@ -107,6 +109,16 @@ def lib():
             "psc_batch_restart": (ctypes.c_int, [_V]),
             "psc_batch_iterate": (ctypes.c_int, [_V, ctypes.c_int]),
             "psc_batch_end": (ctypes.c_int, [_V, _D, ctypes.POINTER(psc_solve_report)]),
+            "psc_mlp_n_params": (ctypes.c_int, []),
+            "psc_mlp_create": (ctypes.c_int, [ctypes.POINTER(_V), ctypes.c_int, _V]),
+            "psc_mlp_destroy": (None, [_V]),
+            "psc_mlp_set_params": (ctypes.c_int, [_V, ctypes.POINTER(ctypes.c_float)]),
+            "psc_mlp_get_params": (ctypes.c_int, [_V, ctypes.POINTER(ctypes.c_float)]),
+            "psc_mlp_forward": (ctypes.c_int, [_V, _V, ctypes.c_int, _V]),
+            "psc_mlp_grad": (ctypes.c_int, [_V, _V, _V, ctypes.c_int, ctypes.POINTER(ctypes.c_float), _D]),
+            "psc_mlp_train_step": (ctypes.c_int, [_V, _V, _V, ctypes.c_int, ctypes.c_double, _D]),
+            "psc_mlp_infer_offsets": (ctypes.c_int, [_V, _V, ctypes.c_int, ctypes.c_double, _D]),
+            "psc_learned_init": (ctypes.c_int, [_V, _V, _V, _V, ctypes.c_double, ctypes.c_double, ctypes.c_int, _D]),
             "psc_features": (ctypes.c_int, [_V, _V, _V, ctypes.c_double, ctypes.c_double, ctypes.c_int, _V]),
             "psc_batch_profile": (ctypes.c_int, [_V, ctypes.c_int]),
             "psc_batch_profile_read": (ctypes.c_int, [_V, _D, ctypes.POINTER(ctypes.c_int)]),
@@ -259,6 +271,13 @@ class Context:
                                   int(time_stride), _ptr(out)), self.h)
         return out
 
+    def psc_learned_init(self, mlp, vis_obs, w=None, w_scale=1.0, sigma_prior=30.0 * 4.84813681109536e-06,
+                         time_stride=1):
+        lm = np.zeros((self.n_ant, 2))
+        _check(lib().psc_learned_init(self.h, mlp.h, _ptr(vis_obs), _ptr(w), float(w_scale), float(sigma_prior),
+                                      int(time_stride), _dp(lm)), self.h)
+        return lm
+
     def psc_lm_restart(self):
         _check(lib().psc_lm_restart(self.h), self.h)
 
@@ -379,3 +398,57 @@ def psc_solve_batch(contexts, vis_obs, w=None, w_scale=None, lm0_list=None, opts
         out.append(flat[off:off + 2 * a].reshape(a, 2))
         off += 2 * a
     return out, list(reps)
+
+
+class Mlp:
+    """Owns one ``psc_mlp`` (the learned initial estimate's network)."""
+
+    def __init__(self, max_batch, stream=None):
+        h = _V()
+        _check(lib().psc_mlp_create(ctypes.byref(h), int(max_batch), _stream(stream)))
+        self.h = h
+        self.n_params = lib().psc_mlp_n_params()
+        self.max_batch = int(max_batch)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().psc_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def psc_mlp_set_params(self, params):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        if p.size != self.n_params:
+            raise ValueError("params must have %d entries" % self.n_params)
+        _check(lib().psc_mlp_set_params(self.h, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+
+    def psc_mlp_get_params(self):
+        p = np.zeros(self.n_params, dtype=np.float32)
+        _check(lib().psc_mlp_get_params(self.h, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+        return p
+
+    def psc_mlp_forward(self, x_dev, out=None):
+        import torch
+        B = x_dev.shape[0]
+        if out is None:
+            out = torch.empty((B, 2), dtype=torch.float32, device=x_dev.device)
+        _check(lib().psc_mlp_forward(self.h, _ptr(x_dev), int(B), _ptr(out)))
+        return out
+
+    def psc_mlp_grad(self, x_dev, t_dev):
+        g = np.zeros(self.n_params, dtype=np.float32)
+        loss = np.zeros(1)
+        _check(lib().psc_mlp_grad(self.h, _ptr(x_dev), _ptr(t_dev), int(x_dev.shape[0]),
+                                  g.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), _dp(loss)))
+        return float(loss[0]), g
+
+    def psc_mlp_train_step(self, x_dev, t_dev, lr, want_loss=False):
+        loss = np.zeros(1)
+        _check(lib().psc_mlp_train_step(self.h, _ptr(x_dev), _ptr(t_dev), int(x_dev.shape[0]), float(lr),
+                                        _dp(loss) if want_loss else None))
+        return float(loss[0]) if want_loss else None

@@ -49,6 +49,7 @@ struct psc_ctx {
     double *d_spart = nullptr;
     size_t spart_cap = 0;
     double *d_sblsum = nullptr;
+    float *d_feat = nullptr;     // [n_ant][52] (psc_learned_init)
     // fused-kernel timing (psc_profile)
     bool prof = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -95,6 +96,7 @@ void free_ctx(psc_ctx *c) {
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     cudaFree(c->d_spart);
     cudaFree(c->d_sblsum);
+    cudaFree(c->d_feat);
     cudaFree(c->d_chan); cudaFree(c->d_tabs); cudaFree(c->d_pairs); cudaFree(c->d_partials);
     cudaFree(c->d_blsum); cudaFree(c->d_ev); cudaFree(c->d_cur); cudaFree(c->d_lm_trial);
     cudaFree(c->d_lm_cur); cudaFree(c->d_mat); cudaFree(c->d_mat32); cudaFree(c->d_rhs); cudaFree(c->d_state);
@@ -561,6 +563,18 @@ psc_status psc_features(psc_ctx *ctx, const void *vis_obs, const float *w, doubl
     a.partials = ctx->d_spart;
     PSC_CUDA(ctx, launch_features(a, ctx->d_sblsum, ctx->d_ev, ctx->n_ant, feat_dev, ctx->stream));
     PSC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));     // zeros[] is pageable host memory
+    return PSC_OK;
+}
+
+psc_status psc_learned_init(psc_ctx *ctx, psc_mlp *m, const void *vis_obs, const float *w, double w_scale,
+                            double sigma_prior_rad, int time_stride, double *lm_out) {
+    if (!ctx) return fail(nullptr, PSC_ERR_ARG, "ctx is NULL");
+    if (!m || !lm_out) return fail(ctx, PSC_ERR_ARG, "mlp and lm_out must be non-NULL");
+    if (!ctx->d_feat) PSC_CUDA(ctx, dalloc(&ctx->d_feat, (size_t)ctx->n_ant * 52));
+    psc_status st = psc_features(ctx, vis_obs, w, w_scale, sigma_prior_rad, time_stride, ctx->d_feat);
+    if (st != PSC_OK) return st;
+    st = psc_mlp_infer_offsets(m, ctx->d_feat, ctx->n_ant, sigma_prior_rad, lm_out);
+    if (st != PSC_OK) return fail(ctx, st, psc_last_error(nullptr));
     return PSC_OK;
 }
 
