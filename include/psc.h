@@ -211,7 +211,7 @@ psc_status psc_set_tiling(psc_ctx *ctx, int t_tile, int c_group);
 /* Input features of the learned initial estimate (an addition to the
  * paper's method: the paper starts the minimiser from zero or from previous
  * solutions).  For each antenna i, 52 floats in feat_dev (device
- * [n_ant][52]):
+ * [n_ant][52]), all from the time steps t with t % time_stride == 0:
  *   [0..1]   the block Newton step -H_ii^{-1} g_i at zero offsets (Eq. DCHIDD
  *            gradient, Gauss-Newton 2x2 block), divided by sigma_prior_rad;
  *   [2..26]  A_i(s) = sum w Re(conj(V_obs) V_s) / sum w |V_s|^2,
@@ -219,8 +219,8 @@ psc_status psc_set_tiling(psc_ctx *ctx, int t_tile, int c_group);
  * for the 25 trial offsets delta_s = sigma_prior_rad (a, b), a, b = -2..2
  * (row-major over b, then a; a moves l, b moves m), applied to antenna i
  * alone, with V_s the model of Eq. AIJPOINTING and sums over the baselines
- * of i and the time steps t with t % time_stride == 0.  Overwrites the
- * context's evaluation state (call it before psc_lm_begin).  Synchronises. */
+ * of i.  One strided pass of one kernel.  Asynchronous (enqueued on the
+ * context's stream). */
 psc_status psc_features(psc_ctx *ctx, const void *vis_obs, const float *w, double w_scale, double sigma_prior_rad,
                         int time_stride, float *feat_dev);
 

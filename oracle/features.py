@@ -19,7 +19,8 @@ trial-offset stencil, read as 2 + 25 + 25 = 52 numbers:
   l_i + l_j and |l_i - l_j| (ramp and decorrelation), putting delta on i or on
   j gives the same V_s: one evaluation per baseline serves both antennas.
 
-Only time steps t with t % time_stride == 0 enter the stencil sums.  Feature
+Only time steps t with t % time_stride == 0 enter the sums (the gradient
+block as well as the stencil).  Feature
 order: [step_l, step_m, A(s) for s in row-major (b, a), C(s) likewise], with
 a indexing the l offset and b the m offset.
 """
@@ -62,7 +63,8 @@ def features(model: psc.Model, vis_obs, w, sigma_prior: float, time_stride: int 
     vis_obs = np.asarray(vis_obs, dtype=np.complex128)
     w = np.ones(vis_obs.shape) if w is None else np.asarray(w, dtype=np.float64)
     n = model.n_ant
-    chi2, g, H, X = psc.chi2_grad_normal(model, np.zeros((n, 2)), vis_obs, w)
+    strided = psc.Model(**{**model.__dict__, "uvw_m": model.uvw_m[::time_stride]})
+    chi2, g, H, X = psc.chi2_grad_normal(strided, np.zeros((n, 2)), vis_obs[::time_stride], w[::time_stride])
     step = np.zeros((n, 2))
     for i in range(n):
         Hi = np.array([[H[i, 0], H[i, 1]], [H[i, 1], H[i, 2]]])

@@ -519,12 +519,6 @@ psc_status psc_features(psc_ctx *ctx, const void *vis_obs, const float *w, doubl
     if (!(w_scale > 0.0) || !std::isfinite(w_scale)) return fail(ctx, PSC_ERR_ARG, "w_scale must be > 0");
     if (!(sigma_prior_rad > 0.0) || !std::isfinite(sigma_prior_rad)) return fail(ctx, PSC_ERR_ARG, "sigma_prior must be > 0");
     if (time_stride < 1) return fail(ctx, PSC_ERR_ARG, "time_stride must be >= 1");
-    // zero-offset evaluation: gradient and diagonal normal blocks
-    std::vector<double> zeros(2 * ctx->n_ant, 0.0);
-    PSC_CUDA(ctx, cudaMemcpyAsync(ctx->d_lm_trial, zeros.data(), sizeof(double) * zeros.size(),
-                                  cudaMemcpyHostToDevice, ctx->stream));
-    psc_status st = eval_reduce(ctx, ctx->d_lm_trial, vis_obs, w, w_scale, ctx->d_ev, nullptr);
-    if (st != PSC_OK) return st;
     const int t_tile = 32, c_group = 4;
     const int nts = (ctx->nt + time_stride - 1) / time_stride;
     StencilArgs a{};
@@ -551,7 +545,7 @@ psc_status psc_features(psc_ctx *ctx, const void *vis_obs, const float *w, doubl
     a.max_tab_len = ctx->max_tab_len;
     a.n_bricks = (long long)ctx->n_bl * a.n_cg * a.n_tt;
     a.sigma = (float)sigma_prior_rad;
-    const size_t need = (size_t)a.n_bricks * 51;
+    const size_t need = (size_t)a.n_bricks * 56;
     if (need > ctx->spart_cap) {
         cudaFree(ctx->d_spart);
         ctx->d_spart = nullptr;
@@ -559,10 +553,9 @@ psc_status psc_features(psc_ctx *ctx, const void *vis_obs, const float *w, doubl
         PSC_CUDA(ctx, dalloc(&ctx->d_spart, need));
         ctx->spart_cap = need;
     }
-    if (!ctx->d_sblsum) PSC_CUDA(ctx, dalloc(&ctx->d_sblsum, (size_t)ctx->n_bl * 51));
+    if (!ctx->d_sblsum) PSC_CUDA(ctx, dalloc(&ctx->d_sblsum, (size_t)ctx->n_bl * 56));
     a.partials = ctx->d_spart;
-    PSC_CUDA(ctx, launch_features(a, ctx->d_sblsum, ctx->d_ev, ctx->n_ant, feat_dev, ctx->stream));
-    PSC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));     // zeros[] is pageable host memory
+    PSC_CUDA(ctx, launch_features(a, ctx->d_sblsum, ctx->n_ant, feat_dev, ctx->stream));
     return PSC_OK;
 }
 

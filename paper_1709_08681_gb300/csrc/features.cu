@@ -1,6 +1,7 @@
 // Input features of the learned initial estimate (not part of the paper; an
 // addition to the method): per antenna i, the block Newton step at zero
-// offsets and a 5 x 5 trial-offset stencil.  For trial offset
+// offsets and a 5 x 5 trial-offset stencil, all from one pass over the time
+// steps t with t % stride == 0.  For trial offset
 // delta_s = sigma (a, b), a, b in -2..2, on antenna i alone:
 //   A_i(s) = sum w Re(conj(V_obs) V_s) / sum w |V_s|^2
 //   C_i(s) = (chi2_i(delta_s) - chi2_i(0)) / sum w |V_0|^2,
@@ -13,8 +14,12 @@
 // is not rotated.  All 25 ramps exp(i pi du sigma (dx a + dy b)) are built
 // from per-tap and per-row phasors z_x, z_y and their squares, so one A° table
 // lookup per tap serves the 25 trial offsets: per row R_a = sum A G z_x^a
-// (a = -2..2), then V[b][a] += R_a z_y^b.  Per visibility it returns
-// X_s = w Re(conj(V_obs) D_s V_s), Y_s = w |D_s V_s|^2 and Z = w |V_obs|^2.
+// (a = -2..2), then V[b][a] += R_a z_y^b.  The centre point also carries the
+// derivative sums of Eq. DAIJPOINTING at zero offsets (dV/dl = i pi Tu,
+// dV/dm = i pi Tv, the same for both antennas there).  Per visibility it
+// returns X_s = w Re(conj(V_obs) D_s V_s), Y_s = w |D_s V_s|^2,
+// Z = w |V_obs|^2, and the gradient (g_l, g_m) and Gauss-Newton block
+// (H_ll, H_lm, H_mm) terms of Eqs. Chisq / DCHIDD at zero offsets.
 #include <climits>
 
 #include "psc_internal.cuh"
@@ -23,7 +28,7 @@ namespace psc {
 namespace {
 
 constexpr int kTabPad = 2;
-constexpr int kSRed = 51;                 // X[25], Y[25], Z
+constexpr int kSRed = 56;                 // X[25], Y[25], Z, g_l, g_m, H_ll, H_lm, H_mm
 
 __device__ __forceinline__ float rsqrt_fast(float x) {
     float r;
@@ -106,6 +111,7 @@ __global__ void __launch_bounds__(128) stencil_kernel(const StencilArgs a) {
     float vr[25], vi[25];
 #pragma unroll
     for (int s = 0; s < 25; ++s) { vr[s] = 0.f; vi[s] = 0.f; }
+    float sur = 0.f, sui = 0.f, svr = 0.f, svi = 0.f;    // centre-point derivative sums
     const float hx = fx + (float)(a.support / 2 - 1);
     const float hy = fy + (float)(a.support / 2 - 1);
     const float ph = a.du * a.sigma;                     // phase per cell per unit of a (units of pi)
@@ -133,6 +139,7 @@ __global__ void __launch_bounds__(128) stencil_kernel(const StencilArgs a) {
             float zr, zi;
             sincospif(ph * (hx - (float)a_lo), &zi, &zr);
             float Rr[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, Ri[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+            float qr = 0.f, qi = 0.f;
             for (int aa = a_lo; aa <= a_hi; ++aa) {
                 float2 g;
                 if (staged) {
@@ -148,6 +155,9 @@ __global__ void __launch_bounds__(128) stencil_kernel(const StencilArgs a) {
                 const float2 e = lds_f2(tab_adj + ((unsigned)__float_as_int(tf) << 3));
                 const float A = fmaf(tv - (tf - 8388608.0f), e.y, e.x);
                 const float pr = A * g.x, pim = A * g.y;
+                const float Ad = A * dxo;
+                qr = fmaf(Ad, g.x, qr);
+                qi = fmaf(Ad, g.y, qi);
                 const float z2r = zr * zr - zi * zi, z2i = 2.f * zr * zi;
                 Rr[2] += pr; Ri[2] += pim;
                 // p z and p conj(z), p z^2 and p conj(z^2)
@@ -162,6 +172,10 @@ __global__ void __launch_bounds__(128) stencil_kernel(const StencilArgs a) {
                 zr = nzr;
                 dxo -= ov;
             }
+            sur += qr;
+            sui += qi;
+            svr = fmaf(dy, Rr[2], svr);
+            svi = fmaf(dy, Ri[2], svi);
             float yr, yi;
             sincospif(ph * dy, &yi, &yr);
             const float y2r = yr * yr - yi * yi, y2i = 2.f * yr * yi;
@@ -201,6 +215,18 @@ __global__ void __launch_bounds__(128) stencil_kernel(const StencilArgs a) {
             }
         }
         acc[50] = w * (vo.x * vo.x + vo.y * vo.y);
+        // zero offsets: V_0 = centre sum, dV/dl = i pi du Su, dV/dm = i pi du Sv
+        const float pi_du = 3.14159265358979f * a.du;
+        const float inv_ov = 1.0f / (float)a.ov;
+        const float2 dl = make_float2(-pi_du * sui * inv_ov, pi_du * sur * inv_ov);
+        const float2 dm = make_float2(-pi_du * svi, pi_du * svr);
+        const float2 R = make_float2(vo.x - vr[12], vo.y - vi[12]);
+        const float w2 = 2.f * w;
+        acc[51] = -w2 * (R.x * dl.x + R.y * dl.y);
+        acc[52] = -w2 * (R.x * dm.x + R.y * dm.y);
+        acc[53] = w2 * (dl.x * dl.x + dl.y * dl.y);
+        acc[54] = w2 * (dl.x * dm.x + dl.y * dm.y);
+        acc[55] = w2 * (dm.x * dm.x + dm.y * dm.y);
     }
 #pragma unroll
     for (int k = 0; k < kSRed; ++k) {
@@ -239,20 +265,11 @@ __global__ void stencil_bl_kernel(const double *__restrict__ partials, int n_bl,
     }
 }
 
-// Features per antenna (thread per antenna): block Newton step from the
-// zero-offset evaluation ev (chi2 | g | H | X) and the stencil sums.
-__global__ void features_kernel(const double *__restrict__ blsum, const double *__restrict__ ev, int n_ant,
-                                float sigma, float *__restrict__ feat) {
+// Features per antenna (thread per antenna): sums over its baselines, then
+// the block Newton step and the stencil ratios.
+__global__ void features_kernel(const double *__restrict__ blsum, int n_ant, float sigma, float *__restrict__ feat) {
     for (int an = blockIdx.x * blockDim.x + threadIdx.x; an < n_ant; an += gridDim.x * blockDim.x) {
-        const double g0 = ev[1 + 2 * an], g1 = ev[2 + 2 * an];
-        const double *H = ev + 1 + 2 * (size_t)n_ant + 3 * (size_t)an;
-        const double det = H[0] * H[2] - H[1] * H[1];
-        float s0 = 0.f, s1 = 0.f;
-        if (det > 0.0 && H[0] > 0.0) {
-            s0 = (float)(-(H[2] * g0 - H[1] * g1) / det / sigma);
-            s1 = (float)(-(-H[1] * g0 + H[0] * g1) / det / sigma);
-        }
-        double X[25], Y[25], Z = 0.0;
+        double X[25], Y[25], Z = 0.0, g0 = 0.0, g1 = 0.0, H[3] = {0.0, 0.0, 0.0};
         for (int s = 0; s < 25; ++s) { X[s] = 0.0; Y[s] = 0.0; }
         for (int o = 0; o < n_ant; ++o) {
             if (o == an) continue;
@@ -261,6 +278,14 @@ __global__ void features_kernel(const double *__restrict__ blsum, const double *
             const double *b = blsum + (size_t)bl * kSRed;
             for (int s = 0; s < 25; ++s) { X[s] += b[s]; Y[s] += b[25 + s]; }
             Z += b[50];
+            g0 += b[51]; g1 += b[52];
+            H[0] += b[53]; H[1] += b[54]; H[2] += b[55];
+        }
+        const double det = H[0] * H[2] - H[1] * H[1];
+        float s0 = 0.f, s1 = 0.f;
+        if (det > 0.0 && H[0] > 0.0) {
+            s0 = (float)(-(H[2] * g0 - H[1] * g1) / det / sigma);
+            s1 = (float)(-(-H[1] * g0 + H[0] * g1) / det / sigma);
         }
         float *f = feat + (size_t)an * 52;
         f[0] = s0;
@@ -279,8 +304,7 @@ size_t stencil_dyn_smem(int c_group, int max_tab_len) {
     return sizeof(float2) * (size_t)c_group * (max_tab_len + kTabPad);
 }
 
-cudaError_t launch_features(const StencilArgs &a, double *blsum, const double *ev, int n_ant, float *feat,
-                            cudaStream_t s) {
+cudaError_t launch_features(const StencilArgs &a, double *blsum, int n_ant, float *feat, cudaStream_t s) {
     const size_t dyn = stencil_dyn_smem(a.c_group, a.max_tab_len);
     cudaError_t e = cudaFuncSetAttribute(stencil_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)(dyn > 48 * 1024 ? dyn : 48 * 1024));
@@ -292,7 +316,7 @@ cudaError_t launch_features(const StencilArgs &a, double *blsum, const double *e
     stencil_bl_kernel<<<(a.n_bl + wpb - 1) / wpb, 32 * wpb, 0, s>>>(a.partials, a.n_bl, a.n_cg * a.n_tt, blsum);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    features_kernel<<<(n_ant + 127) / 128, 128, 0, s>>>(blsum, ev, n_ant, a.sigma, feat);
+    features_kernel<<<(n_ant + 127) / 128, 128, 0, s>>>(blsum, n_ant, a.sigma, feat);
     return cudaGetLastError();
 }
 

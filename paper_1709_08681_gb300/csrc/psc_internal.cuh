@@ -54,7 +54,7 @@ struct StencilArgs {
     const float2 *vis_obs;
     const float *w;
     float w_scale;
-    double *partials;          // [51][n_bricks]
+    double *partials;          // [56][n_bricks]
     int n_bl, nt, nc, ng, support, ov;
     float du;
     int t_tile, c_group, n_tt, n_cg, time_stride;   // n_tt counts the kept (strided) time steps
@@ -125,8 +125,7 @@ cudaError_t set_eval_smem(size_t dyn);
 size_t eval_dyn_smem(int c_group, int max_tab_len);
 // Records msg as the context-free last error (psc_last_error(NULL)); returns st.
 psc_status set_global_error(psc_status st, const char *msg);
-cudaError_t launch_features(const StencilArgs &a, double *blsum, const double *ev, int n_ant, float *feat,
-                            cudaStream_t s);
+cudaError_t launch_features(const StencilArgs &a, double *blsum, int n_ant, float *feat, cudaStream_t s);
 cudaError_t launch_model_grid(int n_img, int n_grid, const float *image, float2 *tmp, float2 *twiddle,
                               float2 *grid_out, cudaStream_t s);
 

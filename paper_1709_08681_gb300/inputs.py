@@ -180,6 +180,7 @@ class Workload:
     alpha_per_dlambda: float
     decorrelation: int
     lm_true: np.ndarray    # [n_interval][n_ant][2]
+    sigma_pt: float        # rms of the true offsets per axis (rad)
     sigma_noise: float
     intervals: list
     seed: int
@@ -212,11 +213,12 @@ def _hour_angles(r: dict) -> np.ndarray:
     """Hour angles (rad): ``n_time`` samples evenly spread over ``span_h``
     hours, or spaced ``dt_s`` seconds apart, centred on transit."""
     n_t = r["n_time"]
+    centre = r.get("ha_centre_h", 0.0) * 15.0 * DEG
     if "dt_s" in r:
-        return (np.arange(n_t) - (n_t - 1) / 2.0) * r["dt_s"] / 3600.0 * 15.0 * DEG
+        return centre + (np.arange(n_t) - (n_t - 1) / 2.0) * r["dt_s"] / 3600.0 * 15.0 * DEG
     if n_t == 1:
-        return np.zeros(1)
-    return np.linspace(-r["span_h"] / 2, r["span_h"] / 2, n_t) * 15.0 * DEG
+        return np.full(1, centre)
+    return centre + np.linspace(-r["span_h"] / 2, r["span_h"] / 2, n_t) * 15.0 * DEG
 
 
 def make_workload(name: str, seed: int = 0, **over) -> Workload:
@@ -248,15 +250,27 @@ def make_workload(name: str, seed: int = 0, **over) -> Workload:
         image=img, cell_rad=cell, n_grid=r["n_img"] * r["pad"], support=r["support"],
         oversample=r["oversample"], ap_kind=r["ap_kind"], diam_m=r["diam_m"],
         alpha_per_dlambda=r.get("alpha_per_dlambda", ALPHA_PER_DLAMBDA_DISK),
-        decorrelation=r["decorrelation"], lm_true=lm_true, sigma_noise=r["noise_jy"],
+        decorrelation=r["decorrelation"], lm_true=lm_true, sigma_pt=r["sigma_pt_arcsec"] * ARCSEC,
+        sigma_noise=r["noise_jy"],
         intervals=intervals, seed=seed)
 
 
-# Recipes.  "vla27_l1ch": the small plain-method case (27 antennas, one
+# Recipes.  "disk64_l16ch": the learned-initialiser case (64 antennas of
+# 13.5 m in a centrally concentrated disk of 4 km radius, 16 channels over
+# 1.3-1.5 GHz, 60 x 10 s, offsets sigma 30", 0.5 mJy noise, 200 sources in
+# the primary beam on a 2048^2 image of 2.5" padded to 8192^2);
+# "vla27_l1ch": the small plain-method case (27 antennas, one
 # channel at 1.4 GHz, 60 x 10 s over +-1 h, 50 sources on a 256^2 image at
 # 6"); "vla27_l64ch": the precision-study case (64 channels over 1-2 GHz,
 # 600 x 2 s in 4 solution intervals, 2000 sources on a 2048^2 image).
 WORKLOADS = {
+    "disk64_l16ch": dict(
+        layout="disk", n_ant=64, extent_m=4000.0, lat_deg=34.0, dec_deg=30.0,
+        n_time=60, dt_s=10.0, n_chan=16, f_lo=1.3e9, f_hi=1.5e9,
+        n_src=200, src_radius_arcmin=30.0, flux=("powerlaw", 1e-4, 1.0, -1.5),
+        n_img=2048, cell_arcsec=2.5, pad=4, support=32, oversample=20,
+        ap_kind="disk", diam_m=13.5, decorrelation=1,
+        sigma_pt_arcsec=30.0, noise_jy=5e-4, n_interval=1),
     "vla27_l1ch": dict(
         layout="y", n_ant=27, extent_m=1000.0, lat_deg=34.0, dec_deg=30.0,
         n_time=60, span_h=2.0, n_chan=1, f_lo=1.4e9, f_hi=1.4e9,
