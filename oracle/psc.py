@@ -110,6 +110,32 @@ def predict(model: Model, lm: np.ndarray, with_derivs: bool = True):
     return V, dV
 
 
+def predict_points(model: Model, lm, t_idx, bl_idx, ch_idx):
+    """V and dV (dV/dl_i, dV/dm_i, dV/dl_j, dV/dm_j) of selected visibilities
+    (index arrays into [nt][nbl][nc]), by the same formulas as ``predict``."""
+    lm = np.asarray(lm, dtype=np.float64)
+    t_idx, bl_idx, ch_idx = (np.asarray(x, dtype=np.int64) for x in (t_idx, bl_idx, ch_idx))
+    ij = model.antenna_pairs()[bl_idx]
+    li, mi = lm[ij[:, 0], 0], lm[ij[:, 0], 1]
+    lj, mj = lm[ij[:, 1], 0], lm[ij[:, 1], 1]
+    f = np.asarray(model.freq_hz, dtype=np.float64)[ch_idx] / C_LIGHT
+    u = model.uvw_m[t_idx, bl_idx, 0] * f
+    v = model.uvw_m[t_idx, bl_idx, 1] * f
+    t0, tu, tv = degrid_sums(u, v, li + lj, mi + mj, ch_idx, model.tables(), model.grid, model.du,
+                             model.support, model.oversample)
+    a2 = model.alpha()[ch_idx] ** 2
+    if model.decorrelation:
+        D = np.exp(-a2 * ((li - lj) ** 2 + (mi - mj) ** 2) / 2.0)
+        dl, dm = (lj - li) * a2, (mj - mi) * a2
+    else:
+        D, dl, dm = np.ones_like(u), np.zeros_like(u), np.zeros_like(u)
+    ipi = 1j * math.pi
+    V = D * t0
+    dV = np.stack([D * (dl * t0 + ipi * tu), D * (dm * t0 + ipi * tv),
+                   D * (-dl * t0 + ipi * tu), D * (-dm * t0 + ipi * tv)])
+    return V, dV
+
+
 def chi2_grad_normal(model: Model, lm, vis_obs, w=None):
     """chi^2, gradient g [n_ant][2] (d/dl, d/dm), diagonal normal blocks
     H [n_ant][3] = (H_ll, H_lm, H_mm) and per-baseline cross blocks

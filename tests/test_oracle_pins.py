@@ -312,3 +312,13 @@ def test_scatter_matches_fisher_information():
     pred = np.sqrt(np.diag(2.0 * np.linalg.inv(A)))
     ratio = spread / pred
     assert 0.7 < np.median(ratio) < 1.3
+
+
+def test_predict_points_equals_predict():
+    m, _, lm, _ = cases.problem(cases.DISK_SMALL, n_ant=5, n_time=7, freqs=(1.3e9, 1.4e9), sigma_arcsec=40.0)
+    V, dV = psc.predict(m, lm)
+    rng = np.random.default_rng(0)
+    t, b, c = rng.integers(0, 7, 30), rng.integers(0, 10, 30), rng.integers(0, 2, 30)
+    Vp, dVp = psc.predict_points(m, lm, t, b, c)
+    assert np.allclose(Vp, V[t, b, c], rtol=1e-13, atol=1e-15)
+    assert np.allclose(dVp, dV[:, t, b, c], rtol=1e-13, atol=1e-12)
