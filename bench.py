@@ -53,14 +53,15 @@ def parse():
     p.add_argument("--seed", type=int, default=0)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
+    p.add_argument("--no-learned", action="store_true", help="skip the learned-initialiser comparison")
+    p.add_argument("--learned-train", type=int, default=1000, help="training intervals of the learned initialiser")
+    p.add_argument("--learned-eval", type=int, default=20, help="held-out intervals of the comparison")
     return p.parse_args()
 
 
 def dist_env():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
+    from paper_1709_08681_gb300 import dist as D
+    return D.rank_info()
 
 
 # ---------------------------------------------------------------- clocks
@@ -234,7 +235,8 @@ def run_ours(args):
     from paper_1709_08681_gb300.session import Session
 
     # weak scaling: every rank solves its own batch of four intervals (own seed)
-    wl = I.make_workload(args.workload, seed=args.seed + rank)
+    from paper_1709_08681_gb300 import dist as D
+    wl = I.make_workload(args.workload, seed=D.rank_seed(args.seed, rank))
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -297,10 +299,7 @@ def run_ours(args):
         time.sleep(0.2)
         sampler.stop()
         clocks = sampler.summary(t_wall0, t_wall1)
-        if ws > 1:
-            t = torch.tensor([ms], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = D.max_over_ranks(ms, device="cuda")
 
         n_vis = wl.n_vis
         value = ws * n_vis * args.steps / (ms * 1e-3) / 1e9
@@ -342,7 +341,7 @@ def run_ours(args):
             batch_e2e.psc_batch_iterate(1)
             lm_out, reps = batch_e2e.psc_batch_end()   # synchronises; offsets + chi^2 to the host
             d2h = sum(x.nbytes for x in lm_out) + 8 * 5 * len(reps)
-        e2e_s = time.perf_counter() - t
+        e2e_s = D.max_over_ranks(time.perf_counter() - t, device="cuda")
         e2e_value = ws * n_vis * k_e2e / e2e_s / 1e9
         h2d = vis.numel() * 8 + w.numel() * 4
         batch_e2e.close()
@@ -375,7 +374,7 @@ def run_ours(args):
                    "oversample": wl.oversample, "aperture": wl.ap_kind,
                    "l2": "inputs larger than L2 (vis 108 MB + weights 54 MB + grid 32 MB per step)",
                    "step": "one LM iteration of all intervals (one persistent fused launch, graph replay)",
-                   "tiles_t": tiles, "precompute_ms": precompute_ms},
+                   "tiling": [list(t) for t in tiles], "precompute_ms": precompute_ms},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": profiled_traffic() if args.workload == "vla27_l64ch" else None,
                      "kernel": "eval_kernel<false>, persistent over all intervals (fused degrid + derivatives + residual + sums)",
@@ -387,6 +386,14 @@ def run_ours(args):
     }
     if solve:
         line["solve"] = solve
+    if rank == 0 and not args.no_learned:
+        # solves/s to 1 arcsec RMS, learned initial estimate vs plain LM, on the
+        # 64-antenna 16-channel workload (network trained here on GPU-simulated
+        # intervals with the library's kernels; sizes reduced to fit the bench)
+        from paper_1709_08681_gb300 import learned_init as LI
+        rep, _ = LI.run(n_train=args.learned_train, n_eval=args.learned_eval, steps=1500, batch=1024, n_geom=8,
+                        seed=args.seed, log=None)
+        line["learned_init"] = {"workload": "disk64_l16ch", **rep}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         vis_host = vis.cpu().numpy()
         w_host = w.cpu().numpy()

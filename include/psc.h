@@ -35,8 +35,8 @@
  *   results synchronise that stream before returning; psc_lm_iterate does not.
  * Errors: every call returns a psc_status and never throws or aborts; the
  *   message of the last failure is available from psc_last_error().  Device
- *   side checks (a tap outside the staged tile, a non-finite LM state) are
- *   reported as PSC_ERR_DEVICE or PSC_ERR_NUMERIC by the next synchronising call.
+ *   side failures (a non-finite chi^2 or LM step) are reported as
+ *   PSC_ERR_NUMERIC by the next synchronising call.
  * Threads: a psc_ctx must not be used by two host threads at once.
  */
 #ifndef PSC_H
@@ -58,6 +58,7 @@ typedef enum {
 } psc_status;
 
 enum { PSC_AP_DISK = 0, PSC_AP_GAUSS = 1 };
+enum { PSC_GRID_F32 = 0, PSC_GRID_BF16 = 1 };
 enum { PSC_LM_FULL = 0, PSC_LM_BLOCK = 1 };
 enum { PSC_STOP_NONE = 0, PSC_STOP_STEP = 1, PSC_STOP_CHI2 = 2, PSC_STOP_LAMBDA = 3,
        PSC_STOP_MAX_ITER = 4, PSC_STOP_NUMERIC = 5 };
@@ -203,10 +204,30 @@ psc_status psc_lm_end(psc_ctx *ctx, double *lm_out, psc_solve_report *rep);
  * same start.  Fails with PSC_ERR_ARG if psc_lm_begin was never called. */
 psc_status psc_lm_restart(psc_ctx *ctx);
 
-/* Launch-shape knobs of the fused kernel (time steps and channels per
- * thread block); 0 keeps the current value.  t_tile in {8,16,32,64,128},
- * c_group in {1,2,4,8}, t_tile * c_group in {32, 64, 128, 256}. */
-psc_status psc_set_tiling(psc_ctx *ctx, int t_tile, int c_group);
+/* Launch-shape knobs of the fused kernel; 0 keeps the current value.  A
+ * thread block holds c_group channels and, per channel, t_tile threads that
+ * each own vis_per_thread visibilities at consecutive time steps (a block
+ * covers t_tile * vis_per_thread time steps; its size is t_tile * c_group
+ * rounded up to a multiple of 32).  t_tile in [1, 256], c_group in [1, 8],
+ * t_tile * c_group <= 256 (<= 128 for contexts in a batch, else the batch
+ * resets them to (32, 4)), vis_per_thread in {1, 2}.  vis_per_thread = 2
+ * shares each staged grid cell between the thread's two visibilities; it is
+ * refused (PSC_ERR_ARG) unless every channel's aperture lies inside the
+ * S x S tap window and consecutive time steps move a baseline by at most 4
+ * grid cells at the highest frequency.  Results do not depend on the shape
+ * beyond FP32 summation order. */
+psc_status psc_set_tiling(psc_ctx *ctx, int t_tile, int c_group, int vis_per_thread);
+
+/* Storage precision of the model grid V° that the fused evaluation reads
+ * (psc_predict, psc_residual_grad, the solvers and batches; the feature pass
+ * of psc_features always reads the FP32 grid).  PSC_GRID_F32 (default) reads
+ * the caller's complex64 grid.  PSC_GRID_BF16 takes a copy of that grid
+ * with both parts rounded to bfloat16 (nearest even), owned by the context
+ * (n_grid^2 * 4 bytes), and reads it instead; all arithmetic stays FP32 with
+ * FP64 sums as before.  The copy is taken at this call: call again after the
+ * caller's grid changes.  Errors: PSC_ERR_ARG for an unknown precision,
+ * PSC_ERR_OOM / PSC_ERR_CUDA.  Synchronises. */
+psc_status psc_set_grid_precision(psc_ctx *ctx, int precision);
 
 /* Input features of the learned initial estimate (an addition to the
  * paper's method: the paper starts the minimiser from zero or from previous
@@ -283,12 +304,14 @@ psc_status psc_batch_create(psc_batch **out, psc_ctx *const *ctxs, int n_ctx, co
 void psc_batch_destroy(psc_batch *b);
 const char *psc_batch_last_error(const psc_batch *b);
 
-/* Times the fused kernel of each context at the tile shapes (t_tile,
- * c_group) = (32, 4), (16, 8) and (64, 2) on its own data and keeps the
- * fastest; contexts of the same shape reuse the first one's choice.  Writes
- * the chosen t_tile of each context to t_tile_out (NULL to skip).
- * Synchronises. */
-psc_status psc_batch_autotune(psc_batch *b, int *t_tile_out);
+/* Picks each context's launch shape by timing the fused kernel on its own
+ * data: for vis_per_thread 1 and (where psc_set_tiling accepts it) 2, the
+ * three channel groups whose smallest fitting time tile leaves the fewest of
+ * 128 lanes idle (ragged time and channel tails count as idle), plus
+ * (32, 4, 1); the fastest is kept.  Contexts of the same shape reuse the
+ * first one's choice.  Writes the chosen (t_tile, c_group, vis_per_thread)
+ * of context k to tiling_out[3k..3k+2] (NULL to skip).  Synchronises. */
+psc_status psc_batch_autotune(psc_batch *b, int *tiling_out);
 
 /* Start (host offsets, options as for psc_lm_begin), restart on the device,
  * n_iter device-resident iterations (graph replays, no synchronisation) and

@@ -2,6 +2,7 @@
 // checks, context workspace, and the launch sequences of Algorithm 1's
 // pre-computes and iteration loop.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -21,6 +22,8 @@ struct psc_ctx {
     double du = 0.0;
     const double *uvw = nullptr;
     const float2 *grid = nullptr;
+    unsigned *d_grid_bf16 = nullptr;   // bfloat16 copy of the grid (PSC_GRID_BF16), else null
+    float4 *d_uvs = nullptr;           // FP32 split of uvw read by the fused kernel
     // workspace (device)
     ChanConst *d_chan = nullptr;
     float2 *d_tabs = nullptr;
@@ -42,6 +45,9 @@ struct psc_ctx {
     int *d_done = nullptr;       // points at d_state->done
     int max_tab_len = 0;
     int t_tile = 32, c_group = 4;
+    int kv = 1;                  // visibilities per thread at consecutive times
+    double step_cells = 0.0;     // largest move of a baseline between time steps (cells, top channel)
+    bool multi_ok = false;       // kv > 1 allowed: every channel's aperture fits inside the S x S window
     LMState h_state{};
     std::vector<double> h_ev;
     std::string err;
@@ -94,6 +100,8 @@ cudaError_t dalloc(T **p, size_t n) {
 void free_ctx(psc_ctx *c) {
     if (!c) return;
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    cudaFree(c->d_grid_bf16);
+    cudaFree(c->d_uvs);
     cudaFree(c->d_spart);
     cudaFree(c->d_sblsum);
     cudaFree(c->d_feat);
@@ -104,7 +112,26 @@ void free_ctx(psc_ctx *c) {
     delete c;
 }
 
-int n_tt(const psc_ctx *c) { return (c->nt + c->t_tile - 1) / c->t_tile; }
+int n_tt(const psc_ctx *c) { return (c->nt + c->t_tile * c->kv - 1) / (c->t_tile * c->kv); }
+
+// Largest visibility separation within one thread's kv time steps (cells).
+double kv_spread(const psc_ctx *c, int kv) { return (kv - 1) * c->step_cells; }
+
+// kv > 1 needs every tap of the thread's union of rows to be either inside a
+// visibility's own S x S window or outside its aperture (then its table entry
+// is zero); the union stays within spread + 1 cells of each visibility.
+bool kv_allowed(const psc_ctx *c, int kv) {
+    if (kv == 1) return true;
+    if (kv != 2) return false;
+    return c->multi_ok && kv_spread(c, kv) <= 4.0;
+}
+
+// Staged table entries per channel: the table plus zero entries for every
+// radius a tap of the thread can reach (rho_max + spread + 1 cells).
+int tab_stride(const psc_ctx *c, int kv) {
+    if (kv == 1) return c->max_tab_len + 2;
+    return c->max_tab_len + (int)std::ceil(c->gd.oversample * (kv_spread(c, kv) + 1.0)) + 2;
+}
 int n_cg(const psc_ctx *c) { return (c->nc + c->c_group - 1) / c->c_group; }
 
 psc_status ensure_partials(psc_ctx *c) {
@@ -121,7 +148,9 @@ psc_status ensure_partials(psc_ctx *c) {
 EvalArgs eval_args(const psc_ctx *c, const double *lm_dev) {
     EvalArgs a{};
     a.uvw = c->uvw;
+    a.uvs = c->d_uvs;
     a.grid = c->grid;
+    a.grid_bf16 = c->d_grid_bf16;
     a.chan = c->d_chan;
     a.tabs = c->d_tabs;
     a.pairs = c->d_pairs;
@@ -137,10 +166,12 @@ EvalArgs eval_args(const psc_ctx *c, const double *lm_dev) {
     a.du = (float)c->du;
     a.t_tile = c->t_tile;
     a.c_group = c->c_group;
+    a.kv = c->kv;
     a.n_tt = n_tt(c);
     a.n_cg = n_cg(c);
     a.decorrelation = c->ap.decorrelation;
     a.max_tab_len = c->max_tab_len;
+    a.tab_stride = tab_stride(c, c->kv);
     a.n_bricks = (long long)c->n_bl * n_cg(c) * n_tt(c);
     return a;
 }
@@ -285,6 +316,8 @@ psc_status psc_create(psc_ctx **out, const psc_obs *obs, const psc_aperture *ap,
         const int L = (int)std::floor(ov * rho_max) + 2;
         if (L > (1 << 20)) { free_ctx(c); return fail(nullptr, PSC_ERR_ARG, "aperture table too long: aperture much wider than the grid cell"); }
         ch[k].uv_scale = obs->freq_hz[k] / (kC * c->du);
+        ch[k].sc_hi = (float)ch[k].uv_scale;
+        ch[k].sc_lo = (float)(ch[k].uv_scale - (double)ch[k].sc_hi);
         ch[k].alpha2 = (float)(alpha * alpha);
         ch[k].rho_max = (float)((double)(L - 1) / ov);
         ch[k].tab_off = total;
@@ -301,6 +334,8 @@ psc_status psc_create(psc_ctx **out, const psc_obs *obs, const psc_aperture *ap,
 
     double *d_freq = nullptr;
     int *d_off = nullptr, *d_len = nullptr;
+    unsigned *d_step = nullptr;
+    unsigned h_step = 0;
     const size_t evn = ev_len(c->n_ant, c->n_bl);
     const int n2 = 2 * c->n_ant;
     cudaError_t e = cudaSuccess;
@@ -321,6 +356,12 @@ psc_status psc_create(psc_ctx **out, const psc_obs *obs, const psc_aperture *ap,
     if (e == cudaSuccess) e = dalloc(&d_freq, c->nc);
     if (e == cudaSuccess) e = dalloc(&d_off, c->nc);
     if (e == cudaSuccess) e = dalloc(&d_len, c->nc);
+    if (e == cudaSuccess) e = dalloc(&d_step, 1);
+    if (e == cudaSuccess) e = dalloc(&c->d_uvs, (size_t)c->nt * c->n_bl);
+    if (e == cudaSuccess) e = launch_split_uv(c->uvw, (size_t)c->nt * c->n_bl, c->d_uvs, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_step, 0, sizeof(unsigned), c->stream);
+    if (e == cudaSuccess) e = launch_step_max(c->uvw, c->nt, c->n_bl, d_step, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h_step, d_step, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_chan, ch.data(), sizeof(ChanConst) * c->nc, cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_pairs, pairs.data(), sizeof(int2) * c->n_bl, cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_freq, obs->freq_hz, sizeof(double) * c->nc, cudaMemcpyHostToDevice, c->stream);
@@ -332,6 +373,7 @@ psc_status psc_create(psc_ctx **out, const psc_obs *obs, const psc_aperture *ap,
     cudaFree(d_freq);
     cudaFree(d_off);
     cudaFree(d_len);
+    cudaFree(d_step);
     if (e != cudaSuccess) {
         psc_status st = cuda_fail(nullptr, e, "psc_create");
         free_ctx(c);
@@ -339,8 +381,21 @@ psc_status psc_create(psc_ctx **out, const psc_obs *obs, const psc_aperture *ap,
     }
     c->d_done = &c->d_state->done;
     c->h_ev.resize(evn);
+    {
+        float step_m = 0.f;
+        std::memcpy(&step_m, &h_step, sizeof(float));
+        double sc_max = 0.0, rho_top = 0.0;
+        for (int k = 0; k < c->nc; ++k) {
+            sc_max = std::max(sc_max, ch[k].uv_scale);
+            rho_top = std::max(rho_top, (double)(len[k] - 1) / ov);
+        }
+        c->step_cells = (double)step_m * sc_max;
+        c->multi_ok = std::isfinite(c->step_cells) && rho_top <= 0.5 * gd->support - 1.0;
+    }
     // room for the tables of the widest channel group, and the LM layouts
-    e = set_eval_smem(eval_dyn_smem(8, c->max_tab_len));
+    int stride_max = tab_stride(c, 1);
+    if (kv_allowed(c, 2)) stride_max = std::max(stride_max, tab_stride(c, 2));
+    e = set_eval_smem(eval_dyn_smem(8, stride_max));
     if (e == cudaSuccess) e = lm_prepare(c->n_ant);
     if (e != cudaSuccess) { psc_status st = cuda_fail(nullptr, e, "psc_create: shared memory"); free_ctx(c); return st; }
     *out = c;
@@ -349,16 +404,37 @@ psc_status psc_create(psc_ctx **out, const psc_obs *obs, const psc_aperture *ap,
 
 void psc_destroy(psc_ctx *ctx) { free_ctx(ctx); }
 
-psc_status psc_set_tiling(psc_ctx *ctx, int t_tile, int c_group) {
+psc_status psc_set_tiling(psc_ctx *ctx, int t_tile, int c_group, int vis_per_thread) {
     if (!ctx) return fail(nullptr, PSC_ERR_ARG, "ctx is NULL");
     const int tt = t_tile ? t_tile : ctx->t_tile;
     const int cg = c_group ? c_group : ctx->c_group;
-    if (!(tt == 8 || tt == 16 || tt == 32 || tt == 64 || tt == 128))
-        return fail(ctx, PSC_ERR_ARG, "t_tile must be 8, 16, 32, 64 or 128");
-    if (!(cg == 1 || cg == 2 || cg == 4 || cg == 8)) return fail(ctx, PSC_ERR_ARG, "c_group must be 1, 2, 4 or 8");
-    if (tt * cg < 32 || tt * cg > kMaxThreads) return fail(ctx, PSC_ERR_ARG, "t_tile * c_group must be in [32, 256]");
+    const int kv = vis_per_thread ? vis_per_thread : ctx->kv;
+    if (!(kv == 1 || kv == 2)) return fail(ctx, PSC_ERR_ARG, "vis_per_thread must be 1 or 2");
+    if (!kv_allowed(ctx, kv))
+        return fail(ctx, PSC_ERR_ARG, "vis_per_thread 2 needs the aperture inside the S x S window and "
+                                      "consecutive time steps within 4 cells");
+    if (tt < 1 || tt > kMaxThreads) return fail(ctx, PSC_ERR_ARG, "t_tile must be in [1, 256]");
+    if (cg < 1 || cg > 8) return fail(ctx, PSC_ERR_ARG, "c_group must be in [1, 8]");
+    if (tt * cg > kMaxThreads) return fail(ctx, PSC_ERR_ARG, "t_tile * c_group must be <= 256");
     ctx->t_tile = tt;
     ctx->c_group = cg;
+    ctx->kv = kv;
+    return PSC_OK;
+}
+
+psc_status psc_set_grid_precision(psc_ctx *ctx, int precision) {
+    if (!ctx) return fail(nullptr, PSC_ERR_ARG, "ctx is NULL");
+    if (precision == PSC_GRID_F32) {
+        PSC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));     // no launch may still read the copy
+        cudaFree(ctx->d_grid_bf16);
+        ctx->d_grid_bf16 = nullptr;
+        return PSC_OK;
+    }
+    if (precision != PSC_GRID_BF16) return fail(ctx, PSC_ERR_ARG, "precision must be PSC_GRID_F32 or PSC_GRID_BF16");
+    const size_t n = (size_t)ctx->gd.n_grid * ctx->gd.n_grid;
+    if (!ctx->d_grid_bf16) PSC_CUDA(ctx, dalloc(&ctx->d_grid_bf16, n));
+    PSC_CUDA(ctx, launch_grid_to_bf16(ctx->grid, n, ctx->d_grid_bf16, ctx->stream));
+    PSC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     return PSC_OK;
 }
 
@@ -670,7 +746,7 @@ psc_status build_tables(psc_batch *b) {
     size_t dyn = 0, lmd = 0;
     for (int k = 0; k < n; ++k) {
         psc_ctx *c = b->ctxs[k];
-        if (c->t_tile * c->c_group != 128) {
+        if (c->t_tile * c->c_group > 128) {          // batches launch 128 threads per block
             c->t_tile = 32;
             c->c_group = 4;
         }
@@ -687,7 +763,7 @@ psc_status build_tables(psc_batch *b) {
         lm[k] = lm_args(c);
         st0[k] = c->d_state0;
         lm0[k] = c->d_lm0;
-        dyn = std::max(dyn, eval_dyn_smem(c->c_group, c->max_tab_len));
+        dyn = std::max(dyn, eval_dyn_smem(c->c_group, tab_stride(c, c->kv)));
         lmd = std::max(lmd, lm_smem_bytes(c->n_ant));
     }
     b->total_bl = blp[n];
@@ -772,6 +848,39 @@ __global__ void count_active_kernel(const LMArgs *la, int n, int *out) {
     if (threadIdx.x == 0) *out = c;
 }
 
+// Launch shapes worth timing for a context: for each vis_per_thread and
+// channel group, the smallest time tile with the fewest tiles that fit 128
+// threads; ranked by the share of the 128 lanes that hold a visibility
+// (ragged time and channel tails and idle lanes count as waste).
+std::vector<std::array<int, 3>> tiling_candidates(const psc_ctx *c) {
+    struct Scored { double util; std::array<int, 3> t; };
+    std::vector<Scored> all;
+    for (int kv : {1, 2}) {
+        if (!kv_allowed(c, kv)) continue;
+        for (int cg : {1, 2, 3, 4, 5, 6, 8}) {
+            if (cg > c->nc && cg > 1) continue;
+            const int tt_max = 128 / cg;
+            const int n_tt = (c->nt + tt_max * kv - 1) / (tt_max * kv);
+            const int tt = (c->nt + n_tt * kv - 1) / (n_tt * kv);
+            const int n_cg = (c->nc + cg - 1) / cg;
+            const double util = (double)c->nt / ((double)n_tt * tt * kv) * (double)c->nc / ((double)n_cg * cg) *
+                                (double)(tt * cg) / 128.0;
+            all.push_back({util, {tt, cg, kv}});
+        }
+    }
+    std::sort(all.begin(), all.end(), [](const Scored &x, const Scored &y) { return x.util > y.util; });
+    std::vector<std::array<int, 3>> out;
+    int per_kv[3] = {0, 0, 0};
+    for (const Scored &x : all) {
+        if (per_kv[x.t[2]] >= 3) continue;                 // the best three of each vis_per_thread
+        ++per_kv[x.t[2]];
+        out.push_back(x.t);
+    }
+    const std::array<int, 3> dflt{32, 4, 1};
+    if (std::find(out.begin(), out.end(), dflt) == out.end()) out.push_back(dflt);
+    return out;
+}
+
 }  // namespace
 
 extern "C" {
@@ -804,9 +913,8 @@ psc_status psc_batch_create(psc_batch **out, psc_ctx *const *ctxs, int n_ctx, co
 
 void psc_batch_destroy(psc_batch *b) { free_batch(b); }
 
-psc_status psc_batch_autotune(psc_batch *b, int *t_tile_out) {
+psc_status psc_batch_autotune(psc_batch *b, int *tiling_out) {
     if (!b) return fail(nullptr, PSC_ERR_ARG, "batch is NULL");
-    static const int cand[3][2] = {{32, 4}, {16, 8}, {64, 2}};
     cudaEvent_t e0, e1;
     PSC_BCUDA(b, cudaEventCreate(&e0));
     PSC_BCUDA(b, cudaEventCreate(&e1));
@@ -819,23 +927,27 @@ psc_status psc_batch_autotune(psc_batch *b, int *t_tile_out) {
         for (int j = 0; j < k && reuse < 0; ++j) {
             psc_ctx *o = b->ctxs[j];
             if (o->n_ant == c->n_ant && o->nc == c->nc && o->nt == c->nt && o->gd.n_grid == c->gd.n_grid &&
-                o->du == c->du && o->max_tab_len == c->max_tab_len)
+                o->du == c->du && o->max_tab_len == c->max_tab_len && o->multi_ok == c->multi_ok &&
+                kv_allowed(c, o->kv))
                 reuse = j;
         }
         if (reuse >= 0) {
             c->t_tile = b->ctxs[reuse]->t_tile;
             c->c_group = b->ctxs[reuse]->c_group;
+            c->kv = b->ctxs[reuse]->kv;
         } else {
             zeros.assign(2 * c->n_ant, 0.0);
             PSC_BCUDA(b, cudaMemcpyAsync(c->d_lm_trial, zeros.data(), sizeof(double) * zeros.size(),
                                          cudaMemcpyHostToDevice, b->stream));
             float best = 1e30f;
-            int bt = 32, bc = 4;
-            for (const auto &cd : cand) {
+            int bt = 32, bc = 4, bk = 1;
+            for (const auto &cd : tiling_candidates(c)) {
                 c->t_tile = cd[0];
                 c->c_group = cd[1];
+                c->kv = cd[2];
                 psc_status st = ensure_partials(c);
                 if (st != PSC_OK) return bfail(b, st, c->err);
+                PSC_BCUDA(b, set_eval_smem(eval_dyn_smem(c->c_group, tab_stride(c, c->kv))));
                 EvalArgs a = eval_args(c, c->d_lm_trial);
                 a.vis_obs = (const float2 *)b->vis[k];
                 a.w = b->w[k];
@@ -847,12 +959,17 @@ psc_status psc_batch_autotune(psc_batch *b, int *t_tile_out) {
                 PSC_BCUDA(b, cudaEventSynchronize(e1));
                 float ms = 0.f;
                 PSC_BCUDA(b, cudaEventElapsedTime(&ms, e0, e1));
-                if (ms < best) { best = ms; bt = cd[0]; bc = cd[1]; }
+                if (ms < best) { best = ms; bt = cd[0]; bc = cd[1]; bk = cd[2]; }
             }
             c->t_tile = bt;
             c->c_group = bc;
+            c->kv = bk;
         }
-        if (t_tile_out) t_tile_out[k] = c->t_tile;
+        if (tiling_out) {
+            tiling_out[3 * k] = c->t_tile;
+            tiling_out[3 * k + 1] = c->c_group;
+            tiling_out[3 * k + 2] = c->kv;
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

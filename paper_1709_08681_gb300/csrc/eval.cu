@@ -8,33 +8,38 @@
 // (extended to m, Sec. 3); chi^2 of Eq. Chisq and its gradient, Eq. DCHIDD.
 //
 // Work decomposition.  One thread block handles one "brick": a baseline
-// (i, j), a group of c_group channels and a tile of t_tile time steps, one
-// visibility per thread (warps are single-channel, consecutive times).  The
-// block stages the grid cells its visibilities touch in shared memory.  The
-// kernel's ramp factorises, exp(i pi (u_k - u_g) L) =
+// (i, j), a group of c_group channels and t_tile * kv consecutive time steps.
+// Each thread owns kv visibilities of one channel at consecutive times; they
+// sit within a fraction of a grid cell of each other (the uv track moves
+// slowly), so the thread walks the union of their tap rows and loads each
+// grid cell once for all kv of them.  The block stages the grid cells its
+// visibilities touch (the bounding box of their aperture disks) in shared
+// memory.  The kernel's ramp factorises, exp(i pi (u_k - u_g) L) =
 // exp(i pi (u_k - u_o) L) exp(-i pi (u_g - u_o) L) for any origin u_o, so the
 // staged cells are pre-multiplied by the second factor (per cell, once per
 // block) and each visibility applies the first factor once; the inner loop
 // over taps then needs only the real radial A° and five FMAs per tap.  Taps
-// outside the aperture's support are not visited (their A° is zero by the
-// table rule).  If a brick's footprint does not fit the staging tile, the
-// block falls back to reading the grid from global memory with the ramp
-// applied per tap (same arithmetic, slower).
+// outside the aperture's support are not visited, or read zero table entries
+// (the tables are zero-padded far enough for every tap a thread visits).  If
+// a brick's footprint does not fit the staging tile, the block falls back to
+// reading the grid from global memory with the ramp applied per tap (same
+// arithmetic, slower).
 //
-// Inner loop per tap (rho in units of table samples, t = rho * ov):
-//   s2 = dxo^2 + dyo^2 (dxo = dx ov, dyo^2 carries a 1e-20 floor so s2 > 0),
-//   t = s2 * rsqrt(s2), n = floor(t) by a round-toward-zero add of 2^23 whose
-//   bit pattern also gives the table address, A° = value + f * slope, then
-//   P += A° G', Q += (A° dxo) G'.  Tables are padded with zero entries so no
-//   index clamp is needed (taps are limited to rho < rho_max).
+// Inner loop per tap and visibility (rho in units of table samples, t = rho
+// ov): s2 = dxo^2 + dyo^2 (dxo = dx ov; dyo^2 carries a 1e-20 floor so s2 > 0),
+// t = s2 rsqrt(s2), n = floor(t) by a round-toward-zero add of 2^23 whose bit
+// pattern also gives the table address, A° = c_n + t s_n with the staged entry
+// (c_n, s_n) = (A°(n) - n s_n, A°(n+1) - A°(n)) (the linear interpolation
+// A°(n) + (t - n) s_n rearranged), then P += A° G', Q += (A° dxo) G'.
+#include <algorithm>
 #include <climits>
+
+#include <cuda_bf16.h>
 
 #include "psc_internal.cuh"
 
 namespace psc {
 namespace {
-
-constexpr int kTabPad = 2;     // zero entries after each staged table
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
@@ -46,32 +51,385 @@ __device__ __forceinline__ float rsqrt_fast(float x) {
     return r;
 }
 
+// Grid cell (gy, gx) as FP32: from the bfloat16 copy when there is one
+// (the widening is exact), else from the complex64 grid.
+__device__ __forceinline__ float2 grid_cell(const EvalArgs &a, size_t idx) {
+    if (a.grid_bf16 != nullptr) {
+        const unsigned u = __ldg(&a.grid_bf16[idx]);
+        return make_float2(__uint_as_float(u << 16), __uint_as_float(u & 0xFFFF0000u));
+    }
+    return __ldg(&a.grid[idx]);
+}
+
 __device__ __forceinline__ float2 lds_f2(unsigned addr) {
     float2 v;
     asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(addr));
     return v;
 }
 
-// One row of taps: a_n consecutive staged cells starting at `row`, first tap
-// at dxo (= dx * ov), table at shared address tab_adj + (0x4B000000 << 3).
-// Accumulates P = sum A G' and Q = sum A dxo G'.
-__device__ __forceinline__ void row_taps(const float2 *__restrict__ row, int a_n, float dxo, float dyo2, float ov,
-                                         unsigned tab_adj, float &pr, float &pi, float &qr, float &qi) {
-#pragma unroll 4
-    for (int k = 0; k < a_n; ++k) {
-        const float s2 = fmaf(dxo, dxo, dyo2);
-        const float t = s2 * rsqrt_fast(s2);
-        const float tf = __fadd_rz(t, 8388608.0f);             // floor(t) + 2^23
-        const float2 e = lds_f2(tab_adj + ((unsigned)__float_as_int(tf) << 3));
-        const float f = t - (tf - 8388608.0f);
-        const float A = fmaf(f, e.y, e.x);
-        const float2 g = row[k];
-        pr = fmaf(A, g.x, pr);
-        pi = fmaf(A, g.y, pi);
-        const float Ad = A * dxo;
-        qr = fmaf(Ad, g.x, qr);
-        qi = fmaf(Ad, g.y, qi);
-        dxo -= ov;
+// Grid position x = u sc + Ng/2 of a baseline coordinate given as two floats
+// (u = uh + ul, metres) and the channel's scale sc = sh + sl, without FP64:
+// the product's rounding error comes from an FMA (exact), the small cross
+// terms are added to it, and Ng/2 is added with Knuth's TwoSum, whose error
+// term is exact.  Returns floor(x) in n and x - floor(x) in f (rounded once
+// to FP32).
+__device__ __forceinline__ void grid_pos(float uh, float ul, float sh, float sl, float half, int &n, float &f) {
+    // _rn intrinsics: no FMA contraction may merge these steps
+    const float p = __fmul_rn(uh, sh);
+    float e = fmaf(uh, sh, -p);
+    e = fmaf(uh, sl, e);
+    e = fmaf(ul, sh, e);
+    const float s = __fadd_rn(half, p);
+    const float bb = __fsub_rn(s, half);
+    const float r = __fadd_rn(__fsub_rn(half, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+    const float fl = floorf(s);
+    f = __fadd_rn(__fsub_rn(s, fl), __fadd_rn(r, e));     // s - fl is exact
+    n = (int)fl;
+    if (f < 0.f) { f += 1.f; n -= 1; }
+    else if (f >= 1.f) { f -= 1.f; n += 1; }
+}
+
+// One row of taps for kV visibilities: n consecutive staged cells starting at
+// shared address g_addr; visibility v's first tap is at dxo[v] (= dx ov).  The
+// table address is tab_adj + (bits of floor(t) + 2^23) * 8.  Accumulates
+// P = sum A G' and Q = sum A dxo G' per visibility.
+template <int kV>
+__device__ __forceinline__ void row_taps(unsigned g_addr, int n, float (&dxo)[kV], const float (&dyo2)[kV],
+                                         float ov, unsigned tab_adj, float (&pr)[kV], float (&pi)[kV],
+                                         float (&qr)[kV], float (&qi)[kV]) {
+    constexpr int kUnroll = kV == 1 ? 4 : 2;
+#pragma unroll kUnroll
+    for (int k = 0; k < n; ++k) {
+        const float2 g = lds_f2(g_addr + 8u * (unsigned)k);
+#pragma unroll
+        for (int v = 0; v < kV; ++v) {
+            const float s2 = fmaf(dxo[v], dxo[v], dyo2[v]);
+            const float t = s2 * rsqrt_fast(s2);
+            const float tf = __fadd_rz(t, 8388608.0f);          // floor(t) + 2^23
+            const float2 e = lds_f2(tab_adj + ((unsigned)__float_as_int(tf) << 3));
+            const float A = fmaf(t, e.y, e.x);
+            pr[v] = fmaf(A, g.x, pr[v]);
+            pi[v] = fmaf(A, g.y, pi[v]);
+            const float Ad = A * dxo[v];
+            qr[v] = fmaf(Ad, g.x, qr[v]);
+            qi[v] = fmaf(Ad, g.y, qi[v]);
+            dxo[v] -= ov;
+        }
+    }
+}
+
+// Shared memory of one block (besides the dynamic tables).
+struct BlockShared {
+    float2 tile[kTile * kTile];
+    float2 phx[kTile], phy[kTile];
+    float red[kMaxThreads / 32][kRed];
+    float bl[4];
+    int box[4];
+};
+
+// One brick: kv visibilities per thread.  acc receives the thread's 15 sums
+// (reduce mode); predict mode writes V and the derivative planes.
+template <bool kPredict, int kV>
+__device__ __forceinline__ void eval_brick(const EvalArgs &a, int brick, float2 *s_tab, BlockShared &sh,
+                                           float (&acc)[kRed]) {
+    const int tid = threadIdx.x;
+    const int tt = brick % a.n_tt;
+    const int cgi = (brick / a.n_tt) % a.n_cg;
+    const int bl = brick / (a.n_tt * a.n_cg);
+    const int lt = tid % a.t_tile;
+    const int lc = tid / a.t_tile;
+    const int t0 = (tt * a.t_tile + lt) * kV;         // first time step of this thread
+    const int c = cgi * a.c_group + lc;
+    const bool active = lc < a.c_group && t0 < a.nt && c < a.nc;
+    const int tab_stride = a.tab_stride;
+    const int S = a.support;
+
+    // per-baseline constants, computed once per block in FP64
+    if (tid == 0) {
+        const int2 ij = a.pairs[bl];
+        const double li = a.lm[2 * ij.x], mi = a.lm[2 * ij.x + 1];
+        const double lj = a.lm[2 * ij.y], mj = a.lm[2 * ij.y + 1];
+        sh.bl[0] = (float)(li + lj);   // ramp: l_i + l_j
+        sh.bl[1] = (float)(mi + mj);
+        sh.bl[2] = (float)(li - lj);   // decorrelation: l_i - l_j
+        sh.bl[3] = (float)(mi - mj);
+        sh.box[0] = INT_MAX; sh.box[1] = INT_MIN; sh.box[2] = INT_MAX; sh.box[3] = INT_MIN;
+    }
+    __syncthreads();
+    const float L = sh.bl[0], M = sh.bl[1], dL = sh.bl[2], dM = sh.bl[3];
+
+    // Grid position of each visibility: x = u / du + Ng/2 (cells), window
+    // origin floor(x) - S/2 + 1, hx = x - origin.  Times past the end of the
+    // interval repeat the last one (computed, never stored), so every tap the
+    // thread visits stays within its table padding.
+    int ix0[kV], iy0[kV];
+    float hx[kV], hy[kV];
+    float rmax = 0.f;
+    if (active) {
+        const ChanConst ch = a.chan[c];
+        rmax = ch.rho_max;
+        int lox = INT_MAX, hix = INT_MIN, loy = INT_MAX, hiy = INT_MIN;
+#pragma unroll
+        for (int v = 0; v < kV; ++v) {
+            const int t = min(t0 + v, a.nt - 1);
+            int nx, ny;
+            float fx, fy;
+            if (a.uvs != nullptr) {
+                const float4 q = a.uvs[(size_t)t * a.n_bl + bl];
+                const float half = 0.5f * (float)a.ng;
+                grid_pos(q.x, q.y, ch.sc_hi, ch.sc_lo, half, nx, fx);
+                grid_pos(q.z, q.w, ch.sc_hi, ch.sc_lo, half, ny, fy);
+            } else {
+                const double *p = a.uvw + ((size_t)t * a.n_bl + bl) * 3;
+                const double x = p[0] * ch.uv_scale + 0.5 * a.ng;
+                const double y = p[1] * ch.uv_scale + 0.5 * a.ng;
+                const double flx = floor(x), fly = floor(y);
+                nx = (int)flx;
+                ny = (int)fly;
+                fx = (float)(x - flx);
+                fy = (float)(y - fly);
+            }
+            ix0[v] = nx - S / 2 + 1;
+            iy0[v] = ny - S / 2 + 1;
+            hx[v] = fx + (float)(S / 2 - 1);
+            hy[v] = fy + (float)(S / 2 - 1);
+            // cells within rho_max of the visibility, inside its window
+            lox = min(lox, ix0[v] + max(0, (int)floorf(hx[v] - rmax) + 1));
+            hix = max(hix, ix0[v] + min(S - 1, (int)ceilf(hx[v] + rmax) - 1));
+            loy = min(loy, iy0[v] + max(0, (int)floorf(hy[v] - rmax) + 1));
+            hiy = max(hiy, iy0[v] + min(S - 1, (int)ceilf(hy[v] + rmax) - 1));
+        }
+        if (lox <= hix && loy <= hiy) {
+            atomicMin(&sh.box[0], lox); atomicMax(&sh.box[1], hix);
+            atomicMin(&sh.box[2], loy); atomicMax(&sh.box[3], hiy);
+        }
+    }
+    // radial tables of this block's channels as (c_n, s_n), zero-padded
+    for (int j = 0; j < a.c_group; ++j) {
+        const int cc = cgi * a.c_group + j;
+        const int off = cc < a.nc ? a.chan[cc].tab_off : 0;
+        const int len = cc < a.nc ? a.chan[cc].tab_len : 0;
+        for (int n = tid; n < tab_stride; n += blockDim.x) {
+            float2 v = make_float2(0.f, 0.f);
+            if (n < len) {
+                const float2 e = a.tabs[off + n];
+                v = make_float2(fmaf(-(float)n, e.y, e.x), e.y);
+            }
+            s_tab[j * tab_stride + n] = v;
+        }
+    }
+    __syncthreads();
+    const bool empty = sh.box[0] > sh.box[1];         // no visibility of the brick has a tap
+    const int bx0 = empty ? 0 : sh.box[0], by0 = empty ? 0 : sh.box[2];
+    const int ex = empty ? 0 : sh.box[1] - bx0 + 1, ey = empty ? 0 : sh.box[3] - by0 + 1;
+    const bool staged = ex <= kTile && ey <= kTile;    // uniform over the block
+
+    if (staged && !empty) {
+        // per-cell half of the ramp, relative to the tile origin
+        for (int k = tid; k < ex; k += blockDim.x) {
+            float s, co;
+            sincospif(-(float)k * a.du * L, &s, &co);
+            sh.phx[k] = make_float2(co, s);
+        }
+        for (int k = tid; k < ey; k += blockDim.x) {
+            float s, co;
+            sincospif(-(float)k * a.du * M, &s, &co);
+            sh.phy[k] = make_float2(co, s);
+        }
+        __syncthreads();
+        // threads -> (column, row group) with shifts: 64 columns per pass for
+        // blocks of >= 64 threads, 32 for a 32-thread block (two passes);
+        // the row step blockDim >> cshift is >= 1 for every allowed block size
+        const int cshift = blockDim.x >= kTile ? 6 : 5;
+        const int cols = 1 << cshift;
+        const int rstep = blockDim.x >> cshift;
+        for (int xx = tid & (cols - 1); xx < ex; xx += cols) {
+            const int gx = bx0 + xx;
+            const bool xin = gx >= 0 && gx < a.ng;
+            const float2 px = sh.phx[xx];
+            for (int yy = tid >> cshift; yy < ey; yy += rstep) {
+                const int gy = by0 + yy;
+                float2 g = make_float2(0.f, 0.f);
+                if (xin && gy >= 0 && gy < a.ng) g = grid_cell(a, (size_t)gy * a.ng + gx);
+                sh.tile[yy * kTile + xx] = cmul(g, cmul(px, sh.phy[yy]));
+            }
+        }
+        __syncthreads();
+    }
+
+    // ---- per-visibility tap sums (relative to each visibility's window) ----
+    float2 S0[kV], Su[kV], Sv[kV];
+#pragma unroll
+    for (int v = 0; v < kV; ++v) S0[v] = Su[v] = Sv[v] = make_float2(0.f, 0.f);
+    if (active && !empty) {
+        const float2 *tab = s_tab + lc * tab_stride;
+        const unsigned tab_adj = (unsigned)__cvta_generic_to_shared(tab) - (0x4B000000u << 3);
+        const float ov = (float)a.ov;
+        const float rmax2 = rmax * rmax;
+        if (staged) {
+            const unsigned tile_addr = (unsigned)__cvta_generic_to_shared(sh.tile);
+            int wx[kV], wy[kV];
+            int r_lo = INT_MAX, r_hi = INT_MIN;
+#pragma unroll
+            for (int v = 0; v < kV; ++v) {
+                wx[v] = ix0[v] - bx0;
+                wy[v] = iy0[v] - by0;
+                r_lo = min(r_lo, wy[v] + max(0, (int)floorf(hy[v] - rmax) + 1));
+                r_hi = max(r_hi, wy[v] + min(S - 1, (int)ceilf(hy[v] + rmax) - 1));
+            }
+            for (int cy = r_lo; cy <= r_hi; ++cy) {
+                float dy[kV], dyo2[kV];
+                int c_lo = INT_MAX, c_hi = INT_MIN;
+#pragma unroll
+                for (int v = 0; v < kV; ++v) {
+                    dy[v] = hy[v] - (float)(cy - wy[v]);
+                    const float dyo = dy[v] * ov;
+                    dyo2[v] = fmaf(dyo, dyo, 1e-20f);
+                    const float rem = rmax2 - dy[v] * dy[v];
+                    if (rem > 0.f) {
+                        // r <= rho_max keeps the span inside the staged box
+                        const float r = fminf(rem * rsqrt_fast(rem), rmax);
+                        const int a_lo = max(0, (int)floorf(hx[v] - r) + 1);
+                        const int a_hi = min(S - 1, (int)ceilf(hx[v] + r) - 1);
+                        if (a_lo <= a_hi) {
+                            c_lo = min(c_lo, wx[v] + a_lo);
+                            c_hi = max(c_hi, wx[v] + a_hi);
+                        }
+                    }
+                }
+                if (c_lo > c_hi) continue;
+                float dxo[kV], pr[kV], pi[kV], qr[kV], qi[kV];
+#pragma unroll
+                for (int v = 0; v < kV; ++v) {
+                    dxo[v] = (hx[v] - (float)(c_lo - wx[v])) * ov;
+                    pr[v] = pi[v] = qr[v] = qi[v] = 0.f;
+                }
+                row_taps<kV>(tile_addr + 8u * (unsigned)(cy * kTile + c_lo), c_hi - c_lo + 1, dxo, dyo2, ov,
+                             tab_adj, pr, pi, qr, qi);
+#pragma unroll
+                for (int v = 0; v < kV; ++v) {
+                    S0[v].x += pr[v]; S0[v].y += pi[v];
+                    Su[v].x += qr[v]; Su[v].y += qi[v];
+                    Sv[v].x = fmaf(dy[v], pr[v], Sv[v].x);
+                    Sv[v].y = fmaf(dy[v], pi[v], Sv[v].y);
+                }
+            }
+        } else {
+            float sdx, cdx;
+            sincospif(-a.du * L, &sdx, &cdx);                  // per-column ramp step
+            const float2 step = make_float2(cdx, sdx);
+#pragma unroll
+            for (int v = 0; v < kV; ++v) {
+                const int b_lo = max(0, (int)floorf(hy[v] - rmax) + 1);
+                const int b_hi = min(S - 1, (int)ceilf(hy[v] + rmax) - 1);
+                for (int b = b_lo; b <= b_hi; ++b) {
+                    const float dy = hy[v] - (float)b;
+                    const float rem = rmax2 - dy * dy;
+                    if (!(rem > 0.f)) continue;
+                    const float r = fminf(rem * rsqrt_fast(rem), rmax);
+                    const int a_lo = max(0, (int)floorf(hx[v] - r) + 1);
+                    const int a_hi = min(S - 1, (int)ceilf(hx[v] + r) - 1);
+                    const float dyo = dy * ov;
+                    const float dyo2 = fmaf(dyo, dyo, 1e-20f);
+                    float pr = 0.f, pi = 0.f, qr = 0.f, qi = 0.f;
+                    // ramp exp(-i pi du (a L + b M)) relative to this visibility's window origin
+                    float sz, cz;
+                    sincospif(-a.du * ((float)a_lo * L + (float)b * M), &sz, &cz);
+                    float2 z = make_float2(cz, sz);
+                    const int gy = iy0[v] + b;
+                    float dd = (hx[v] - (float)a_lo) * ov;
+                    for (int aa = a_lo; aa <= a_hi; ++aa, dd -= ov) {
+                        const int gx = ix0[v] + aa;
+                        float2 g = make_float2(0.f, 0.f);
+                        if (gx >= 0 && gx < a.ng && gy >= 0 && gy < a.ng) g = grid_cell(a, (size_t)gy * a.ng + gx);
+                        g = cmul(g, z);
+                        z = cmul(z, step);
+                        const float s2 = fmaf(dd, dd, dyo2);
+                        const float tv = s2 * rsqrt_fast(s2);
+                        const float tf = __fadd_rz(tv, 8388608.0f);
+                        const float2 e = lds_f2(tab_adj + ((unsigned)__float_as_int(tf) << 3));
+                        const float A = fmaf(tv, e.y, e.x);
+                        pr = fmaf(A, g.x, pr);
+                        pi = fmaf(A, g.y, pi);
+                        const float Ad = A * dd;
+                        qr = fmaf(Ad, g.x, qr);
+                        qi = fmaf(Ad, g.y, qi);
+                    }
+                    S0[v].x += pr; S0[v].y += pi;
+                    Su[v].x += qr; Su[v].y += qi;
+                    Sv[v].x = fmaf(dy, pr, Sv[v].x);
+                    Sv[v].y = fmaf(dy, pi, Sv[v].y);
+                }
+            }
+        }
+        const float inv_ov = 1.0f / ov;
+#pragma unroll
+        for (int v = 0; v < kV; ++v) {                       // Q was accumulated with dx * ov
+            Su[v].x *= inv_ov; Su[v].y *= inv_ov;
+        }
+    }
+
+    // ---- epilogue: visibility half of the ramp, decorrelation, derivatives ----
+    if (!active) return;
+    const float al2 = a.chan[c].alpha2;
+    float D = 1.f, el = 0.f, em = 0.f;
+    if (a.decorrelation) {
+        D = expf(-0.5f * al2 * (dL * dL + dM * dM));
+        el = -dL * al2;                      // (l_j - l_i) alpha^2
+        em = -dM * al2;
+    }
+    const float pi_f = 3.14159265358979f;
+#pragma unroll
+    for (int v = 0; v < kV; ++v) {
+        const int t = t0 + v;
+        if (t >= a.nt) break;
+        const int ox = staged ? bx0 : ix0[v];
+        const int oy = staged ? by0 : iy0[v];
+        const float ph_arg = a.du * (((float)(ix0[v] - ox) + hx[v]) * L + ((float)(iy0[v] - oy) + hy[v]) * M);
+        float s, co;
+        sincospif(ph_arg, &s, &co);
+        const float2 ph = make_float2(co, s);
+        const float2 T0 = cmul(ph, S0[v]);
+        float2 Tu = cmul(ph, Su[v]), Tv = cmul(ph, Sv[v]);
+        Tu.x *= a.du; Tu.y *= a.du;          // tap offsets in wavelengths
+        Tv.x *= a.du; Tv.y *= a.du;
+        const float2 V = make_float2(D * T0.x, D * T0.y);
+        // d/dl_i = D [(l_j - l_i) a^2 T0 + i pi Tu]; d/dl_j flips the first term; m likewise
+        const float2 dli = make_float2(D * (el * T0.x - pi_f * Tu.y), D * (el * T0.y + pi_f * Tu.x));
+        const float2 dmi = make_float2(D * (em * T0.x - pi_f * Tv.y), D * (em * T0.y + pi_f * Tv.x));
+        const float2 dlj = make_float2(D * (-el * T0.x - pi_f * Tu.y), D * (-el * T0.y + pi_f * Tu.x));
+        const float2 dmj = make_float2(D * (-em * T0.x - pi_f * Tv.y), D * (-em * T0.y + pi_f * Tv.x));
+        const size_t k = ((size_t)t * a.n_bl + bl) * a.nc + c;
+        if constexpr (kPredict) {
+            a.vis_out[k] = V;
+            if (a.dvis_out != nullptr) {
+                const size_t plane = (size_t)a.nt * a.n_bl * a.nc;
+                a.dvis_out[k] = dli;
+                a.dvis_out[plane + k] = dmi;
+                a.dvis_out[2 * plane + k] = dlj;
+                a.dvis_out[3 * plane + k] = dmj;
+            }
+        } else {
+            const float2 vo = a.vis_obs[k];
+            const float w = a.w_scale * (a.w != nullptr ? a.w[k] : 1.f);
+            const float2 R = make_float2(vo.x - V.x, vo.y - V.y);
+            const float w2 = 2.f * w;
+            acc[0] += w * (R.x * R.x + R.y * R.y);
+            acc[1] -= w2 * (R.x * dli.x + R.y * dli.y);
+            acc[2] -= w2 * (R.x * dmi.x + R.y * dmi.y);
+            acc[3] -= w2 * (R.x * dlj.x + R.y * dlj.y);
+            acc[4] -= w2 * (R.x * dmj.x + R.y * dmj.y);
+            acc[5] += w2 * (dli.x * dli.x + dli.y * dli.y);
+            acc[6] += w2 * (dli.x * dmi.x + dli.y * dmi.y);
+            acc[7] += w2 * (dmi.x * dmi.x + dmi.y * dmi.y);
+            acc[8] += w2 * (dlj.x * dlj.x + dlj.y * dlj.y);
+            acc[9] += w2 * (dlj.x * dmj.x + dlj.y * dmj.y);
+            acc[10] += w2 * (dmj.x * dmj.x + dmj.y * dmj.y);
+            acc[11] += w2 * (dli.x * dlj.x + dli.y * dlj.y);
+            acc[12] += w2 * (dli.x * dmj.x + dli.y * dmj.y);
+            acc[13] += w2 * (dmi.x * dlj.x + dmi.y * dlj.y);
+            acc[14] += w2 * (dmi.x * dmj.x + dmi.y * dmj.y);
+        }
     }
 }
 
@@ -84,14 +442,10 @@ template <bool kPredict>
 __global__ void __launch_bounds__(kMaxThreads) eval_kernel(const EvalArgs a0, const EvalArgs *__restrict__ args,
                                                            const long long *__restrict__ prefix, int n_ctx,
                                                            unsigned long long *queue) {
-    extern __shared__ float2 s_tab[];                 // c_group * (max_tab_len + kTabPad)
-    __shared__ float2 s_tile[kTile * kTile];
-    __shared__ float2 s_phx[kTile], s_phy[kTile];
-    __shared__ int s_box[4];
-    __shared__ double s_red[kMaxThreads / 32][kRed];
+    extern __shared__ float2 s_tab[];                 // c_group * tab_stride
+    __shared__ BlockShared sh;
     __shared__ EvalArgs s_a;
     __shared__ long long s_work, s_first;
-    __shared__ int s_ctx;
     const bool persistent = queue != nullptr;
     long long next = -1;                              // thread 0: prefetched queue entry
     for (;;) {
@@ -106,7 +460,6 @@ __global__ void __launch_bounds__(kMaxThreads) eval_kernel(const EvalArgs a0, co
                 if (prefix[mid] <= gb) lo = mid; else hi = mid - 1;
             }
             s_work = gb;
-            s_ctx = lo;
             s_first = prefix[lo];
             if (gb < prefix[n_ctx]) s_a = args[lo];
         }
@@ -120,222 +473,11 @@ __global__ void __launch_bounds__(kMaxThreads) eval_kernel(const EvalArgs a0, co
     if (!(a.skip != nullptr && *a.skip)) {
     const int tid = threadIdx.x;
     const int brick = persistent ? (int)(s_work - s_first) : (int)blockIdx.x;
-    const int tt = brick % a.n_tt;
-    const int cgi = (brick / a.n_tt) % a.n_cg;
-    const int bl = brick / (a.n_tt * a.n_cg);
-    const int lt = tid % a.t_tile;
-    const int lc = tid / a.t_tile;
-    const int t = tt * a.t_tile + lt;
-    const int c = cgi * a.c_group + lc;
-    const bool valid = lc < a.c_group && t < a.nt && c < a.nc;
-    const int tab_stride = a.max_tab_len + kTabPad;
-
-    // per-baseline constants, computed once per block in FP64
-    __shared__ float s_bl[4];
-    if (tid == 0) {
-        const int2 ij = a.pairs[bl];
-        const double li = a.lm[2 * ij.x], mi = a.lm[2 * ij.x + 1];
-        const double lj = a.lm[2 * ij.y], mj = a.lm[2 * ij.y + 1];
-        s_bl[0] = (float)(li + lj);   // ramp: l_i + l_j
-        s_bl[1] = (float)(mi + mj);
-        s_bl[2] = (float)(li - lj);   // decorrelation: l_i - l_j
-        s_bl[3] = (float)(mi - mj);
-        s_box[0] = INT_MAX; s_box[1] = INT_MIN; s_box[2] = INT_MAX; s_box[3] = INT_MIN;
-    }
-    __syncthreads();
-    const float L = s_bl[0], M = s_bl[1], dL = s_bl[2], dM = s_bl[3];
-
-    // Grid position of this visibility: x = u / du + Ng/2 (cells), window
-    // origin floor(x) - S/2 + 1.
-    int ix0 = 0, iy0 = 0;
-    float fx = 0.f, fy = 0.f;
-    if (valid) {
-        const double *p = a.uvw + ((size_t)t * a.n_bl + bl) * 3;
-        const double sc = a.chan[c].uv_scale;
-        const double x = p[0] * sc + 0.5 * a.ng;
-        const double y = p[1] * sc + 0.5 * a.ng;
-        const double flx = floor(x), fly = floor(y);
-        fx = (float)(x - flx);
-        fy = (float)(y - fly);
-        ix0 = (int)flx - a.support / 2 + 1;
-        iy0 = (int)fly - a.support / 2 + 1;
-        atomicMin(&s_box[0], ix0); atomicMax(&s_box[1], ix0);
-        atomicMin(&s_box[2], iy0); atomicMax(&s_box[3], iy0);
-    }
-    // radial tables of this block's channels, zero-padded
-    for (int k = tid; k < a.c_group * tab_stride; k += blockDim.x) {
-        const int cc = cgi * a.c_group + k / tab_stride;
-        const int n = k % tab_stride;
-        float2 v = make_float2(0.f, 0.f);
-        if (cc < a.nc) {
-            const ChanConst ch = a.chan[cc];
-            if (n < ch.tab_len) v = a.tabs[ch.tab_off + n];
-        }
-        s_tab[k] = v;
-    }
-    __syncthreads();
-    const int bx0 = s_box[0], by0 = s_box[2];
-    const int ex = s_box[1] - bx0 + a.support, ey = s_box[3] - by0 + a.support;
-    const bool staged = ex <= kTile && ey <= kTile;      // uniform over the block
-
-    if (staged) {
-        // per-cell half of the ramp, relative to the tile origin
-        for (int k = tid; k < ex; k += blockDim.x) {
-            float s, co;
-            sincospif(-(float)k * a.du * L, &s, &co);
-            s_phx[k] = make_float2(co, s);
-        }
-        for (int k = tid; k < ey; k += blockDim.x) {
-            float s, co;
-            sincospif(-(float)k * a.du * M, &s, &co);
-            s_phy[k] = make_float2(co, s);
-        }
-        __syncthreads();
-        // threads -> (column, row group) with shifts: 64 columns per pass for
-        // blocks of >= 64 threads, 32 for a 32-thread block (two passes);
-        // the row step blockDim >> cshift is >= 1 for every allowed block size
-        const int cshift = blockDim.x >= kTile ? 6 : 5;
-        const int cols = 1 << cshift;
-        const int rstep = blockDim.x >> cshift;
-        for (int xx = tid & (cols - 1); xx < kTile; xx += cols) {
-            const int gx = bx0 + xx;
-            const bool xin = xx < ex && gx >= 0 && gx < a.ng;
-            const float2 px = xin ? s_phx[xx] : make_float2(0.f, 0.f);
-            for (int yy = tid >> cshift; yy < ey; yy += rstep) {
-                const int gy = by0 + yy;
-                float2 g = make_float2(0.f, 0.f);
-                if (xin && gy >= 0 && gy < a.ng) g = __ldg(&a.grid[(size_t)gy * a.ng + gx]);
-                s_tile[yy * kTile + xx] = cmul(g, cmul(px, s_phy[yy]));
-            }
-        }
-        __syncthreads();
-    }
-
-    // ---- per-visibility tap sums (relative to origin (ox, oy)) ----
-    const int ox = staged ? bx0 : ix0;
-    const int oy = staged ? by0 : iy0;
-    float2 S0 = make_float2(0.f, 0.f), Su = S0, Sv = S0;
-    const float hx = fx + (float)(a.support / 2 - 1);   // dx of tap 0 (cells)
-    const float hy = fy + (float)(a.support / 2 - 1);
-    if (valid) {
-        const ChanConst ch = a.chan[c];
-        const float2 *tab = s_tab + lc * tab_stride;
-        const unsigned tab_adj = (unsigned)__cvta_generic_to_shared(tab) - (0x4B000000u << 3);
-        const float ov = (float)a.ov;
-        const float rmax = ch.rho_max;
-        const float rmax2 = rmax * rmax;
-        const int b_lo = max(0, (int)floorf(hy - rmax) + 1);
-        const int b_hi = min(a.support - 1, (int)ceilf(hy + rmax) - 1);
-        float sdx = 0.f, cdx = 0.f;
-        if (!staged) sincospif(-a.du * L, &sdx, &cdx);     // per-column ramp step
-        for (int b = b_lo; b <= b_hi; ++b) {
-            const float dy = hy - (float)b;
-            const float rem = rmax2 - dy * dy;
-            if (!(rem > 0.f)) continue;
-            const float r = rem * rsqrt_fast(rem);
-            const int a_lo = max(0, (int)floorf(hx - r) + 1);
-            const int a_hi = min(a.support - 1, (int)ceilf(hx + r) - 1);
-            const float dyo = dy * ov;
-            const float dyo2 = fmaf(dyo, dyo, 1e-20f);
-            float pr = 0.f, pi = 0.f, qr = 0.f, qi = 0.f;
-            const float dxo = (hx - (float)a_lo) * ov;
-            if (staged) {
-                const float2 *row = s_tile + (iy0 - oy + b) * kTile + (ix0 - ox) + a_lo;
-                row_taps(row, a_hi - a_lo + 1, dxo, dyo2, ov, tab_adj, pr, pi, qr, qi);
-            } else {
-                // ramp exp(-i pi du (a L + b M)) relative to this visibility's window origin
-                float sz, cz;
-                sincospif(-a.du * ((float)a_lo * L + (float)b * M), &sz, &cz);
-                float2 z = make_float2(cz, sz);
-                const float2 step = make_float2(cdx, sdx);
-                const int gy = iy0 + b;
-                float dd = dxo;
-                for (int aa = a_lo; aa <= a_hi; ++aa, dd -= ov) {
-                    const int gx = ix0 + aa;
-                    float2 g = make_float2(0.f, 0.f);
-                    if (gx >= 0 && gx < a.ng && gy >= 0 && gy < a.ng) g = __ldg(&a.grid[(size_t)gy * a.ng + gx]);
-                    g = cmul(g, z);
-                    z = cmul(z, step);
-                    const float s2 = fmaf(dd, dd, dyo2);
-                    const float tv = s2 * rsqrt_fast(s2);
-                    const float tf = __fadd_rz(tv, 8388608.0f);
-                    const float2 e = lds_f2(tab_adj + ((unsigned)__float_as_int(tf) << 3));
-                    const float A = fmaf(tv - (tf - 8388608.0f), e.y, e.x);
-                    pr = fmaf(A, g.x, pr);
-                    pi = fmaf(A, g.y, pi);
-                    const float Ad = A * dd;
-                    qr = fmaf(Ad, g.x, qr);
-                    qi = fmaf(Ad, g.y, qi);
-                }
-            }
-            S0.x += pr; S0.y += pi;
-            Su.x += qr; Su.y += qi;
-            Sv.x = fmaf(dy, pr, Sv.x);
-            Sv.y = fmaf(dy, pi, Sv.y);
-        }
-        const float inv_ov = 1.0f / ov;
-        Su.x *= inv_ov; Su.y *= inv_ov;                  // Q was accumulated with dx * ov
-    }
-
-    // ---- epilogue: visibility half of the ramp, decorrelation, derivatives ----
     float acc[kRed];
 #pragma unroll
     for (int k = 0; k < kRed; ++k) acc[k] = 0.f;
-    if (valid) {
-        const float ph_arg = a.du * (((float)(ix0 - ox) + hx) * L + ((float)(iy0 - oy) + hy) * M);
-        float s, co;
-        sincospif(ph_arg, &s, &co);
-        const float2 ph = make_float2(co, s);
-        const float2 T0 = cmul(ph, S0);
-        float2 Tu = cmul(ph, Su), Tv = cmul(ph, Sv);
-        Tu.x *= a.du; Tu.y *= a.du;          // tap offsets in wavelengths
-        Tv.x *= a.du; Tv.y *= a.du;
-        const float al2 = a.chan[c].alpha2;
-        float D = 1.f, el = 0.f, em = 0.f;
-        if (a.decorrelation) {
-            D = expf(-0.5f * al2 * (dL * dL + dM * dM));
-            el = -dL * al2;                  // (l_j - l_i) alpha^2
-            em = -dM * al2;
-        }
-        const float pi_f = 3.14159265358979f;
-        const float2 V = make_float2(D * T0.x, D * T0.y);
-        // d/dl_i = D [(l_j - l_i) a^2 T0 + i pi Tu]; d/dl_j flips the first term; m likewise
-        const float2 dli = make_float2(D * (el * T0.x - pi_f * Tu.y), D * (el * T0.y + pi_f * Tu.x));
-        const float2 dmi = make_float2(D * (em * T0.x - pi_f * Tv.y), D * (em * T0.y + pi_f * Tv.x));
-        const float2 dlj = make_float2(D * (-el * T0.x - pi_f * Tu.y), D * (-el * T0.y + pi_f * Tu.x));
-        const float2 dmj = make_float2(D * (-em * T0.x - pi_f * Tv.y), D * (-em * T0.y + pi_f * Tv.x));
-        const size_t k = ((size_t)t * a.n_bl + bl) * a.nc + c;
-        if (kPredict) {
-            a.vis_out[k] = V;
-            if (a.dvis_out != nullptr) {
-                const size_t plane = (size_t)a.nt * a.n_bl * a.nc;
-                a.dvis_out[k] = dli;
-                a.dvis_out[plane + k] = dmi;
-                a.dvis_out[2 * plane + k] = dlj;
-                a.dvis_out[3 * plane + k] = dmj;
-            }
-        } else {
-            const float2 vo = a.vis_obs[k];
-            const float w = a.w_scale * (a.w != nullptr ? a.w[k] : 1.f);
-            const float2 R = make_float2(vo.x - V.x, vo.y - V.y);
-            const float w2 = 2.f * w;
-            acc[0] = w * (R.x * R.x + R.y * R.y);
-            acc[1] = -w2 * (R.x * dli.x + R.y * dli.y);
-            acc[2] = -w2 * (R.x * dmi.x + R.y * dmi.y);
-            acc[3] = -w2 * (R.x * dlj.x + R.y * dlj.y);
-            acc[4] = -w2 * (R.x * dmj.x + R.y * dmj.y);
-            acc[5] = w2 * (dli.x * dli.x + dli.y * dli.y);
-            acc[6] = w2 * (dli.x * dmi.x + dli.y * dmi.y);
-            acc[7] = w2 * (dmi.x * dmi.x + dmi.y * dmi.y);
-            acc[8] = w2 * (dlj.x * dlj.x + dlj.y * dlj.y);
-            acc[9] = w2 * (dlj.x * dmj.x + dlj.y * dmj.y);
-            acc[10] = w2 * (dmj.x * dmj.x + dmj.y * dmj.y);
-            acc[11] = w2 * (dli.x * dlj.x + dli.y * dlj.y);
-            acc[12] = w2 * (dli.x * dmj.x + dli.y * dmj.y);
-            acc[13] = w2 * (dmi.x * dlj.x + dmi.y * dlj.y);
-            acc[14] = w2 * (dmi.x * dmj.x + dmi.y * dmj.y);
-        }
-    }
+    if (a.kv == 2) eval_brick<kPredict, 2>(a, brick, s_tab, sh, acc);
+    else eval_brick<kPredict, 1>(a, brick, s_tab, sh, acc);
     if constexpr (!kPredict) {
         // ---- block reduction: FP32 within a warp, FP64 across warps ----
 #pragma unroll
@@ -348,14 +490,14 @@ __global__ void __launch_bounds__(kMaxThreads) eval_kernel(const EvalArgs a0, co
         const int warp = tid >> 5, lane = tid & 31;
         if (lane == 0) {
 #pragma unroll
-            for (int k = 0; k < kRed; ++k) s_red[warp][k] = (double)acc[k];
+            for (int k = 0; k < kRed; ++k) sh.red[warp][k] = acc[k];
         }
         __syncthreads();
         if (tid < kRed) {
-            double s = 0.0;
+            float s = 0.f;
             const int nw = (blockDim.x + 31) >> 5;
-            for (int wi = 0; wi < nw; ++wi) s += s_red[wi][tid];
-            a.partials[(size_t)tid * a.n_bricks + brick] = s;      // [kRed][n_bricks]
+            for (int wi = 0; wi < nw; ++wi) s += sh.red[wi][tid];
+            a.partials[(size_t)tid * a.n_bricks + brick] = (double)s;      // [kRed][n_bricks]
         }
     }
     }                                                 // not skipped
@@ -439,16 +581,66 @@ __global__ void ev_kernel(const RedArgs r0, const RedArgs *__restrict__ ra) {
     }
 }
 
+// Largest |uv(t+1) - uv(t)| over consecutive time steps and baselines.
+__global__ void step_max_kernel(const double *__restrict__ uvw, int nt, int n_bl, unsigned *out_bits) {
+    float m = 0.f;
+    const long long n = (long long)(nt - 1) * n_bl;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        const double *p = uvw + 3 * k;
+        const double *q = p + 3 * (size_t)n_bl;
+        const double du = q[0] - p[0], dv = q[1] - p[1];
+        m = fmaxf(m, (float)sqrt(du * du + dv * dv));
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out_bits, __float_as_uint(m));   // m >= 0: bits order as values
+}
+
+__global__ void grid_to_bf16_kernel(const float2 *__restrict__ g, size_t n, unsigned *__restrict__ out) {
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
+        const __nv_bfloat162 b = __float22bfloat162_rn(g[k]);
+        out[k] = *reinterpret_cast<const unsigned *>(&b);
+    }
+}
+
+__global__ void split_uv_kernel(const double *__restrict__ uvw, size_t n, float4 *__restrict__ out) {
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
+        const double u = uvw[3 * k], v = uvw[3 * k + 1];
+        const float uh = (float)u, vh = (float)v;
+        out[k] = make_float4(uh, (float)(u - (double)uh), vh, (float)(v - (double)vh));
+    }
+}
+
 }  // namespace
 
-size_t eval_dyn_smem(int c_group, int max_tab_len) {
-    return sizeof(float2) * (size_t)c_group * (max_tab_len + kTabPad);
+cudaError_t launch_split_uv(const double *uvw, size_t n, float4 *out, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    const int blocks = (int)std::min<size_t>((n + 255) / 256, 4096);
+    split_uv_kernel<<<blocks, 256, 0, s>>>(uvw, n, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_grid_to_bf16(const float2 *grid, size_t n, unsigned *out, cudaStream_t s) {
+    const int blocks = (int)std::min<size_t>((n + 255) / 256, 4096);
+    grid_to_bf16_kernel<<<blocks, 256, 0, s>>>(grid, n, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_step_max(const double *uvw, int nt, int n_bl, unsigned *out_bits, cudaStream_t s) {
+    if (nt < 2) return cudaSuccess;
+    const long long n = (long long)(nt - 1) * n_bl;
+    const int blocks = (int)std::min<long long>((n + 255) / 256, 1024);
+    step_max_kernel<<<blocks, 256, 0, s>>>(uvw, nt, n_bl, out_bits);
+    return cudaGetLastError();
+}
+
+size_t eval_dyn_smem(int c_group, int tab_stride) {
+    return sizeof(float2) * (size_t)c_group * tab_stride;
 }
 
 cudaError_t launch_eval(const EvalArgs &a, bool predict, cudaStream_t s) {
-    const int threads = a.t_tile * a.c_group;
+    const int threads = (a.t_tile * a.c_group + 31) / 32 * 32;
     const int blocks = (int)a.n_bricks;
-    const size_t dyn = eval_dyn_smem(a.c_group, a.max_tab_len);
+    const size_t dyn = eval_dyn_smem(a.c_group, a.tab_stride);
     if (predict) {
         eval_kernel<true><<<blocks, threads, dyn, s>>>(a, nullptr, nullptr, 0, nullptr);
     } else {

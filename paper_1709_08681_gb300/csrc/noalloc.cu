@@ -51,6 +51,8 @@ __global__ void noalloc_setup_kernel(const double *freq, int nc, double du, int 
             const int L = (int)floor(ov * rho_max) + 2;
             ChanConst ch;
             ch.uv_scale = freq[c] / (kC * du);
+            ch.sc_hi = (float)ch.uv_scale;
+            ch.sc_lo = (float)(ch.uv_scale - (double)ch.sc_hi);
             ch.alpha2 = (float)(alpha * alpha);
             ch.rho_max = (float)((double)(L - 1) / ov);
             ch.tab_off = total;
@@ -178,7 +180,7 @@ extern "C" psc_status psc_residual_grad_noalloc(const psc_obs *obs, const psc_ap
                                            gd->support, d_chan, d_toff, d_tlen, n_ant, d_pairs);
     NA_CUDA(cudaGetLastError());
     NA_CUDA(launch_tables(*ap, d_freq, nc, du, ov, gd->support, d_toff, d_tlen, d_tabs, s));
-    NA_CUDA(set_eval_smem(eval_dyn_smem(c_group, max_tab)));
+    NA_CUDA(set_eval_smem(eval_dyn_smem(c_group, max_tab + 2)));
 
     EvalArgs a{};
     a.uvw = obs->uvw_dev;
@@ -202,8 +204,10 @@ extern "C" psc_status psc_residual_grad_noalloc(const psc_obs *obs, const psc_ap
     a.c_group = c_group;
     a.n_tt = n_tt;
     a.n_cg = n_cg;
+    a.kv = 1;
     a.decorrelation = ap->decorrelation;
     a.max_tab_len = max_tab;
+    a.tab_stride = max_tab + 2;              // the table and two zero entries
     a.n_bricks = (long long)n_bricks;
     RedArgs r{};
     r.partials = d_part;

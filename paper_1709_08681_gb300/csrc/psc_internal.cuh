@@ -16,6 +16,7 @@ constexpr int kMaxThreads = 256;   // fused-kernel block size upper bound
 // Per-channel constants, built once per context.
 struct ChanConst {
     double uv_scale;   // nu / (c du): metres of baseline -> grid cells
+    float sc_hi, sc_lo;  // uv_scale split into two floats (sc_hi + sc_lo = uv_scale to ~2^-48)
     float alpha2;      // alpha(nu)^2 (rad^-2)
     float rho_max;     // (len - 1) / ov: taps at rho >= rho_max (cells) get A° = 0
     int tab_off;       // first table entry (float2 units)
@@ -25,7 +26,9 @@ struct ChanConst {
 // Arguments of the fused evaluation kernel (one launch covers one context).
 struct EvalArgs {
     const double *uvw;         // [nt][nbl][3] metres
+    const float4 *uvs;         // nullptr or [nt][nbl] (u_hi, u_lo, v_hi, v_lo) metres: the FP32 split of uvw, read instead
     const float2 *grid;        // [ng][ng] V° (complex64)
+    const unsigned *grid_bf16; // nullptr or [ng][ng] V° as bfloat16 pairs (re in the low half), read instead
     const ChanConst *chan;     // [nc]
     const float2 *tabs;        // radial tables: (A°(n), A°(n+1) - A°(n)) pairs
     const int2 *pairs;         // [nbl] antenna (i, j)
@@ -39,9 +42,11 @@ struct EvalArgs {
     const int *skip;           // nullptr or device flag: nonzero = solver stopped, do nothing
     int n_bl, nt, nc, ng, support, ov;
     float du;                  // grid cell (wavelengths)
-    int t_tile, c_group, n_tt, n_cg;
+    int t_tile, c_group, n_tt, n_cg;   // n_tt = ceil(nt / (t_tile * kv))
+    int kv;                    // visibilities per thread at consecutive times: 1 or 2
     int decorrelation;
-    int max_tab_len;           // longest table among the channels (for shared staging)
+    int max_tab_len;           // longest table among the channels
+    int tab_stride;            // staged entries per channel: max_tab_len + zero padding
     long long n_bricks;        // n_bl * n_cg * n_tt (partials are [kRed][n_bricks])
 };
 
@@ -121,12 +126,19 @@ size_t lm_smem_bytes(int n_ant);
 cudaError_t lm_prepare(int n_ant);
 cudaError_t launch_lm_restart(const LMArgs &a, const LMState *st0, const double *lm0, cudaStream_t s);
 cudaError_t set_eval_smem(size_t dyn);
-// Dynamic shared memory of one fused-kernel block (zero-padded tables).
-size_t eval_dyn_smem(int c_group, int max_tab_len);
+// Dynamic shared memory of one fused-kernel block (c_group zero-padded tables).
+size_t eval_dyn_smem(int c_group, int tab_stride);
+// Largest distance (metres, u-v plane) between the baselines of consecutive
+// time steps: *out_bits receives its FP32 bit pattern (atomic max; zero it first).
+cudaError_t launch_step_max(const double *uvw, int nt, int n_bl, unsigned *out_bits, cudaStream_t s);
 // Records msg as the context-free last error (psc_last_error(NULL)); returns st.
 psc_status set_global_error(psc_status st, const char *msg);
 cudaError_t launch_features(const StencilArgs &a, double *blsum, int n_ant, float *feat, cudaStream_t s);
 cudaError_t launch_model_grid(int n_img, int n_grid, const float *image, float2 *tmp, float2 *twiddle,
                               float2 *grid_out, cudaStream_t s);
+// FP32 split (u_hi, u_lo, v_hi, v_lo) of n uvw triples (FP64 metres).
+cudaError_t launch_split_uv(const double *uvw, size_t n, float4 *out, cudaStream_t s);
+// bfloat16 copy (nearest even, re in the low half) of n complex64 values.
+cudaError_t launch_grid_to_bf16(const float2 *grid, size_t n, unsigned *out, cudaStream_t s);
 
 }  // namespace psc

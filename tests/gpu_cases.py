@@ -9,7 +9,7 @@ from paper_1709_08681_gb300 import _abi
 
 
 class GpuProblem:
-    def __init__(self, m, img, use_oracle_grid=False, t_tile=None, c_group=None):
+    def __init__(self, m, img, use_oracle_grid=False, t_tile=None, c_group=None, kv=None):
         self.m = m
         dev = torch.device("cuda:0")
         self.uvw = torch.from_numpy(np.ascontiguousarray(m.uvw_m)).to(dev)
@@ -26,8 +26,8 @@ class GpuProblem:
         self.ctx = _abi.Context(m.n_ant, nt, len(m.freq_hz), self.uvw, m.freq_hz, m.ap_kind, m.diam_m,
                                 m.alpha_per_dlambda, m.decorrelation, n_img, ng, m.cell_rad, m.support,
                                 m.oversample, self.grid)
-        if t_tile or c_group:
-            self.ctx.psc_set_tiling(t_tile or 0, c_group or 0)
+        if t_tile or c_group or kv:
+            self.ctx.psc_set_tiling(t_tile or 0, c_group or 0, kv or 0)
 
     def predict(self, lm, derivs=True):
         v = torch.empty(self.shape, dtype=torch.complex64, device="cuda:0")

@@ -56,6 +56,7 @@ def test_model_grid_dense_random_image():
 # (spec, n_ant, n_time, freqs, t_tile, c_group): several tiles and ragged tails
 PREDICT_CASES = [
     (cases.DISK_SMALL, 7, 40, (1.2e9, 1.3e9, 1.4e9, 1.5e9, 1.6e9), 32, 4),
+    (cases.DISK_SMALL, 6, 31, (1.2e9, 1.3e9, 1.4e9), 25, 3),                # 75 threads: idle lanes
     (cases.DISK_SMALL, 5, 9, (1.4e9,), 8, 4),
     (cases.GAUSS_SMALL, 6, 20, (1.3e9, 1.4e9, 1.45e9), 16, 2),
     (cases.DISK_SMALL, 2, 1, (1.4e9,), 32, 4),
@@ -72,6 +73,52 @@ def test_predict_matches_oracle(case):
     assert _rel(Vg, V) < TOL_V
     for p in range(4):
         assert _rel(dVg[p], dV[p]) < TOL_V, p
+
+
+# Two visibilities per thread (consecutive times share the staged cells):
+# (n_ant, n_time, freqs, t_tile, c_group) with ragged time tails (odd n_time,
+# a last thread holding one visibility) and channel groups.  Frequencies stay
+# below 1.45 GHz so that the disk aperture fits inside the 32 x 32 window.
+KV2_CASES = [
+    (7, 37, (1.3e9, 1.35e9, 1.4e9), 8, 4),
+    (5, 64, (1.4e9,), 32, 1),
+    (6, 13, (1.25e9, 1.3e9, 1.35e9, 1.4e9, 1.42e9), 16, 2),
+    (2, 1, (1.4e9,), 32, 4),
+    (6, 23, (1.3e9, 1.33e9, 1.36e9, 1.39e9, 1.41e9, 1.43e9), 5, 5),     # warps straddle channels
+]
+
+
+@pytest.mark.parametrize("case", KV2_CASES)
+def test_two_visibilities_per_thread_match_oracle(case):
+    n_ant, nt, freqs, tt, cg = case
+    m, _, lmt, img = cases.problem(cases.DISK_SMALL, n_ant=n_ant, n_time=nt, freqs=freqs, sigma_arcsec=30.0)
+    V, dV = psc.predict(m, lmt)
+    gp = GpuProblem(m, img, t_tile=tt, c_group=cg, kv=2)
+    Vg, dVg = gp.predict(lmt)
+    assert _rel(Vg, V) < TOL_V
+    for p in range(4):
+        assert _rel(dVg[p], dV[p]) < TOL_V, p
+    vobs, w = _obs(m, lmt)
+    lm = 0.5 * lmt
+    chi2, g, H, X = psc.chi2_grad_normal(m, lm, vobs, w)
+    chi2g, gg, Hg, Xg = gp.ctx.psc_residual_grad(lm, gp.upload(vobs), gp.upload(w, torch.float32), 1.0, cross=True)
+    assert abs(chi2g - chi2) < TOL_V * chi2
+    Vl, dVl = psc.predict(m, lm)
+    gscale = 2.0 * np.sum(w[None] * np.abs(vobs - Vl)[None] * np.abs(dVl))
+    assert np.max(np.abs(gg - g)) < TOL_V * gscale
+    assert np.max(np.abs(Hg - H)) < TOL_V * np.max(np.abs(H))
+    assert np.max(np.abs(Xg - X)) < TOL_V * np.max(np.abs(H))
+
+
+def test_two_visibilities_per_thread_refused_when_the_aperture_leaves_the_window():
+    """The Gaussian table reaches S/sqrt(2) cells, beyond the window's half-width."""
+    m, _, _, img = cases.problem(cases.GAUSS_SMALL, n_ant=4, n_time=6)
+    gp = GpuProblem(m, img)
+    with pytest.raises(_abi.PscError) as e:
+        gp.ctx.psc_set_tiling(0, 0, 2)
+    assert e.value.status == _abi.PSC_ERR_ARG
+    with pytest.raises(_abi.PscError):
+        gp.ctx.psc_set_tiling(0, 0, 3)
 
 
 def test_predict_with_the_oracle_grid():
@@ -113,7 +160,7 @@ def _obs(m, lmt, sigma=1e-3, seed=7):
     return vobs, w
 
 
-@pytest.mark.parametrize("case", PREDICT_CASES[:3])
+@pytest.mark.parametrize("case", PREDICT_CASES[:4])
 def test_residual_grad_matches_oracle(case):
     spec, n_ant, nt, freqs, tt, cg = case
     m, _, lmt, img = cases.problem(spec, n_ant=n_ant, n_time=nt, freqs=freqs, sigma_arcsec=30.0)
@@ -208,9 +255,11 @@ def test_argument_errors_are_reported():
     m, _, lmt, img = cases.problem(cases.DISK_SMALL, n_ant=4, n_time=4)
     gp = GpuProblem(m, img)
     with pytest.raises(_abi.PscError) as e:
-        gp.ctx.psc_set_tiling(12, 4)
+        gp.ctx.psc_set_tiling(257, 1)
     with pytest.raises(_abi.PscError):
-        gp.ctx.psc_set_tiling(8, 1)
+        gp.ctx.psc_set_tiling(64, 8)
+    with pytest.raises(_abi.PscError):
+        gp.ctx.psc_set_tiling(32, 9)
     assert e.value.status == _abi.PSC_ERR_ARG
     with pytest.raises(_abi.PscError):
         gp.ctx.psc_residual_grad(lmt, gp.upload(np.zeros(gp.shape, np.complex64)), None, -1.0)
