@@ -99,7 +99,10 @@ typedef struct {
 } psc_aperture;
 
 /* One block of observation (normally one solution interval, Algorithm 1's
- * (tau_sol, dnu_sol)).  uvw_dev is borrowed for the lifetime of the ctx. */
+ * (tau_sol, dnu_sol)).  uvw_dev is borrowed for the lifetime of the ctx and
+ * must not change: psc_create also keeps a copy of (u, v) split into FP32
+ * high and low parts (16 bytes per time and baseline), which the fused
+ * kernel reads instead of FP64. */
 typedef struct {
     int           n_ant;     /* 2..512 */
     int           n_time;    /* >= 1 */
@@ -209,8 +212,7 @@ psc_status psc_lm_restart(psc_ctx *ctx);
  * each own vis_per_thread visibilities at consecutive time steps (a block
  * covers t_tile * vis_per_thread time steps; its size is t_tile * c_group
  * rounded up to a multiple of 32).  t_tile in [1, 256], c_group in [1, 8],
- * t_tile * c_group <= 256 (<= 128 for contexts in a batch, else the batch
- * resets them to (32, 4)), vis_per_thread in {1, 2}.  vis_per_thread = 2
+ * t_tile * c_group <= 256, vis_per_thread in {1, 2}.  vis_per_thread = 2
  * shares each staged grid cell between the thread's two visibilities; it is
  * refused (PSC_ERR_ARG) unless every channel's aperture lies inside the
  * S x S tap window and consecutive time steps move a baseline by at most 4
@@ -291,8 +293,9 @@ psc_status psc_learned_init(psc_ctx *ctx, psc_mlp *m, const void *vis_obs, const
  * reductions and the LM updates of all contexts follow as one launch each,
  * and the iteration is captured once in a CUDA graph and replayed (unless the
  * batch runs on the legacy NULL stream).  Contexts whose solver stopped skip
- * their bricks.  Every context in a batch uses 128 threads per block
- * (t_tile * c_group = 128; other tilings are reset to 32 x 4).
+ * their bricks.  The persistent launch uses the block size of the widest
+ * context's shape (t_tile * c_group rounded up to a multiple of 32); narrower
+ * contexts leave the extra lanes idle.
  * vis_obs[k], w[k] (NULL = ones) and w_scale[k] (NULL = all 1) are the data
  * of ctxs[k], borrowed like the contexts for the batch's lifetime.  The
  * offsets of all contexts are concatenated in the order of ctxs: lm0,
@@ -305,11 +308,13 @@ void psc_batch_destroy(psc_batch *b);
 const char *psc_batch_last_error(const psc_batch *b);
 
 /* Picks each context's launch shape by timing the fused kernel on its own
- * data: for vis_per_thread 1 and (where psc_set_tiling accepts it) 2, the
- * three channel groups whose smallest fitting time tile leaves the fewest of
- * 128 lanes idle (ragged time and channel tails count as idle), plus
- * (32, 4, 1); the fastest is kept.  Contexts of the same shape reuse the
- * first one's choice.  Writes the chosen (t_tile, c_group, vis_per_thread)
+ * data: for blocks of 128 and 256 threads and vis_per_thread 1 and (where
+ * psc_set_tiling accepts it) 2, the three channel groups whose smallest
+ * fitting time tile leaves the fewest lanes idle (ragged time and channel
+ * tails count as idle), plus (32, 4, 1); the fastest is kept, then contexts
+ * narrower than the widest choice take their fastest shape of that width (one
+ * block size serves the persistent launch).  Contexts of the same shape reuse
+ * the first one's choice.  Writes the chosen (t_tile, c_group, vis_per_thread)
  * of context k to tiling_out[3k..3k+2] (NULL to skip).  Synchronises. */
 psc_status psc_batch_autotune(psc_batch *b, int *tiling_out);
 

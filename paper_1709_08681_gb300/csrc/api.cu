@@ -692,6 +692,7 @@ struct psc_batch {
     int *d_active = nullptr;
     int total_bl = 0;
     int grid = 0;
+    int threads = 128;           // fused-kernel block size: the widest context's shape
     size_t eval_dyn = 0, lm_dyn = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -744,12 +745,10 @@ psc_status build_tables(psc_batch *b) {
     std::vector<const LMState *> st0(n);
     std::vector<const double *> lm0(n);
     size_t dyn = 0, lmd = 0;
+    int threads = 32;
     for (int k = 0; k < n; ++k) {
         psc_ctx *c = b->ctxs[k];
-        if (c->t_tile * c->c_group > 128) {          // batches launch 128 threads per block
-            c->t_tile = 32;
-            c->c_group = 4;
-        }
+        threads = std::max(threads, (c->t_tile * c->c_group + 31) / 32 * 32);
         psc_status st = ensure_partials(c);
         if (st != PSC_OK) return bfail(b, st, c->err);
         ev[k] = eval_args(c, c->d_lm_trial);
@@ -767,11 +766,12 @@ psc_status build_tables(psc_batch *b) {
         lmd = std::max(lmd, lm_smem_bytes(c->n_ant));
     }
     b->total_bl = blp[n];
+    b->threads = threads;
     b->eval_dyn = dyn;
     b->lm_dyn = lmd;
     PSC_BCUDA(b, set_eval_smem(dyn));
     int per_sm = 0, dev = 0, n_sm = 0;
-    PSC_BCUDA(b, eval_batch_occupancy(128, dyn, &per_sm));
+    PSC_BCUDA(b, eval_batch_occupancy(b->threads, dyn, &per_sm));
     PSC_BCUDA(b, cudaGetDevice(&dev));
     PSC_BCUDA(b, cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
     b->grid = std::max(1, per_sm) * n_sm;
@@ -812,7 +812,7 @@ psc_status enqueue_iteration(psc_batch *b) {
         }
         PSC_BCUDA(b, cudaEventRecord(b->ev_pool[b->ev_used], s));
     }
-    PSC_BCUDA(b, launch_eval_batch(b->d_eval, b->d_prefix, n, b->d_queue, 128, b->eval_dyn, b->grid, s));
+    PSC_BCUDA(b, launch_eval_batch(b->d_eval, b->d_prefix, n, b->d_queue, b->threads, b->eval_dyn, b->grid, s));
     if (b->prof) {
         PSC_BCUDA(b, cudaEventRecord(b->ev_pool[b->ev_used + 1], s));
         b->ev_used += 2;
@@ -848,32 +848,37 @@ __global__ void count_active_kernel(const LMArgs *la, int n, int *out) {
     if (threadIdx.x == 0) *out = c;
 }
 
-// Launch shapes worth timing for a context: for each vis_per_thread and
-// channel group, the smallest time tile with the fewest tiles that fit 128
-// threads; ranked by the share of the 128 lanes that hold a visibility
-// (ragged time and channel tails and idle lanes count as waste).
+// Launch shapes worth timing for a context: for each block size (128 and 256
+// threads), vis_per_thread and channel group, the smallest time tile with the
+// fewest tiles that fit the block; ranked by the share of the block's lanes
+// that hold a visibility (ragged time and channel tails and idle lanes count
+// as waste), the best three of each (block size, vis_per_thread).
 std::vector<std::array<int, 3>> tiling_candidates(const psc_ctx *c) {
-    struct Scored { double util; std::array<int, 3> t; };
+    struct Scored { double util; int threads; std::array<int, 3> t; };
     std::vector<Scored> all;
-    for (int kv : {1, 2}) {
-        if (!kv_allowed(c, kv)) continue;
-        for (int cg : {1, 2, 3, 4, 5, 6, 8}) {
-            if (cg > c->nc && cg > 1) continue;
-            const int tt_max = 128 / cg;
-            const int n_tt = (c->nt + tt_max * kv - 1) / (tt_max * kv);
-            const int tt = (c->nt + n_tt * kv - 1) / (n_tt * kv);
-            const int n_cg = (c->nc + cg - 1) / cg;
-            const double util = (double)c->nt / ((double)n_tt * tt * kv) * (double)c->nc / ((double)n_cg * cg) *
-                                (double)(tt * cg) / 128.0;
-            all.push_back({util, {tt, cg, kv}});
+    for (int threads : {128, 256}) {
+        for (int kv : {1, 2}) {
+            if (!kv_allowed(c, kv)) continue;
+            for (int cg : {1, 2, 3, 4, 5, 6, 8}) {
+                if (cg > c->nc && cg > 1) continue;
+                const int tt_max = threads / cg;
+                const int n_tt = (c->nt + tt_max * kv - 1) / (tt_max * kv);
+                const int tt = (c->nt + n_tt * kv - 1) / (n_tt * kv);
+                if ((tt * cg + 31) / 32 * 32 != threads) continue;   // belongs to the smaller block size
+                const int n_cg = (c->nc + cg - 1) / cg;
+                const double util = (double)c->nt / ((double)n_tt * tt * kv) * (double)c->nc / ((double)n_cg * cg) *
+                                    (double)(tt * cg) / threads;
+                all.push_back({util, threads, {tt, cg, kv}});
+            }
         }
     }
     std::sort(all.begin(), all.end(), [](const Scored &x, const Scored &y) { return x.util > y.util; });
     std::vector<std::array<int, 3>> out;
-    int per_kv[3] = {0, 0, 0};
+    int taken[2][3] = {{0, 0, 0}, {0, 0, 0}};
     for (const Scored &x : all) {
-        if (per_kv[x.t[2]] >= 3) continue;                 // the best three of each vis_per_thread
-        ++per_kv[x.t[2]];
+        int &n = taken[x.threads == 256][x.t[2]];
+        if (n >= 3) continue;
+        ++n;
         out.push_back(x.t);
     }
     const std::array<int, 3> dflt{32, 4, 1};
@@ -920,6 +925,8 @@ psc_status psc_batch_autotune(psc_batch *b, int *tiling_out) {
     PSC_BCUDA(b, cudaEventCreate(&e1));
     const int n = (int)b->ctxs.size();
     std::vector<double> zeros;
+    std::vector<std::vector<std::pair<float, std::array<int, 3>>>> timed(n);
+    std::vector<int> reused(n, -1);
     for (int k = 0; k < n; ++k) {
         psc_ctx *c = b->ctxs[k];
         // reuse the choice of an earlier context with the same shape
@@ -931,6 +938,7 @@ psc_status psc_batch_autotune(psc_batch *b, int *tiling_out) {
                 kv_allowed(c, o->kv))
                 reuse = j;
         }
+        reused[k] = reuse;
         if (reuse >= 0) {
             c->t_tile = b->ctxs[reuse]->t_tile;
             c->c_group = b->ctxs[reuse]->c_group;
@@ -941,6 +949,7 @@ psc_status psc_batch_autotune(psc_batch *b, int *tiling_out) {
                                          cudaMemcpyHostToDevice, b->stream));
             float best = 1e30f;
             int bt = 32, bc = 4, bk = 1;
+            timed[k].clear();
             for (const auto &cd : tiling_candidates(c)) {
                 c->t_tile = cd[0];
                 c->c_group = cd[1];
@@ -959,11 +968,30 @@ psc_status psc_batch_autotune(psc_batch *b, int *tiling_out) {
                 PSC_BCUDA(b, cudaEventSynchronize(e1));
                 float ms = 0.f;
                 PSC_BCUDA(b, cudaEventElapsedTime(&ms, e0, e1));
+                timed[k].push_back({ms, cd});
                 if (ms < best) { best = ms; bt = cd[0]; bc = cd[1]; bk = cd[2]; }
             }
             c->t_tile = bt;
             c->c_group = bc;
             c->kv = bk;
+        }
+    }
+    // one block size serves the whole persistent launch: contexts whose best
+    // shape is narrower take their fastest timed shape of the widest size
+    int width = 32;
+    for (psc_ctx *c : b->ctxs) width = std::max(width, (c->t_tile * c->c_group + 31) / 32 * 32);
+    for (int k = 0; k < n; ++k) {
+        psc_ctx *c = b->ctxs[k];
+        if (reused[k] >= 0) {
+            psc_ctx *o = b->ctxs[reused[k]];
+            c->t_tile = o->t_tile; c->c_group = o->c_group; c->kv = o->kv;
+        } else if ((c->t_tile * c->c_group + 31) / 32 * 32 != width) {
+            float best = 1e30f;
+            for (const auto &x : timed[k])
+                if ((x.second[0] * x.second[1] + 31) / 32 * 32 == width && x.first < best) {
+                    best = x.first;
+                    c->t_tile = x.second[0]; c->c_group = x.second[1]; c->kv = x.second[2];
+                }
         }
         if (tiling_out) {
             tiling_out[3 * k] = c->t_tile;

@@ -61,9 +61,12 @@ __device__ __forceinline__ float2 grid_cell(const EvalArgs &a, size_t idx) {
     return __ldg(&a.grid[idx]);
 }
 
+// Shared-memory load at a 32-bit shared address.  Not volatile: the loads
+// are pure, and the compiler may schedule them early (they are only issued
+// inside tap loops that follow the barrier publishing the tables).
 __device__ __forceinline__ float2 lds_f2(unsigned addr) {
     float2 v;
-    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(addr));
+    asm("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(addr));
     return v;
 }
 
@@ -90,17 +93,17 @@ __device__ __forceinline__ void grid_pos(float uh, float ul, float sh, float sl,
 }
 
 // One row of taps for kV visibilities: n consecutive staged cells starting at
-// shared address g_addr; visibility v's first tap is at dxo[v] (= dx ov).  The
+// row (shared memory); visibility v's first tap is at dxo[v] (= dx ov).  The
 // table address is tab_adj + (bits of floor(t) + 2^23) * 8.  Accumulates
 // P = sum A G' and Q = sum A dxo G' per visibility.
 template <int kV>
-__device__ __forceinline__ void row_taps(unsigned g_addr, int n, float (&dxo)[kV], const float (&dyo2)[kV],
-                                         float ov, unsigned tab_adj, float (&pr)[kV], float (&pi)[kV],
-                                         float (&qr)[kV], float (&qi)[kV]) {
+__device__ __forceinline__ void row_taps(const float2 *__restrict__ row, int n, float (&dxo)[kV],
+                                         const float (&dyo2)[kV], float ov, unsigned tab_adj, float (&pr)[kV],
+                                         float (&pi)[kV], float (&qr)[kV], float (&qi)[kV]) {
     constexpr int kUnroll = kV == 1 ? 4 : 2;
 #pragma unroll kUnroll
     for (int k = 0; k < n; ++k) {
-        const float2 g = lds_f2(g_addr + 8u * (unsigned)k);
+        const float2 g = row[k];
 #pragma unroll
         for (int v = 0; v < kV; ++v) {
             const float s2 = fmaf(dxo[v], dxo[v], dyo2[v]);
@@ -267,7 +270,6 @@ __device__ __forceinline__ void eval_brick(const EvalArgs &a, int brick, float2 
         const float ov = (float)a.ov;
         const float rmax2 = rmax * rmax;
         if (staged) {
-            const unsigned tile_addr = (unsigned)__cvta_generic_to_shared(sh.tile);
             int wx[kV], wy[kV];
             int r_lo = INT_MAX, r_hi = INT_MIN;
 #pragma unroll
@@ -304,8 +306,7 @@ __device__ __forceinline__ void eval_brick(const EvalArgs &a, int brick, float2 
                     dxo[v] = (hx[v] - (float)(c_lo - wx[v])) * ov;
                     pr[v] = pi[v] = qr[v] = qi[v] = 0.f;
                 }
-                row_taps<kV>(tile_addr + 8u * (unsigned)(cy * kTile + c_lo), c_hi - c_lo + 1, dxo, dyo2, ov,
-                             tab_adj, pr, pi, qr, qi);
+                row_taps<kV>(sh.tile + cy * kTile + c_lo, c_hi - c_lo + 1, dxo, dyo2, ov, tab_adj, pr, pi, qr, qi);
 #pragma unroll
                 for (int v = 0; v < kV; ++v) {
                     S0[v].x += pr[v]; S0[v].y += pi[v];
