@@ -38,9 +38,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "Gvis/s predict+∂/∂pointing; solves/s to 1″ RMS offset, learned vs plain LM"
-FLOPS_PER_TAP = 15      # s = dx^2+dy^2 (2), sqrt (1), t = rho ov (1), A° lerp (2), P += A G (4), A dx (1), Q += (A dx) G (4)
 SMS_GB300 = 152
-FP32_LANES_PER_SM = 128
 
 
 def parse():
@@ -54,6 +52,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     p.add_argument("--no-learned", action="store_true", help="skip the learned-initialiser comparison")
+    p.add_argument("--mixed-intervals", type=int, default=256,
+                   help="intervals of the mixed-array batched-solve section (0 skips it)")
     p.add_argument("--learned-train", type=int, default=1000, help="training intervals of the learned initialiser")
     p.add_argument("--learned-eval", type=int, default=20, help="held-out intervals of the comparison")
     return p.parse_args()
@@ -119,20 +119,6 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- workload helpers
-
-def taps_per_channel(wl):
-    """Expected non-zero taps per visibility per channel: pi rho_max^2 cells^2
-    with rho_max the radial table's support (disk), clipped to the window."""
-    du = 1.0 / (wl.n_grid * wl.cell_rad)
-    out = []
-    for f in wl.freq_hz:
-        dl = wl.diam_m * f / 299_792_458.0
-        rho = dl / du if wl.ap_kind == "disk" else 0.5 * wl.support * math.sqrt(2)
-        L = math.floor(wl.oversample * rho) + 2
-        r = (L - 1) / wl.oversample
-        out.append(min(math.pi * r * r, wl.support * wl.support))
-    return np.asarray(out)
-
 
 def cpu_sample_oracle(wl, vis_host, w_host, target_s, interval=0, min_t=1):
     """Times the FP64 oracle (predict + derivatives + reductions) on the first
@@ -232,6 +218,7 @@ def run_ours(args):
         raise SystemExit("bench.py needs a CUDA device (the CUDA library is the only implementation)")
     torch.cuda.set_device(local)
     from paper_1709_08681_gb300 import _abi, inputs as I
+    from paper_1709_08681_gb300 import roofline as RL
     from paper_1709_08681_gb300.session import Session
 
     # weak scaling: every rank solves its own batch of four intervals (own seed)
@@ -308,15 +295,15 @@ def run_ours(args):
         launches_per_step = 5
 
         # roofline of the fused kernel (FP32 ALU bound); one launch = all intervals
-        taps = taps_per_channel(wl)
+        taps = RL.taps_per_channel(wl)
         flops_per_launch = 0.0
         for (t0, nt) in wl.intervals:
-            flops_per_launch += nt * wl.n_bl * float(np.sum(taps)) * FLOPS_PER_TAP
+            flops_per_launch += nt * wl.n_bl * float(np.sum(taps)) * RL.FLOPS_PER_TAP
         avg_launch_ms = kern_ms / max(kern_n, 1)
         achieved = flops_per_launch / (avg_launch_ms * 1e-3) / 1e12
         props = torch.cuda.get_device_properties(local)
         n_sm = props.multi_processor_count
-        peak = n_sm * FP32_LANES_PER_SM * 2 * 2.070e9 / 1e12
+        peak = RL.fp32_peak_tflops(n_sm)
 
         # end to end: pinned host buffers, copies inside the timed region
         vis_h = vis.cpu().pin_memory()
@@ -394,6 +381,18 @@ def run_ours(args):
         rep, _ = LI.run(n_train=args.learned_train, n_eval=args.learned_eval, steps=1500, batch=1024, n_geom=8,
                         seed=args.seed, log=None)
         line["learned_init"] = {"workload": "disk64_l16ch", **rep}
+    if rank == 0 and args.mixed_intervals > 0:
+        # batched solves over mixed intervals: 27/64/197-antenna arrays,
+        # 30-600 time steps, offsets 10-60" with 2' outliers (one persistent
+        # launch per LM iteration over all intervals, graph-replayed)
+        from paper_1709_08681_gb300 import mixed as MX
+        mrep, _ = MX.run(n_intervals=args.mixed_intervals, seed=args.seed)
+        mrep.pop("tiling", None)
+        props = torch.cuda.get_device_properties(local)
+        mrep["roofline"] = {"bound": "alu", "achieved": mrep["fused_tflops"],
+                            "peak": RL.fp32_peak_tflops(props.multi_processor_count), "unit": "TFLOP/s"}
+        mrep["roofline"]["frac"] = mrep["roofline"]["achieved"] / mrep["roofline"]["peak"]
+        line["mixed_batch"] = {"workload": "mixed_batch%d" % args.mixed_intervals, **mrep}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         vis_host = vis.cpu().numpy()
         w_host = w.cpu().numpy()

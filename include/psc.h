@@ -59,6 +59,7 @@ typedef enum {
 
 enum { PSC_AP_DISK = 0, PSC_AP_GAUSS = 1 };
 enum { PSC_GRID_F32 = 0, PSC_GRID_BF16 = 1 };
+enum { PSC_STAGE_AUTO = 0, PSC_STAGE_NEVER = 1 };
 enum { PSC_LM_FULL = 0, PSC_LM_BLOCK = 1 };
 enum { PSC_STOP_NONE = 0, PSC_STOP_STEP = 1, PSC_STOP_CHI2 = 2, PSC_STOP_LAMBDA = 3,
        PSC_STOP_MAX_ITER = 4, PSC_STOP_NUMERIC = 5 };
@@ -220,6 +221,15 @@ psc_status psc_lm_restart(psc_ctx *ctx);
  * beyond FP32 summation order. */
 psc_status psc_set_tiling(psc_ctx *ctx, int t_tile, int c_group, int vis_per_thread);
 
+/* Grid access of the fused kernel.  PSC_STAGE_AUTO (default): a thread
+ * block copies the grid cells its visibilities touch (with the per-cell half
+ * of the pointing ramp applied) into shared memory when they fit a 64 x 64
+ * tile, else reads them from global memory.  PSC_STAGE_NEVER: always read
+ * from global memory (pays off for small apertures and long baselines, where
+ * a brick's visibilities share few cells).  Results are the same up to FP32
+ * summation order.  Errors: PSC_ERR_ARG for an unknown mode. */
+psc_status psc_set_staging(psc_ctx *ctx, int mode);
+
 /* Storage precision of the model grid V° that the fused evaluation reads
  * (psc_predict, psc_residual_grad, the solvers and batches; the feature pass
  * of psc_features always reads the FP32 grid).  PSC_GRID_F32 (default) reads
@@ -313,9 +323,12 @@ const char *psc_batch_last_error(const psc_batch *b);
  * fitting time tile leaves the fewest lanes idle (ragged time and channel
  * tails count as idle), plus (32, 4, 1); the fastest is kept, then contexts
  * narrower than the widest choice take their fastest shape of that width (one
- * block size serves the persistent launch).  Contexts of the same shape reuse
- * the first one's choice.  Writes the chosen (t_tile, c_group, vis_per_thread)
- * of context k to tiling_out[3k..3k+2] (NULL to skip).  Synchronises. */
+ * block size serves the persistent launch); the winner is also timed with
+ * PSC_STAGE_NEVER and the faster grid access kept.  Contexts of the same
+ * array, channels and grid reuse the first one's choice, with the time tile
+ * refitted to their own length.  Writes the chosen (t_tile, c_group,
+ * vis_per_thread, staging mode) of context k to tiling_out[4k..4k+3] (NULL to
+ * skip).  Synchronises. */
 psc_status psc_batch_autotune(psc_batch *b, int *tiling_out);
 
 /* Start (host offsets, options as for psc_lm_begin), restart on the device,

@@ -20,12 +20,13 @@ PSC_OK, PSC_ERR_ARG, PSC_ERR_CUDA, PSC_ERR_OOM = 0, 1, 2, 3
 PSC_ERR_NOT_CONVERGED, PSC_ERR_TIMEOUT, PSC_ERR_NUMERIC, PSC_ERR_DEVICE = 4, 5, 6, 7
 PSC_AP_DISK, PSC_AP_GAUSS = 0, 1
 PSC_GRID_F32, PSC_GRID_BF16 = 0, 1
+PSC_STAGE_AUTO, PSC_STAGE_NEVER = 0, 1
 PSC_LM_FULL, PSC_LM_BLOCK = 0, 1
 STOP_REASONS = {0: "none", 1: "step", 2: "chi2", 3: "lambda", 4: "max_iter", 5: "numeric"}
 
 EXPORTS = ("psc_solve_opts_default", "psc_model_grid", "psc_create", "psc_destroy", "psc_last_error",
            "psc_predict", "psc_residual_grad", "psc_solve_offsets", "psc_lm_begin", "psc_lm_iterate",
-           "psc_lm_end", "psc_lm_restart", "psc_set_tiling", "psc_set_grid_precision", "psc_profile", "psc_profile_read",
+           "psc_lm_end", "psc_lm_restart", "psc_set_tiling", "psc_set_grid_precision", "psc_set_staging", "psc_profile", "psc_profile_read",
            "psc_residual_grad_noalloc", "psc_batch_create", "psc_batch_destroy", "psc_batch_last_error",
            "psc_batch_autotune", "psc_batch_begin", "psc_batch_restart", "psc_batch_iterate", "psc_batch_end",
            "psc_solve_batch", "psc_batch_profile", "psc_batch_profile_read", "psc_features",
@@ -97,6 +98,7 @@ def lib():
             "psc_lm_restart": (ctypes.c_int, [_V]),
             "psc_set_tiling": (ctypes.c_int, [_V, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
             "psc_set_grid_precision": (ctypes.c_int, [_V, ctypes.c_int]),
+            "psc_set_staging": (ctypes.c_int, [_V, ctypes.c_int]),
             "psc_profile": (ctypes.c_int, [_V, ctypes.c_int]),
             "psc_profile_read": (ctypes.c_int, [_V, _D, ctypes.POINTER(ctypes.c_int)]),
             "psc_residual_grad_noalloc": (ctypes.c_int, [ctypes.POINTER(psc_obs), ctypes.POINTER(psc_aperture),
@@ -234,6 +236,9 @@ class Context:
     def psc_set_tiling(self, t_tile=0, c_group=0, vis_per_thread=0):
         _check(lib().psc_set_tiling(self.h, int(t_tile), int(c_group), int(vis_per_thread)), self.h)
 
+    def psc_set_staging(self, mode):
+        _check(lib().psc_set_staging(self.h, int(mode)), self.h)
+
     def psc_set_grid_precision(self, precision):
         _check(lib().psc_set_grid_precision(self.h, int(precision)), self.h)
 
@@ -355,10 +360,10 @@ class Batch:
         return out
 
     def psc_batch_autotune(self):
-        """Chosen (t_tile, c_group, vis_per_thread) of every context."""
-        t = (ctypes.c_int * (3 * len(self.contexts)))()
+        """Chosen (t_tile, c_group, vis_per_thread, staging mode) of every context."""
+        t = (ctypes.c_int * (4 * len(self.contexts)))()
         _bcheck(lib().psc_batch_autotune(self.h, t), self.h)
-        return [tuple(t[3 * k:3 * k + 3]) for k in range(len(self.contexts))]
+        return [tuple(t[4 * k:4 * k + 4]) for k in range(len(self.contexts))]
 
     def psc_batch_begin(self, lm0_list, opts=None):
         self._lm0 = self._concat(lm0_list)

@@ -46,6 +46,7 @@ struct psc_ctx {
     int max_tab_len = 0;
     int t_tile = 32, c_group = 4;
     int kv = 1;                  // visibilities per thread at consecutive times
+    int no_stage = 0;            // PSC_STAGE_NEVER: taps read the grid from global memory
     double step_cells = 0.0;     // largest move of a baseline between time steps (cells, top channel)
     bool multi_ok = false;       // kv > 1 allowed: every channel's aperture fits inside the S x S window
     LMState h_state{};
@@ -167,6 +168,7 @@ EvalArgs eval_args(const psc_ctx *c, const double *lm_dev) {
     a.t_tile = c->t_tile;
     a.c_group = c->c_group;
     a.kv = c->kv;
+    a.no_stage = c->no_stage;
     a.n_tt = n_tt(c);
     a.n_cg = n_cg(c);
     a.decorrelation = c->ap.decorrelation;
@@ -419,6 +421,13 @@ psc_status psc_set_tiling(psc_ctx *ctx, int t_tile, int c_group, int vis_per_thr
     ctx->t_tile = tt;
     ctx->c_group = cg;
     ctx->kv = kv;
+    return PSC_OK;
+}
+
+psc_status psc_set_staging(psc_ctx *ctx, int mode) {
+    if (!ctx) return fail(nullptr, PSC_ERR_ARG, "ctx is NULL");
+    if (mode != PSC_STAGE_AUTO && mode != PSC_STAGE_NEVER) return fail(ctx, PSC_ERR_ARG, "mode must be PSC_STAGE_AUTO or PSC_STAGE_NEVER");
+    ctx->no_stage = mode == PSC_STAGE_NEVER;
     return PSC_OK;
 }
 
@@ -848,6 +857,14 @@ __global__ void count_active_kernel(const LMArgs *la, int n, int *out) {
     if (threadIdx.x == 0) *out = c;
 }
 
+// Smallest time tile that covers nt steps in the fewest tiles of at most
+// threads / c_group threads per channel.
+int fit_t_tile(int nt, int threads, int cg, int kv) {
+    const int tt_max = std::max(1, threads / cg);
+    const int n_tt = (nt + tt_max * kv - 1) / (tt_max * kv);
+    return (nt + n_tt * kv - 1) / (n_tt * kv);
+}
+
 // Launch shapes worth timing for a context: for each block size (128 and 256
 // threads), vis_per_thread and channel group, the smallest time tile with the
 // fewest tiles that fit the block; ranked by the share of the block's lanes
@@ -861,9 +878,8 @@ std::vector<std::array<int, 3>> tiling_candidates(const psc_ctx *c) {
             if (!kv_allowed(c, kv)) continue;
             for (int cg : {1, 2, 3, 4, 5, 6, 8}) {
                 if (cg > c->nc && cg > 1) continue;
-                const int tt_max = threads / cg;
-                const int n_tt = (c->nt + tt_max * kv - 1) / (tt_max * kv);
-                const int tt = (c->nt + n_tt * kv - 1) / (n_tt * kv);
+                const int tt = fit_t_tile(c->nt, threads, cg, kv);
+                const int n_tt = (c->nt + tt * kv - 1) / (tt * kv);
                 if ((tt * cg + 31) / 32 * 32 != threads) continue;   // belongs to the smaller block size
                 const int n_cg = (c->nc + cg - 1) / cg;
                 const double util = (double)c->nt / ((double)n_tt * tt * kv) * (double)c->nc / ((double)n_cg * cg) *
@@ -929,27 +945,24 @@ psc_status psc_batch_autotune(psc_batch *b, int *tiling_out) {
     std::vector<int> reused(n, -1);
     for (int k = 0; k < n; ++k) {
         psc_ctx *c = b->ctxs[k];
-        // reuse the choice of an earlier context with the same shape
+        // contexts of the same array, channels and grid (any length) reuse the
+        // first one's choice, refitted to their own number of time steps
         int reuse = -1;
         for (int j = 0; j < k && reuse < 0; ++j) {
             psc_ctx *o = b->ctxs[j];
-            if (o->n_ant == c->n_ant && o->nc == c->nc && o->nt == c->nt && o->gd.n_grid == c->gd.n_grid &&
-                o->du == c->du && o->max_tab_len == c->max_tab_len && o->multi_ok == c->multi_ok &&
-                kv_allowed(c, o->kv))
+            if (reused[j] < 0 && o->n_ant == c->n_ant && o->nc == c->nc && o->gd.n_grid == c->gd.n_grid &&
+                o->du == c->du && o->max_tab_len == c->max_tab_len && o->multi_ok == c->multi_ok)
                 reuse = j;
         }
         reused[k] = reuse;
-        if (reuse >= 0) {
-            c->t_tile = b->ctxs[reuse]->t_tile;
-            c->c_group = b->ctxs[reuse]->c_group;
-            c->kv = b->ctxs[reuse]->kv;
-        } else {
+        if (reuse < 0) {
             zeros.assign(2 * c->n_ant, 0.0);
             PSC_BCUDA(b, cudaMemcpyAsync(c->d_lm_trial, zeros.data(), sizeof(double) * zeros.size(),
                                          cudaMemcpyHostToDevice, b->stream));
             float best = 1e30f;
             int bt = 32, bc = 4, bk = 1;
             timed[k].clear();
+            c->no_stage = 0;
             for (const auto &cd : tiling_candidates(c)) {
                 c->t_tile = cd[0];
                 c->c_group = cd[1];
@@ -974,17 +987,38 @@ psc_status psc_batch_autotune(psc_batch *b, int *tiling_out) {
             c->t_tile = bt;
             c->c_group = bc;
             c->kv = bk;
+            // and whether staging the grid pays for this shape
+            c->no_stage = 1;
+            {
+                EvalArgs a = eval_args(c, c->d_lm_trial);
+                a.vis_obs = (const float2 *)b->vis[k];
+                a.w = b->w[k];
+                a.w_scale = (float)b->w_scale[k];
+                PSC_BCUDA(b, set_eval_smem(eval_dyn_smem(c->c_group, tab_stride(c, c->kv))));
+                PSC_BCUDA(b, launch_eval(a, false, b->stream));
+                PSC_BCUDA(b, cudaEventRecord(e0, b->stream));
+                for (int r = 0; r < 3; ++r) PSC_BCUDA(b, launch_eval(a, false, b->stream));
+                PSC_BCUDA(b, cudaEventRecord(e1, b->stream));
+                PSC_BCUDA(b, cudaEventSynchronize(e1));
+                float ms = 0.f;
+                PSC_BCUDA(b, cudaEventElapsedTime(&ms, e0, e1));
+                c->no_stage = ms < best ? 1 : 0;
+            }
         }
     }
     // one block size serves the whole persistent launch: contexts whose best
     // shape is narrower take their fastest timed shape of the widest size
     int width = 32;
-    for (psc_ctx *c : b->ctxs) width = std::max(width, (c->t_tile * c->c_group + 31) / 32 * 32);
+    for (int k = 0; k < n; ++k)
+        if (reused[k] < 0) width = std::max(width, (b->ctxs[k]->t_tile * b->ctxs[k]->c_group + 31) / 32 * 32);
     for (int k = 0; k < n; ++k) {
         psc_ctx *c = b->ctxs[k];
         if (reused[k] >= 0) {
-            psc_ctx *o = b->ctxs[reused[k]];
-            c->t_tile = o->t_tile; c->c_group = o->c_group; c->kv = o->kv;
+            const psc_ctx *o = b->ctxs[reused[k]];
+            c->no_stage = o->no_stage;
+            c->c_group = o->c_group;
+            c->kv = kv_allowed(c, o->kv) ? o->kv : 1;
+            c->t_tile = fit_t_tile(c->nt, (o->t_tile * o->c_group + 31) / 32 * 32, c->c_group, c->kv);
         } else if ((c->t_tile * c->c_group + 31) / 32 * 32 != width) {
             float best = 1e30f;
             for (const auto &x : timed[k])
@@ -994,9 +1028,10 @@ psc_status psc_batch_autotune(psc_batch *b, int *tiling_out) {
                 }
         }
         if (tiling_out) {
-            tiling_out[3 * k] = c->t_tile;
-            tiling_out[3 * k + 1] = c->c_group;
-            tiling_out[3 * k + 2] = c->kv;
+            tiling_out[4 * k] = c->t_tile;
+            tiling_out[4 * k + 1] = c->c_group;
+            tiling_out[4 * k + 2] = c->kv;
+            tiling_out[4 * k + 3] = c->no_stage ? PSC_STAGE_NEVER : PSC_STAGE_AUTO;
         }
     }
     cudaEventDestroy(e0);

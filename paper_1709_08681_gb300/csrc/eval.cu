@@ -128,6 +128,7 @@ struct BlockShared {
     float red[kMaxThreads / 32][kRed];
     float bl[4];
     int box[4];
+    int taps;          // taps of the brick's visibilities (pi rho_max^2 each, rounded up)
 };
 
 // One brick: kv visibilities per thread.  acc receives the thread's 15 sums
@@ -157,6 +158,7 @@ __device__ __forceinline__ void eval_brick(const EvalArgs &a, int brick, float2 
         sh.bl[2] = (float)(li - lj);   // decorrelation: l_i - l_j
         sh.bl[3] = (float)(mi - mj);
         sh.box[0] = INT_MAX; sh.box[1] = INT_MIN; sh.box[2] = INT_MAX; sh.box[3] = INT_MIN;
+        sh.taps = 0;
     }
     __syncthreads();
     const float L = sh.bl[0], M = sh.bl[1], dL = sh.bl[2], dM = sh.bl[3];
@@ -205,6 +207,8 @@ __device__ __forceinline__ void eval_brick(const EvalArgs &a, int brick, float2 
         if (lox <= hix && loy <= hiy) {
             atomicMin(&sh.box[0], lox); atomicMax(&sh.box[1], hix);
             atomicMin(&sh.box[2], loy); atomicMax(&sh.box[3], hiy);
+            const int nv = min(kV, a.nt - t0);
+            atomicAdd(&sh.taps, nv * (int)ceilf(3.14159265f * rmax * rmax));
         }
     }
     // radial tables of this block's channels as (c_n, s_n), zero-padded
@@ -225,21 +229,30 @@ __device__ __forceinline__ void eval_brick(const EvalArgs &a, int brick, float2 
     const bool empty = sh.box[0] > sh.box[1];         // no visibility of the brick has a tap
     const int bx0 = empty ? 0 : sh.box[0], by0 = empty ? 0 : sh.box[2];
     const int ex = empty ? 0 : sh.box[1] - bx0 + 1, ey = empty ? 0 : sh.box[3] - by0 + 1;
-    const bool staged = ex <= kTile && ey <= kTile;    // uniform over the block
+    // Staging pays when the brick's taps reuse its cells: a staged cell costs
+    // a global load, two complex products and a store (about four unstaged
+    // taps' extra work), so stage only boxes of at most taps / 4 cells that
+    // fit the tile.  Uniform over the block.
+    const bool staged = !a.no_stage && ex <= kTile && ey <= kTile && 4 * ex * ey <= sh.taps;
 
-    if (staged && !empty) {
-        // per-cell half of the ramp, relative to the tile origin
-        for (int k = tid; k < ex; k += blockDim.x) {
+    // per-cell half of the ramp, exp(-i pi du (k_x L + k_y M)) = phx[k_x] phy[k_y],
+    // with (k_x, k_y) relative to the tile origin (staged) or to each
+    // visibility's window origin (unstaged: k < S)
+    if (!empty) {
+        const int nx = staged ? ex : S, ny = staged ? ey : S;
+        for (int k = tid; k < nx; k += blockDim.x) {
             float s, co;
             sincospif(-(float)k * a.du * L, &s, &co);
             sh.phx[k] = make_float2(co, s);
         }
-        for (int k = tid; k < ey; k += blockDim.x) {
+        for (int k = tid; k < ny; k += blockDim.x) {
             float s, co;
             sincospif(-(float)k * a.du * M, &s, &co);
             sh.phy[k] = make_float2(co, s);
         }
         __syncthreads();
+    }
+    if (staged && !empty) {
         // threads -> (column, row group) with shifts: 64 columns per pass for
         // blocks of >= 64 threads, 32 for a 32-thread block (two passes);
         // the row step blockDim >> cshift is >= 1 for every allowed block size
@@ -316,35 +329,26 @@ __device__ __forceinline__ void eval_brick(const EvalArgs &a, int brick, float2 
                 }
             }
         } else {
-            float sdx, cdx;
-            sincospif(-a.du * L, &sdx, &cdx);                  // per-column ramp step
-            const float2 step = make_float2(cdx, sdx);
+            // unstaged: taps read the grid (L1/L2), the cell half of the ramp
+            // comes from phx / phy; rows and columns are clipped to the grid
 #pragma unroll
             for (int v = 0; v < kV; ++v) {
-                const int b_lo = max(0, (int)floorf(hy[v] - rmax) + 1);
-                const int b_hi = min(S - 1, (int)ceilf(hy[v] + rmax) - 1);
+                const int b_lo = max(max(0, (int)floorf(hy[v] - rmax) + 1), -iy0[v]);
+                const int b_hi = min(min(S - 1, (int)ceilf(hy[v] + rmax) - 1), a.ng - 1 - iy0[v]);
                 for (int b = b_lo; b <= b_hi; ++b) {
                     const float dy = hy[v] - (float)b;
                     const float rem = rmax2 - dy * dy;
                     if (!(rem > 0.f)) continue;
                     const float r = fminf(rem * rsqrt_fast(rem), rmax);
-                    const int a_lo = max(0, (int)floorf(hx[v] - r) + 1);
-                    const int a_hi = min(S - 1, (int)ceilf(hx[v] + r) - 1);
+                    const int a_lo = max(max(0, (int)floorf(hx[v] - r) + 1), -ix0[v]);
+                    const int a_hi = min(min(S - 1, (int)ceilf(hx[v] + r) - 1), a.ng - 1 - ix0[v]);
                     const float dyo = dy * ov;
                     const float dyo2 = fmaf(dyo, dyo, 1e-20f);
                     float pr = 0.f, pi = 0.f, qr = 0.f, qi = 0.f;
-                    // ramp exp(-i pi du (a L + b M)) relative to this visibility's window origin
-                    float sz, cz;
-                    sincospif(-a.du * ((float)a_lo * L + (float)b * M), &sz, &cz);
-                    float2 z = make_float2(cz, sz);
-                    const int gy = iy0[v] + b;
+                    const size_t row = (size_t)(iy0[v] + b) * a.ng + ix0[v];
                     float dd = (hx[v] - (float)a_lo) * ov;
                     for (int aa = a_lo; aa <= a_hi; ++aa, dd -= ov) {
-                        const int gx = ix0[v] + aa;
-                        float2 g = make_float2(0.f, 0.f);
-                        if (gx >= 0 && gx < a.ng && gy >= 0 && gy < a.ng) g = grid_cell(a, (size_t)gy * a.ng + gx);
-                        g = cmul(g, z);
-                        z = cmul(z, step);
+                        const float2 g = cmul(grid_cell(a, row + aa), sh.phx[aa]);
                         const float s2 = fmaf(dd, dd, dyo2);
                         const float tv = s2 * rsqrt_fast(s2);
                         const float tf = __fadd_rz(tv, 8388608.0f);
@@ -356,10 +360,13 @@ __device__ __forceinline__ void eval_brick(const EvalArgs &a, int brick, float2 
                         qr = fmaf(Ad, g.x, qr);
                         qi = fmaf(Ad, g.y, qi);
                     }
-                    S0[v].x += pr; S0[v].y += pi;
-                    Su[v].x += qr; Su[v].y += qi;
-                    Sv[v].x = fmaf(dy, pr, Sv[v].x);
-                    Sv[v].y = fmaf(dy, pi, Sv[v].y);
+                    const float2 py = sh.phy[b];
+                    const float2 P = cmul(make_float2(pr, pi), py);
+                    const float2 Q = cmul(make_float2(qr, qi), py);
+                    S0[v].x += P.x; S0[v].y += P.y;
+                    Su[v].x += Q.x; Su[v].y += Q.y;
+                    Sv[v].x = fmaf(dy, P.x, Sv[v].x);
+                    Sv[v].y = fmaf(dy, P.y, Sv[v].y);
                 }
             }
         }

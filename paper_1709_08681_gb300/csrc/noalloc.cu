@@ -205,6 +205,7 @@ extern "C" psc_status psc_residual_grad_noalloc(const psc_obs *obs, const psc_ap
     a.n_tt = n_tt;
     a.n_cg = n_cg;
     a.kv = 1;
+    a.no_stage = 0;
     a.decorrelation = ap->decorrelation;
     a.max_tab_len = max_tab;
     a.tab_stride = max_tab + 2;              // the table and two zero entries

@@ -44,6 +44,7 @@ struct EvalArgs {
     float du;                  // grid cell (wavelengths)
     int t_tile, c_group, n_tt, n_cg;   // n_tt = ceil(nt / (t_tile * kv))
     int kv;                    // visibilities per thread at consecutive times: 1 or 2
+    int no_stage;              // 1: never stage the grid (taps read it from L1/L2)
     int decorrelation;
     int max_tab_len;           // longest table among the channels
     int tab_stride;            // staged entries per channel: max_tab_len + zero padding

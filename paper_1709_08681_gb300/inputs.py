@@ -286,3 +286,119 @@ WORKLOADS = {
         ap_kind="disk", diam_m=25.0, decorrelation=1,
         sigma_pt_arcsec=20.0, noise_jy=1e-3, n_interval=4),
 }
+
+
+# ---------------------------------------------------------------- mixed batches
+
+# Array types of the batched-solve workload: 16 channels over 1.3-1.5 GHz,
+# 10 s samples; per type a layout, dish, sky and grid.  Pixel size about
+# 1 / (2.2 u_max), the image covering about 1.5 primary-beam widths.
+MIXED_ARRAYS = {
+    "y27": dict(layout="y", n_ant=27, extent_m=1000.0, diam_m=25.0, n_img=256, cell_arcsec=11.0, pad=4,
+                n_src=50, src_radius_arcmin=15.0),
+    "disk64": dict(layout="disk", n_ant=64, extent_m=4000.0, diam_m=13.5, n_img=2048, cell_arcsec=2.5, pad=4,
+                   n_src=200, src_radius_arcmin=30.0),
+    "disk197": dict(layout="disk", n_ant=197, extent_m=8000.0, diam_m=15.0, n_img=4096, cell_arcsec=1.2, pad=2,
+                    n_src=400, src_radius_arcmin=27.0),
+}
+MIXED_COMMON = dict(lat_deg=34.0, dec_deg=30.0, dt_s=10.0, n_chan=16, f_lo=1.3e9, f_hi=1.5e9, support=32,
+                    oversample=20, ap_kind="disk", decorrelation=1, noise_jy=1e-3,
+                    flux=("powerlaw", 1e-4, 1.0, -1.5))
+
+
+@dataclasses.dataclass
+class MixedArray:
+    """One array type of a mixed batch: geometry, channels, sky and grid."""
+    name: str
+    enu_m: np.ndarray
+    freq_hz: np.ndarray
+    sky: np.ndarray
+    image: np.ndarray
+    cell_rad: float
+    n_grid: int
+    support: int
+    oversample: int
+    ap_kind: str
+    diam_m: float
+    alpha_per_dlambda: float
+    decorrelation: int
+    sigma_noise: float
+    lat_rad: float
+    dec_rad: float
+
+    @property
+    def n_ant(self):
+        return self.enu_m.shape[0]
+
+    @property
+    def n_bl(self):
+        return self.n_ant * (self.n_ant - 1) // 2
+
+
+@dataclasses.dataclass
+class MixedInterval:
+    """One solution interval of a mixed batch."""
+    array: str
+    hour_angles: np.ndarray    # [n_time] rad
+    lm_true: np.ndarray        # [n_ant][2] rad
+    sigma_pt: float            # rad
+    outliers: np.ndarray       # antennas whose offset is an outlier
+    noise_seed: int
+
+    @property
+    def n_time(self):
+        return self.hour_angles.shape[0]
+
+
+def mixed_arrays(seed: int = 0, names=("y27", "disk64", "disk197")) -> dict:
+    out = {}
+    c = MIXED_COMMON
+    nc = c["n_chan"]
+    freq = c["f_lo"] + (np.arange(nc) + 0.5) * (c["f_hi"] - c["f_lo"]) / nc
+    for k, name in enumerate(names):
+        a = MIXED_ARRAYS[name]
+        s = seed * 7 + k
+        enu = y_layout(a["n_ant"], a["extent_m"], s) if a["layout"] == "y" else disk_layout(a["n_ant"], a["extent_m"], s)
+        cell = a["cell_arcsec"] * ARCSEC
+        sky = sky_points(a["n_src"], a["src_radius_arcmin"] * ARCMIN, a["n_img"], cell, c["flux"], s)
+        out[name] = MixedArray(
+            name=name, enu_m=enu, freq_hz=freq.astype(np.float64), sky=sky, image=sky_image(sky, a["n_img"], cell),
+            cell_rad=cell, n_grid=a["n_img"] * a["pad"], support=c["support"], oversample=c["oversample"],
+            ap_kind=c["ap_kind"], diam_m=a["diam_m"], alpha_per_dlambda=ALPHA_PER_DLAMBDA_DISK,
+            decorrelation=c["decorrelation"], sigma_noise=c["noise_jy"], lat_rad=c["lat_deg"] * DEG,
+            dec_rad=c["dec_deg"] * DEG)
+    return out
+
+
+def mixed_intervals(arrays: dict, n_intervals: int = 256, seed: int = 0, t_range=(30, 600),
+                    sigma_range_arcsec=(10.0, 60.0), outlier_frac: float = 0.05,
+                    outlier_arcsec: float = 120.0) -> list:
+    """Intervals of uneven length on arrays drawn uniformly from ``arrays``:
+    n_time ~ U{t_range}, a start hour angle U(-4 h, 4 h - length), offsets
+    Gaussian with sigma ~ U(sigma_range) per interval, and each antenna with
+    probability ``outlier_frac`` an outlier of ``outlier_arcsec`` in a random
+    direction instead."""
+    rng = _rng(seed, 50)
+    names = list(arrays)
+    dt = MIXED_COMMON["dt_s"]
+    out = []
+    for k in range(n_intervals):
+        name = names[int(rng.integers(len(names)))]
+        n_ant = arrays[name].n_ant
+        nt = int(rng.integers(t_range[0], t_range[1] + 1))
+        span_h = nt * dt / 3600.0
+        h0 = rng.uniform(-4.0, 4.0 - span_h)
+        ha = (h0 + np.arange(nt) * dt / 3600.0) * 15.0 * DEG
+        sig = rng.uniform(*sigma_range_arcsec) * ARCSEC
+        lm = rng.normal(0.0, sig, (n_ant, 2))
+        out_mask = rng.uniform(0.0, 1.0, n_ant) < outlier_frac
+        th = rng.uniform(0.0, 2.0 * math.pi, n_ant)
+        lm[out_mask, 0] = outlier_arcsec * ARCSEC * np.cos(th[out_mask])
+        lm[out_mask, 1] = outlier_arcsec * ARCSEC * np.sin(th[out_mask])
+        out.append(MixedInterval(array=name, hour_angles=ha, lm_true=lm, sigma_pt=sig,
+                                 outliers=np.nonzero(out_mask)[0], noise_seed=int(seed) * 100003 + k))
+    return out
+
+
+def mixed_uvw(arr: MixedArray, iv: MixedInterval) -> np.ndarray:
+    return uvw_tracks(arr.enu_m, arr.lat_rad, arr.dec_rad, iv.hour_angles)

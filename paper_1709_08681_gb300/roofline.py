@@ -1,0 +1,36 @@
+"""Algorithmic work of the fused evaluation, for roofline figures.
+
+Per visibility the fused kernel visits the grid cells inside the aperture's
+support, pi rho_max^2 of them (rho_max in cells: the radial table's reach,
+clipped to the S x S window), and per tap does FLOPS_PER_TAP FP32 flops:
+s = dx^2 + dy^2 (2), the square root (1), t = rho ov (1), the A° interpolation
+(2), P += A° G (4), A° dx (1), Q += (A° dx) G (4).  The bound is the FP32 ALU:
+SMs x 128 lanes x 2 flops (FMA) x clock.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+FLOPS_PER_TAP = 15
+FP32_LANES_PER_SM = 128
+C_LIGHT = 299_792_458.0
+
+
+def taps_per_channel(geom) -> np.ndarray:
+    """Non-zero taps per visibility for each channel of ``geom`` (any object
+    with n_grid, cell_rad, freq_hz, diam_m, ap_kind, support, oversample)."""
+    du = 1.0 / (geom.n_grid * geom.cell_rad)
+    out = []
+    for f in geom.freq_hz:
+        dl = geom.diam_m * f / C_LIGHT
+        rho = dl / du if geom.ap_kind == "disk" else 0.5 * geom.support * math.sqrt(2)
+        L = math.floor(geom.oversample * rho) + 2
+        r = (L - 1) / geom.oversample
+        out.append(min(math.pi * r * r, geom.support * geom.support))
+    return np.asarray(out)
+
+
+def fp32_peak_tflops(n_sm: int, clock_hz: float = 2.070e9) -> float:
+    return n_sm * FP32_LANES_PER_SM * 2 * clock_hz / 1e12

@@ -67,3 +67,65 @@ class Session:
         for c in self.ctxs:
             c.close()
         self.ctxs = []
+
+
+class MixedSession:
+    """Device-resident setup of a mixed batch (``inputs.mixed_arrays`` /
+    ``inputs.mixed_intervals``): one model grid per array type, and per
+    interval its own uvw upload, context and observed visibilities -- the GPU
+    predictor at the interval's true offsets plus thermal noise from a seeded
+    device generator (the data are too large to draw on the host)."""
+
+    def __init__(self, arrays: dict, intervals: list, device: str = "cuda:0", stream=None):
+        from . import inputs as I
+        self.arrays = arrays
+        self.intervals = intervals
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.grids = {}
+        for name, arr in arrays.items():
+            n_img = arr.image.shape[0]
+            img = torch.from_numpy(np.ascontiguousarray(arr.image, dtype=np.float32)).to(self.device)
+            g = torch.empty((arr.n_grid, arr.n_grid), dtype=torch.complex64, device=self.device)
+            _abi.psc_model_grid(n_img, arr.n_grid, arr.cell_rad, arr.support, arr.oversample, img, g, self.stream)
+            self.grids[name] = g
+            del img
+        self.uvw, self.ctxs = [], []
+        for iv in intervals:
+            arr = arrays[iv.array]
+            u = torch.from_numpy(I.mixed_uvw(arr, iv)).to(self.device)
+            self.uvw.append(u)
+            self.ctxs.append(_abi.Context(
+                arr.n_ant, iv.n_time, len(arr.freq_hz), u, arr.freq_hz, arr.ap_kind, arr.diam_m,
+                arr.alpha_per_dlambda, arr.decorrelation, arr.image.shape[0], arr.n_grid, arr.cell_rad,
+                arr.support, arr.oversample, self.grids[iv.array], self.stream))
+
+    def shape(self, k):
+        iv = self.intervals[k]
+        arr = self.arrays[iv.array]
+        return (iv.n_time, arr.n_bl, len(arr.freq_hz))
+
+    def n_vis(self, k=None):
+        if k is None:
+            return sum(self.n_vis(j) for j in range(len(self.intervals)))
+        s = self.shape(k)
+        return s[0] * s[1] * s[2]
+
+    def simulate(self, noise: bool = True):
+        """Observed visibilities of every interval (list of device tensors)."""
+        out = []
+        for k, iv in enumerate(self.intervals):
+            v = torch.empty(self.shape(k), dtype=torch.complex64, device=self.device)
+            self.ctxs[k].psc_predict(iv.lm_true, v)
+            if noise:
+                g = torch.Generator(device=self.device)
+                g.manual_seed(iv.noise_seed)
+                sig = self.arrays[iv.array].sigma_noise
+                v += torch.view_as_complex(torch.randn(v.shape + (2,), generator=g, device=self.device) * sig)
+            out.append(v)
+        return out
+
+    def close(self):
+        for c in self.ctxs:
+            c.close()
+        self.ctxs = []

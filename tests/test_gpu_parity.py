@@ -143,6 +143,29 @@ def test_unstaged_fallback_matches_oracle():
     assert max(_rel(dVg[p], dV[p]) for p in range(4)) < TOL_V
 
 
+@pytest.mark.parametrize("kv", [1, 2])
+def test_never_staged_matches_oracle(kv):
+    """PSC_STAGE_NEVER: every tap reads the grid from global memory, with the
+    cell half of the ramp from the block's tables; includes visibilities whose
+    windows reach past the grid edge (cells outside contribute nothing)."""
+    m, _, lmt, img = cases.problem(cases.DISK_SMALL, n_ant=6, n_time=41, freqs=(1.3e9, 1.4e9), sigma_arcsec=30.0,
+                                   extent_m=1200.0)
+    V, dV = psc.predict(m, lmt)
+    gp = GpuProblem(m, img, t_tile=16, c_group=2, kv=kv)
+    gp.ctx.psc_set_staging(_abi.PSC_STAGE_NEVER)
+    Vg, dVg = gp.predict(lmt)
+    assert _rel(Vg, V) < TOL_V
+    assert max(_rel(dVg[p], dV[p]) for p in range(4)) < TOL_V
+    vobs, w = _obs(m, lmt)
+    chi2, g, H, X = psc.chi2_grad_normal(m, 0.5 * lmt, vobs, w)
+    chi2g, gg, Hg, Xg = gp.ctx.psc_residual_grad(0.5 * lmt, gp.upload(vobs), gp.upload(w, torch.float32), 1.0,
+                                                 cross=True)
+    assert abs(chi2g - chi2) < TOL_V * chi2
+    assert np.max(np.abs(Hg - H)) < TOL_V * np.max(np.abs(H))
+    with pytest.raises(_abi.PscError):
+        gp.ctx.psc_set_staging(2)
+
+
 def test_zero_offset_invariant_bitwise():
     """At zero offsets the decorrelation factor is one: both settings agree bit for bit."""
     m, _, _, img = cases.problem(cases.DISK_SMALL, n_ant=6, n_time=12)
