@@ -54,7 +54,7 @@ def parse():
     p.add_argument("--no-learned", action="store_true", help="skip the learned-initialiser comparison")
     p.add_argument("--mixed-intervals", type=int, default=256,
                    help="intervals of the mixed-array batched-solve section (0 skips it)")
-    p.add_argument("--learned-train", type=int, default=1000, help="training intervals of the learned initialiser")
+    p.add_argument("--learned-train", type=int, default=3000, help="training intervals of the learned initialiser")
     p.add_argument("--learned-eval", type=int, default=20, help="held-out intervals of the comparison")
     return p.parse_args()
 
@@ -378,8 +378,8 @@ def run_ours(args):
         # 64-antenna 16-channel workload (network trained here on GPU-simulated
         # intervals with the library's kernels; sizes reduced to fit the bench)
         from paper_1709_08681_gb300 import learned_init as LI
-        rep, _ = LI.run(n_train=args.learned_train, n_eval=args.learned_eval, steps=1500, batch=1024, n_geom=8,
-                        seed=args.seed, log=None)
+        rep, _ = LI.run(n_train=args.learned_train, n_eval=args.learned_eval, steps=3000, batch=1024, n_geom=8,
+                        seed=args.seed, log=None, n_eval_batched=64)
         line["learned_init"] = {"workload": "disk64_l16ch", **rep}
     if rank == 0 and args.mixed_intervals > 0:
         # batched solves over mixed intervals: 27/64/197-antenna arrays,

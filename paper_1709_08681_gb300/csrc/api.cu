@@ -604,8 +604,12 @@ psc_status psc_features(psc_ctx *ctx, const void *vis_obs, const float *w, doubl
     if (!(w_scale > 0.0) || !std::isfinite(w_scale)) return fail(ctx, PSC_ERR_ARG, "w_scale must be > 0");
     if (!(sigma_prior_rad > 0.0) || !std::isfinite(sigma_prior_rad)) return fail(ctx, PSC_ERR_ARG, "sigma_prior must be > 0");
     if (time_stride < 1) return fail(ctx, PSC_ERR_ARG, "time_stride must be >= 1");
-    const int t_tile = 32, c_group = 4;
+    // brick shape: every kept time step of up to 32 in one tile, and as many
+    // channels as fill 128 threads (few kept steps would otherwise leave most
+    // lanes of a 32-step tile idle)
     const int nts = (ctx->nt + time_stride - 1) / time_stride;
+    const int t_tile = std::min(32, nts);
+    const int c_group = std::min(std::min(8, ctx->nc), std::max(1, 128 / t_tile));
     StencilArgs a{};
     a.uvw = ctx->uvw;
     a.grid = ctx->grid;
@@ -628,6 +632,9 @@ psc_status psc_features(psc_ctx *ctx, const void *vis_obs, const float *w, doubl
     a.time_stride = time_stride;
     a.decorrelation = ctx->ap.decorrelation;
     a.max_tab_len = ctx->max_tab_len;
+    // a 64 x 64 staged tile pays only for bricks of many visibilities; small
+    // bricks read the grid directly and keep shared memory (and occupancy) free
+    a.stage = t_tile * c_group >= 64;
     a.n_bricks = (long long)ctx->n_bl * a.n_cg * a.n_tt;
     a.sigma = (float)sigma_prior_rad;
     const size_t need = (size_t)a.n_bricks * 56;

@@ -43,8 +43,8 @@ __device__ __forceinline__ float2 lds_f2(unsigned addr) {
 }
 
 __global__ void __launch_bounds__(128) stencil_kernel(const StencilArgs a) {
-    extern __shared__ float2 s_tab[];
-    __shared__ float2 s_tile[kTile * kTile];
+    extern __shared__ float2 s_tab[];                 // tables, then the staged tile when a.stage
+    float2 *s_tile = s_tab + a.c_group * (a.max_tab_len + kTabPad);
     __shared__ int s_box[4];
     __shared__ double s_red[4][kSRed];
 
@@ -74,30 +74,37 @@ __global__ void __launch_bounds__(128) stencil_kernel(const StencilArgs a) {
         fy = (float)(y - fly);
         ix0 = (int)flx - a.support / 2 + 1;
         iy0 = (int)fly - a.support / 2 + 1;
-        atomicMin(&s_box[0], ix0); atomicMax(&s_box[1], ix0);
-        atomicMin(&s_box[2], iy0); atomicMax(&s_box[3], iy0);
-    }
-    for (int k = tid; k < a.c_group * tab_stride; k += blockDim.x) {
-        const int cc = cgi * a.c_group + k / tab_stride;
-        const int n = k % tab_stride;
-        float2 v = make_float2(0.f, 0.f);
-        if (cc < a.nc) {
-            const ChanConst ch = a.chan[cc];
-            if (n < ch.tab_len) v = a.tabs[ch.tab_off + n];
+        // staged box: the cells within rho_max of the visibility, inside its window
+        const float rm = a.chan[c].rho_max;
+        const float hx0 = fx + (float)(a.support / 2 - 1), hy0 = fy + (float)(a.support / 2 - 1);
+        const int lox = ix0 + max(0, (int)floorf(hx0 - rm) + 1);
+        const int hix = ix0 + min(a.support - 1, (int)ceilf(hx0 + rm) - 1);
+        const int loy = iy0 + max(0, (int)floorf(hy0 - rm) + 1);
+        const int hiy = iy0 + min(a.support - 1, (int)ceilf(hy0 + rm) - 1);
+        if (lox <= hix && loy <= hiy) {
+            atomicMin(&s_box[0], lox); atomicMax(&s_box[1], hix);
+            atomicMin(&s_box[2], loy); atomicMax(&s_box[3], hiy);
         }
-        s_tab[k] = v;
+    }
+    for (int j = 0; j < a.c_group; ++j) {
+        const int cc = cgi * a.c_group + j;
+        const int off = cc < a.nc ? a.chan[cc].tab_off : 0;
+        const int len = cc < a.nc ? a.chan[cc].tab_len : 0;
+        for (int n = tid; n < tab_stride; n += blockDim.x)
+            s_tab[j * tab_stride + n] = n < len ? a.tabs[off + n] : make_float2(0.f, 0.f);
     }
     __syncthreads();
-    const int bx0 = s_box[0], by0 = s_box[2];
-    const int ex = s_box[1] - bx0 + a.support, ey = s_box[3] - by0 + a.support;
-    const bool staged = ex <= kTile && ey <= kTile;
-    if (staged) {
+    const bool empty = s_box[0] > s_box[1];
+    const int bx0 = empty ? 0 : s_box[0], by0 = empty ? 0 : s_box[2];
+    const int ex = empty ? 0 : s_box[1] - bx0 + 1, ey = empty ? 0 : s_box[3] - by0 + 1;
+    const bool staged = a.stage && ex <= kTile && ey <= kTile;
+    if (staged && !empty) {
         const int cshift = blockDim.x >= kTile ? 6 : 5;
         const int cols = 1 << cshift;
         const int rstep = blockDim.x >> cshift;
-        for (int xx = tid & (cols - 1); xx < kTile; xx += cols) {
+        for (int xx = tid & (cols - 1); xx < ex; xx += cols) {
             const int gx = bx0 + xx;
-            const bool xin = xx < ex && gx >= 0 && gx < a.ng;
+            const bool xin = gx >= 0 && gx < a.ng;
             for (int yy = tid >> cshift; yy < ey; yy += rstep) {
                 const int gy = by0 + yy;
                 float2 g = make_float2(0.f, 0.f);
@@ -130,7 +137,7 @@ __global__ void __launch_bounds__(128) stencil_kernel(const StencilArgs a) {
             const float dy = hy - (float)b;
             const float rem = rmax2 - dy * dy;
             if (!(rem > 0.f)) continue;
-            const float r = rem * rsqrt_fast(rem);
+            const float r = fminf(rem * rsqrt_fast(rem), rmax);     // keeps the span inside the staged box
             const int a_lo = max(0, (int)floorf(hx - r) + 1);
             const int a_hi = min(a.support - 1, (int)ceilf(hx + r) - 1);
             const float dyo = dy * ov;
@@ -241,82 +248,85 @@ __global__ void __launch_bounds__(128) stencil_kernel(const StencilArgs a) {
         for (int k = 0; k < kSRed; ++k) s_red[warp][k] = (double)acc[k];
     }
     __syncthreads();
-    if (tid < kSRed) {
+    // kSRed sums may outnumber the threads of a small block
+    const int nw = (blockDim.x + 31) >> 5;
+    for (int k = tid; k < kSRed; k += blockDim.x) {
         double sum = 0.0;
-        const int nw = (blockDim.x + 31) >> 5;
-        for (int wi = 0; wi < nw; ++wi) sum += s_red[wi][tid];
-        a.partials[(size_t)tid * a.n_bricks + brick] = sum;
+        for (int wi = 0; wi < nw; ++wi) sum += s_red[wi][k];
+        a.partials[(size_t)k * a.n_bricks + brick] = sum;
     }
 }
 
-// Per-baseline sums of the stencil partials, one warp per baseline.
+// Per-baseline sums of the stencil partials: one thread per (sum, baseline),
+// bricks added in order (deterministic).
 __global__ void stencil_bl_kernel(const double *__restrict__ partials, int n_bl, int bpb, double *__restrict__ blsum) {
-    const int bl = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (bl >= n_bl) return;
+    const long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (id >= (long long)n_bl * kSRed) return;
+    const int k = (int)(id / n_bl), bl = (int)(id % n_bl);
     const size_t nb = (size_t)n_bl * bpb;
-    for (int k = 0; k < kSRed; ++k) {
-        const double *p = partials + (size_t)k * nb + (size_t)bl * bpb;
-        double s = 0.0;
-        for (int b = lane; b < bpb; b += 32) s += p[b];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) blsum[(size_t)bl * kSRed + k] = s;
-    }
+    const double *p = partials + (size_t)k * nb + (size_t)bl * bpb;
+    double sum = 0.0;
+    for (int b = 0; b < bpb; ++b) sum += p[b];
+    blsum[(size_t)bl * kSRed + k] = sum;
 }
 
-// Features per antenna (thread per antenna): sums over its baselines, then
-// the block Newton step and the stencil ratios.
+// Features of one antenna per block: thread k < kSRed sums value k over the
+// antenna's baselines (partners in increasing order), then the block Newton
+// step and the 25 stencil ratios and chi^2 changes.
 __global__ void features_kernel(const double *__restrict__ blsum, int n_ant, float sigma, float *__restrict__ feat) {
-    for (int an = blockIdx.x * blockDim.x + threadIdx.x; an < n_ant; an += gridDim.x * blockDim.x) {
-        double X[25], Y[25], Z = 0.0, g0 = 0.0, g1 = 0.0, H[3] = {0.0, 0.0, 0.0};
-        for (int s = 0; s < 25; ++s) { X[s] = 0.0; Y[s] = 0.0; }
+    __shared__ double v[kSRed];
+    const int an = blockIdx.x;
+    const int k = threadIdx.x;
+    if (k < kSRed) {
+        double sum = 0.0;
         for (int o = 0; o < n_ant; ++o) {
             if (o == an) continue;
             const int i = min(an, o), j = max(an, o);
             const int bl = i * (2 * n_ant - i - 1) / 2 + (j - i - 1);
-            const double *b = blsum + (size_t)bl * kSRed;
-            for (int s = 0; s < 25; ++s) { X[s] += b[s]; Y[s] += b[25 + s]; }
-            Z += b[50];
-            g0 += b[51]; g1 += b[52];
-            H[0] += b[53]; H[1] += b[54]; H[2] += b[55];
+            sum += blsum[(size_t)bl * kSRed + k];
         }
-        const double det = H[0] * H[2] - H[1] * H[1];
+        v[k] = sum;
+    }
+    __syncthreads();
+    float *f = feat + (size_t)an * 52;
+    const double *X = v, *Y = v + 25;
+    const double Z = v[50], g0 = v[51], g1 = v[52], H0 = v[53], H1 = v[54], H2 = v[55];
+    if (k == 0) {
+        const double det = H0 * H2 - H1 * H1;
         float s0 = 0.f, s1 = 0.f;
-        if (det > 0.0 && H[0] > 0.0) {
-            s0 = (float)(-(H[2] * g0 - H[1] * g1) / det / sigma);
-            s1 = (float)(-(-H[1] * g0 + H[0] * g1) / det / sigma);
+        if (det > 0.0 && H0 > 0.0) {
+            s0 = (float)(-(H2 * g0 - H1 * g1) / det / sigma);
+            s1 = (float)(-(-H1 * g0 + H0 * g1) / det / sigma);
         }
-        float *f = feat + (size_t)an * 52;
         f[0] = s0;
         f[1] = s1;
+    }
+    if (k < 25) {
         const double chi0 = Z - 2.0 * X[12] + Y[12];
-        for (int s = 0; s < 25; ++s) {
-            f[2 + s] = Y[s] > 0.0 ? (float)(X[s] / Y[s]) : 0.f;
-            f[27 + s] = Y[12] > 0.0 ? (float)((Z - 2.0 * X[s] + Y[s] - chi0) / Y[12]) : 0.f;
-        }
+        f[2 + k] = Y[k] > 0.0 ? (float)(X[k] / Y[k]) : 0.f;
+        f[27 + k] = Y[12] > 0.0 ? (float)((Z - 2.0 * X[k] + Y[k] - chi0) / Y[12]) : 0.f;
     }
 }
 
 }  // namespace
 
-size_t stencil_dyn_smem(int c_group, int max_tab_len) {
-    return sizeof(float2) * (size_t)c_group * (max_tab_len + kTabPad);
+size_t stencil_dyn_smem(int c_group, int max_tab_len, int stage) {
+    return sizeof(float2) * ((size_t)c_group * (max_tab_len + kTabPad) + (stage ? (size_t)kTile * kTile : 0));
 }
 
 cudaError_t launch_features(const StencilArgs &a, double *blsum, int n_ant, float *feat, cudaStream_t s) {
-    const size_t dyn = stencil_dyn_smem(a.c_group, a.max_tab_len);
+    const size_t dyn = stencil_dyn_smem(a.c_group, a.max_tab_len, a.stage);
     cudaError_t e = cudaFuncSetAttribute(stencil_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)(dyn > 48 * 1024 ? dyn : 48 * 1024));
     if (e != cudaSuccess) return e;
-    stencil_kernel<<<(int)a.n_bricks, a.t_tile * a.c_group, dyn, s>>>(a);
+    stencil_kernel<<<(int)a.n_bricks, (a.t_tile * a.c_group + 31) / 32 * 32, dyn, s>>>(a);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const int wpb = 8;
-    stencil_bl_kernel<<<(a.n_bl + wpb - 1) / wpb, 32 * wpb, 0, s>>>(a.partials, a.n_bl, a.n_cg * a.n_tt, blsum);
+    const long long n_sum = (long long)a.n_bl * kSRed;
+    stencil_bl_kernel<<<(int)((n_sum + 255) / 256), 256, 0, s>>>(a.partials, a.n_bl, a.n_cg * a.n_tt, blsum);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    features_kernel<<<(n_ant + 127) / 128, 128, 0, s>>>(blsum, n_ant, a.sigma, feat);
+    features_kernel<<<n_ant, 64, 0, s>>>(blsum, n_ant, a.sigma, feat);
     return cudaGetLastError();
 }
 

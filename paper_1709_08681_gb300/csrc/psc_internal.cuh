@@ -66,6 +66,7 @@ struct StencilArgs {
     int t_tile, c_group, n_tt, n_cg, time_stride;   // n_tt counts the kept (strided) time steps
     int decorrelation;
     int max_tab_len;
+    int stage;                 // 1: stage the grid cells of a brick in shared memory when they fit
     long long n_bricks;
     float sigma;               // stencil spacing (rad)
 };

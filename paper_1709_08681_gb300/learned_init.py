@@ -72,7 +72,7 @@ class Simulator:
             s.close()
 
 
-def make_dataset(sim: Simulator, n_intervals: int, time_stride: int = 4):
+def make_dataset(sim: Simulator, n_intervals: int, time_stride: int = 15):
     X = torch.empty((n_intervals * sim.n_ant, N_FEAT), dtype=torch.float32, device="cuda")
     T = torch.empty((n_intervals * sim.n_ant, 2), dtype=torch.float32, device="cuda")
     for i in range(n_intervals):
@@ -145,7 +145,7 @@ def _iterations_to(ctx, vis, w_scale, lm0, truth, target_arcsec, max_iter):
     return None
 
 
-def evaluate(sim: Simulator, net: "_abi.Mlp", n_eval: int, time_stride=4, target_arcsec=1.0, max_iter=20):
+def evaluate(sim: Simulator, net: "_abi.Mlp", n_eval: int, time_stride=15, target_arcsec=1.0, max_iter=20):
     """Per-interval iterations to the target from zero and from the network,
     and the measured times of one LM iteration and of the learned estimate."""
     plain_it, learned_it, init_rms = [], [], []
@@ -202,15 +202,119 @@ def evaluate(sim: Simulator, net: "_abi.Mlp", n_eval: int, time_stride=4, target
     }
 
 
-def run(n_train=2000, n_eval=50, steps=2000, batch=1024, lr=1e-3, n_geom=8, seed=0, time_stride=4, log=print):
-    """Simulate, train and evaluate; returns (report dict, trained params)."""
+def _batch_rms_trace(batch, lm0, truth, max_iter):
+    """Per-interval RMS error (arcsec) after 0..max_iter batched LM
+    iterations from lm0; [max_iter + 1][n]."""
+    opts = _abi.psc_solve_opts_default()
+    batch.psc_batch_begin(lm0, opts)
+    trace = [[_rms_arcsec(a, b) for a, b in zip(lm0, truth)]]
+    batch.psc_batch_iterate(1)                       # evaluation at the start, first step proposed
+    for _ in range(max_iter):
+        batch.psc_batch_iterate(1)                   # evaluates the trial, accepts or rejects
+        lm, _ = batch.psc_batch_end()
+        trace.append([_rms_arcsec(a, b) for a, b in zip(lm, truth)])
+    return np.asarray(trace)
+
+
+def evaluate_batched(sim: Simulator, net: "_abi.Mlp", n_eval: int, time_stride=15, target_arcsec=1.0,
+                     max_iter=10, reps=5):
+    """The held-out intervals solved as one batch (one persistent launch per
+    LM iteration over all of them), from zero and from the network's
+    estimate.  Iterations to the target: the first batched iteration after
+    which every interval is within target_arcsec RMS of its truth.  Times
+    (CUDA events on the stream): a batched iteration, and the learned
+    estimate of all intervals (features of each, then one network forward
+    over all their antennas)."""
+    stream = sim.stream
+    draws = [sim.draw() for _ in range(n_eval)]
+    # one context per interval (a batch holds each context once); they borrow
+    # the geometry's uvw and the shared grid
+    ctxs = []
+    for k, vis, lm in draws:
+        s = sim.sessions[k]
+        wl = s.wl
+        g = s.grid_args
+        ctxs.append(_abi.Context(wl.n_ant, wl.n_time, wl.n_chan, s.uvw, wl.freq_hz, wl.ap_kind, wl.diam_m,
+                                 wl.alpha_per_dlambda, wl.decorrelation, g["n_img"], g["n_grid"], g["cell_rad"],
+                                 g["support"], g["oversample"], s.grid, stream))
+    vis = [d[1] for d in draws]
+    truth = [d[2] for d in draws]
+    n_ant = sim.n_ant
+    feats = torch.empty((n_eval * n_ant, N_FEAT), dtype=torch.float32, device=vis[0].device)
+    y = torch.empty((n_eval * n_ant, 2), dtype=torch.float32, device=vis[0].device)
+
+    def learned_estimate():
+        for j, c in enumerate(ctxs):
+            c.psc_features(vis[j], None, sim.w_scale, SIGMA_PRIOR, time_stride, out=feats[j * n_ant:(j + 1) * n_ant])
+        net.psc_mlp_forward(feats, out=y)
+
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    learned_estimate()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        learned_estimate()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_init = e0.elapsed_time(e1) / reps / 1e3
+    lm_init = [(y[j * n_ant:(j + 1) * n_ant].double().cpu().numpy() * SIGMA_PRIOR) for j in range(n_eval)]
+    w_scale = [sim.w_scale] * n_eval
+    batch = _abi.Batch(ctxs, vis, None, w_scale=w_scale, stream=stream)
+    batch.psc_batch_autotune()
+    zeros = [np.zeros_like(t) for t in truth]
+    plain = _batch_rms_trace(batch, zeros, truth, max_iter)
+    learned = _batch_rms_trace(batch, lm_init, truth, max_iter)
+    # batched iteration time (graph replay), event-timed
+    batch.psc_batch_begin(zeros)
+    batch.psc_batch_iterate(2)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        batch.psc_batch_restart()
+        batch.psc_batch_iterate(1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_iter = e0.elapsed_time(e1) / reps / 1e3
+    batch.close()
+    for c in ctxs:
+        c.close()
+
+    def first_all(trace):
+        ok = np.nonzero(np.all(trace <= target_arcsec, axis=1))[0]
+        return int(ok[0]) if len(ok) else None
+
+    def mean_first(trace):
+        it = [np.nonzero(trace[:, j] <= target_arcsec)[0] for j in range(trace.shape[1])]
+        return float(np.mean([x[0] if len(x) else np.nan for x in it]))
+
+    kp, kl = first_all(plain), first_all(learned)
+    # time to the target: the start evaluation plus k iterations (none if the
+    # start already meets it); the learned arm adds its estimate
+    tp = (kp + 1) * t_iter if kp is not None and kp > 0 else (0.0 if kp == 0 else None)
+    tl = (t_init + ((kl + 1) * t_iter if kl > 0 else 0.0)) if kl is not None else None
+    return {
+        "n_eval": n_eval, "batched": True,
+        "plain_iters_all": kp, "learned_iters_all": kl,
+        "plain_mean_iters": mean_first(plain), "learned_mean_iters": mean_first(learned),
+        "learned_init_rms_arcsec": float(np.median(learned[0])),
+        "t_batch_iter_ms": 1e3 * t_iter, "t_learned_init_ms": 1e3 * t_init,
+        "plain_intervals_per_s": n_eval / tp if tp else None,
+        "learned_intervals_per_s": n_eval / tl if tl else None,
+        "target_arcsec": target_arcsec,
+    }
+
+
+def run(n_train=2000, n_eval=50, steps=2000, batch=1024, lr=1e-3, n_geom=8, seed=0, time_stride=15, log=print,
+        n_eval_batched=0):
+    """Simulate, train and evaluate (per interval, and as one batch of
+    n_eval_batched held-out intervals if > 0); returns (report, params)."""
     stream = torch.cuda.current_stream()
     sim = Simulator(n_geom=n_geom, seed=seed, stream=stream)
     t = time.perf_counter()
     X, T = make_dataset(sim, n_train, time_stride)
     torch.cuda.synchronize()
     t_data = time.perf_counter() - t
-    net = _abi.Mlp(max(batch, sim.n_ant), stream=stream)
+    net = _abi.Mlp(max(batch, sim.n_ant, n_eval_batched * sim.n_ant), stream=stream)
     net.psc_mlp_set_params(init_params(X, seed))
     t = time.perf_counter()
     losses = train(net, X, T, steps=steps, batch=batch, lr=lr, seed=seed, log_every=max(1, steps // 10))
@@ -220,6 +324,8 @@ def run(n_train=2000, n_eval=50, steps=2000, batch=1024, lr=1e-3, n_geom=8, seed
         log("train losses: " + ", ".join("%d:%.4f" % x for x in losses))
     # held-out evaluation draws continue the same seeded stream
     rep = evaluate(sim, net, n_eval, time_stride)
+    if n_eval_batched > 0:
+        rep["batched"] = evaluate_batched(sim, net, n_eval_batched, time_stride)
     rep.update({"n_train_intervals": n_train, "n_train_samples": int(X.shape[0]), "train_steps": steps,
                 "batch": batch, "t_simulate_s": t_data, "t_train_s": t_train,
                 "final_train_loss": losses[-1][1] if losses else None})

@@ -32,8 +32,12 @@ def test_learned_init_is_consistent_with_features_and_network():
 
 
 def test_trained_network_beats_the_zero_start():
-    rep, params = LI.run(n_train=150, n_eval=6, steps=300, batch=512, n_geom=2, seed=1, log=None)
+    rep, params = LI.run(n_train=150, n_eval=6, steps=300, batch=512, n_geom=2, seed=1, log=None, n_eval_batched=4)
     assert rep["final_train_loss"] < 1.0                       # targets have unit variance
     assert rep["learned_init_rms_arcsec"] < 0.8 * 30.0
     assert rep["plain_reached"] == rep["n_eval"]
     assert np.all(np.isfinite(params))
+    b = rep["batched"]
+    assert b["plain_iters_all"] is not None and b["learned_iters_all"] is not None
+    assert b["learned_init_rms_arcsec"] < 0.8 * 30.0
+    assert b["t_batch_iter_ms"] > 0 and b["t_learned_init_ms"] > 0
