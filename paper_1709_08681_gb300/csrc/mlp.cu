@@ -9,11 +9,13 @@
 //
 // Precision: FP32 master weights and AdamW state; every GEMM operand is
 // bfloat16 (weights, standardised input, GELU outputs, output gradients),
-// multiplied on the tensor cores with FP32 accumulation (mma.sync m16n8k16);
-// biases, GELU, its derivative and the optimiser are FP32.
+// multiplied on the 5th-generation tensor cores (tcgen05.mma, FP32
+// accumulator in tensor memory); biases, GELU, its derivative and the
+// optimiser are FP32.
 #include <cuda_bf16.h>
 
 #include <cmath>
+#include <cstdint>
 #include <string>
 #include <vector>
 
@@ -45,7 +47,9 @@ struct GemmArgs {
     int gelu;
 };
 
-constexpr int kGM = 64, kGN = 64, kGK = 32, kPadK = kGK + 8;
+// Tile of one block: kGM x kGN outputs, K in chunks of kGK, two chunk buffers.
+constexpr int kGM = 128, kGN = 64, kGK = 32;
+constexpr long kWaitLimit = 1L << 24;       // mbarrier polls before a GEMM gives up (sets *err)
 
 __device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
 
@@ -53,79 +57,143 @@ __device__ __forceinline__ float gelu_grad_f(float z) {
     return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * expf(-0.5f * z * z) * 0.3989422804014327f;
 }
 
-__global__ void __launch_bounds__(128) gemm_bf16_kernel(const GemmArgs g) {
-    __shared__ __align__(16) bf16 As[kGM][kPadK];
-    __shared__ __align__(16) bf16 Bs[kGN][kPadK];      // Bs[n][k]
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int wm = warp >> 1, wn = warp & 1;           // 2 x 2 warps, 32 x 32 each
-    const int gid = lane >> 2, tig = lane & 3;
+// Shared-memory matrix descriptor of tcgen05.mma for a K-major operand in the
+// no-swizzle core-matrix layout: core matrices of 8 rows x 16 bytes, those
+// adjacent along K `lbo` bytes apart, those adjacent along M/N `sbo` bytes
+// apart (descriptor version 1, layout type 0).
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+
+// Byte offset of element (r, k) of a rows x kGK chunk in that layout
+// (lbo = 128: the two 8-wide K halves of a 16-wide step are adjacent;
+// sbo = kGK / 8 * 128: one 8-row group holds all of the chunk's K).
+__device__ __forceinline__ uint32_t core_off(int r, int k) {
+    return (uint32_t)((r >> 3) * (kGK / 8 * 128) + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity) {
+    for (long it = 0; it < kWaitLimit; ++it) {
+        uint32_t ok;
+        asm volatile("{\n.reg .pred q;\nmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\nselp.u32 %0, 1, 0, q;\n}"
+                     : "=r"(ok) : "r"(addr), "r"(parity));
+        if (ok) return true;
+    }
+    return false;
+}
+
+// C = A B on the 5th-generation tensor cores: bfloat16 operands staged into
+// shared memory (any strides, zero-filled past M, N, K), tcgen05.mma with the
+// 128 x 64 FP32 accumulator in tensor memory (one elected thread issues the
+// MMAs and commits them to a chunk buffer's mbarrier), tcgen05.ld into
+// registers for the epilogue (bias, GELU, FP32 and bfloat16 stores).  Block
+// = 4 warps; warp w owns accumulator rows 32w..32w+31.  A chunk buffer is
+// restaged only after the MMAs that read it have completed.
+__global__ void __launch_bounds__(128) gemm_tc_kernel(const GemmArgs g, int *err) {
+    __shared__ __align__(128) bf16 sA[2][kGM * kGK];
+    __shared__ __align__(128) bf16 sB[2][kGN * kGK];
+    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ uint32_t tmem_base;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m0 = blockIdx.y * kGM, n0 = blockIdx.x * kGN;
-    float acc[2][4][4];
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.f;
+    const uint32_t mb0 = (uint32_t)__cvta_generic_to_shared(&mbar[0]);
+    const uint32_t mb1 = (uint32_t)__cvta_generic_to_shared(&mbar[1]);
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(mb0));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(mb1));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    if (warp == 0) {
+        const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&tmem_base);
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" :: "r"(dst), "r"(kGN));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = tmem_base;
+    // kind::f16 instruction descriptor: D FP32, A and B bfloat16, both K-major, N = kGN, M = kGM
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kGN >> 3) << 17) |
+                           ((uint32_t)(kGM >> 4) << 24);
     const bf16 zero = __float2bfloat16(0.f);
-    for (int k0 = 0; k0 < g.K; k0 += kGK) {
+    const int nk = (g.K + kGK - 1) / kGK;
+    bool ok = true;
+    for (int c = 0; c < nk && ok; ++c) {
+        const int b = c & 1;
+        if (c >= 2) ok = mbar_wait(b ? mb1 : mb0, (uint32_t)((c - 2) >> 1) & 1u);   // MMAs of chunk c-2 done
+        if (!ok) break;
+        const int k0 = c * kGK;
+        char *ab = reinterpret_cast<char *>(sA[b]);
+        char *bb = reinterpret_cast<char *>(sB[b]);
         for (int e = tid; e < kGM * kGK; e += blockDim.x) {
             const int mm = e / kGK, kk = e % kGK;
             const int m = m0 + mm, k = k0 + kk;
-            As[mm][kk] = (m < g.M && k < g.K) ? g.A[(long long)m * g.sam + (long long)k * g.sak] : zero;
+            *reinterpret_cast<bf16 *>(ab + core_off(mm, kk)) =
+                (m < g.M && k < g.K) ? g.A[(long long)m * g.sam + (long long)k * g.sak] : zero;
         }
         for (int e = tid; e < kGN * kGK; e += blockDim.x) {
             const int nn = e / kGK, kk = e % kGK;
             const int n = n0 + nn, k = k0 + kk;
-            Bs[nn][kk] = (n < g.N && k < g.K) ? g.B[(long long)k * g.sbk + (long long)n * g.sbn] : zero;
+            *reinterpret_cast<bf16 *>(bb + core_off(nn, kk)) =
+                (n < g.N && k < g.K) ? g.B[(long long)k * g.sbk + (long long)n * g.sbn] : zero;
         }
+        asm volatile("fence.proxy.async.shared::cta;");      // the stores above, visible to the tensor core
+        asm volatile("tcgen05.fence::before_thread_sync;");
         __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        if (tid == 0) {
+            const uint32_t a0 = (uint32_t)__cvta_generic_to_shared(sA[b]);
+            const uint32_t b0 = (uint32_t)__cvta_generic_to_shared(sB[b]);
 #pragma unroll
-        for (int ks = 0; ks < kGK; ks += 16) {
-            unsigned af[2][4], bfr[4][2];
-#pragma unroll
-            for (int mt = 0; mt < 2; ++mt) {
-                const int r = wm * 32 + mt * 16 + gid;
-                af[mt][0] = *reinterpret_cast<const unsigned *>(&As[r][ks + 2 * tig]);
-                af[mt][1] = *reinterpret_cast<const unsigned *>(&As[r + 8][ks + 2 * tig]);
-                af[mt][2] = *reinterpret_cast<const unsigned *>(&As[r][ks + 2 * tig + 8]);
-                af[mt][3] = *reinterpret_cast<const unsigned *>(&As[r + 8][ks + 2 * tig + 8]);
+            for (int kk = 0; kk < kGK / 16; ++kk) {
+                const uint64_t ad = smem_desc(a0 + 256u * kk, 128u, kGK / 8 * 128);
+                const uint64_t bd = smem_desc(b0 + 256u * kk, 128u, kGK / 8 * 128);
+                const uint32_t accum = (c > 0 || kk > 0) ? 1u : 0u;
+                asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                             "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}"
+                             :: "r"(tmem), "l"(ad), "l"(bd), "r"(idesc), "r"(accum));
             }
-#pragma unroll
-            for (int nt = 0; nt < 4; ++nt) {
-                const int c = wn * 32 + nt * 8 + gid;
-                bfr[nt][0] = *reinterpret_cast<const unsigned *>(&Bs[c][ks + 2 * tig]);
-                bfr[nt][1] = *reinterpret_cast<const unsigned *>(&Bs[c][ks + 2 * tig + 8]);
-            }
-#pragma unroll
-            for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-                for (int nt = 0; nt < 4; ++nt) {
-                    float *d = acc[mt][nt];
-                    asm volatile(
-                        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
-                        "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
-                        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-                        : "r"(af[mt][0]), "r"(af[mt][1]), "r"(af[mt][2]), "r"(af[mt][3]), "r"(bfr[nt][0]),
-                          "r"(bfr[nt][1]));
-                }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                         :: "r"(b ? mb1 : mb0));
         }
-        __syncthreads();
     }
+    // the last commit completes after every earlier MMA of this thread
+    if (ok && nk > 0) ok = mbar_wait(((nk - 1) & 1) ? mb1 : mb0, (uint32_t)((nk - 1) >> 1) & 1u);
+    if (!ok) {
+        if (tid == 0) atomicExch(err, 1);
+        // MMAs may still be in flight: wait once more (bounded) before freeing TMEM
+        if (nk > 0) mbar_wait(((nk - 1) & 1) ? mb1 : mb0, (uint32_t)((nk - 1) >> 1) & 1u);
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (ok) {
+        const int m = m0 + 32 * warp + lane;              // accumulator lane = output row
 #pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
+        for (int c0 = 0; c0 < kGN; c0 += 16) {
+            uint32_t r[16];
+            const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0;
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                           "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                           "=r"(r[14]), "=r"(r[15])
+                         : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;");
+            if (m < g.M) {
 #pragma unroll
-        for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                const int m = m0 + wm * 32 + mt * 16 + gid + (r >= 2 ? 8 : 0);
-                const int n = n0 + wn * 32 + nt * 8 + 2 * tig + (r & 1);
-                if (m >= g.M || n >= g.N) continue;
-                float v = acc[mt][nt][r];
-                if (g.bias) v += g.bias[n];
-                if (g.out) g.out[(long long)m * g.ldo + n] = v;
-                if (g.out_bf) g.out_bf[(long long)m * g.ldb + n] = __float2bfloat16(g.gelu ? gelu_f(v) : v);
+                for (int j = 0; j < 16; ++j) {
+                    const int n = n0 + c0 + j;
+                    if (n >= g.N) break;
+                    float v = __uint_as_float(r[j]);
+                    if (g.bias) v += g.bias[n];
+                    if (g.out) g.out[(long long)m * g.ldo + n] = v;
+                    if (g.out_bf) g.out_bf[(long long)m * g.ldb + n] = __float2bfloat16(g.gelu ? gelu_f(v) : v);
+                }
             }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(kGN));
 }
 
 // ------------------------------------------------------------------ small kernels
@@ -217,6 +285,7 @@ struct psc_mlp {
     float *dy = nullptr, *da = nullptr, *dz = nullptr;
     bf16 *dy_bf = nullptr, *dz_bf = nullptr;
     double *d_loss = nullptr;
+    int *d_err = nullptr;        // set by a GEMM whose tensor-core wait ran out
     long long step = 0;
     std::vector<float> host;
     std::string err;
@@ -240,17 +309,33 @@ psc_status mfail(psc_mlp *m, psc_status st, const std::string &msg) {
 template <class T>
 cudaError_t mall(T **p, size_t n) { return cudaMalloc((void **)p, sizeof(T) * (n ? n : 1)); }
 
+// After a synchronisation: PSC_ERR_TIMEOUT (and the flag cleared) if a GEMM
+// gave up waiting for its tensor-core work since the last check.
+psc_status check_device_err(psc_mlp *m) {
+    int h = 0;
+    cudaError_t e = cudaMemcpy(&h, m->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return mfail(m, PSC_ERR_CUDA, std::string("device error flag: ") + cudaGetErrorString(e));
+    if (h == 0) return PSC_OK;
+    cudaMemset(m->d_err, 0, sizeof(int));
+    return mfail(m, PSC_ERR_TIMEOUT, "a tensor-core GEMM timed out waiting for its MMAs");
+}
+
 void mfree(psc_mlp *m) {
     if (!m) return;
     void *ptrs[] = {m->p, m->g, m->m, m->v, m->w1, m->w2, m->w3, m->w4, m->a0, m->a1, m->a2, m->a3, m->z1, m->z2,
-                    m->z3, m->y, m->dy, m->da, m->dz, m->dy_bf, m->dz_bf, m->d_loss};
+                    m->z3, m->y, m->dy, m->da, m->dz, m->dy_bf, m->dz_bf, m->d_loss, m->d_err};
     for (void *q : ptrs) cudaFree(q);
     delete m;
 }
 
-cudaError_t gemm(const GemmArgs &a, cudaStream_t s) {
+// Each block holds kGN TMEM columns; 4 KB of unused dynamic shared memory
+// keeps a block at >= 28 KB, so at most 7 blocks (448 of the 512 columns)
+// are resident on an SM and a TMEM allocation never has to wait.
+constexpr size_t kTmemGuardSmem = 4096;
+
+cudaError_t gemm(const GemmArgs &a, int *err, cudaStream_t s) {
     dim3 grid((a.N + kGN - 1) / kGN, (a.M + kGM - 1) / kGM);
-    gemm_bf16_kernel<<<grid, 128, 0, s>>>(a);
+    gemm_tc_kernel<<<grid, 128, kTmemGuardSmem, s>>>(a, err);
     return cudaGetLastError();
 }
 
@@ -279,10 +364,10 @@ psc_status forward(psc_mlp *m, const float *x, int B) {
     cudaStream_t s = m->stream;
     standardise_kernel<<<blocks_for((size_t)B * kIn), 256, 0, s>>>(x, m->p + omu, m->p + os, B, m->a0);
     PSC_MCUDA(m, cudaGetLastError());
-    PSC_MCUDA(m, gemm(fwd_layer(m->a0, B, kIn, m->w1, kHid, m->p + ob1, m->z1, m->a1, 1), s));
-    PSC_MCUDA(m, gemm(fwd_layer(m->a1, B, kHid, m->w2, kHid, m->p + ob2, m->z2, m->a2, 1), s));
-    PSC_MCUDA(m, gemm(fwd_layer(m->a2, B, kHid, m->w3, kHid, m->p + ob3, m->z3, m->a3, 1), s));
-    PSC_MCUDA(m, gemm(fwd_layer(m->a3, B, kHid, m->w4, kOut, m->p + ob4, m->y, nullptr, 0), s));
+    PSC_MCUDA(m, gemm(fwd_layer(m->a0, B, kIn, m->w1, kHid, m->p + ob1, m->z1, m->a1, 1), m->d_err, s));
+    PSC_MCUDA(m, gemm(fwd_layer(m->a1, B, kHid, m->w2, kHid, m->p + ob2, m->z2, m->a2, 1), m->d_err, s));
+    PSC_MCUDA(m, gemm(fwd_layer(m->a2, B, kHid, m->w3, kHid, m->p + ob3, m->z3, m->a3, 1), m->d_err, s));
+    PSC_MCUDA(m, gemm(fwd_layer(m->a3, B, kHid, m->w4, kOut, m->p + ob4, m->y, nullptr, 0), m->d_err, s));
     return PSC_OK;
 }
 
@@ -312,9 +397,9 @@ psc_status backward(psc_mlp *m, const float *t, int B) {
     PSC_MCUDA(m, cudaGetLastError());
     float *g = m->g;
     PSC_MCUDA(m, cudaMemsetAsync(g, 0, sizeof(float) * kNParams, s));
-    PSC_MCUDA(m, gemm(wgrad(m->a3, B, kHid, m->dy_bf, kOut, g + oW4), s));
+    PSC_MCUDA(m, gemm(wgrad(m->a3, B, kHid, m->dy_bf, kOut, g + oW4), m->d_err, s));
     colsum_kernel<<<1, 32 * kOut, 0, s>>>(m->dy, B, kOut, g + ob4);
-    PSC_MCUDA(m, gemm(dgrad(m->dy_bf, B, kOut, m->w4, kHid, m->da), s));
+    PSC_MCUDA(m, gemm(dgrad(m->dy_bf, B, kOut, m->w4, kHid, m->da), m->d_err, s));
     const float *zs[3] = {m->z1, m->z2, m->z3};
     const bf16 *as[3] = {m->a0, m->a1, m->a2};
     const bf16 *ws[3] = {m->w1, m->w2, m->w3};
@@ -323,10 +408,10 @@ psc_status backward(psc_mlp *m, const float *t, int B) {
     for (int L = 2; L >= 0; --L) {
         gelu_back_kernel<<<blocks_for((size_t)B * kHid), 256, 0, s>>>(m->da, zs[L], B * kHid, m->dz, m->dz_bf);
         PSC_MCUDA(m, cudaGetLastError());
-        PSC_MCUDA(m, gemm(wgrad(as[L], B, kin[L], m->dz_bf, kHid, g + ow[L]), s));
+        PSC_MCUDA(m, gemm(wgrad(as[L], B, kin[L], m->dz_bf, kHid, g + ow[L]), m->d_err, s));
         colsum_kernel<<<(kHid * 32 + 255) / 256, 256, 0, s>>>(m->dz, B, kHid, g + ob[L]);
         PSC_MCUDA(m, cudaGetLastError());
-        if (L > 0) PSC_MCUDA(m, gemm(dgrad(m->dz_bf, B, kHid, ws[L], kin[L], m->da), s));
+        if (L > 0) PSC_MCUDA(m, gemm(dgrad(m->dz_bf, B, kHid, ws[L], kin[L], m->da), m->d_err, s));
     }
     return PSC_OK;
 }
@@ -375,6 +460,8 @@ psc_status psc_mlp_create(psc_mlp **out, int max_batch, void *stream) {
     if (e == cudaSuccess) e = mall(&m->dy_bf, B * kOut);
     if (e == cudaSuccess) e = mall(&m->dz_bf, B * kHid);
     if (e == cudaSuccess) e = mall(&m->d_loss, 1);
+    if (e == cudaSuccess) e = mall(&m->d_err, 1);
+    if (e == cudaSuccess) e = cudaMemsetAsync(m->d_err, 0, sizeof(int), m->stream);
     if (e != cudaSuccess) {
         mfree(m);
         return set_global_error(e == cudaErrorMemoryAllocation ? PSC_ERR_OOM : PSC_ERR_CUDA, "psc_mlp_create: allocation");
@@ -402,7 +489,7 @@ psc_status psc_mlp_get_params(psc_mlp *m, float *params) {
     if (!m || !params) return set_global_error(PSC_ERR_ARG, "mlp and params must be non-NULL");
     PSC_MCUDA(m, cudaMemcpyAsync(params, m->p, sizeof(float) * kNParams, cudaMemcpyDeviceToHost, m->stream));
     PSC_MCUDA(m, cudaStreamSynchronize(m->stream));
-    return PSC_OK;
+    return check_device_err(m);
 }
 
 psc_status psc_mlp_forward(psc_mlp *m, const float *x_dev, int batch, float *y_dev) {
@@ -424,7 +511,10 @@ psc_status psc_mlp_grad(psc_mlp *m, const float *x_dev, const float *t_dev, int 
     if (st != PSC_OK) return st;
     if (grad_host) PSC_MCUDA(m, cudaMemcpyAsync(grad_host, m->g, sizeof(float) * kNParams, cudaMemcpyDeviceToHost, m->stream));
     if (loss) PSC_MCUDA(m, cudaMemcpyAsync(loss, m->d_loss, sizeof(double), cudaMemcpyDeviceToHost, m->stream));
-    if (grad_host || loss) PSC_MCUDA(m, cudaStreamSynchronize(m->stream));
+    if (grad_host || loss) {
+        PSC_MCUDA(m, cudaStreamSynchronize(m->stream));
+        return check_device_err(m);
+    }
     return PSC_OK;
 }
 
@@ -447,6 +537,7 @@ psc_status psc_mlp_train_step(psc_mlp *m, const float *x_dev, const float *t_dev
     if (loss) {
         PSC_MCUDA(m, cudaMemcpyAsync(loss, m->d_loss, sizeof(double), cudaMemcpyDeviceToHost, m->stream));
         PSC_MCUDA(m, cudaStreamSynchronize(m->stream));
+        return check_device_err(m);
     }
     return PSC_OK;
 }
@@ -460,6 +551,8 @@ psc_status psc_mlp_infer_offsets(psc_mlp *m, const float *feat_dev, int n_ant, d
     if (m->host.size() < (size_t)n_ant * kOut) m->host.resize((size_t)n_ant * kOut);
     PSC_MCUDA(m, cudaMemcpyAsync(m->host.data(), m->y, sizeof(float) * n_ant * kOut, cudaMemcpyDeviceToHost, m->stream));
     PSC_MCUDA(m, cudaStreamSynchronize(m->stream));
+    st = check_device_err(m);
+    if (st != PSC_OK) return st;
     for (int i = 0; i < n_ant * kOut; ++i) lm_out[i] = (double)m->host[i] * sigma_prior_rad;
     return PSC_OK;
 }
