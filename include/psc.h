@@ -269,7 +269,9 @@ psc_status psc_features(psc_ctx *ctx, const void *vis_obs, const float *w, doubl
  * the AdamW state).  Loss: (1/B) sum_b sum_o (y_bo - t_bo)^2.
  * x_dev [batch][52], t_dev and y_dev [batch][2] are device FP32; batch is
  * 1..max_batch.  All calls enqueue on the stream given to psc_mlp_create;
- * those with host outputs synchronise it.  Errors: psc_last_error(NULL). */
+ * those with host outputs synchronise it.  The GEMMs run on the tensor cores
+ * (tcgen05.mma); if one gives up waiting for its MMAs (a bounded wait), the
+ * next synchronising call returns PSC_ERR_TIMEOUT.  Errors: psc_last_error(NULL). */
 typedef struct psc_mlp psc_mlp;
 int psc_mlp_n_params(void);
 psc_status psc_mlp_create(psc_mlp **out, int max_batch, void *stream);
