@@ -145,8 +145,12 @@ void psc_solve_opts_default(psc_solve_opts *opts);
  * image zero-padded to Ng x Ng, G[gy][gx] = sum I[row][col]
  * exp(+2 pi i ((gx-Ng/2)(col-N/2) + (gy-Ng/2)(row-N/2)) / Ng).
  * image_dev: device float [N][N]; grid_out: device complex64 [Ng][Ng];
- * stream: cudaStream_t or NULL.  Allocates a temporary complex64 [N][Ng]
- * buffer and synchronises the stream before freeing it and returning. */
+ * stream: cudaStream_t or NULL.  For N % 8 == 0 the two matrix products run
+ * on the tensor cores in split bfloat16 (each FP32 operand as three bfloat16
+ * parts, FP32 accumulation; error at FP32 rounding level) and need a
+ * temporary workspace of 6 N^2 + 24 Ng N bytes; otherwise FP32 SIMT with a
+ * temporary complex64 [N][Ng].  Synchronises the stream before freeing the
+ * workspace and returning; PSC_ERR_TIMEOUT if a tensor-core wait ran out. */
 psc_status psc_model_grid(const psc_grid_desc *gd, const float *image_dev, void *grid_out,
                           void *stream);
 

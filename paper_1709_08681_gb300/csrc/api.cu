@@ -267,14 +267,16 @@ psc_status psc_model_grid(const psc_grid_desc *gd, const float *image_dev, void 
     if (!check_grid_desc(gd, &why)) return fail(nullptr, PSC_ERR_ARG, why);
     if (!image_dev || !grid_out) return fail(nullptr, PSC_ERR_ARG, "image and grid pointers must be non-NULL");
     cudaStream_t s = (cudaStream_t)stream;
-    float2 *tmp = nullptr, *tw = nullptr;
-    cudaError_t e = dalloc(&tmp, (size_t)gd->n_img * gd->n_grid);
-    if (e == cudaSuccess) e = dalloc(&tw, (size_t)gd->n_grid);
-    if (e == cudaSuccess) e = launch_model_grid(gd->n_img, gd->n_grid, image_dev, tmp, tw, (float2 *)grid_out, s);
+    void *ws = nullptr;
+    int *err_dev = nullptr;
+    int herr = 0;
+    cudaError_t e = cudaMalloc(&ws, model_grid_ws_bytes(gd->n_img, gd->n_grid));
+    if (e == cudaSuccess) e = launch_model_grid(gd->n_img, gd->n_grid, image_dev, ws, (float2 *)grid_out, &err_dev, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    cudaFree(tmp);
-    cudaFree(tw);
+    if (e == cudaSuccess) e = cudaMemcpy(&herr, err_dev, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(ws);
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "psc_model_grid");
+    if (herr) return fail(nullptr, PSC_ERR_TIMEOUT, "psc_model_grid: a tensor-core wait timed out");
     return PSC_OK;
 }
 

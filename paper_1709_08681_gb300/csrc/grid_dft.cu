@@ -7,6 +7,11 @@
 // with F[g][c] = W((g - Ng/2)(c - N/2)) generated on the fly from a twiddle
 // table (exact integer phase index modulo Ng, table values from FP64 sincospi).
 // FP32 SIMT GEMM tiles: 64 x 64 outputs per 256-thread block, 4 x 4 per thread.
+#include <algorithm>
+#include <cstdint>
+
+#include <cuda_bf16.h>
+
 #include "psc_internal.cuh"
 
 namespace psc {
@@ -130,15 +135,340 @@ __global__ void __launch_bounds__(256) dft_cols_kernel(const float2 *__restrict_
         }
 }
 
+
+// ---------------------------------------------------------------------------
+// Tensor-core path (N % 8 == 0): the same two products on the 5th-generation
+// tensor cores in split bfloat16.  Every FP32 operand x is written as three
+// bfloat16 planes x = h + m + l (h = bf16(x), m = bf16(x - h), l = bf16(x - h
+// - m), each residual exact in FP32), and a product x y is accumulated in FP32
+// from the six plane pairs (h,h) (h,m) (m,h) (m,m) (h,l) (l,h); the dropped
+// pairs are below 2^-24 of |x y|, FP32's own rounding.
+//   pass 1: T[r][g] = sum_c I[r][c] E[g][c]       (tile rows r, columns g)
+//   pass 2: G[gy][gx]^T tile: rows gx, columns gy, sum over r of T[r][gx] E[gy][r]
+// with E[g][c] = W((g - Ng/2)(c - N/2)).  Pass 1 writes T already split and
+// transposed (planes [3][Ng][N]) so that both passes read K-major operands.
+// A block owns a 128 x 128 tile with two FP32 accumulators (real, imaginary)
+// in tensor memory; K advances in chunks of 32 through two shared-memory
+// buffers of all operand planes; one thread issues the MMAs (kind::f16, the
+// negative term of the complex product by the descriptor's negate-A bit) and
+// commits each chunk to its buffer's mbarrier.  Waits are bounded (*err).
+
+typedef __nv_bfloat16 bf16;
+constexpr int kTM = 128, kTN = 64, kTK = 32;
+constexpr int kPlaneA = kTM * kTK * 2;               // one A operand plane of a chunk (8 KB)
+constexpr int kPlaneB = kTN * kTK * 2;               // one B operand plane of a chunk (4 KB)
+constexpr int kEpoch = 4;                            // chunks (K = 128) between promotions to registers
+constexpr long kTcWait = 1L << 24;
+
+__device__ __forceinline__ void split3(float x, bf16 &h, bf16 &m, bf16 &l) {
+    h = __float2bfloat16_rn(x);
+    const float r = x - __bfloat162float(h);
+    m = __float2bfloat16_rn(r);
+    l = __float2bfloat16_rn(r - __bfloat162float(m));
+}
+
+// The same split of an FP64 value (the twiddles), residuals in FP64.
+__device__ __forceinline__ void split3d(double x, bf16 &h, bf16 &m, bf16 &l) {
+    h = __double2bfloat16(x);
+    const double r = x - (double)__bfloat162float(h);
+    m = __double2bfloat16(r);
+    l = __double2bfloat16(r - (double)__bfloat162float(m));
+}
+
+__global__ void twiddle64_kernel(double2 *W, int ng) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < ng; k += gridDim.x * blockDim.x) {
+        double s, c;
+        sincospi(2.0 * (double)k / (double)ng, &s, &c);
+        W[k] = make_double2(c, s);
+    }
+}
+
+// I3[p][r][c] of the N x N image.
+__global__ void split_image_kernel(const float *__restrict__ img, long long n2, bf16 *__restrict__ I3) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n2; e += (long long)gridDim.x * blockDim.x) {
+        bf16 h, m, l;
+        split3(img[e], h, m, l);
+        I3[e] = h; I3[n2 + e] = m; I3[2 * n2 + e] = l;
+    }
+}
+
+// E3re[p][g][c], E3im[p][g][c] (g < Ng, c < N).
+__global__ void split_dft_matrix_kernel(const double2 *__restrict__ W, int n, int ng, bf16 *__restrict__ Er,
+                                        bf16 *__restrict__ Ei) {
+    const long long total = (long long)ng * n;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+        const int g = (int)(e / n), c = (int)(e % n);
+        const double2 w = W[phase_index(g, c, ng, n)];
+        bf16 h, m, l;
+        split3d(w.x, h, m, l);
+        Er[e] = h; Er[total + e] = m; Er[2 * total + e] = l;
+        split3d(w.y, h, m, l);
+        Ei[e] = h; Ei[total + e] = m; Ei[2 * total + e] = l;
+    }
+}
+
+__device__ __forceinline__ uint32_t tc_core_off(int r, int k) {
+    return (uint32_t)((r >> 3) * (kTK / 8 * 128) + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
+    // K-major, no swizzle: K-adjacent core matrices 128 B apart, 8-row groups kTK / 8 * 128 B apart
+    return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)(128 >> 4) << 16) |
+           ((uint64_t)((kTK / 8 * 128) >> 4) << 32) | ((uint64_t)1 << 46);
+}
+
+__device__ __forceinline__ bool tc_wait(uint32_t addr, uint32_t parity) {
+    for (long it = 0; it < kTcWait; ++it) {
+        uint32_t ok;
+        asm volatile("{\n.reg .pred q;\nmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\nselp.u32 %0, 1, 0, q;\n}"
+                     : "=r"(ok) : "r"(addr), "r"(parity));
+        if (ok) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t accum) {
+    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}"
+                 :: "r"(tmem), "l"(ad), "l"(bd), "r"(idesc), "r"(accum));
+}
+
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                 : "r"(taddr));
+}
+
+struct TcPassArgs {
+    const bf16 *A[2];       // split planes [3][a_rows][k] of each A source (pass 1: image; pass 2: T re, T im)
+    const bf16 *B[2];       // split planes [3][b_rows][k] of each B source (E re, E im)
+    int n_a;                // A sources: 1 (pass 1) or 2 (pass 2)
+    int a_rows, b_rows, k;  // rows of the A and B operands, depth (= N, also the plane pitch)
+    bf16 *Tr, *Ti;          // pass 1 output planes [3][Ng][N]
+    float2 *G;              // pass 2 output [Ng][Ng]
+    int ng;
+    int *err;
+};
+
+template <int kPass>
+__global__ void __launch_bounds__(128, 1) dft_tc_kernel(const TcPassArgs g) {
+    constexpr int kNA = kPass == 1 ? 1 : 2;
+    constexpr int kStage = 3 * kNA * kPlaneA + 6 * kPlaneB;   // A planes, then B planes (E re, E im)
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ uint32_t tmem_base;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.y * kTM, n0 = blockIdx.x * kTN;
+    const uint32_t mb[2] = {(uint32_t)__cvta_generic_to_shared(&mbar[0]), (uint32_t)__cvta_generic_to_shared(&mbar[1])};
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(mb[0]));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(mb[1]));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    if (warp == 0) {
+        const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&tmem_base);
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" :: "r"(dst), "r"(4 * kTN));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    // accumulators of kTN columns: 0 real, 1 imaginary (head x head plane
+    // products), 2 real, 3 imaginary (the smaller cross-plane products, kept
+    // apart so that the tensor core's accumulation does not round them away
+    // against the head terms).  Every kEpoch chunks all four are added into
+    // FP32 registers (round to nearest) and restarted, which bounds the depth
+    // of any tensor-core sum at kEpoch * kTK = 128.
+    const uint32_t tmem = tmem_base;
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTN >> 3) << 17) |
+                           ((uint32_t)(kTM >> 4) << 24);
+    const uint32_t idesc_neg = idesc | (1u << 13);  // negate A
+    const size_t plane_a = (size_t)g.a_rows * g.k, plane_b = (size_t)g.b_rows * g.k;
+    const int nk = (g.k + kTK - 1) / kTK;
+    const uint32_t smem_base = (uint32_t)__cvta_generic_to_shared(smem);
+    const uint32_t lane_base = tmem + ((uint32_t)(32 * warp) << 16);
+    float sum_re[kTN], sum_im[kTN];
+#pragma unroll
+    for (int j = 0; j < kTN; ++j) { sum_re[j] = 0.f; sum_im[j] = 0.f; }
+    bool ok = true;
+    bool started[4] = {false, false, false, false};  // used by thread 0 only
+    for (int c = 0; c < nk && ok; ++c) {
+        const int b = c & 1;
+        if (c >= 2) ok = tc_wait(mb[b], (uint32_t)((c - 2) >> 1) & 1u);
+        if (!ok) break;
+        unsigned char *buf = smem + b * kStage;
+        const int k0 = c * kTK;
+#pragma unroll 1
+        for (int pl = 0; pl < 3 * kNA + 6; ++pl) {
+            const bf16 *src;
+            int rows, r0, nrow;
+            unsigned char *dst;
+            if (pl < 3 * kNA) {
+                src = g.A[pl / 3] + (pl % 3) * plane_a; rows = g.a_rows; r0 = m0; nrow = kTM;
+                dst = buf + pl * kPlaneA;
+            } else {
+                const int q = pl - 3 * kNA;
+                src = g.B[q / 3] + (q % 3) * plane_b; rows = g.b_rows; r0 = n0; nrow = kTN;
+                dst = buf + 3 * kNA * kPlaneA + q * kPlaneB;
+            }
+            for (int seg = tid; seg < nrow * (kTK / 8); seg += blockDim.x) {
+                const int r = seg / (kTK / 8), kq = (seg % (kTK / 8)) * 8;
+                uint4 v = make_uint4(0u, 0u, 0u, 0u);
+                if (r0 + r < rows && k0 + kq < g.k)
+                    v = *reinterpret_cast<const uint4 *>(src + (size_t)(r0 + r) * g.k + k0 + kq);
+                *reinterpret_cast<uint4 *>(dst + tc_core_off(r, kq)) = v;
+            }
+        }
+        asm volatile("fence.proxy.async.shared::cta;");
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        if (tid == 0) {
+            const uint32_t sb = smem_base + (uint32_t)(b * kStage);
+            // plane pairs (A split, B split) kept in each product; pair 0 is head x head
+            const int pp[6][2] = {{0, 0}, {0, 1}, {1, 0}, {1, 1}, {0, 2}, {2, 0}};
+            // terms (accumulator, A source, B source, negate):
+            // pass 1: re += I Er, im += I Ei; pass 2: re += Tr Er - Ti Ei, im += Ti Er + Tr Ei
+            constexpr int kTerms = kPass == 1 ? 2 : 4;
+            const int terms[4][4] = {{0, 0, 0, 0},
+                                     {kPass == 1 ? 1 : 0, kPass == 1 ? 0 : 1, 1, kPass == 1 ? 0 : 1},
+                                     {1, 1, 0, 0},
+                                     {1, 0, 1, 0}};
+            for (int t = 0; t < kTerms; ++t) {
+                const int acc = terms[t][0], sa = terms[t][1], sbs = terms[t][2], neg = terms[t][3];
+                for (int q = 0; q < 6; ++q) {
+                    const uint32_t a_pl = sb + (uint32_t)((sa * 3 + pp[q][0]) * kPlaneA);
+                    const uint32_t b_pl = sb + (uint32_t)(3 * kNA * kPlaneA + (sbs * 3 + pp[q][1]) * kPlaneB);
+                    const int dst = acc + (q == 0 ? 0 : 2);
+#pragma unroll
+                    for (int kk = 0; kk < kTK / 16; ++kk) {
+                        tc_mma(tmem + (uint32_t)(dst * kTN), tc_desc(a_pl + 256u * kk), tc_desc(b_pl + 256u * kk),
+                               neg ? idesc_neg : idesc, started[dst] ? 1u : 0u);
+                        started[dst] = true;
+                    }
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(mb[b]));
+        }
+        if ((c + 1) % kEpoch == 0 || c == nk - 1) {
+            // promote: wait for this chunk's MMAs (and with them all earlier ones),
+            // add the four accumulators into the FP32 sums, restart them
+            ok = tc_wait(mb[b], (uint32_t)(c >> 1) & 1u);
+            if (!ok) break;
+            asm volatile("tcgen05.fence::after_thread_sync;");
+#pragma unroll
+            for (int c0 = 0; c0 < kTN; c0 += 16) {
+                uint32_t re[16], im[16], rs[16], is[16];
+                tc_ld16(lane_base + (uint32_t)c0, re);
+                tc_ld16(lane_base + (uint32_t)(kTN + c0), im);
+                tc_ld16(lane_base + (uint32_t)(2 * kTN + c0), rs);
+                tc_ld16(lane_base + (uint32_t)(3 * kTN + c0), is);
+                asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    sum_re[c0 + j] += __uint_as_float(re[j]) + __uint_as_float(rs[j]);
+                    sum_im[c0 + j] += __uint_as_float(im[j]) + __uint_as_float(is[j]);
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            __syncthreads();                               // every warp has read before the accumulators restart
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            if (tid == 0) started[0] = started[1] = started[2] = started[3] = false;
+        }
+    }
+    if (!ok) {
+        if (tid == 0) atomicExch(g.err, 1);
+        if (nk > 0) tc_wait(mb[(nk - 1) & 1], (uint32_t)((nk - 1) >> 1) & 1u);   // in-flight MMAs, bounded
+    }
+    if (ok) {
+        const int m = m0 + 32 * warp + lane;         // accumulator lane: pass 1 image row, pass 2 grid column gx
+        if (m < g.a_rows) {
+#pragma unroll
+            for (int j = 0; j < kTN; ++j) {
+                const int col = n0 + j;                      // pass 1: grid column g; pass 2: grid row gy
+                if (col >= g.b_rows) break;
+                if constexpr (kPass == 1) {
+                    const size_t plane_t = (size_t)g.b_rows * g.k;
+                    const size_t o = (size_t)col * g.k + m;  // T planes [3][Ng][N]: row g, column image row m
+                    bf16 h, mm, l;
+                    split3(sum_re[j], h, mm, l);
+                    g.Tr[o] = h; g.Tr[plane_t + o] = mm; g.Tr[2 * plane_t + o] = l;
+                    split3(sum_im[j], h, mm, l);
+                    g.Ti[o] = h; g.Ti[plane_t + o] = mm; g.Ti[2 * plane_t + o] = l;
+                } else {
+                    g.G[(size_t)col * g.ng + m] = make_float2(sum_re[j], sum_im[j]);
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(4 * kTN));
+}
 }  // namespace
 
-cudaError_t launch_model_grid(int n_img, int n_grid, const float *image, float2 *tmp, float2 *twiddle,
-                              float2 *grid_out, cudaStream_t s) {
-    twiddle_kernel<<<(n_grid + 255) / 256, 256, 0, s>>>(twiddle, n_grid);
-    dim3 g1((n_grid + kBN - 1) / kBN, (n_img + kBM - 1) / kBM);
-    dft_rows_kernel<<<g1, 256, 0, s>>>(image, twiddle, n_img, n_grid, tmp);
-    dim3 g2((n_grid + kBN - 1) / kBN, (n_grid + kBM - 1) / kBM);
-    dft_cols_kernel<<<g2, 256, 0, s>>>(tmp, twiddle, n_img, n_grid, grid_out);
+namespace {
+size_t al256(size_t x) { return (x + 255) / 256 * 256; }
+bool use_tc(int n_img) { return n_img % 8 == 0; }
+}  // namespace
+
+size_t model_grid_ws_bytes(int n_img, int n_grid) {
+    const size_t n = (size_t)n_img, ng = (size_t)n_grid;
+    if (use_tc(n_img))
+        return al256(ng * sizeof(double2)) + al256(3 * n * n * 2) + 4 * al256(3 * ng * n * 2) + 256;
+    return al256(n * ng * sizeof(float2)) + al256(ng * sizeof(float2)) + 256;
+}
+
+cudaError_t launch_model_grid(int n_img, int n_grid, const float *image, void *ws, float2 *grid_out, int **err_dev,
+                              cudaStream_t s) {
+    const size_t n = (size_t)n_img, ng = (size_t)n_grid;
+    unsigned char *p = (unsigned char *)ws;
+    if (!use_tc(n_img)) {
+        float2 *tmp = (float2 *)p;
+        float2 *twiddle = (float2 *)(p + al256(n * ng * sizeof(float2)));
+        *err_dev = (int *)(p + al256(n * ng * sizeof(float2)) + al256(ng * sizeof(float2)));
+        cudaError_t e = cudaMemsetAsync(*err_dev, 0, sizeof(int), s);
+        if (e != cudaSuccess) return e;
+        twiddle_kernel<<<(n_grid + 255) / 256, 256, 0, s>>>(twiddle, n_grid);
+        dim3 g1((n_grid + kBN - 1) / kBN, (n_img + kBM - 1) / kBM);
+        dft_rows_kernel<<<g1, 256, 0, s>>>(image, twiddle, n_img, n_grid, tmp);
+        dim3 g2((n_grid + kBN - 1) / kBN, (n_grid + kBM - 1) / kBM);
+        dft_cols_kernel<<<g2, 256, 0, s>>>(tmp, twiddle, n_img, n_grid, grid_out);
+        return cudaGetLastError();
+    }
+    double2 *tw = (double2 *)p;
+    p += al256(ng * sizeof(double2));
+    bf16 *I3 = (bf16 *)p;
+    p += al256(3 * n * n * 2);
+    bf16 *Er = (bf16 *)p; p += al256(3 * ng * n * 2);
+    bf16 *Ei = (bf16 *)p; p += al256(3 * ng * n * 2);
+    bf16 *Tr = (bf16 *)p; p += al256(3 * ng * n * 2);
+    bf16 *Ti = (bf16 *)p; p += al256(3 * ng * n * 2);
+    *err_dev = (int *)p;
+    cudaError_t e = cudaMemsetAsync(*err_dev, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    const int smem1 = 2 * (3 * kPlaneA + 6 * kPlaneB), smem2 = 2 * (6 * kPlaneA + 6 * kPlaneB);
+    e = cudaFuncSetAttribute(dft_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem1);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(dft_tc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem2);
+    if (e != cudaSuccess) return e;
+    twiddle64_kernel<<<(n_grid + 255) / 256, 256, 0, s>>>(tw, n_grid);
+    split_image_kernel<<<(int)std::min<size_t>((n * n + 255) / 256, 4096), 256, 0, s>>>(image, (long long)(n * n), I3);
+    split_dft_matrix_kernel<<<(int)std::min<size_t>((ng * n + 255) / 256, 8192), 256, 0, s>>>(tw, n_img, n_grid, Er, Ei);
+    TcPassArgs a1{};
+    a1.A[0] = I3; a1.n_a = 1;
+    a1.B[0] = Er; a1.B[1] = Ei;
+    a1.a_rows = n_img; a1.b_rows = n_grid; a1.k = n_img;
+    a1.Tr = Tr; a1.Ti = Ti; a1.ng = n_grid; a1.err = *err_dev;
+    dim3 g1((n_grid + kTN - 1) / kTN, (n_img + kTM - 1) / kTM);
+    dft_tc_kernel<1><<<g1, 128, smem1, s>>>(a1);
+    TcPassArgs a2{};
+    a2.A[0] = Tr; a2.A[1] = Ti; a2.n_a = 2;
+    a2.B[0] = Er; a2.B[1] = Ei;
+    a2.a_rows = n_grid; a2.b_rows = n_grid; a2.k = n_img;
+    a2.G = grid_out; a2.ng = n_grid; a2.err = *err_dev;
+    dim3 g2((n_grid + kTN - 1) / kTN, (n_grid + kTM - 1) / kTM);
+    dft_tc_kernel<2><<<g2, 128, smem2, s>>>(a2);
     return cudaGetLastError();
 }
 

@@ -136,8 +136,11 @@ cudaError_t launch_step_max(const double *uvw, int nt, int n_bl, unsigned *out_b
 // Records msg as the context-free last error (psc_last_error(NULL)); returns st.
 psc_status set_global_error(psc_status st, const char *msg);
 cudaError_t launch_features(const StencilArgs &a, double *blsum, int n_ant, float *feat, cudaStream_t s);
-cudaError_t launch_model_grid(int n_img, int n_grid, const float *image, float2 *tmp, float2 *twiddle,
-                              float2 *grid_out, cudaStream_t s);
+// Workspace (bytes) of launch_model_grid; the model grid goes to grid_out
+// and *err_dev points (inside ws) at a flag set if a tensor-core wait ran out.
+size_t model_grid_ws_bytes(int n_img, int n_grid);
+cudaError_t launch_model_grid(int n_img, int n_grid, const float *image, void *ws, float2 *grid_out, int **err_dev,
+                              cudaStream_t s);
 // FP32 split (u_hi, u_lo, v_hi, v_lo) of n uvw triples (FP64 metres).
 cudaError_t launch_split_uv(const double *uvw, size_t n, float4 *out, cudaStream_t s);
 // bfloat16 copy (nearest even, re in the low half) of n complex64 values.

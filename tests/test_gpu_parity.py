@@ -41,11 +41,13 @@ def test_model_grid_matches_oracle(spec):
     assert _rel(G, m.grid) < 1e-6
 
 
-def test_model_grid_dense_random_image():
-    """A dense image with both signs, ragged against the 64-wide GEMM tiles."""
+@pytest.mark.parametrize("N,Ng", [(72, 200), (256, 520), (62, 130)])
+def test_model_grid_dense_random_image(N, Ng):
+    """A dense image with both signs, ragged against the GEMM tiles: N % 8 == 0
+    takes the split-bfloat16 tensor-core path (128 x 128 tiles, 32-deep K
+    chunks), N = 62 the FP32 SIMT path."""
     from oracle import model_grid
     rng = np.random.default_rng(5)
-    N, Ng = 72, 200
     img = rng.normal(size=(N, N)).astype(np.float32)
     ref = model_grid.grid_from_image(img.astype(np.float64), Ng)
     out = torch.empty((Ng, Ng), dtype=torch.complex64, device="cuda:0")
@@ -102,7 +104,7 @@ def test_two_visibilities_per_thread_match_oracle(case):
     lm = 0.5 * lmt
     chi2, g, H, X = psc.chi2_grad_normal(m, lm, vobs, w)
     chi2g, gg, Hg, Xg = gp.ctx.psc_residual_grad(lm, gp.upload(vobs), gp.upload(w, torch.float32), 1.0, cross=True)
-    assert abs(chi2g - chi2) < TOL_V * chi2
+    assert abs(chi2g - chi2) < TOL_V * _chi2_scale(m, lm, vobs, w)
     Vl, dVl = psc.predict(m, lm)
     gscale = 2.0 * np.sum(w[None] * np.abs(vobs - Vl)[None] * np.abs(dVl))
     assert np.max(np.abs(gg - g)) < TOL_V * gscale
@@ -160,7 +162,7 @@ def test_never_staged_matches_oracle(kv):
     chi2, g, H, X = psc.chi2_grad_normal(m, 0.5 * lmt, vobs, w)
     chi2g, gg, Hg, Xg = gp.ctx.psc_residual_grad(0.5 * lmt, gp.upload(vobs), gp.upload(w, torch.float32), 1.0,
                                                  cross=True)
-    assert abs(chi2g - chi2) < TOL_V * chi2
+    assert abs(chi2g - chi2) < TOL_V * _chi2_scale(m, 0.5 * lmt, vobs, w)
     assert np.max(np.abs(Hg - H)) < TOL_V * np.max(np.abs(H))
     with pytest.raises(_abi.PscError):
         gp.ctx.psc_set_staging(2)
@@ -183,6 +185,15 @@ def _obs(m, lmt, sigma=1e-3, seed=7):
     return vobs, w
 
 
+def _chi2_scale(m, lm, vobs, w):
+    """Error scale of chi^2 = sum w |R|^2 for visibilities within TOL_V of the
+    oracle: chi^2 itself plus its first-order sensitivity sum 2 w |R| |V|
+    (when |R| << |V|, as for a single visibility near the fit, the relative
+    error of chi^2 exceeds that of V by |V| / |R|)."""
+    V, _ = psc.predict(m, lm, False)
+    return float(np.sum(w * np.abs(vobs - V) ** 2) + 2.0 * np.sum(w * np.abs(vobs - V) * np.abs(V)))
+
+
 @pytest.mark.parametrize("case", PREDICT_CASES[:4])
 def test_residual_grad_matches_oracle(case):
     spec, n_ant, nt, freqs, tt, cg = case
@@ -192,7 +203,7 @@ def test_residual_grad_matches_oracle(case):
     chi2, g, H, X = psc.chi2_grad_normal(m, lm, vobs, w)
     gp = GpuProblem(m, img, t_tile=tt, c_group=cg)
     chi2g, gg, Hg, Xg = gp.ctx.psc_residual_grad(lm, gp.upload(vobs), gp.upload(w, torch.float32), 1.0, cross=True)
-    assert abs(chi2g - chi2) < TOL_V * chi2
+    assert abs(chi2g - chi2) < TOL_V * _chi2_scale(m, lm, vobs, w)
     # gradient scale: sum over visibilities of |2 w R dV|
     V, dV = psc.predict(m, lm)
     gscale = 2.0 * np.sum(w[None] * np.abs(vobs - V)[None] * np.abs(dV))
