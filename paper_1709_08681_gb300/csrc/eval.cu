@@ -100,7 +100,7 @@ template <int kV>
 __device__ __forceinline__ void row_taps(const float2 *__restrict__ row, int n, float (&dxo)[kV],
                                          const float (&dyo2)[kV], float ov, unsigned tab_adj, float (&pr)[kV],
                                          float (&pi)[kV], float (&qr)[kV], float (&qi)[kV]) {
-    constexpr int kUnroll = kV == 1 ? 4 : 2;
+    constexpr int kUnroll = 4;
 #pragma unroll kUnroll
     for (int k = 0; k < n; ++k) {
         const float2 g = row[k];
@@ -454,25 +454,36 @@ __global__ void __launch_bounds__(kMaxThreads) eval_kernel(const EvalArgs a0, co
     __shared__ BlockShared sh;
     __shared__ EvalArgs s_a;
     __shared__ long long s_work, s_first;
+    __shared__ int s_done;
     const bool persistent = queue != nullptr;
     long long next = -1;                              // thread 0: prefetched queue entry
+    int cur = -1;                                     // thread 0: context whose arguments s_a holds
     for (;;) {
     if (persistent) {
         __syncthreads();                              // the previous brick is done with shared memory
         if (threadIdx.x == 0) {
             const long long gb = next >= 0 ? next : (long long)atomicAdd(queue, 1ull);
             next = (long long)atomicAdd(queue, 1ull);  // consumed next round: its latency overlaps this brick
-            int lo = 0, hi = n_ctx - 1;               // last context with prefix[k] <= gb
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (prefix[mid] <= gb) lo = mid; else hi = mid - 1;
+            const long long end = prefix[n_ctx];
+            s_done = gb >= end;
+            if (gb < end) {
+                // a block's bricks come in increasing order: the context is the
+                // current one unless gb has passed its end
+                if (cur < 0 || gb < prefix[cur] || gb >= prefix[cur + 1]) {
+                    int lo = 0, hi = n_ctx - 1;       // last context with prefix[k] <= gb
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (prefix[mid] <= gb) lo = mid; else hi = mid - 1;
+                    }
+                    cur = lo;
+                    s_a = args[lo];                   // copied once per context change
+                    s_first = prefix[lo];
+                }
+                s_work = gb;
             }
-            s_work = gb;
-            s_first = prefix[lo];
-            if (gb < prefix[n_ctx]) s_a = args[lo];
         }
         __syncthreads();
-        if (s_work >= prefix[n_ctx]) return;
+        if (s_done) return;
     } else {
         if (threadIdx.x == 0) s_a = a0;
         __syncthreads();
