@@ -27,10 +27,11 @@
 //
 // Inner loop per tap and visibility (rho in units of table samples, t = rho
 // ov): s2 = dxo^2 + dyo^2 (dxo = dx ov; dyo^2 carries a 1e-20 floor so s2 > 0),
-// t = s2 rsqrt(s2), n = floor(t) by a round-toward-zero add of 2^23 whose bit
+// t = sqrt(s2) (hardware approximation, ~1 ulp), n = floor(t) by a round-toward-zero add of 2^23 whose bit
 // pattern also gives the table address, A° = c_n + t s_n with the staged entry
 // (c_n, s_n) = (A°(n) - n s_n, A°(n+1) - A°(n)) (the linear interpolation
-// A°(n) + (t - n) s_n rearranged), then P += A° G', Q += (A° dxo) G'.
+// A°(n) + (t - n) s_n rearranged), then P += A° G', Q += (A° dxo) G' (each a
+// packed FP32x2 FMA over the real and imaginary parts).
 #include <algorithm>
 #include <climits>
 
@@ -49,6 +50,20 @@ __device__ __forceinline__ float rsqrt_fast(float x) {
     float r;
     asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
     return r;
+}
+
+__device__ __forceinline__ float sqrt_fast(float x) {
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// (px, py) += a (gx, gy) as one packed FP32x2 FMA: each lane rounds exactly
+// like fmaf, and the pair costs one instruction instead of two.
+__device__ __forceinline__ void fma2_acc(float &px, float &py, float a, float gx, float gy) {
+    asm("{\n.reg .b64 aa, gg, pp;\nmov.b64 aa, {%2, %2};\nmov.b64 gg, {%3, %4};\nmov.b64 pp, {%0, %1};\n"
+        "fma.rn.f32x2 pp, aa, gg, pp;\nmov.b64 {%0, %1}, pp;\n}"
+        : "+f"(px), "+f"(py) : "f"(a), "f"(gx), "f"(gy));
 }
 
 // Grid cell (gy, gx) as FP32: from the bfloat16 copy when there is one
@@ -107,15 +122,12 @@ __device__ __forceinline__ void row_taps(const float2 *__restrict__ row, int n, 
 #pragma unroll
         for (int v = 0; v < kV; ++v) {
             const float s2 = fmaf(dxo[v], dxo[v], dyo2[v]);
-            const float t = s2 * rsqrt_fast(s2);
+            const float t = sqrt_fast(s2);
             const float tf = __fadd_rz(t, 8388608.0f);          // floor(t) + 2^23
             const float2 e = lds_f2(tab_adj + ((unsigned)__float_as_int(tf) << 3));
             const float A = fmaf(t, e.y, e.x);
-            pr[v] = fmaf(A, g.x, pr[v]);
-            pi[v] = fmaf(A, g.y, pi[v]);
-            const float Ad = A * dxo[v];
-            qr[v] = fmaf(Ad, g.x, qr[v]);
-            qi[v] = fmaf(Ad, g.y, qi[v]);
+            fma2_acc(pr[v], pi[v], A, g.x, g.y);
+            fma2_acc(qr[v], qi[v], A * dxo[v], g.x, g.y);
             dxo[v] -= ov;
         }
     }
@@ -350,7 +362,7 @@ __device__ __forceinline__ void eval_brick(const EvalArgs &a, int brick, float2 
                     for (int aa = a_lo; aa <= a_hi; ++aa, dd -= ov) {
                         const float2 g = cmul(grid_cell(a, row + aa), sh.phx[aa]);
                         const float s2 = fmaf(dd, dd, dyo2);
-                        const float tv = s2 * rsqrt_fast(s2);
+                        const float tv = sqrt_fast(s2);
                         const float tf = __fadd_rz(tv, 8388608.0f);
                         const float2 e = lds_f2(tab_adj + ((unsigned)__float_as_int(tf) << 3));
                         const float A = fmaf(tv, e.y, e.x);
