@@ -107,6 +107,62 @@ __device__ __forceinline__ void grid_pos(float uh, float ul, float sh, float sl,
     else if (f >= 1.f) { f -= 1.f; n += 1; }
 }
 
+// Packed FP32x2 helpers on float2 pairs (each lane rounds like the scalar op).
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
+    float2 d;
+    asm("{\n.reg .b64 aa, bb, cc;\nmov.b64 aa, {%2, %3};\nmov.b64 bb, {%4, %5};\nmov.b64 cc, {%6, %7};\n"
+        "fma.rn.f32x2 cc, aa, bb, cc;\nmov.b64 {%0, %1}, cc;\n}"
+        : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return d;
+}
+__device__ __forceinline__ float2 fmul2(float2 a, float2 b) {
+    float2 d;
+    asm("{\n.reg .b64 aa, bb;\nmov.b64 aa, {%2, %3};\nmov.b64 bb, {%4, %5};\n"
+        "mul.rn.f32x2 aa, aa, bb;\nmov.b64 {%0, %1}, aa;\n}"
+        : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+__device__ __forceinline__ float2 fadd2(float2 a, float2 b) {
+    float2 d;
+    asm("{\n.reg .b64 aa, bb;\nmov.b64 aa, {%2, %3};\nmov.b64 bb, {%4, %5};\n"
+        "add.rn.f32x2 aa, aa, bb;\nmov.b64 {%0, %1}, aa;\n}"
+        : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+__device__ __forceinline__ float2 fadd2_rz(float2 a, float2 b) {
+    float2 d;
+    asm("{\n.reg .b64 aa, bb;\nmov.b64 aa, {%2, %3};\nmov.b64 bb, {%4, %5};\n"
+        "add.rz.f32x2 aa, aa, bb;\nmov.b64 {%0, %1}, aa;\n}"
+        : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+
+// The row loop for two visibilities with their per-visibility scalars
+// packed in pairs: s2, floor(t) + 2^23, A dxo and the dxo step are one packed
+// instruction for both.
+__device__ __forceinline__ void row_taps2(const float2 *__restrict__ row, int n, float2 dxo, float2 dyo2, float ov,
+                                          unsigned tab_adj, float (&pr)[2], float (&pi)[2], float (&qr)[2],
+                                          float (&qi)[2]) {
+    const float2 step = make_float2(-ov, -ov);
+    const float2 magic = make_float2(8388608.0f, 8388608.0f);
+#pragma unroll 4
+    for (int k = 0; k < n; ++k) {
+        const float2 g = row[k];
+        const float2 s2 = ffma2(dxo, dxo, dyo2);
+        const float2 t = make_float2(sqrt_fast(s2.x), sqrt_fast(s2.y));
+        const float2 tf = fadd2_rz(t, magic);                       // floor(t) + 2^23, both
+        const float2 e0 = lds_f2(tab_adj + ((unsigned)__float_as_int(tf.x) << 3));
+        const float2 e1 = lds_f2(tab_adj + ((unsigned)__float_as_int(tf.y) << 3));
+        const float2 A = make_float2(fmaf(t.x, e0.y, e0.x), fmaf(t.y, e1.y, e1.x));
+        const float2 Ad = fmul2(A, dxo);
+        fma2_acc(pr[0], pi[0], A.x, g.x, g.y);
+        fma2_acc(pr[1], pi[1], A.y, g.x, g.y);
+        fma2_acc(qr[0], qi[0], Ad.x, g.x, g.y);
+        fma2_acc(qr[1], qi[1], Ad.y, g.x, g.y);
+        dxo = fadd2(dxo, step);
+    }
+}
+
 // One row of taps for kV visibilities: n consecutive staged cells starting at
 // row (shared memory); visibility v's first tap is at dxo[v] (= dx ov).  The
 // table address is tab_adj + (bits of floor(t) + 2^23) * 8.  Accumulates
@@ -331,7 +387,11 @@ __device__ __forceinline__ void eval_brick(const EvalArgs &a, int brick, float2 
                     dxo[v] = (hx[v] - (float)(c_lo - wx[v])) * ov;
                     pr[v] = pi[v] = qr[v] = qi[v] = 0.f;
                 }
-                row_taps<kV>(sh.tile + cy * kTile + c_lo, c_hi - c_lo + 1, dxo, dyo2, ov, tab_adj, pr, pi, qr, qi);
+                if constexpr (kV == 2)
+                    row_taps2(sh.tile + cy * kTile + c_lo, c_hi - c_lo + 1, make_float2(dxo[0], dxo[1]),
+                              make_float2(dyo2[0], dyo2[1]), ov, tab_adj, pr, pi, qr, qi);
+                else
+                    row_taps<kV>(sh.tile + cy * kTile + c_lo, c_hi - c_lo + 1, dxo, dyo2, ov, tab_adj, pr, pi, qr, qi);
 #pragma unroll
                 for (int v = 0; v < kV; ++v) {
                     S0[v].x += pr[v]; S0[v].y += pi[v];
