@@ -52,6 +52,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     p.add_argument("--no-learned", action="store_true", help="skip the learned-initialiser comparison")
+    p.add_argument("--no-drift", action="store_true", help="skip the full-scale drifting-pointing section")
     p.add_argument("--mixed-intervals", type=int, default=256,
                    help="intervals of the mixed-array batched-solve section (0 skips it)")
     p.add_argument("--learned-train", type=int, default=3000, help="training intervals of the learned initialiser")
@@ -393,6 +394,18 @@ def run_ours(args):
                             "peak": RL.fp32_peak_tflops(props.multi_processor_count), "unit": "TFLOP/s"}
         mrep["roofline"]["frac"] = mrep["roofline"]["achieved"] / mrep["roofline"]["peak"]
         line["mixed_batch"] = {"workload": "mixed_batch%d" % args.mixed_intervals, **mrep}
+    if rank == 0 and not args.no_drift:
+        # full scale: 197 antennas, 128 channels, 1800 x 1 s (4.45e9 visibilities),
+        # pointing drifting as a random walk, solved every 60 s (30 intervals):
+        # cold batched solves vs warm-started solves in time order
+        from paper_1709_08681_gb300 import drift as DR
+        drep = DR.run(seed=args.seed)
+        props = torch.cuda.get_device_properties(local)
+        drep["roofline"] = {"bound": "alu", "achieved": drep["fused_tflops"],
+                            "peak": RL.fp32_peak_tflops(props.multi_processor_count), "unit": "TFLOP/s"}
+        drep["roofline"]["frac"] = drep["roofline"]["achieved"] / drep["roofline"]["peak"]
+        drep["warm_latency_ms_per_interval"] = 1e3 * drep["warm_sequential_s"] / drep["n_intervals"]
+        line["drift_full"] = {"workload": "drift197_l128ch", **drep}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         vis_host = vis.cpu().numpy()
         w_host = w.cpu().numpy()

@@ -149,6 +149,19 @@ def true_offsets(n_ant: int, sigma_rad: float, seed: int, stream: int = 4) -> np
     return _rng(seed, stream).normal(0.0, sigma_rad, (n_ant, 2))
 
 
+def drifting_offsets(n_ant: int, n_steps: int, sigma_mean_rad: float, step_rad: float, seed: int,
+                     stream: int = 6) -> np.ndarray:
+    """Pointing that drifts: per antenna a mean offset, Gaussian sigma_mean per
+    axis, plus a random walk whose steps (one per solution interval) are
+    Gaussian step_rad per axis; the offset is constant within an interval.
+    Returns [n_steps][n_ant][2] (rad)."""
+    rng = _rng(seed, stream)
+    mean = rng.normal(0.0, sigma_mean_rad, (n_ant, 2))
+    steps = rng.normal(0.0, step_rad, (n_steps, n_ant, 2))
+    steps[0] = 0.0
+    return mean[None] + np.cumsum(steps, axis=0)
+
+
 def complex_noise(shape, sigma: float, seed: int, stream: int = 5) -> np.ndarray:
     """Complex Gaussian noise, real and imaginary parts each N(0, sigma^2)."""
     g = _rng(seed, stream).normal(0.0, sigma, tuple(shape) + (2,))
@@ -243,8 +256,12 @@ def make_workload(name: str, seed: int = 0, **over) -> Workload:
     n_int = r["n_interval"]
     nt = r["n_time"] // n_int
     intervals = [(k * nt, nt) for k in range(n_int)]
-    lm_true = np.stack([true_offsets(r["n_ant"], r["sigma_pt_arcsec"] * ARCSEC, seed, 100 + k)
-                        for k in range(n_int)])
+    if r.get("pointing") == "walk":
+        lm_true = drifting_offsets(r["n_ant"], n_int, r["sigma_pt_arcsec"] * ARCSEC,
+                                   r["walk_arcsec_per_step"] * ARCSEC, seed)
+    else:
+        lm_true = np.stack([true_offsets(r["n_ant"], r["sigma_pt_arcsec"] * ARCSEC, seed, 100 + k)
+                            for k in range(n_int)])
     return Workload(
         name=name, enu_m=enu, uvw_m=uvw, freq_hz=np.asarray(freq, dtype=np.float64), sky=sky,
         image=img, cell_rad=cell, n_grid=r["n_img"] * r["pad"], support=r["support"],
@@ -263,7 +280,18 @@ def make_workload(name: str, seed: int = 0, **over) -> Workload:
 # channel at 1.4 GHz, 60 x 10 s over +-1 h, 50 sources on a 256^2 image at
 # 6"); "vla27_l64ch": the precision-study case (64 channels over 1-2 GHz,
 # 600 x 2 s in 4 solution intervals, 2000 sources on a 2048^2 image).
+# "drift197_l128ch": the full-scale case (197 antennas of 15 m in a random
+# disk of 8 km radius, 128 channels over 0.95-1.76 GHz, 1800 x 1 s, a 4096^2
+# image at 1" padded to 8192^2 with 10^4 sources; pointing = a 30" mean plus
+# a random walk of 2" per minute, solved every 60 s: 30 intervals).
 WORKLOADS = {
+    "drift197_l128ch": dict(
+        layout="disk", n_ant=197, extent_m=8000.0, lat_deg=34.0, dec_deg=30.0,
+        n_time=1800, dt_s=1.0, n_chan=128, f_lo=0.95e9, f_hi=1.76e9,
+        n_src=10000, src_radius_arcmin=30.0, flux=("powerlaw", 1e-4, 1.0, -1.5),
+        n_img=4096, cell_arcsec=1.0, pad=2, support=32, oversample=20,
+        ap_kind="disk", diam_m=15.0, decorrelation=1,
+        sigma_pt_arcsec=30.0, walk_arcsec_per_step=2.0, pointing="walk", noise_jy=1e-3, n_interval=30),
     "disk64_l16ch": dict(
         layout="disk", n_ant=64, extent_m=4000.0, lat_deg=34.0, dec_deg=30.0,
         n_time=60, dt_s=10.0, n_chan=16, f_lo=1.3e9, f_hi=1.5e9,

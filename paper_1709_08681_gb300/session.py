@@ -55,12 +55,25 @@ class Session:
             ctx.psc_predict(lm_per_interval[k], self.vis_slice(out, k))
         return out
 
-    def simulate(self, noise: bool = True, noise_stream: int = 5) -> torch.Tensor:
-        """Observed visibilities at the true offsets plus thermal noise."""
+    def simulate(self, noise: bool = True, noise_stream: int = 5, device_noise=None) -> torch.Tensor:
+        """Observed visibilities at the true offsets plus thermal noise.  The
+        noise comes from ``inputs`` (host, the same numbers on every machine)
+        unless the data are too large to draw on the host (more than 2e8
+        visibilities, or device_noise=True): then from a device generator
+        seeded with (seed, noise_stream), one interval at a time."""
         v = self.predict(self.wl.lm_true)
         if noise and self.wl.sigma_noise > 0:
-            n = torch.from_numpy(self.wl.noise(noise_stream)).to(self.device)
-            v += n
+            if device_noise is None:
+                device_noise = self.wl.n_vis > 200_000_000
+            if not device_noise:
+                v += torch.from_numpy(self.wl.noise(noise_stream)).to(self.device)
+            else:
+                g = torch.Generator(device=self.device)
+                g.manual_seed(int(self.wl.seed) * 1000003 + int(noise_stream))
+                for k in range(len(self.wl.intervals)):
+                    sl = self.vis_slice(v, k)
+                    sl += torch.view_as_complex(torch.randn(sl.shape + (2,), generator=g, device=self.device)
+                                                * self.wl.sigma_noise)
         return v
 
     def close(self):
