@@ -145,7 +145,7 @@ __device__ __forceinline__ void row_taps2(const float2 *__restrict__ row, int n,
                                           float (&qi)[2]) {
     const float2 step = make_float2(-ov, -ov);
     const float2 magic = make_float2(8388608.0f, 8388608.0f);
-#pragma unroll 4
+#pragma unroll 2
     for (int k = 0; k < n; ++k) {
         const float2 g = row[k];
         const float2 s2 = ffma2(dxo, dxo, dyo2);
