@@ -225,6 +225,13 @@ psc_status psc_lm_restart(psc_ctx *ctx);
  * beyond FP32 summation order. */
 psc_status psc_set_tiling(psc_ctx *ctx, int t_tile, int c_group, int vis_per_thread);
 
+/* Measured FP32 FMA throughput of the current device (TFLOP/s, an FMA counted
+ * as 2 flops): eight independent FMA chains per thread on 8 blocks of 256
+ * threads per SM, timed with CUDA events.  A check of the FP32 peak that the
+ * fused kernel's roofline divides by.  Synchronises.  Errors: PSC_ERR_ARG,
+ * PSC_ERR_CUDA (psc_last_error(NULL)). */
+psc_status psc_fp32_fma_rate(double *tflops, void *stream);
+
 /* Grid access of the fused kernel.  PSC_STAGE_AUTO (default): a thread
  * block copies the grid cells its visibilities touch (with the per-cell half
  * of the pointing ramp applied) into shared memory when they fit a 64 x 64

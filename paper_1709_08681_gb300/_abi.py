@@ -26,7 +26,7 @@ STOP_REASONS = {0: "none", 1: "step", 2: "chi2", 3: "lambda", 4: "max_iter", 5: 
 
 EXPORTS = ("psc_solve_opts_default", "psc_model_grid", "psc_create", "psc_destroy", "psc_last_error",
            "psc_predict", "psc_residual_grad", "psc_solve_offsets", "psc_lm_begin", "psc_lm_iterate",
-           "psc_lm_end", "psc_lm_restart", "psc_set_tiling", "psc_set_grid_precision", "psc_set_staging", "psc_profile", "psc_profile_read",
+           "psc_lm_end", "psc_lm_restart", "psc_set_tiling", "psc_set_grid_precision", "psc_set_staging", "psc_fp32_fma_rate", "psc_profile", "psc_profile_read",
            "psc_residual_grad_noalloc", "psc_batch_create", "psc_batch_destroy", "psc_batch_last_error",
            "psc_batch_autotune", "psc_batch_begin", "psc_batch_restart", "psc_batch_iterate", "psc_batch_end",
            "psc_solve_batch", "psc_batch_profile", "psc_batch_profile_read", "psc_features",
@@ -99,6 +99,7 @@ def lib():
             "psc_set_tiling": (ctypes.c_int, [_V, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
             "psc_set_grid_precision": (ctypes.c_int, [_V, ctypes.c_int]),
             "psc_set_staging": (ctypes.c_int, [_V, ctypes.c_int]),
+            "psc_fp32_fma_rate": (ctypes.c_int, [_D, _V]),
             "psc_profile": (ctypes.c_int, [_V, ctypes.c_int]),
             "psc_profile_read": (ctypes.c_int, [_V, _D, ctypes.POINTER(ctypes.c_int)]),
             "psc_residual_grad_noalloc": (ctypes.c_int, [ctypes.POINTER(psc_obs), ctypes.POINTER(psc_aperture),
@@ -390,6 +391,13 @@ class Batch:
         reps = (psc_solve_report * len(self.contexts))()
         _bcheck(lib().psc_batch_end(self.h, _dp(flat), reps), self.h)
         return self._split(flat), list(reps)
+
+
+def psc_fp32_fma_rate(stream=None):
+    """Measured FP32 FMA throughput of the device (TFLOP/s)."""
+    out = np.zeros(1)
+    _check(lib().psc_fp32_fma_rate(_dp(out), _stream(stream)))
+    return float(out[0])
 
 
 def psc_solve_batch(contexts, vis_obs, w=None, w_scale=None, lm0_list=None, opts=None):
