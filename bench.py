@@ -435,6 +435,12 @@ def run_ours(args):
                             "peak": RL.fp32_peak_tflops(props.multi_processor_count), "unit": "TFLOP/s"}
         mrep["roofline"]["frac"] = mrep["roofline"]["achieved"] / mrep["roofline"]["peak"]
         line["mixed_batch"] = {"workload": "mixed_batch%d" % args.mixed_intervals, **mrep}
+    if rank == 0:
+        # two parallel-hand polarisations solved separately: squint and
+        # mechanical offsets of every antenna (4 intervals x 2 polarisations, one batch)
+        from paper_1709_08681_gb300 import squint as SQ
+        srep, _, _ = SQ.run("vla27_l64ch", seed=args.seed)
+        line["squint"] = {"workload": "vla27_l64ch, R and L", **srep}
     if rank == 0 and not args.no_drift:
         # full scale: 197 antennas, 128 channels, 1800 x 1 s (4.45e9 visibilities),
         # pointing drifting as a random walk, solved every 60 s (30 intervals):

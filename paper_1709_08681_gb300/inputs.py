@@ -162,6 +162,19 @@ def drifting_offsets(n_ant: int, n_steps: int, sigma_mean_rad: float, step_rad: 
     return mean[None] + np.cumsum(steps, axis=0)
 
 
+def squinted_offsets(n_ant: int, sigma_mech_rad: float, squint_rad: float, seed: int, stream: int = 7):
+    """Pointing of the two parallel-hand polarisations (R, L) of each antenna:
+    a mechanical offset, Gaussian sigma_mech per axis, and a beam squint of
+    length squint_rad in a random direction per antenna that displaces the R
+    beam by +squint/2 and the L beam by -squint/2.  Returns (mech [n_ant][2],
+    squint [n_ant][2], lm_R, lm_L) in rad."""
+    rng = _rng(seed, stream)
+    mech = rng.normal(0.0, sigma_mech_rad, (n_ant, 2))
+    th = rng.uniform(0.0, 2.0 * math.pi, n_ant)
+    sq = squint_rad * np.stack([np.cos(th), np.sin(th)], axis=1)
+    return mech, sq, mech + 0.5 * sq, mech - 0.5 * sq
+
+
 def complex_noise(shape, sigma: float, seed: int, stream: int = 5) -> np.ndarray:
     """Complex Gaussian noise, real and imaginary parts each N(0, sigma^2)."""
     g = _rng(seed, stream).normal(0.0, sigma, tuple(shape) + (2,))
