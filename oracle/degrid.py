@@ -1,8 +1,9 @@
 """Oracle: ctypes front of ``degrid.c`` (FP64 degridding sums).
 
 Test infrastructure only (see ``oracle/__init__``).  ``build()`` compiles the
-C file with the host gcc (portable C99, no intrinsics) into ``oracle/_bin``;
-the first call builds it if it is missing or older than its source.
+oracle's C files (``degrid.c``, ``exact.c``) with the host gcc (portable C99,
+no intrinsics) into one library in ``oracle/_bin``; the first call builds it
+if it is missing or older than a source.
 """
 from __future__ import annotations
 
@@ -13,7 +14,7 @@ import subprocess
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "degrid.c")
+_SRCS = [os.path.join(_HERE, "degrid.c"), os.path.join(_HERE, "exact.c")]
 _BIN = os.path.join(_HERE, "_bin")
 _SO = os.path.join(_BIN, "liboracle_degrid.so")
 _lib = None
@@ -21,10 +22,10 @@ _lib = None
 
 def build(force: bool = False) -> str:
     os.makedirs(_BIN, exist_ok=True)
-    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+    if force or not os.path.exists(_SO) or any(os.path.getmtime(_SO) < os.path.getmtime(f) for f in _SRCS):
         tmp = _SO + ".%d.tmp" % os.getpid()
         subprocess.check_call(["gcc", "-O2", "-std=c99", "-fopenmp", "-fPIC", "-shared",
-                               _SRC, "-o", tmp, "-lm"])
+                               *_SRCS, "-o", tmp, "-lm"])
         os.replace(tmp, _SO)
     return _SO
 
@@ -39,6 +40,11 @@ def _load():
         lib.oracle_degrid.argtypes = [ctypes.c_long, d, d, d, d, i, d, lp, i, ctypes.c_int,
                                       d, ctypes.c_int, ctypes.c_double, ctypes.c_int, d, d, d]
         lib.oracle_degrid.restype = None
+        lib.oracle_exact_overlap.argtypes = [ctypes.c_long, d, d, d, ctypes.c_double, d, d, d]
+        lib.oracle_exact_overlap.restype = None
+        lib.oracle_exact_degrid.argtypes = [ctypes.c_long, d, d, d, d, d, d, d, i, ctypes.c_int, d,
+                                            ctypes.c_int, ctypes.c_double, ctypes.c_int, d, d, d, d, d]
+        lib.oracle_exact_degrid.restype = None
         _lib = lib
     return _lib
 

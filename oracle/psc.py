@@ -20,6 +20,10 @@ blocks are the Gauss-Newton ones, H_pq = 2 sum w Re(conj(dV/dp) dV/dq), for
 p, q in {l_a, m_a} of one antenna a.  alpha scales with frequency as
 alpha = alpha_per_dlambda * D nu / c.  With ``decorrelation = 0`` the bracketed
 amplitude factor of Eq. AIJPOINTING is dropped and so is its derivative term.
+With ``kernel = "exact"`` (uniform disks only) the kernel is the exact
+transform of the two shifted disk patterns' product (``oracle/exact``), which
+carries the amplitude's dependence on l_i - l_j itself; ``decorrelation`` is
+then not used.
 """
 from __future__ import annotations
 
@@ -30,6 +34,7 @@ import numpy as np
 
 from . import aperture
 from .degrid import degrid_sums
+from .exact import degrid_sums_exact
 
 C_LIGHT = 299_792_458.0
 
@@ -48,6 +53,7 @@ class Model:
     diam_m: float
     alpha_per_dlambda: float
     decorrelation: int
+    kernel: str = "gauss"      # "gauss": Eq. AIJPOINTING; "exact": the disks' exact kernel
 
     @property
     def du(self) -> float:
@@ -87,6 +93,10 @@ def predict(model: Model, lm: np.ndarray, with_derivs: bool = True):
     L = np.broadcast_to((li + lj)[None, :, None], shape)
     M = np.broadcast_to((mi + mj)[None, :, None], shape)
     chan = np.broadcast_to(np.arange(nc)[None, None, :], shape)
+    if model.kernel == "exact":
+        dlx = np.broadcast_to((li - lj)[None, :, None], shape)
+        dly = np.broadcast_to((mi - mj)[None, :, None], shape)
+        return _exact_out(model, u, v, L, M, dlx, dly, chan, with_derivs)
     t0, tu, tv = degrid_sums(u, v, L, M, chan, model.tables(), model.grid, model.du,
                              model.support, model.oversample)
     a2 = (model.alpha() ** 2)[None, None, :]
@@ -110,6 +120,22 @@ def predict(model: Model, lm: np.ndarray, with_derivs: bool = True):
     return V, dV
 
 
+def _exact_out(model: Model, u, v, L, M, dlx, dly, chan, with_derivs):
+    """V and dV with the exact disk kernel: V = T0, dV/dl_i = TX + i pi Tu,
+    dV/dl_j = -TX + i pi Tu (m likewise with TY, Tv)."""
+    if model.ap_kind != "disk":
+        raise ValueError("the exact kernel is defined for uniform disks")
+    dl = aperture.d_lambda(model.diam_m, model.freq_hz)
+    lens = np.asarray([aperture.table_len("disk", d, model.du, model.oversample, model.support) for d in dl])
+    chan = np.asarray(chan)
+    t0, tu, tv, tx, ty = degrid_sums_exact(u, v, L, M, dlx, dly, 0.5 * dl[chan], lens[chan], model.grid,
+                                           model.du, model.support, model.oversample)
+    if not with_derivs:
+        return t0, None
+    ipi = 1j * math.pi
+    return t0, np.stack([tx + ipi * tu, ty + ipi * tv, -tx + ipi * tu, -ty + ipi * tv])
+
+
 def predict_points(model: Model, lm, t_idx, bl_idx, ch_idx):
     """V and dV (dV/dl_i, dV/dm_i, dV/dl_j, dV/dm_j) of selected visibilities
     (index arrays into [nt][nbl][nc]), by the same formulas as ``predict``."""
@@ -121,6 +147,8 @@ def predict_points(model: Model, lm, t_idx, bl_idx, ch_idx):
     f = np.asarray(model.freq_hz, dtype=np.float64)[ch_idx] / C_LIGHT
     u = model.uvw_m[t_idx, bl_idx, 0] * f
     v = model.uvw_m[t_idx, bl_idx, 1] * f
+    if model.kernel == "exact":
+        return _exact_out(model, u, v, li + lj, mi + mj, li - lj, mi - mj, ch_idx, True)
     t0, tu, tv = degrid_sums(u, v, li + lj, mi + mj, ch_idx, model.tables(), model.grid, model.du,
                              model.support, model.oversample)
     a2 = model.alpha()[ch_idx] ** 2
