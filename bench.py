@@ -53,6 +53,7 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     p.add_argument("--no-learned", action="store_true", help="skip the learned-initialiser comparison")
     p.add_argument("--no-drift", action="store_true", help="skip the full-scale drifting-pointing section")
+    p.add_argument("--no-exact", action="store_true", help="skip the exact-disk-kernel section")
     p.add_argument("--mixed-intervals", type=int, default=256,
                    help="intervals of the mixed-array batched-solve section (0 skips it)")
     p.add_argument("--learned-train", type=int, default=3000, help="training intervals of the learned initialiser")
@@ -441,6 +442,12 @@ def run_ours(args):
         from paper_1709_08681_gb300 import squint as SQ
         srep, _, _ = SQ.run("vla27_l64ch", seed=args.seed)
         line["squint"] = {"workload": "vla27_l64ch, R and L", **srep}
+    if rank == 0 and not args.no_exact:
+        # the exact disk kernel (two shifted disk patterns' product) in place of
+        # the Gaussian decorrelation model: throughput of its fused evaluation
+        # and its solutions against the Gaussian model's, on data it simulates
+        from paper_1709_08681_gb300 import exact_kernel as EK
+        line["exact_kernel"] = {"workload": "vla27_l64ch, offsets sigma 60\"", **EK.run("vla27_l64ch", seed=args.seed)}
     if rank == 0 and not args.no_drift:
         # full scale: 197 antennas, 128 channels, 1800 x 1 s (4.45e9 visibilities),
         # pointing drifting as a random walk, solved every 60 s (30 intervals):

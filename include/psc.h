@@ -60,6 +60,7 @@ typedef enum {
 enum { PSC_AP_DISK = 0, PSC_AP_GAUSS = 1 };
 enum { PSC_GRID_F32 = 0, PSC_GRID_BF16 = 1 };
 enum { PSC_STAGE_AUTO = 0, PSC_STAGE_NEVER = 1 };
+enum { PSC_KERNEL_GAUSS = 0, PSC_KERNEL_EXACT_DISK = 1 };
 enum { PSC_LM_FULL = 0, PSC_LM_BLOCK = 1 };
 enum { PSC_STOP_NONE = 0, PSC_STOP_STEP = 1, PSC_STOP_CHI2 = 2, PSC_STOP_LAMBDA = 3,
        PSC_STOP_MAX_ITER = 4, PSC_STOP_NUMERIC = 5 };
@@ -240,6 +241,35 @@ psc_status psc_fp32_fma_rate(double *tflops, void *stream);
  * a brick's visibilities share few cells).  Results are the same up to FP32
  * summation order.  Errors: PSC_ERR_ARG for an unknown mode. */
 psc_status psc_set_staging(psc_ctx *ctx, int mode);
+
+/* Aperture kernel model of psc_predict, psc_residual_grad, psc_lm_* and
+ * psc_solve_offsets on this context.
+ *
+ * PSC_KERNEL_GAUSS (default): Eq. AIJPOINTING -- A° times the Gaussian
+ * decorrelation factor exp(-alpha^2 |l_i - l_j|^2 / 2) (dropped when the
+ * aperture's decorrelation is 0) times the phase ramp exp(i pi du.(l_i+l_j)).
+ *
+ * PSC_KERNEL_EXACT_DISK (uniform-disk apertures only): the exact transform of
+ * the product of the two antennas' disk patterns, each shifted by its offset
+ * (Sec. 3: a more accurate pattern in place of the Gaussian main lobe):
+ *   A_ij(du) = exp(i pi du.(l_i + l_j)) O(du; l_i - l_j) / (pi R^2)^2,
+ *   O = integral of cos(2 pi w.(l_i - l_j)) over the lens where the two
+ *       apertures of radius R = D_lambda / 2, centred du apart, overlap,
+ * with its exact derivatives.  At l_i = l_j it equals A° times the ramp.  The
+ * GPU evaluates O by its Taylor series in (2 pi w.(l_i - l_j)) up to the 6th
+ * power, from per-channel lens moments computed once (FP64 quadrature) by this
+ * call: with x = pi D_lambda |l_i - l_j| the relative truncation error is at
+ * most x^8/8! for O and x^6/(7!/8) for its derivative (1e-7 at x = 0.3, i.e.
+ * 2 arcmin of offset difference for a 25 m dish at 1.5 GHz), growing fast
+ * beyond x = 1.  It runs one visibility per thread (the tiling's
+ * vis_per_thread becomes 1; psc_set_tiling refuses 2), reads the FP32 grid
+ * (not the BF16 copy) and the FP64 uvw.  Batches (psc_batch_create,
+ * psc_solve_batch) refuse contexts in this mode; psc_features and the
+ * learned initialiser keep the Gaussian model.
+ *
+ * Errors: PSC_ERR_ARG (unknown model, non-disk aperture, aperture table too
+ * long for shared memory), PSC_ERR_CUDA / PSC_ERR_OOM (moment tables). */
+psc_status psc_set_kernel_model(psc_ctx *ctx, int model);
 
 /* Storage precision of the model grid V° that the fused evaluation reads
  * (psc_predict, psc_residual_grad, the solvers and batches; the feature pass

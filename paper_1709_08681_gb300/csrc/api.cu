@@ -47,6 +47,10 @@ struct psc_ctx {
     int t_tile = 32, c_group = 4;
     int kv = 1;                  // visibilities per thread at consecutive times
     int no_stage = 0;            // PSC_STAGE_NEVER: taps read the grid from global memory
+    int kernel_model = PSC_KERNEL_GAUSS;
+    float *d_kmom = nullptr;     // exact disk kernel: lens-moment combinations (psc_set_kernel_model)
+    std::vector<double> h_freq;  // channel frequencies (Hz)
+    std::vector<int> h_tab_off, h_tab_len;   // radial table layout per channel
     double step_cells = 0.0;     // largest move of a baseline between time steps (cells, top channel)
     bool multi_ok = false;       // kv > 1 allowed: every channel's aperture fits inside the S x S window
     LMState h_state{};
@@ -102,6 +106,7 @@ void free_ctx(psc_ctx *c) {
     if (!c) return;
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     cudaFree(c->d_grid_bf16);
+    cudaFree(c->d_kmom);
     cudaFree(c->d_uvs);
     cudaFree(c->d_spart);
     cudaFree(c->d_sblsum);
@@ -175,6 +180,8 @@ EvalArgs eval_args(const psc_ctx *c, const double *lm_dev) {
     a.max_tab_len = c->max_tab_len;
     a.tab_stride = tab_stride(c, c->kv);
     a.n_bricks = (long long)c->n_bl * n_cg(c) * n_tt(c);
+    a.exact = c->kernel_model == PSC_KERNEL_EXACT_DISK;
+    a.kmom = c->d_kmom;
     return a;
 }
 
@@ -331,6 +338,9 @@ psc_status psc_create(psc_ctx **out, const psc_obs *obs, const psc_aperture *ap,
         total += L;
         if (L > c->max_tab_len) c->max_tab_len = L;
     }
+    c->h_freq.assign(obs->freq_hz, obs->freq_hz + c->nc);
+    c->h_tab_off = off;
+    c->h_tab_len = len;
     std::vector<int2> pairs;
     pairs.reserve(c->n_bl);
     for (int i = 0; i < c->n_ant; ++i)
@@ -414,6 +424,8 @@ psc_status psc_set_tiling(psc_ctx *ctx, int t_tile, int c_group, int vis_per_thr
     const int cg = c_group ? c_group : ctx->c_group;
     const int kv = vis_per_thread ? vis_per_thread : ctx->kv;
     if (!(kv == 1 || kv == 2)) return fail(ctx, PSC_ERR_ARG, "vis_per_thread must be 1 or 2");
+    if (kv != 1 && ctx->kernel_model == PSC_KERNEL_EXACT_DISK)
+        return fail(ctx, PSC_ERR_ARG, "the exact disk kernel takes one visibility per thread");
     if (!kv_allowed(ctx, kv))
         return fail(ctx, PSC_ERR_ARG, "vis_per_thread 2 needs the aperture inside the S x S window and "
                                       "consecutive time steps within 4 cells");
@@ -423,6 +435,49 @@ psc_status psc_set_tiling(psc_ctx *ctx, int t_tile, int c_group, int vis_per_thr
     ctx->t_tile = tt;
     ctx->c_group = cg;
     ctx->kv = kv;
+    return PSC_OK;
+}
+
+psc_status psc_set_kernel_model(psc_ctx *ctx, int model) {
+    if (!ctx) return fail(nullptr, PSC_ERR_ARG, "ctx is NULL");
+    if (model == PSC_KERNEL_GAUSS) {
+        ctx->kernel_model = model;
+        return PSC_OK;
+    }
+    if (model != PSC_KERNEL_EXACT_DISK) return fail(ctx, PSC_ERR_ARG, "model must be PSC_KERNEL_GAUSS or PSC_KERNEL_EXACT_DISK");
+    if (ctx->ap.kind != PSC_AP_DISK) return fail(ctx, PSC_ERR_ARG, "the exact kernel needs a uniform-disk aperture");
+    int dev = 0, optin = 0;
+    PSC_CUDA(ctx, cudaGetDevice(&dev));
+    PSC_CUDA(ctx, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    if (exact_dyn_smem(1, ctx->max_tab_len + 2) + (size_t)kTile * kTile * sizeof(float2) + 4096 > (size_t)optin)
+        return fail(ctx, PSC_ERR_ARG, "aperture table too long for the exact kernel's shared memory");
+    if (!ctx->d_kmom) {
+        const int nc = ctx->nc;
+        const size_t total = (size_t)ctx->h_tab_off[nc - 1] + ctx->h_tab_len[nc - 1];
+        double *d_freq = nullptr;
+        int *d_off = nullptr, *d_len = nullptr;
+        cudaError_t e = dalloc(&ctx->d_kmom, total * 10);
+        if (e == cudaSuccess) e = dalloc(&d_freq, nc);
+        if (e == cudaSuccess) e = dalloc(&d_off, nc);
+        if (e == cudaSuccess) e = dalloc(&d_len, nc);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(d_freq, ctx->h_freq.data(), sizeof(double) * nc, cudaMemcpyHostToDevice, ctx->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(d_off, ctx->h_tab_off.data(), sizeof(int) * nc, cudaMemcpyHostToDevice, ctx->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(d_len, ctx->h_tab_len.data(), sizeof(int) * nc, cudaMemcpyHostToDevice, ctx->stream);
+        if (e == cudaSuccess)
+            e = launch_exact_moments(ctx->ap.diam_m, d_freq, nc, ctx->du, ctx->gd.oversample, d_off, d_len, ctx->d_kmom,
+                                     ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        cudaFree(d_freq);
+        cudaFree(d_off);
+        cudaFree(d_len);
+        if (e != cudaSuccess) {
+            cudaFree(ctx->d_kmom);
+            ctx->d_kmom = nullptr;
+            return cuda_fail(ctx, e, "psc_set_kernel_model");
+        }
+    }
+    ctx->kernel_model = model;
+    ctx->kv = 1;
     return PSC_OK;
 }
 
@@ -928,6 +983,10 @@ psc_status psc_batch_create(psc_batch **out, psc_ctx *const *ctxs, int n_ctx, co
         if (!(ws > 0.0) || !std::isfinite(ws)) { free_batch(b); return fail(nullptr, PSC_ERR_ARG, "w_scale must be > 0"); }
         for (int j = 0; j < k; ++j)
             if (ctxs[j] == ctxs[k]) { free_batch(b); return fail(nullptr, PSC_ERR_ARG, "a context appears twice in the batch"); }
+        if (ctxs[k]->kernel_model != PSC_KERNEL_GAUSS) {
+            free_batch(b);
+            return fail(nullptr, PSC_ERR_ARG, "batches take contexts with the Gaussian kernel model only");
+        }
         b->ctxs.push_back(ctxs[k]);
         b->vis.push_back(vis_obs[k]);
         b->w.push_back(w ? w[k] : nullptr);

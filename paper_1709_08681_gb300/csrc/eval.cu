@@ -729,6 +729,7 @@ size_t eval_dyn_smem(int c_group, int tab_stride) {
 }
 
 cudaError_t launch_eval(const EvalArgs &a, bool predict, cudaStream_t s) {
+    if (a.exact) return launch_exact(a, predict, s);
     const int threads = (a.t_tile * a.c_group + 31) / 32 * 32;
     const int blocks = (int)a.n_bricks;
     const size_t dyn = eval_dyn_smem(a.c_group, a.tab_stride);

@@ -49,6 +49,8 @@ struct EvalArgs {
     int max_tab_len;           // longest table among the channels
     int tab_stride;            // staged entries per channel: max_tab_len + zero padding
     long long n_bricks;        // n_bl * n_cg * n_tt (partials are [kRed][n_bricks])
+    const float *kmom;         // exact disk kernel: [table entries][10] lens-moment combinations
+    int exact;                 // 1: exact disk kernel (exact.cu) instead of Eq. AIJPOINTING's
 };
 
 // Arguments of the stencil-feature kernel (learned initial estimate).
@@ -128,6 +130,14 @@ size_t lm_smem_bytes(int n_ant);
 cudaError_t lm_prepare(int n_ant);
 cudaError_t launch_lm_restart(const LMArgs &a, const LMState *st0, const double *lm0, cudaStream_t s);
 cudaError_t set_eval_smem(size_t dyn);
+// Exact disk kernel (exact.cu): the fused evaluation with it (one launch per
+// context, one visibility per thread), its dynamic shared memory, and the
+// per-channel lens-moment combinations ([sum of table lengths][10] floats)
+// it reads, computed once per context.
+cudaError_t launch_exact(const EvalArgs &a, bool predict, cudaStream_t s);
+size_t exact_dyn_smem(int c_group, int tab_stride);
+cudaError_t launch_exact_moments(double diam_m, const double *freq_dev, int nc, double du, int ov,
+                                 const int *tab_off_dev, const int *tab_len_dev, float *kmom, cudaStream_t s);
 // Dynamic shared memory of one fused-kernel block (c_group zero-padded tables).
 size_t eval_dyn_smem(int c_group, int tab_stride);
 // Largest distance (metres, u-v plane) between the baselines of consecutive

@@ -14,6 +14,12 @@ import math
 import numpy as np
 
 FLOPS_PER_TAP = 15
+# Exact disk kernel (exact.cu), per tap: s (2), square root (1), seven
+# interpolated series coefficients (14), 1 / s (1), (dl.du)/|du|^2 (1),
+# A = (dl.e)^2 (1), O (6), dO/dA (6), dO/ds (4), its product with
+# (dl.du)/|du|^2 (1), O dx and W dx (2), five complex accumulations (20), the
+# two per-tap steps (2).
+FLOPS_PER_TAP_EXACT = 61
 FP32_LANES_PER_SM = 128
 C_LIGHT = 299_792_458.0
 
