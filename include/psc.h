@@ -226,6 +226,20 @@ psc_status psc_lm_restart(psc_ctx *ctx);
  * beyond FP32 summation order. */
 psc_status psc_set_tiling(psc_ctx *ctx, int t_tile, int c_group, int vis_per_thread);
 
+/* Flat bricks: the fused kernel's work items of a baseline are its (channel,
+ * group of vis_per_thread consecutive time steps) pairs in channel-major
+ * order, and a thread block takes `items` consecutive ones (one per thread),
+ * so only the baseline's last block has idle lanes -- unlike the (t_tile x
+ * c_group) blocks of psc_set_tiling, which idle whole warps when t_tile *
+ * c_group falls short of a multiple of 32 and when the channel or time count
+ * is not a multiple of the group.  A block may then span several channels
+ * (at most 8).  items in {32, 64, ..., 256}; vis_per_thread as for
+ * psc_set_tiling.  psc_set_tiling switches back.  Gaussian kernel model only
+ * (PSC_ERR_ARG under PSC_KERNEL_EXACT_DISK, which also resets this).  Errors:
+ * PSC_ERR_ARG for out-of-range values or a brick spanning more than 8
+ * channels (fewer time steps per channel than items / 7). */
+psc_status psc_set_flat_tiling(psc_ctx *ctx, int items, int vis_per_thread);
+
 /* Measured FP32 FMA throughput of the current device (TFLOP/s, an FMA counted
  * as 2 flops): eight independent FMA chains per thread on 8 blocks of 256
  * threads per SM, timed with CUDA events.  A check of the FP32 peak that the
@@ -364,14 +378,16 @@ const char *psc_batch_last_error(const psc_batch *b);
  * data: for blocks of 128 and 256 threads and vis_per_thread 1 and (where
  * psc_set_tiling accepts it) 2, the three channel groups whose smallest
  * fitting time tile leaves the fewest lanes idle (ragged time and channel
- * tails count as idle), plus (32, 4, 1); the fastest is kept, then contexts
+ * tails count as idle), plus (32, 4, 1), plus flat bricks of 64, 128, 192
+ * and 256 items (psc_set_flat_tiling); the fastest is kept, then contexts
  * narrower than the widest choice take their fastest shape of that width (one
  * block size serves the persistent launch); the winner is also timed with
  * PSC_STAGE_NEVER and the faster grid access kept.  Contexts of the same
  * array, channels and grid reuse the first one's choice, with the time tile
- * refitted to their own length.  Writes the chosen (t_tile, c_group,
- * vis_per_thread, staging mode) of context k to tiling_out[4k..4k+3] (NULL to
- * skip).  Synchronises. */
+ * refitted to their own length (flat bricks need no refit).  Writes the chosen
+ * (t_tile, c_group, vis_per_thread, staging mode) of context k to
+ * tiling_out[4k..4k+3] (NULL to skip); flat bricks are written as (items, 0,
+ * vis_per_thread, staging mode).  Synchronises. */
 psc_status psc_batch_autotune(psc_batch *b, int *tiling_out);
 
 /* Start (host offsets, options as for psc_lm_begin), restart on the device,

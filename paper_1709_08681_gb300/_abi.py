@@ -28,7 +28,7 @@ STOP_REASONS = {0: "none", 1: "step", 2: "chi2", 3: "lambda", 4: "max_iter", 5: 
 EXPORTS = ("psc_solve_opts_default", "psc_model_grid", "psc_create", "psc_destroy", "psc_last_error",
            "psc_predict", "psc_residual_grad", "psc_solve_offsets", "psc_lm_begin", "psc_lm_iterate",
            "psc_lm_end", "psc_lm_restart", "psc_set_tiling", "psc_set_grid_precision", "psc_set_staging",
-           "psc_set_kernel_model", "psc_fp32_fma_rate", "psc_profile", "psc_profile_read",
+           "psc_set_kernel_model", "psc_set_flat_tiling", "psc_fp32_fma_rate", "psc_profile", "psc_profile_read",
            "psc_residual_grad_noalloc", "psc_batch_create", "psc_batch_destroy", "psc_batch_last_error",
            "psc_batch_autotune", "psc_batch_begin", "psc_batch_restart", "psc_batch_iterate", "psc_batch_end",
            "psc_solve_batch", "psc_batch_profile", "psc_batch_profile_read", "psc_features",
@@ -102,6 +102,7 @@ def lib():
             "psc_set_grid_precision": (ctypes.c_int, [_V, ctypes.c_int]),
             "psc_set_staging": (ctypes.c_int, [_V, ctypes.c_int]),
             "psc_set_kernel_model": (ctypes.c_int, [_V, ctypes.c_int]),
+            "psc_set_flat_tiling": (ctypes.c_int, [_V, ctypes.c_int, ctypes.c_int]),
             "psc_fp32_fma_rate": (ctypes.c_int, [_D, _V]),
             "psc_profile": (ctypes.c_int, [_V, ctypes.c_int]),
             "psc_profile_read": (ctypes.c_int, [_V, _D, ctypes.POINTER(ctypes.c_int)]),
@@ -242,6 +243,9 @@ class Context:
 
     def psc_set_staging(self, mode):
         _check(lib().psc_set_staging(self.h, int(mode)), self.h)
+
+    def psc_set_flat_tiling(self, items, vis_per_thread):
+        _check(lib().psc_set_flat_tiling(self.h, int(items), int(vis_per_thread)), self.h)
 
     def psc_set_kernel_model(self, model):
         _check(lib().psc_set_kernel_model(self.h, int(model)), self.h)

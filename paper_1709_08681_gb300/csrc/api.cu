@@ -46,6 +46,7 @@ struct psc_ctx {
     int max_tab_len = 0;
     int t_tile = 32, c_group = 4;
     int kv = 1;                  // visibilities per thread at consecutive times
+    int flat = 0;                // > 0: bricks of `flat` consecutive (channel, time-group) items
     int no_stage = 0;            // PSC_STAGE_NEVER: taps read the grid from global memory
     int kernel_model = PSC_KERNEL_GAUSS;
     float *d_kmom = nullptr;     // exact disk kernel: lens-moment combinations (psc_set_kernel_model)
@@ -139,9 +140,21 @@ int tab_stride(const psc_ctx *c, int kv) {
     return c->max_tab_len + (int)std::ceil(c->gd.oversample * (kv_spread(c, kv) + 1.0)) + 2;
 }
 int n_cg(const psc_ctx *c) { return (c->nc + c->c_group - 1) / c->c_group; }
+// Flat bricks: groups of kv consecutive time steps per channel, the bricks
+// per baseline, and the most channels one brick's items can span.
+int n_tp(const psc_ctx *c) { return (c->nt + c->kv - 1) / c->kv; }
+long long bricks_per_bl(const psc_ctx *c) {
+    if (c->flat > 0) return ((long long)c->nc * n_tp(c) + c->flat - 1) / c->flat;
+    return (long long)n_cg(c) * n_tt(c);
+}
+int ch_span(const psc_ctx *c) {
+    return c->flat > 0 ? std::min(c->nc, (c->flat + n_tp(c) - 2) / n_tp(c) + 1) : c->c_group;
+}
+// Block width of the fused kernel for this context's bricks.
+int eval_threads(const psc_ctx *c) { return ((c->flat > 0 ? c->flat : c->t_tile * c->c_group) + 31) / 32 * 32; }
 
 psc_status ensure_partials(psc_ctx *c) {
-    const size_t need = (size_t)c->n_bl * n_cg(c) * n_tt(c);
+    const size_t need = (size_t)c->n_bl * bricks_per_bl(c);
     if (need <= c->partials_cap) return PSC_OK;
     cudaFree(c->d_partials);
     c->d_partials = nullptr;
@@ -179,7 +192,11 @@ EvalArgs eval_args(const psc_ctx *c, const double *lm_dev) {
     a.decorrelation = c->ap.decorrelation;
     a.max_tab_len = c->max_tab_len;
     a.tab_stride = tab_stride(c, c->kv);
-    a.n_bricks = (long long)c->n_bl * n_cg(c) * n_tt(c);
+    a.n_bricks = (long long)c->n_bl * bricks_per_bl(c);
+    a.flat = c->flat;
+    a.n_tp = n_tp(c);
+    a.bpb = (int)bricks_per_bl(c);
+    a.ch_span = ch_span(c);
     a.exact = c->kernel_model == PSC_KERNEL_EXACT_DISK;
     a.kmom = c->d_kmom;
     return a;
@@ -192,7 +209,7 @@ RedArgs red_args(const psc_ctx *c, double *ev_out, const int *skip) {
     r.ev = ev_out;
     r.skip = skip;
     r.n_bl = c->n_bl;
-    r.bpb = n_cg(c) * n_tt(c);
+    r.bpb = (int)bricks_per_bl(c);
     r.n_ant = c->n_ant;
     return r;
 }
@@ -435,6 +452,26 @@ psc_status psc_set_tiling(psc_ctx *ctx, int t_tile, int c_group, int vis_per_thr
     ctx->t_tile = tt;
     ctx->c_group = cg;
     ctx->kv = kv;
+    ctx->flat = 0;
+    return PSC_OK;
+}
+
+psc_status psc_set_flat_tiling(psc_ctx *ctx, int items, int vis_per_thread) {
+    if (!ctx) return fail(nullptr, PSC_ERR_ARG, "ctx is NULL");
+    if (ctx->kernel_model != PSC_KERNEL_GAUSS) return fail(ctx, PSC_ERR_ARG, "flat bricks serve the Gaussian kernel model only");
+    if (items < 32 || items > kMaxThreads || items % 32) return fail(ctx, PSC_ERR_ARG, "items must be 32, 64, ..., 256");
+    if (!(vis_per_thread == 1 || vis_per_thread == 2)) return fail(ctx, PSC_ERR_ARG, "vis_per_thread must be 1 or 2");
+    if (!kv_allowed(ctx, vis_per_thread))
+        return fail(ctx, PSC_ERR_ARG, "vis_per_thread 2 needs the aperture inside the S x S window and "
+                                      "consecutive time steps within 4 cells");
+    const int old_kv = ctx->kv, old_flat = ctx->flat;
+    ctx->kv = vis_per_thread;
+    ctx->flat = items;
+    if (ch_span(ctx) > 8) {
+        ctx->kv = old_kv;
+        ctx->flat = old_flat;
+        return fail(ctx, PSC_ERR_ARG, "a brick would span more than 8 channels (too few time steps per channel)");
+    }
     return PSC_OK;
 }
 
@@ -478,6 +515,7 @@ psc_status psc_set_kernel_model(psc_ctx *ctx, int model) {
     }
     ctx->kernel_model = model;
     ctx->kv = 1;
+    ctx->flat = 0;
     return PSC_OK;
 }
 
@@ -821,7 +859,7 @@ psc_status build_tables(psc_batch *b) {
     int threads = 32;
     for (int k = 0; k < n; ++k) {
         psc_ctx *c = b->ctxs[k];
-        threads = std::max(threads, (c->t_tile * c->c_group + 31) / 32 * 32);
+        threads = std::max(threads, eval_threads(c));
         psc_status st = ensure_partials(c);
         if (st != PSC_OK) return bfail(b, st, c->err);
         ev[k] = eval_args(c, c->d_lm_trial);
@@ -835,7 +873,7 @@ psc_status build_tables(psc_batch *b) {
         lm[k] = lm_args(c);
         st0[k] = c->d_state0;
         lm0[k] = c->d_lm0;
-        dyn = std::max(dyn, eval_dyn_smem(c->c_group, tab_stride(c, c->kv)));
+        dyn = std::max(dyn, eval_dyn_smem(ch_span(c), tab_stride(c, c->kv)));
         lmd = std::max(lmd, lm_smem_bytes(c->n_ant));
     }
     b->total_bl = blp[n];
@@ -934,8 +972,23 @@ int fit_t_tile(int nt, int threads, int cg, int kv) {
 // fewest tiles that fit the block; ranked by the share of the block's lanes
 // that hold a visibility (ragged time and channel tails and idle lanes count
 // as waste), the best three of each (block size, vis_per_thread).
-std::vector<std::array<int, 3>> tiling_candidates(const psc_ctx *c) {
-    struct Scored { double util; int threads; std::array<int, 3> t; };
+// A brick shape: {t_tile, c_group, kv, flat} (flat > 0: bricks of `flat`
+// consecutive (channel, time-group) items; t_tile and c_group unused).
+using Tiling = std::array<int, 4>;
+
+void apply_tiling(psc_ctx *c, const Tiling &t) {
+    if (t[3] > 0) {
+        c->flat = t[3];
+    } else {
+        c->t_tile = t[0];
+        c->c_group = t[1];
+        c->flat = 0;
+    }
+    c->kv = t[2];
+}
+
+std::vector<Tiling> tiling_candidates(const psc_ctx *c) {
+    struct Scored { double util; int threads; Tiling t; };
     std::vector<Scored> all;
     for (int threads : {128, 256}) {
         for (int kv : {1, 2}) {
@@ -948,12 +1001,12 @@ std::vector<std::array<int, 3>> tiling_candidates(const psc_ctx *c) {
                 const int n_cg = (c->nc + cg - 1) / cg;
                 const double util = (double)c->nt / ((double)n_tt * tt * kv) * (double)c->nc / ((double)n_cg * cg) *
                                     (double)(tt * cg) / threads;
-                all.push_back({util, threads, {tt, cg, kv}});
+                all.push_back({util, threads, {tt, cg, kv, 0}});
             }
         }
     }
     std::sort(all.begin(), all.end(), [](const Scored &x, const Scored &y) { return x.util > y.util; });
-    std::vector<std::array<int, 3>> out;
+    std::vector<Tiling> out;
     int taken[2][3] = {{0, 0, 0}, {0, 0, 0}};
     for (const Scored &x : all) {
         int &n = taken[x.threads == 256][x.t[2]];
@@ -961,8 +1014,15 @@ std::vector<std::array<int, 3>> tiling_candidates(const psc_ctx *c) {
         ++n;
         out.push_back(x.t);
     }
-    const std::array<int, 3> dflt{32, 4, 1};
+    const Tiling dflt{32, 4, 1, 0};
     if (std::find(out.begin(), out.end(), dflt) == out.end()) out.push_back(dflt);
+    // flat bricks: every lane but the last brick's tail holds an item
+    for (int items : {64, 128, 192, 256})
+        for (int kv : {1, 2}) {
+            if (!kv_allowed(c, kv)) continue;
+            const int tp = (c->nt + kv - 1) / kv;
+            if (std::min(c->nc, (items + tp - 2) / tp + 1) <= 8) out.push_back({0, 0, kv, items});
+        }
     return out;
 }
 
@@ -1009,8 +1069,24 @@ psc_status psc_batch_autotune(psc_batch *b, int *tiling_out) {
     PSC_BCUDA(b, cudaEventCreate(&e1));
     const int n = (int)b->ctxs.size();
     std::vector<double> zeros;
-    std::vector<std::vector<std::pair<float, std::array<int, 3>>>> timed(n);
+    std::vector<std::vector<std::pair<float, Tiling>>> timed(n);
     std::vector<int> reused(n, -1);
+    auto time_eval = [&](psc_ctx *c, int k, float *ms) -> psc_status {
+        psc_status st = ensure_partials(c);
+        if (st != PSC_OK) return bfail(b, st, c->err);
+        PSC_BCUDA(b, set_eval_smem(eval_dyn_smem(ch_span(c), tab_stride(c, c->kv))));
+        EvalArgs a = eval_args(c, c->d_lm_trial);
+        a.vis_obs = (const float2 *)b->vis[k];
+        a.w = b->w[k];
+        a.w_scale = (float)b->w_scale[k];
+        PSC_BCUDA(b, launch_eval(a, false, b->stream));          // warm
+        PSC_BCUDA(b, cudaEventRecord(e0, b->stream));
+        for (int r = 0; r < 3; ++r) PSC_BCUDA(b, launch_eval(a, false, b->stream));
+        PSC_BCUDA(b, cudaEventRecord(e1, b->stream));
+        PSC_BCUDA(b, cudaEventSynchronize(e1));
+        PSC_BCUDA(b, cudaEventElapsedTime(ms, e0, e1));
+        return PSC_OK;
+    };
     for (int k = 0; k < n; ++k) {
         psc_ctx *c = b->ctxs[k];
         // contexts of the same array, channels and grid (any length) reuse the
@@ -1028,57 +1104,31 @@ psc_status psc_batch_autotune(psc_batch *b, int *tiling_out) {
             PSC_BCUDA(b, cudaMemcpyAsync(c->d_lm_trial, zeros.data(), sizeof(double) * zeros.size(),
                                          cudaMemcpyHostToDevice, b->stream));
             float best = 1e30f;
-            int bt = 32, bc = 4, bk = 1;
+            Tiling bt{32, 4, 1, 0};
             timed[k].clear();
             c->no_stage = 0;
-            for (const auto &cd : tiling_candidates(c)) {
-                c->t_tile = cd[0];
-                c->c_group = cd[1];
-                c->kv = cd[2];
-                psc_status st = ensure_partials(c);
-                if (st != PSC_OK) return bfail(b, st, c->err);
-                PSC_BCUDA(b, set_eval_smem(eval_dyn_smem(c->c_group, tab_stride(c, c->kv))));
-                EvalArgs a = eval_args(c, c->d_lm_trial);
-                a.vis_obs = (const float2 *)b->vis[k];
-                a.w = b->w[k];
-                a.w_scale = (float)b->w_scale[k];
-                PSC_BCUDA(b, launch_eval(a, false, b->stream));          // warm
-                PSC_BCUDA(b, cudaEventRecord(e0, b->stream));
-                for (int r = 0; r < 3; ++r) PSC_BCUDA(b, launch_eval(a, false, b->stream));
-                PSC_BCUDA(b, cudaEventRecord(e1, b->stream));
-                PSC_BCUDA(b, cudaEventSynchronize(e1));
+            for (const Tiling &cd : tiling_candidates(c)) {
+                apply_tiling(c, cd);
                 float ms = 0.f;
-                PSC_BCUDA(b, cudaEventElapsedTime(&ms, e0, e1));
+                psc_status st = time_eval(c, k, &ms);
+                if (st != PSC_OK) return st;
                 timed[k].push_back({ms, cd});
-                if (ms < best) { best = ms; bt = cd[0]; bc = cd[1]; bk = cd[2]; }
+                if (ms < best) { best = ms; bt = cd; }
             }
-            c->t_tile = bt;
-            c->c_group = bc;
-            c->kv = bk;
+            apply_tiling(c, bt);
             // and whether staging the grid pays for this shape
             c->no_stage = 1;
-            {
-                EvalArgs a = eval_args(c, c->d_lm_trial);
-                a.vis_obs = (const float2 *)b->vis[k];
-                a.w = b->w[k];
-                a.w_scale = (float)b->w_scale[k];
-                PSC_BCUDA(b, set_eval_smem(eval_dyn_smem(c->c_group, tab_stride(c, c->kv))));
-                PSC_BCUDA(b, launch_eval(a, false, b->stream));
-                PSC_BCUDA(b, cudaEventRecord(e0, b->stream));
-                for (int r = 0; r < 3; ++r) PSC_BCUDA(b, launch_eval(a, false, b->stream));
-                PSC_BCUDA(b, cudaEventRecord(e1, b->stream));
-                PSC_BCUDA(b, cudaEventSynchronize(e1));
-                float ms = 0.f;
-                PSC_BCUDA(b, cudaEventElapsedTime(&ms, e0, e1));
-                c->no_stage = ms < best ? 1 : 0;
-            }
+            float ms = 0.f;
+            psc_status st = time_eval(c, k, &ms);
+            if (st != PSC_OK) return st;
+            c->no_stage = ms < best ? 1 : 0;
         }
     }
     // one block size serves the whole persistent launch: contexts whose best
     // shape is narrower take their fastest timed shape of the widest size
     int width = 32;
     for (int k = 0; k < n; ++k)
-        if (reused[k] < 0) width = std::max(width, (b->ctxs[k]->t_tile * b->ctxs[k]->c_group + 31) / 32 * 32);
+        if (reused[k] < 0) width = std::max(width, eval_threads(b->ctxs[k]));
     for (int k = 0; k < n; ++k) {
         psc_ctx *c = b->ctxs[k];
         if (reused[k] >= 0) {
@@ -1086,18 +1136,27 @@ psc_status psc_batch_autotune(psc_batch *b, int *tiling_out) {
             c->no_stage = o->no_stage;
             c->c_group = o->c_group;
             c->kv = kv_allowed(c, o->kv) ? o->kv : 1;
-            c->t_tile = fit_t_tile(c->nt, (o->t_tile * o->c_group + 31) / 32 * 32, c->c_group, c->kv);
-        } else if ((c->t_tile * c->c_group + 31) / 32 * 32 != width) {
+            c->flat = o->flat;
+            if (c->flat > 0 && ch_span(c) > 8) {          // a shorter interval: fall back to the default shape
+                c->flat = 0;
+                c->c_group = 4;
+            }
+            if (c->flat == 0)
+                c->t_tile = fit_t_tile(c->nt, o->flat > 0 ? o->flat : eval_threads(o), c->c_group, c->kv);
+        } else if (eval_threads(c) != width) {
             float best = 1e30f;
-            for (const auto &x : timed[k])
-                if ((x.second[0] * x.second[1] + 31) / 32 * 32 == width && x.first < best) {
+            for (const auto &x : timed[k]) {
+                const Tiling &t = x.second;
+                const int w = ((t[3] > 0 ? t[3] : t[0] * t[1]) + 31) / 32 * 32;
+                if (w == width && x.first < best) {
                     best = x.first;
-                    c->t_tile = x.second[0]; c->c_group = x.second[1]; c->kv = x.second[2];
+                    apply_tiling(c, t);
                 }
+            }
         }
         if (tiling_out) {
-            tiling_out[4 * k] = c->t_tile;
-            tiling_out[4 * k + 1] = c->c_group;
+            tiling_out[4 * k] = c->flat > 0 ? c->flat : c->t_tile;
+            tiling_out[4 * k + 1] = c->flat > 0 ? 0 : c->c_group;
             tiling_out[4 * k + 2] = c->kv;
             tiling_out[4 * k + 3] = c->no_stage ? PSC_STAGE_NEVER : PSC_STAGE_AUTO;
         }

@@ -205,14 +205,32 @@ template <bool kPredict, int kV>
 __device__ __forceinline__ void eval_brick(const EvalArgs &a, int brick, float2 *s_tab, BlockShared &sh,
                                            float (&acc)[kRed]) {
     const int tid = threadIdx.x;
-    const int tt = brick % a.n_tt;
-    const int cgi = (brick / a.n_tt) % a.n_cg;
-    const int bl = brick / (a.n_tt * a.n_cg);
-    const int lt = tid % a.t_tile;
-    const int lc = tid / a.t_tile;
-    const int t0 = (tt * a.t_tile + lt) * kV;         // first time step of this thread
-    const int c = cgi * a.c_group + lc;
-    const bool active = lc < a.c_group && t0 < a.nt && c < a.nc;
+    // brick -> baseline, this thread's channel c and first time step t0, and
+    // the block's channels [c_first, c_first + n_ch) (lc = c - c_first)
+    int bl, c, t0, c_first, n_ch;
+    bool active;
+    if (a.flat > 0) {
+        bl = brick / a.bpb;
+        const int first = (brick - bl * a.bpb) * a.flat;
+        const int k = first + tid;
+        c = k / a.n_tp;
+        t0 = (k - c * a.n_tp) * kV;
+        c_first = first / a.n_tp;
+        n_ch = min(a.nc - 1, (first + a.flat - 1) / a.n_tp) - c_first + 1;
+        active = tid < a.flat && c < a.nc;
+    } else {
+        const int tt = brick % a.n_tt;
+        const int cgi = (brick / a.n_tt) % a.n_cg;
+        bl = brick / (a.n_tt * a.n_cg);
+        const int lt = tid % a.t_tile;
+        const int lcg = tid / a.t_tile;
+        t0 = (tt * a.t_tile + lt) * kV;
+        c_first = cgi * a.c_group;
+        c = c_first + lcg;
+        n_ch = a.c_group;
+        active = lcg < a.c_group && t0 < a.nt && c < a.nc;
+    }
+    const int lc = c - c_first;
     const int tab_stride = a.tab_stride;
     const int S = a.support;
 
@@ -280,8 +298,8 @@ __device__ __forceinline__ void eval_brick(const EvalArgs &a, int brick, float2 
         }
     }
     // radial tables of this block's channels as (c_n, s_n), zero-padded
-    for (int j = 0; j < a.c_group; ++j) {
-        const int cc = cgi * a.c_group + j;
+    for (int j = 0; j < n_ch; ++j) {
+        const int cc = c_first + j;
         const int off = cc < a.nc ? a.chan[cc].tab_off : 0;
         const int len = cc < a.nc ? a.chan[cc].tab_len : 0;
         for (int n = tid; n < tab_stride; n += blockDim.x) {
@@ -730,9 +748,9 @@ size_t eval_dyn_smem(int c_group, int tab_stride) {
 
 cudaError_t launch_eval(const EvalArgs &a, bool predict, cudaStream_t s) {
     if (a.exact) return launch_exact(a, predict, s);
-    const int threads = (a.t_tile * a.c_group + 31) / 32 * 32;
+    const int threads = ((a.flat > 0 ? a.flat : a.t_tile * a.c_group) + 31) / 32 * 32;
     const int blocks = (int)a.n_bricks;
-    const size_t dyn = eval_dyn_smem(a.c_group, a.tab_stride);
+    const size_t dyn = eval_dyn_smem(a.flat > 0 ? a.ch_span : a.c_group, a.tab_stride);
     if (predict) {
         eval_kernel<true><<<blocks, threads, dyn, s>>>(a, nullptr, nullptr, 0, nullptr);
     } else {

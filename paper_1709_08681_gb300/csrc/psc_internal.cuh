@@ -51,6 +51,12 @@ struct EvalArgs {
     long long n_bricks;        // n_bl * n_cg * n_tt (partials are [kRed][n_bricks])
     const float *kmom;         // exact disk kernel: [table entries][10] lens-moment combinations
     int exact;                 // 1: exact disk kernel (exact.cu) instead of Eq. AIJPOINTING's
+    // Flat bricks (flat > 0; t_tile, c_group, n_tt, n_cg unused): the items of a
+    // baseline are its (channel, group of kv consecutive time steps) pairs in
+    // channel-major order, n_tp groups per channel; brick b of the baseline
+    // holds items [b flat, (b + 1) flat), so bpb bricks per baseline, each
+    // spanning at most ch_span channels.
+    int flat, n_tp, bpb, ch_span;
 };
 
 // Arguments of the stencil-feature kernel (learned initial estimate).

@@ -80,7 +80,9 @@ def test_batch_autotune_keeps_results():
     ivs = _intervals()
     b = _abi.Batch([iv["gp"].ctx for iv in ivs], [iv["dv"] for iv in ivs], [iv["dw"] for iv in ivs])
     tiles = b.psc_batch_autotune()
-    assert all(1 <= tt * cg <= 256 and kv in (1, 2) and st in (0, 1) for tt, cg, kv, st in tiles)
+    # c_group 0 marks flat bricks of tt items
+    assert all((1 <= tt * cg <= 256 or (cg == 0 and tt in (64, 128, 192, 256))) and kv in (1, 2) and st in (0, 1)
+               for tt, cg, kv, st in tiles)
     b.psc_batch_begin([np.zeros((iv["m"].n_ant, 2)) for iv in ivs])
     b.psc_batch_iterate(60)
     got, reps = b.psc_batch_end()

@@ -145,6 +145,52 @@ def test_unstaged_fallback_matches_oracle():
     assert max(_rel(dVg[p], dV[p]) for p in range(4)) < TOL_V
 
 
+# Flat bricks (psc_set_flat_tiling): (n_ant, n_time, freqs, items, kv) with
+# blocks that straddle channel boundaries, a baseline's last block ragged,
+# blocks wider than a channel's items, and a single visibility
+FLAT_CASES = [
+    (6, 37, (1.3e9, 1.35e9, 1.4e9, 1.45e9), 64, 2),      # 19 groups per channel: 4 channels per block
+    (7, 40, (1.2e9, 1.3e9, 1.4e9, 1.5e9, 1.6e9), 128, 1),
+    (5, 150, (1.3e9, 1.4e9, 1.5e9), 256, 2),             # 75 groups per channel: 5 channels per block
+    (6, 13, (1.25e9, 1.3e9, 1.35e9, 1.4e9, 1.42e9), 32, 1),
+    (2, 1, (1.4e9,), 32, 2),
+]
+
+
+@pytest.mark.parametrize("case", FLAT_CASES)
+def test_flat_bricks_match_oracle(case):
+    n_ant, nt, freqs, items, kv = case
+    m, _, lmt, img = cases.problem(cases.DISK_SMALL, n_ant=n_ant, n_time=nt, freqs=freqs, sigma_arcsec=30.0)
+    V, dV = psc.predict(m, lmt)
+    gp = GpuProblem(m, img)
+    gp.ctx.psc_set_flat_tiling(items, kv)
+    Vg, dVg = gp.predict(lmt)
+    assert _rel(Vg, V) < TOL_V
+    assert max(_rel(dVg[p], dV[p]) for p in range(4)) < TOL_V
+    vobs, w = _obs(m, lmt)
+    lm = 0.5 * lmt
+    chi2, g, H, X = psc.chi2_grad_normal(m, lm, vobs, w)
+    chi2g, gg, Hg, Xg = gp.ctx.psc_residual_grad(lm, gp.upload(vobs), gp.upload(w, torch.float32), 1.0, cross=True)
+    assert abs(chi2g - chi2) < TOL_V * _chi2_scale(m, lm, vobs, w)
+    Vh, dVh = psc.predict(m, lm)
+    gscale = 2.0 * np.sum(w[None] * np.abs(vobs - Vh)[None] * np.abs(dVh))
+    assert np.max(np.abs(gg - g)) < TOL_V * gscale
+    assert np.max(np.abs(Hg - H)) < TOL_V * np.max(np.abs(H))
+    assert np.max(np.abs(Xg - X)) < TOL_V * np.max(np.abs(H))
+
+
+def test_flat_tiling_arguments():
+    m, _, _, img = cases.problem(cases.DISK_SMALL, n_ant=4, n_time=3, freqs=(1.3e9, 1.4e9))
+    gp = GpuProblem(m, img)
+    for items, kv in ((48, 1), (0, 1), (512, 1), (64, 3)):
+        with pytest.raises(_abi.PscError):
+            gp.ctx.psc_set_flat_tiling(items, kv)
+    m9, _, _, img9 = cases.problem(cases.DISK_SMALL, n_ant=4, n_time=3, freqs=tuple(1.3e9 + 1e7 * k for k in range(12)))
+    g9 = GpuProblem(m9, img9)
+    with pytest.raises(_abi.PscError):
+        g9.ctx.psc_set_flat_tiling(256, 1)                 # 3 items per channel: 86 channels per block
+
+
 @pytest.mark.parametrize("kv", [1, 2])
 def test_never_staged_matches_oracle(kv):
     """PSC_STAGE_NEVER: every tap reads the grid from global memory, with the
