@@ -234,8 +234,9 @@ psc_status psc_set_tiling(psc_ctx *ctx, int t_tile, int c_group, int vis_per_thr
  * c_group falls short of a multiple of 32 and when the channel or time count
  * is not a multiple of the group.  A block may then span several channels
  * (at most 8).  items in {32, 64, ..., 256}; vis_per_thread as for
- * psc_set_tiling.  psc_set_tiling switches back.  Gaussian kernel model only
- * (PSC_ERR_ARG under PSC_KERNEL_EXACT_DISK, which also resets this).  Errors:
+ * psc_set_tiling.  psc_set_tiling switches back.  Under PSC_KERNEL_EXACT_DISK
+ * vis_per_thread must be 1 (psc_set_kernel_model resets the shape to
+ * rectangular bricks; set flat bricks after it).  Errors:
  * PSC_ERR_ARG for out-of-range values or a brick spanning more than 8
  * channels (fewer time steps per channel than items / 7). */
 psc_status psc_set_flat_tiling(psc_ctx *ctx, int items, int vis_per_thread);

@@ -458,7 +458,8 @@ psc_status psc_set_tiling(psc_ctx *ctx, int t_tile, int c_group, int vis_per_thr
 
 psc_status psc_set_flat_tiling(psc_ctx *ctx, int items, int vis_per_thread) {
     if (!ctx) return fail(nullptr, PSC_ERR_ARG, "ctx is NULL");
-    if (ctx->kernel_model != PSC_KERNEL_GAUSS) return fail(ctx, PSC_ERR_ARG, "flat bricks serve the Gaussian kernel model only");
+    if (ctx->kernel_model != PSC_KERNEL_GAUSS && vis_per_thread != 1)
+        return fail(ctx, PSC_ERR_ARG, "the exact disk kernel takes one visibility per thread");
     if (items < 32 || items > kMaxThreads || items % 32) return fail(ctx, PSC_ERR_ARG, "items must be 32, 64, ..., 256");
     if (!(vis_per_thread == 1 || vis_per_thread == 2)) return fail(ctx, PSC_ERR_ARG, "vis_per_thread must be 1 or 2");
     if (!kv_allowed(ctx, vis_per_thread))

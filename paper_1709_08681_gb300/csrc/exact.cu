@@ -207,14 +207,32 @@ __global__ void __launch_bounds__(kMaxThreads) exact_kernel(const EvalArgs a) {
     __shared__ ExactShared sh;
     const int tid = threadIdx.x;
     const int brick = blockIdx.x;
-    const int tt = brick % a.n_tt;
-    const int cgi = (brick / a.n_tt) % a.n_cg;
-    const int bl = brick / (a.n_tt * a.n_cg);
-    const int lt = tid % a.t_tile;
-    const int lc = tid / a.t_tile;
-    const int t = tt * a.t_tile + lt;
-    const int c = cgi * a.c_group + lc;
-    const bool active = lc < a.c_group && t < a.nt && c < a.nc;
+    // brick -> baseline, this thread's channel c and time step t, and the
+    // block's channels [c_first, c_first + n_ch) (flat or rectangular bricks
+    // as in eval.cu, one visibility per thread)
+    int bl, c, t, c_first, n_ch;
+    bool active;
+    if (a.flat > 0) {
+        bl = brick / a.bpb;
+        const int first = (brick - bl * a.bpb) * a.flat;
+        const int k = first + tid;
+        c = k / a.n_tp;
+        t = k - c * a.n_tp;
+        c_first = first / a.n_tp;
+        n_ch = min(a.nc - 1, (first + a.flat - 1) / a.n_tp) - c_first + 1;
+        active = tid < a.flat && c < a.nc;
+    } else {
+        const int tt = brick % a.n_tt;
+        const int cgi = (brick / a.n_tt) % a.n_cg;
+        bl = brick / (a.n_tt * a.n_cg);
+        const int lcg = tid / a.t_tile;
+        t = tt * a.t_tile + tid % a.t_tile;
+        c_first = cgi * a.c_group;
+        c = c_first + lcg;
+        n_ch = a.c_group;
+        active = lcg < a.c_group && t < a.nt && c < a.nc;
+    }
+    const int lc = c - c_first;
     const int tab_stride = a.tab_stride;
     const int S = a.support;
     if (a.skip != nullptr && *a.skip) return;
@@ -260,8 +278,8 @@ __global__ void __launch_bounds__(kMaxThreads) exact_kernel(const EvalArgs a) {
         }
     }
     // interpolation entries of this block's channels for this baseline's s
-    for (int j = 0; j < a.c_group; ++j) {
-        const int cc = cgi * a.c_group + j;
+    for (int j = 0; j < n_ch; ++j) {
+        const int cc = c_first + j;
         const int off = cc < a.nc ? a.chan[cc].tab_off : 0;
         const int len = cc < a.nc ? a.chan[cc].tab_len : 0;
         for (int n = tid; n < tab_stride; n += blockDim.x) {
@@ -481,9 +499,9 @@ size_t exact_dyn_smem(int c_group, int tab_stride) {
 }
 
 cudaError_t launch_exact(const EvalArgs &a, bool predict, cudaStream_t s) {
-    const int threads = (a.t_tile * a.c_group + 31) / 32 * 32;
+    const int threads = ((a.flat > 0 ? a.flat : a.t_tile * a.c_group) + 31) / 32 * 32;
     const int blocks = (int)a.n_bricks;
-    const size_t dyn = exact_dyn_smem(a.c_group, a.tab_stride);
+    const size_t dyn = exact_dyn_smem(a.flat > 0 ? a.ch_span : a.c_group, a.tab_stride);
     int dev = 0, optin = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;

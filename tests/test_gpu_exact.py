@@ -66,6 +66,30 @@ def test_exact_predict_matches_oracle(case, staging):
         assert cases.rel_l2(dVg[p], dV[p]) < TOL_V, p
 
 
+@pytest.mark.parametrize("case", [(6, 37, (1.2e9, 1.3e9, 1.4e9, 1.5e9), 64, 120.0),
+                                  (5, 150, (1.3e9, 1.4e9, 1.5e9), 256, 60.0),
+                                  (7, 40, (1.2e9, 1.3e9, 1.4e9, 1.5e9, 1.6e9), 128, 60.0)])
+def test_exact_flat_bricks_match_oracle(case):
+    """Flat bricks (blocks straddling channels) with the exact kernel."""
+    n_ant, nt, freqs, items, sigma = case
+    m, _, lmt, img = cases.problem(cases.DISK_SMALL, n_ant=n_ant, n_time=nt, freqs=freqs, sigma_arcsec=sigma)
+    me = _exact(m)
+    V, dV = psc.predict(me, lmt)
+    gp = _gpu(m, img)
+    gp.ctx.psc_set_flat_tiling(items, 1)
+    Vg, dVg = gp.predict(lmt)
+    assert cases.rel_l2(Vg, V) < TOL_V
+    for p in range(4):
+        assert cases.rel_l2(dVg[p], dV[p]) < TOL_V, p
+    vobs, w = _obs(m, lmt)
+    lm = 0.5 * lmt
+    chi2, g, H, X = psc.chi2_grad_normal(me, lm, vobs, w)
+    chi2g, gg, Hg, Xg = gp.ctx.psc_residual_grad(lm, gp.upload(vobs), gp.upload(w, torch.float32), 1.0, cross=True)
+    assert np.max(np.abs(Hg - H)) < TOL_V * np.max(np.abs(H))
+    with pytest.raises(_abi.PscError):
+        gp.ctx.psc_set_flat_tiling(items, 2)                  # one visibility per thread
+
+
 def test_exact_equals_gauss_kernel_without_offsets():
     """At l_i = l_j the exact kernel is A° times the ramp (decorrelation 1)."""
     m, _, lm, img = cases.problem(cases.DISK_SMALL, n_ant=6, n_time=12, freqs=(1.3e9, 1.5e9), sigma_arcsec=0.0)
