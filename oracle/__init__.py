@@ -15,6 +15,10 @@ paper (Bhatnagar & Cornwell 2017) in double precision:
                       primary beams (Eq. ME; the paper's simulation, Sec. 4.1)
 * ``lm``           -- Levenberg-Marquardt minimiser standing in for the
                       paper's unspecified f() and Terminate() (Sec. 2.2, Algorithm 1)
+* ``exact``        -- the exact kernel of two shifted uniform-disk patterns
+                      (Sec. 3's more accurate pattern), quadrature in ``exact.c``
+* ``wsnap``        -- W-snapshots: the interval's least-squares uvw plane and
+                      the sky moved to the snapshot frame (Sec. 6.1)
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import it.  The GPU library shares no code with it.

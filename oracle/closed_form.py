@@ -11,8 +11,10 @@ PB with pointing offsets"):
 
     V_ij(u, v) = sum_k S_k E(s_k - p_i) E(s_k - p_j) exp(+2 pi i (u l_k + v m_k))
 
-where p_i = (l_i, m_i) is antenna i's pointing offset.  The w term and
-n - 1 are left out (co-planar model, the same as the degridding path).
+where p_i = (l_i, m_i) is antenna i's pointing offset.  By default the w term
+and n - 1 are left out (co-planar model, the same as the degridding path);
+with ``w_term=True`` the phase also carries w (n_k - 1), n_k = sqrt(1 - l_k^2 - m_k^2)
+(the non-coplanar measurement equation, for the W-snapshot pins).
 """
 from __future__ import annotations
 
@@ -33,10 +35,12 @@ def efp(kind: str, rho, freq_hz: float, diam_m: float, alpha_per_dlambda: float)
     raise ValueError(kind)
 
 
-def visibilities(uvw_m, freq_hz, n_ant, src, lm, kind, diam_m, alpha_per_dlambda):
+def visibilities(uvw_m, freq_hz, n_ant, src, lm, kind, diam_m, alpha_per_dlambda, w_term=False):
     """complex128 [nt][nbl][nc] direct-sum visibilities (see module docstring)."""
     lm = np.asarray(lm, dtype=np.float64)
-    u, v = uv_lambda(np.asarray(uvw_m, dtype=np.float64), freq_hz)
+    uvw_m = np.asarray(uvw_m, dtype=np.float64)
+    u, v = uv_lambda(uvw_m, freq_hz)
+    w = uvw_m[..., 2:3] * (np.asarray(freq_hz, dtype=np.float64) / 299_792_458.0)
     ij = np.asarray([(i, j) for i in range(n_ant) for j in range(i + 1, n_ant)])
     out = np.zeros(u.shape, dtype=np.complex128)
     for c, f in enumerate(np.asarray(freq_hz, dtype=np.float64)):
@@ -44,5 +48,8 @@ def visibilities(uvw_m, freq_hz, n_ant, src, lm, kind, diam_m, alpha_per_dlambda
             rho = np.hypot(lk - lm[:, 0], mk - lm[:, 1])           # per antenna
             e = efp(kind, rho, f, diam_m, alpha_per_dlambda)
             amp = sk * e[ij[:, 0]] * e[ij[:, 1]]                    # [nbl]
-            out[:, :, c] += amp[None, :] * np.exp(2j * math.pi * (u[:, :, c] * lk + v[:, :, c] * mk))
+            ph = u[:, :, c] * lk + v[:, :, c] * mk
+            if w_term:
+                ph = ph + w[:, :, c] * (math.sqrt(1.0 - lk * lk - mk * mk) - 1.0)
+            out[:, :, c] += amp[None, :] * np.exp(2j * math.pi * ph)
     return out
