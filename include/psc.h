@@ -155,6 +155,41 @@ void psc_solve_opts_default(psc_solve_opts *opts);
 psc_status psc_model_grid(const psc_grid_desc *gd, const float *image_dev, void *grid_out,
                           void *stream);
 
+/* V° of a model given as n_comp point components (comp_lmS: host
+ * [n_comp][3] = l, m (radians), S (Jy)): G[gy][gx] = sum_k S_k
+ * exp(+2 pi i ((gx-Ng/2) du l_k + (gy-Ng/2) du m_k)), du = 1 / (n_grid
+ * cell_rad) -- for sources at pixel centres the same grid as psc_model_grid
+ * of their image.  One complex matrix product on the tensor cores (split
+ * bfloat16 as psc_model_grid; operands from FP64 sincospi; the component
+ * count padded to a multiple of 8 with zero flux).  grid_out: device
+ * complex64 [n_grid][n_grid].  Temporary workspace of 24 n_grid K bytes, K
+ * the padded count.  Synchronises.  Errors: PSC_ERR_ARG (sizes, NULL or
+ * non-finite input), PSC_ERR_CUDA / PSC_ERR_OOM, PSC_ERR_TIMEOUT (a
+ * tensor-core wait ran out). */
+psc_status psc_model_grid_components(int n_comp, const double *comp_lmS, int n_grid, double cell_rad,
+                                     void *grid_out, void *stream);
+
+/* W-snapshots (Sec. 6.1: for short solution intervals the array may be
+ * treated as co-planar).  psc_snapshot_plane fits the plane w = a u + b v to
+ * n_rows baselines (uvw_dev: device double [n_rows][3], metres) by least
+ * squares (FP64 sums on the GPU, 2 x 2 solve on the host); synchronises;
+ * PSC_ERR_NUMERIC when the (u, v) are collinear.
+ * psc_snapshot_components moves each component (host [n_comp][3] = l, m, S)
+ * to the snapshot frame of that plane, l' = l + a (n-1), m' = m + b (n-1),
+ * n = sqrt(1 - l^2 - m^2), where the co-planar degridding reproduces the
+ * w-term exactly for baselines on the plane, and rescales its flux by
+ * PB(l) / PB(l'), PB the aperture's pointing-free power pattern at freq_hz
+ * (the degridding kernel weights a source by the beam at its grid position);
+ * comp_out may equal comp_in.  Feed the result to psc_model_grid_components
+ * and give each interval's context its own grid.  What the method neglects is
+ * the interval's departure w - a u - b v from the plane, and the beam ratio's
+ * change across the band away from freq_hz.  Errors: PSC_ERR_ARG (NULL,
+ * aperture, a component outside the unit disk), PSC_ERR_NUMERIC (a moved
+ * component on a beam null). */
+psc_status psc_snapshot_plane(const double *uvw_dev, long long n_rows, double *a, double *b, void *stream);
+psc_status psc_snapshot_components(int n_comp, const double *comp_in, double a, double b, const psc_aperture *ap,
+                                   double freq_hz, double *comp_out);
+
 /* Creates a context for one observation block: copies the channel list,
  * builds the A° tables on the device (Algorithm 1, second pre-compute) and
  * allocates the workspace.  grid_dev (complex64 [Ng][Ng], from

@@ -25,7 +25,8 @@ PSC_KERNEL_GAUSS, PSC_KERNEL_EXACT_DISK = 0, 1
 PSC_LM_FULL, PSC_LM_BLOCK = 0, 1
 STOP_REASONS = {0: "none", 1: "step", 2: "chi2", 3: "lambda", 4: "max_iter", 5: "numeric"}
 
-EXPORTS = ("psc_solve_opts_default", "psc_model_grid", "psc_create", "psc_destroy", "psc_last_error",
+EXPORTS = ("psc_solve_opts_default", "psc_model_grid", "psc_model_grid_components", "psc_snapshot_plane",
+           "psc_snapshot_components", "psc_create", "psc_destroy", "psc_last_error",
            "psc_predict", "psc_residual_grad", "psc_solve_offsets", "psc_lm_begin", "psc_lm_iterate",
            "psc_lm_end", "psc_lm_restart", "psc_set_tiling", "psc_set_grid_precision", "psc_set_staging",
            "psc_set_kernel_model", "psc_set_flat_tiling", "psc_fp32_fma_rate", "psc_profile", "psc_profile_read",
@@ -86,6 +87,10 @@ def lib():
         sig = {
             "psc_solve_opts_default": (None, [ctypes.POINTER(psc_solve_opts)]),
             "psc_model_grid": (ctypes.c_int, [ctypes.POINTER(psc_grid_desc), _V, _V, _V]),
+            "psc_model_grid_components": (ctypes.c_int, [ctypes.c_int, _D, ctypes.c_int, ctypes.c_double, _V, _V]),
+            "psc_snapshot_plane": (ctypes.c_int, [_V, ctypes.c_longlong, _D, _D, _V]),
+            "psc_snapshot_components": (ctypes.c_int, [ctypes.c_int, _D, ctypes.c_double, ctypes.c_double,
+                                                       ctypes.POINTER(psc_aperture), ctypes.c_double, _D]),
             "psc_create": (ctypes.c_int, [ctypes.POINTER(_V), ctypes.POINTER(psc_obs), ctypes.POINTER(psc_aperture),
                                           ctypes.POINTER(psc_grid_desc), _V, _V]),
             "psc_destroy": (None, [_V]),
@@ -179,6 +184,33 @@ def psc_solve_opts_default() -> psc_solve_opts:
 def psc_model_grid(n_img, n_grid, cell_rad, support, oversample, image_dev, grid_out, stream=None):
     gd = psc_grid_desc(n_img, n_grid, cell_rad, support, oversample)
     _check(lib().psc_model_grid(ctypes.byref(gd), _ptr(image_dev), _ptr(grid_out), _stream(stream)))
+
+
+def psc_model_grid_components(comp_lmS, n_grid, cell_rad, grid_out, stream=None):
+    """V° of point components (host array [n][3] = l, m, S) into grid_out."""
+    comp = np.ascontiguousarray(comp_lmS, dtype=np.float64).reshape(-1, 3)
+    _check(lib().psc_model_grid_components(comp.shape[0], _dp(comp), int(n_grid), float(cell_rad), _ptr(grid_out),
+                                           _stream(stream)))
+
+
+def psc_snapshot_plane(uvw_dev, n_rows, stream=None):
+    """(a, b) of the least-squares plane w = a u + b v of n_rows device uvw rows."""
+    a = np.zeros(1)
+    b = np.zeros(1)
+    _check(lib().psc_snapshot_plane(_ptr(uvw_dev), int(n_rows), _dp(a), _dp(b), _stream(stream)))
+    return float(a[0]), float(b[0])
+
+
+def psc_snapshot_components(comp_lmS, a, b, ap_kind, diam_m, alpha_per_dlambda, freq_hz):
+    """Components moved to the snapshot frame of plane (a, b), fluxes rescaled
+    by the beam ratio at freq_hz (host [n][3] in, new array out)."""
+    comp = np.ascontiguousarray(comp_lmS, dtype=np.float64).reshape(-1, 3)
+    out = np.empty_like(comp)
+    kind = {"disk": PSC_AP_DISK, "gauss": PSC_AP_GAUSS}.get(ap_kind, ap_kind)
+    ap = psc_aperture(int(kind), float(diam_m), float(alpha_per_dlambda), 1)
+    _check(lib().psc_snapshot_components(comp.shape[0], _dp(comp), float(a), float(b), ctypes.byref(ap),
+                                         float(freq_hz), _dp(out)))
+    return out
 
 
 def psc_residual_grad_noalloc(n_ant, n_time, n_chan, uvw_dev, freq_hz, ap_kind, diam_m, alpha_per_dlambda,

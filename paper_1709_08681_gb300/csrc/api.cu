@@ -304,6 +304,79 @@ psc_status psc_model_grid(const psc_grid_desc *gd, const float *image_dev, void 
     return PSC_OK;
 }
 
+psc_status psc_model_grid_components(int n_comp, const double *comp_lmS, int n_grid, double cell_rad,
+                                     void *grid_out, void *stream) {
+    if (n_comp < 0 || n_comp > (1 << 24)) return fail(nullptr, PSC_ERR_ARG, "n_comp must be in [0, 2^24]");
+    if (n_comp > 0 && !comp_lmS) return fail(nullptr, PSC_ERR_ARG, "comp_lmS is NULL");
+    if (!grid_out) return fail(nullptr, PSC_ERR_ARG, "grid_out is NULL");
+    if (n_grid < 2 || n_grid > 16384 || n_grid % 2) return fail(nullptr, PSC_ERR_ARG, "n_grid must be even in [2, 16384]");
+    if (!(cell_rad > 0.0) || !std::isfinite(cell_rad)) return fail(nullptr, PSC_ERR_ARG, "cell_rad must be > 0");
+    for (int k = 0; k < 3 * n_comp; ++k)
+        if (!std::isfinite(comp_lmS[k])) return fail(nullptr, PSC_ERR_ARG, "components must be finite");
+    cudaStream_t s = (cudaStream_t)stream;
+    void *ws = nullptr;
+    int *err_dev = nullptr;
+    int herr = 0;
+    const double du = 1.0 / (n_grid * cell_rad);
+    cudaError_t e = cudaMalloc(&ws, model_grid_comp_ws_bytes(n_comp, n_grid));
+    if (e == cudaSuccess) e = launch_model_grid_comp(n_comp, comp_lmS, n_grid, du, ws, (float2 *)grid_out, &err_dev, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaMemcpy(&herr, err_dev, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(ws);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "psc_model_grid_components");
+    if (herr) return fail(nullptr, PSC_ERR_TIMEOUT, "psc_model_grid_components: a tensor-core wait timed out");
+    return PSC_OK;
+}
+
+psc_status psc_snapshot_plane(const double *uvw_dev, long long n_rows, double *a, double *b, void *stream) {
+    if (!uvw_dev || !a || !b) return fail(nullptr, PSC_ERR_ARG, "uvw, a and b must be non-NULL");
+    if (n_rows < 2) return fail(nullptr, PSC_ERR_ARG, "n_rows must be >= 2");
+    cudaStream_t s = (cudaStream_t)stream;
+    double *d_sums = nullptr;
+    double h[5] = {};
+    cudaError_t e = cudaMalloc(&d_sums, 5 * sizeof(double));
+    if (e == cudaSuccess) e = launch_plane_sums(uvw_dev, n_rows, d_sums, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, d_sums, sizeof(h), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(d_sums);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "psc_snapshot_plane");
+    // normal equations [uu uv; uv vv] (a, b) = (uw, vw)
+    const double det = h[0] * h[2] - h[1] * h[1];
+    if (!(det > 1e-12 * h[0] * h[2])) return fail(nullptr, PSC_ERR_NUMERIC, "psc_snapshot_plane: the baselines span no plane (collinear u, v)");
+    *a = (h[3] * h[2] - h[4] * h[1]) / det;
+    *b = (h[4] * h[0] - h[3] * h[1]) / det;
+    return PSC_OK;
+}
+
+psc_status psc_snapshot_components(int n_comp, const double *comp_in, double a, double b, const psc_aperture *ap,
+                                   double freq_hz, double *comp_out) {
+    if (n_comp < 0 || (n_comp > 0 && (!comp_in || !comp_out))) return fail(nullptr, PSC_ERR_ARG, "component arrays must be non-NULL");
+    if (!ap || (ap->kind != PSC_AP_DISK && ap->kind != PSC_AP_GAUSS)) return fail(nullptr, PSC_ERR_ARG, "unknown aperture");
+    if (!(ap->diam_m > 0.0) || !(freq_hz > 0.0) || !std::isfinite(a) || !std::isfinite(b))
+        return fail(nullptr, PSC_ERR_ARG, "diam_m, freq_hz must be > 0 and a, b finite");
+    const double dl = ap->diam_m * freq_hz / kC;
+    const double alpha = ap->alpha_per_dlambda * dl;
+    auto pb = [&](double rho) {                       // pointing-free power pattern
+        if (ap->kind == PSC_AP_GAUSS) return std::exp(-2.0 * alpha * alpha * rho * rho);
+        const double x = M_PI * dl * rho;
+        const double e = x > 1e-12 ? 2.0 * std::cyl_bessel_j(1.0, x) / x : 1.0;
+        return e * e;
+    };
+    for (int k = 0; k < n_comp; ++k) {
+        const double l = comp_in[3 * k], m = comp_in[3 * k + 1], S = comp_in[3 * k + 2];
+        const double r2 = l * l + m * m;
+        if (!(r2 < 1.0)) return fail(nullptr, PSC_ERR_ARG, "a component lies outside the unit disk");
+        const double nm1 = -r2 / (1.0 + std::sqrt(1.0 - r2));     // n - 1 without cancellation
+        const double l1 = l + a * nm1, m1 = m + b * nm1;
+        const double p1 = pb(std::hypot(l1, m1));
+        if (!(p1 > 1e-300)) return fail(nullptr, PSC_ERR_NUMERIC, "a moved component sits on a null of the beam");
+        comp_out[3 * k] = l1;
+        comp_out[3 * k + 1] = m1;
+        comp_out[3 * k + 2] = S * pb(std::sqrt(r2)) / p1;
+    }
+    return PSC_OK;
+}
+
 psc_status psc_create(psc_ctx **out, const psc_obs *obs, const psc_aperture *ap, const psc_grid_desc *gd,
                       const void *grid_dev, void *stream) {
     if (!out) return fail(nullptr, PSC_ERR_ARG, "out is NULL");

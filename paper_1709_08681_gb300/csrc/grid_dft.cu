@@ -207,6 +207,36 @@ __global__ void split_dft_matrix_kernel(const double2 *__restrict__ W, int n, in
     }
 }
 
+// Component operands of the grid G[gy][gx] = sum_k S_k exp(2 pi i (u_gx l_k + v_gy m_k)),
+// u_g = v_g = (g - Ng/2) du, as the second tensor-core pass with
+// A[gx][k] = S_k exp(2 pi i u_gx l_k) and B[gy][k] = exp(2 pi i v_gy m_k): split planes
+// [3][Ng][kp] of the real and imaginary parts, phases from FP64 sincospi,
+// columns k >= n_comp zero (kp = n_comp rounded up to a multiple of 8).
+__global__ void split_comp_kernel(const double *__restrict__ comp, int n_comp, int kp, int ng, double du,
+                                  bf16 *__restrict__ Ar, bf16 *__restrict__ Ai, bf16 *__restrict__ Br,
+                                  bf16 *__restrict__ Bi) {
+    const long long total = (long long)ng * kp;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+        const int g = (int)(e / kp), k = (int)(e % kp);
+        double ar = 0.0, ai = 0.0, br = 0.0, bi = 0.0;
+        if (k < n_comp) {
+            const double x = (double)(g - ng / 2) * du;
+            double sn, cs;
+            sincospi(2.0 * x * comp[3 * k], &sn, &cs);
+            ar = comp[3 * k + 2] * cs;
+            ai = comp[3 * k + 2] * sn;
+            sincospi(2.0 * x * comp[3 * k + 1], &sn, &cs);
+            br = cs;
+            bi = sn;
+        }
+        bf16 h, m, l;
+        split3d(ar, h, m, l); Ar[e] = h; Ar[total + e] = m; Ar[2 * total + e] = l;
+        split3d(ai, h, m, l); Ai[e] = h; Ai[total + e] = m; Ai[2 * total + e] = l;
+        split3d(br, h, m, l); Br[e] = h; Br[total + e] = m; Br[2 * total + e] = l;
+        split3d(bi, h, m, l); Bi[e] = h; Bi[total + e] = m; Bi[2 * total + e] = l;
+    }
+}
+
 __device__ __forceinline__ uint32_t tc_core_off(int r, int k) {
     return (uint32_t)((r >> 3) * (kTK / 8 * 128) + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
 }
@@ -411,6 +441,8 @@ __global__ void __launch_bounds__(128, 1) dft_tc_kernel(const TcPassArgs g) {
 namespace {
 size_t al256(size_t x) { return (x + 255) / 256 * 256; }
 bool use_tc(int n_img) { return n_img % 8 == 0; }
+// GEMM depth of the component grid: n_comp padded to a multiple of 8 (16-byte rows)
+int comp_depth(int n_comp) { return std::max(8, (n_comp + 7) / 8 * 8); }
 }  // namespace
 
 size_t model_grid_ws_bytes(int n_img, int n_grid) {
@@ -466,6 +498,40 @@ cudaError_t launch_model_grid(int n_img, int n_grid, const float *image, void *w
     a2.A[0] = Tr; a2.A[1] = Ti; a2.n_a = 2;
     a2.B[0] = Er; a2.B[1] = Ei;
     a2.a_rows = n_grid; a2.b_rows = n_grid; a2.k = n_img;
+    a2.G = grid_out; a2.ng = n_grid; a2.err = *err_dev;
+    dim3 g2((n_grid + kTN - 1) / kTN, (n_grid + kTM - 1) / kTM);
+    dft_tc_kernel<2><<<g2, 128, smem2, s>>>(a2);
+    return cudaGetLastError();
+}
+
+size_t model_grid_comp_ws_bytes(int n_comp, int n_grid) {
+    const size_t kp = (size_t)comp_depth(n_comp), ng = (size_t)n_grid;
+    return al256((size_t)n_comp * 3 * sizeof(double)) + 4 * al256(3 * ng * kp * 2) + 256;
+}
+
+cudaError_t launch_model_grid_comp(int n_comp, const double *comp_host, int n_grid, double du, void *ws,
+                                   float2 *grid_out, int **err_dev, cudaStream_t s) {
+    const int kp = comp_depth(n_comp);
+    const size_t ng = (size_t)n_grid;
+    unsigned char *p = (unsigned char *)ws;
+    double *comp = (double *)p; p += al256((size_t)n_comp * 3 * sizeof(double));
+    bf16 *Ar = (bf16 *)p; p += al256(3 * ng * kp * 2);
+    bf16 *Ai = (bf16 *)p; p += al256(3 * ng * kp * 2);
+    bf16 *Br = (bf16 *)p; p += al256(3 * ng * kp * 2);
+    bf16 *Bi = (bf16 *)p; p += al256(3 * ng * kp * 2);
+    *err_dev = (int *)p;
+    cudaError_t e = cudaMemsetAsync(*err_dev, 0, sizeof(int), s);
+    if (e == cudaSuccess && n_comp > 0)
+        e = cudaMemcpyAsync(comp, comp_host, (size_t)n_comp * 3 * sizeof(double), cudaMemcpyHostToDevice, s);
+    const int smem2 = 2 * (6 * kPlaneA + 6 * kPlaneB);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(dft_tc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem2);
+    if (e != cudaSuccess) return e;
+    split_comp_kernel<<<(int)std::min<size_t>((ng * kp + 255) / 256, 8192), 256, 0, s>>>(comp, n_comp, kp, n_grid, du,
+                                                                                          Ar, Ai, Br, Bi);
+    TcPassArgs a2{};
+    a2.A[0] = Ar; a2.A[1] = Ai; a2.n_a = 2;
+    a2.B[0] = Br; a2.B[1] = Bi;
+    a2.a_rows = n_grid; a2.b_rows = n_grid; a2.k = kp;
     a2.G = grid_out; a2.ng = n_grid; a2.err = *err_dev;
     dim3 g2((n_grid + kTN - 1) / kTN, (n_grid + kTM - 1) / kTM);
     dft_tc_kernel<2><<<g2, 128, smem2, s>>>(a2);

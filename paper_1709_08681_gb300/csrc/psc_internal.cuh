@@ -155,6 +155,15 @@ cudaError_t launch_features(const StencilArgs &a, double *blsum, int n_ant, floa
 // Workspace (bytes) of launch_model_grid; the model grid goes to grid_out
 // and *err_dev points (inside ws) at a flag set if a tensor-core wait ran out.
 size_t model_grid_ws_bytes(int n_img, int n_grid);
+// Model grid of n_comp point components (host [n_comp][3] = l, m, S) on the
+// tensor cores, in the workspace of model_grid_comp_ws_bytes; *err_dev is set
+// if a tensor-core wait ran out.
+size_t model_grid_comp_ws_bytes(int n_comp, int n_grid);
+cudaError_t launch_model_grid_comp(int n_comp, const double *comp_host, int n_grid, double du, void *ws,
+                                   float2 *grid_out, int **err_dev, cudaStream_t s);
+// Least-squares plane w = a u + b v of n_rows baselines (device uvw [n_rows][3]):
+// the sums uu, uv, vv, uw, vw in FP64 go to sums_dev[5] (zeroed by the launcher).
+cudaError_t launch_plane_sums(const double *uvw, long long n_rows, double *sums_dev, cudaStream_t s);
 cudaError_t launch_model_grid(int n_img, int n_grid, const float *image, void *ws, float2 *grid_out, int **err_dev,
                               cudaStream_t s);
 // FP32 split (u_hi, u_lo, v_hi, v_lo) of n uvw triples (FP64 metres).
