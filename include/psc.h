@@ -148,9 +148,10 @@ void psc_solve_opts_default(psc_solve_opts *opts);
  * image_dev: device float [N][N]; grid_out: device complex64 [Ng][Ng];
  * stream: cudaStream_t or NULL.  For N % 8 == 0 the two matrix products run
  * on the tensor cores in split bfloat16 (each FP32 operand as three bfloat16
- * parts, FP32 accumulation; error at FP32 rounding level) and need a
- * temporary workspace of 6 N^2 + 24 Ng N bytes; otherwise FP32 SIMT with a
- * temporary complex64 [N][Ng].  Synchronises the stream before freeing the
+ * parts, FP32 accumulation; error at FP32 rounding level; operands staged by
+ * TMA) and need a temporary workspace of 6 N K + 24 Ng K bytes, K = N rounded
+ * up to a multiple of 32; otherwise FP32 SIMT with a temporary complex64
+ * [N][Ng].  Synchronises the stream before freeing the
  * workspace and returning; PSC_ERR_TIMEOUT if a tensor-core wait ran out. */
 psc_status psc_model_grid(const psc_grid_desc *gd, const float *image_dev, void *grid_out,
                           void *stream);
@@ -161,7 +162,7 @@ psc_status psc_model_grid(const psc_grid_desc *gd, const float *image_dev, void 
  * cell_rad) -- for sources at pixel centres the same grid as psc_model_grid
  * of their image.  One complex matrix product on the tensor cores (split
  * bfloat16 as psc_model_grid; operands from FP64 sincospi; the component
- * count padded to a multiple of 8 with zero flux).  grid_out: device
+ * count padded to a multiple of 32 with zero flux).  grid_out: device
  * complex64 [n_grid][n_grid].  Temporary workspace of 24 n_grid K bytes, K
  * the padded count.  Synchronises.  Errors: PSC_ERR_ARG (sizes, NULL or
  * non-finite input), PSC_ERR_CUDA / PSC_ERR_OOM, PSC_ERR_TIMEOUT (a

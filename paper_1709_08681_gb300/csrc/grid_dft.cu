@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <cstdint>
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 
 #include "psc_internal.cuh"
@@ -147,16 +148,24 @@ __global__ void __launch_bounds__(256) dft_cols_kernel(const float2 *__restrict_
 //   pass 2: G[gy][gx]^T tile: rows gx, columns gy, sum over r of T[r][gx] E[gy][r]
 // with E[g][c] = W((g - Ng/2)(c - N/2)).  Pass 1 writes T already split and
 // transposed (planes [3][Ng][N]) so that both passes read K-major operands.
-// A block owns a 128 x 128 tile with two FP32 accumulators (real, imaginary)
-// in tensor memory; K advances in chunks of 32 through two shared-memory
-// buffers of all operand planes; one thread issues the MMAs (kind::f16, the
+// A block owns a 128 x 64 tile with FP32 accumulators in tensor memory; K
+// advances in chunks of 32 through two shared-memory buffers of all operand
+// planes.  One thread runs the pipeline: it loads a chunk's operands with TMA
+// (cp.async.bulk.tensor, one copy per source and 8-wide K column: the box
+// 8 x rows x 3 planes lands as [plane][row][8 elements], i.e. the no-swizzle
+// K-major core-matrix layout, K columns 3 * rows * 16 bytes apart), waits for
+// the copies on the buffer's load mbarrier, issues the MMAs (kind::f16, the
 // negative term of the complex product by the descriptor's negate-A bit) and
-// commits each chunk to its buffer's mbarrier.  Waits are bounded (*err).
+// commits them to the buffer's MMA mbarrier, which it waits on before the
+// buffer is loaded again.  Tiles past the operands' edges read TMA's zero
+// fill.  Every wait is bounded (*err).
 
 typedef __nv_bfloat16 bf16;
 constexpr int kTM = 128, kTN = 64, kTK = 32;
-constexpr int kPlaneA = kTM * kTK * 2;               // one A operand plane of a chunk (8 KB)
-constexpr int kPlaneB = kTN * kTK * 2;               // one B operand plane of a chunk (4 KB)
+constexpr int kColA = 3 * kTM * 16;                 // one 8-wide K column of an A source, 3 planes (6 KB)
+constexpr int kColB = 3 * kTN * 16;                 // the same of a B source (3 KB)
+constexpr int kSrcA = kTK / 8 * kColA;              // an A source's share of a chunk (24 KB)
+constexpr int kSrcB = kTK / 8 * kColB;              // a B source's share (12 KB)
 constexpr int kEpoch = 4;                            // chunks (K = 128) between promotions to registers
 constexpr long kTcWait = 1L << 24;
 
@@ -183,22 +192,25 @@ __global__ void twiddle64_kernel(double2 *W, int ng) {
     }
 }
 
-// I3[p][r][c] of the N x N image.
-__global__ void split_image_kernel(const float *__restrict__ img, long long n2, bf16 *__restrict__ I3) {
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n2; e += (long long)gridDim.x * blockDim.x) {
+// I3[p][r][c] of the N x N image, each row padded with zeros to kp columns
+// (the GEMM depth, a multiple of the K chunk, so that no chunk is ragged).
+__global__ void split_image_kernel(const float *__restrict__ img, int n, int kp, bf16 *__restrict__ I3) {
+    const long long total = (long long)n * kp;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(e / kp), c = (int)(e % kp);
         bf16 h, m, l;
-        split3(img[e], h, m, l);
-        I3[e] = h; I3[n2 + e] = m; I3[2 * n2 + e] = l;
+        split3(c < n ? img[(size_t)r * n + c] : 0.f, h, m, l);
+        I3[e] = h; I3[total + e] = m; I3[2 * total + e] = l;
     }
 }
 
-// E3re[p][g][c], E3im[p][g][c] (g < Ng, c < N).
-__global__ void split_dft_matrix_kernel(const double2 *__restrict__ W, int n, int ng, bf16 *__restrict__ Er,
+// E3re[p][g][c], E3im[p][g][c] (g < Ng, c < kp; zero for c >= N).
+__global__ void split_dft_matrix_kernel(const double2 *__restrict__ W, int n, int ng, int kp, bf16 *__restrict__ Er,
                                         bf16 *__restrict__ Ei) {
-    const long long total = (long long)ng * n;
+    const long long total = (long long)ng * kp;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
-        const int g = (int)(e / n), c = (int)(e % n);
-        const double2 w = W[phase_index(g, c, ng, n)];
+        const int g = (int)(e / kp), c = (int)(e % kp);
+        const double2 w = c < n ? W[phase_index(g, c, ng, n)] : make_double2(0.0, 0.0);
         bf16 h, m, l;
         split3d(w.x, h, m, l);
         Er[e] = h; Er[total + e] = m; Er[2 * total + e] = l;
@@ -211,7 +223,7 @@ __global__ void split_dft_matrix_kernel(const double2 *__restrict__ W, int n, in
 // u_g = v_g = (g - Ng/2) du, as the second tensor-core pass with
 // A[gx][k] = S_k exp(2 pi i u_gx l_k) and B[gy][k] = exp(2 pi i v_gy m_k): split planes
 // [3][Ng][kp] of the real and imaginary parts, phases from FP64 sincospi,
-// columns k >= n_comp zero (kp = n_comp rounded up to a multiple of 8).
+// columns k >= n_comp zero (kp = n_comp rounded up to a multiple of the K chunk).
 __global__ void split_comp_kernel(const double *__restrict__ comp, int n_comp, int kp, int ng, double du,
                                   bf16 *__restrict__ Ar, bf16 *__restrict__ Ai, bf16 *__restrict__ Br,
                                   bf16 *__restrict__ Bi) {
@@ -237,14 +249,20 @@ __global__ void split_comp_kernel(const double *__restrict__ comp, int n_comp, i
     }
 }
 
-__device__ __forceinline__ uint32_t tc_core_off(int r, int k) {
-    return (uint32_t)((r >> 3) * (kTK / 8 * 128) + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t k_stride) {
+    // K-major, no swizzle: K-adjacent core matrices k_stride bytes apart, 8-row groups 128 B apart
+    return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)((k_stride >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)(128 >> 4) << 32) | ((uint64_t)1 << 46);
 }
 
-__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
-    // K-major, no swizzle: K-adjacent core matrices 128 B apart, 8-row groups kTK / 8 * 128 B apart
-    return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)(128 >> 4) << 16) |
-           ((uint64_t)((kTK / 8 * 128) >> 4) << 32) | ((uint64_t)1 << 46);
+// TMA load of one box of a 3-D tensor map into shared memory, completing on mbar.
+__device__ __forceinline__ void tma_load3(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2, uint32_t mbar) {
+    asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+                 :: "r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(mbar) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect(uint32_t mbar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(mbar), "r"(bytes) : "memory");
 }
 
 __device__ __forceinline__ bool tc_wait(uint32_t addr, uint32_t parity) {
@@ -282,18 +300,31 @@ struct TcPassArgs {
 };
 
 template <int kPass>
-__global__ void __launch_bounds__(128, 1) dft_tc_kernel(const TcPassArgs g) {
+__global__ void __launch_bounds__(128, 1) dft_tc_kernel(const TcPassArgs g, const __grid_constant__ CUtensorMap mA0,
+                                                        const __grid_constant__ CUtensorMap mA1,
+                                                        const __grid_constant__ CUtensorMap mB0,
+                                                        const __grid_constant__ CUtensorMap mB1) {
     constexpr int kNA = kPass == 1 ? 1 : 2;
-    constexpr int kStage = 3 * kNA * kPlaneA + 6 * kPlaneB;   // A planes, then B planes (E re, E im)
+    constexpr int kStage = kNA * kSrcA + 2 * kSrcB;           // A sources, then B sources (E re, E im)
+    constexpr uint32_t kBytes = (uint32_t)kStage;              // TMA bytes of one chunk (zero fill included)
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ __align__(8) uint64_t mbar[2];                  // MMAs of the buffer's chunk done
+    __shared__ __align__(8) uint64_t lbar[2];                  // TMA copies of the buffer's chunk done
+    __shared__ __align__(8) uint64_t pbar;                     // MMAs up to an epoch's last chunk done
     __shared__ uint32_t tmem_base;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m0 = blockIdx.y * kTM, n0 = blockIdx.x * kTN;
     const uint32_t mb[2] = {(uint32_t)__cvta_generic_to_shared(&mbar[0]), (uint32_t)__cvta_generic_to_shared(&mbar[1])};
+    const uint32_t lb[2] = {(uint32_t)__cvta_generic_to_shared(&lbar[0]), (uint32_t)__cvta_generic_to_shared(&lbar[1])};
+    const uint32_t pb = (uint32_t)__cvta_generic_to_shared(&pbar);
+    const CUtensorMap *mapA[2] = {&mA0, &mA1};
+    const CUtensorMap *mapB[2] = {&mB0, &mB1};
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(mb[0]));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(mb[1]));
+        for (int i = 0; i < 2; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(mb[i]));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(lb[i]));
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(pb));
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
     if (warp == 0) {
@@ -314,7 +345,6 @@ __global__ void __launch_bounds__(128, 1) dft_tc_kernel(const TcPassArgs g) {
     const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTN >> 3) << 17) |
                            ((uint32_t)(kTM >> 4) << 24);
     const uint32_t idesc_neg = idesc | (1u << 13);  // negate A
-    const size_t plane_a = (size_t)g.a_rows * g.k, plane_b = (size_t)g.b_rows * g.k;
     const int nk = (g.k + kTK - 1) / kTK;
     const uint32_t smem_base = (uint32_t)__cvta_generic_to_shared(smem);
     const uint32_t lane_base = tmem + ((uint32_t)(32 * warp) << 16);
@@ -323,68 +353,70 @@ __global__ void __launch_bounds__(128, 1) dft_tc_kernel(const TcPassArgs g) {
     for (int j = 0; j < kTN; ++j) { sum_re[j] = 0.f; sum_im[j] = 0.f; }
     bool ok = true;
     bool started[4] = {false, false, false, false};  // used by thread 0 only
+    // Only thread 0 waits on the buffers' barriers (in chunk order, so never
+    // two phases behind); the other threads wait on pbar, one phase per epoch,
+    // committed after the epoch's last chunk and waited by every thread before
+    // the block barrier of the promotion.
+    int loads = 0;                                    // thread 0: chunks whose copies were issued
+    int epoch = 0;                                    // promotions done
     for (int c = 0; c < nk && ok; ++c) {
         const int b = c & 1;
-        if (c >= 2) ok = tc_wait(mb[b], (uint32_t)((c - 2) >> 1) & 1u);
-        if (!ok) break;
-        unsigned char *buf = smem + b * kStage;
-        const int k0 = c * kTK;
-#pragma unroll 1
-        for (int pl = 0; pl < 3 * kNA + 6; ++pl) {
-            const bf16 *src;
-            int rows, r0, nrow;
-            unsigned char *dst;
-            if (pl < 3 * kNA) {
-                src = g.A[pl / 3] + (pl % 3) * plane_a; rows = g.a_rows; r0 = m0; nrow = kTM;
-                dst = buf + pl * kPlaneA;
-            } else {
-                const int q = pl - 3 * kNA;
-                src = g.B[q / 3] + (q % 3) * plane_b; rows = g.b_rows; r0 = n0; nrow = kTN;
-                dst = buf + 3 * kNA * kPlaneA + q * kPlaneB;
-            }
-            for (int seg = tid; seg < nrow * (kTK / 8); seg += blockDim.x) {
-                const int r = seg / (kTK / 8), kq = (seg % (kTK / 8)) * 8;
-                uint4 v = make_uint4(0u, 0u, 0u, 0u);
-                if (r0 + r < rows && k0 + kq < g.k)
-                    v = *reinterpret_cast<const uint4 *>(src + (size_t)(r0 + r) * g.k + k0 + kq);
-                *reinterpret_cast<uint4 *>(dst + tc_core_off(r, kq)) = v;
-            }
-        }
-        asm volatile("fence.proxy.async.shared::cta;");
-        asm volatile("tcgen05.fence::before_thread_sync;");
-        __syncthreads();
-        asm volatile("tcgen05.fence::after_thread_sync;");
+        const bool promote = (c + 1) % kEpoch == 0 || c == nk - 1;
         if (tid == 0) {
+            // the buffer is free once the MMAs of chunk c - 2 are done
+            if (c >= 2) ok = tc_wait(mb[b], (uint32_t)((c - 2) >> 1) & 1u);
             const uint32_t sb = smem_base + (uint32_t)(b * kStage);
-            // plane pairs (A split, B split) kept in each product; pair 0 is head x head
-            const int pp[6][2] = {{0, 0}, {0, 1}, {1, 0}, {1, 1}, {0, 2}, {2, 0}};
-            // terms (accumulator, A source, B source, negate):
-            // pass 1: re += I Er, im += I Ei; pass 2: re += Tr Er - Ti Ei, im += Ti Er + Tr Ei
-            constexpr int kTerms = kPass == 1 ? 2 : 4;
-            const int terms[4][4] = {{0, 0, 0, 0},
-                                     {kPass == 1 ? 1 : 0, kPass == 1 ? 0 : 1, 1, kPass == 1 ? 0 : 1},
-                                     {1, 1, 0, 0},
-                                     {1, 0, 1, 0}};
-            for (int t = 0; t < kTerms; ++t) {
-                const int acc = terms[t][0], sa = terms[t][1], sbs = terms[t][2], neg = terms[t][3];
-                for (int q = 0; q < 6; ++q) {
-                    const uint32_t a_pl = sb + (uint32_t)((sa * 3 + pp[q][0]) * kPlaneA);
-                    const uint32_t b_pl = sb + (uint32_t)(3 * kNA * kPlaneA + (sbs * 3 + pp[q][1]) * kPlaneB);
-                    const int dst = acc + (q == 0 ? 0 : 2);
+            if (ok) {
+                mbar_expect(lb[b], kBytes);
+                const int k0 = c * kTK;
+                for (int j = 0; j < kTK / 8; ++j) {
+                    for (int s_ = 0; s_ < kNA; ++s_)
+                        tma_load3(sb + (uint32_t)(s_ * kSrcA + j * kColA), mapA[s_], k0 + 8 * j, m0, 0, lb[b]);
+                    for (int s_ = 0; s_ < 2; ++s_)
+                        tma_load3(sb + (uint32_t)(kNA * kSrcA + s_ * kSrcB + j * kColB), mapB[s_], k0 + 8 * j, n0, 0,
+                                  lb[b]);
+                }
+                loads = c + 1;
+                ok = tc_wait(lb[b], (uint32_t)(c >> 1) & 1u);
+            }
+            if (ok) {
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                // plane pairs (A split, B split) kept in each product; pair 0 is head x head
+                const int pp[6][2] = {{0, 0}, {0, 1}, {1, 0}, {1, 1}, {0, 2}, {2, 0}};
+                // terms (accumulator, A source, B source, negate):
+                // pass 1: re += I Er, im += I Ei; pass 2: re += Tr Er - Ti Ei, im += Ti Er + Tr Ei
+                constexpr int kTerms = kPass == 1 ? 2 : 4;
+                const int terms[4][4] = {{0, 0, 0, 0},
+                                         {kPass == 1 ? 1 : 0, kPass == 1 ? 0 : 1, 1, kPass == 1 ? 0 : 1},
+                                         {1, 1, 0, 0},
+                                         {1, 0, 1, 0}};
+                for (int t = 0; t < kTerms; ++t) {
+                    const int acc = terms[t][0], sa = terms[t][1], sbs = terms[t][2], neg = terms[t][3];
+                    for (int q = 0; q < 6; ++q) {
+                        // plane p of source s: K column j at + j * kCol, plane p at + p * rows * 16
+                        const uint32_t a_pl = sb + (uint32_t)(sa * kSrcA + pp[q][0] * kTM * 16);
+                        const uint32_t b_pl = sb + (uint32_t)(kNA * kSrcA + sbs * kSrcB + pp[q][1] * kTN * 16);
+                        const int dst = acc + (q == 0 ? 0 : 2);
 #pragma unroll
-                    for (int kk = 0; kk < kTK / 16; ++kk) {
-                        tc_mma(tmem + (uint32_t)(dst * kTN), tc_desc(a_pl + 256u * kk), tc_desc(b_pl + 256u * kk),
-                               neg ? idesc_neg : idesc, started[dst] ? 1u : 0u);
-                        started[dst] = true;
+                        for (int kk = 0; kk < kTK / 16; ++kk) {
+                            tc_mma(tmem + (uint32_t)(dst * kTN), tc_desc(a_pl + (uint32_t)(2 * kk * kColA), kColA),
+                                   tc_desc(b_pl + (uint32_t)(2 * kk * kColB), kColB), neg ? idesc_neg : idesc,
+                                   started[dst] ? 1u : 0u);
+                            started[dst] = true;
+                        }
                     }
                 }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(mb[b]));
+                if (promote)
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(pb));
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(mb[b]));
+            if (!ok) break;
         }
-        if ((c + 1) % kEpoch == 0 || c == nk - 1) {
+        if (promote) {
             // promote: wait for this chunk's MMAs (and with them all earlier ones),
             // add the four accumulators into the FP32 sums, restart them
-            ok = tc_wait(mb[b], (uint32_t)(c >> 1) & 1u);
+            ok = tc_wait(pb, (uint32_t)epoch & 1u);
+            ++epoch;
             if (!ok) break;
             asm volatile("tcgen05.fence::after_thread_sync;");
 #pragma unroll
@@ -408,8 +440,13 @@ __global__ void __launch_bounds__(128, 1) dft_tc_kernel(const TcPassArgs g) {
         }
     }
     if (!ok) {
-        if (tid == 0) atomicExch(g.err, 1);
-        if (nk > 0) tc_wait(mb[(nk - 1) & 1], (uint32_t)((nk - 1) >> 1) & 1u);   // in-flight MMAs, bounded
+        if (tid == 0) {
+            atomicExch(g.err, 1);
+            // copies and MMAs still in flight, bounded: the last issued chunk's copies and
+            // the MMAs of the chunks before it
+            if (loads > 0) tc_wait(lb[(loads - 1) & 1], (uint32_t)((loads - 1) >> 1) & 1u);
+            for (int c = std::max(0, loads - 2); c < loads; ++c) tc_wait(mb[c & 1], (uint32_t)(c >> 1) & 1u);
+        }
     }
     if (ok) {
         const int m = m0 + 32 * warp + lane;         // accumulator lane: pass 1 image row, pass 2 grid column gx
@@ -441,14 +478,75 @@ __global__ void __launch_bounds__(128, 1) dft_tc_kernel(const TcPassArgs g) {
 namespace {
 size_t al256(size_t x) { return (x + 255) / 256 * 256; }
 bool use_tc(int n_img) { return n_img % 8 == 0; }
-// GEMM depth of the component grid: n_comp padded to a multiple of 8 (16-byte rows)
-int comp_depth(int n_comp) { return std::max(8, (n_comp + 7) / 8 * 8); }
+// GEMM depth: padded with zeros to a multiple of the K chunk (no ragged chunk;
+// TMA boxes never start past an operand's end)
+int kpad(int n) { return std::max(kTK, (n + kTK - 1) / kTK * kTK); }
+int comp_depth(int n_comp) { return kpad(n_comp); }
+
+using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// The driver's tensor-map encoder, through the runtime (no link against libcuda).
+cudaError_t encode_fn(EncodeTiled *out) {
+    static EncodeTiled fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q);
+        if (e != cudaSuccess) return e;
+        if (q != cudaDriverEntryPointSuccess || !p) return cudaErrorNotSupported;
+        fn = reinterpret_cast<EncodeTiled>(p);
+    }
+    *out = fn;
+    return cudaSuccess;
+}
+
+// Tensor map of split bfloat16 planes [3][rows][k] (k % 8 == 0, 16-byte aligned
+// base): dimensions (k, rows, 3), box 8 x box_rows x 3 (one 8-wide K column of a
+// tile, all planes), zero fill outside.
+cudaError_t plane_map(CUtensorMap *m, const bf16 *base, int rows, int k, int box_rows) {
+    if (k % 8 || ((uintptr_t)base & 15)) return cudaErrorInvalidValue;
+    EncodeTiled fn = nullptr;
+    cudaError_t e = encode_fn(&fn);
+    if (e != cudaSuccess) return e;
+    const cuuint64_t dims[3] = {(cuuint64_t)k, (cuuint64_t)rows, 3};
+    const cuuint64_t strides[2] = {(cuuint64_t)k * 2, (cuuint64_t)rows * (cuuint64_t)k * 2};
+    const cuuint32_t box[3] = {8, (cuuint32_t)box_rows, 3};
+    const cuuint32_t es[3] = {1, 1, 1};
+    const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<bf16 *>(base), dims, strides, box, es,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+// One pass on the tensor cores: maps of the A sources (rows a_rows) and B
+// sources (rows b_rows), then the launch.
+template <int kPass>
+cudaError_t launch_tc_pass(const TcPassArgs &a, cudaStream_t s) {
+    constexpr int kNA = kPass == 1 ? 1 : 2;
+    const int smem = 2 * (kNA * kSrcA + 2 * kSrcB);
+    CUtensorMap mA[2], mB[2];
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < kNA && e == cudaSuccess; ++i) e = plane_map(&mA[i], a.A[i], a.a_rows, a.k, kTM);
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = plane_map(&mB[i], a.B[i], a.b_rows, a.k, kTN);
+    if (e != cudaSuccess) return e;
+    if (kNA == 1) mA[1] = mA[0];
+    e = cudaFuncSetAttribute(dft_tc_kernel<kPass>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((a.b_rows + kTN - 1) / kTN, (a.a_rows + kTM - 1) / kTM);
+    dft_tc_kernel<kPass><<<grid, 128, smem, s>>>(a, mA[0], mA[1], mB[0], mB[1]);
+    return cudaGetLastError();
+}
 }  // namespace
 
 size_t model_grid_ws_bytes(int n_img, int n_grid) {
     const size_t n = (size_t)n_img, ng = (size_t)n_grid;
     if (use_tc(n_img))
-        return al256(ng * sizeof(double2)) + al256(3 * n * n * 2) + 4 * al256(3 * ng * n * 2) + 256;
+    {
+        const size_t kp = (size_t)kpad(n_img);
+        return al256(ng * sizeof(double2)) + al256(3 * n * kp * 2) + 4 * al256(3 * ng * kp * 2) + 256;
+    }
     return al256(n * ng * sizeof(float2)) + al256(ng * sizeof(float2)) + 256;
 }
 
@@ -469,39 +567,38 @@ cudaError_t launch_model_grid(int n_img, int n_grid, const float *image, void *w
         dft_cols_kernel<<<g2, 256, 0, s>>>(tmp, twiddle, n_img, n_grid, grid_out);
         return cudaGetLastError();
     }
+    const int kp = kpad(n_img);
+    const size_t kz = (size_t)kp;
     double2 *tw = (double2 *)p;
     p += al256(ng * sizeof(double2));
     bf16 *I3 = (bf16 *)p;
-    p += al256(3 * n * n * 2);
-    bf16 *Er = (bf16 *)p; p += al256(3 * ng * n * 2);
-    bf16 *Ei = (bf16 *)p; p += al256(3 * ng * n * 2);
-    bf16 *Tr = (bf16 *)p; p += al256(3 * ng * n * 2);
-    bf16 *Ti = (bf16 *)p; p += al256(3 * ng * n * 2);
+    p += al256(3 * n * kz * 2);
+    bf16 *Er = (bf16 *)p; p += al256(3 * ng * kz * 2);
+    bf16 *Ei = (bf16 *)p; p += al256(3 * ng * kz * 2);
+    bf16 *Tr = (bf16 *)p; p += al256(3 * ng * kz * 2);
+    bf16 *Ti = (bf16 *)p; p += al256(3 * ng * kz * 2);
     *err_dev = (int *)p;
     cudaError_t e = cudaMemsetAsync(*err_dev, 0, sizeof(int), s);
-    if (e != cudaSuccess) return e;
-    const int smem1 = 2 * (3 * kPlaneA + 6 * kPlaneB), smem2 = 2 * (6 * kPlaneA + 6 * kPlaneB);
-    e = cudaFuncSetAttribute(dft_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem1);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(dft_tc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem2);
+    // pass 1 writes T's first N columns; the padding columns stay zero
+    if (e == cudaSuccess) e = cudaMemsetAsync(Tr, 0, 2 * al256(3 * ng * kz * 2), s);
     if (e != cudaSuccess) return e;
     twiddle64_kernel<<<(n_grid + 255) / 256, 256, 0, s>>>(tw, n_grid);
-    split_image_kernel<<<(int)std::min<size_t>((n * n + 255) / 256, 4096), 256, 0, s>>>(image, (long long)(n * n), I3);
-    split_dft_matrix_kernel<<<(int)std::min<size_t>((ng * n + 255) / 256, 8192), 256, 0, s>>>(tw, n_img, n_grid, Er, Ei);
+    split_image_kernel<<<(int)std::min<size_t>((n * kz + 255) / 256, 4096), 256, 0, s>>>(image, n_img, kp, I3);
+    split_dft_matrix_kernel<<<(int)std::min<size_t>((ng * kz + 255) / 256, 8192), 256, 0, s>>>(tw, n_img, n_grid, kp, Er,
+                                                                                                  Ei);
     TcPassArgs a1{};
     a1.A[0] = I3; a1.n_a = 1;
     a1.B[0] = Er; a1.B[1] = Ei;
-    a1.a_rows = n_img; a1.b_rows = n_grid; a1.k = n_img;
+    a1.a_rows = n_img; a1.b_rows = n_grid; a1.k = kp;
     a1.Tr = Tr; a1.Ti = Ti; a1.ng = n_grid; a1.err = *err_dev;
-    dim3 g1((n_grid + kTN - 1) / kTN, (n_img + kTM - 1) / kTM);
-    dft_tc_kernel<1><<<g1, 128, smem1, s>>>(a1);
+    e = launch_tc_pass<1>(a1, s);
+    if (e != cudaSuccess) return e;
     TcPassArgs a2{};
     a2.A[0] = Tr; a2.A[1] = Ti; a2.n_a = 2;
     a2.B[0] = Er; a2.B[1] = Ei;
-    a2.a_rows = n_grid; a2.b_rows = n_grid; a2.k = n_img;
+    a2.a_rows = n_grid; a2.b_rows = n_grid; a2.k = kp;
     a2.G = grid_out; a2.ng = n_grid; a2.err = *err_dev;
-    dim3 g2((n_grid + kTN - 1) / kTN, (n_grid + kTM - 1) / kTM);
-    dft_tc_kernel<2><<<g2, 128, smem2, s>>>(a2);
-    return cudaGetLastError();
+    return launch_tc_pass<2>(a2, s);
 }
 
 size_t model_grid_comp_ws_bytes(int n_comp, int n_grid) {
@@ -523,8 +620,6 @@ cudaError_t launch_model_grid_comp(int n_comp, const double *comp_host, int n_gr
     cudaError_t e = cudaMemsetAsync(*err_dev, 0, sizeof(int), s);
     if (e == cudaSuccess && n_comp > 0)
         e = cudaMemcpyAsync(comp, comp_host, (size_t)n_comp * 3 * sizeof(double), cudaMemcpyHostToDevice, s);
-    const int smem2 = 2 * (6 * kPlaneA + 6 * kPlaneB);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(dft_tc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem2);
     if (e != cudaSuccess) return e;
     split_comp_kernel<<<(int)std::min<size_t>((ng * kp + 255) / 256, 8192), 256, 0, s>>>(comp, n_comp, kp, n_grid, du,
                                                                                           Ar, Ai, Br, Bi);
@@ -533,9 +628,7 @@ cudaError_t launch_model_grid_comp(int n_comp, const double *comp_host, int n_gr
     a2.B[0] = Br; a2.B[1] = Bi;
     a2.a_rows = n_grid; a2.b_rows = n_grid; a2.k = kp;
     a2.G = grid_out; a2.ng = n_grid; a2.err = *err_dev;
-    dim3 g2((n_grid + kTN - 1) / kTN, (n_grid + kTM - 1) / kTM);
-    dft_tc_kernel<2><<<g2, 128, smem2, s>>>(a2);
-    return cudaGetLastError();
+    return launch_tc_pass<2>(a2, s);
 }
 
 }  // namespace psc
