@@ -61,6 +61,7 @@ enum { PSC_AP_DISK = 0, PSC_AP_GAUSS = 1 };
 enum { PSC_GRID_F32 = 0, PSC_GRID_BF16 = 1 };
 enum { PSC_STAGE_AUTO = 0, PSC_STAGE_NEVER = 1 };
 enum { PSC_KERNEL_GAUSS = 0, PSC_KERNEL_EXACT_DISK = 1 };
+enum { PSC_ORDER_BASELINE = 0, PSC_ORDER_UV = 1 };
 enum { PSC_LM_FULL = 0, PSC_LM_BLOCK = 1 };
 enum { PSC_STOP_NONE = 0, PSC_STOP_STEP = 1, PSC_STOP_CHI2 = 2, PSC_STOP_LAMBDA = 3,
        PSC_STOP_MAX_ITER = 4, PSC_STOP_NUMERIC = 5 };
@@ -292,6 +293,16 @@ psc_status psc_fp32_fma_rate(double *tflops, void *stream);
  * a brick's visibilities share few cells).  Results are the same up to FP32
  * summation order.  Errors: PSC_ERR_ARG for an unknown mode. */
 psc_status psc_set_staging(psc_ctx *ctx, int mode);
+
+/* Launch order of the fused kernel's bricks.  PSC_ORDER_BASELINE: baselines
+ * in (i, j) order.  PSC_ORDER_UV: baselines in Morton (Z-curve) order of
+ * their (u, v) at the interval's middle time step, so that the bricks running
+ * together read nearby grid cells (L2 reuse when the grid is larger than L2).
+ * psc_create picks PSC_ORDER_UV for grids of more than 128 MB, else
+ * PSC_ORDER_BASELINE.  Results are identical: each brick's partial sums keep
+ * their place, and the reductions run in the same order.  Used by the
+ * Gaussian-model kernel (single launches and batches).  Errors: PSC_ERR_ARG. */
+psc_status psc_set_brick_order(psc_ctx *ctx, int order);
 
 /* Aperture kernel model of psc_predict, psc_residual_grad, psc_lm_* and
  * psc_solve_offsets on this context.

@@ -22,6 +22,7 @@ PSC_AP_DISK, PSC_AP_GAUSS = 0, 1
 PSC_GRID_F32, PSC_GRID_BF16 = 0, 1
 PSC_STAGE_AUTO, PSC_STAGE_NEVER = 0, 1
 PSC_KERNEL_GAUSS, PSC_KERNEL_EXACT_DISK = 0, 1
+PSC_ORDER_BASELINE, PSC_ORDER_UV = 0, 1
 PSC_LM_FULL, PSC_LM_BLOCK = 0, 1
 STOP_REASONS = {0: "none", 1: "step", 2: "chi2", 3: "lambda", 4: "max_iter", 5: "numeric"}
 
@@ -29,7 +30,7 @@ EXPORTS = ("psc_solve_opts_default", "psc_model_grid", "psc_model_grid_component
            "psc_snapshot_components", "psc_create", "psc_destroy", "psc_last_error",
            "psc_predict", "psc_residual_grad", "psc_solve_offsets", "psc_lm_begin", "psc_lm_iterate",
            "psc_lm_end", "psc_lm_restart", "psc_set_tiling", "psc_set_grid_precision", "psc_set_staging",
-           "psc_set_kernel_model", "psc_set_flat_tiling", "psc_fp32_fma_rate", "psc_profile", "psc_profile_read",
+           "psc_set_kernel_model", "psc_set_flat_tiling", "psc_set_brick_order", "psc_fp32_fma_rate", "psc_profile", "psc_profile_read",
            "psc_residual_grad_noalloc", "psc_batch_create", "psc_batch_destroy", "psc_batch_last_error",
            "psc_batch_autotune", "psc_batch_begin", "psc_batch_restart", "psc_batch_iterate", "psc_batch_end",
            "psc_solve_batch", "psc_batch_profile", "psc_batch_profile_read", "psc_features",
@@ -108,6 +109,7 @@ def lib():
             "psc_set_staging": (ctypes.c_int, [_V, ctypes.c_int]),
             "psc_set_kernel_model": (ctypes.c_int, [_V, ctypes.c_int]),
             "psc_set_flat_tiling": (ctypes.c_int, [_V, ctypes.c_int, ctypes.c_int]),
+            "psc_set_brick_order": (ctypes.c_int, [_V, ctypes.c_int]),
             "psc_fp32_fma_rate": (ctypes.c_int, [_D, _V]),
             "psc_profile": (ctypes.c_int, [_V, ctypes.c_int]),
             "psc_profile_read": (ctypes.c_int, [_V, _D, ctypes.POINTER(ctypes.c_int)]),
@@ -275,6 +277,9 @@ class Context:
 
     def psc_set_staging(self, mode):
         _check(lib().psc_set_staging(self.h, int(mode)), self.h)
+
+    def psc_set_brick_order(self, order):
+        _check(lib().psc_set_brick_order(self.h, int(order)), self.h)
 
     def psc_set_flat_tiling(self, items, vis_per_thread):
         _check(lib().psc_set_flat_tiling(self.h, int(items), int(vis_per_thread)), self.h)

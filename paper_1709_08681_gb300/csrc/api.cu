@@ -49,6 +49,8 @@ struct psc_ctx {
     int flat = 0;                // > 0: bricks of `flat` consecutive (channel, time-group) items
     int no_stage = 0;            // PSC_STAGE_NEVER: taps read the grid from global memory
     int kernel_model = PSC_KERNEL_GAUSS;
+    int brick_order = PSC_ORDER_BASELINE;
+    int *d_bl_order = nullptr;   // baselines in Morton order of their mid-interval (u, v)
     float *d_kmom = nullptr;     // exact disk kernel: lens-moment combinations (psc_set_kernel_model)
     std::vector<double> h_freq;  // channel frequencies (Hz)
     std::vector<int> h_tab_off, h_tab_len;   // radial table layout per channel
@@ -108,6 +110,7 @@ void free_ctx(psc_ctx *c) {
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     cudaFree(c->d_grid_bf16);
     cudaFree(c->d_kmom);
+    cudaFree(c->d_bl_order);
     cudaFree(c->d_uvs);
     cudaFree(c->d_spart);
     cudaFree(c->d_sblsum);
@@ -198,6 +201,7 @@ EvalArgs eval_args(const psc_ctx *c, const double *lm_dev) {
     a.bpb = (int)bricks_per_bl(c);
     a.ch_span = ch_span(c);
     a.exact = c->kernel_model == PSC_KERNEL_EXACT_DISK;
+    a.bl_order = c->brick_order == PSC_ORDER_UV ? c->d_bl_order : nullptr;
     a.kmom = c->d_kmom;
     return a;
 }
@@ -473,6 +477,32 @@ psc_status psc_create(psc_ctx **out, const psc_obs *obs, const psc_aperture *ap,
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_len, len.data(), sizeof(int) * c->nc, cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = launch_tables(*ap, d_freq, c->nc, c->du, ov, gd->support, d_off, d_len, c->d_tabs, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_state, 0, sizeof(LMState), c->stream);
+    // baselines in Morton (Z) order of their (u, v) at the middle time step, for
+    // PSC_ORDER_UV: bricks launched together then read nearby grid cells
+    std::vector<double> mid((size_t)c->n_bl * 3);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(mid.data(), c->uvw + (size_t)(c->nt / 2) * c->n_bl * 3, sizeof(double) * mid.size(),
+                            cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess) e = dalloc(&c->d_bl_order, c->n_bl);
+    if (e == cudaSuccess) {
+        double span = 0.0;
+        for (int b = 0; b < c->n_bl; ++b) span = std::max(span, std::max(std::fabs(mid[3 * b]), std::fabs(mid[3 * b + 1])));
+        std::vector<std::pair<uint32_t, int>> key(c->n_bl);
+        for (int b = 0; b < c->n_bl; ++b) {
+            auto q = [&](double x) { return (uint32_t)std::min(1023.0, std::max(0.0, (x / (span > 0 ? span : 1.0) * 0.5 + 0.5) * 1024.0)); };
+            const uint32_t qu = q(mid[3 * b]), qv = q(mid[3 * b + 1]);
+            uint32_t z = 0;
+            for (int bit = 0; bit < 10; ++bit) z |= (((qu >> bit) & 1u) << (2 * bit)) | (((qv >> bit) & 1u) << (2 * bit + 1));
+            key[b] = {z, b};
+        }
+        std::sort(key.begin(), key.end());
+        std::vector<int> order(c->n_bl);
+        for (int b = 0; b < c->n_bl; ++b) order[b] = key[b].second;
+        e = cudaMemcpyAsync(c->d_bl_order, order.data(), sizeof(int) * c->n_bl, cudaMemcpyHostToDevice, c->stream);
+        // default: locality order when the grid is larger than L2 (128 MB)
+        if ((size_t)gd->n_grid * gd->n_grid * sizeof(float2) > ((size_t)128 << 20)) c->brick_order = PSC_ORDER_UV;
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     cudaFree(d_freq);
     cudaFree(d_off);
@@ -590,6 +620,13 @@ psc_status psc_set_kernel_model(psc_ctx *ctx, int model) {
     ctx->kernel_model = model;
     ctx->kv = 1;
     ctx->flat = 0;
+    return PSC_OK;
+}
+
+psc_status psc_set_brick_order(psc_ctx *ctx, int order) {
+    if (!ctx) return fail(nullptr, PSC_ERR_ARG, "ctx is NULL");
+    if (order != PSC_ORDER_BASELINE && order != PSC_ORDER_UV) return fail(ctx, PSC_ERR_ARG, "order must be PSC_ORDER_BASELINE or PSC_ORDER_UV");
+    ctx->brick_order = order;
     return PSC_OK;
 }
 

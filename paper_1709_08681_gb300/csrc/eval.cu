@@ -581,7 +581,9 @@ __global__ void __launch_bounds__(kMaxThreads) eval_kernel(const EvalArgs a0, co
     const EvalArgs &a = s_a;
     if (!(a.skip != nullptr && *a.skip)) {
     const int tid = threadIdx.x;
-    const int brick = persistent ? (int)(s_work - s_first) : (int)blockIdx.x;
+    const int qbrick = persistent ? (int)(s_work - s_first) : (int)blockIdx.x;
+    // launch order -> brick (baseline groups permuted for locality when bl_order is set)
+    const int brick = a.bl_order != nullptr ? a.bl_order[qbrick / a.bpb] * a.bpb + qbrick % a.bpb : qbrick;
     float acc[kRed];
 #pragma unroll
     for (int k = 0; k < kRed; ++k) acc[k] = 0.f;

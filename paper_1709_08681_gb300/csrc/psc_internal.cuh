@@ -57,6 +57,9 @@ struct EvalArgs {
     // holds items [b flat, (b + 1) flat), so bpb bricks per baseline, each
     // spanning at most ch_span channels.
     int flat, n_tp, bpb, ch_span;
+    // nullptr, or [n_bl]: the baseline of each group of bpb consecutive bricks in
+    // launch order (partials stay indexed by baseline: brick = bl * bpb + j)
+    const int *bl_order;
 };
 
 // Arguments of the stencil-feature kernel (learned initial estimate).

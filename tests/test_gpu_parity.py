@@ -364,3 +364,29 @@ def test_visibilities_on_and_near_grid_nodes():
     Vg, dVg = GpuProblem(m2, img).predict(lm)
     assert _rel(Vg, V) < TOL_V
     assert max(_rel(dVg[p], dV[p]) for p in range(4)) < TOL_V
+
+
+def test_brick_order_keeps_results_bitwise():
+    """PSC_ORDER_UV permutes the launch order of baseline groups; every brick's
+    partial sums keep their place, so the results are identical."""
+    m, _, lmt, img = cases.problem(cases.DISK_SMALL, n_ant=9, n_time=37, freqs=(1.3e9, 1.4e9, 1.5e9),
+                                   sigma_arcsec=30.0, extent_m=800.0)
+    vobs, w = _obs(m, lmt)
+    gp = GpuProblem(m, img)
+    vd, wd = gp.upload(vobs), gp.upload(w, torch.float32)
+    for flat in (False, True):
+        if flat:
+            gp.ctx.psc_set_flat_tiling(128, 2)
+        gp.ctx.psc_set_brick_order(_abi.PSC_ORDER_BASELINE)
+        a = gp.ctx.psc_residual_grad(0.5 * lmt, vd, wd, 1.0, cross=True)
+        gp.ctx.psc_set_brick_order(_abi.PSC_ORDER_UV)
+        b = gp.ctx.psc_residual_grad(0.5 * lmt, vd, wd, 1.0, cross=True)
+        assert a[0] == b[0]
+        for x, y in zip(a[1:], b[1:]):
+            assert np.array_equal(x, y)
+        sol, rep = gp.ctx.psc_solve_offsets(vd, wd, 1.0)
+        gp.ctx.psc_set_brick_order(_abi.PSC_ORDER_BASELINE)
+        sol0, rep0 = gp.ctx.psc_solve_offsets(vd, wd, 1.0)
+        assert np.array_equal(sol, sol0) and rep.n_iter == rep0.n_iter
+    with pytest.raises(_abi.PscError):
+        gp.ctx.psc_set_brick_order(5)
