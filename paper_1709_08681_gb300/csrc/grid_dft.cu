@@ -149,16 +149,17 @@ __global__ void __launch_bounds__(256) dft_cols_kernel(const float2 *__restrict_
 // with E[g][c] = W((g - Ng/2)(c - N/2)).  Pass 1 writes T already split and
 // transposed (planes [3][Ng][N]) so that both passes read K-major operands.
 // A block owns a 128 x 64 tile with FP32 accumulators in tensor memory; K
-// advances in chunks of 32 through two shared-memory buffers of all operand
-// planes.  One thread runs the pipeline: it loads a chunk's operands with TMA
-// (cp.async.bulk.tensor, one copy per source and 8-wide K column: the box
-// 8 x rows x 3 planes lands as [plane][row][8 elements], i.e. the no-swizzle
-// K-major core-matrix layout, K columns 3 * rows * 16 bytes apart), waits for
-// the copies on the buffer's load mbarrier, issues the MMAs (kind::f16, the
-// negative term of the complex product by the descriptor's negate-A bit) and
-// commits them to the buffer's MMA mbarrier, which it waits on before the
-// buffer is loaded again.  Tiles past the operands' edges read TMA's zero
-// fill.  Every wait is bounded (*err).
+// advances in chunks of 32 through shared-memory buffers of all operand
+// planes.  One thread runs the pipeline over three shared-memory buffers: it
+// loads chunks two ahead with TMA (cp.async.bulk.tensor, one copy per source
+// and 8-wide K column: the box 8 x rows x 3 planes lands as [plane][row][8
+// elements], i.e. the no-swizzle K-major core-matrix layout, K columns
+// 3 * rows * 16 bytes apart), waits for a chunk's copies on its buffer's load
+// mbarrier, issues the MMAs (kind::f16, the negative term of the complex
+// product by the descriptor's negate-A bit), commits them to the buffer's MMA
+// mbarrier, and refills the previous chunk's buffer once those MMAs are done.
+// Rows past the operands' edges read TMA's zero fill; the depth K is padded
+// with zeros to a multiple of the chunk.  Every wait is bounded (*err).
 
 typedef __nv_bfloat16 bf16;
 constexpr int kTM = 128, kTN = 64, kTK = 32;
@@ -167,6 +168,7 @@ constexpr int kColB = 3 * kTN * 16;                 // the same of a B source (3
 constexpr int kSrcA = kTK / 8 * kColA;              // an A source's share of a chunk (24 KB)
 constexpr int kSrcB = kTK / 8 * kColB;              // a B source's share (12 KB)
 constexpr int kEpoch = 4;                            // chunks (K = 128) between promotions to registers
+constexpr int kStages = 3;                           // shared-memory buffers of the TMA pipeline
 constexpr long kTcWait = 1L << 24;
 
 __device__ __forceinline__ void split3(float x, bf16 &h, bf16 &m, bf16 &l) {
@@ -308,19 +310,22 @@ __global__ void __launch_bounds__(128, 1) dft_tc_kernel(const TcPassArgs g, cons
     constexpr int kStage = kNA * kSrcA + 2 * kSrcB;           // A sources, then B sources (E re, E im)
     constexpr uint32_t kBytes = (uint32_t)kStage;              // TMA bytes of one chunk (zero fill included)
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ __align__(8) uint64_t mbar[2];                  // MMAs of the buffer's chunk done
-    __shared__ __align__(8) uint64_t lbar[2];                  // TMA copies of the buffer's chunk done
+    __shared__ __align__(8) uint64_t mbar[kStages];            // MMAs of the buffer's chunk done
+    __shared__ __align__(8) uint64_t lbar[kStages];            // TMA copies of the buffer's chunk done
     __shared__ __align__(8) uint64_t pbar;                     // MMAs up to an epoch's last chunk done
     __shared__ uint32_t tmem_base;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m0 = blockIdx.y * kTM, n0 = blockIdx.x * kTN;
-    const uint32_t mb[2] = {(uint32_t)__cvta_generic_to_shared(&mbar[0]), (uint32_t)__cvta_generic_to_shared(&mbar[1])};
-    const uint32_t lb[2] = {(uint32_t)__cvta_generic_to_shared(&lbar[0]), (uint32_t)__cvta_generic_to_shared(&lbar[1])};
+    uint32_t mb[kStages], lb[kStages];
+    for (int i = 0; i < kStages; ++i) {
+        mb[i] = (uint32_t)__cvta_generic_to_shared(&mbar[i]);
+        lb[i] = (uint32_t)__cvta_generic_to_shared(&lbar[i]);
+    }
     const uint32_t pb = (uint32_t)__cvta_generic_to_shared(&pbar);
     const CUtensorMap *mapA[2] = {&mA0, &mA1};
     const CUtensorMap *mapB[2] = {&mB0, &mB1};
     if (tid == 0) {
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < kStages; ++i) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(mb[i]));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(lb[i]));
         }
@@ -356,29 +361,33 @@ __global__ void __launch_bounds__(128, 1) dft_tc_kernel(const TcPassArgs g, cons
     // Only thread 0 waits on the buffers' barriers (in chunk order, so never
     // two phases behind); the other threads wait on pbar, one phase per epoch,
     // committed after the epoch's last chunk and waited by every thread before
-    // the block barrier of the promotion.
+    // the block barrier of the promotion.  Thread 0 keeps the copies kStages - 1
+    // chunks ahead: it issues a chunk's MMAs as soon as its copies have landed,
+    // then refills the buffer of the previous chunk once that chunk's MMAs are done.
     int loads = 0;                                    // thread 0: chunks whose copies were issued
+    int mmas = 0;                                     // thread 0: chunks whose MMAs were issued
     int epoch = 0;                                    // promotions done
+    auto issue_copies = [&](int ch) {
+        const int bb = ch % kStages;
+        const uint32_t sb = smem_base + (uint32_t)(bb * kStage);
+        mbar_expect(lb[bb], kBytes);
+        const int k0 = ch * kTK;
+        for (int j = 0; j < kTK / 8; ++j) {
+            for (int s_ = 0; s_ < kNA; ++s_)
+                tma_load3(sb + (uint32_t)(s_ * kSrcA + j * kColA), mapA[s_], k0 + 8 * j, m0, 0, lb[bb]);
+            for (int s_ = 0; s_ < 2; ++s_)
+                tma_load3(sb + (uint32_t)(kNA * kSrcA + s_ * kSrcB + j * kColB), mapB[s_], k0 + 8 * j, n0, 0, lb[bb]);
+        }
+        loads = ch + 1;
+    };
+    if (tid == 0)
+        for (int ch = 0; ch < kStages - 1 && ch < nk; ++ch) issue_copies(ch);
     for (int c = 0; c < nk && ok; ++c) {
-        const int b = c & 1;
+        const int b = c % kStages;
         const bool promote = (c + 1) % kEpoch == 0 || c == nk - 1;
         if (tid == 0) {
-            // the buffer is free once the MMAs of chunk c - 2 are done
-            if (c >= 2) ok = tc_wait(mb[b], (uint32_t)((c - 2) >> 1) & 1u);
+            ok = tc_wait(lb[b], (uint32_t)(c / kStages) & 1u);          // this chunk's copies
             const uint32_t sb = smem_base + (uint32_t)(b * kStage);
-            if (ok) {
-                mbar_expect(lb[b], kBytes);
-                const int k0 = c * kTK;
-                for (int j = 0; j < kTK / 8; ++j) {
-                    for (int s_ = 0; s_ < kNA; ++s_)
-                        tma_load3(sb + (uint32_t)(s_ * kSrcA + j * kColA), mapA[s_], k0 + 8 * j, m0, 0, lb[b]);
-                    for (int s_ = 0; s_ < 2; ++s_)
-                        tma_load3(sb + (uint32_t)(kNA * kSrcA + s_ * kSrcB + j * kColB), mapB[s_], k0 + 8 * j, n0, 0,
-                                  lb[b]);
-                }
-                loads = c + 1;
-                ok = tc_wait(lb[b], (uint32_t)(c >> 1) & 1u);
-            }
             if (ok) {
                 asm volatile("tcgen05.fence::after_thread_sync;");
                 // plane pairs (A split, B split) kept in each product; pair 0 is head x head
@@ -409,6 +418,13 @@ __global__ void __launch_bounds__(128, 1) dft_tc_kernel(const TcPassArgs g, cons
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(mb[b]));
                 if (promote)
                     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(pb));
+                mmas = c + 1;
+            }
+            // refill: chunk c + kStages - 1 goes into the buffer of chunk c - 1
+            const int nx = c + kStages - 1;
+            if (ok && nx < nk) {
+                if (c >= 1) ok = tc_wait(mb[(c - 1) % kStages], (uint32_t)((c - 1) / kStages) & 1u);
+                if (ok) issue_copies(nx);
             }
             if (!ok) break;
         }
@@ -444,8 +460,9 @@ __global__ void __launch_bounds__(128, 1) dft_tc_kernel(const TcPassArgs g, cons
             atomicExch(g.err, 1);
             // copies and MMAs still in flight, bounded: the last issued chunk's copies and
             // the MMAs of the chunks before it
-            if (loads > 0) tc_wait(lb[(loads - 1) & 1], (uint32_t)((loads - 1) >> 1) & 1u);
-            for (int c = std::max(0, loads - 2); c < loads; ++c) tc_wait(mb[c & 1], (uint32_t)(c >> 1) & 1u);
+            for (int c = mmas; c < loads; ++c) tc_wait(lb[c % kStages], (uint32_t)(c / kStages) & 1u);
+            for (int c = std::max(0, mmas - kStages); c < mmas; ++c)
+                tc_wait(mb[c % kStages], (uint32_t)(c / kStages) & 1u);
         }
     }
     if (ok) {
@@ -525,7 +542,7 @@ cudaError_t plane_map(CUtensorMap *m, const bf16 *base, int rows, int k, int box
 template <int kPass>
 cudaError_t launch_tc_pass(const TcPassArgs &a, cudaStream_t s) {
     constexpr int kNA = kPass == 1 ? 1 : 2;
-    const int smem = 2 * (kNA * kSrcA + 2 * kSrcB);
+    const int smem = kStages * (kNA * kSrcA + 2 * kSrcB);
     CUtensorMap mA[2], mB[2];
     cudaError_t e = cudaSuccess;
     for (int i = 0; i < kNA && e == cudaSuccess; ++i) e = plane_map(&mA[i], a.A[i], a.a_rows, a.k, kTM);

@@ -390,3 +390,40 @@ def test_brick_order_keeps_results_bitwise():
         assert np.array_equal(sol, sol0) and rep.n_iter == rep0.n_iter
     with pytest.raises(_abi.PscError):
         gp.ctx.psc_set_brick_order(5)
+
+
+# Support and oversampling at the ends of their ranges: a window narrower than
+# the disk (S = 8, taps clipped to it), the widest window (S = 64, boxes past
+# the staging tile for the Gaussian pattern), and a coarse table (ov = 4).
+SUPPORT_CASES = [
+    (cases.DISK_SMALL, 8, 20),
+    (cases.DISK_SMALL, 16, 4),
+    (cases.DISK_SMALL, 64, 20),
+    (cases.GAUSS_SMALL, 64, 8),
+]
+
+
+@pytest.mark.parametrize("spec,support,ov", SUPPORT_CASES)
+def test_support_and_oversampling_extremes_match_oracle(spec, support, ov):
+    import dataclasses
+    m, _, lmt, img = cases.problem(spec, n_ant=6, n_time=17, freqs=(1.3e9, 1.45e9), sigma_arcsec=40.0,
+                                   support=support)
+    m = dataclasses.replace(m, oversample=ov)
+    V, dV = psc.predict(m, lmt)
+    gp = GpuProblem(m, img)
+    Vg, dVg = gp.predict(lmt)
+    assert _rel(Vg, V) < TOL_V
+    assert max(_rel(dVg[p], dV[p]) for p in range(4)) < TOL_V
+    vobs, w = _obs(m, lmt)
+    chi2, g, H, X = psc.chi2_grad_normal(m, 0.5 * lmt, vobs, w)
+    chi2g, gg, Hg, Xg = gp.ctx.psc_residual_grad(0.5 * lmt, gp.upload(vobs), gp.upload(w, torch.float32), 1.0,
+                                                 cross=True)
+    assert abs(chi2g - chi2) < TOL_V * _chi2_scale(m, 0.5 * lmt, vobs, w)
+    assert np.max(np.abs(Hg - H)) < TOL_V * np.max(np.abs(H))
+
+
+def test_blank_sky_predicts_exact_zeros():
+    m, _, lmt, img = cases.problem(cases.DISK_SMALL, n_ant=5, n_time=9)
+    gp = GpuProblem(m, np.zeros_like(img))
+    Vg, dVg = gp.predict(lmt)
+    assert not np.any(Vg) and not np.any(dVg)
