@@ -59,7 +59,14 @@ namespace psc {
 namespace {
 
 constexpr int kNodes = 32;            // Gauss-Legendre nodes of the moment quadrature
-constexpr int kTabF4 = 4;             // float4s per interpolation entry
+// An interpolation entry is three float4 (P0, P1 | P2, P3 | Q0, Q1 as intercepts
+// then slopes) and one float2 (Q2); each of the four parts lives in its own
+// array, so that entries of neighbouring radii are 16 (8) bytes apart and the
+// lanes' lookups spread over the shared-memory banks.
+struct TabView {
+    const float4 *e0, *e1, *e2;
+    const float2 *e3;
+};
 __constant__ double c_gl[2 * kNodes]; // nodes on [-1, 1], then weights
 
 // gamma_n = (-1)^n (2 pi)^(2n) / (2n)!
@@ -159,9 +166,9 @@ struct ExactShared {
 };
 
 // Per-tap sums of one row of taps (n cells from `row`, the first at table
-// coordinate dxo, the row at dyo2 = dyo^2, q = dl.(dxo, dyo)).  Entry layout
-// (intercept, slope) per value: e[0] = (P0, P1 | P0, P1), e[1] = (P2, P3 | ..),
-// e[2] = (Q0, Q1 | ..), e[3] = (Q2 | Q2, -, -).
+// coordinate dxo, the row at dyo2 = dyo^2, q = dl.(dxo, dyo)).  Entry parts
+// (intercepts, then slopes): e0 = (P0, P1 | P0, P1), e1 = (P2, P3 | ..),
+// e2 = (Q0, Q1 | ..), e3 = (Q2 | Q2).
 struct RowSums {
     float2 P, Q, X, Y, Z;   // sum O g, O dxo g, Os g, W g, W dxo g
 };
@@ -169,15 +176,15 @@ struct RowSums {
 template <bool kGlobal>
 __device__ __forceinline__ void exact_row(const float2 *__restrict__ row, const float2 *__restrict__ phx, int a0,
                                           int n, float dxo, float dyo2, float q, float ov, float dlx_ov,
-                                          const float4 *__restrict__ tab, RowSums &r) {
+                                          const TabView tab, RowSums &r) {
     for (int k = 0; k < n; ++k) {
         float2 g = row[k];
         if constexpr (kGlobal) g = cmul(g, phx[a0 + k]);
         const float s2 = fmaf(dxo, dxo, dyo2);
         const float t = sqrt_fast(s2);
         const int idx = (int)t;
-        const float4 e0 = tab[idx * kTabF4], e1 = tab[idx * kTabF4 + 1], e2 = tab[idx * kTabF4 + 2];
-        const float2 e3 = *reinterpret_cast<const float2 *>(&tab[idx * kTabF4 + 3]);
+        const float4 e0 = tab.e0[idx], e1 = tab.e1[idx], e2 = tab.e2[idx];
+        const float2 e3 = tab.e3[idx];
         const float P0 = fmaf(t, e0.z, e0.x), P1 = fmaf(t, e0.w, e0.y);
         const float P2 = fmaf(t, e1.z, e1.x), P3 = fmaf(t, e1.w, e1.y);
         const float Q0 = fmaf(t, e2.z, e2.x), Q1 = fmaf(t, e2.w, e2.y);
@@ -203,7 +210,7 @@ __device__ __forceinline__ void exact_row(const float2 *__restrict__ row, const 
 // partials[k * n_bricks + brick]; predict mode writes V and dV.
 template <bool kPredict>
 __global__ void __launch_bounds__(kMaxThreads) exact_kernel(const EvalArgs a) {
-    extern __shared__ float4 s_tab[];                 // c_group * tab_stride entries of kTabF4 float4s
+    extern __shared__ float4 s_tab[];                 // three float4 arrays, then a float2 array, of c_group * tab_stride
     __shared__ ExactShared sh;
     const int tid = threadIdx.x;
     const int brick = blockIdx.x;
@@ -233,6 +240,8 @@ __global__ void __launch_bounds__(kMaxThreads) exact_kernel(const EvalArgs a) {
         active = lcg < a.c_group && t < a.nt && c < a.nc;
     }
     const int lc = c - c_first;
+    // channel slots of the tables in shared memory (as launch_exact sizes them)
+    const size_t cs = (size_t)(a.flat > 0 ? a.ch_span : a.c_group) * a.tab_stride;
     const int tab_stride = a.tab_stride;
     const int S = a.support;
     if (a.skip != nullptr && *a.skip) return;
@@ -293,11 +302,11 @@ __global__ void __launch_bounds__(kMaxThreads) exact_kernel(const EvalArgs a) {
                     c0[k] = fmaf(-(float)n, sl[k], v0[k]);
                 }
             }
-            float4 *e = s_tab + ((size_t)j * tab_stride + n) * kTabF4;
-            e[0] = make_float4(c0[0], c0[1], sl[0], sl[1]);
-            e[1] = make_float4(c0[2], c0[3], sl[2], sl[3]);
-            e[2] = make_float4(c0[4], c0[5], sl[4], sl[5]);
-            e[3] = make_float4(c0[6], sl[6], 0.f, 0.f);
+            const size_t at = (size_t)j * tab_stride + n;
+            s_tab[at] = make_float4(c0[0], c0[1], sl[0], sl[1]);
+            s_tab[cs + at] = make_float4(c0[2], c0[3], sl[2], sl[3]);
+            s_tab[2 * cs + at] = make_float4(c0[4], c0[5], sl[4], sl[5]);
+            reinterpret_cast<float2 *>(s_tab + 3 * cs)[at] = make_float2(c0[6], sl[6]);
         }
     }
     __syncthreads();
@@ -333,7 +342,9 @@ __global__ void __launch_bounds__(kMaxThreads) exact_kernel(const EvalArgs a) {
     // ---- tap sums, relative to the visibility's window ----
     float2 S0 = make_float2(0.f, 0.f), Su = S0, Sv = S0, SX = S0, SZx = S0, SZy = S0;
     if (active && !empty) {
-        const float4 *tab = s_tab + (size_t)lc * tab_stride * kTabF4;
+        const size_t at = (size_t)lc * tab_stride;
+        const TabView tab{s_tab + at, s_tab + cs + at, s_tab + 2 * cs + at,
+                          reinterpret_cast<const float2 *>(s_tab + 3 * cs) + at};
         const float ov = (float)a.ov;
         const float rmax2 = rmax * rmax;
         const float dlx_ov = dlx * ov;
@@ -495,7 +506,7 @@ cudaError_t launch_exact_moments(double diam_m, const double *freq_dev, int nc, 
 }
 
 size_t exact_dyn_smem(int c_group, int tab_stride) {
-    return sizeof(float4) * kTabF4 * (size_t)c_group * tab_stride;
+    return (3 * sizeof(float4) + sizeof(float2)) * (size_t)c_group * tab_stride;
 }
 
 cudaError_t launch_exact(const EvalArgs &a, bool predict, cudaStream_t s) {

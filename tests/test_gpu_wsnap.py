@@ -154,3 +154,9 @@ def test_snapshot_plane_rejects_collinear_baselines():
     uvw = I.uvw_tracks(enu, 34 * I.DEG, 30 * I.DEG, np.zeros(1))          # one instant, one line
     with pytest.raises(_abi.PscError):
         _abi.psc_snapshot_plane(torch.from_numpy(np.ascontiguousarray(uvw)).cuda(), uvw.shape[1])
+
+
+def test_component_grid_without_components_is_zero():
+    out = torch.full((130, 130), 1.0 + 1.0j, dtype=torch.complex64, device="cuda")
+    _abi.psc_model_grid_components(np.zeros((0, 3)), 130, 5.0 * I.ARCSEC, out)
+    assert not torch.any(out).item()
