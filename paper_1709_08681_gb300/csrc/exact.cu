@@ -59,6 +59,7 @@ namespace psc {
 namespace {
 
 constexpr int kNodes = 32;            // Gauss-Legendre nodes of the moment quadrature
+constexpr int kExTile = 48;           // staged box of this kernel: at most kExTile x kExTile cells (18 KB)
 // An interpolation entry is three float4 (P0, P1 | P2, P3 | Q0, Q1 as intercepts
 // then slopes) and one float2 (Q2); each of the four parts lives in its own
 // array, so that entries of neighbouring radii are 16 (8) bytes apart and the
@@ -157,7 +158,7 @@ __device__ __forceinline__ void series_values(const float *K, float s, float (&v
 }
 
 struct ExactShared {
-    float2 tile[kTile * kTile];
+    float2 tile[kExTile * kExTile];
     float2 phx[kTile], phy[kTile];
     float red[kMaxThreads / 32][kRed];
     float bl[6];       // L, M, dl_x, dl_y, s = |dl|^2
@@ -313,7 +314,7 @@ __global__ void __launch_bounds__(kMaxThreads) exact_kernel(const EvalArgs a) {
     const bool empty = sh.box[0] > sh.box[1];
     const int bx0 = empty ? 0 : sh.box[0], by0 = empty ? 0 : sh.box[2];
     const int ex = empty ? 0 : sh.box[1] - bx0 + 1, ey = empty ? 0 : sh.box[3] - by0 + 1;
-    const bool staged = !a.no_stage && ex <= kTile && ey <= kTile && 4 * ex * ey <= sh.taps;
+    const bool staged = !a.no_stage && ex <= kExTile && ey <= kExTile && 4 * ex * ey <= sh.taps;
     if (!empty) {
         const int nx = staged ? ex : S, ny = staged ? ey : S;
         for (int k = tid; k < nx; k += blockDim.x) {
@@ -334,7 +335,7 @@ __global__ void __launch_bounds__(kMaxThreads) exact_kernel(const EvalArgs a) {
             const int gx = bx0 + xx, gy = by0 + yy;
             float2 g = make_float2(0.f, 0.f);
             if (gx >= 0 && gx < a.ng && gy >= 0 && gy < a.ng) g = __ldg(&a.grid[(size_t)gy * a.ng + gx]);
-            sh.tile[yy * kTile + xx] = cmul(g, cmul(sh.phx[xx], sh.phy[yy]));
+            sh.tile[yy * kExTile + xx] = cmul(g, cmul(sh.phx[xx], sh.phy[yy]));
         }
         __syncthreads();
     }
@@ -368,7 +369,7 @@ __global__ void __launch_bounds__(kMaxThreads) exact_kernel(const EvalArgs a) {
             const float q = fmaf(dlx, dxo, dly * dyo);
             RowSums rs{};
             if (staged) {
-                const float2 *row = sh.tile + (iy0 - by0 + b) * kTile + (ix0 - bx0 + a_lo);
+                const float2 *row = sh.tile + (iy0 - by0 + b) * kExTile + (ix0 - bx0 + a_lo);
                 exact_row<false>(row, nullptr, 0, a_hi - a_lo + 1, dxo, dyo2, q, ov, dlx_ov, tab, rs);
             } else {
                 const float2 *row = a.grid + (size_t)(iy0 + b) * a.ng + ix0 + a_lo;
