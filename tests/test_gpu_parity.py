@@ -427,3 +427,24 @@ def test_blank_sky_predicts_exact_zeros():
     gp = GpuProblem(m, np.zeros_like(img))
     Vg, dVg = gp.predict(lmt)
     assert not np.any(Vg) and not np.any(dVg)
+
+
+@pytest.mark.parametrize("kv", [1, 2])
+def test_flat_bricks_never_staged_and_bf16_grid(kv):
+    """Flat bricks with every tap read from global memory, and with the BF16
+    grid copy (bound: bfloat16's unit roundoff on the grid, 2^-9)."""
+    m, _, lmt, img = cases.problem(cases.DISK_SMALL, n_ant=6, n_time=29, freqs=(1.3e9, 1.4e9, 1.5e9),
+                                   sigma_arcsec=30.0, extent_m=1200.0)
+    V, dV = psc.predict(m, lmt)
+    gp = GpuProblem(m, img)
+    gp.ctx.psc_set_flat_tiling(64, kv)
+    gp.ctx.psc_set_staging(_abi.PSC_STAGE_NEVER)
+    Vg, dVg = gp.predict(lmt)
+    assert _rel(Vg, V) < TOL_V
+    assert max(_rel(dVg[p], dV[p]) for p in range(4)) < TOL_V
+    gp.ctx.psc_set_staging(_abi.PSC_STAGE_AUTO)
+    gp.ctx.psc_set_grid_precision(_abi.PSC_GRID_BF16)
+    Vb, dVb = gp.predict(lmt)
+    assert _rel(Vb, V) < 2.0 ** -9
+    assert max(_rel(dVb[p], dV[p]) for p in range(4)) < 2.0 ** -9
+    gp.ctx.psc_set_grid_precision(_abi.PSC_GRID_F32)
