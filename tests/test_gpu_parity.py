@@ -432,9 +432,11 @@ def test_blank_sky_predicts_exact_zeros():
 @pytest.mark.parametrize("kv", [1, 2])
 def test_flat_bricks_never_staged_and_bf16_grid(kv):
     """Flat bricks with every tap read from global memory, and with the BF16
-    grid copy (bound: bfloat16's unit roundoff on the grid, 2^-9)."""
+    grid copy (bound: bfloat16's unit roundoff on the grid, 2^-9).  Two
+    visibilities per thread need consecutive time steps within 4 cells, which
+    the 300 m array keeps and the 1200 m one does not."""
     m, _, lmt, img = cases.problem(cases.DISK_SMALL, n_ant=6, n_time=29, freqs=(1.3e9, 1.4e9, 1.5e9),
-                                   sigma_arcsec=30.0, extent_m=1200.0)
+                                   sigma_arcsec=30.0, extent_m=1200.0 if kv == 1 else 300.0)
     V, dV = psc.predict(m, lmt)
     gp = GpuProblem(m, img)
     gp.ctx.psc_set_flat_tiling(64, kv)
