@@ -19,6 +19,8 @@ paper (Bhatnagar & Cornwell 2017) in double precision:
                       (Sec. 3's more accurate pattern), quadrature in ``exact.c``
 * ``wsnap``        -- W-snapshots: the interval's least-squares uvw plane and
                       the sky moved to the snapshot frame (Sec. 6.1)
+* ``wstack``       -- what W-snapshots leave on long intervals: the model grid
+                      stacked in the residual w, interpolated per visibility
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import it.  The GPU library shares no code with it.

@@ -32,9 +32,11 @@ def grid_from_image(image: np.ndarray, n_grid: int) -> np.ndarray:
     return (E @ image) @ E.T
 
 
-def grid_from_components(src: np.ndarray, n_grid: int, du: float) -> np.ndarray:
-    """Same grid from point components (l, m, S): G = sum_k S_k exp(+2 pi i (u l_k + v m_k))."""
+def grid_from_components(src: np.ndarray, n_grid: int, du: float, flux=None) -> np.ndarray:
+    """Same grid from point components (l, m, S): G = sum_k S_k exp(+2 pi i (u l_k + v m_k)).
+    ``flux`` (optional, complex) replaces the column S."""
     g = (np.arange(n_grid, dtype=np.float64) - n_grid // 2) * du
     ex = np.exp(2j * np.pi * np.outer(g, src[:, 0]))
     ey = np.exp(2j * np.pi * np.outer(g, src[:, 1]))
-    return (ey * src[:, 2][None, :]) @ ex.T
+    s = src[:, 2] if flux is None else np.asarray(flux)
+    return (ey * s[None, :]) @ ex.T
