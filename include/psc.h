@@ -192,6 +192,53 @@ psc_status psc_snapshot_plane(const double *uvw_dev, long long n_rows, double *a
 psc_status psc_snapshot_components(int n_comp, const double *comp_in, double a, double b, const psc_aperture *ap,
                                    double freq_hz, double *comp_out);
 
+/* Residual w of long intervals (Sec. 6.1 and the conclusions: an array that is
+ * not co-planar over a solution interval makes the w-term cost; W-snapshots
+ * remove the plane, these calls the rest).  After the plane fit each
+ * visibility keeps w_r = (w - a u - b v) nu / c wavelengths of w, which
+ * multiplies component k by exp(2 pi i w_r (n_k - 1)), n_k from its true
+ * direction.  The model grid becomes a stack of n_planes grids at
+ * w_p = w0 + p dw (wavelengths): plane p is the grid of the snapshot-frame
+ * components with fluxes S'_k exp(2 pi i w_p (n_k - 1)).  A visibility
+ * degrids (1 - f) G_p + f G_{p+1} with q = (w_r - w0) / dw,
+ * p = min(floor(q), n_planes - 2), f = q - p: linear interpolation in w of
+ * each source's w-phase, in error by at most (2 pi |n_k - 1| dw)^2 / 8 of its
+ * flux.  The pointing derivatives keep their form (the w-phase belongs to the
+ * sky, not to the antennas).
+ *
+ * psc_wstack_components (host): comp_in [n_comp][3] = (l, m, S) at their true
+ * directions -> comp_out [n_comp][4] = (l', m', S', n - 1): the result of
+ * psc_snapshot_components plus n - 1.  The arrays must not overlap.  Errors as
+ * psc_snapshot_components.
+ * psc_wstack_range: the least and greatest w - a u - b v (metres) over n_rows
+ * baselines of uvw_dev (device double [n_rows][3]); scale by the lowest and
+ * highest nu / c to size a stack.  Synchronises.  PSC_ERR_NUMERIC for
+ * non-finite uvw.
+ * psc_model_grid_wstack: the n_planes (>= 2) grids, each as
+ * psc_model_grid_components with the plane's complex fluxes, into grids_out
+ * (device complex64 [n_planes][n_grid][n_grid], caller-owned).  Temporary
+ * workspace as psc_model_grid_components.  Synchronises.  Errors as
+ * psc_model_grid_components, plus PSC_ERR_ARG for n_planes or dw.
+ * psc_set_wstack: the context degrids from the stack (borrowed like the grid of
+ * psc_create, planes [n_planes][Ng][Ng] of the context's grid size) instead of
+ * its grid, for every evaluation (predict, residual_grad, the solvers);
+ * n_planes = 0 returns to its grid.  It checks on the GPU that the stack
+ * covers the residual w of every baseline, time and channel of the context,
+ * and refuses with PSC_ERR_ARG otherwise (the message gives both ranges).
+ * Taps then read two planes each from global memory (the grid is never
+ * staged).  Gaussian kernel model and FP32 grid only: this call refuses a
+ * context with the exact kernel or the BF16 grid copy, psc_set_kernel_model
+ * and psc_set_grid_precision refuse those while a stack is set, and batches
+ * refuse stacked contexts; psc_features reads the context's own grid.
+ * Synchronises. */
+psc_status psc_wstack_components(int n_comp, const double *comp_in, double a, double b, const psc_aperture *ap,
+                                 double freq_hz, double *comp_out);
+psc_status psc_wstack_range(const double *uvw_dev, long long n_rows, double a, double b, double *wmin_m,
+                            double *wmax_m, void *stream);
+psc_status psc_model_grid_wstack(int n_comp, const double *comp_lmSn, int n_grid, double cell_rad, int n_planes,
+                                 double w0, double dw, void *grids_out, void *stream);
+psc_status psc_set_wstack(psc_ctx *ctx, const void *grids, int n_planes, double w0, double dw, double a, double b);
+
 /* Creates a context for one observation block: copies the channel list,
  * builds the A° tables on the device (Algorithm 1, second pre-compute) and
  * allocates the workspace.  grid_dev (complex64 [Ng][Ng], from

@@ -27,7 +27,8 @@ PSC_LM_FULL, PSC_LM_BLOCK = 0, 1
 STOP_REASONS = {0: "none", 1: "step", 2: "chi2", 3: "lambda", 4: "max_iter", 5: "numeric"}
 
 EXPORTS = ("psc_solve_opts_default", "psc_model_grid", "psc_model_grid_components", "psc_snapshot_plane",
-           "psc_snapshot_components", "psc_create", "psc_destroy", "psc_last_error",
+           "psc_snapshot_components", "psc_wstack_components", "psc_wstack_range", "psc_model_grid_wstack",
+           "psc_set_wstack", "psc_create", "psc_destroy", "psc_last_error",
            "psc_predict", "psc_residual_grad", "psc_solve_offsets", "psc_lm_begin", "psc_lm_iterate",
            "psc_lm_end", "psc_lm_restart", "psc_set_tiling", "psc_set_grid_precision", "psc_set_staging",
            "psc_set_kernel_model", "psc_set_flat_tiling", "psc_set_brick_order", "psc_fp32_fma_rate", "psc_profile", "psc_profile_read",
@@ -92,6 +93,13 @@ def lib():
             "psc_snapshot_plane": (ctypes.c_int, [_V, ctypes.c_longlong, _D, _D, _V]),
             "psc_snapshot_components": (ctypes.c_int, [ctypes.c_int, _D, ctypes.c_double, ctypes.c_double,
                                                        ctypes.POINTER(psc_aperture), ctypes.c_double, _D]),
+            "psc_wstack_components": (ctypes.c_int, [ctypes.c_int, _D, ctypes.c_double, ctypes.c_double,
+                                                     ctypes.POINTER(psc_aperture), ctypes.c_double, _D]),
+            "psc_wstack_range": (ctypes.c_int, [_V, ctypes.c_longlong, ctypes.c_double, ctypes.c_double, _D, _D, _V]),
+            "psc_model_grid_wstack": (ctypes.c_int, [ctypes.c_int, _D, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                                     ctypes.c_double, ctypes.c_double, _V, _V]),
+            "psc_set_wstack": (ctypes.c_int, [_V, _V, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                              ctypes.c_double]),
             "psc_create": (ctypes.c_int, [ctypes.POINTER(_V), ctypes.POINTER(psc_obs), ctypes.POINTER(psc_aperture),
                                           ctypes.POINTER(psc_grid_desc), _V, _V]),
             "psc_destroy": (None, [_V]),
@@ -215,6 +223,32 @@ def psc_snapshot_components(comp_lmS, a, b, ap_kind, diam_m, alpha_per_dlambda, 
     return out
 
 
+def psc_wstack_components(comp_lmS, a, b, ap_kind, diam_m, alpha_per_dlambda, freq_hz):
+    """(l', m', S', n - 1) per component (host [n][3] true l, m, S in, [n][4] out)."""
+    comp = np.ascontiguousarray(comp_lmS, dtype=np.float64).reshape(-1, 3)
+    out = np.empty((comp.shape[0], 4))
+    kind = {"disk": PSC_AP_DISK, "gauss": PSC_AP_GAUSS}.get(ap_kind, ap_kind)
+    ap = psc_aperture(int(kind), float(diam_m), float(alpha_per_dlambda), 1)
+    _check(lib().psc_wstack_components(comp.shape[0], _dp(comp), float(a), float(b), ctypes.byref(ap),
+                                       float(freq_hz), _dp(out)))
+    return out
+
+
+def psc_wstack_range(uvw_dev, n_rows, a, b, stream=None):
+    """(least, greatest) w - a u - b v in metres over n_rows device uvw rows."""
+    lo = np.zeros(1)
+    hi = np.zeros(1)
+    _check(lib().psc_wstack_range(_ptr(uvw_dev), int(n_rows), float(a), float(b), _dp(lo), _dp(hi), _stream(stream)))
+    return float(lo[0]), float(hi[0])
+
+
+def psc_model_grid_wstack(comp_lmSn, n_grid, cell_rad, n_planes, w0, dw, grids_out, stream=None):
+    """The n_planes grids of a residual-w stack (components [n][4]) into grids_out."""
+    comp = np.ascontiguousarray(comp_lmSn, dtype=np.float64).reshape(-1, 4)
+    _check(lib().psc_model_grid_wstack(comp.shape[0], _dp(comp), int(n_grid), float(cell_rad), int(n_planes),
+                                       float(w0), float(dw), _ptr(grids_out), _stream(stream)))
+
+
 def psc_residual_grad_noalloc(n_ant, n_time, n_chan, uvw_dev, freq_hz, ap_kind, diam_m, alpha_per_dlambda,
                               decorrelation, n_img, n_grid, cell_rad, support, oversample, grid_dev, lm, vis_obs,
                               w=None, w_scale=1.0, cross=False, stream=None):
@@ -289,6 +323,12 @@ class Context:
 
     def psc_set_grid_precision(self, precision):
         _check(lib().psc_set_grid_precision(self.h, int(precision)), self.h)
+
+    def psc_set_wstack(self, grids, n_planes, w0=0.0, dw=1.0, a=0.0, b=0.0):
+        """Degrid from a residual-w stack (n_planes = 0: the context's own grid)."""
+        _check(lib().psc_set_wstack(self.h, _ptr(grids), int(n_planes), float(w0), float(dw), float(a), float(b)),
+               self.h)
+        self._wstack = grids if n_planes else None          # borrowed: keep it alive
 
     def psc_predict(self, lm, vis_out, dvis_out=None):
         lm = self._lm(lm)

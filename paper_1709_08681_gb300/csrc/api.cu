@@ -52,6 +52,11 @@ struct psc_ctx {
     int brick_order = PSC_ORDER_BASELINE;
     int *d_bl_order = nullptr;   // baselines in Morton order of their mid-interval (u, v)
     float *d_kmom = nullptr;     // exact disk kernel: lens-moment combinations (psc_set_kernel_model)
+    // residual-w stack (psc_set_wstack): borrowed planes [wp_n][ng][ng], plane
+    // w_p = wp_w0 + p wp_dw (wavelengths), residual w of the plane w = wp_a u + wp_b v
+    const float2 *wp_grid = nullptr;
+    int wp_n = 0;
+    double wp_w0 = 0.0, wp_dw = 0.0, wp_a = 0.0, wp_b = 0.0;
     std::vector<double> h_freq;  // channel frequencies (Hz)
     std::vector<int> h_tab_off, h_tab_len;   // radial table layout per channel
     double step_cells = 0.0;     // largest move of a baseline between time steps (cells, top channel)
@@ -203,6 +208,15 @@ EvalArgs eval_args(const psc_ctx *c, const double *lm_dev) {
     a.exact = c->kernel_model == PSC_KERNEL_EXACT_DISK;
     a.bl_order = c->brick_order == PSC_ORDER_UV ? c->d_bl_order : nullptr;
     a.kmom = c->d_kmom;
+    if (c->wp_n > 0) {
+        a.grid = c->wp_grid;
+        a.grid_bf16 = nullptr;
+        a.wp_n = c->wp_n;
+        a.wp_a = c->wp_a;
+        a.wp_b = c->wp_b;
+        a.wp_scale = c->du / c->wp_dw;             // uv_scale du = nu / c
+        a.wp_q0 = c->wp_w0 / c->wp_dw;
+    }
     return a;
 }
 
@@ -322,8 +336,9 @@ psc_status psc_model_grid_components(int n_comp, const double *comp_lmS, int n_g
     int *err_dev = nullptr;
     int herr = 0;
     const double du = 1.0 / (n_grid * cell_rad);
-    cudaError_t e = cudaMalloc(&ws, model_grid_comp_ws_bytes(n_comp, n_grid));
-    if (e == cudaSuccess) e = launch_model_grid_comp(n_comp, comp_lmS, n_grid, du, ws, (float2 *)grid_out, &err_dev, s);
+    cudaError_t e = cudaMalloc(&ws, model_grid_comp_ws_bytes(n_comp, n_grid, 3));
+    if (e == cudaSuccess)
+        e = launch_model_grid_comp(n_comp, comp_lmS, 3, 0.0, n_grid, du, ws, (float2 *)grid_out, &err_dev, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e == cudaSuccess) e = cudaMemcpy(&herr, err_dev, sizeof(int), cudaMemcpyDeviceToHost);
     cudaFree(ws);
@@ -378,6 +393,86 @@ psc_status psc_snapshot_components(int n_comp, const double *comp_in, double a, 
         comp_out[3 * k + 1] = m1;
         comp_out[3 * k + 2] = S * pb(std::sqrt(r2)) / p1;
     }
+    return PSC_OK;
+}
+
+psc_status psc_wstack_components(int n_comp, const double *comp_in, double a, double b, const psc_aperture *ap,
+                                 double freq_hz, double *comp_out) {
+    if (n_comp < 0 || (n_comp > 0 && (!comp_in || !comp_out))) return fail(nullptr, PSC_ERR_ARG, "component arrays must be non-NULL");
+    if (n_comp > 0 && comp_out < comp_in + 3 * (size_t)n_comp && comp_in < comp_out + 4 * (size_t)n_comp)
+        return fail(nullptr, PSC_ERR_ARG, "comp_out must not overlap comp_in");
+    std::vector<double> snap(3 * (size_t)n_comp);
+    psc_status st = psc_snapshot_components(n_comp, comp_in, a, b, ap, freq_hz, snap.data());
+    if (st != PSC_OK) return st;
+    for (int k = 0; k < n_comp; ++k) {
+        const double l = comp_in[3 * k], m = comp_in[3 * k + 1];
+        const double r2 = l * l + m * m;
+        comp_out[4 * k] = snap[3 * k];
+        comp_out[4 * k + 1] = snap[3 * k + 1];
+        comp_out[4 * k + 2] = snap[3 * k + 2];
+        comp_out[4 * k + 3] = -r2 / (1.0 + std::sqrt(1.0 - r2));   // n - 1 of the true direction
+    }
+    return PSC_OK;
+}
+
+psc_status psc_wstack_range(const double *uvw_dev, long long n_rows, double a, double b, double *wmin_m, double *wmax_m,
+                            void *stream) {
+    if (!uvw_dev || !wmin_m || !wmax_m) return fail(nullptr, PSC_ERR_ARG, "uvw, wmin and wmax must be non-NULL");
+    if (n_rows < 1) return fail(nullptr, PSC_ERR_ARG, "n_rows must be >= 1");
+    if (!std::isfinite(a) || !std::isfinite(b)) return fail(nullptr, PSC_ERR_ARG, "a and b must be finite");
+    cudaStream_t s = (cudaStream_t)stream;
+    double *d_out = nullptr;
+    int blocks = 0;
+    std::vector<double> h;
+    cudaError_t e = cudaMalloc(&d_out, 2 * 1024 * sizeof(double));
+    if (e == cudaSuccess) e = launch_wrange(uvw_dev, n_rows, a, b, d_out, &blocks, s);
+    if (e == cudaSuccess) {
+        h.resize(2 * (size_t)blocks);
+        e = cudaMemcpyAsync(h.data(), d_out, h.size() * sizeof(double), cudaMemcpyDeviceToHost, s);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(d_out);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "psc_wstack_range");
+    double lo = h[0], hi = h[1];
+    for (int k = 1; k < blocks; ++k) {
+        lo = std::min(lo, h[2 * k]);
+        hi = std::max(hi, h[2 * k + 1]);
+    }
+    if (!std::isfinite(lo) || !std::isfinite(hi)) return fail(nullptr, PSC_ERR_NUMERIC, "psc_wstack_range: non-finite uvw");
+    *wmin_m = lo;
+    *wmax_m = hi;
+    return PSC_OK;
+}
+
+psc_status psc_model_grid_wstack(int n_comp, const double *comp_lmSn, int n_grid, double cell_rad, int n_planes,
+                                 double w0, double dw, void *grids_out, void *stream) {
+    if (n_comp < 0 || n_comp > (1 << 24)) return fail(nullptr, PSC_ERR_ARG, "n_comp must be in [0, 2^24]");
+    if (n_comp > 0 && !comp_lmSn) return fail(nullptr, PSC_ERR_ARG, "comp_lmSn is NULL");
+    if (!grids_out) return fail(nullptr, PSC_ERR_ARG, "grids_out is NULL");
+    if (n_grid < 2 || n_grid > 16384 || n_grid % 2) return fail(nullptr, PSC_ERR_ARG, "n_grid must be even in [2, 16384]");
+    if (!(cell_rad > 0.0) || !std::isfinite(cell_rad)) return fail(nullptr, PSC_ERR_ARG, "cell_rad must be > 0");
+    if (n_planes < 2 || n_planes > 65536) return fail(nullptr, PSC_ERR_ARG, "n_planes must be in [2, 65536]");
+    if (!std::isfinite(w0) || !(dw > 0.0) || !std::isfinite(dw)) return fail(nullptr, PSC_ERR_ARG, "w0 must be finite and dw > 0");
+    for (int k = 0; k < 4 * n_comp; ++k)
+        if (!std::isfinite(comp_lmSn[k])) return fail(nullptr, PSC_ERR_ARG, "components must be finite");
+    cudaStream_t s = (cudaStream_t)stream;
+    void *ws = nullptr;
+    int *err_dev = nullptr;
+    int herr = 0;
+    const double du = 1.0 / (n_grid * cell_rad);
+    const size_t plane = (size_t)n_grid * n_grid;
+    cudaError_t e = cudaMalloc(&ws, model_grid_comp_ws_bytes(n_comp, n_grid, 4));
+    for (int p = 0; p < n_planes && e == cudaSuccess; ++p) {
+        e = launch_model_grid_comp(n_comp, comp_lmSn, 4, w0 + p * dw, n_grid, du, ws, (float2 *)grids_out + p * plane,
+                                   &err_dev, s);
+        // the workspace (and its error flag) is reused by the next plane
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e == cudaSuccess) e = cudaMemcpy(&herr, err_dev, sizeof(int), cudaMemcpyDeviceToHost);
+        if (herr) break;
+    }
+    cudaFree(ws);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "psc_model_grid_wstack");
+    if (herr) return fail(nullptr, PSC_ERR_TIMEOUT, "psc_model_grid_wstack: a tensor-core wait timed out");
     return PSC_OK;
 }
 
@@ -586,6 +681,7 @@ psc_status psc_set_kernel_model(psc_ctx *ctx, int model) {
         return PSC_OK;
     }
     if (model != PSC_KERNEL_EXACT_DISK) return fail(ctx, PSC_ERR_ARG, "model must be PSC_KERNEL_GAUSS or PSC_KERNEL_EXACT_DISK");
+    if (ctx->wp_n > 0) return fail(ctx, PSC_ERR_ARG, "the exact kernel does not read a residual-w stack");
     if (ctx->ap.kind != PSC_AP_DISK) return fail(ctx, PSC_ERR_ARG, "the exact kernel needs a uniform-disk aperture");
     int dev = 0, optin = 0;
     PSC_CUDA(ctx, cudaGetDevice(&dev));
@@ -646,10 +742,46 @@ psc_status psc_set_grid_precision(psc_ctx *ctx, int precision) {
         return PSC_OK;
     }
     if (precision != PSC_GRID_BF16) return fail(ctx, PSC_ERR_ARG, "precision must be PSC_GRID_F32 or PSC_GRID_BF16");
+    if (ctx->wp_n > 0) return fail(ctx, PSC_ERR_ARG, "a residual-w stack is read in FP32 only");
     const size_t n = (size_t)ctx->gd.n_grid * ctx->gd.n_grid;
     if (!ctx->d_grid_bf16) PSC_CUDA(ctx, dalloc(&ctx->d_grid_bf16, n));
     PSC_CUDA(ctx, launch_grid_to_bf16(ctx->grid, n, ctx->d_grid_bf16, ctx->stream));
     PSC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return PSC_OK;
+}
+
+psc_status psc_set_wstack(psc_ctx *ctx, const void *grids, int n_planes, double w0, double dw, double a, double b) {
+    if (!ctx) return fail(nullptr, PSC_ERR_ARG, "ctx is NULL");
+    if (n_planes == 0) {
+        ctx->wp_n = 0;
+        ctx->wp_grid = nullptr;
+        return PSC_OK;
+    }
+    if (n_planes < 2 || n_planes > 65536) return fail(ctx, PSC_ERR_ARG, "n_planes must be 0 or in [2, 65536]");
+    if (!grids) return fail(ctx, PSC_ERR_ARG, "grids is NULL");
+    if (!std::isfinite(w0) || !(dw > 0.0) || !std::isfinite(dw) || !std::isfinite(a) || !std::isfinite(b))
+        return fail(ctx, PSC_ERR_ARG, "w0, a, b must be finite and dw > 0");
+    if (ctx->kernel_model != PSC_KERNEL_GAUSS) return fail(ctx, PSC_ERR_ARG, "a residual-w stack needs the Gaussian kernel model");
+    if (ctx->d_grid_bf16) return fail(ctx, PSC_ERR_ARG, "a residual-w stack is read in FP32 only (grid precision is BF16)");
+    // coverage: the residual w of every row, at the lowest and highest channel
+    double lo_m = 0.0, hi_m = 0.0;
+    psc_status st = psc_wstack_range(ctx->uvw, (long long)ctx->nt * ctx->n_bl, a, b, &lo_m, &hi_m, ctx->stream);
+    if (st != PSC_OK) return fail(ctx, st, psc_last_error(nullptr));
+    const auto fr = std::minmax_element(ctx->h_freq.begin(), ctx->h_freq.end());
+    const double s_lo = *fr.first / kC, s_hi = *fr.second / kC;
+    const double w_lo = std::min(lo_m * s_lo, lo_m * s_hi), w_hi = std::max(hi_m * s_lo, hi_m * s_hi);
+    if (w_lo < w0 || w_hi > w0 + (n_planes - 1) * dw) {
+        char msg[200];
+        std::snprintf(msg, sizeof msg, "the stack covers w in [%.6g, %.6g] wavelengths, the context needs [%.6g, %.6g]",
+                      w0, w0 + (n_planes - 1) * dw, w_lo, w_hi);
+        return fail(ctx, PSC_ERR_ARG, msg);
+    }
+    ctx->wp_grid = (const float2 *)grids;
+    ctx->wp_n = n_planes;
+    ctx->wp_w0 = w0;
+    ctx->wp_dw = dw;
+    ctx->wp_a = a;
+    ctx->wp_b = b;
     return PSC_OK;
 }
 
@@ -1157,6 +1289,10 @@ psc_status psc_batch_create(psc_batch **out, psc_ctx *const *ctxs, int n_ctx, co
         if (ctxs[k]->kernel_model != PSC_KERNEL_GAUSS) {
             free_batch(b);
             return fail(nullptr, PSC_ERR_ARG, "batches take contexts with the Gaussian kernel model only");
+        }
+        if (ctxs[k]->wp_n > 0) {
+            free_batch(b);
+            return fail(nullptr, PSC_ERR_ARG, "batches take contexts without a residual-w stack only");
         }
         b->ctxs.push_back(ctxs[k]);
         b->vis.push_back(vis_obs[k]);

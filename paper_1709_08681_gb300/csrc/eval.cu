@@ -201,7 +201,9 @@ struct BlockShared {
 
 // One brick: kv visibilities per thread.  acc receives the thread's 15 sums
 // (reduce mode); predict mode writes V and the derivative planes.
-template <bool kPredict, int kV>
+// kW: the grid is a residual-w stack (EvalArgs::wp_n); every tap reads the two
+// planes around its visibility's w and interpolates, unstaged.
+template <bool kPredict, int kV, bool kW>
 __device__ __forceinline__ void eval_brick(const EvalArgs &a, int brick, float2 *s_tab, BlockShared &sh,
                                            float (&acc)[kRed]) {
     const int tid = threadIdx.x;
@@ -256,6 +258,8 @@ __device__ __forceinline__ void eval_brick(const EvalArgs &a, int brick, float2 
     int ix0[kV], iy0[kV];
     float hx[kV], hy[kV];
     float rmax = 0.f;
+    size_t woff[kV];                                  // kW: first cell of the lower plane
+    float wf[kV];                                     // kW: weight of the upper plane
     if (active) {
         const ChanConst ch = a.chan[c];
         rmax = ch.rho_max;
@@ -279,6 +283,14 @@ __device__ __forceinline__ void eval_brick(const EvalArgs &a, int brick, float2 
                 ny = (int)fly;
                 fx = (float)(x - flx);
                 fy = (float)(y - fly);
+            }
+            if constexpr (kW) {
+                const double *p = a.uvw + ((size_t)t * a.n_bl + bl) * 3;
+                double q = (p[2] - a.wp_a * p[0] - a.wp_b * p[1]) * ch.uv_scale * a.wp_scale - a.wp_q0;
+                q = fmin(fmax(q, 0.0), (double)(a.wp_n - 1));
+                const int pl = min((int)floor(q), a.wp_n - 2);
+                woff[v] = (size_t)pl * a.ng * a.ng;
+                wf[v] = (float)(q - (double)pl);
             }
             ix0[v] = nx - S / 2 + 1;
             iy0[v] = ny - S / 2 + 1;
@@ -319,7 +331,7 @@ __device__ __forceinline__ void eval_brick(const EvalArgs &a, int brick, float2 
     // a global load, two complex products and a store (about four unstaged
     // taps' extra work), so stage only boxes of at most taps / 4 cells that
     // fit the tile.  Uniform over the block.
-    const bool staged = !a.no_stage && ex <= kTile && ey <= kTile && 4 * ex * ey <= sh.taps;
+    const bool staged = !kW && !a.no_stage && ex <= kTile && ey <= kTile && 4 * ex * ey <= sh.taps;
 
     // per-cell half of the ramp, exp(-i pi du (k_x L + k_y M)) = phx[k_x] phy[k_y],
     // with (k_x, k_y) relative to the tile origin (staged) or to each
@@ -338,7 +350,7 @@ __device__ __forceinline__ void eval_brick(const EvalArgs &a, int brick, float2 
         }
         __syncthreads();
     }
-    if (staged && !empty) {
+    if (!kW && staged && !empty) {
         // threads -> (column, row group) with shifts: 64 columns per pass for
         // blocks of >= 64 threads, 32 for a 32-thread block (two passes);
         // the row step blockDim >> cshift is >= 1 for every allowed block size
@@ -368,7 +380,7 @@ __device__ __forceinline__ void eval_brick(const EvalArgs &a, int brick, float2 
         const unsigned tab_adj = (unsigned)__cvta_generic_to_shared(tab) - (0x4B000000u << 3);
         const float ov = (float)a.ov;
         const float rmax2 = rmax * rmax;
-        if (staged) {
+        if (!kW && staged) {
             int wx[kV], wy[kV];
             int r_lo = INT_MAX, r_hi = INT_MIN;
 #pragma unroll
@@ -438,7 +450,15 @@ __device__ __forceinline__ void eval_brick(const EvalArgs &a, int brick, float2 
                     const size_t row = (size_t)(iy0[v] + b) * a.ng + ix0[v];
                     float dd = (hx[v] - (float)a_lo) * ov;
                     for (int aa = a_lo; aa <= a_hi; ++aa, dd -= ov) {
-                        const float2 g = cmul(grid_cell(a, row + aa), sh.phx[aa]);
+                        float2 gc;
+                        if constexpr (kW) {
+                            const float2 g0 = __ldg(&a.grid[woff[v] + row + aa]);
+                            const float2 g1 = __ldg(&a.grid[woff[v] + (size_t)a.ng * a.ng + row + aa]);
+                            gc = make_float2(fmaf(wf[v], g1.x - g0.x, g0.x), fmaf(wf[v], g1.y - g0.y, g0.y));
+                        } else {
+                            gc = grid_cell(a, row + aa);
+                        }
+                        const float2 g = cmul(gc, sh.phx[aa]);
                         const float s2 = fmaf(dd, dd, dyo2);
                         const float tv = sqrt_fast(s2);
                         const float tf = __fadd_rz(tv, 8388608.0f);
@@ -536,7 +556,7 @@ __device__ __forceinline__ void eval_brick(const EvalArgs &a, int brick, float2 
 // brick numbers from an atomic queue until all sum(bricks) are taken; prefix
 // holds the first global brick of each context).  Every brick writes its own
 // partial record, so the result does not depend on which block ran it.
-template <bool kPredict>
+template <bool kPredict, bool kW>
 __global__ void __launch_bounds__(kMaxThreads) eval_kernel(const EvalArgs a0, const EvalArgs *__restrict__ args,
                                                            const long long *__restrict__ prefix, int n_ctx,
                                                            unsigned long long *queue) {
@@ -587,8 +607,8 @@ __global__ void __launch_bounds__(kMaxThreads) eval_kernel(const EvalArgs a0, co
     float acc[kRed];
 #pragma unroll
     for (int k = 0; k < kRed; ++k) acc[k] = 0.f;
-    if (a.kv == 2) eval_brick<kPredict, 2>(a, brick, s_tab, sh, acc);
-    else eval_brick<kPredict, 1>(a, brick, s_tab, sh, acc);
+    if (a.kv == 2) eval_brick<kPredict, 2, kW>(a, brick, s_tab, sh, acc);
+    else eval_brick<kPredict, 1, kW>(a, brick, s_tab, sh, acc);
     if constexpr (!kPredict) {
         // ---- block reduction: FP32 within a warp, FP64 across warps ----
 #pragma unroll
@@ -753,10 +773,13 @@ cudaError_t launch_eval(const EvalArgs &a, bool predict, cudaStream_t s) {
     const int threads = ((a.flat > 0 ? a.flat : a.t_tile * a.c_group) + 31) / 32 * 32;
     const int blocks = (int)a.n_bricks;
     const size_t dyn = eval_dyn_smem(a.flat > 0 ? a.ch_span : a.c_group, a.tab_stride);
-    if (predict) {
-        eval_kernel<true><<<blocks, threads, dyn, s>>>(a, nullptr, nullptr, 0, nullptr);
+    if (a.wp_n > 0) {
+        if (predict) eval_kernel<true, true><<<blocks, threads, dyn, s>>>(a, nullptr, nullptr, 0, nullptr);
+        else eval_kernel<false, true><<<blocks, threads, dyn, s>>>(a, nullptr, nullptr, 0, nullptr);
+    } else if (predict) {
+        eval_kernel<true, false><<<blocks, threads, dyn, s>>>(a, nullptr, nullptr, 0, nullptr);
     } else {
-        eval_kernel<false><<<blocks, threads, dyn, s>>>(a, nullptr, nullptr, 0, nullptr);
+        eval_kernel<false, false><<<blocks, threads, dyn, s>>>(a, nullptr, nullptr, 0, nullptr);
     }
     return cudaGetLastError();
 }
@@ -764,12 +787,12 @@ cudaError_t launch_eval(const EvalArgs &a, bool predict, cudaStream_t s) {
 cudaError_t launch_eval_batch(const EvalArgs *args_dev, const long long *prefix_dev, int n_ctx,
                               unsigned long long *queue, int threads, size_t dyn, int grid, cudaStream_t s) {
     EvalArgs none{};
-    eval_kernel<false><<<grid, threads, dyn, s>>>(none, args_dev, prefix_dev, n_ctx, queue);
+    eval_kernel<false, false><<<grid, threads, dyn, s>>>(none, args_dev, prefix_dev, n_ctx, queue);
     return cudaGetLastError();
 }
 
 cudaError_t eval_batch_occupancy(int threads, size_t dyn, int *blocks_per_sm) {
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, eval_kernel<false>, threads, dyn);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, eval_kernel<false, false>, threads, dyn);
 }
 
 // Raises the fused kernel's dynamic shared-memory limit to everything the
@@ -783,13 +806,16 @@ cudaError_t set_eval_smem(size_t dyn) {
     e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
     cudaFuncAttributes fa{};
-    e = cudaFuncGetAttributes(&fa, eval_kernel<false>);
+    e = cudaFuncGetAttributes(&fa, eval_kernel<false, false>);
     if (e != cudaSuccess) return e;
     const size_t allowed = (size_t)optin > fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes : 0;
     if (dyn > allowed) return cudaErrorInvalidValue;
-    e = cudaFuncSetAttribute(eval_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)allowed);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(eval_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)allowed);
+    for (const void *k : {(const void *)eval_kernel<true, false>, (const void *)eval_kernel<false, false>,
+                          (const void *)eval_kernel<true, true>, (const void *)eval_kernel<false, true>}) {
+        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)allowed);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_reduce(const RedArgs &r, cudaStream_t s) {

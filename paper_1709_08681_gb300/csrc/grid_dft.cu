@@ -226,8 +226,8 @@ __global__ void split_dft_matrix_kernel(const double2 *__restrict__ W, int n, in
 // A[gx][k] = S_k exp(2 pi i u_gx l_k) and B[gy][k] = exp(2 pi i v_gy m_k): split planes
 // [3][Ng][kp] of the real and imaginary parts, phases from FP64 sincospi,
 // columns k >= n_comp zero (kp = n_comp rounded up to a multiple of the K chunk).
-__global__ void split_comp_kernel(const double *__restrict__ comp, int n_comp, int kp, int ng, double du,
-                                  bf16 *__restrict__ Ar, bf16 *__restrict__ Ai, bf16 *__restrict__ Br,
+__global__ void split_comp_kernel(const double *__restrict__ comp, int n_comp, int stride, double wp, int kp, int ng,
+                                  double du, bf16 *__restrict__ Ar, bf16 *__restrict__ Ai, bf16 *__restrict__ Br,
                                   bf16 *__restrict__ Bi) {
     const long long total = (long long)ng * kp;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
@@ -235,11 +235,14 @@ __global__ void split_comp_kernel(const double *__restrict__ comp, int n_comp, i
         double ar = 0.0, ai = 0.0, br = 0.0, bi = 0.0;
         if (k < n_comp) {
             const double x = (double)(g - ng / 2) * du;
+            const double *ck = comp + (size_t)stride * k;
+            // flux phase of a w-plane: 2 pi wp (n - 1), folded into the u factor
+            const double wph = stride == 4 ? wp * ck[3] : 0.0;
             double sn, cs;
-            sincospi(2.0 * x * comp[3 * k], &sn, &cs);
-            ar = comp[3 * k + 2] * cs;
-            ai = comp[3 * k + 2] * sn;
-            sincospi(2.0 * x * comp[3 * k + 1], &sn, &cs);
+            sincospi(2.0 * (x * ck[0] + wph), &sn, &cs);
+            ar = ck[2] * cs;
+            ai = ck[2] * sn;
+            sincospi(2.0 * x * ck[1], &sn, &cs);
             br = cs;
             bi = sn;
         }
@@ -618,17 +621,17 @@ cudaError_t launch_model_grid(int n_img, int n_grid, const float *image, void *w
     return launch_tc_pass<2>(a2, s);
 }
 
-size_t model_grid_comp_ws_bytes(int n_comp, int n_grid) {
+size_t model_grid_comp_ws_bytes(int n_comp, int n_grid, int stride) {
     const size_t kp = (size_t)comp_depth(n_comp), ng = (size_t)n_grid;
-    return al256((size_t)n_comp * 3 * sizeof(double)) + 4 * al256(3 * ng * kp * 2) + 256;
+    return al256((size_t)n_comp * stride * sizeof(double)) + 4 * al256(3 * ng * kp * 2) + 256;
 }
 
-cudaError_t launch_model_grid_comp(int n_comp, const double *comp_host, int n_grid, double du, void *ws,
-                                   float2 *grid_out, int **err_dev, cudaStream_t s) {
+cudaError_t launch_model_grid_comp(int n_comp, const double *comp_host, int stride, double wp, int n_grid, double du,
+                                   void *ws, float2 *grid_out, int **err_dev, cudaStream_t s) {
     const int kp = comp_depth(n_comp);
     const size_t ng = (size_t)n_grid;
     unsigned char *p = (unsigned char *)ws;
-    double *comp = (double *)p; p += al256((size_t)n_comp * 3 * sizeof(double));
+    double *comp = (double *)p; p += al256((size_t)n_comp * stride * sizeof(double));
     bf16 *Ar = (bf16 *)p; p += al256(3 * ng * kp * 2);
     bf16 *Ai = (bf16 *)p; p += al256(3 * ng * kp * 2);
     bf16 *Br = (bf16 *)p; p += al256(3 * ng * kp * 2);
@@ -636,10 +639,10 @@ cudaError_t launch_model_grid_comp(int n_comp, const double *comp_host, int n_gr
     *err_dev = (int *)p;
     cudaError_t e = cudaMemsetAsync(*err_dev, 0, sizeof(int), s);
     if (e == cudaSuccess && n_comp > 0)
-        e = cudaMemcpyAsync(comp, comp_host, (size_t)n_comp * 3 * sizeof(double), cudaMemcpyHostToDevice, s);
+        e = cudaMemcpyAsync(comp, comp_host, (size_t)n_comp * stride * sizeof(double), cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return e;
-    split_comp_kernel<<<(int)std::min<size_t>((ng * kp + 255) / 256, 8192), 256, 0, s>>>(comp, n_comp, kp, n_grid, du,
-                                                                                          Ar, Ai, Br, Bi);
+    split_comp_kernel<<<(int)std::min<size_t>((ng * kp + 255) / 256, 8192), 256, 0, s>>>(
+        comp, n_comp, stride, wp, kp, n_grid, du, Ar, Ai, Br, Bi);
     TcPassArgs a2{};
     a2.A[0] = Ar; a2.A[1] = Ai; a2.n_a = 2;
     a2.B[0] = Br; a2.B[1] = Bi;

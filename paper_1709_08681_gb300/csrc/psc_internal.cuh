@@ -60,6 +60,12 @@ struct EvalArgs {
     // nullptr, or [n_bl]: the baseline of each group of bpb consecutive bricks in
     // launch order (partials stay indexed by baseline: brick = bl * bpb + j)
     const int *bl_order;
+    // Residual-w stack (wp_n >= 2): grid holds wp_n planes of ng^2 cells.  A
+    // visibility at q = (w - wp_a u - wp_b v) uv_scale wp_scale - wp_q0 (uvw in
+    // metres, q clamped to [0, wp_n - 1]) reads (1 - f) plane p + f plane p + 1,
+    // p = min(floor(q), wp_n - 2), f = q - p.  Taps read the planes unstaged.
+    int wp_n;
+    double wp_a, wp_b, wp_scale, wp_q0;
 };
 
 // Arguments of the stencil-feature kernel (learned initial estimate).
@@ -158,15 +164,20 @@ cudaError_t launch_features(const StencilArgs &a, double *blsum, int n_ant, floa
 // Workspace (bytes) of launch_model_grid; the model grid goes to grid_out
 // and *err_dev points (inside ws) at a flag set if a tensor-core wait ran out.
 size_t model_grid_ws_bytes(int n_img, int n_grid);
-// Model grid of n_comp point components (host [n_comp][3] = l, m, S) on the
-// tensor cores, in the workspace of model_grid_comp_ws_bytes; *err_dev is set
-// if a tensor-core wait ran out.
-size_t model_grid_comp_ws_bytes(int n_comp, int n_grid);
-cudaError_t launch_model_grid_comp(int n_comp, const double *comp_host, int n_grid, double du, void *ws,
-                                   float2 *grid_out, int **err_dev, cudaStream_t s);
+// Model grid of n_comp point components (host [n_comp][stride] = l, m, S, and
+// with stride 4 also n - 1, which gives flux k the phase 2 pi wp (n_k - 1)) on
+// the tensor cores, in the workspace of model_grid_comp_ws_bytes(n_comp, n_grid,
+// stride); *err_dev is set if a tensor-core wait ran out.
+size_t model_grid_comp_ws_bytes(int n_comp, int n_grid, int stride);
+cudaError_t launch_model_grid_comp(int n_comp, const double *comp_host, int stride, double wp, int n_grid, double du,
+                                   void *ws, float2 *grid_out, int **err_dev, cudaStream_t s);
 // Least-squares plane w = a u + b v of n_rows baselines (device uvw [n_rows][3]):
 // the sums uu, uv, vv, uw, vw in FP64 go to sums_dev[5] (zeroed by the launcher).
 cudaError_t launch_plane_sums(const double *uvw, long long n_rows, double *sums_dev, cudaStream_t s);
+// Per-block (min, max) of w - a u - b v over n_rows baselines into
+// out_dev[2 * blocks]; returns the block count used (at most 1024) in *blocks.
+cudaError_t launch_wrange(const double *uvw, long long n_rows, double a, double b, double *out_dev, int *blocks,
+                          cudaStream_t s);
 cudaError_t launch_model_grid(int n_img, int n_grid, const float *image, void *ws, float2 *grid_out, int **err_dev,
                               cudaStream_t s);
 // FP32 split (u_hi, u_lo, v_hi, v_lo) of n uvw triples (FP64 metres).

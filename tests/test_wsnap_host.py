@@ -29,3 +29,24 @@ def test_snapshot_components_arguments():
         _abi.psc_snapshot_components(src, 0.1, 0.1, "disk", -1.0, 1.0, 1.4e9)
     with pytest.raises(_abi.PscError):
         _abi.psc_snapshot_components(src, float("nan"), 0.1, "gauss", 25.0, 1.0, 1.4e9)
+
+
+@pytest.mark.parametrize("kind", ["disk", "gauss"])
+def test_wstack_components_match_oracle(kind):
+    """psc_wstack_components = the snapshot components plus n - 1 of each true
+    direction (``wstack.stack_sources``; the oracle forms n - 1 by a plain
+    subtraction, so it agrees to its cancellation error, about 1e-16 absolute)."""
+    from oracle import wstack
+    rng = np.random.default_rng(5)
+    n = 29
+    src = np.stack([rng.uniform(-0.01, 0.01, n), rng.uniform(-0.01, 0.01, n), rng.uniform(0.1, 2.0, n)], axis=1)
+    alpha = I.ALPHA_PER_DLAMBDA_DISK
+    for a, b in ((0.0, -1.7320508), (0.31, -0.07)):
+        got = _abi.psc_wstack_components(src, a, b, kind, 25.0, alpha, 1.4e9)
+        ref = wstack.stack_sources(src, a, b, kind, 1.4e9, 25.0, alpha)
+        assert got.shape == (n, 4)
+        assert np.array_equal(got[:, :3], _abi.psc_snapshot_components(src, a, b, kind, 25.0, alpha, 1.4e9))
+        assert np.allclose(got[:, 3], ref[:, 3], rtol=0, atol=1e-15)
+        assert np.all(got[:, 3] < 0)
+    with pytest.raises(_abi.PscError):
+        _abi.psc_wstack_components(np.array([[0.8, 0.7, 1.0]]), 0.1, 0.1, kind, 25.0, alpha, 1.4e9)
