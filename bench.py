@@ -55,6 +55,7 @@ def parse():
     p.add_argument("--no-drift", action="store_true", help="skip the full-scale drifting-pointing section")
     p.add_argument("--no-exact", action="store_true", help="skip the exact-disk-kernel section")
     p.add_argument("--no-wsnap", action="store_true", help="skip the W-snapshot section")
+    p.add_argument("--no-wstack", action="store_true", help="skip the residual-w stack section")
     p.add_argument("--mixed-intervals", type=int, default=256,
                    help="intervals of the mixed-array batched-solve section (0 skips it)")
     p.add_argument("--learned-train", type=int, default=3000, help="training intervals of the learned initialiser")
@@ -479,6 +480,11 @@ def run_ours(args):
         # snapshot frame, their grid on the tensor cores, then the usual batch
         from paper_1709_08681_gb300 import wsnap as WS
         line["wsnap"] = {"workload": "vla27_l64ch, W-snapshot grid per interval", **WS.run("vla27_l64ch", seed=args.seed)}
+    if rank == 0 and not args.no_wstack:
+        # residual-w stack: all 600 time steps as one interval, the model grid
+        # stacked in the w left after the plane fit, two planes read per tap
+        from paper_1709_08681_gb300 import wstack as WK
+        line["wstack"] = {"workload": "vla27_l64ch, 600 time steps as one interval", **WK.run("vla27_l64ch", seed=args.seed)}
     if rank == 0 and not args.no_drift:
         # full scale: 197 antennas, 128 channels, 1800 x 1 s (4.45e9 visibilities),
         # pointing drifting as a random walk, solved every 60 s (30 intervals):

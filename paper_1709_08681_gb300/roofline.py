@@ -20,6 +20,9 @@ FLOPS_PER_TAP = 15
 # (dl.du)/|du|^2 (1), O dx and W dx (2), five complex accumulations (20), the
 # two per-tap steps (2).
 FLOPS_PER_TAP_EXACT = 61
+# Residual-w stack: the Gaussian-model tap plus the interpolation between the
+# two planes' cells, G_p + f (G_{p+1} - G_p) (2 subtractions, 2 FMAs).
+FLOPS_PER_TAP_WSTACK = FLOPS_PER_TAP + 4
 FP32_LANES_PER_SM = 128
 C_LIGHT = 299_792_458.0
 
