@@ -190,8 +190,10 @@ __device__ __forceinline__ void row_taps(const float2 *__restrict__ row, int n, 
 }
 
 // Shared memory of one block (besides the dynamic tables).
-struct BlockShared {
-    float2 tile[kTile * kTile];
+// Block shared memory; the staging tile only in instantiations that stage.
+template <bool kTiled>
+struct BlockSharedT {
+    float2 tile[kTiled ? kTile * kTile : 1];
     float2 phx[kTile], phy[kTile];
     float red[kMaxThreads / 32][kRed];
     float bl[4];
@@ -204,7 +206,7 @@ struct BlockShared {
 // kW: the grid is a residual-w stack (EvalArgs::wp_n); every tap reads the two
 // planes around its visibility's w and interpolates, unstaged.
 template <bool kPredict, int kV, bool kW>
-__device__ __forceinline__ void eval_brick(const EvalArgs &a, int brick, float2 *s_tab, BlockShared &sh,
+__device__ __forceinline__ void eval_brick(const EvalArgs &a, int brick, float2 *s_tab, BlockSharedT<!kW> &sh,
                                            float (&acc)[kRed]) {
     const int tid = threadIdx.x;
     // brick -> baseline, this thread's channel c and first time step t0, and
@@ -556,12 +558,17 @@ __device__ __forceinline__ void eval_brick(const EvalArgs &a, int brick, float2 
 // brick numbers from an atomic queue until all sum(bricks) are taken; prefix
 // holds the first global brick of each context).  Every brick writes its own
 // partial record, so the result does not depend on which block ran it.
+// The stacked instantiation (kW) asks for 4 blocks of kMaxThreads per SM,
+// i.e. at most 64 registers (some spill): its unstaged two-plane taps gain
+// more from the warps than they lose (vla27_l64ch as one interval: 5.56 ms
+// against 6.36 ms at 99 registers).  A minimum of 0 leaves the co-planar
+// instantiations with the plain bound.
 template <bool kPredict, bool kW>
-__global__ void __launch_bounds__(kMaxThreads) eval_kernel(const EvalArgs a0, const EvalArgs *__restrict__ args,
+__global__ void __launch_bounds__(kMaxThreads, kW ? 4 : 0) eval_kernel(const EvalArgs a0, const EvalArgs *__restrict__ args,
                                                            const long long *__restrict__ prefix, int n_ctx,
                                                            unsigned long long *queue) {
     extern __shared__ float2 s_tab[];                 // c_group * tab_stride
-    __shared__ BlockShared sh;
+    __shared__ BlockSharedT<!kW> sh;
     __shared__ EvalArgs s_a;
     __shared__ long long s_work, s_first;
     __shared__ int s_done;
