@@ -246,3 +246,72 @@ def test_stack_arguments_are_checked():
     with pytest.raises(_abi.PscError):
         _abi.psc_model_grid_wstack(np.zeros((1, 4)), Ng, cell, 1, 0.0, DW, gs.planes)
     gs.close()
+
+
+def test_stack_on_the_64_channel_workload_sampled():
+    """vla27_l64ch solved as one interval of all 600 time steps, with the
+    benchmark's stack (dw from the interpolation bound at 1e-6: 33 planes of
+    2048^2) and brick shape (flat bricks of 128): 48 visibilities, sampled
+    between two pairs of planes, against the oracle, which builds only the four
+    planes they read.  The stack's extent comes from the oracle's plane and
+    residual w; the GPU fits its own plane and moves its own components."""
+    wl = I.make_workload("vla27_l64ch")
+    Ng, cell = wl.n_grid, wl.cell_rad
+    a, b = wsnap.plane_fit(wl.uvw_m)
+    f_c = 0.5 * (float(np.min(wl.freq_hz)) + float(np.max(wl.freq_hz)))
+    s4 = wstack.stack_sources(wl.sky, a, b, wl.ap_kind, f_c, wl.diam_m, wl.alpha_per_dlambda)
+    wr = wstack.residual_w(wl.uvw_m, wl.freq_hz, a, b)
+    dw = math.sqrt(8e-6) / (2.0 * math.pi * float(np.max(np.abs(s4[:, 3]))))
+    w0 = math.floor(wr.min() / dw) * dw
+    P = int(math.ceil((wr.max() - w0) / dw)) + 1
+    assert P >= 20
+    # GPU: its own plane and stack components, the oracle's extent
+    uvw_d = torch.from_numpy(np.ascontiguousarray(wl.uvw_m)).cuda()
+    ga, gb = _abi.psc_snapshot_plane(uvw_d, wl.n_time * wl.n_bl)
+    comp = _abi.psc_wstack_components(wl.sky, ga, gb, wl.ap_kind, wl.diam_m, wl.alpha_per_dlambda, f_c)
+    planes = torch.empty((P, Ng, Ng), dtype=torch.complex64, device="cuda")
+    _abi.psc_model_grid_wstack(comp, Ng, cell, P, w0, dw, planes)
+    grid = torch.empty((Ng, Ng), dtype=torch.complex64, device="cuda")
+    _abi.psc_model_grid_components(comp[:, :3], Ng, cell, grid)
+    ctx = _abi.Context(wl.n_ant, wl.n_time, wl.n_chan, uvw_d, wl.freq_hz, wl.ap_kind, wl.diam_m,
+                       wl.alpha_per_dlambda, wl.decorrelation, wl.image.shape[0], Ng, cell, wl.support,
+                       wl.oversample, grid)
+    ctx.psc_set_flat_tiling(128, 1)
+    ctx.psc_set_wstack(planes, P, w0, dw, ga, gb)
+    lm = wl.lm_true[0]
+    shape = (wl.n_time, wl.n_bl, wl.n_chan)
+    vg = torch.empty(shape, dtype=torch.complex64, device="cuda")
+    dg = torch.empty((4,) + shape, dtype=torch.complex64, device="cuda")
+    ctx.psc_predict(lm, vg, dg)
+    # samples: 24 visibilities whose lower plane is pa, 24 whose lower plane is pb
+    q = (wr - w0) / dw
+    p = np.minimum(np.floor(q).astype(np.int64), P - 2)
+    rng = np.random.default_rng(12)
+    pa, pb = P // 2, 2
+    idx = []
+    for pk in (pa, pb):
+        cand = np.flatnonzero(p.ravel() == pk)
+        assert cand.size >= 24
+        idx.append(rng.choice(cand, 24, replace=False))
+    idx = np.concatenate(idx)
+    ti, bi, ci = np.unravel_index(idx, shape)
+    f = (q - p).ravel()[idx]
+    du = 1.0 / (Ng * cell)
+    V = np.zeros(idx.size, dtype=np.complex128)
+    dV = np.zeros((4, idx.size), dtype=np.complex128)
+    for k in (pa, pa + 1, pb, pb + 1):
+        h = np.where(p.ravel()[idx] == k, 1.0 - f, 0.0) + np.where(p.ravel()[idx] + 1 == k, f, 0.0)
+        sel = np.flatnonzero(h)
+        flux = s4[:, 2] * np.exp(2j * np.pi * (w0 + k * dw) * s4[:, 3])
+        gk = model_grid.grid_from_components(s4[:, :3], Ng, du, flux=flux)
+        m = psc.Model(uvw_m=wl.uvw_m, freq_hz=wl.freq_hz, n_ant=wl.n_ant, grid=gk, cell_rad=cell,
+                      support=wl.support, oversample=wl.oversample, ap_kind=wl.ap_kind, diam_m=wl.diam_m,
+                      alpha_per_dlambda=wl.alpha_per_dlambda, decorrelation=wl.decorrelation)
+        Vk, dVk = psc.predict_points(m, lm, ti[sel], bi[sel], ci[sel])
+        V[sel] += h[sel] * Vk
+        dV[:, sel] += h[sel][None] * dVk
+    assert cases.rel_l2(vg.cpu().numpy()[ti, bi, ci], V) < TOL_V
+    dgs = dg.cpu().numpy()[:, ti, bi, ci]
+    for c in range(4):
+        assert cases.rel_l2(dgs[c], dV[c]) < TOL_V, c
+    ctx.close()
