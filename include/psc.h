@@ -228,8 +228,9 @@ psc_status psc_snapshot_components(int n_comp, const double *comp_in, double a, 
  * Taps then read two planes each from global memory (the grid is never
  * staged).  Gaussian kernel model and FP32 grid only: this call refuses a
  * context with the exact kernel or the BF16 grid copy, psc_set_kernel_model
- * and psc_set_grid_precision refuse those while a stack is set, and batches
- * refuse stacked contexts; psc_features reads the context's own grid.
+ * and psc_set_grid_precision refuse those while a stack is set.  A batch
+ * takes either only stacked contexts (its persistent launch then runs the
+ * stacked kernel) or none.  psc_features reads the context's own grid.
  * Synchronises. */
 psc_status psc_wstack_components(int n_comp, const double *comp_in, double a, double b, const psc_aperture *ap,
                                  double freq_hz, double *comp_out);
@@ -458,6 +459,9 @@ psc_status psc_learned_init(psc_ctx *ctx, psc_mlp *m, const void *vis_obs, const
  * their bricks.  The persistent launch uses the block size of the widest
  * context's shape (t_tile * c_group rounded up to a multiple of 32); narrower
  * contexts leave the extra lanes idle.
+ * The contexts must all use the Gaussian kernel model, and either all read
+ * a residual-w stack (psc_set_wstack) or none; each context's settings are
+ * read when the batch is created or autotuned (PSC_ERR_ARG otherwise).
  * vis_obs[k], w[k] (NULL = ones) and w_scale[k] (NULL = all 1) are the data
  * of ctxs[k], borrowed like the contexts for the batch's lifetime.  The
  * offsets of all contexts are concatenated in the order of ctxs: lm0,

@@ -1047,6 +1047,7 @@ struct psc_batch {
     int total_bl = 0;
     int grid = 0;
     int threads = 128;           // fused-kernel block size: the widest context's shape
+    bool stacked = false;        // every context reads a residual-w stack (else none does)
     size_t eval_dyn = 0, lm_dyn = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -1125,7 +1126,8 @@ psc_status build_tables(psc_batch *b) {
     b->lm_dyn = lmd;
     PSC_BCUDA(b, set_eval_smem(dyn));
     int per_sm = 0, dev = 0, n_sm = 0;
-    PSC_BCUDA(b, eval_batch_occupancy(b->threads, dyn, &per_sm));
+    b->stacked = b->ctxs[0]->wp_n > 0;
+    PSC_BCUDA(b, eval_batch_occupancy(b->threads, dyn, b->stacked, &per_sm));
     PSC_BCUDA(b, cudaGetDevice(&dev));
     PSC_BCUDA(b, cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
     b->grid = std::max(1, per_sm) * n_sm;
@@ -1166,7 +1168,8 @@ psc_status enqueue_iteration(psc_batch *b) {
         }
         PSC_BCUDA(b, cudaEventRecord(b->ev_pool[b->ev_used], s));
     }
-    PSC_BCUDA(b, launch_eval_batch(b->d_eval, b->d_prefix, n, b->d_queue, b->threads, b->eval_dyn, b->grid, s));
+    PSC_BCUDA(b, launch_eval_batch(b->d_eval, b->d_prefix, n, b->d_queue, b->threads, b->eval_dyn, b->grid,
+                                   b->stacked, s));
     if (b->prof) {
         PSC_BCUDA(b, cudaEventRecord(b->ev_pool[b->ev_used + 1], s));
         b->ev_used += 2;
@@ -1290,9 +1293,9 @@ psc_status psc_batch_create(psc_batch **out, psc_ctx *const *ctxs, int n_ctx, co
             free_batch(b);
             return fail(nullptr, PSC_ERR_ARG, "batches take contexts with the Gaussian kernel model only");
         }
-        if (ctxs[k]->wp_n > 0) {
+        if ((ctxs[k]->wp_n > 0) != (ctxs[0]->wp_n > 0)) {
             free_batch(b);
-            return fail(nullptr, PSC_ERR_ARG, "batches take contexts without a residual-w stack only");
+            return fail(nullptr, PSC_ERR_ARG, "a batch takes either only contexts with a residual-w stack or none");
         }
         b->ctxs.push_back(ctxs[k]);
         b->vis.push_back(vis_obs[k]);

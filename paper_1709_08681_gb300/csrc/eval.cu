@@ -189,8 +189,8 @@ __device__ __forceinline__ void row_taps(const float2 *__restrict__ row, int n, 
     }
 }
 
-// Shared memory of one block (besides the dynamic tables).
-// Block shared memory; the staging tile only in instantiations that stage.
+// Shared memory of one block besides the dynamic tables; the staging tile only
+// in instantiations that stage.
 template <bool kTiled>
 struct BlockSharedT {
     float2 tile[kTiled ? kTile * kTile : 1];
@@ -792,13 +792,17 @@ cudaError_t launch_eval(const EvalArgs &a, bool predict, cudaStream_t s) {
 }
 
 cudaError_t launch_eval_batch(const EvalArgs *args_dev, const long long *prefix_dev, int n_ctx,
-                              unsigned long long *queue, int threads, size_t dyn, int grid, cudaStream_t s) {
+                              unsigned long long *queue, int threads, size_t dyn, int grid, bool stacked,
+                              cudaStream_t s) {
     EvalArgs none{};
-    eval_kernel<false, false><<<grid, threads, dyn, s>>>(none, args_dev, prefix_dev, n_ctx, queue);
+    if (stacked) eval_kernel<false, true><<<grid, threads, dyn, s>>>(none, args_dev, prefix_dev, n_ctx, queue);
+    else eval_kernel<false, false><<<grid, threads, dyn, s>>>(none, args_dev, prefix_dev, n_ctx, queue);
     return cudaGetLastError();
 }
 
-cudaError_t eval_batch_occupancy(int threads, size_t dyn, int *blocks_per_sm) {
+cudaError_t eval_batch_occupancy(int threads, size_t dyn, bool stacked, int *blocks_per_sm) {
+    if (stacked)
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, eval_kernel<false, true>, threads, dyn);
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, eval_kernel<false, false>, threads, dyn);
 }
 

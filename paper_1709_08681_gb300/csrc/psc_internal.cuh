@@ -125,10 +125,12 @@ __host__ __device__ inline size_t ev_len(int n_ant, int n_bl) { return 1 + 2 * (
 // Launchers (defined in the .cu files).
 cudaError_t launch_eval(const EvalArgs &a, bool predict, cudaStream_t s);
 // Persistent fused launch over several contexts (device arrays of EvalArgs and
-// first-brick prefixes [n_ctx + 1]; *queue must be zero at launch).
+// first-brick prefixes [n_ctx + 1]; *queue must be zero at launch).  stacked:
+// every context reads a residual-w stack (else none does).
 cudaError_t launch_eval_batch(const EvalArgs *args_dev, const long long *prefix_dev, int n_ctx,
-                              unsigned long long *queue, int threads, size_t dyn, int grid, cudaStream_t s);
-cudaError_t eval_batch_occupancy(int threads, size_t dyn, int *blocks_per_sm);
+                              unsigned long long *queue, int threads, size_t dyn, int grid, bool stacked,
+                              cudaStream_t s);
+cudaError_t eval_batch_occupancy(int threads, size_t dyn, bool stacked, int *blocks_per_sm);
 cudaError_t launch_reduce(const RedArgs &r, cudaStream_t s);
 cudaError_t launch_reduce_batch(const RedArgs *ra_dev, const int *bl_prefix_dev, int n_ctx, int total_bl,
                                 cudaStream_t s);

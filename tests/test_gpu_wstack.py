@@ -230,9 +230,12 @@ def test_stack_arguments_are_checked():
         ctx.psc_set_grid_precision(_abi.PSC_GRID_BF16)      # stack set: FP32 only
     with pytest.raises(_abi.PscError):
         ctx.psc_set_kernel_model(_abi.PSC_KERNEL_EXACT_DISK)
-    vis = [torch.zeros(gs.shape, dtype=torch.complex64, device="cuda")]
+    plain = _abi.Context(gs.n_ant, uvw.shape[0], len(freq), gs.uvw, freq, "disk", 25.0, I.ALPHA_PER_DLAMBDA_DISK, 1,
+                         64, Ng, cell, 32, 20, gs.grid)
+    vis = [torch.zeros(gs.shape, dtype=torch.complex64, device="cuda")] * 2
     with pytest.raises(_abi.PscError):
-        _abi.Batch([ctx], vis, None)
+        _abi.Batch([ctx, plain], vis, None)                 # stacked and plain contexts mixed
+    plain.close()
     ctx.psc_set_wstack(None, 0)
     ctx.psc_set_grid_precision(_abi.PSC_GRID_BF16)
     with pytest.raises(_abi.PscError):
@@ -315,3 +318,26 @@ def test_stack_on_the_64_channel_workload_sampled():
     for c in range(4):
         assert cases.rel_l2(dgs[c], dV[c]) < TOL_V, c
     ctx.close()
+
+
+def test_stacked_batch_equals_single_solves():
+    """Three stacked contexts (the 6-hour track, offsets of three seeds) solved
+    as one batch -- one persistent launch of the stacked kernel per LM
+    iteration -- give the same offsets, bit for bit, as three single solves."""
+    uvw, freq, cell, Ng, sky, _ = _problem(n_time=16)
+    (a, b, w0, P), m, planes = _oracle_stack(uvw, freq, cell, Ng, sky)
+    stacks, vis, truths = [], [], []
+    for seed in (3, 4, 5):
+        lmt = I.true_offsets(_n_ant(uvw), 20.0 * I.ARCSEC, seed)
+        vobs, _ = _obs(uvw, freq, sky, lmt, seed=seed)
+        stacks.append(GpuStack(uvw, freq, cell, Ng, sky, w0, P))
+        vis.append(torch.from_numpy(vobs).cuda())
+        truths.append(lmt)
+    single = [gs.ctx.psc_solve_offsets(v, None, 1e10) for gs, v in zip(stacks, vis)]
+    sols, reps = _abi.psc_solve_batch([gs.ctx for gs in stacks], vis, None, w_scale=[1e10] * 3)
+    for k in range(3):
+        assert np.array_equal(sols[k], single[k][0]), k
+        assert reps[k].n_iter == single[k][1].n_iter
+        assert np.max(np.abs(sols[k] - truths[k])) < 0.5 * I.ARCSEC
+    for gs in stacks:
+        gs.close()
