@@ -15,6 +15,10 @@ context reading them (``psc_set_wstack``).
 evaluation's time with the stack and with the snapshot grid alone (same
 context and brick shape), how far apart the two models are, and the offsets
 both recover from data predicted by a stack eight times finer.
+``batched_intervals`` covers the workload's own short intervals instead: per
+interval a plane, a snapshot grid and a stack of what the plane leaves, all
+contexts in one batch (one persistent launch of the stacked kernel per LM
+iteration), timed with and without the stacks.
 """
 from __future__ import annotations
 
@@ -60,10 +64,7 @@ class StackSession:
         """Plane grids for interpolation error eps (relative, per source)."""
         if eps in self.stacks:
             return self.stacks[eps]
-        t_max = 2.0 * math.pi * float(np.max(np.abs(self.comp[:, 3])))
-        dw = math.sqrt(8.0 * eps) / t_max
-        w0 = math.floor(self.w_lo / dw) * dw
-        n = max(2, int(math.ceil((self.w_hi - w0) / dw)) + 1)
+        w0, dw, n = _stack_extent(self.comp, self.w_lo, self.w_hi, eps)
         planes = torch.empty((n, self.wl.n_grid, self.wl.n_grid), dtype=torch.complex64, device=self.device)
         torch.cuda.synchronize(self.device)
         t = time.perf_counter()
@@ -83,6 +84,77 @@ class StackSession:
     def close(self):
         self.ctx.close()
         self.stacks = {}
+
+
+def _stack_extent(comp, w_lo, w_hi, eps):
+    """(w0, dw, n_planes) covering [w_lo, w_hi] with interpolation error eps."""
+    dw = math.sqrt(8.0 * eps) / (2.0 * math.pi * float(np.max(np.abs(comp[:, 3]))))
+    w0 = math.floor(w_lo / dw) * dw
+    return w0, dw, max(2, int(math.ceil((w_hi - w0) / dw)) + 1)
+
+
+def batched_intervals(wl: I.Workload, eps: float = 1e-6, n_iter: int = 5, stream=None):
+    """W-snapshots plus a residual-w stack per solution interval, batched."""
+    dev = torch.device("cuda:0")
+    stream = stream if stream is not None else torch.cuda.current_stream(dev)
+    uvw = torch.from_numpy(np.ascontiguousarray(wl.uvw_m)).to(dev)
+    row = wl.n_bl * 3 * 8
+    f_lo, f_hi = float(np.min(wl.freq_hz)), float(np.max(wl.freq_hz))
+    ctxs, keep, n_planes = [], [], []
+    for (t0, nt) in wl.intervals:
+        ptr = uvw.data_ptr() + t0 * row
+        a, b = _abi.psc_snapshot_plane(ptr, nt * wl.n_bl, stream)
+        lo_m, hi_m = _abi.psc_wstack_range(ptr, nt * wl.n_bl, a, b, stream)
+        comp = _abi.psc_wstack_components(wl.sky, a, b, wl.ap_kind, wl.diam_m, wl.alpha_per_dlambda,
+                                          0.5 * (f_lo + f_hi))
+        w0, dw, n = _stack_extent(comp, min(lo_m * f_lo, lo_m * f_hi) / C_LIGHT,
+                                  max(hi_m * f_lo, hi_m * f_hi) / C_LIGHT, eps)
+        grid = torch.empty((wl.n_grid, wl.n_grid), dtype=torch.complex64, device=dev)
+        _abi.psc_model_grid_components(comp[:, :3], wl.n_grid, wl.cell_rad, grid, stream)
+        planes = torch.empty((n, wl.n_grid, wl.n_grid), dtype=torch.complex64, device=dev)
+        _abi.psc_model_grid_wstack(comp, wl.n_grid, wl.cell_rad, n, w0, dw, planes, stream)
+        ctx = _abi.Context(wl.n_ant, nt, wl.n_chan, ptr, wl.freq_hz, wl.ap_kind, wl.diam_m, wl.alpha_per_dlambda,
+                           wl.decorrelation, wl.image.shape[0], wl.n_grid, wl.cell_rad, wl.support, wl.oversample,
+                           grid.data_ptr(), stream)
+        ctx.psc_set_wstack(planes, n, w0, dw, a, b)
+        ctxs.append(ctx)
+        keep.append((grid, planes, (w0, dw, n, a, b)))
+        n_planes.append(n)
+    vis = torch.empty((wl.n_time, wl.n_bl, wl.n_chan), dtype=torch.complex64, device=dev)
+    vk = []
+    for k, ((t0, nt), ctx) in enumerate(zip(wl.intervals, ctxs)):
+        vk.append(vis[t0:t0 + nt])
+        ctx.psc_predict(wl.lm_true[k], vk[-1])
+
+    def iteration_ms():
+        batch = _abi.Batch(ctxs, vk, None, w_scale=[1.0 / wl.sigma_noise ** 2] * len(ctxs), stream=stream)
+        batch.psc_batch_autotune()
+        batch.psc_batch_begin([np.zeros((wl.n_ant, 2))] * len(ctxs))
+        for _ in range(2):
+            batch.psc_batch_restart()
+            batch.psc_batch_iterate(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(n_iter):
+            batch.psc_batch_restart()
+            batch.psc_batch_iterate(1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        batch.close()
+        return e0.elapsed_time(e1) / n_iter
+
+    ms_stack = iteration_ms()
+    for ctx in ctxs:
+        ctx.psc_set_wstack(None, 0)
+    ms_snap = iteration_ms()
+    for ctx in ctxs:
+        ctx.close()
+    n_vis = wl.n_time * wl.n_bl * wl.n_chan
+    return {"n_intervals": len(wl.intervals), "planes_per_interval": n_planes,
+            "stack_bytes": int(sum(n_planes)) * wl.n_grid * wl.n_grid * 8,
+            "batched_iteration_ms_stack": ms_stack, "gvis_per_s_stack": n_vis / (ms_stack * 1e-3) / 1e9,
+            "batched_iteration_ms_snapshot_grids": ms_snap, "gvis_per_s_snapshot_grids": n_vis / (ms_snap * 1e-3) / 1e9}
 
 
 def _apply(ctx, tl):
@@ -149,6 +221,8 @@ def run(name="vla27_l64ch", seed=0, eps=1e-6, n_eval=5, **over):
         solves[label] = {"rms_err_arcsec": float(np.sqrt(np.mean((sol - lm_true) ** 2)) / I.ARCSEC),
                          "lm_iters": rep.n_iter, "solve_s": time.perf_counter() - t}
     st = sess.stacks[eps]
+    sess.close()
+    batched = batched_intervals(wl, eps)
     taps = RL.taps_per_channel(wl)
     flops = wl.n_time * wl.n_bl * float(np.sum(taps)) * RL.FLOPS_PER_TAP_WSTACK
     props = torch.cuda.get_device_properties(vis.device)
@@ -162,8 +236,8 @@ def run(name="vla27_l64ch", seed=0, eps=1e-6, n_eval=5, **over):
            "eval_ms_snapshot_grid": ms_snap, "gvis_per_s_snapshot_grid": n_vis / (ms_snap * 1e-3) / 1e9,
            "model_gap_rel_l2": model_gap, "data_stack": fine_info, "solve": solves,
            "roofline": {"bound": "alu", "achieved": tflops, "peak": peak, "unit": "TFLOP/s", "frac": tflops / peak,
-                        "flops_per_tap": RL.FLOPS_PER_TAP_WSTACK}}
-    sess.close()
+                        "flops_per_tap": RL.FLOPS_PER_TAP_WSTACK},
+           "batched_short_intervals": batched}
     return out
 
 
