@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
+#include <cstdint>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -399,7 +400,9 @@ psc_status psc_snapshot_components(int n_comp, const double *comp_in, double a, 
 psc_status psc_wstack_components(int n_comp, const double *comp_in, double a, double b, const psc_aperture *ap,
                                  double freq_hz, double *comp_out) {
     if (n_comp < 0 || (n_comp > 0 && (!comp_in || !comp_out))) return fail(nullptr, PSC_ERR_ARG, "component arrays must be non-NULL");
-    if (n_comp > 0 && comp_out < comp_in + 3 * (size_t)n_comp && comp_in < comp_out + 4 * (size_t)n_comp)
+    const uintptr_t in0 = (uintptr_t)comp_in, out0 = (uintptr_t)comp_out;
+    if (n_comp > 0 && out0 < in0 + 3 * sizeof(double) * (size_t)n_comp &&
+        in0 < out0 + 4 * sizeof(double) * (size_t)n_comp)
         return fail(nullptr, PSC_ERR_ARG, "comp_out must not overlap comp_in");
     std::vector<double> snap(3 * (size_t)n_comp);
     psc_status st = psc_snapshot_components(n_comp, comp_in, a, b, ap, freq_hz, snap.data());

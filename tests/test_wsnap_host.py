@@ -50,3 +50,8 @@ def test_wstack_components_match_oracle(kind):
         assert np.all(got[:, 3] < 0)
     with pytest.raises(_abi.PscError):
         _abi.psc_wstack_components(np.array([[0.8, 0.7, 1.0]]), 0.1, 0.1, kind, 25.0, alpha, 1.4e9)
+    import ctypes
+    buf = np.zeros((4, 4))                                   # output overlapping the input
+    ap = _abi.psc_aperture(_abi.PSC_AP_DISK if kind == "disk" else _abi.PSC_AP_GAUSS, 25.0, alpha, 1)
+    assert _abi.lib().psc_wstack_components(3, buf.ctypes.data_as(_abi._D), 0.0, 0.0, ctypes.byref(ap), 1.4e9,
+                                            buf.ctypes.data_as(_abi._D)) == _abi.PSC_ERR_ARG
