@@ -31,3 +31,16 @@ def test_reference_arm_prints_one_contract_line():
 
 def test_reference_arm_is_silent_on_other_ranks():
     assert _run({"RANK": "1", "LOCAL_RANK": "1", "WORLD_SIZE": "2"}) == []
+
+
+def test_our_arm_refuses_to_run_without_a_gpu():
+    """No CPU fallback: without a CUDA device the benchmark exits non-zero."""
+    import pytest
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    out = subprocess.run([sys.executable, "bench.py", "--steps", "1", "--warmup", "3"], cwd=ROOT,
+                         capture_output=True, text=True, timeout=300)
+    assert out.returncode != 0
+    assert "needs a CUDA device" in out.stderr + out.stdout
+    assert not [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
