@@ -37,3 +37,21 @@ def test_binding_loads_and_reports_argument_errors_without_a_device():
     st = L.psc_model_grid(ctypes.byref(gd), None, None, None)
     assert st == _abi.PSC_ERR_ARG
     assert L.psc_lm_restart(None) == _abi.PSC_ERR_ARG
+
+
+def test_stack_calls_check_their_arguments_without_a_device():
+    """The residual-w stack's calls refuse bad arguments before any CUDA call."""
+    L = _abi.lib()
+    D = ctypes.POINTER(ctypes.c_double)
+    x = (ctypes.c_double * 8)()
+    lo, hi = ctypes.c_double(), ctypes.c_double()
+    assert L.psc_set_wstack(None, None, 0, 0.0, 1.0, 0.0, 0.0) == _abi.PSC_ERR_ARG        # no context
+    assert L.psc_wstack_range(None, 10, 0.0, 0.0, ctypes.byref(lo), ctypes.byref(hi), None) == _abi.PSC_ERR_ARG
+    assert L.psc_wstack_range(ctypes.addressof(x), 0, 0.0, 0.0, ctypes.byref(lo), ctypes.byref(hi),
+                              None) == _abi.PSC_ERR_ARG                                 # no rows
+    for n_planes, dw in ((1, 10.0), (4, 0.0), (4, float("nan"))):
+        assert L.psc_model_grid_wstack(1, ctypes.cast(x, D), 64, 1e-5, n_planes, 0.0, dw, ctypes.addressof(x),
+                                       None) == _abi.PSC_ERR_ARG
+    assert L.psc_model_grid_wstack(1, ctypes.cast(x, D), 63, 1e-5, 4, 0.0, 10.0, ctypes.addressof(x),
+                                   None) == _abi.PSC_ERR_ARG                            # odd grid
+    assert b"n_grid" in L.psc_last_error(None)
