@@ -63,3 +63,50 @@ def test_time_stride_keeps_every_kth_step():
     f1 = F.features(m, V, None, SIG, time_stride=3)
     f2 = F.features(m3, V[::3], None, SIG, time_stride=1)
     assert np.allclose(f1[:, 2:], f2[:, 2:], rtol=1e-12)
+
+
+def _chi2(m, lm, vobs):
+    V, _ = psc.predict(m, lm, False)
+    return float(np.sum(np.abs(vobs - V) ** 2))
+
+
+def test_newton_step_columns_follow_the_offset_and_finite_differences():
+    """Columns 0-1 are the block Newton step -H_ii^-1 g_i at zero offsets over
+    sigma_prior.  With one antenna offset by a small delta (unequal l and m, so
+    a swapped pair or a flipped sign shows) on noiseless data, the step of that
+    antenna is delta to first order, and every antenna's step equals the one
+    formed from a central finite-difference gradient and Hessian of chi^2
+    (a route that never uses the analytic derivatives of Eq. DAIJPOINTING)."""
+    m, _, _, _ = cases.problem(cases.DISK_SMALL, n_ant=5, n_time=6, freqs=(1.3e9, 1.45e9))
+    n = m.n_ant
+    delta = np.array([3.0, -1.2]) * I.ARCSEC
+    lm = np.zeros((n, 2))
+    lm[2] = delta
+    vobs, _ = psc.predict(m, lm, False)
+    f = F.features(m, vobs, None, SIG)
+    step = f[:, :2] * SIG
+    # antenna 2: the offset itself, to first order in delta
+    assert np.allclose(step[2], delta, rtol=0.03, atol=0.02 * I.ARCSEC)
+    # every antenna: -H_ii^-1 g_i with g and H from finite differences of chi^2
+    h = 0.05 * I.ARCSEC
+    z = np.zeros((n, 2))
+    for a in range(n):
+        g = np.zeros(2)
+        H = np.zeros((2, 2))
+        for p in range(2):
+            e = np.zeros((n, 2))
+            e[a, p] = h
+            g[p] = (_chi2(m, z + e, vobs) - _chi2(m, z - e, vobs)) / (2 * h)
+            for q in range(2):
+                d = np.zeros((n, 2))
+                d[a, q] = h
+                H[p, q] = (_chi2(m, z + e + d, vobs) - _chi2(m, z + e - d, vobs)
+                           - _chi2(m, z - e + d, vobs) + _chi2(m, z - e - d, vobs)) / (4 * h * h)
+        # the full Hessian at small residuals is the Gauss-Newton block to O(delta)
+        s_fd = -np.linalg.solve(0.5 * (H + H.T), g)
+        assert np.allclose(step[a], s_fd, rtol=0.05, atol=0.01 * np.linalg.norm(delta)), a
+    # the antennas that share no term with antenna 2's offset see a smaller,
+    # same-signed pull: baseline (i, 2) moves with l_i + l_2
+    for a in (0, 1, 3, 4):
+        assert np.dot(step[a], delta) > 0
+        assert np.linalg.norm(step[a]) < np.linalg.norm(step[2])
