@@ -519,26 +519,33 @@ psc_status psc_solve_batch(psc_ctx *const *ctxs, int n_ctx, const void *const *v
  * run in a real-time loop where cudaMalloc / cudaFree, which can synchronise
  * the whole device, are not acceptable.  It needs no psc_ctx and allocates
  * no memory: its working memory (channel constants, A° tables, antenna
- * pairs, per-brick partial sums, per-baseline sums, the packed result) lives
- * in one file-scope device array of 16 MiB that every GPU which loads the
- * library holds until the process exits.
+ * pairs, the FP32 split of the baseline coordinates, per-brick partial sums,
+ * per-baseline sums, the packed result) lives in one file-scope device array
+ * of 16 MiB that every GPU which loads the library holds until the process
+ * exits.
  * Inputs and outputs are those of psc_create + psc_residual_grad: obs,
  * ap and gd as for psc_create; grid_dev device complex64 [Ng][Ng]; lm host
  * [n_ant][2]; vis_obs device complex64 [n_time][n_bl][n_chan]; w device float
  * of the same shape or NULL (all ones), scaled by w_scale > 0; outputs on the
  * host: chi2 (1), grad [n_ant][2], normal [n_ant][3], cross [n_bl][4] (NULL
- * to skip).  The fused kernel runs with t_tile 32 and c_group 4, so results
- * equal those of psc_residual_grad with the default tiling.
+ * to skip).  The fused kernel runs with t_tile 32, c_group 4, one visibility
+ * per thread and staging on, on the same inputs as a context's, so the
+ * results equal bit for bit those of psc_residual_grad with that tiling.
  * Limits: a problem whose scratch exceeds 16 MiB -- about 15 * 8 bytes per
- * (baseline, 4 channels, 32 time steps) brick plus the tables -- is rejected
- * with PSC_ERR_ARG and a message giving the size it needed; for example 351
- * baselines x 64 channels x 150 time steps needs about 3.5 MB.
+ * (baseline, 4 channels, 32 time steps) brick plus 16 bytes per (time step,
+ * baseline) plus the tables -- is rejected with PSC_ERR_ARG and a message
+ * giving the size it needed; for example 351 baselines x 64 channels x 150
+ * time steps needs about 4.4 MB.  Tables of 4 channels that do not fit the
+ * fused kernel's shared memory are rejected with PSC_ERR_ARG too.  Both
+ * checks come before any work is queued.
  * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  Every call shares the one array and overwrites
- * what it reads, so nothing needs clearing, but calls that overlap on the GPU
- * (different streams or host threads) race on it and must be serialised by
- * the caller.  Runs on `stream` (cudaStream_t or NULL) and synchronises it.
+ * (cudaGetSymbolAddress) and raises the fused kernel's shared-memory limit,
+ * with that device current; make that first call before any stream capture.
+ * Every call shares the one array and overwrites what it reads, so nothing
+ * needs clearing, but calls that overlap on the GPU (different streams or host
+ * threads) race on it and must be serialised by the caller.  The call copies
+ * lm from pageable host memory, runs on `stream` (cudaStream_t or NULL) and
+ * returns after synchronising it, with the outputs on the host.
  * Errors are reported through psc_last_error(NULL). */
 psc_status psc_residual_grad_noalloc(const psc_obs *obs, const psc_aperture *ap, const psc_grid_desc *gd,
                                      const void *grid_dev, const double *lm, const void *vis_obs,

@@ -253,8 +253,21 @@ def psc_residual_grad_noalloc(n_ant, n_time, n_chan, uvw_dev, freq_hz, ap_kind, 
                               decorrelation, n_img, n_grid, cell_rad, support, oversample, grid_dev, lm, vis_obs,
                               w=None, w_scale=1.0, cross=False, stream=None):
     """Allocation-free fused evaluation (no psc_ctx; scratch in the
-    library's static device array).  Returns (chi2, g, H[, X])."""
+    library's static device array).  Returns (chi2, g, H[, X]).
+
+    Device tensors are checked against the problem's sizes before the call,
+    so a short buffer raises here instead of being read past its end."""
     freq = np.ascontiguousarray(freq_hz, dtype=np.float64)
+    n_ant, n_time, n_chan = int(n_ant), int(n_time), int(n_chan)
+    n_vis = n_time * (n_ant * (n_ant - 1) // 2) * n_chan
+    if freq.shape != (n_chan,):
+        raise ValueError("freq_hz must hold n_chan values")
+    if np.shape(lm) != (n_ant, 2):
+        raise ValueError("lm must be [n_ant][2]")
+    for name, x, need in (("uvw_dev", uvw_dev, 3 * n_vis // max(n_chan, 1)), ("vis_obs", vis_obs, n_vis),
+                          ("w", w, n_vis), ("grid_dev", grid_dev, int(n_grid) ** 2)):
+        if x is not None and not isinstance(x, int) and x.numel() < need:
+            raise ValueError("%s holds %d elements; the problem needs %d" % (name, x.numel(), need))
     obs = psc_obs(int(n_ant), int(n_time), int(n_chan), _ptr(uvw_dev), _dp(freq))
     kind = {"disk": PSC_AP_DISK, "gauss": PSC_AP_GAUSS}.get(ap_kind, ap_kind)
     ap = psc_aperture(int(kind), float(diam_m), float(alpha_per_dlambda), int(decorrelation))

@@ -806,11 +806,9 @@ cudaError_t eval_batch_occupancy(int threads, size_t dyn, bool stacked, int *blo
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, eval_kernel<false, false>, threads, dyn);
 }
 
-// Raises the fused kernel's dynamic shared-memory limit to everything the
-// device allows beyond its static shared memory (never lowers it, so contexts
-// with different channel groups can share the kernel), after checking that
-// `dyn` bytes fit.
-cudaError_t set_eval_smem(size_t dyn) {
+// Dynamic shared memory the fused kernel can have on the current device: the
+// opt-in limit less its static shared memory.
+cudaError_t eval_smem_allowed(size_t *allowed) {
     int dev = 0, optin = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
@@ -819,7 +817,18 @@ cudaError_t set_eval_smem(size_t dyn) {
     cudaFuncAttributes fa{};
     e = cudaFuncGetAttributes(&fa, eval_kernel<false, false>);
     if (e != cudaSuccess) return e;
-    const size_t allowed = (size_t)optin > fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes : 0;
+    *allowed = (size_t)optin > fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes : 0;
+    return cudaSuccess;
+}
+
+// Raises the fused kernel's dynamic shared-memory limit to everything the
+// device allows beyond its static shared memory (never lowers it, so contexts
+// with different channel groups can share the kernel), after checking that
+// `dyn` bytes fit.
+cudaError_t set_eval_smem(size_t dyn) {
+    size_t allowed = 0;
+    cudaError_t e = eval_smem_allowed(&allowed);
+    if (e != cudaSuccess) return e;
     if (dyn > allowed) return cudaErrorInvalidValue;
     for (const void *k : {(const void *)eval_kernel<true, false>, (const void *)eval_kernel<false, false>,
                           (const void *)eval_kernel<true, true>, (const void *)eval_kernel<false, true>}) {

@@ -8,18 +8,20 @@
 // point needs no psc_ctx and allocates nothing.  All of its working memory
 // lives in one file-scope device array of kScratchBytes (16 MiB), which every
 // GPU that loads the library holds until the process exits: channel
-// constants, A° tables, antenna pairs, per-brick partial sums, per-baseline
-// sums and the packed result.  The caller still passes every input and
-// output.
+// constants, A° tables, antenna pairs, the FP32 split of the baseline
+// coordinates, per-brick partial sums, per-baseline sums and the packed
+// result.  The caller still passes every input and output.
 //
 // The host cannot use the array's name as a device address (in host code it
 // names a host-side stand-in), so the address is looked up with
 // cudaGetSymbolAddress once per device, with that device current, on the
-// first call made on that device.  Every call shares the array: each call
+// first call made on that device; that call also raises the fused kernel's
+// shared-memory limit on the device.  Every call shares the array: each call
 // rewrites every scratch word that it reads, so no clearing is needed, and
 // calls that overlap on the GPU (two streams, or two host threads) race on it.
-// The kernels are the ones psc_residual_grad launches, so the results are the
-// same.
+// The kernels, their inputs and their launch shape are the ones
+// psc_residual_grad uses with its default tiling, so the results are the same
+// bit for bit.
 #include <cmath>
 #include <cstdio>
 #include <mutex>
@@ -36,6 +38,7 @@ static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
 std::mutex g_addr_mu;
 unsigned char *g_addr[kMaxDevices] = {};
+size_t g_smem_allowed[kMaxDevices] = {};      // fused kernel's dynamic shared memory on each device
 
 // Channel constants, table layout and antenna pairs, computed on the device
 // from the channel frequencies (one block).
@@ -130,6 +133,7 @@ extern "C" psc_status psc_residual_grad_noalloc(const psc_obs *obs, const psc_ap
     const size_t o_tlen = off;  off = align256(off + sizeof(int) * nc);
     const size_t o_tabs = off;  off = align256(off + sizeof(float2) * (size_t)total_tab);
     const size_t o_pair = off;  off = align256(off + sizeof(int2) * (size_t)n_bl);
+    const size_t o_uvs = off;   off = align256(off + sizeof(float4) * (size_t)nt * n_bl);
     const size_t o_part = off;  off = align256(off + sizeof(double) * kRed * n_bricks);
     const size_t o_blsm = off;  off = align256(off + sizeof(double) * kRed * (size_t)n_bl);
     const size_t o_ev = off;    off = align256(off + sizeof(double) * evn);
@@ -142,22 +146,36 @@ extern "C" psc_status psc_residual_grad_noalloc(const psc_obs *obs, const psc_ap
         return set_global_error(PSC_ERR_ARG, buf);
     }
 
-    // once per device, with that device current: the array's device address
+    // once per device, with that device current: the array's device address,
+    // and the fused kernel's shared-memory limit raised to what the device allows
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return fail_cuda(e, "cudaGetDevice");
     if (dev < 0 || dev >= kMaxDevices) return fail_arg("psc_residual_grad_noalloc: device ordinal beyond 63");
     unsigned char *base = nullptr;
+    size_t smem_allowed = 0;
     {
         std::lock_guard<std::mutex> lk(g_addr_mu);
         if (!g_addr[dev]) {
             void *p = nullptr;
             e = cudaGetSymbolAddress(&p, g_scratch);
             if (e != cudaSuccess) return fail_cuda(e, "cudaGetSymbolAddress");
+            size_t allowed = 0;
+            e = eval_smem_allowed(&allowed);
+            if (e != cudaSuccess) return fail_cuda(e, "shared-memory limit");
+            e = set_eval_smem(0);
+            if (e != cudaSuccess) return fail_cuda(e, "shared-memory limit");
+            g_smem_allowed[dev] = allowed;
             g_addr[dev] = (unsigned char *)p;
         }
         base = g_addr[dev];
+        smem_allowed = g_smem_allowed[dev];
     }
+    // the tables of one channel group must fit the block's shared memory; checked
+    // before any work is queued
+    if (eval_dyn_smem(c_group, max_tab + 2) > smem_allowed)
+        return fail_arg("psc_residual_grad_noalloc: the aperture tables of 4 channels exceed the fused kernel's "
+                        "shared memory (aperture much wider than the grid cell)");
 
     cudaStream_t s = (cudaStream_t)stream;
     double *d_freq = (double *)(base + o_freq);
@@ -165,6 +183,7 @@ extern "C" psc_status psc_residual_grad_noalloc(const psc_obs *obs, const psc_ap
     int *d_toff = (int *)(base + o_toff), *d_tlen = (int *)(base + o_tlen);
     float2 *d_tabs = (float2 *)(base + o_tabs);
     int2 *d_pairs = (int2 *)(base + o_pair);
+    float4 *d_uvs = (float4 *)(base + o_uvs);
     double *d_part = (double *)(base + o_part), *d_blsum = (double *)(base + o_blsm);
     double *d_ev = (double *)(base + o_ev), *d_lm = (double *)(base + o_lm);
 
@@ -180,10 +199,11 @@ extern "C" psc_status psc_residual_grad_noalloc(const psc_obs *obs, const psc_ap
                                            gd->support, d_chan, d_toff, d_tlen, n_ant, d_pairs);
     NA_CUDA(cudaGetLastError());
     NA_CUDA(launch_tables(*ap, d_freq, nc, du, ov, gd->support, d_toff, d_tlen, d_tabs, s));
-    NA_CUDA(set_eval_smem(eval_dyn_smem(c_group, max_tab + 2)));
+    NA_CUDA(launch_split_uv(obs->uvw_dev, (size_t)nt * n_bl, d_uvs, s));
 
     EvalArgs a{};
     a.uvw = obs->uvw_dev;
+    a.uvs = d_uvs;
     a.grid = (const float2 *)grid_dev;
     a.chan = d_chan;
     a.tabs = d_tabs;

@@ -147,6 +147,8 @@ size_t lm_smem_bytes(int n_ant);
 cudaError_t lm_prepare(int n_ant);
 cudaError_t launch_lm_restart(const LMArgs &a, const LMState *st0, const double *lm0, cudaStream_t s);
 cudaError_t set_eval_smem(size_t dyn);
+// Dynamic shared memory available to one fused-kernel block on the current device.
+cudaError_t eval_smem_allowed(size_t *allowed);
 // Exact disk kernel (exact.cu): the fused evaluation with it (one launch per
 // context, one visibility per thread), its dynamic shared memory, and the
 // per-channel lens-moment combinations ([sum of table lengths][10] floats)

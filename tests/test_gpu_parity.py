@@ -1,10 +1,12 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 oracle.
 
 Tolerances: visibilities and their derivatives within a relative L2 error of
-1e-5 (FP32 complex against FP64); chi^2 and the normal blocks to the same
-relative level; the gradient, which is a sum of terms of both signs, to 1e-5
-of the sum of the magnitudes of its terms; solved offsets within 0.1 arcsec
-of the oracle's solution.
+1e-5 (FP32 complex against FP64), and every single visibility within 2e-5 of
+the array's largest magnitude (so that a few wrong visibilities cannot hide
+under the norm); chi^2 and the normal blocks to the same relative level; the
+gradient, which is a sum of terms of both signs, to 1e-5 of the sum of the
+magnitudes of its terms; solved offsets within 0.1 arcsec of the oracle's
+solution.
 """
 import math
 
@@ -21,6 +23,7 @@ import cases
 from gpu_cases import GpuProblem
 
 TOL_V = 1e-5
+TOL_PT = 2e-5      # per visibility, relative to the largest |V| of the array
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -31,6 +34,12 @@ def _need_gpu():
 
 def _rel(a, b):
     return cases.rel_l2(a, b)
+
+
+def _assert_vis(got, ref):
+    """Relative L2 within TOL_V and every element within TOL_PT of max |ref|."""
+    assert _rel(got, ref) < TOL_V
+    assert np.max(np.abs(np.asarray(got) - ref)) <= TOL_PT * np.max(np.abs(ref))
 
 
 @pytest.mark.parametrize("spec", [cases.GAUSS_SMALL, cases.DISK_SMALL])
@@ -72,9 +81,9 @@ def test_predict_matches_oracle(case):
     V, dV = psc.predict(m, lm)
     gp = GpuProblem(m, img, t_tile=tt, c_group=cg)
     Vg, dVg = gp.predict(lm)
-    assert _rel(Vg, V) < TOL_V
+    _assert_vis(Vg, V)
     for p in range(4):
-        assert _rel(dVg[p], dV[p]) < TOL_V, p
+        _assert_vis(dVg[p], dV[p])
 
 
 # Two visibilities per thread (consecutive times share the staged cells):
@@ -97,9 +106,9 @@ def test_two_visibilities_per_thread_match_oracle(case):
     V, dV = psc.predict(m, lmt)
     gp = GpuProblem(m, img, t_tile=tt, c_group=cg, kv=2)
     Vg, dVg = gp.predict(lmt)
-    assert _rel(Vg, V) < TOL_V
+    _assert_vis(Vg, V)
     for p in range(4):
-        assert _rel(dVg[p], dV[p]) < TOL_V, p
+        _assert_vis(dVg[p], dV[p])
     vobs, w = _obs(m, lmt)
     lm = 0.5 * lmt
     chi2, g, H, X = psc.chi2_grad_normal(m, lm, vobs, w)
@@ -129,8 +138,9 @@ def test_predict_with_the_oracle_grid():
     gp = GpuProblem(m, img, use_oracle_grid=True)
     V, dV = psc.predict(m, lm)
     Vg, dVg = gp.predict(lm)
-    assert _rel(Vg, V) < TOL_V
-    assert max(_rel(dVg[p], dV[p]) for p in range(4)) < TOL_V
+    _assert_vis(Vg, V)
+    for p in range(4):
+        _assert_vis(dVg[p], dV[p])
 
 
 def test_unstaged_fallback_matches_oracle():
@@ -141,8 +151,9 @@ def test_unstaged_fallback_matches_oracle():
     V, dV = psc.predict(m, lm)
     gp = GpuProblem(m, img, t_tile=8, c_group=4)
     Vg, dVg = gp.predict(lm)
-    assert _rel(Vg, V) < TOL_V
-    assert max(_rel(dVg[p], dV[p]) for p in range(4)) < TOL_V
+    _assert_vis(Vg, V)
+    for p in range(4):
+        _assert_vis(dVg[p], dV[p])
 
 
 # Flat bricks (psc_set_flat_tiling): (n_ant, n_time, freqs, items, kv) with
@@ -165,8 +176,9 @@ def test_flat_bricks_match_oracle(case):
     gp = GpuProblem(m, img)
     gp.ctx.psc_set_flat_tiling(items, kv)
     Vg, dVg = gp.predict(lmt)
-    assert _rel(Vg, V) < TOL_V
-    assert max(_rel(dVg[p], dV[p]) for p in range(4)) < TOL_V
+    _assert_vis(Vg, V)
+    for p in range(4):
+        _assert_vis(dVg[p], dV[p])
     vobs, w = _obs(m, lmt)
     lm = 0.5 * lmt
     chi2, g, H, X = psc.chi2_grad_normal(m, lm, vobs, w)
@@ -202,8 +214,9 @@ def test_never_staged_matches_oracle(kv):
     gp = GpuProblem(m, img, t_tile=16, c_group=2, kv=kv)
     gp.ctx.psc_set_staging(_abi.PSC_STAGE_NEVER)
     Vg, dVg = gp.predict(lmt)
-    assert _rel(Vg, V) < TOL_V
-    assert max(_rel(dVg[p], dV[p]) for p in range(4)) < TOL_V
+    _assert_vis(Vg, V)
+    for p in range(4):
+        _assert_vis(dVg[p], dV[p])
     vobs, w = _obs(m, lmt)
     chi2, g, H, X = psc.chi2_grad_normal(m, 0.5 * lmt, vobs, w)
     chi2g, gg, Hg, Xg = gp.ctx.psc_residual_grad(0.5 * lmt, gp.upload(vobs), gp.upload(w, torch.float32), 1.0,
@@ -250,6 +263,9 @@ def test_residual_grad_matches_oracle(case):
     gp = GpuProblem(m, img, t_tile=tt, c_group=cg)
     chi2g, gg, Hg, Xg = gp.ctx.psc_residual_grad(lm, gp.upload(vobs), gp.upload(w, torch.float32), 1.0, cross=True)
     assert abs(chi2g - chi2) < TOL_V * _chi2_scale(m, lm, vobs, w)
+    # at half the true offsets the residuals are not small against V, so chi^2
+    # also holds plain relative accuracy
+    assert abs(chi2g - chi2) < TOL_V * chi2
     # gradient scale: sum over visibilities of |2 w R dV|
     V, dV = psc.predict(m, lm)
     gscale = 2.0 * np.sum(w[None] * np.abs(vobs - V)[None] * np.abs(dV))
@@ -362,8 +378,9 @@ def test_visibilities_on_and_near_grid_nodes():
     m2 = psc.Model(**{**m.__dict__, "uvw_m": uvw})
     V, dV = psc.predict(m2, lm)
     Vg, dVg = GpuProblem(m2, img).predict(lm)
-    assert _rel(Vg, V) < TOL_V
-    assert max(_rel(dVg[p], dV[p]) for p in range(4)) < TOL_V
+    _assert_vis(Vg, V)
+    for p in range(4):
+        _assert_vis(dVg[p], dV[p])
 
 
 def test_brick_order_keeps_results_bitwise():
@@ -412,8 +429,9 @@ def test_support_and_oversampling_extremes_match_oracle(spec, support, ov):
     V, dV = psc.predict(m, lmt)
     gp = GpuProblem(m, img)
     Vg, dVg = gp.predict(lmt)
-    assert _rel(Vg, V) < TOL_V
-    assert max(_rel(dVg[p], dV[p]) for p in range(4)) < TOL_V
+    _assert_vis(Vg, V)
+    for p in range(4):
+        _assert_vis(dVg[p], dV[p])
     vobs, w = _obs(m, lmt)
     chi2, g, H, X = psc.chi2_grad_normal(m, 0.5 * lmt, vobs, w)
     chi2g, gg, Hg, Xg = gp.ctx.psc_residual_grad(0.5 * lmt, gp.upload(vobs), gp.upload(w, torch.float32), 1.0,
@@ -442,11 +460,43 @@ def test_flat_bricks_never_staged_and_bf16_grid(kv):
     gp.ctx.psc_set_flat_tiling(64, kv)
     gp.ctx.psc_set_staging(_abi.PSC_STAGE_NEVER)
     Vg, dVg = gp.predict(lmt)
-    assert _rel(Vg, V) < TOL_V
-    assert max(_rel(dVg[p], dV[p]) for p in range(4)) < TOL_V
+    _assert_vis(Vg, V)
+    for p in range(4):
+        _assert_vis(dVg[p], dV[p])
     gp.ctx.psc_set_staging(_abi.PSC_STAGE_AUTO)
     gp.ctx.psc_set_grid_precision(_abi.PSC_GRID_BF16)
     Vb, dVb = gp.predict(lmt)
     assert _rel(Vb, V) < 2.0 ** -9
     assert max(_rel(dVb[p], dV[p]) for p in range(4)) < 2.0 ** -9
     gp.ctx.psc_set_grid_precision(_abi.PSC_GRID_F32)
+
+
+def test_nan_weight_stops_the_solver_with_a_numeric_error():
+    """One NaN weight (set on the host) makes chi^2 non-finite at the first
+    evaluation: the solver stops and the synchronising call reports
+    PSC_ERR_NUMERIC; the context then solves clean data as before."""
+    m, _, lmt, img = cases.problem(cases.DISK_SMALL, n_ant=5, n_time=8)
+    vobs, w = _obs(m, lmt)
+    gp = GpuProblem(m, img)
+    bad = w.copy()
+    bad[3, 2, 0] = np.nan
+    with pytest.raises(_abi.PscError) as e:
+        gp.ctx.psc_solve_offsets(gp.upload(vobs), gp.upload(bad, torch.float32), 1.0)
+    assert e.value.status == _abi.PSC_ERR_NUMERIC
+    sol, rep = gp.ctx.psc_solve_offsets(gp.upload(vobs), gp.upload(w, torch.float32), 1.0)
+    assert np.all(np.isfinite(sol)) and _abi.STOP_REASONS[rep.reason] in ("step", "chi2")
+
+
+def test_solve_197_antennas_matches_oracle():
+    """The 394 x 394 damped system of a 197-antenna interval (the arrays of the
+    batched and full-scale workloads) is factored in global memory with FP32
+    Cholesky and FP64 refinement; the offsets must match the oracle's full LM
+    solve within 0.1 arcsec."""
+    m, _, lmt, img = cases.problem(cases.DISK_SMALL, n_ant=197, n_time=3, freqs=(1.3e9, 1.4e9), n_src=8)
+    vobs, w = _obs(m, lmt)
+    sol_o, rep_o = _oracle_solve(m, vobs, w)
+    gp = GpuProblem(m, img)
+    sol_g, rep_g = gp.ctx.psc_solve_offsets(gp.upload(vobs), gp.upload(w, torch.float32), 1.0)
+    assert _abi.STOP_REASONS[rep_g.reason] in ("step", "chi2")
+    assert np.max(np.abs(sol_g - sol_o)) < 0.1 * I.ARCSEC
+    assert abs(rep_g.chi2 - rep_o.chi2) < 1e-4 * rep_o.chi2
