@@ -1,22 +1,30 @@
 #!/usr/bin/env python
 """Benchmark of the Pointing SelfCal hot path on GB300 (one JSON line).
 
-Workload: "vla27_l64ch" -- 27 antennas (351 baselines) in a Y layout with
-1 km arms, 25 m uniform-disk apertures, 64 channels over 1-2 GHz, 600 x 2 s
-split into 4 solution intervals, a 2048^2 model image (8") with 2000
-power-law sources; 13,478,400 visibilities, observed data simulated by the
-GPU predictor at seeded true offsets (sigma 20") plus 1 mJy noise.
+Headline workload (default): "drift197_l128ch", the full-scale case -- 197
+antennas (19,306 baselines) of 15 m uniform-disk apertures in a centrally
+concentrated disk of 8 km radius, 128 channels over 0.95-1.76 GHz, 1800 x 1 s
+in 30 solution intervals of 60 s, a 4096^2 model image (1") with 10^4
+power-law sources padded to an 8192^2 grid; 4,448,102,400 visibilities
+(35.6 GB of complex64, resident in HBM), weights one scalar 1/sigma^2 per
+interval.  Observed data are simulated by the GPU predictor at the seeded
+drifting true offsets plus 1 mJy noise from a seeded device generator.
 
-One step = one Levenberg-Marquardt iteration over all four intervals as one
+One step = one Levenberg-Marquardt iteration over all 30 intervals as one
 batch: a solver restart to the zero start (one small kernel), one persistent
-fused launch over the bricks of all intervals (degrid with the
-pointing-modified kernel, the four pointing derivatives, residuals,
-per-baseline chi^2 / gradient / normal sums), the deterministic per-antenna
-reductions and the LM updates (damped full solve), replayed from a CUDA graph.  value = visibilities evaluated with derivatives per second
-(Gvis/s).  Every step is the first iteration of a solve from zero offsets,
-so no step can be skipped by a stopped solver.  The model-grid DFT and the aperture tables are
-pre-computes outside the iteration loop (Algorithm 1); their time is reported
-under "precompute_ms".
+fused launch over all intervals (degrid with the pointing-modified kernel,
+the four pointing derivatives, residuals, per-baseline chi^2 / gradient /
+normal sums), the deterministic per-antenna reductions and the LM updates
+(damped full solve), replayed from a CUDA graph.  value = visibilities
+evaluated with derivatives per second (Gvis/s).  Every step is the first
+iteration of a solve from zero offsets, so no step can be skipped by a
+stopped solver.  The model-grid DFT and the aperture tables are pre-computes
+outside the iteration loop (Algorithm 1); their time is "precompute_ms".
+
+Secondary keys: the precision-study workload "vla27_l64ch" measured the same
+way; solves/s of the small plain-method workload "vla27_l1ch"; the learned
+initial estimate against plain LM ("learned_init"); and the further sections
+(mixed batch, two polarisations, exact kernel, W-snapshots, residual-w stack).
 
 ``--impl reference`` times the FP64 CPU oracle on the host cores instead
 (rank 0 only), on a bounded sample of the same workload per step.
@@ -24,9 +32,10 @@ under "precompute_ms".
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
-import math
 import os
+import re
 import subprocess
 import sys
 import threading
@@ -38,28 +47,32 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "Gvis/s predict+∂/∂pointing; solves/s to 1″ RMS offset, learned vs plain LM"
-SMS_GB300 = 152
+# workloads whose weights are one scalar per interval (w = NULL): the 35.6 GB
+# of visibilities stay the only per-visibility input
+SCALAR_WEIGHTS = ("drift197_l128ch",)
 
 
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=300)
-    p.add_argument("--warmup", type=int, default=10)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="vla27_l64ch")
+    p.add_argument("--workload", default="drift197_l128ch")
     p.add_argument("--seed", type=int, default=0)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
+    p.add_argument("--no-e2e", action="store_true", help="skip the end-to-end measurement")
+    p.add_argument("--no-secondary", action="store_true", help="skip every section after the headline")
     p.add_argument("--no-learned", action="store_true", help="skip the learned-initialiser comparison")
-    p.add_argument("--no-drift", action="store_true", help="skip the full-scale drifting-pointing section")
     p.add_argument("--no-exact", action="store_true", help="skip the exact-disk-kernel section")
     p.add_argument("--no-wsnap", action="store_true", help="skip the W-snapshot section")
     p.add_argument("--no-wstack", action="store_true", help="skip the residual-w stack section")
+    p.add_argument("--no-squint", action="store_true", help="skip the two-polarisation section")
     p.add_argument("--mixed-intervals", type=int, default=256,
                    help="intervals of the mixed-array batched-solve section (0 skips it)")
-    p.add_argument("--learned-train", type=int, default=3000, help="training intervals of the learned initialiser")
-    p.add_argument("--learned-eval", type=int, default=20, help="held-out intervals of the comparison")
+    p.add_argument("--learned-train", type=int, default=20000, help="training intervals of the learned initialiser")
+    p.add_argument("--learned-eval", type=int, default=512, help="held-out intervals of the comparison")
     return p.parse_args()
 
 
@@ -122,47 +135,89 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(win)}
 
 
-# ---------------------------------------------------------------- workload helpers
+# ---------------------------------------------------------------- shared helpers
 
-def cpu_sample_oracle(wl, vis_host, w_host, target_s, interval=0, min_t=1):
-    """Times the FP64 oracle (predict + derivatives + reductions) on the first
-    timesteps of one interval, enough to take about ``target_s`` seconds."""
+def config_for(wl) -> dict:
+    """The workload description both arms print (identical dictionaries)."""
+    scalar_w = wl.name in SCALAR_WEIGHTS
+    vis_gb = wl.n_vis * 8 / 1e9
+    w_gb = 0.0 if scalar_w else wl.n_vis * 4 / 1e9
+    return {"workload": wl.name, "n_ant": wl.n_ant, "n_bl": wl.n_bl, "n_time": wl.n_time, "n_chan": wl.n_chan,
+            "n_interval": len(wl.intervals), "n_vis": int(wl.n_vis), "image": int(wl.image.shape[0]),
+            "grid": int(wl.n_grid), "support": wl.support, "oversample": wl.oversample, "aperture": wl.ap_kind,
+            "weights": "scalar 1/sigma^2 per interval" if scalar_w else "per visibility",
+            "l2": "inputs larger than L2 (vis %.1f GB + weights %.1f GB + grid %.2f GB per step)"
+                  % (vis_gb, w_gb, wl.n_grid ** 2 * 8 / 1e9),
+            "step": "one LM iteration of all intervals (one persistent fused launch, graph replay)"}
+
+
+def oracle_model(wl, grid, t0, n_t, chans):
+    from oracle import psc
+    return psc.Model(uvw_m=wl.uvw_m[t0:t0 + n_t], freq_hz=wl.freq_hz[chans], n_ant=wl.n_ant, grid=grid,
+                     cell_rad=wl.cell_rad, support=wl.support, oversample=wl.oversample, ap_kind=wl.ap_kind,
+                     diam_m=wl.diam_m, alpha_per_dlambda=wl.alpha_per_dlambda, decorrelation=wl.decorrelation)
+
+
+def sample_channels(wl, n=8):
+    """n channels spread over the band (all of them when there are fewer)."""
+    if wl.n_chan <= n:
+        return np.arange(wl.n_chan)
+    return np.unique(np.round(np.linspace(0, wl.n_chan - 1, n)).astype(int))
+
+
+def oracle_sample(wl, target_s, seed=0):
+    """Times the FP64 oracle (predict + derivatives + chi^2/gradient/normal
+    sums, at zero offsets) on the first time steps of interval 0 over a few
+    channels spread across the band, enough for about ``target_s`` seconds.
+    The oracle's cost per visibility does not depend on the values, so the
+    observed data are seeded noise of the sample's shape."""
     from oracle import model_grid, psc
+    from paper_1709_08681_gb300 import inputs as I
     grid = model_grid.grid_from_image(wl.image, wl.n_grid)
-    t0, nt = 0, wl.n_time          # the sample may run over every interval's time steps
+    chans = sample_channels(wl)
+    t_max = wl.intervals[0][1]
 
     def run(n_t):
-        m = psc.Model(uvw_m=wl.uvw_m[t0:t0 + n_t], freq_hz=wl.freq_hz, n_ant=wl.n_ant, grid=grid,
-                      cell_rad=wl.cell_rad, support=wl.support, oversample=wl.oversample, ap_kind=wl.ap_kind,
-                      diam_m=wl.diam_m, alpha_per_dlambda=wl.alpha_per_dlambda, decorrelation=wl.decorrelation)
-        lm = np.zeros((wl.n_ant, 2))
+        m = oracle_model(wl, grid, 0, n_t, chans)
+        vis = I.complex_noise((n_t, wl.n_bl, len(chans)), 1.0, seed, 77)
+        w = np.full(vis.shape, 1.0 / wl.sigma_noise ** 2)
         t = time.perf_counter()
-        psc.chi2_grad_normal(m, lm, vis_host[t0:t0 + n_t], w_host[t0:t0 + n_t])
+        psc.chi2_grad_normal(m, np.zeros((wl.n_ant, 2)), vis, w)
         return time.perf_counter() - t
 
-    dt1 = run(min_t)
-    n_t = int(max(min_t, min(nt, round(min_t * target_s / max(dt1, 1e-3)))))
-    dt = run(n_t) if n_t != min_t else dt1
-    n_vis = n_t * wl.n_bl * wl.n_chan
-    return n_vis, dt, n_t, grid
+    dt1 = run(1)
+    n_t = int(max(1, min(t_max, round(target_s / max(dt1, 1e-3)))))
+    dt = run(n_t) if n_t != 1 else dt1
+    n_vis = n_t * wl.n_bl * len(chans)
+    return n_vis, dt, n_t, len(chans)
 
 
-def profiled_traffic():
-    """DRAM bytes per fused launch from the committed ncu summary, or None
-    when eval.cu changed since the counters were taken (sha256 prefix)."""
-    import hashlib
-    import re
-    path = os.path.join(ROOT, "profiles", "eval_kernel_vla27_l64ch.md")
-    src = os.path.join(ROOT, "paper_1709_08681_gb300", "csrc", "eval.cu")
+def profiled_traffic(wl_name):
+    """DRAM bytes per fused launch of ``wl_name`` from its committed ncu
+    summary (profiles/*.md naming the workload), or None when the kernel
+    source changed since the counters were taken (sha256 prefix)."""
+    pdir = os.path.join(ROOT, "profiles")
     try:
-        text = open(path).read()
-        want = re.search(r"eval.cu sha256 prefix: ([0-9a-f]+)", text).group(1)
-        have = hashlib.sha256(open(src, "rb").read()).hexdigest()[:len(want)]
-        if want != have:
-            return None
-        return float(re.search(r"traffic per launch \(read \+ write\) \| ([0-9.]+) MB", text).group(1)) * 1e6
-    except (OSError, AttributeError, ValueError):
+        names = sorted(os.listdir(pdir))
+    except OSError:
         return None
+    for fn in names:
+        if not fn.endswith(".md"):
+            continue
+        text = open(os.path.join(pdir, fn)).read()
+        m = re.search(r"headline traffic for: (\S+)", text)
+        if not m or m.group(1) != wl_name:
+            continue
+        try:
+            src, want = re.search(r"source sha256 prefix: (\S+) ([0-9a-f]+)", text).groups()
+            have = hashlib.sha256(open(os.path.join(ROOT, src), "rb").read()).hexdigest()[:len(want)]
+            if have != want:
+                return None
+            return float(re.search(r"traffic per launch \(read \+ write, full workload\) \| ([0-9.e+]+) B", text)
+                         .group(1))
+        except (OSError, AttributeError, ValueError):
+            return None
+    return None
 
 
 def hbm_peak_gbs():
@@ -180,6 +235,18 @@ def omp_threads():
     return int(v) if v else (os.cpu_count() or 1)
 
 
+def host_mem_available():
+    """Bytes of host memory available (Linux /proc/meminfo), or 0."""
+    try:
+        with open("/proc/meminfo") as f:
+            for line in f:
+                if line.startswith("MemAvailable:"):
+                    return int(line.split()[1]) * 1024
+    except (OSError, ValueError, IndexError):
+        pass
+    return 0
+
+
 # ---------------------------------------------------------------- reference arm
 
 def run_reference(args):
@@ -189,15 +256,12 @@ def run_reference(args):
     from paper_1709_08681_gb300 import inputs as I
     from oracle import model_grid, psc
     wl = I.make_workload(args.workload, seed=args.seed)
-    # observed data for the sample: the oracle's own prediction at the true offsets plus noise
     grid = model_grid.grid_from_image(wl.image, wl.n_grid)
-    t0, nt = wl.intervals[0]
-    n_t = 1
-    m = psc.Model(uvw_m=wl.uvw_m[t0:t0 + n_t], freq_hz=wl.freq_hz, n_ant=wl.n_ant, grid=grid, cell_rad=wl.cell_rad,
-                  support=wl.support, oversample=wl.oversample, ap_kind=wl.ap_kind, diam_m=wl.diam_m,
-                  alpha_per_dlambda=wl.alpha_per_dlambda, decorrelation=wl.decorrelation)
+    chans = sample_channels(wl)
+    m = oracle_model(wl, grid, 0, 1, chans)
+    # the oracle's own observed data for the sample: its prediction at the true offsets plus noise
     V, _ = psc.predict(m, wl.lm_true[0], False)
-    vis = V + wl.noise()[t0:t0 + n_t]
+    vis = V + I.complex_noise(V.shape, wl.sigma_noise, wl.seed, 5)
     w = np.full(vis.shape, 1.0 / wl.sigma_noise ** 2)
     lm = np.zeros((wl.n_ant, 2))
     for _ in range(args.warmup):
@@ -208,19 +272,187 @@ def run_reference(args):
     dt = time.perf_counter() - t
     n_vis = vis.size
     value = n_vis * args.steps / dt / 1e9
+    sample = ("interval 0, time step 0 x %d baselines x %d channels spread over the band (%d visibilities) per "
+              "step; FP64 predict + derivatives + chi^2/gradient/normal sums" % (wl.n_bl, len(chans), n_vis))
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "Gvis/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "sample": "interval 0, first timestep: %d visibilities per step" % n_vis},
+        "config": config_for(wl),
         "cpu_baseline": {"value": value, "unit": "Gvis/s", "cores": omp_threads(), "kind": "oracle",
-                         "sample": "interval 0, 1 timestep x 351 baselines x 64 channels per step"},
+                         "sample": sample},
         "e2e": {"value": value, "unit": "Gvis/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
 # ---------------------------------------------------------------- our arm
+
+def gpu_index_of(local):
+    vis_dev = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis_dev:
+        try:
+            return int(vis_dev.split(",")[local])
+        except (ValueError, IndexError):
+            return local
+    return local
+
+
+def measure_iteration(wl, sess, vis, w, stream, steps, warmup, ws=1, sample_clocks=None):
+    """Times `steps` batched LM iterations (restart + one iteration, graph
+    replay) over all intervals, then the fused launch alone with CUDA events.
+    Returns a dict with value, ms, roofline and the batch (kept open)."""
+    import torch
+    from paper_1709_08681_gb300 import _abi, dist as D, roofline as RL
+    n_ctx = len(sess.ctxs)
+    lm0 = np.zeros((wl.n_ant, 2))
+    w_scale = [1.0 if w is not None else 1.0 / wl.sigma_noise ** 2] * n_ctx
+    vk = [sess.vis_slice(vis, k) for k in range(n_ctx)]
+    wk = [sess.vis_slice(w, k) for k in range(n_ctx)] if w is not None else None
+    batch = _abi.Batch(sess.ctxs, vk, wk, w_scale=w_scale, stream=stream)
+    tiles = batch.psc_batch_autotune()
+    batch.psc_batch_begin([lm0] * n_ctx, _abi.psc_solve_opts_default())
+
+    def step():
+        batch.psc_batch_restart()
+        batch.psc_batch_iterate(1)
+
+    for _ in range(max(3, warmup)):
+        step()
+    stream.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler = sample_clocks() if sample_clocks else None
+    if sampler:
+        time.sleep(0.3)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    t_wall0 = time.time()
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_wall1 = time.time()
+    if ws > 1:
+        torch.distributed.barrier()
+    ms = D.max_over_ranks(e0.elapsed_time(e1), device="cuda")
+    # the fused kernel's own launch time: the same steps again, launched
+    # directly with CUDA events around each persistent fused launch
+    batch.psc_batch_profile(True)
+    for _ in range(max(3, min(steps, 20))):
+        step()
+    batch.psc_batch_profile(False)
+    kern_ms, kern_n = batch.psc_batch_profile_read()
+    clocks = None
+    if sampler:
+        time.sleep(0.2)
+        sampler.stop()
+        clocks = sampler.summary(t_wall0, t_wall1)
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    peak = RL.fp32_peak_tflops(props.multi_processor_count)
+    flops = RL.flops_per_eval(wl, wl.intervals, wl.n_bl)
+    flops_impl = RL.flops_per_eval(wl, wl.intervals, wl.n_bl, RL.FLOPS_PER_TAP_IMPL)
+    avg = kern_ms / max(kern_n, 1)
+    achieved = flops / (avg * 1e-3) / 1e12
+    kern = batch.psc_batch_kernel()
+    return {
+        "value": ws * wl.n_vis * steps / (ms * 1e-3) / 1e9, "ms_per_step": ms / steps, "tiling": tiles,
+        "clocks": clocks, "batch": batch, "vk": vk, "wk": wk, "w_scale": w_scale,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                     "traffic": profiled_traffic(wl.name),
+                     "kernel": kern + ", persistent over all intervals (fused degrid + derivatives + residual + sums)",
+                     "avg_launch_ms": avg, "flops_per_launch": flops, "flops_per_tap": RL.FLOPS_PER_TAP,
+                     "frac_at_implemented_flops": flops_impl / (avg * 1e-3) / 1e12 / peak,
+                     "implemented_flops_per_tap": RL.FLOPS_PER_TAP_IMPL,
+                     "peak_basis": "%d SMs x 128 FP32 lanes x 2 x 2070 MHz" % props.multi_processor_count},
+    }
+
+
+def measure_e2e(wl, sess, vis, w, w_scale, stream, k_steps):
+    """The same step through the public batch API with its inputs copied from
+    pinned host memory every step and the offsets plus chi^2 read back (a
+    synchronising call).  The copies run on a second stream into two
+    alternating device buffers (one batch per buffer over the same contexts):
+    step k+1's copy overlaps step k's evaluation, and an event keeps a buffer
+    from being overwritten before the step that reads it has finished.  The
+    resident input buffer serves as one of the two."""
+    import torch
+    from paper_1709_08681_gb300 import _abi, dist as D
+    n_ctx = len(sess.ctxs)
+    lm0 = np.zeros((wl.n_ant, 2))
+    opts = _abi.psc_solve_opts_default()
+    vis_h = torch.empty(vis.shape, dtype=vis.dtype, pin_memory=True)
+    vis_h.copy_(vis)
+    w_h = None
+    if w is not None:
+        w_h = torch.empty(w.shape, dtype=w.dtype, pin_memory=True)
+        w_h.copy_(w)
+    bufs = [(vis, w), (torch.empty_like(vis), torch.empty_like(w) if w is not None else None)]
+    batches = [_abi.Batch(sess.ctxs, [sess.vis_slice(vd, k) for k in range(n_ctx)],
+                          [sess.vis_slice(wd, k) for k in range(n_ctx)] if wd is not None else None,
+                          w_scale=w_scale, stream=stream) for vd, wd in bufs]
+    for b_ in batches:
+        b_.psc_batch_begin([lm0] * n_ctx, opts)
+    copy_stream = torch.cuda.Stream(device=vis.device)
+    ev_copied = [torch.cuda.Event() for _ in range(2)]
+    ev_done = [torch.cuda.Event() for _ in range(2)]
+
+    def issue_copy(slot):
+        with torch.cuda.stream(copy_stream):
+            copy_stream.wait_event(ev_done[slot])              # the step that last read this buffer is done
+            bufs[slot][0].copy_(vis_h, non_blocking=True)
+            if w_h is not None:
+                bufs[slot][1].copy_(w_h, non_blocking=True)
+            ev_copied[slot].record(copy_stream)
+
+    for slot, b_ in enumerate(batches):                        # untimed: graph capture of both batches
+        bufs[slot][0].copy_(vis)
+        if w is not None:
+            bufs[slot][1].copy_(w)
+        b_.psc_batch_restart()
+        b_.psc_batch_iterate(1)
+        b_.psc_batch_end()
+    d2h = 0
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    issue_copy(0)
+    for step_i in range(k_steps):
+        slot = step_i % 2
+        stream.wait_event(ev_copied[slot])
+        batches[slot].psc_batch_restart()
+        batches[slot].psc_batch_iterate(1)
+        ev_done[slot].record(stream)
+        if step_i + 1 < k_steps:
+            issue_copy(1 - slot)
+        lm_out, reps = batches[slot].psc_batch_end()           # synchronises; offsets + chi^2 to the host
+        d2h = sum(x.nbytes for x in lm_out) + 8 * 5 * len(reps)
+    dt = D.max_over_ranks(time.perf_counter() - t, device="cuda")
+    for b_ in batches:
+        b_.close()
+    del bufs
+    h2d = vis.numel() * 8 + (w.numel() * 4 if w is not None else 0)
+    return {"value": wl.n_vis * k_steps / dt / 1e9, "unit": "Gvis/s", "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "steps": k_steps,
+            "h2d_gb_per_s": h2d * k_steps / dt / 1e9}
+
+
+def setup_workload(wl, stream):
+    import torch
+    from paper_1709_08681_gb300.session import Session
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sess = Session(wl, stream=stream)
+    e1.record(stream)
+    stream.synchronize()
+    precompute_ms = e0.elapsed_time(e1)
+    vis = sess.simulate()
+    w = None
+    if wl.name not in SCALAR_WEIGHTS:
+        w = torch.full(vis.shape, 1.0 / wl.sigma_noise ** 2, dtype=torch.float32, device=vis.device)
+    stream.synchronize()
+    return sess, vis, w, precompute_ms
+
 
 def run_ours(args):
     import torch
@@ -231,285 +463,139 @@ def run_ours(args):
     if not torch.cuda.is_available():
         raise SystemExit("bench.py needs a CUDA device (the CUDA library is the only implementation)")
     torch.cuda.set_device(local)
-    from paper_1709_08681_gb300 import _abi, inputs as I
+    from paper_1709_08681_gb300 import _abi, dist as D, inputs as I
     from paper_1709_08681_gb300 import roofline as RL
-    from paper_1709_08681_gb300.session import Session
 
-    # weak scaling: every rank solves its own batch of four intervals (own seed)
-    from paper_1709_08681_gb300 import dist as D
+    # weak scaling: every rank solves its own copy of the workload (own seed)
     wl = I.make_workload(args.workload, seed=D.rank_seed(args.seed, rank))
     stream = torch.cuda.Stream()
+    gpu_index = gpu_index_of(local)
     with torch.cuda.stream(stream):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        sess = Session(wl, stream=stream)
-        e1.record(stream)
-        stream.synchronize()
-        precompute_ms = e0.elapsed_time(e1)
-        vis = sess.simulate()
-        w = torch.full(vis.shape, 1.0 / wl.sigma_noise ** 2, dtype=torch.float32, device=vis.device)
-        stream.synchronize()
-
-        lm0 = np.zeros((wl.n_ant, 2))
-        opts = _abi.psc_solve_opts_default()
-        vk = [sess.vis_slice(vis, k) for k in range(len(sess.ctxs))]
-        wk = [sess.vis_slice(w, k) for k in range(len(sess.ctxs))]
-        # all intervals in one batch: one persistent fused launch per iteration
-        batch = _abi.Batch(sess.ctxs, vk, wk, stream=stream)
-        tiles = batch.psc_batch_autotune()
-        batch.psc_batch_begin([lm0] * len(sess.ctxs), opts)
-
-        def step():
-            batch.psc_batch_restart()
-            batch.psc_batch_iterate(1)
-
-        for _ in range(max(3, args.warmup)):
-            step()
-        stream.synchronize()
-
-        gpu_index = local
-        vis_dev = os.environ.get("CUDA_VISIBLE_DEVICES")
-        if vis_dev:
-            try:
-                gpu_index = int(vis_dev.split(",")[local])
-            except ValueError:
-                gpu_index = local
-        sampler = ClockSampler(gpu_index)
-        time.sleep(0.3)
-        if ws > 1:
-            torch.distributed.barrier()
-        torch.cuda.synchronize()
-        t_wall0 = time.time()
-        e0.record(stream)
-        for _ in range(args.steps):
-            step()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        t_wall1 = time.time()
-        if ws > 1:
-            torch.distributed.barrier()
-        ms = e0.elapsed_time(e1)
-        # the fused kernel's own launch time: the same steps again, launched
-        # directly with CUDA events around each persistent fused launch
-        batch.psc_batch_profile(True)
-        k_prof = max(3, min(args.steps, 50))
-        for _ in range(k_prof):
-            step()
-        batch.psc_batch_profile(False)
-        kern_ms, kern_n = batch.psc_batch_profile_read()
-        time.sleep(0.2)
-        sampler.stop()
-        clocks = sampler.summary(t_wall0, t_wall1)
-        ms = D.max_over_ranks(ms, device="cuda")
-
-        n_vis = wl.n_vis
-        value = ws * n_vis * args.steps / (ms * 1e-3) / 1e9
-        # restart, persistent fused launch, per-baseline reduce, per-antenna
-        # assembly, LM update (the queue reset is a memset, not a kernel)
-        launches_per_step = 5
-
-        # roofline of the fused kernel (FP32 ALU bound); one launch = all intervals
-        taps = RL.taps_per_channel(wl)
-        flops_per_launch = 0.0
-        for (t0, nt) in wl.intervals:
-            flops_per_launch += nt * wl.n_bl * float(np.sum(taps)) * RL.FLOPS_PER_TAP
-        avg_launch_ms = kern_ms / max(kern_n, 1)
-        achieved = flops_per_launch / (avg_launch_ms * 1e-3) / 1e12
-        props = torch.cuda.get_device_properties(local)
-        n_sm = props.multi_processor_count
-        peak = RL.fp32_peak_tflops(n_sm)
-        fma_measured = _abi.psc_fp32_fma_rate(stream)
-
-        # materialised predict (V and the four derivative planes written to HBM):
-        # HBM-bound, 40 bytes written per visibility
-        vo = torch.empty((max(nt for _, nt in wl.intervals), wl.n_bl, wl.n_chan), dtype=torch.complex64,
-                         device=vis.device)
-        do = torch.empty((4,) + tuple(vo.shape), dtype=torch.complex64, device=vis.device)
-        pm_ms = 0.0
-        for k, ctx in enumerate(sess.ctxs):
-            nt_k = wl.intervals[k][1]
-            vv, dd = vo[:nt_k], do[:, :nt_k]
-            lm_k = 0.5 * wl.lm_true[k]
-            ctx.psc_predict(lm_k, vv, dd)                    # warm
-            e0.record(stream)
-            ctx.psc_predict(lm_k, vv, dd)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            pm_ms += e0.elapsed_time(e1)
-        del vo, do
-        hbm_peak = hbm_peak_gbs()
-        pm_gbs = 40.0 * wl.n_vis / (pm_ms * 1e-3) / 1e9
-        # same taps as the fused evaluation, so the FP32 ALU still binds; the
-        # HBM share of its 40 written bytes per visibility is reported beside it
-        pm_tflops = flops_per_launch / (pm_ms * 1e-3) / 1e12
-        predict_mat = {"gvis_per_s": wl.n_vis / (pm_ms * 1e-3) / 1e9, "ms": pm_ms,
-                       "roofline": {"bound": "alu", "achieved": pm_tflops, "peak": peak, "unit": "TFLOP/s",
-                                    "frac": pm_tflops / peak},
-                       "hbm": {"achieved_gbs": pm_gbs, "peak_gbs": hbm_peak, "frac": pm_gbs / hbm_peak,
-                               "bytes_per_vis": 40, "peak_source": "measured copy bandwidth"}}
-
-        # end to end: pinned host buffers; every step copies its inputs host->device
-        # and reads its offsets and chi^2 back (a synchronising call).  The copies
-        # run on a second stream into two alternating device buffers (one batch
-        # per buffer over the same contexts), so that step k+1's copy overlaps
-        # step k's evaluation; an event keeps a buffer from being overwritten
-        # before the step that reads it has finished.
-        vis_h = vis.cpu().pin_memory()
-        w_h = w.cpu().pin_memory()
-        n_ctx = len(sess.ctxs)
-        bufs = [(torch.empty_like(vis), torch.empty_like(w)) for _ in range(2)]
-        batches_e2e = [_abi.Batch(sess.ctxs, [sess.vis_slice(vd, k) for k in range(n_ctx)],
-                                  [sess.vis_slice(wd, k) for k in range(n_ctx)], stream=stream) for vd, wd in bufs]
-        for b_ in batches_e2e:
-            b_.psc_batch_begin([lm0] * n_ctx, opts)
-        copy_stream = torch.cuda.Stream(device=vis.device)
-        ev_copied = [torch.cuda.Event() for _ in range(2)]
-        ev_done = [torch.cuda.Event() for _ in range(2)]
-
-        def issue_copy(slot):
-            with torch.cuda.stream(copy_stream):
-                copy_stream.wait_event(ev_done[slot])          # the step that last read this buffer is done
-                bufs[slot][0].copy_(vis_h, non_blocking=True)
-                bufs[slot][1].copy_(w_h, non_blocking=True)
-                ev_copied[slot].record(copy_stream)
-
-        for slot, b_ in enumerate(batches_e2e):                # untimed: graph capture of both batches
-            bufs[slot][0].copy_(vis)
-            bufs[slot][1].copy_(w)
-            b_.psc_batch_restart()
-            b_.psc_batch_iterate(1)
-            b_.psc_batch_end()
-        k_e2e = max(3, min(args.steps, 50))
-        d2h = 0
-        torch.cuda.synchronize()
-        t = time.perf_counter()
-        issue_copy(0)
-        for step_i in range(k_e2e):
-            slot = step_i % 2
-            stream.wait_event(ev_copied[slot])
-            batches_e2e[slot].psc_batch_restart()
-            batches_e2e[slot].psc_batch_iterate(1)
-            ev_done[slot].record(stream)
-            if step_i + 1 < k_e2e:
-                issue_copy(1 - slot)
-            lm_out, reps = batches_e2e[slot].psc_batch_end()   # synchronises; offsets + chi^2 to the host
-            d2h = sum(x.nbytes for x in lm_out) + 8 * 5 * len(reps)
-        e2e_s = D.max_over_ranks(time.perf_counter() - t, device="cuda")
-        e2e_value = ws * n_vis * k_e2e / e2e_s / 1e9
-        h2d = vis.numel() * 8 + w.numel() * 4
-        for b_ in batches_e2e:
-            b_.close()
-        del bufs
-
-        # full solves (plain LM from zero) of the four intervals, batched
+        sess, vis, w, precompute_ms = setup_workload(wl, stream)
+        head = measure_iteration(wl, sess, vis, w, stream, args.steps, args.warmup, ws,
+                                 sample_clocks=lambda: ClockSampler(gpu_index))
+        # full batched solves (plain LM from zero) of every interval
         solve = None
         if rank == 0:
-            iters, errs = [], []
-            n_rep = 3
-            _abi.psc_solve_batch(sess.ctxs, vk, wk)              # warm
+            vk, wk = head["vk"], head["wk"]
+            _abi.psc_solve_batch(sess.ctxs, vk, wk, w_scale=head["w_scale"])       # warm
             torch.cuda.synchronize()
             t = time.perf_counter()
-            for _ in range(n_rep):
-                sols, reps = _abi.psc_solve_batch(sess.ctxs, vk, wk)
-                for k in range(len(sess.ctxs)):
-                    iters.append(reps[k].n_iter)
-                    errs.append(np.sqrt(np.mean((sols[k] - wl.lm_true[k]) ** 2)) / I.ARCSEC)
+            sols, reps = _abi.psc_solve_batch(sess.ctxs, vk, wk, w_scale=head["w_scale"])
             dt = time.perf_counter() - t
-            solve = {"intervals_per_s": n_rep * len(sess.ctxs) / dt, "mean_lm_iters": float(np.mean(iters)),
-                     "rms_err_arcsec": float(np.mean(errs)), "init": "zero (plain LM)", "batched": True}
-        batch.close()
+            errs = [np.sqrt(np.mean((sols[k] - wl.lm_true[k]) ** 2)) / I.ARCSEC for k in range(len(sess.ctxs))]
+            solve = {"intervals_per_s": len(sess.ctxs) / dt, "solve_s": dt,
+                     "mean_lm_iters": float(np.mean([r.n_iter for r in reps])),
+                     "rms_err_arcsec_median": float(np.median(errs)), "init": "zero (plain LM)", "batched": True}
+        head["batch"].close()
+        e2e = None
+        if not args.no_e2e:
+            need = wl.n_vis * 8 * 1.3 + (wl.n_vis * 4 if w is not None else 0) + (16 << 30)
+            if host_mem_available() >= need:
+                e2e = measure_e2e(wl, sess, vis, w, head["w_scale"], stream, max(3, min(args.steps, 10)))
+            else:
+                e2e = {"value": None, "unit": "Gvis/s", "skipped": "host memory below %.0f GB" % (need / 1e9)}
+        if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+            n_s, dt, n_t, n_c = oracle_sample(wl, args.cpu_seconds, args.seed)
+            rate = n_s / dt
+            cpu = {"value": rate / 1e9, "unit": "Gvis/s", "cores": omp_threads(), "kind": "oracle",
+                   "sample": "interval 0, first %d time steps x %d baselines x %d channels spread over the band "
+                             "(%d visibilities, %.1f s): FP64 predict + derivatives + chi^2/gradient/normal sums "
+                             "at zero offsets" % (n_t, wl.n_bl, n_c, n_s, dt),
+                   "extrapolated": True,
+                   "step_s_extrapolated": wl.n_vis / rate,
+                   "extrapolation": "linear in visibilities (the oracle's cost per visibility is fixed: the full "
+                                    "S x S window)"}
+        else:
+            cpu = None
+        sess.close()
+        del vis, w
+        torch.cuda.empty_cache()
 
     line = {
-        "metric": METRIC, "value": value, "unit": "Gvis/s", "n_gpus": ws, "steps": args.steps,
-        "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "metric": METRIC, "value": head["value"], "unit": "Gvis/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": head["ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": args.workload, "n_ant": wl.n_ant, "n_bl": wl.n_bl, "n_time": wl.n_time,
-                   "n_chan": wl.n_chan, "n_interval": len(wl.intervals), "n_vis": n_vis,
-                   "image": wl.image.shape[0], "grid": wl.n_grid, "support": wl.support,
-                   "oversample": wl.oversample, "aperture": wl.ap_kind,
-                   "l2": "inputs larger than L2 (vis 108 MB + weights 54 MB + grid 32 MB per step)",
-                   "step": "one LM iteration of all intervals (one persistent fused launch, graph replay)",
-                   "tiling": [list(t) for t in tiles], "precompute_ms": precompute_ms},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": profiled_traffic() if args.workload == "vla27_l64ch" else None,
-                     "kernel": "eval_kernel<false>, persistent over all intervals (fused degrid + derivatives + residual + sums)",
-                     "avg_launch_ms": avg_launch_ms, "flops_per_launch": flops_per_launch,
-                     "peak_basis": "%d SMs x 128 FP32 lanes x 2 x 2070 MHz" % n_sm,
-                     "fp32_fma_measured_tflops": fma_measured, "frac_of_measured_fma": achieved / fma_measured},
-        "predict_materialised": predict_mat,
-        "e2e": {"value": e2e_value, "unit": "Gvis/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
-        "clocks": clocks,
-        "gpu_launches": launches_per_step * args.steps,
+        "config": config_for(wl),
+        "roofline": head["roofline"],
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+        "clocks": head["clocks"],
+        # restart, persistent fused launch, per-baseline reduce, per-antenna
+        # assembly, LM update per step (the queue reset is a memset)
+        "gpu_launches": 5 * args.steps,
+        "tiling": [list(t) for t in head["tiling"][:1]],
+        "precompute_ms": precompute_ms,
     }
+    if line["cpu_baseline"] is None:
+        del line["cpu_baseline"]
     if solve:
         line["solve"] = solve
-    if rank == 0 and not args.no_learned:
+    if rank == 0 and not args.no_secondary:
+        secondary(args, line, local)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def secondary(args, line, local):
+    import torch
+    from paper_1709_08681_gb300 import inputs as I, roofline as RL
+    stream = torch.cuda.Stream()
+    props = torch.cuda.get_device_properties(local)
+    peak = RL.fp32_peak_tflops(props.multi_processor_count)
+    with torch.cuda.stream(stream):
+        # the precision-study workload, measured the same way as the headline
+        if args.workload != "vla27_l64ch":
+            wl = I.make_workload("vla27_l64ch", seed=args.seed)
+            sess, vis, w, pre = setup_workload(wl, stream)
+            r = measure_iteration(wl, sess, vis, w, stream, 50, 5)
+            r["batch"].close()
+            line["vla27_l64ch"] = {"value": r["value"], "unit": "Gvis/s", "ms_per_step": r["ms_per_step"],
+                                   "n_vis": int(wl.n_vis), "roofline": r["roofline"],
+                                   "tiling": [list(t) for t in r["tiling"][:1]]}
+            sess.close()
+            del vis, w
+        # solves/s of the small plain-method workload: 64 draws of offsets and
+        # noise on its geometry and sky, batched and one at a time
+        from paper_1709_08681_gb300 import solves as SV
+        line["vla27_l1ch"] = SV.run("vla27_l1ch", n_draws=64, seed=args.seed, stream=stream)
+    if not args.no_learned:
         # solves/s to 1 arcsec RMS, learned initial estimate vs plain LM, on the
         # 64-antenna 16-channel workload (network trained here on GPU-simulated
-        # intervals with the library's kernels; sizes reduced to fit the bench)
+        # intervals with the library's kernels)
         from paper_1709_08681_gb300 import learned_init as LI
-        rep, _ = LI.run(n_train=args.learned_train, n_eval=args.learned_eval, steps=3000, batch=1024, n_geom=8,
-                        seed=args.seed, log=None, n_eval_batched=64)
+        rep, _ = LI.run(n_train=3000, n_eval=20, steps=3000, batch=1024, n_geom=8, seed=args.seed, log=None,
+                        n_eval_batched=64)
         line["learned_init"] = {"workload": "disk64_l16ch", **rep}
-    if rank == 0 and args.mixed_intervals > 0:
-        # batched solves over mixed intervals: 27/64/197-antenna arrays,
-        # 30-600 time steps, offsets 10-60" with 2' outliers (one persistent
-        # launch per LM iteration over all intervals, graph-replayed)
+    if args.mixed_intervals > 0:
         from paper_1709_08681_gb300 import mixed as MX
         mrep, _ = MX.run(n_intervals=args.mixed_intervals, seed=args.seed)
         mrep.pop("tiling", None)
-        props = torch.cuda.get_device_properties(local)
-        mrep["roofline"] = {"bound": "alu", "achieved": mrep["fused_tflops"],
-                            "peak": RL.fp32_peak_tflops(props.multi_processor_count), "unit": "TFLOP/s"}
-        mrep["roofline"]["frac"] = mrep["roofline"]["achieved"] / mrep["roofline"]["peak"]
+        mrep["roofline"] = {"bound": "alu", "achieved": mrep["fused_tflops"], "peak": peak, "unit": "TFLOP/s",
+                            "frac": mrep["fused_tflops"] / peak}
         line["mixed_batch"] = {"workload": "mixed_batch%d" % args.mixed_intervals, **mrep}
-    if rank == 0:
-        # two parallel-hand polarisations solved separately: squint and
-        # mechanical offsets of every antenna (4 intervals x 2 polarisations, one batch)
+    if not args.no_squint:
         from paper_1709_08681_gb300 import squint as SQ
         srep, _, _ = SQ.run("vla27_l64ch", seed=args.seed)
         line["squint"] = {"workload": "vla27_l64ch, R and L", **srep}
-    if rank == 0 and not args.no_exact:
-        # the exact disk kernel (two shifted disk patterns' product) in place of
-        # the Gaussian decorrelation model: throughput of its fused evaluation
-        # and its solutions against the Gaussian model's, on data it simulates
+    if not args.no_exact:
         from paper_1709_08681_gb300 import exact_kernel as EK
         line["exact_kernel"] = {"workload": "vla27_l64ch, offsets sigma 60\"", **EK.run("vla27_l64ch", seed=args.seed)}
-    if rank == 0 and not args.no_wsnap:
-        # W-snapshots: per-interval uvw plane, model components moved to the
-        # snapshot frame, their grid on the tensor cores, then the usual batch
+    if not args.no_wsnap:
         from paper_1709_08681_gb300 import wsnap as WS
         line["wsnap"] = {"workload": "vla27_l64ch, W-snapshot grid per interval", **WS.run("vla27_l64ch", seed=args.seed)}
-    if rank == 0 and not args.no_wstack:
-        # residual-w stack: all 600 time steps as one interval, the model grid
-        # stacked in the w left after the plane fit, two planes read per tap
+    if not args.no_wstack:
         from paper_1709_08681_gb300 import wstack as WK
         line["wstack"] = {"workload": "vla27_l64ch, 600 time steps as one interval", **WK.run("vla27_l64ch", seed=args.seed)}
-    if rank == 0 and not args.no_drift:
-        # full scale: 197 antennas, 128 channels, 1800 x 1 s (4.45e9 visibilities),
-        # pointing drifting as a random walk, solved every 60 s (30 intervals):
-        # cold batched solves vs warm-started solves in time order
-        from paper_1709_08681_gb300 import drift as DR
-        drep = DR.run(seed=args.seed)
-        props = torch.cuda.get_device_properties(local)
-        drep["roofline"] = {"bound": "alu", "achieved": drep["fused_tflops"],
-                            "peak": RL.fp32_peak_tflops(props.multi_processor_count), "unit": "TFLOP/s"}
-        drep["roofline"]["frac"] = drep["roofline"]["achieved"] / drep["roofline"]["peak"]
-        drep["warm_latency_ms_per_interval"] = 1e3 * drep["warm_sequential_s"] / drep["n_intervals"]
-        line["drift_full"] = {"workload": "drift197_l128ch", **drep}
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        vis_host = vis.cpu().numpy()
-        w_host = w.cpu().numpy()
-        n_s, dt, n_t, _ = cpu_sample_oracle(wl, vis_host, w_host, args.cpu_seconds)
-        line["cpu_baseline"] = {"value": n_s / dt / 1e9, "unit": "Gvis/s", "cores": omp_threads(), "kind": "oracle",
-                                "sample": "first %d timesteps x %d baselines x %d channels (%d vis, %.1f s): FP64 "
-                                          "predict + derivatives + chi^2/gradient/normal sums at zero offsets"
-                                          % (n_t, wl.n_bl, wl.n_chan, n_s, dt)}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-    sess.close()
-    if ws > 1:
-        torch.distributed.destroy_process_group()
+    # drifting pointing: cold batched solves against warm-started solves in time order
+    from paper_1709_08681_gb300 import drift as DR
+    drep = DR.run(seed=args.seed)
+    drep["roofline"] = {"bound": "alu", "achieved": drep["fused_tflops"], "peak": peak, "unit": "TFLOP/s",
+                        "frac": drep["fused_tflops"] / peak}
+    drep["warm_latency_ms_per_interval"] = 1e3 * drep["warm_sequential_s"] / drep["n_intervals"]
+    line["drift_full"] = {"workload": "drift197_l128ch", **drep}
 
 
 def main():

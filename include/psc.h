@@ -326,6 +326,41 @@ psc_status psc_set_tiling(psc_ctx *ctx, int t_tile, int c_group, int vis_per_thr
  * channels (fewer time steps per channel than items / 7). */
 psc_status psc_set_flat_tiling(psc_ctx *ctx, int items, int vis_per_thread);
 
+/* Track kernel (Alg. 1's inner loop, Eqs. AIJPOINTING, DAIJPOINTING, Chisq,
+ * DCHIDD; the same arithmetic as the brick kernel, for small apertures of a
+ * few to a few tens of taps per visibility).  vis_per_lane in {1, 2} makes
+ * every later reduce-mode evaluation of ctx (psc_residual_grad, the solver,
+ * batches) run one warp per (baseline, 32 x vis_per_lane consecutive time
+ * steps) that loops over all channels; each channel's grid box (the cells
+ * within the aperture of the warp's visibilities, at most 32 cells wide and
+ * 512 cells in all) and A° table are copied into shared memory by TMA
+ * (cp.async.bulk.tensor) one channel ahead, and the cell half of the phase
+ * ramp is applied there.  Boxes beyond that size read the grid from global
+ * memory instead.  chi^2 and the gradient are summed with compensated FP32
+ * (TwoSum) per lane and across the warp, then in FP64.  Predictions
+ * (psc_predict) keep the brick kernel.  0 switches back to the brick kernel;
+ * so do psc_set_tiling, psc_set_flat_tiling, psc_set_kernel_model,
+ * psc_set_grid_precision(PSC_GRID_BF16) and psc_set_wstack.  The first call
+ * with vis_per_lane > 0 builds the tensor maps of the grid and per-channel
+ * tables (a few KB; synchronises the stream).  Errors: PSC_ERR_ARG when the
+ * context uses the exact kernel, a residual-w stack or the BF16 grid copy, a
+ * grid not 16-byte aligned, an aperture reaching outside the S x S window,
+ * or (vis_per_lane 2) consecutive time steps more than 4 cells apart.
+ * Results equal the brick kernel's up to FP32 summation order. */
+psc_status psc_set_track_tiling(psc_ctx *ctx, int vis_per_lane);
+
+/* Polls of one bounded mbarrier wait in the library's kernels (the TMA and
+ * tensor-core pipelines of the track kernel, the model-grid DFT and the
+ * network).  A wait that runs out makes the kernel record a flag, wait with a
+ * fixed larger bound for its own copies and MMAs still in flight, release its
+ * tensor memory and return; the next synchronising call on the object
+ * reports PSC_ERR_TIMEOUT and the object stays usable.  0 restores the default
+ * (2^24 polls, far beyond any wait that completes).  A tiny limit is for
+ * testing that error path.  psc_get_wait_limit returns the current value.
+ * Errors: PSC_ERR_ARG for polls < 0. */
+psc_status psc_set_wait_limit(long long polls);
+long long psc_get_wait_limit(void);
+
 /* Measured FP32 FMA throughput of the current device (TFLOP/s, an FMA counted
  * as 2 flops): eight independent FMA chains per thread on 8 blocks of 256
  * threads per SM, timed with CUDA events.  A check of the FP32 peak that the
@@ -473,6 +508,11 @@ psc_status psc_batch_create(psc_batch **out, psc_ctx *const *ctxs, int n_ctx, co
 void psc_batch_destroy(psc_batch *b);
 const char *psc_batch_last_error(const psc_batch *b);
 
+/* Name of the fused kernel that the batch's persistent launch runs
+ * ("eval_kernel<...>" for brick tilings, "track_kernel<kv>" when every
+ * context has the track tiling).  Static storage; never NULL. */
+const char *psc_batch_kernel(const psc_batch *b);
+
 /* Picks each context's launch shape by timing the fused kernel on its own
  * data: for blocks of 128 and 256 threads and vis_per_thread 1 and (where
  * psc_set_tiling accepts it) 2, the three channel groups whose smallest
@@ -483,10 +523,15 @@ const char *psc_batch_last_error(const psc_batch *b);
  * block size serves the persistent launch); the winner is also timed with
  * PSC_STAGE_NEVER and the faster grid access kept.  Contexts of the same
  * array, channels and grid reuse the first one's choice, with the time tile
- * refitted to their own length (flat bricks need no refit).  Writes the chosen
- * (t_tile, c_group, vis_per_thread, staging mode) of context k to
- * tiling_out[4k..4k+3] (NULL to skip); flat bricks are written as (items, 0,
- * vis_per_thread, staging mode).  Synchronises. */
+ * refitted to their own length (flat bricks need no refit).  Each
+ * representative is also timed with the track kernel (psc_set_track_tiling,
+ * 1 and 2 visibilities per lane, where allowed); if the track kernel's total
+ * over the batch (each representative weighted by the time steps of the
+ * contexts that reuse it) beats the brick kernel's, every context takes the
+ * faster track tiling.  Writes the chosen (t_tile, c_group, vis_per_thread,
+ * staging mode) of context k to tiling_out[4k..4k+3] (NULL to skip); flat
+ * bricks are written as (items, 0, vis_per_thread, staging mode) and the
+ * track tiling as (-1, 0, vis_per_lane, PSC_STAGE_AUTO).  Synchronises. */
 psc_status psc_batch_autotune(psc_batch *b, int *tiling_out);
 
 /* Start (host offsets, options as for psc_lm_begin), restart on the device,

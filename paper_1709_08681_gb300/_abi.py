@@ -31,9 +31,10 @@ EXPORTS = ("psc_solve_opts_default", "psc_model_grid", "psc_model_grid_component
            "psc_set_wstack", "psc_create", "psc_destroy", "psc_last_error",
            "psc_predict", "psc_residual_grad", "psc_solve_offsets", "psc_lm_begin", "psc_lm_iterate",
            "psc_lm_end", "psc_lm_restart", "psc_set_tiling", "psc_set_grid_precision", "psc_set_staging",
-           "psc_set_kernel_model", "psc_set_flat_tiling", "psc_set_brick_order", "psc_fp32_fma_rate", "psc_profile", "psc_profile_read",
+           "psc_set_kernel_model", "psc_set_flat_tiling", "psc_set_track_tiling", "psc_set_wait_limit",
+           "psc_get_wait_limit", "psc_set_brick_order", "psc_fp32_fma_rate", "psc_profile", "psc_profile_read",
            "psc_residual_grad_noalloc", "psc_batch_create", "psc_batch_destroy", "psc_batch_last_error",
-           "psc_batch_autotune", "psc_batch_begin", "psc_batch_restart", "psc_batch_iterate", "psc_batch_end",
+           "psc_batch_autotune", "psc_batch_begin", "psc_batch_restart", "psc_batch_kernel", "psc_batch_iterate", "psc_batch_end",
            "psc_solve_batch", "psc_batch_profile", "psc_batch_profile_read", "psc_features",
            "psc_mlp_n_params", "psc_mlp_create", "psc_mlp_destroy", "psc_mlp_set_params", "psc_mlp_get_params",
            "psc_mlp_forward", "psc_mlp_grad", "psc_mlp_train_step", "psc_mlp_infer_offsets", "psc_learned_init")
@@ -131,6 +132,10 @@ def lib():
             "psc_batch_autotune": (ctypes.c_int, [_V, ctypes.POINTER(ctypes.c_int)]),
             "psc_batch_begin": (ctypes.c_int, [_V, _D, ctypes.POINTER(psc_solve_opts)]),
             "psc_batch_restart": (ctypes.c_int, [_V]),
+            "psc_batch_kernel": (ctypes.c_char_p, [_V]),
+            "psc_set_track_tiling": (ctypes.c_int, [_V, ctypes.c_int]),
+            "psc_set_wait_limit": (ctypes.c_int, [ctypes.c_longlong]),
+            "psc_get_wait_limit": (ctypes.c_longlong, []),
             "psc_batch_iterate": (ctypes.c_int, [_V, ctypes.c_int]),
             "psc_batch_end": (ctypes.c_int, [_V, _D, ctypes.POINTER(psc_solve_report)]),
             "psc_mlp_n_params": (ctypes.c_int, []),
@@ -183,6 +188,15 @@ def _stream(stream):
     if isinstance(stream, int):
         return stream
     return stream.cuda_stream
+
+
+def psc_set_wait_limit(polls):
+    """Polls of one bounded mbarrier wait in the library's kernels (0: default)."""
+    _check(lib().psc_set_wait_limit(int(polls)))
+
+
+def psc_get_wait_limit():
+    return int(lib().psc_get_wait_limit())
 
 
 def psc_solve_opts_default() -> psc_solve_opts:
@@ -331,6 +345,9 @@ class Context:
     def psc_set_flat_tiling(self, items, vis_per_thread):
         _check(lib().psc_set_flat_tiling(self.h, int(items), int(vis_per_thread)), self.h)
 
+    def psc_set_track_tiling(self, vis_per_lane):
+        _check(lib().psc_set_track_tiling(self.h, int(vis_per_lane)), self.h)
+
     def psc_set_kernel_model(self, model):
         _check(lib().psc_set_kernel_model(self.h, int(model)), self.h)
 
@@ -470,6 +487,10 @@ class Batch:
         self._lm0 = self._concat(lm0_list)
         _bcheck(lib().psc_batch_begin(self.h, _dp(self._lm0), ctypes.byref(opts) if opts is not None else None),
                 self.h)
+
+    def psc_batch_kernel(self):
+        """Name of the fused kernel the batch's persistent launch runs."""
+        return lib().psc_batch_kernel(self.h).decode()
 
     def psc_batch_restart(self):
         _bcheck(lib().psc_batch_restart(self.h), self.h)

@@ -49,6 +49,11 @@ struct psc_ctx {
     int kv = 1;                  // visibilities per thread at consecutive times
     int flat = 0;                // > 0: bricks of `flat` consecutive (channel, time-group) items
     int no_stage = 0;            // PSC_STAGE_NEVER: taps read the grid from global memory
+    int trk_kv = 0;              // > 0: reduce-mode evaluations run the track kernel, trk_kv visibilities per lane
+    float2 *d_tabcs = nullptr;   // track kernel: per-channel (intercept, slope) tables [nc][trk_stride]
+    int trk_stride = 0;
+    void *d_tmap = nullptr;      // track kernel: tensor maps over the grid (3 x 128 bytes)
+    int *d_err = nullptr;        // set by a kernel whose bounded wait ran out
     int kernel_model = PSC_KERNEL_GAUSS;
     int brick_order = PSC_ORDER_BASELINE;
     int *d_bl_order = nullptr;   // baselines in Morton order of their mid-interval (u, v)
@@ -79,6 +84,9 @@ struct psc_ctx {
 namespace {
 
 thread_local std::string g_err;
+// polls of one bounded mbarrier wait in the library's kernels (psc_set_wait_limit)
+constexpr long long kDefaultWaitPolls = 1LL << 24;
+long long g_wait_polls = kDefaultWaitPolls;
 
 psc_status fail(psc_ctx *ctx, psc_status st, const std::string &msg) {
     if (ctx) ctx->err = msg;
@@ -87,6 +95,8 @@ psc_status fail(psc_ctx *ctx, psc_status st, const std::string &msg) {
 }
 
 }  // namespace
+
+long long psc::wait_limit() { return g_wait_polls; }
 
 psc_status psc::set_global_error(psc_status st, const char *msg) {
     g_err = msg;
@@ -116,6 +126,9 @@ void free_ctx(psc_ctx *c) {
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     cudaFree(c->d_grid_bf16);
     cudaFree(c->d_kmom);
+    cudaFree(c->d_tabcs);
+    cudaFree(c->d_tmap);
+    cudaFree(c->d_err);
     cudaFree(c->d_bl_order);
     cudaFree(c->d_uvs);
     cudaFree(c->d_spart);
@@ -149,10 +162,15 @@ int tab_stride(const psc_ctx *c, int kv) {
     return c->max_tab_len + (int)std::ceil(c->gd.oversample * (kv_spread(c, kv) + 1.0)) + 2;
 }
 int n_cg(const psc_ctx *c) { return (c->nc + c->c_group - 1) / c->c_group; }
+// Track kernel: time chunks of 32 lanes x trk_kv steps per baseline, and the
+// staged tile capacity of one buffer (cells).
+int trk_chunks(const psc_ctx *c) { return (c->nt + 32 * c->trk_kv - 1) / (32 * c->trk_kv); }
+constexpr int kTrkCap = 512;
 // Flat bricks: groups of kv consecutive time steps per channel, the bricks
 // per baseline, and the most channels one brick's items can span.
 int n_tp(const psc_ctx *c) { return (c->nt + c->kv - 1) / c->kv; }
 long long bricks_per_bl(const psc_ctx *c) {
+    if (c->trk_kv > 0) return trk_chunks(c);
     if (c->flat > 0) return ((long long)c->nc * n_tp(c) + c->flat - 1) / c->flat;
     return (long long)n_cg(c) * n_tt(c);
 }
@@ -160,7 +178,10 @@ int ch_span(const psc_ctx *c) {
     return c->flat > 0 ? std::min(c->nc, (c->flat + n_tp(c) - 2) / n_tp(c) + 1) : c->c_group;
 }
 // Block width of the fused kernel for this context's bricks.
-int eval_threads(const psc_ctx *c) { return ((c->flat > 0 ? c->flat : c->t_tile * c->c_group) + 31) / 32 * 32; }
+int eval_threads(const psc_ctx *c) {
+    if (c->trk_kv > 0) return kTrkThreads;
+    return ((c->flat > 0 ? c->flat : c->t_tile * c->c_group) + 31) / 32 * 32;
+}
 
 psc_status ensure_partials(psc_ctx *c) {
     const size_t need = (size_t)c->n_bl * bricks_per_bl(c);
@@ -209,6 +230,17 @@ EvalArgs eval_args(const psc_ctx *c, const double *lm_dev) {
     a.exact = c->kernel_model == PSC_KERNEL_EXACT_DISK;
     a.bl_order = c->brick_order == PSC_ORDER_UV ? c->d_bl_order : nullptr;
     a.kmom = c->d_kmom;
+    a.err = c->d_err;
+    a.wait_limit = wait_limit();
+    if (c->trk_kv > 0) {
+        a.trk_kv = c->trk_kv;
+        a.trk_chunks = trk_chunks(c);
+        a.trk_cap = kTrkCap;
+        a.trk_stride = c->trk_stride;
+        a.trk_pad = tab_stride(c, c->trk_kv) - c->max_tab_len;
+        a.tabs_cs = c->d_tabcs;
+        a.tmap = c->d_tmap;
+    }
     if (c->wp_n > 0) {
         a.grid = c->wp_grid;
         a.grid_bf16 = nullptr;
@@ -276,7 +308,7 @@ psc_status eval_reduce(psc_ctx *c, const double *lm_dev, const void *vis_obs, co
         }
         PSC_CUDA(c, cudaEventRecord(c->ev_pool[c->ev_used], c->stream));
     }
-    PSC_CUDA(c, launch_eval(a, false, c->stream));
+    PSC_CUDA(c, a.trk_kv > 0 ? launch_track(a, c->stream) : launch_eval(a, false, c->stream));
     if (c->prof) {
         PSC_CUDA(c, cudaEventRecord(c->ev_pool[c->ev_used + 1], c->stream));
         c->ev_used += 2;
@@ -285,9 +317,63 @@ psc_status eval_reduce(psc_ctx *c, const double *lm_dev, const void *vis_obs, co
     return PSC_OK;
 }
 
+// Track kernel set-up of a context: the per-channel (intercept, slope)
+// tables and the grid's tensor maps, once.
+psc_status trk_prepare(psc_ctx *c) {
+    if (c->d_tmap) return PSC_OK;
+    const int stride = (std::max(tab_stride(c, 1), kv_allowed(c, 2) ? tab_stride(c, 2) : 0) + 1) & ~1;
+    cudaError_t e = dalloc(&c->d_tabcs, (size_t)c->nc * stride);
+    if (e == cudaSuccess) e = launch_track_tables(c->d_chan, c->d_tabs, c->nc, stride, c->d_tabcs, c->stream);
+    void *maps = nullptr;
+    if (e == cudaSuccess) e = cudaMalloc(&maps, 3 * 128);
+    if (e == cudaSuccess) e = make_grid_maps(c->grid, c->gd.n_grid, maps, c->stream);
+    if (e != cudaSuccess) {
+        cudaFree(maps);
+        cudaFree(c->d_tabcs);
+        c->d_tabcs = nullptr;
+        return cuda_fail(c, e, "track kernel set-up");
+    }
+    c->trk_stride = stride;
+    c->d_tmap = maps;
+    return PSC_OK;
+}
+
+// Why the track kernel cannot serve this context with kv visibilities per
+// lane (empty: it can).
+std::string trk_refusal(const psc_ctx *c, int kv) {
+    if (kv != 1 && kv != 2) return "vis_per_lane must be 1 or 2";
+    if (c->kernel_model != PSC_KERNEL_GAUSS) return "the track kernel uses the Gaussian kernel model";
+    if (c->wp_n > 0) return "the track kernel does not read a residual-w stack";
+    if (c->d_grid_bf16) return "the track kernel reads the FP32 grid";
+    if ((uintptr_t)c->grid % 16) return "the track kernel needs a 16-byte aligned grid";
+    if (!c->multi_ok) return "the track kernel needs every channel's aperture inside the S x S window";
+    if (!kv_allowed(c, kv)) return "vis_per_lane 2 needs consecutive time steps within 4 cells";
+    return "";
+}
+
+// The evaluation's bounded waits ran out (a kernel set *d_err): clears the flag.
+psc_status check_err_flag(psc_ctx *c) {
+    int h = 0;
+    PSC_CUDA(c, cudaMemcpyAsync(&h, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    PSC_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (h) {
+        PSC_CUDA(c, cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
+        return fail(c, PSC_ERR_TIMEOUT, "a bounded wait of the fused evaluation ran out; its results were discarded");
+    }
+    return PSC_OK;
+}
+
 }  // namespace
 
 extern "C" {
+
+psc_status psc_set_wait_limit(long long polls) {
+    if (polls < 0) return fail(nullptr, PSC_ERR_ARG, "polls must be >= 0");
+    g_wait_polls = polls == 0 ? kDefaultWaitPolls : polls;
+    return PSC_OK;
+}
+
+long long psc_get_wait_limit(void) { return g_wait_polls; }
 
 void psc_solve_opts_default(psc_solve_opts *o) {
     if (!o) return;
@@ -559,6 +645,8 @@ psc_status psc_create(psc_ctx **out, const psc_obs *obs, const psc_aperture *ap,
     if (e == cudaSuccess) e = dalloc(&c->d_state, 1);
     if (e == cudaSuccess) e = dalloc(&c->d_state0, 1);
     if (e == cudaSuccess) e = dalloc(&c->d_lm0, n2);
+    if (e == cudaSuccess) e = dalloc(&c->d_err, 1);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);
     if (e == cudaSuccess) e = dalloc(&d_freq, c->nc);
     if (e == cudaSuccess) e = dalloc(&d_off, c->nc);
     if (e == cudaSuccess) e = dalloc(&d_len, c->nc);
@@ -654,6 +742,7 @@ psc_status psc_set_tiling(psc_ctx *ctx, int t_tile, int c_group, int vis_per_thr
     ctx->c_group = cg;
     ctx->kv = kv;
     ctx->flat = 0;
+    ctx->trk_kv = 0;
     return PSC_OK;
 }
 
@@ -674,6 +763,21 @@ psc_status psc_set_flat_tiling(psc_ctx *ctx, int items, int vis_per_thread) {
         ctx->flat = old_flat;
         return fail(ctx, PSC_ERR_ARG, "a brick would span more than 8 channels (too few time steps per channel)");
     }
+    ctx->trk_kv = 0;
+    return PSC_OK;
+}
+
+psc_status psc_set_track_tiling(psc_ctx *ctx, int vis_per_lane) {
+    if (!ctx) return fail(nullptr, PSC_ERR_ARG, "ctx is NULL");
+    if (vis_per_lane == 0) {
+        ctx->trk_kv = 0;
+        return PSC_OK;
+    }
+    const std::string why = trk_refusal(ctx, vis_per_lane);
+    if (!why.empty()) return fail(ctx, PSC_ERR_ARG, why);
+    psc_status st = trk_prepare(ctx);
+    if (st != PSC_OK) return st;
+    ctx->trk_kv = vis_per_lane;
     return PSC_OK;
 }
 
@@ -719,6 +823,7 @@ psc_status psc_set_kernel_model(psc_ctx *ctx, int model) {
     ctx->kernel_model = model;
     ctx->kv = 1;
     ctx->flat = 0;
+    ctx->trk_kv = 0;
     return PSC_OK;
 }
 
@@ -747,6 +852,7 @@ psc_status psc_set_grid_precision(psc_ctx *ctx, int precision) {
     if (precision != PSC_GRID_BF16) return fail(ctx, PSC_ERR_ARG, "precision must be PSC_GRID_F32 or PSC_GRID_BF16");
     if (ctx->wp_n > 0) return fail(ctx, PSC_ERR_ARG, "a residual-w stack is read in FP32 only");
     const size_t n = (size_t)ctx->gd.n_grid * ctx->gd.n_grid;
+    ctx->trk_kv = 0;                                  // the track kernel reads the FP32 grid
     if (!ctx->d_grid_bf16) PSC_CUDA(ctx, dalloc(&ctx->d_grid_bf16, n));
     PSC_CUDA(ctx, launch_grid_to_bf16(ctx->grid, n, ctx->d_grid_bf16, ctx->stream));
     PSC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
@@ -781,6 +887,7 @@ psc_status psc_set_wstack(psc_ctx *ctx, const void *grids, int n_planes, double 
     }
     ctx->wp_grid = (const float2 *)grids;
     ctx->wp_n = n_planes;
+    ctx->trk_kv = 0;                                  // stacks run the brick kernel
     ctx->wp_w0 = w0;
     ctx->wp_dw = dw;
     ctx->wp_a = a;
@@ -792,7 +899,10 @@ psc_status psc_predict(psc_ctx *ctx, const double *lm, void *vis_out, void *dvis
     if (!ctx) return fail(nullptr, PSC_ERR_ARG, "ctx is NULL");
     if (!lm || !vis_out) return fail(ctx, PSC_ERR_ARG, "lm and vis_out must be non-NULL");
     PSC_CUDA(ctx, cudaMemcpyAsync(ctx->d_lm_trial, lm, sizeof(double) * 2 * ctx->n_ant, cudaMemcpyHostToDevice, ctx->stream));
+    const int trk = ctx->trk_kv;                  // predictions always run the brick kernel
+    ctx->trk_kv = 0;
     EvalArgs a = eval_args(ctx, ctx->d_lm_trial);
+    ctx->trk_kv = trk;
     a.vis_out = (float2 *)vis_out;
     a.dvis_out = (float2 *)dvis_out;
     PSC_CUDA(ctx, launch_eval(a, true, ctx->stream));
@@ -811,6 +921,8 @@ psc_status psc_residual_grad(psc_ctx *ctx, const double *lm, const void *vis_obs
     const size_t evn = ev_len(ctx->n_ant, ctx->n_bl);
     PSC_CUDA(ctx, cudaMemcpyAsync(ctx->h_ev.data(), ctx->d_ev, sizeof(double) * evn, cudaMemcpyDeviceToHost, ctx->stream));
     PSC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    st = check_err_flag(ctx);
+    if (st != PSC_OK) return st;
     const int n = ctx->n_ant;
     *chi2 = ctx->h_ev[0];
     std::memcpy(grad, ctx->h_ev.data() + 1, sizeof(double) * 2 * n);
@@ -868,6 +980,8 @@ psc_status lm_fetch(psc_ctx *ctx, double *lm_out, psc_solve_report *rep, cudaStr
         rep->chi2 = ctx->h_state.chi2;
         rep->lam = ctx->h_state.lam;
     }
+    psc_status st = check_err_flag(ctx);
+    if (st != PSC_OK) return st;
     if (ctx->h_state.done && ctx->h_state.reason == PSC_STOP_NUMERIC)
         return fail(ctx, PSC_ERR_NUMERIC, "solver stopped on a non-finite chi^2 or step");
     return PSC_OK;
@@ -1051,6 +1165,8 @@ struct psc_batch {
     int grid = 0;
     int threads = 128;           // fused-kernel block size: the widest context's shape
     bool stacked = false;        // every context reads a residual-w stack (else none does)
+    int track = 0;               // > 0: the persistent launch runs the track kernel, this many visibilities per lane
+    int trk_tabc = 0;            // track kernel: table capacity of a warp buffer (entries)
     size_t eval_dyn = 0, lm_dyn = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -1127,10 +1243,30 @@ psc_status build_tables(psc_batch *b) {
     b->threads = threads;
     b->eval_dyn = dyn;
     b->lm_dyn = lmd;
-    PSC_BCUDA(b, set_eval_smem(dyn));
+    // one fused kernel per persistent launch: the track kernel for all
+    // contexts (same visibilities per lane) or for none
+    int n_trk = 0, kv_trk = 0, tabc = 0;
+    for (psc_ctx *c : b->ctxs) {
+        if (c->trk_kv <= 0) continue;
+        ++n_trk;
+        if (kv_trk && kv_trk != c->trk_kv) kv_trk = -1;
+        else if (kv_trk == 0) kv_trk = c->trk_kv;
+        tabc = std::max(tabc, (c->trk_stride + 15) / 16 * 16);
+    }
+    if (n_trk != 0 && (n_trk != n || kv_trk < 0))
+        return bfail(b, PSC_ERR_ARG, "a batch runs one fused kernel: give every context the same track tiling, or none");
+    b->track = n_trk ? kv_trk : 0;
+    b->trk_tabc = tabc;
     int per_sm = 0, dev = 0, n_sm = 0;
     b->stacked = b->ctxs[0]->wp_n > 0;
-    PSC_BCUDA(b, eval_batch_occupancy(b->threads, dyn, b->stacked, &per_sm));
+    if (b->track) {
+        const size_t tdyn = track_dyn_smem(kTrkCap, tabc);
+        PSC_BCUDA(b, set_track_smem(tdyn));
+        PSC_BCUDA(b, track_occupancy(b->track, tdyn, &per_sm));
+    } else {
+        PSC_BCUDA(b, set_eval_smem(dyn));
+        PSC_BCUDA(b, eval_batch_occupancy(b->threads, dyn, b->stacked, &per_sm));
+    }
     PSC_BCUDA(b, cudaGetDevice(&dev));
     PSC_BCUDA(b, cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
     b->grid = std::max(1, per_sm) * n_sm;
@@ -1171,8 +1307,11 @@ psc_status enqueue_iteration(psc_batch *b) {
         }
         PSC_BCUDA(b, cudaEventRecord(b->ev_pool[b->ev_used], s));
     }
-    PSC_BCUDA(b, launch_eval_batch(b->d_eval, b->d_prefix, n, b->d_queue, b->threads, b->eval_dyn, b->grid,
-                                   b->stacked, s));
+    if (b->track)
+        PSC_BCUDA(b, launch_track_batch(b->d_eval, b->d_prefix, n, b->d_queue, b->track, kTrkCap, b->trk_tabc, b->grid, s));
+    else
+        PSC_BCUDA(b, launch_eval_batch(b->d_eval, b->d_prefix, n, b->d_queue, b->threads, b->eval_dyn, b->grid,
+                                       b->stacked, s));
     if (b->prof) {
         PSC_BCUDA(b, cudaEventRecord(b->ev_pool[b->ev_used + 1], s));
         b->ev_used += 2;
@@ -1226,6 +1365,7 @@ int fit_t_tile(int nt, int threads, int cg, int kv) {
 using Tiling = std::array<int, 4>;
 
 void apply_tiling(psc_ctx *c, const Tiling &t) {
+    c->trk_kv = 0;
     if (t[3] > 0) {
         c->flat = t[3];
     } else {
@@ -1324,17 +1464,22 @@ psc_status psc_batch_autotune(psc_batch *b, int *tiling_out) {
     std::vector<double> zeros;
     std::vector<std::vector<std::pair<float, Tiling>>> timed(n);
     std::vector<int> reused(n, -1);
+    // per representative context: best brick-kernel time, track-kernel time per
+    // visibilities per lane (1, 2; infinite where not allowed)
+    std::vector<float> t_brick(n, 1e30f);
+    std::vector<std::array<float, 3>> t_trk(n, {1e30f, 1e30f, 1e30f});
     auto time_eval = [&](psc_ctx *c, int k, float *ms) -> psc_status {
         psc_status st = ensure_partials(c);
         if (st != PSC_OK) return bfail(b, st, c->err);
-        PSC_BCUDA(b, set_eval_smem(eval_dyn_smem(ch_span(c), tab_stride(c, c->kv))));
+        if (c->trk_kv == 0) PSC_BCUDA(b, set_eval_smem(eval_dyn_smem(ch_span(c), tab_stride(c, c->kv))));
         EvalArgs a = eval_args(c, c->d_lm_trial);
         a.vis_obs = (const float2 *)b->vis[k];
         a.w = b->w[k];
         a.w_scale = (float)b->w_scale[k];
-        PSC_BCUDA(b, launch_eval(a, false, b->stream));          // warm
+        auto launch = [&]() { return a.trk_kv > 0 ? launch_track(a, b->stream) : launch_eval(a, false, b->stream); };
+        PSC_BCUDA(b, launch());                                  // warm
         PSC_BCUDA(b, cudaEventRecord(e0, b->stream));
-        for (int r = 0; r < 3; ++r) PSC_BCUDA(b, launch_eval(a, false, b->stream));
+        for (int r = 0; r < 3; ++r) PSC_BCUDA(b, launch());
         PSC_BCUDA(b, cudaEventRecord(e1, b->stream));
         PSC_BCUDA(b, cudaEventSynchronize(e1));
         PSC_BCUDA(b, cudaEventElapsedTime(ms, e0, e1));
@@ -1375,7 +1520,56 @@ psc_status psc_batch_autotune(psc_batch *b, int *tiling_out) {
             psc_status st = time_eval(c, k, &ms);
             if (st != PSC_OK) return st;
             c->no_stage = ms < best ? 1 : 0;
+            t_brick[k] = std::min(best, ms);
+            // the track kernel, where the context allows it
+            for (int kv = 1; kv <= 2; ++kv) {
+                if (!trk_refusal(c, kv).empty()) continue;
+                st = trk_prepare(c);
+                if (st != PSC_OK) return bfail(b, st, c->err);
+                c->trk_kv = kv;
+                st = time_eval(c, k, &ms);
+                c->trk_kv = 0;
+                if (st != PSC_OK) return st;
+                t_trk[k][kv] = ms;
+            }
         }
+    }
+    // batch-wide choice of the fused kernel: the total time of the
+    // representatives, each weighted by the time steps of the contexts that
+    // reuse its choice
+    std::vector<double> weight(n, 0.0);
+    for (int k = 0; k < n; ++k) {
+        const int r = reused[k] < 0 ? k : reused[k];
+        weight[r] += (double)b->ctxs[k]->nt / b->ctxs[r]->nt;
+    }
+    double tot_brick = 0.0, tot_trk[3] = {0.0, 0.0, 0.0};
+    for (int k = 0; k < n; ++k) {
+        if (reused[k] >= 0) continue;
+        tot_brick += weight[k] * t_brick[k];
+        for (int kv = 1; kv <= 2; ++kv) tot_trk[kv] += weight[k] * t_trk[k][kv];
+    }
+    int use_trk = 0;
+    for (int kv = 1; kv <= 2; ++kv)
+        if (tot_trk[kv] < 1e29 && tot_trk[kv] < tot_brick && (use_trk == 0 || tot_trk[kv] < tot_trk[use_trk]))
+            use_trk = kv;
+    for (int k = 0; k < n && use_trk; ++k)               // every context must take that tiling
+        if (!trk_refusal(b->ctxs[k], use_trk).empty()) use_trk = 0;
+    if (use_trk) {
+        for (int k = 0; k < n; ++k) {
+            psc_ctx *c = b->ctxs[k];
+            psc_status st = trk_prepare(c);
+            if (st != PSC_OK) return bfail(b, st, c->err);
+            c->trk_kv = use_trk;
+            if (tiling_out) {
+                tiling_out[4 * k] = -1;
+                tiling_out[4 * k + 1] = 0;
+                tiling_out[4 * k + 2] = use_trk;
+                tiling_out[4 * k + 3] = PSC_STAGE_AUTO;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return build_tables(b);
     }
     // one block size serves the whole persistent launch: contexts whose best
     // shape is narrower take their fastest timed shape of the widest size
@@ -1384,6 +1578,7 @@ psc_status psc_batch_autotune(psc_batch *b, int *tiling_out) {
         if (reused[k] < 0) width = std::max(width, eval_threads(b->ctxs[k]));
     for (int k = 0; k < n; ++k) {
         psc_ctx *c = b->ctxs[k];
+        c->trk_kv = 0;
         if (reused[k] >= 0) {
             const psc_ctx *o = b->ctxs[reused[k]];
             c->no_stage = o->no_stage;
@@ -1502,6 +1697,13 @@ psc_status psc_solve_batch(psc_ctx *const *ctxs, int n_ctx, const void *const *v
 }
 
 const char *psc_batch_last_error(const psc_batch *b) { return b ? b->err.c_str() : g_err.c_str(); }
+
+const char *psc_batch_kernel(const psc_batch *b) {
+    if (!b) return "";
+    if (b->track == 2) return "track_kernel<2>";
+    if (b->track == 1) return "track_kernel<1>";
+    return b->stacked ? "eval_kernel<false, true>" : "eval_kernel<false, false>";
+}
 
 psc_status psc_batch_profile(psc_batch *b, int enable) {
     if (!b) return fail(nullptr, PSC_ERR_ARG, "batch is NULL");

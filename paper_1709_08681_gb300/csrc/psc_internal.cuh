@@ -66,6 +66,20 @@ struct EvalArgs {
     // p = min(floor(q), wp_n - 2), f = q - p.  Taps read the planes unstaged.
     int wp_n;
     double wp_a, wp_b, wp_scale, wp_q0;
+    // Track kernel (track.cu; trk_kv > 0, reduce mode only): one warp per item
+    // (baseline, chunk of 32 trk_kv consecutive time steps), looping over the
+    // channels; each channel's grid box and table are staged by TMA into the
+    // warp's double buffer.  Partials are [kRed][n_bricks] with
+    // n_bricks = n_bl trk_chunks (bpb = trk_chunks).
+    int trk_kv;                // 0: brick kernel (eval_kernel); 1 or 2: visibilities per lane
+    int trk_chunks;            // time chunks per baseline: ceil(nt / (32 trk_kv))
+    int trk_cap;               // staged tile capacity of one buffer (cells)
+    int trk_stride;            // entries per channel in tabs_cs (even)
+    int trk_pad;               // zero entries past a channel's table that a lane can reach
+    const float2 *tabs_cs;     // [nc][trk_stride]: (A°(n) - n s_n, s_n), s_n = A°(n+1) - A°(n), zero padded
+    const void *tmap;          // 3 CUtensorMaps over the grid (8-byte cells), boxes 8, 16, 32 wide x 8 rows
+    int *err;                  // device flag, set when a bounded wait ran out (the results are then invalid)
+    long long wait_limit;      // polls of one bounded mbarrier wait
 };
 
 // Arguments of the stencil-feature kernel (learned initial estimate).
@@ -121,6 +135,23 @@ struct LMArgs {
 };
 
 __host__ __device__ inline size_t ev_len(int n_ant, int n_bl) { return 1 + 2 * (size_t)n_ant + 3 * (size_t)n_ant + 4 * (size_t)n_bl; }
+
+// Track kernel (track.cu): dynamic shared memory of one block for tile
+// capacity cap and table capacity tabc (cells / entries per buffer), its
+// attribute, occupancy, single-context and persistent launches, the per-channel
+// (intercept, slope) tables and the grid's tensor maps (3 x 128 bytes, device).
+constexpr int kTrkThreads = 128;
+size_t track_dyn_smem(int cap, int tabc);
+cudaError_t set_track_smem(size_t dyn);
+cudaError_t track_occupancy(int kv, size_t dyn, int *blocks_per_sm);
+cudaError_t launch_track(const EvalArgs &a, cudaStream_t s);
+cudaError_t launch_track_batch(const EvalArgs *args_dev, const long long *prefix_dev, int n_ctx,
+                               unsigned long long *queue, int kv, int cap, int tabc, int grid, cudaStream_t s);
+cudaError_t launch_track_tables(const ChanConst *chan, const float2 *tabs, int nc, int stride, float2 *out,
+                                cudaStream_t s);
+cudaError_t make_grid_maps(const float2 *grid, int ng, void *maps_dev, cudaStream_t s);
+// Polls of a bounded mbarrier wait (the default unless psc_set_wait_limit changed it).
+long long wait_limit();
 
 // Launchers (defined in the .cu files).
 cudaError_t launch_eval(const EvalArgs &a, bool predict, cudaStream_t s);

@@ -1,0 +1,605 @@
+// Track kernel: the fused evaluation of Algorithm 1's inner loop for small
+// apertures (a few to a few tens of taps per visibility), one warp per
+// baseline track.
+//
+// Paper basis (Bhatnagar & Cornwell 2017): the kernel A_ij of Eq.
+// AIJPOINTING and its derivatives of Eq. DAIJPOINTING (extended to m, Sec. 3),
+// chi^2 of Eq. Chisq and its gradient, Eq. DCHIDD -- the same arithmetic as
+// eval.cu, organised for a different regime.
+//
+// Work decomposition.  An item is one baseline and one chunk of 32 kV
+// consecutive time steps; lane l owns the kV visibilities at times
+// chunk 32 kV + l kV + v of one channel, and the warp loops over all channels.
+// Within one channel the chunk's visibilities sit on a short arc of the uv
+// track (a 60 s chunk of a 16 km baseline moves under 20 cells), so the
+// warp's footprint -- the box of cells within rho_max of its visibilities --
+// is small.  Each channel's box (8, 16 or 32 cells wide, in copies of 8 rows)
+// and the channel's radial table are staged by TMA (cp.async.bulk.tensor for
+// the grid, cp.async.bulk for the table) into one of the warp's two shared
+// buffers, completing on that buffer's mbarrier; the copies of channel c + 1
+// are issued before channel c is computed, so their latency hides behind it.
+// The staged cells are then multiplied in place by the cell half of the phase
+// ramp (origin: the box corner), exactly as eval.cu stages its tiles, and the
+// taps run the same inner loop.  Warps never wait on one another: there is no
+// block barrier.  Boxes wider than 32 cells or taller than the tile fall back
+// to taps read from global memory with the ramp applied per tap.
+//
+// Sums.  Each lane accumulates its visibilities' chi^2 and gradient terms with
+// Knuth's TwoSum (compensated FP32: a running sum and its rounding error), and
+// the normal-equation terms in plain FP32.  One butterfly over the warp per
+// item (TwoSum again for the five compensated sums) gives the item's record;
+// records are summed per baseline in FP64 in a fixed order (bl_reduce_kernel),
+// so the results do not depend on which warp ran which item.
+//
+// Waits.  Every mbarrier wait is bounded (wait_limit polls).  A wait that runs
+// out sets *err; the warp then waits, with a fixed larger bound, for its own
+// copies still in flight and returns.  The host reports PSC_ERR_TIMEOUT.
+#include <cuda.h>
+
+#include <algorithm>
+#include <climits>
+#include <cstdint>
+
+#include "psc_internal.cuh"
+#include "tap_math.cuh"
+
+namespace psc {
+namespace {
+
+using namespace tap;
+
+constexpr int kTrkWarps = kTrkThreads / 32;
+constexpr int kBoxRows = 8;                 // rows of one TMA copy
+constexpr int kMaxBoxW = 32;                // widest staged box (cells)
+constexpr unsigned kFull = 0xffffffffu;
+constexpr long long kDrainPolls = 1LL << 26;
+
+__device__ __forceinline__ uint32_t saddr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t mb) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(mb));
+}
+
+__device__ __forceinline__ void mbar_expect(uint32_t mb, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(mb), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t mb, uint32_t parity, long long limit) {
+    for (long long it = 0; it < limit; ++it) {
+        uint32_t ok;
+        asm volatile("{\n.reg .pred q;\nmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\nselp.u32 %0, 1, 0, q;\n}"
+                     : "=r"(ok) : "r"(mb), "r"(parity) : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+// One 2-D TMA copy of a W x 8 box of the grid (x = column, y = row) to dst.
+__device__ __forceinline__ void tma_box(uint32_t dst, const void *map, int x, int y, uint32_t mb) {
+    asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+                 :: "r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(mb) : "memory");
+}
+
+// Contiguous bulk copy (16-byte aligned addresses, size a multiple of 16).
+__device__ __forceinline__ void bulk_copy(uint32_t dst, const void *src, uint32_t bytes, uint32_t mb) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 :: "r"(dst), "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(mb) : "memory");
+}
+
+// Grid position x = u sc + Ng/2 from the FP32 split u = uh + ul and
+// sc = sh + sl: the product's rounding error by an FMA (exact) plus the cross
+// terms; p - floor(p) is exact, so f carries the bits below p's ulp.
+__device__ __forceinline__ void trk_pos(float uh, float ul, float sh, float sl, int half, int &n, float &f) {
+    const float p = __fmul_rn(uh, sh);
+    float e = fmaf(uh, sh, -p);
+    e = fmaf(uh, sl, e);
+    e = fmaf(ul, sh, e);
+    const float fl = floorf(p);
+    f = __fadd_rn(__fsub_rn(p, fl), e);
+    n = (int)fl + half;
+    if (f < 0.f) { f += 1.f; n -= 1; }
+    else if (f >= 1.f) { f -= 1.f; n += 1; }
+}
+
+// s + c += x with Knuth's TwoSum: s keeps the rounded sum, c the exact rounding errors.
+__device__ __forceinline__ void two_sum_acc(float &s, float &c, float x) {
+    const float t = __fadd_rn(s, x);
+    const float bp = __fsub_rn(t, s);
+    const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(x, bp));
+    s = t;
+    c = __fadd_rn(c, err);
+}
+
+struct Box {
+    int x0, x1, y0, y1;   // inclusive cell range of the warp's footprint; x0 rounded down to even
+    bool empty;
+};
+
+// Positions of the lane's visibilities in channel ch and the warp's footprint.
+template <int kV>
+__device__ __forceinline__ void chan_pos(const float4 (&q)[kV], const ChanConst &ch, int half, int (&nx)[kV],
+                                         float (&fx)[kV], int (&ny)[kV], float (&fy)[kV], Box &b) {
+    const float r = ch.rho_max;
+    int xl = INT_MAX, xh = INT_MIN, yl = INT_MAX, yh = INT_MIN;
+#pragma unroll
+    for (int v = 0; v < kV; ++v) {
+        trk_pos(q[v].x, q[v].y, ch.sc_hi, ch.sc_lo, half, nx[v], fx[v]);
+        trk_pos(q[v].z, q[v].w, ch.sc_hi, ch.sc_lo, half, ny[v], fy[v]);
+        xl = min(xl, nx[v] + (int)floorf(fx[v] - r) + 1);
+        xh = max(xh, nx[v] + (int)ceilf(fx[v] + r) - 1);
+        yl = min(yl, ny[v] + (int)floorf(fy[v] - r) + 1);
+        yh = max(yh, ny[v] + (int)ceilf(fy[v] + r) - 1);
+    }
+    const int x0 = __reduce_min_sync(kFull, xl);
+    b.x1 = __reduce_max_sync(kFull, xh);
+    b.y0 = __reduce_min_sync(kFull, yl);
+    b.y1 = __reduce_max_sync(kFull, yh);
+    b.empty = x0 > b.x1 || b.y0 > b.y1;
+    b.x0 = x0 & ~1;                           // TMA: the box's first column at a 16-byte boundary
+}
+
+// Box width class (8, 16 or 32 cells; 0 = does not fit) and its TMA copies.
+__device__ __forceinline__ int box_width(const Box &b) {
+    const int w = b.x1 - b.x0 + 1;
+    return w <= 8 ? 8 : w <= 16 ? 16 : w <= kMaxBoxW ? 32 : 0;
+}
+
+template <int kV>
+__global__ void __launch_bounds__(kTrkThreads, 4)
+track_kernel(const EvalArgs a0, const EvalArgs *__restrict__ args, const long long *__restrict__ prefix, int n_ctx,
+             unsigned long long *queue, int cap, int tabc) {
+    extern __shared__ __align__(128) unsigned char trk_raw[];
+    __shared__ EvalArgs s_args[kTrkWarps];
+    __shared__ __align__(8) unsigned long long s_mbar[kTrkWarps][2];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const bool persistent = queue != nullptr;
+    EvalArgs &a = s_args[warp];
+    // this warp's two buffers: [tile cap][table tabc] each, from a 128-byte boundary
+    float2 *trk_dyn = reinterpret_cast<float2 *>(((uintptr_t)trk_raw + 127) & ~(uintptr_t)127);
+    float2 *buf0 = trk_dyn + (size_t)warp * 2 * (cap + tabc);
+    float2 *tile_b[2] = {buf0, buf0 + cap + tabc};
+    float2 *tab_b[2] = {buf0 + cap, buf0 + 2 * cap + tabc};
+    const uint32_t mb[2] = {saddr(&s_mbar[warp][0]), saddr(&s_mbar[warp][1])};
+    if (lane == 0) {
+        mbar_init(mb[0]);
+        mbar_init(mb[1]);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        if (!persistent) a = a0;
+    }
+    __syncwarp();
+    uint32_t par = 0;                  // bit b: parity of buffer b's next completion
+    uint32_t pending = 0;              // bit b: a copy into buffer b not yet waited for
+    int cur = -1;
+    long long first = 0;
+    long long gi_static = (long long)blockIdx.x * kTrkWarps + warp;
+    const float pi_f = 3.14159265358979f;
+
+    for (;;) {
+        long long gi;
+        if (persistent) {
+            unsigned long long t = 0;
+            if (lane == 0) t = atomicAdd(queue, 1ull);
+            gi = (long long)__shfl_sync(kFull, t, 0);
+            if (gi >= prefix[n_ctx]) break;
+            if (cur < 0 || gi < prefix[cur] || gi >= prefix[cur + 1]) {
+                int lo = 0, hi = n_ctx - 1;            // last context with prefix[k] <= gi
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (prefix[mid] <= gi) lo = mid; else hi = mid - 1;
+                }
+                cur = lo;
+                first = prefix[lo];
+                __syncwarp();                          // every lane is done reading the old arguments
+                const int *src = reinterpret_cast<const int *>(&args[lo]);
+                int *dst = reinterpret_cast<int *>(&a);
+                for (int i = lane; i < (int)(sizeof(EvalArgs) / 4); i += 32) dst[i] = src[i];
+                __syncwarp();
+            }
+        } else {
+            gi = gi_static;
+            gi_static += (long long)gridDim.x * kTrkWarps;
+            if (gi >= a.n_bricks) break;
+        }
+        if (a.skip != nullptr && *a.skip) continue;
+        const int item = (int)(gi - first);
+        const int chunks = a.trk_chunks;
+        const int qbl = item / chunks, chunk = item - qbl * chunks;
+        const int bl = a.bl_order != nullptr ? a.bl_order[qbl] : qbl;
+        const int brick = bl * chunks + chunk;
+        const int2 ij = a.pairs[bl];
+        const double li = a.lm[2 * ij.x], mi = a.lm[2 * ij.x + 1];
+        const double lj = a.lm[2 * ij.y], mj = a.lm[2 * ij.y + 1];
+        const float L = (float)(li + lj), M = (float)(mi + mj);       // ramp
+        const float dL = (float)(li - lj), dM = (float)(mi - mj);     // decorrelation
+        const int nt = a.nt, nc = a.nc, n_bl = a.n_bl, half = a.ng / 2;
+        const float du = a.du, ov = (float)a.ov;
+        const int tb = chunk * 32 * kV + lane * kV;
+        float4 q[kV];
+        bool valid[kV];
+#pragma unroll
+        for (int v = 0; v < kV; ++v) {
+            valid[v] = tb + v < nt;
+            q[v] = a.uvs[(size_t)min(tb + v, nt - 1) * n_bl + bl];     // past the end: repeat the last step
+        }
+        float S[kRed], Cc[5];
+#pragma unroll
+        for (int k = 0; k < kRed; ++k) S[k] = 0.f;
+#pragma unroll
+        for (int k = 0; k < 5; ++k) Cc[k] = 0.f;
+        // per-tap ramp steps of the global-memory fallback
+        float zxs, zxc;
+        __sincosf(-pi_f * du * L, &zxs, &zxc);
+
+        int nx[kV], ny[kV];
+        float fx[kV], fy[kV];
+        Box box;
+        ChanConst ch = a.chan[0];
+        chan_pos<kV>(q, ch, half, nx, fx, ny, fy, box);
+        bool ok = true;
+        // issues the copies of channel cc (box bx) into buffer bb
+        auto issue = [&](int cc, const ChanConst &chc, const Box &bx, int bb) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic writes before async-proxy writes
+            __syncwarp();
+            if (lane == 0) {
+                const int W = bx.empty ? 0 : box_width(bx);
+                const int ncp = (bx.y1 - bx.y0 + 1 + kBoxRows - 1) / kBoxRows;
+                const bool fits = W > 0 && W * kBoxRows * ncp <= a.trk_cap;
+                const int n_tab = min(a.trk_stride, (chc.tab_len + a.trk_pad + 1) & ~1);
+                const uint32_t tab_bytes = (uint32_t)n_tab * 8u;
+                const uint32_t box_bytes = fits ? (uint32_t)(W * kBoxRows * ncp) * 8u : 0u;
+                mbar_expect(mb[bb], tab_bytes + box_bytes);
+                if (fits) {
+                    const char *map = reinterpret_cast<const char *>(a.tmap) + (W == 8 ? 0 : W == 16 ? 128 : 256);
+                    const uint32_t dst = saddr(tile_b[bb]);
+                    for (int k = 0; k < ncp; ++k)
+                        tma_box(dst + (uint32_t)(k * kBoxRows * W * 8), map, bx.x0, bx.y0 + k * kBoxRows, mb[bb]);
+                }
+                bulk_copy(saddr(tab_b[bb]), a.tabs_cs + (size_t)cc * a.trk_stride, tab_bytes, mb[bb]);
+            }
+            pending |= 1u << bb;
+        };
+        issue(0, ch, box, 0);
+
+        for (int c = 0; c < nc; ++c) {
+            const int b = c & 1;
+            // prefetch channel c + 1 into the other buffer (its last reader was channel c - 1)
+            int nxn[kV], nyn[kV];
+            float fxn[kV], fyn[kV];
+            Box boxn = box;
+            ChanConst chn = ch;
+            if (c + 1 < nc) {
+                chn = a.chan[c + 1];
+                chan_pos<kV>(q, chn, half, nxn, fxn, nyn, fyn, boxn);
+                issue(c + 1, chn, boxn, b ^ 1);
+            }
+            bool got = mbar_wait(mb[b], (par >> b) & 1u, a.wait_limit);
+            if (__any_sync(kFull, !got)) { ok = false; break; }
+            par ^= 1u << b;
+            pending &= ~(1u << b);
+
+            const float rmax = ch.rho_max, rmax2 = rmax * rmax;
+            const int W = box.empty ? 0 : box_width(box);
+            const int ncp = (box.y1 - box.y0 + 1 + kBoxRows - 1) / kBoxRows;
+            const bool staged = W > 0 && W * kBoxRows * ncp <= a.trk_cap;
+            float2 *tile = tile_b[b];
+            const unsigned tab_adj = saddr(tab_b[b]) - (0x4B000000u << 3);
+            float2 S0[kV], Su[kV], Sv[kV];
+#pragma unroll
+            for (int v = 0; v < kV; ++v) S0[v] = Su[v] = Sv[v] = make_float2(0.f, 0.f);
+            float hx[kV], hy[kV];                      // positions relative to the ramp origin
+            if (staged) {
+                // cell half of the ramp, in place: cell (col, r) *= exp(-i pi du (col L + r M))
+                const int lw = W == 8 ? 3 : W == 16 ? 4 : 5;
+                const int col = lane & (W - 1);
+                const int rstep = 32 >> lw;
+                const int rows = box.y1 - box.y0 + 1;
+                if (col <= box.x1 - box.x0) {
+                    int r = lane >> lw;
+                    float zs, zc, ss, sc;
+                    __sincosf(-pi_f * du * ((float)col * L + (float)r * M), &zs, &zc);
+                    __sincosf(-pi_f * du * ((float)rstep * M), &ss, &sc);
+                    float2 z = make_float2(zc, zs);
+                    const float2 step = make_float2(sc, ss);
+                    for (; r < rows; r += rstep) {
+                        float2 *cell = tile + r * W + col;
+                        *cell = cmul(*cell, z);
+                        z = cmul(z, step);
+                    }
+                }
+                __syncwarp();
+#pragma unroll
+                for (int v = 0; v < kV; ++v) {
+                    hx[v] = (float)(nx[v] - box.x0) + fx[v];
+                    hy[v] = (float)(ny[v] - box.y0) + fy[v];
+                }
+                int r_lo = INT_MAX, r_hi = INT_MIN;
+#pragma unroll
+                for (int v = 0; v < kV; ++v) {
+                    r_lo = min(r_lo, (int)floorf(hy[v] - rmax) + 1);
+                    r_hi = max(r_hi, (int)ceilf(hy[v] + rmax) - 1);
+                }
+                r_lo = max(r_lo, 0);
+                r_hi = min(r_hi, rows - 1);
+                for (int cy = r_lo; cy <= r_hi; ++cy) {
+                    float dy[kV], dyo2[kV];
+                    int c_lo = INT_MAX, c_hi = INT_MIN;
+#pragma unroll
+                    for (int v = 0; v < kV; ++v) {
+                        dy[v] = hy[v] - (float)cy;
+                        const float dyo = dy[v] * ov;
+                        dyo2[v] = fmaf(dyo, dyo, 1e-20f);
+                        const float rem = rmax2 - dy[v] * dy[v];
+                        if (rem > 0.f) {
+                            const float r = fminf(rem * rsqrt_fast(rem), rmax);
+                            const int lo = max(0, (int)floorf(hx[v] - r) + 1);
+                            const int hi = min(W - 1, (int)ceilf(hx[v] + r) - 1);
+                            if (lo <= hi) {
+                                c_lo = min(c_lo, lo);
+                                c_hi = max(c_hi, hi);
+                            }
+                        }
+                    }
+                    if (c_lo > c_hi) continue;
+                    float dxo[kV], pr[kV], pi[kV], qr[kV], qi[kV];
+#pragma unroll
+                    for (int v = 0; v < kV; ++v) {
+                        dxo[v] = (hx[v] - (float)c_lo) * ov;
+                        pr[v] = pi[v] = qr[v] = qi[v] = 0.f;
+                    }
+                    if constexpr (kV == 2)
+                        row_taps2(tile + cy * W + c_lo, c_hi - c_lo + 1, make_float2(dxo[0], dxo[1]),
+                                  make_float2(dyo2[0], dyo2[1]), ov, tab_adj, pr, pi, qr, qi);
+                    else
+                        row_taps<kV>(tile + cy * W + c_lo, c_hi - c_lo + 1, dxo, dyo2, ov, tab_adj, pr, pi, qr, qi);
+#pragma unroll
+                    for (int v = 0; v < kV; ++v) {
+                        S0[v].x += pr[v]; S0[v].y += pi[v];
+                        Su[v].x += qr[v]; Su[v].y += qi[v];
+                        Sv[v].x = fmaf(dy[v], pr[v], Sv[v].x);
+                        Sv[v].y = fmaf(dy[v], pi[v], Sv[v].y);
+                    }
+                }
+            } else if (!box.empty) {
+                // fallback: taps read the grid (L1/L2), ramp per tap from each
+                // visibility's own cell (nx, ny)
+#pragma unroll
+                for (int v = 0; v < kV; ++v) {
+                    hx[v] = fx[v];
+                    hy[v] = fy[v];
+                    const int b_lo = max((int)floorf(fy[v] - rmax) + 1, -ny[v]);
+                    const int b_hi = min((int)ceilf(fy[v] + rmax) - 1, a.ng - 1 - ny[v]);
+                    for (int bb = b_lo; bb <= b_hi; ++bb) {
+                        const float dy = fy[v] - (float)bb;
+                        const float rem = rmax2 - dy * dy;
+                        if (!(rem > 0.f)) continue;
+                        const float r = fminf(rem * rsqrt_fast(rem), rmax);
+                        const int a_lo = max((int)floorf(fx[v] - r) + 1, -nx[v]);
+                        const int a_hi = min((int)ceilf(fx[v] + r) - 1, a.ng - 1 - nx[v]);
+                        if (a_lo > a_hi) continue;
+                        const float dyo = dy * ov;
+                        const float dyo2 = fmaf(dyo, dyo, 1e-20f);
+                        float zs, zc;
+                        __sincosf(-pi_f * du * ((float)a_lo * L + (float)bb * M), &zs, &zc);
+                        float2 z = make_float2(zc, zs);
+                        const float2 zx = make_float2(zxc, zxs);
+                        float pr = 0.f, pi = 0.f, qr = 0.f, qi = 0.f;
+                        const float2 *row = a.grid + (size_t)(ny[v] + bb) * a.ng + nx[v];
+                        float dd = (fx[v] - (float)a_lo) * ov;
+                        for (int aa = a_lo; aa <= a_hi; ++aa, dd -= ov) {
+                            const float2 g = cmul(__ldg(&row[aa]), z);
+                            z = cmul(z, zx);
+                            const float s2 = fmaf(dd, dd, dyo2);
+                            const float tv = sqrt_fast(s2);
+                            const float tf = __fadd_rz(tv, 8388608.0f);
+                            const float2 e = lds_f2(tab_adj + ((unsigned)__float_as_int(tf) << 3));
+                            const float A = fmaf(tv, e.y, e.x);
+                            pr = fmaf(A, g.x, pr);
+                            pi = fmaf(A, g.y, pi);
+                            const float Ad = A * dd;
+                            qr = fmaf(Ad, g.x, qr);
+                            qi = fmaf(Ad, g.y, qi);
+                        }
+                        S0[v].x += pr; S0[v].y += pi;
+                        Su[v].x += qr; Su[v].y += qi;
+                        Sv[v].x = fmaf(dy, pr, Sv[v].x);
+                        Sv[v].y = fmaf(dy, pi, Sv[v].y);
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int v = 0; v < kV; ++v) hx[v] = hy[v] = 0.f;
+            }
+
+            // ---- epilogue: visibility half of the ramp, decorrelation, derivatives ----
+            const float inv_ov = 1.0f / ov;
+            const float al2 = ch.alpha2;
+            float D = 1.f, el = 0.f, em = 0.f;
+            if (a.decorrelation) {
+                D = expf(-0.5f * al2 * (dL * dL + dM * dM));
+                el = -dL * al2;                      // (l_j - l_i) alpha^2
+                em = -dM * al2;
+            }
+#pragma unroll
+            for (int v = 0; v < kV; ++v) {
+                if (!valid[v]) continue;
+                float s, co;
+                sincospif(du * (hx[v] * L + hy[v] * M), &s, &co);
+                const float2 ph = make_float2(co, s);
+                const float2 T0 = cmul(ph, S0[v]);
+                float2 Tu = cmul(ph, Su[v]), Tv = cmul(ph, Sv[v]);
+                const float su = du * inv_ov;        // Q was accumulated with dx * ov; taps in wavelengths
+                Tu.x *= su; Tu.y *= su;
+                Tv.x *= du; Tv.y *= du;
+                const float2 V = make_float2(D * T0.x, D * T0.y);
+                const float2 dli = make_float2(D * (el * T0.x - pi_f * Tu.y), D * (el * T0.y + pi_f * Tu.x));
+                const float2 dmi = make_float2(D * (em * T0.x - pi_f * Tv.y), D * (em * T0.y + pi_f * Tv.x));
+                const float2 dlj = make_float2(D * (-el * T0.x - pi_f * Tu.y), D * (-el * T0.y + pi_f * Tu.x));
+                const float2 dmj = make_float2(D * (-em * T0.x - pi_f * Tv.y), D * (-em * T0.y + pi_f * Tv.x));
+                const size_t k = ((size_t)(tb + v) * n_bl + bl) * nc + c;
+                const float2 vo = a.vis_obs[k];
+                const float w = a.w_scale * (a.w != nullptr ? a.w[k] : 1.f);
+                const float2 R = make_float2(vo.x - V.x, vo.y - V.y);
+                const float w2 = 2.f * w;
+                two_sum_acc(S[0], Cc[0], w * (R.x * R.x + R.y * R.y));
+                two_sum_acc(S[1], Cc[1], -w2 * (R.x * dli.x + R.y * dli.y));
+                two_sum_acc(S[2], Cc[2], -w2 * (R.x * dmi.x + R.y * dmi.y));
+                two_sum_acc(S[3], Cc[3], -w2 * (R.x * dlj.x + R.y * dlj.y));
+                two_sum_acc(S[4], Cc[4], -w2 * (R.x * dmj.x + R.y * dmj.y));
+                S[5] += w2 * (dli.x * dli.x + dli.y * dli.y);
+                S[6] += w2 * (dli.x * dmi.x + dli.y * dmi.y);
+                S[7] += w2 * (dmi.x * dmi.x + dmi.y * dmi.y);
+                S[8] += w2 * (dlj.x * dlj.x + dlj.y * dlj.y);
+                S[9] += w2 * (dlj.x * dmj.x + dlj.y * dmj.y);
+                S[10] += w2 * (dmj.x * dmj.x + dmj.y * dmj.y);
+                S[11] += w2 * (dli.x * dlj.x + dli.y * dlj.y);
+                S[12] += w2 * (dli.x * dmj.x + dli.y * dmj.y);
+                S[13] += w2 * (dmi.x * dlj.x + dmi.y * dlj.y);
+                S[14] += w2 * (dmi.x * dmj.x + dmi.y * dmj.y);
+            }
+            if (c + 1 < nc) {
+                ch = chn;
+                box = boxn;
+#pragma unroll
+                for (int v = 0; v < kV; ++v) {
+                    nx[v] = nxn[v]; ny[v] = nyn[v]; fx[v] = fxn[v]; fy[v] = fyn[v];
+                }
+            }
+        }
+        if (!ok) {
+            // a wait ran out: report it, wait (longer bound) for this warp's own
+            // copies still in flight, and stop
+            if (lane == 0) atomicExch(a.err, 1);
+            for (int bb = 0; bb < 2; ++bb)
+                if (pending & (1u << bb)) mbar_wait(mb[bb], (par >> bb) & 1u, kDrainPolls);
+            __syncwarp();
+            return;
+        }
+        // ---- the item's record: butterfly over the warp ----
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+            for (int k = 0; k < 5; ++k) {
+                const float so = __shfl_xor_sync(kFull, S[k], o);
+                const float co = __shfl_xor_sync(kFull, Cc[k], o);
+                float cs = 0.f;
+                two_sum_acc(S[k], cs, so);
+                Cc[k] = __fadd_rn(__fadd_rn(Cc[k], co), cs);
+            }
+#pragma unroll
+            for (int k = 5; k < kRed; ++k) S[k] += __shfl_xor_sync(kFull, S[k], o);
+        }
+        double out = 0.0;
+#pragma unroll
+        for (int k = 0; k < kRed; ++k)
+            if (lane == k) out = k < 5 ? (double)S[k] + (double)Cc[k] : (double)S[k];
+        if (lane < kRed) a.partials[(size_t)lane * a.n_bricks + brick] = out;
+    }
+}
+
+// (intercept, slope) tables of every channel at a common stride, zero padded:
+// entry n of channel c is (A°(n) - n s_n, s_n) with s_n = A°(n+1) - A°(n).
+__global__ void track_tables_kernel(const ChanConst *__restrict__ chan, const float2 *__restrict__ tabs, int nc,
+                                    int stride, float2 *__restrict__ out) {
+    const size_t total = (size_t)nc * stride;
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < total; k += (size_t)gridDim.x * blockDim.x) {
+        const int c = (int)(k / stride), n = (int)(k - (size_t)c * stride);
+        float2 v = make_float2(0.f, 0.f);
+        if (n < chan[c].tab_len) {
+            const float2 e = tabs[chan[c].tab_off + n];
+            v = make_float2(fmaf(-(float)n, e.y, e.x), e.y);
+        }
+        out[k] = v;
+    }
+}
+
+}  // namespace
+
+size_t track_dyn_smem(int cap, int tabc) {
+    return (size_t)kTrkWarps * 2 * (size_t)(cap + tabc) * sizeof(float2) + 128;    // + alignment slack
+}
+
+cudaError_t set_track_smem(size_t dyn) {
+    for (const void *k : {(const void *)track_kernel<1>, (const void *)track_kernel<2>}) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t track_occupancy(int kv, size_t dyn, int *blocks_per_sm) {
+    if (kv == 2)
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, track_kernel<2>, kTrkThreads, dyn);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, track_kernel<1>, kTrkThreads, dyn);
+}
+
+cudaError_t launch_track(const EvalArgs &a, cudaStream_t s) {
+    const int cap = a.trk_cap, tabc = (a.trk_stride + 15) / 16 * 16;
+    const size_t dyn = track_dyn_smem(cap, tabc);
+    cudaError_t e = set_track_smem(dyn);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0, dev = 0, n_sm = 0;
+    e = track_occupancy(a.trk_kv, dyn, &per_sm);
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const long long need = (a.n_bricks + kTrkWarps - 1) / kTrkWarps;
+    const int grid = (int)std::max<long long>(1, std::min<long long>(need, (long long)std::max(1, per_sm) * n_sm));
+    if (a.trk_kv == 2) track_kernel<2><<<grid, kTrkThreads, dyn, s>>>(a, nullptr, nullptr, 0, nullptr, cap, tabc);
+    else track_kernel<1><<<grid, kTrkThreads, dyn, s>>>(a, nullptr, nullptr, 0, nullptr, cap, tabc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_track_batch(const EvalArgs *args_dev, const long long *prefix_dev, int n_ctx,
+                               unsigned long long *queue, int kv, int cap, int tabc, int grid, cudaStream_t s) {
+    EvalArgs none{};
+    const size_t dyn = track_dyn_smem(cap, tabc);
+    if (kv == 2) track_kernel<2><<<grid, kTrkThreads, dyn, s>>>(none, args_dev, prefix_dev, n_ctx, queue, cap, tabc);
+    else track_kernel<1><<<grid, kTrkThreads, dyn, s>>>(none, args_dev, prefix_dev, n_ctx, queue, cap, tabc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_track_tables(const ChanConst *chan, const float2 *tabs, int nc, int stride, float2 *out,
+                                cudaStream_t s) {
+    const size_t total = (size_t)nc * stride;
+    const int blocks = (int)std::min<size_t>((total + 255) / 256, 1024);
+    track_tables_kernel<<<blocks, 256, 0, s>>>(chan, tabs, nc, stride, out);
+    return cudaGetLastError();
+}
+
+namespace {
+using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+}
+
+// Three tensor maps over the complex64 grid [ng][ng] viewed as 8-byte cells:
+// boxes of 8, 16 and 32 cells by 8 rows, zero fill outside the grid.
+cudaError_t make_grid_maps(const float2 *grid, int ng, void *maps_dev, cudaStream_t s) {
+    if (((uintptr_t)grid & 15) || ng % 2) return cudaErrorInvalidValue;
+    static EncodeTiled fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q);
+        if (e != cudaSuccess) return e;
+        if (q != cudaDriverEntryPointSuccess || !p) return cudaErrorNotSupported;
+        fn = reinterpret_cast<EncodeTiled>(p);
+    }
+    CUtensorMap maps[3];
+    const int widths[3] = {8, 16, 32};
+    for (int k = 0; k < 3; ++k) {
+        const cuuint64_t dims[2] = {(cuuint64_t)ng, (cuuint64_t)ng};
+        const cuuint64_t strides[1] = {(cuuint64_t)ng * 8};
+        const cuuint32_t box[2] = {(cuuint32_t)widths[k], (cuuint32_t)kBoxRows};
+        const cuuint32_t es[2] = {1, 1};
+        const CUresult r = fn(&maps[k], CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, const_cast<float2 *>(grid), dims, strides,
+                              box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    }
+    cudaError_t e = cudaMemcpyAsync(maps_dev, maps, sizeof(maps), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    return cudaStreamSynchronize(s);
+}
+
+}  // namespace psc

@@ -12,7 +12,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def declared_functions():
     src = open(os.path.join(ROOT, "include", "psc.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"^\s*(?:psc_status|void|int|const char \*)\s*(psc_\w+)\s*\(", src, flags=re.M)))
+    return sorted(set(re.findall(r"^\s*(?:psc_status|void|int|long long|const char \*)\s*(psc_\w+)\s*\(", src, flags=re.M)))
 
 
 def test_library_exports_every_declared_function():

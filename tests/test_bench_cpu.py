@@ -26,7 +26,11 @@ def test_reference_arm_prints_one_contract_line():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": "Gvis/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
-    assert d["config"]["workload"] == "vla27_l64ch"
+    # the same config dictionary as the GPU arm prints for its headline workload
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_1709_08681_gb300 import inputs as I
+    assert d["config"] == bench.config_for(I.make_workload("drift197_l128ch"))
 
 
 def test_reference_arm_is_silent_on_other_ranks():
