@@ -166,6 +166,12 @@ int n_cg(const psc_ctx *c) { return (c->nc + c->c_group - 1) / c->c_group; }
 // staged tile capacity of one buffer (cells).
 int trk_chunks(const psc_ctx *c) { return (c->nt + 32 * c->trk_kv - 1) / (32 * c->trk_kv); }
 constexpr int kTrkCap = 512;
+// Zero table entries the track kernel's tap pattern can reach past a
+// channel's table with kv visibilities per lane: its taps lie within
+// rho_max + 2 spread + sqrt(2) (+ a margin) cells of each visibility.
+int trk_pad(const psc_ctx *c, int kv) {
+    return (int)std::ceil(c->gd.oversample * (2.0 * kv_spread(c, kv) + 1.5)) + 2;
+}
 // Flat bricks: groups of kv consecutive time steps per channel, the bricks
 // per baseline, and the most channels one brick's items can span.
 int n_tp(const psc_ctx *c) { return (c->nt + c->kv - 1) / c->kv; }
@@ -237,7 +243,8 @@ EvalArgs eval_args(const psc_ctx *c, const double *lm_dev) {
         a.trk_chunks = trk_chunks(c);
         a.trk_cap = kTrkCap;
         a.trk_stride = c->trk_stride;
-        a.trk_pad = tab_stride(c, c->trk_kv) - c->max_tab_len;
+        a.trk_pad = trk_pad(c, c->trk_kv);
+        a.trk_spread = (float)c->step_cells;
         a.tabs_cs = c->d_tabcs;
         a.tmap = c->d_tmap;
     }
@@ -321,7 +328,7 @@ psc_status eval_reduce(psc_ctx *c, const double *lm_dev, const void *vis_obs, co
 // tables and the grid's tensor maps, once.
 psc_status trk_prepare(psc_ctx *c) {
     if (c->d_tmap) return PSC_OK;
-    const int stride = (std::max(tab_stride(c, 1), kv_allowed(c, 2) ? tab_stride(c, 2) : 0) + 1) & ~1;
+    const int stride = (c->max_tab_len + trk_pad(c, kv_allowed(c, 2) ? 2 : 1) + 1) & ~1;
     cudaError_t e = dalloc(&c->d_tabcs, (size_t)c->nc * stride);
     if (e == cudaSuccess) e = launch_track_tables(c->d_chan, c->d_tabs, c->nc, stride, c->d_tabcs, c->stream);
     void *maps = nullptr;

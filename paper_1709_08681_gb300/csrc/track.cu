@@ -115,26 +115,24 @@ struct Box {
     bool empty;
 };
 
-// Positions of the lane's visibilities in channel ch and the warp's footprint.
+// Positions of the lane's visibilities in channel ch, and the warp's
+// footprint: the union over lanes of each lane's tap pattern, the cells
+// (n0 + a, m0 + b) with a, b in [1 - R, R] around the base cell (n0, m0) of
+// its first visibility (R = ceil of the pattern radius rp, see tap_pattern).
 template <int kV>
-__device__ __forceinline__ void chan_pos(const float4 (&q)[kV], const ChanConst &ch, int half, int (&nx)[kV],
-                                         float (&fx)[kV], int (&ny)[kV], float (&fy)[kV], Box &b) {
-    const float r = ch.rho_max;
-    int xl = INT_MAX, xh = INT_MIN, yl = INT_MAX, yh = INT_MIN;
+__device__ __forceinline__ void chan_pos(const float4 (&q)[kV], const ChanConst &ch, int half, float rp,
+                                         int (&nx)[kV], float (&fx)[kV], int (&ny)[kV], float (&fy)[kV], Box &b) {
 #pragma unroll
     for (int v = 0; v < kV; ++v) {
         trk_pos(q[v].x, q[v].y, ch.sc_hi, ch.sc_lo, half, nx[v], fx[v]);
         trk_pos(q[v].z, q[v].w, ch.sc_hi, ch.sc_lo, half, ny[v], fy[v]);
-        xl = min(xl, nx[v] + (int)floorf(fx[v] - r) + 1);
-        xh = max(xh, nx[v] + (int)ceilf(fx[v] + r) - 1);
-        yl = min(yl, ny[v] + (int)floorf(fy[v] - r) + 1);
-        yh = max(yh, ny[v] + (int)ceilf(fy[v] + r) - 1);
     }
-    const int x0 = __reduce_min_sync(kFull, xl);
-    b.x1 = __reduce_max_sync(kFull, xh);
-    b.y0 = __reduce_min_sync(kFull, yl);
-    b.y1 = __reduce_max_sync(kFull, yh);
-    b.empty = x0 > b.x1 || b.y0 > b.y1;
+    const int R = (int)ceilf(rp);
+    const int x0 = __reduce_min_sync(kFull, nx[0] + 1 - R);
+    b.x1 = __reduce_max_sync(kFull, nx[0] + R);
+    b.y0 = __reduce_min_sync(kFull, ny[0] + 1 - R);
+    b.y1 = __reduce_max_sync(kFull, ny[0] + R);
+    b.empty = false;
     b.x0 = x0 & ~1;                           // TMA: the box's first column at a 16-byte boundary
 }
 
@@ -234,7 +232,10 @@ track_kernel(const EvalArgs a0, const EvalArgs *__restrict__ args, const long lo
         float fx[kV], fy[kV];
         Box box;
         ChanConst ch = a.chan[0];
-        chan_pos<kV>(q, ch, half, nx, fx, ny, fy, box);
+        // pattern radius: the aperture's reach plus the largest distance between
+        // a lane's visibilities (consecutive time steps), plus a margin
+        const float spread = (float)(kV - 1) * a.trk_spread + 1e-3f;
+        chan_pos<kV>(q, ch, half, ch.rho_max + spread, nx, fx, ny, fy, box);
         bool ok = true;
         // issues the copies of channel cc (box bx) into buffer bb
         auto issue = [&](int cc, const ChanConst &chc, const Box &bx, int bb) {
@@ -269,7 +270,7 @@ track_kernel(const EvalArgs a0, const EvalArgs *__restrict__ args, const long lo
             ChanConst chn = ch;
             if (c + 1 < nc) {
                 chn = a.chan[c + 1];
-                chan_pos<kV>(q, chn, half, nxn, fxn, nyn, fyn, boxn);
+                chan_pos<kV>(q, chn, half, chn.rho_max + spread, nxn, fxn, nyn, fyn, boxn);
                 issue(c + 1, chn, boxn, b ^ 1);
             }
             bool got = mbar_wait(mb[b], (par >> b) & 1u, a.wait_limit);
@@ -312,45 +313,43 @@ track_kernel(const EvalArgs a0, const EvalArgs *__restrict__ args, const long lo
                     hx[v] = (float)(nx[v] - box.x0) + fx[v];
                     hy[v] = (float)(ny[v] - box.y0) + fy[v];
                 }
-                int r_lo = INT_MAX, r_hi = INT_MIN;
+                // The tap pattern, the same for every lane of the warp (no
+                // divergence, no per-lane spans): relative to the lane's base
+                // cell (n0, m0), the cells (a, b) within rp of some point of
+                // the unit cell [0, 1)^2 -- rows b in [1 - R, R], row b's
+                // columns a in [1 - ceil(w_b), ceil(w_b)], w_b = sqrt(rp^2 - d_b^2)
+                // with d_b the row's distance from the unit cell.  Every cell
+                // within rho_max of any of the lane's visibilities is in it;
+                // the others read zero table entries (the tables are padded
+                // past rp + sqrt(2) + spread).
+                const float rp = rmax + spread, rp2 = rp * rp;
+                const int R = (int)ceilf(rp);
+                float ux[kV], uy[kV];                  // visibilities relative to the base cell
 #pragma unroll
                 for (int v = 0; v < kV; ++v) {
-                    r_lo = min(r_lo, (int)floorf(hy[v] - rmax) + 1);
-                    r_hi = max(r_hi, (int)ceilf(hy[v] + rmax) - 1);
+                    ux[v] = (float)(nx[v] - nx[0]) + fx[v];
+                    uy[v] = (float)(ny[v] - ny[0]) + fy[v];
                 }
-                r_lo = max(r_lo, 0);
-                r_hi = min(r_hi, rows - 1);
-                for (int cy = r_lo; cy <= r_hi; ++cy) {
-                    float dy[kV], dyo2[kV];
-                    int c_lo = INT_MAX, c_hi = INT_MIN;
+                const float2 *base = tile + (ny[0] - box.y0) * W + (nx[0] - box.x0);
+                for (int rb = 1 - R; rb <= R; ++rb) {
+                    const float d = rb <= 0 ? (float)(-rb) : (float)(rb - 1);
+                    const float rem = rp2 - d * d;
+                    const int cw = (int)ceilf(rem * rsqrt_fast(rem));
+                    const int a_lo = 1 - cw;
+                    float dy[kV], dyo2[kV], dxo[kV], pr[kV], pi[kV], qr[kV], qi[kV];
 #pragma unroll
                     for (int v = 0; v < kV; ++v) {
-                        dy[v] = hy[v] - (float)cy;
+                        dy[v] = uy[v] - (float)rb;
                         const float dyo = dy[v] * ov;
                         dyo2[v] = fmaf(dyo, dyo, 1e-20f);
-                        const float rem = rmax2 - dy[v] * dy[v];
-                        if (rem > 0.f) {
-                            const float r = fminf(rem * rsqrt_fast(rem), rmax);
-                            const int lo = max(0, (int)floorf(hx[v] - r) + 1);
-                            const int hi = min(W - 1, (int)ceilf(hx[v] + r) - 1);
-                            if (lo <= hi) {
-                                c_lo = min(c_lo, lo);
-                                c_hi = max(c_hi, hi);
-                            }
-                        }
-                    }
-                    if (c_lo > c_hi) continue;
-                    float dxo[kV], pr[kV], pi[kV], qr[kV], qi[kV];
-#pragma unroll
-                    for (int v = 0; v < kV; ++v) {
-                        dxo[v] = (hx[v] - (float)c_lo) * ov;
+                        dxo[v] = (ux[v] - (float)a_lo) * ov;
                         pr[v] = pi[v] = qr[v] = qi[v] = 0.f;
                     }
                     if constexpr (kV == 2)
-                        row_taps2(tile + cy * W + c_lo, c_hi - c_lo + 1, make_float2(dxo[0], dxo[1]),
+                        row_taps2(base + rb * W + a_lo, 2 * cw, make_float2(dxo[0], dxo[1]),
                                   make_float2(dyo2[0], dyo2[1]), ov, tab_adj, pr, pi, qr, qi);
                     else
-                        row_taps<kV>(tile + cy * W + c_lo, c_hi - c_lo + 1, dxo, dyo2, ov, tab_adj, pr, pi, qr, qi);
+                        row_taps<kV>(base + rb * W + a_lo, 2 * cw, dxo, dyo2, ov, tab_adj, pr, pi, qr, qi);
 #pragma unroll
                     for (int v = 0; v < kV; ++v) {
                         S0[v].x += pr[v]; S0[v].y += pi[v];
@@ -419,11 +418,12 @@ track_kernel(const EvalArgs a0, const EvalArgs *__restrict__ args, const long lo
                 el = -dL * al2;                      // (l_j - l_i) alpha^2
                 em = -dM * al2;
             }
+            float cs[5] = {0.f, 0.f, 0.f, 0.f, 0.f};   // this channel's chi^2 and gradient terms
 #pragma unroll
             for (int v = 0; v < kV; ++v) {
                 if (!valid[v]) continue;
                 float s, co;
-                sincospif(du * (hx[v] * L + hy[v] * M), &s, &co);
+                __sincosf(pi_f * du * (hx[v] * L + hy[v] * M), &s, &co);
                 const float2 ph = make_float2(co, s);
                 const float2 T0 = cmul(ph, S0[v]);
                 float2 Tu = cmul(ph, Su[v]), Tv = cmul(ph, Sv[v]);
@@ -440,11 +440,11 @@ track_kernel(const EvalArgs a0, const EvalArgs *__restrict__ args, const long lo
                 const float w = a.w_scale * (a.w != nullptr ? a.w[k] : 1.f);
                 const float2 R = make_float2(vo.x - V.x, vo.y - V.y);
                 const float w2 = 2.f * w;
-                two_sum_acc(S[0], Cc[0], w * (R.x * R.x + R.y * R.y));
-                two_sum_acc(S[1], Cc[1], -w2 * (R.x * dli.x + R.y * dli.y));
-                two_sum_acc(S[2], Cc[2], -w2 * (R.x * dmi.x + R.y * dmi.y));
-                two_sum_acc(S[3], Cc[3], -w2 * (R.x * dlj.x + R.y * dlj.y));
-                two_sum_acc(S[4], Cc[4], -w2 * (R.x * dmj.x + R.y * dmj.y));
+                cs[0] += w * (R.x * R.x + R.y * R.y);
+                cs[1] -= w2 * (R.x * dli.x + R.y * dli.y);
+                cs[2] -= w2 * (R.x * dmi.x + R.y * dmi.y);
+                cs[3] -= w2 * (R.x * dlj.x + R.y * dlj.y);
+                cs[4] -= w2 * (R.x * dmj.x + R.y * dmj.y);
                 S[5] += w2 * (dli.x * dli.x + dli.y * dli.y);
                 S[6] += w2 * (dli.x * dmi.x + dli.y * dmi.y);
                 S[7] += w2 * (dmi.x * dmi.x + dmi.y * dmi.y);
@@ -456,6 +456,8 @@ track_kernel(const EvalArgs a0, const EvalArgs *__restrict__ args, const long lo
                 S[13] += w2 * (dmi.x * dlj.x + dmi.y * dlj.y);
                 S[14] += w2 * (dmi.x * dmj.x + dmi.y * dmj.y);
             }
+#pragma unroll
+            for (int k = 0; k < 5; ++k) two_sum_acc(S[k], Cc[k], cs[k]);
             if (c + 1 < nc) {
                 ch = chn;
                 box = boxn;

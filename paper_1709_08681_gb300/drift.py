@@ -110,5 +110,13 @@ def run(name="drift197_l128ch", seed=0, log=None, **over):
 
 
 if __name__ == "__main__":
+    import argparse
     import json
-    print(json.dumps(run()))
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--n-time", type=int, default=None, help="time steps (reduced sizes; 60 per interval)")
+    ap.add_argument("--seed", type=int, default=0)
+    args = ap.parse_args()
+    over = {}
+    if args.n_time:
+        over = {"n_time": args.n_time, "n_interval": max(1, args.n_time // 60)}
+    print(json.dumps(run(seed=args.seed, **over)))

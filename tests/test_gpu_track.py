@@ -47,7 +47,8 @@ def _check_sums(m, lm, vobs, w, got):
     R = vobs - V
     chi_scale = float(np.sum(w * np.abs(R) ** 2) + 2.0 * np.sum(w * np.abs(R) * np.abs(V)))
     assert abs(got[0] - chi2) < TOL * chi_scale
-    assert abs(got[0] - chi2) < TOL * chi2
+    if chi2 > 0.1 * chi_scale:                    # residuals not small against V: plain relative accuracy too
+        assert abs(got[0] - chi2) < TOL * chi2
     gscale = 2.0 * np.sum(w[None] * np.abs(R)[None] * np.abs(dV))
     assert np.max(np.abs(got[1] - g)) < TOL * gscale
     assert np.max(np.abs(got[2] - H)) < TOL * np.max(np.abs(H))
@@ -77,9 +78,8 @@ def test_track_kernel_matches_oracle_and_brick_kernel(case):
     gp.ctx.psc_set_track_tiling(kv)
     got = gp.ctx.psc_residual_grad(lm, dv, dw, 1.0, cross=True)
     _check_sums(m, lm, vobs, w, got)
-    # the brick kernel computes the same sums in another order
+    # the brick kernel computes the same sums in another order, to the same bar
     _check_sums(m, lm, vobs, w, brick)
-    assert abs(got[0] - brick[0]) < TOL * abs(brick[0])
     assert np.max(np.abs(got[2] - brick[2])) < TOL * np.max(np.abs(brick[2]))
     # predictions keep the brick kernel; switching back restores it bit for bit
     gp.ctx.psc_set_track_tiling(0)
