@@ -142,6 +142,98 @@ __device__ __forceinline__ int box_width(const Box &b) {
     return w <= 8 ? 8 : w <= 16 ? 16 : w <= kMaxBoxW ? 32 : 0;
 }
 
+__device__ __forceinline__ void sts_f2(uint32_t addr, float2 v) {
+    asm volatile("st.shared.v2.f32 [%0], {%1, %2};" :: "r"(addr), "f"(v.x), "f"(v.y) : "memory");
+}
+
+__device__ __forceinline__ unsigned tab_addr(unsigned tab_adj, float tf) {
+    return tab_adj + ((unsigned)__float_as_int(tf) << 3);
+}
+
+// One row of the tap pattern for a lane's two visibilities, unrolled: the
+// 2 kCW cells from shared address `row` (the row's first column a = 1 - kCW),
+// visibility v's first column at dxo.v = (x_v - a) ov.  Returns the row sums
+// P_v = sum A G' in p0, p1 and adds sum A dxo G' to su0, su1.
+template <int kCW>
+__device__ __forceinline__ void pat_row2(uint32_t row, float2 dxo, float2 dyo2, float2 step, uint32_t tab_adj,
+                                         float2 &p0, float2 &p1, float2 &su0, float2 &su1) {
+    const float2 magic = make_float2(8388608.0f, 8388608.0f);
+#pragma unroll
+    for (int k = 0; k < 2 * kCW; ++k) {
+        const float2 g = lds_f2(row + 8u * k);
+        const float2 s2 = ffma2(dxo, dxo, dyo2);
+        const float2 t = make_float2(sqrt_fast(s2.x), sqrt_fast(s2.y));
+        const float2 tf = fadd2_rz(t, magic);                       // floor(t) + 2^23, both
+        const float2 e0 = lds_f2(tab_addr(tab_adj, tf.x));
+        const float2 e1 = lds_f2(tab_addr(tab_adj, tf.y));
+        const float2 A = make_float2(fmaf(t.x, e0.y, e0.x), fmaf(t.y, e1.y, e1.x));
+        const float2 Ad = fmul2(A, dxo);
+        if (k == 0) {
+            p0 = fmul2(make_float2(A.x, A.x), g);
+            p1 = fmul2(make_float2(A.y, A.y), g);
+        } else {
+            fma2_acc(p0.x, p0.y, A.x, g.x, g.y);
+            fma2_acc(p1.x, p1.y, A.y, g.x, g.y);
+        }
+        fma2_acc(su0.x, su0.y, Ad.x, g.x, g.y);
+        fma2_acc(su1.x, su1.y, Ad.y, g.x, g.y);
+        dxo = fadd2(dxo, step);
+    }
+}
+
+// The same for one visibility per lane.
+template <int kCW>
+__device__ __forceinline__ void pat_row1(uint32_t row, float dxo, float dyo2, float ov, uint32_t tab_adj, float2 &p,
+                                         float2 &su) {
+#pragma unroll
+    for (int k = 0; k < 2 * kCW; ++k) {
+        const float2 g = lds_f2(row + 8u * k);
+        const float t = sqrt_fast(fmaf(dxo, dxo, dyo2));
+        const float2 e = lds_f2(tab_addr(tab_adj, __fadd_rz(t, 8388608.0f)));
+        const float A = fmaf(t, e.y, e.x);
+        if (k == 0) p = make_float2(A * g.x, A * g.y);
+        else fma2_acc(p.x, p.y, A, g.x, g.y);
+        fma2_acc(su.x, su.y, A * dxo, g.x, g.y);
+        dxo -= ov;
+    }
+}
+
+// Rows wider than the unrolled ones (apertures past 6 cells): the same taps in a loop.
+__device__ __forceinline__ void pat_row2_n(uint32_t row, int n, float2 dxo, float2 dyo2, float2 step, uint32_t tab_adj,
+                                           float2 &p0, float2 &p1, float2 &su0, float2 &su1) {
+    const float2 magic = make_float2(8388608.0f, 8388608.0f);
+    p0 = p1 = make_float2(0.f, 0.f);
+    for (int k = 0; k < n; ++k) {
+        const float2 g = lds_f2(row + 8u * k);
+        const float2 s2 = ffma2(dxo, dxo, dyo2);
+        const float2 t = make_float2(sqrt_fast(s2.x), sqrt_fast(s2.y));
+        const float2 tf = fadd2_rz(t, magic);
+        const float2 e0 = lds_f2(tab_addr(tab_adj, tf.x));
+        const float2 e1 = lds_f2(tab_addr(tab_adj, tf.y));
+        const float2 A = make_float2(fmaf(t.x, e0.y, e0.x), fmaf(t.y, e1.y, e1.x));
+        const float2 Ad = fmul2(A, dxo);
+        fma2_acc(p0.x, p0.y, A.x, g.x, g.y);
+        fma2_acc(p1.x, p1.y, A.y, g.x, g.y);
+        fma2_acc(su0.x, su0.y, Ad.x, g.x, g.y);
+        fma2_acc(su1.x, su1.y, Ad.y, g.x, g.y);
+        dxo = fadd2(dxo, step);
+    }
+}
+
+__device__ __forceinline__ void pat_row1_n(uint32_t row, int n, float dxo, float dyo2, float ov, uint32_t tab_adj,
+                                           float2 &p, float2 &su) {
+    p = make_float2(0.f, 0.f);
+    for (int k = 0; k < n; ++k) {
+        const float2 g = lds_f2(row + 8u * k);
+        const float t = sqrt_fast(fmaf(dxo, dxo, dyo2));
+        const float2 e = lds_f2(tab_addr(tab_adj, __fadd_rz(t, 8388608.0f)));
+        const float A = fmaf(t, e.y, e.x);
+        fma2_acc(p.x, p.y, A, g.x, g.y);
+        fma2_acc(su.x, su.y, A * dxo, g.x, g.y);
+        dxo -= ov;
+    }
+}
+
 template <int kV>
 __global__ void __launch_bounds__(kTrkThreads, 4)
 track_kernel(const EvalArgs a0, const EvalArgs *__restrict__ args, const long long *__restrict__ prefix, int n_ctx,
@@ -152,15 +244,15 @@ track_kernel(const EvalArgs a0, const EvalArgs *__restrict__ args, const long lo
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const bool persistent = queue != nullptr;
     EvalArgs &a = s_args[warp];
-    // this warp's two buffers: [tile cap][table tabc] each, from a 128-byte boundary
-    float2 *trk_dyn = reinterpret_cast<float2 *>(((uintptr_t)trk_raw + 127) & ~(uintptr_t)127);
-    float2 *buf0 = trk_dyn + (size_t)warp * 2 * (cap + tabc);
-    float2 *tile_b[2] = {buf0, buf0 + cap + tabc};
-    float2 *tab_b[2] = {buf0 + cap, buf0 + 2 * cap + tabc};
-    const uint32_t mb[2] = {saddr(&s_mbar[warp][0]), saddr(&s_mbar[warp][1])};
+    // this warp's two buffers, [tile cap][table tabc] each (shared addresses),
+    // from a 128-byte boundary
+    const uint32_t dyn0 = (saddr(trk_raw) + 127u) & ~127u;
+    const uint32_t buf_bytes = (uint32_t)(cap + tabc) * 8u;
+    const uint32_t tile0 = dyn0 + (uint32_t)warp * 2u * buf_bytes;
+    const uint32_t mb0 = saddr(&s_mbar[warp][0]), mb1 = saddr(&s_mbar[warp][1]);
     if (lane == 0) {
-        mbar_init(mb[0]);
-        mbar_init(mb[1]);
+        mbar_init(mb0);
+        mbar_init(mb1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         if (!persistent) a = a0;
     }
@@ -211,30 +303,36 @@ track_kernel(const EvalArgs a0, const EvalArgs *__restrict__ args, const long lo
         const float dL = (float)(li - lj), dM = (float)(mi - mj);     // decorrelation
         const int nt = a.nt, nc = a.nc, n_bl = a.n_bl, half = a.ng / 2;
         const float du = a.du, ov = (float)a.ov;
+        const float2 *vis_obs = a.vis_obs;
+        const float *wgt = a.w;
+        const float2 step2 = make_float2(-ov, -ov);
         const int tb = chunk * 32 * kV + lane * kV;
         float4 q[kV];
-        bool valid[kV];
+        float wv[kV];                  // weight scale of each visibility: 0 past the interval's end
+        size_t kb[kV];                 // its first channel in [nt][n_bl][nc]
 #pragma unroll
         for (int v = 0; v < kV; ++v) {
-            valid[v] = tb + v < nt;
-            q[v] = a.uvs[(size_t)min(tb + v, nt - 1) * n_bl + bl];     // past the end: repeat the last step
+            const int t = min(tb + v, nt - 1);         // past the end: repeat the last step, weight 0
+            wv[v] = tb + v < nt ? a.w_scale : 0.f;
+            q[v] = a.uvs[(size_t)t * n_bl + bl];
+            kb[v] = ((size_t)t * n_bl + bl) * nc;
         }
         float S[kRed], Cc[5];
 #pragma unroll
         for (int k = 0; k < kRed; ++k) S[k] = 0.f;
 #pragma unroll
         for (int k = 0; k < 5; ++k) Cc[k] = 0.f;
-        // per-tap ramp steps of the global-memory fallback
-        float zxs, zxc;
+        float zxs, zxc;                // per-tap ramp step of the global-memory fallback
         __sincosf(-pi_f * du * L, &zxs, &zxc);
+        const float dsq = dL * dL + dM * dM;
+        // pattern radius: the aperture's reach plus the largest distance between
+        // a lane's visibilities (consecutive time steps), plus a margin
+        const float spread = (float)(kV - 1) * a.trk_spread + 1e-3f;
 
         int nx[kV], ny[kV];
         float fx[kV], fy[kV];
         Box box;
         ChanConst ch = a.chan[0];
-        // pattern radius: the aperture's reach plus the largest distance between
-        // a lane's visibilities (consecutive time steps), plus a margin
-        const float spread = (float)(kV - 1) * a.trk_spread + 1e-3f;
         chan_pos<kV>(q, ch, half, ch.rho_max + spread, nx, fx, ny, fy, box);
         bool ok = true;
         // issues the copies of channel cc (box bx) into buffer bb
@@ -242,20 +340,21 @@ track_kernel(const EvalArgs a0, const EvalArgs *__restrict__ args, const long lo
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic writes before async-proxy writes
             __syncwarp();
             if (lane == 0) {
-                const int W = bx.empty ? 0 : box_width(bx);
+                const int W = box_width(bx);
                 const int ncp = (bx.y1 - bx.y0 + 1 + kBoxRows - 1) / kBoxRows;
                 const bool fits = W > 0 && W * kBoxRows * ncp <= a.trk_cap;
                 const int n_tab = min(a.trk_stride, (chc.tab_len + a.trk_pad + 1) & ~1);
                 const uint32_t tab_bytes = (uint32_t)n_tab * 8u;
                 const uint32_t box_bytes = fits ? (uint32_t)(W * kBoxRows * ncp) * 8u : 0u;
-                mbar_expect(mb[bb], tab_bytes + box_bytes);
+                const uint32_t mb = bb ? mb1 : mb0;
+                const uint32_t tile = tile0 + (uint32_t)bb * buf_bytes;
+                mbar_expect(mb, tab_bytes + box_bytes);
                 if (fits) {
                     const char *map = reinterpret_cast<const char *>(a.tmap) + (W == 8 ? 0 : W == 16 ? 128 : 256);
-                    const uint32_t dst = saddr(tile_b[bb]);
                     for (int k = 0; k < ncp; ++k)
-                        tma_box(dst + (uint32_t)(k * kBoxRows * W * 8), map, bx.x0, bx.y0 + k * kBoxRows, mb[bb]);
+                        tma_box(tile + (uint32_t)(k * kBoxRows * W * 8), map, bx.x0, bx.y0 + k * kBoxRows, mb);
                 }
-                bulk_copy(saddr(tab_b[bb]), a.tabs_cs + (size_t)cc * a.trk_stride, tab_bytes, mb[bb]);
+                bulk_copy(tile + (uint32_t)cap * 8u, a.tabs_cs + (size_t)cc * a.trk_stride, tab_bytes, mb);
             }
             pending |= 1u << bb;
         };
@@ -273,17 +372,17 @@ track_kernel(const EvalArgs a0, const EvalArgs *__restrict__ args, const long lo
                 chan_pos<kV>(q, chn, half, chn.rho_max + spread, nxn, fxn, nyn, fyn, boxn);
                 issue(c + 1, chn, boxn, b ^ 1);
             }
-            bool got = mbar_wait(mb[b], (par >> b) & 1u, a.wait_limit);
+            const bool got = mbar_wait(b ? mb1 : mb0, (par >> b) & 1u, a.wait_limit);
             if (__any_sync(kFull, !got)) { ok = false; break; }
             par ^= 1u << b;
             pending &= ~(1u << b);
 
             const float rmax = ch.rho_max, rmax2 = rmax * rmax;
-            const int W = box.empty ? 0 : box_width(box);
+            const int W = box_width(box);
             const int ncp = (box.y1 - box.y0 + 1 + kBoxRows - 1) / kBoxRows;
             const bool staged = W > 0 && W * kBoxRows * ncp <= a.trk_cap;
-            float2 *tile = tile_b[b];
-            const unsigned tab_adj = saddr(tab_b[b]) - (0x4B000000u << 3);
+            const uint32_t tile = tile0 + (uint32_t)b * buf_bytes;
+            const unsigned tab_adj = tile + (uint32_t)cap * 8u - (0x4B000000u << 3);
             float2 S0[kV], Su[kV], Sv[kV];
 #pragma unroll
             for (int v = 0; v < kV; ++v) S0[v] = Su[v] = Sv[v] = make_float2(0.f, 0.f);
@@ -300,11 +399,12 @@ track_kernel(const EvalArgs a0, const EvalArgs *__restrict__ args, const long lo
                     __sincosf(-pi_f * du * ((float)col * L + (float)r * M), &zs, &zc);
                     __sincosf(-pi_f * du * ((float)rstep * M), &ss, &sc);
                     float2 z = make_float2(zc, zs);
-                    const float2 step = make_float2(sc, ss);
-                    for (; r < rows; r += rstep) {
-                        float2 *cell = tile + r * W + col;
-                        *cell = cmul(*cell, z);
-                        z = cmul(z, step);
+                    const float2 stp = make_float2(sc, ss);
+                    uint32_t cell = tile + (uint32_t)(r * W + col) * 8u;
+                    const uint32_t cstep = (uint32_t)(rstep * W) * 8u;
+                    for (; r < rows; r += rstep, cell += cstep) {
+                        sts_f2(cell, cmul(lds_f2(cell), z));
+                        z = cmul(z, stp);
                     }
                 }
                 __syncwarp();
@@ -324,41 +424,65 @@ track_kernel(const EvalArgs a0, const EvalArgs *__restrict__ args, const long lo
                 // past rp + sqrt(2) + spread).
                 const float rp = rmax + spread, rp2 = rp * rp;
                 const int R = (int)ceilf(rp);
-                float ux[kV], uy[kV];                  // visibilities relative to the base cell
-#pragma unroll
-                for (int v = 0; v < kV; ++v) {
-                    ux[v] = (float)(nx[v] - nx[0]) + fx[v];
-                    uy[v] = (float)(ny[v] - ny[0]) + fy[v];
-                }
-                const float2 *base = tile + (ny[0] - box.y0) * W + (nx[0] - box.x0);
-                for (int rb = 1 - R; rb <= R; ++rb) {
-                    const float d = rb <= 0 ? (float)(-rb) : (float)(rb - 1);
-                    const float rem = rp2 - d * d;
-                    const int cw = (int)ceilf(rem * rsqrt_fast(rem));
-                    const int a_lo = 1 - cw;
-                    float dy[kV], dyo2[kV], dxo[kV], pr[kV], pi[kV], qr[kV], qi[kV];
-#pragma unroll
-                    for (int v = 0; v < kV; ++v) {
-                        dy[v] = uy[v] - (float)rb;
-                        const float dyo = dy[v] * ov;
-                        dyo2[v] = fmaf(dyo, dyo, 1e-20f);
-                        dxo[v] = (ux[v] - (float)a_lo) * ov;
-                        pr[v] = pi[v] = qr[v] = qi[v] = 0.f;
+                const uint32_t base = tile + (uint32_t)((ny[0] - box.y0) * W + (nx[0] - box.x0)) * 8u;
+                if constexpr (kV == 2) {
+                    const float2 ux = make_float2(fx[0], (float)(nx[1] - nx[0]) + fx[1]);
+                    const float2 uy = make_float2(fy[0], (float)(ny[1] - ny[0]) + fy[1]);
+                    const float2 ov2 = make_float2(ov, ov);
+                    float2 su0 = make_float2(0.f, 0.f), su1 = su0, s00 = su0, s01 = su0, sv0 = su0, sv1 = su0;
+                    for (int rb = 1 - R; rb <= R; ++rb) {
+                        const float d = (float)(rb <= 0 ? -rb : rb - 1);
+                        const float rem = fmaf(-d, d, rp2);
+                        const int cw = (int)ceilf(rem * rsqrt_fast(rem));
+                        const float fb = (float)rb, fa = (float)(1 - cw);
+                        const float2 dy = fadd2(uy, make_float2(-fb, -fb));
+                        const float2 dyo = fmul2(dy, ov2);
+                        const float2 dyo2 = ffma2(dyo, dyo, make_float2(1e-20f, 1e-20f));
+                        const float2 dxo = fmul2(fadd2(ux, make_float2(-fa, -fa)), ov2);
+                        const uint32_t row = base + (uint32_t)(rb * W + 1 - cw) * 8u;
+                        float2 p0, p1;
+                        switch (cw) {
+                            case 1: pat_row2<1>(row, dxo, dyo2, step2, tab_adj, p0, p1, su0, su1); break;
+                            case 2: pat_row2<2>(row, dxo, dyo2, step2, tab_adj, p0, p1, su0, su1); break;
+                            case 3: pat_row2<3>(row, dxo, dyo2, step2, tab_adj, p0, p1, su0, su1); break;
+                            case 4: pat_row2<4>(row, dxo, dyo2, step2, tab_adj, p0, p1, su0, su1); break;
+                            case 5: pat_row2<5>(row, dxo, dyo2, step2, tab_adj, p0, p1, su0, su1); break;
+                            case 6: pat_row2<6>(row, dxo, dyo2, step2, tab_adj, p0, p1, su0, su1); break;
+                            default: pat_row2_n(row, 2 * cw, dxo, dyo2, step2, tab_adj, p0, p1, su0, su1);
+                        }
+                        s00 = fadd2(s00, p0);
+                        s01 = fadd2(s01, p1);
+                        sv0 = ffma2(make_float2(dy.x, dy.x), p0, sv0);
+                        sv1 = ffma2(make_float2(dy.y, dy.y), p1, sv1);
                     }
-                    if constexpr (kV == 2)
-                        row_taps2(base + rb * W + a_lo, 2 * cw, make_float2(dxo[0], dxo[1]),
-                                  make_float2(dyo2[0], dyo2[1]), ov, tab_adj, pr, pi, qr, qi);
-                    else
-                        row_taps<kV>(base + rb * W + a_lo, 2 * cw, dxo, dyo2, ov, tab_adj, pr, pi, qr, qi);
-#pragma unroll
-                    for (int v = 0; v < kV; ++v) {
-                        S0[v].x += pr[v]; S0[v].y += pi[v];
-                        Su[v].x += qr[v]; Su[v].y += qi[v];
-                        Sv[v].x = fmaf(dy[v], pr[v], Sv[v].x);
-                        Sv[v].y = fmaf(dy[v], pi[v], Sv[v].y);
+                    S0[0] = s00; S0[1] = s01; Su[0] = su0; Su[1] = su1; Sv[0] = sv0; Sv[1] = sv1;
+                } else {
+                    const float ux = fx[0], uy = fy[0];
+                    for (int rb = 1 - R; rb <= R; ++rb) {
+                        const float d = (float)(rb <= 0 ? -rb : rb - 1);
+                        const float rem = fmaf(-d, d, rp2);
+                        const int cw = (int)ceilf(rem * rsqrt_fast(rem));
+                        const float dy = uy - (float)rb;
+                        const float dyo = dy * ov;
+                        const float dyo2 = fmaf(dyo, dyo, 1e-20f);
+                        const float dxo = (ux - (float)(1 - cw)) * ov;
+                        const uint32_t row = base + (uint32_t)(rb * W + 1 - cw) * 8u;
+                        float2 p;
+                        switch (cw) {
+                            case 1: pat_row1<1>(row, dxo, dyo2, ov, tab_adj, p, Su[0]); break;
+                            case 2: pat_row1<2>(row, dxo, dyo2, ov, tab_adj, p, Su[0]); break;
+                            case 3: pat_row1<3>(row, dxo, dyo2, ov, tab_adj, p, Su[0]); break;
+                            case 4: pat_row1<4>(row, dxo, dyo2, ov, tab_adj, p, Su[0]); break;
+                            case 5: pat_row1<5>(row, dxo, dyo2, ov, tab_adj, p, Su[0]); break;
+                            case 6: pat_row1<6>(row, dxo, dyo2, ov, tab_adj, p, Su[0]); break;
+                            default: pat_row1_n(row, 2 * cw, dxo, dyo2, ov, tab_adj, p, Su[0]);
+                        }
+                        S0[0].x += p.x; S0[0].y += p.y;
+                        Sv[0].x = fmaf(dy, p.x, Sv[0].x);
+                        Sv[0].y = fmaf(dy, p.y, Sv[0].y);
                     }
                 }
-            } else if (!box.empty) {
+            } else {
                 // fallback: taps read the grid (L1/L2), ramp per tap from each
                 // visibility's own cell (nx, ny)
 #pragma unroll
@@ -382,15 +506,14 @@ track_kernel(const EvalArgs a0, const EvalArgs *__restrict__ args, const long lo
                         float2 z = make_float2(zc, zs);
                         const float2 zx = make_float2(zxc, zxs);
                         float pr = 0.f, pi = 0.f, qr = 0.f, qi = 0.f;
-                        const float2 *row = a.grid + (size_t)(ny[v] + bb) * a.ng + nx[v];
+                        const float2 *rowp = a.grid + (size_t)(ny[v] + bb) * a.ng + nx[v];
                         float dd = (fx[v] - (float)a_lo) * ov;
                         for (int aa = a_lo; aa <= a_hi; ++aa, dd -= ov) {
-                            const float2 g = cmul(__ldg(&row[aa]), z);
+                            const float2 g = cmul(__ldg(&rowp[aa]), z);
                             z = cmul(z, zx);
                             const float s2 = fmaf(dd, dd, dyo2);
                             const float tv = sqrt_fast(s2);
-                            const float tf = __fadd_rz(tv, 8388608.0f);
-                            const float2 e = lds_f2(tab_adj + ((unsigned)__float_as_int(tf) << 3));
+                            const float2 e = lds_f2(tab_addr(tab_adj, __fadd_rz(tv, 8388608.0f)));
                             const float A = fmaf(tv, e.y, e.x);
                             pr = fmaf(A, g.x, pr);
                             pi = fmaf(A, g.y, pi);
@@ -404,30 +527,25 @@ track_kernel(const EvalArgs a0, const EvalArgs *__restrict__ args, const long lo
                         Sv[v].y = fmaf(dy, pi, Sv[v].y);
                     }
                 }
-            } else {
-#pragma unroll
-                for (int v = 0; v < kV; ++v) hx[v] = hy[v] = 0.f;
             }
 
             // ---- epilogue: visibility half of the ramp, decorrelation, derivatives ----
-            const float inv_ov = 1.0f / ov;
             const float al2 = ch.alpha2;
             float D = 1.f, el = 0.f, em = 0.f;
             if (a.decorrelation) {
-                D = expf(-0.5f * al2 * (dL * dL + dM * dM));
+                D = __expf(-0.5f * al2 * dsq);
                 el = -dL * al2;                      // (l_j - l_i) alpha^2
                 em = -dM * al2;
             }
+            const float su = du / ov;                // Q was accumulated with dx * ov; taps in wavelengths
             float cs[5] = {0.f, 0.f, 0.f, 0.f, 0.f};   // this channel's chi^2 and gradient terms
 #pragma unroll
             for (int v = 0; v < kV; ++v) {
-                if (!valid[v]) continue;
                 float s, co;
                 __sincosf(pi_f * du * (hx[v] * L + hy[v] * M), &s, &co);
                 const float2 ph = make_float2(co, s);
                 const float2 T0 = cmul(ph, S0[v]);
                 float2 Tu = cmul(ph, Su[v]), Tv = cmul(ph, Sv[v]);
-                const float su = du * inv_ov;        // Q was accumulated with dx * ov; taps in wavelengths
                 Tu.x *= su; Tu.y *= su;
                 Tv.x *= du; Tv.y *= du;
                 const float2 V = make_float2(D * T0.x, D * T0.y);
@@ -435,9 +553,9 @@ track_kernel(const EvalArgs a0, const EvalArgs *__restrict__ args, const long lo
                 const float2 dmi = make_float2(D * (em * T0.x - pi_f * Tv.y), D * (em * T0.y + pi_f * Tv.x));
                 const float2 dlj = make_float2(D * (-el * T0.x - pi_f * Tu.y), D * (-el * T0.y + pi_f * Tu.x));
                 const float2 dmj = make_float2(D * (-em * T0.x - pi_f * Tv.y), D * (-em * T0.y + pi_f * Tv.x));
-                const size_t k = ((size_t)(tb + v) * n_bl + bl) * nc + c;
-                const float2 vo = a.vis_obs[k];
-                const float w = a.w_scale * (a.w != nullptr ? a.w[k] : 1.f);
+                const size_t k = kb[v] + c;
+                const float2 vo = vis_obs[k];
+                const float w = wv[v] * (wgt != nullptr ? wgt[k] : 1.f);
                 const float2 R = make_float2(vo.x - V.x, vo.y - V.y);
                 const float w2 = 2.f * w;
                 cs[0] += w * (R.x * R.x + R.y * R.y);
@@ -472,7 +590,7 @@ track_kernel(const EvalArgs a0, const EvalArgs *__restrict__ args, const long lo
             // copies still in flight, and stop
             if (lane == 0) atomicExch(a.err, 1);
             for (int bb = 0; bb < 2; ++bb)
-                if (pending & (1u << bb)) mbar_wait(mb[bb], (par >> bb) & 1u, kDrainPolls);
+                if (pending & (1u << bb)) mbar_wait(bb ? mb1 : mb0, (par >> bb) & 1u, kDrainPolls);
             __syncwarp();
             return;
         }
