@@ -64,11 +64,15 @@ __device__ __forceinline__ void mbar_expect(uint32_t mb, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(mb), "r"(bytes) : "memory");
 }
 
+// Bounded wait for a phase of mbarrier mb: at most `limit` polls, each of
+// which may suspend the warp for up to a microsecond (a hint to the
+// hardware) instead of spinning.
 __device__ __forceinline__ bool mbar_wait(uint32_t mb, uint32_t parity, long long limit) {
     for (long long it = 0; it < limit; ++it) {
         uint32_t ok;
-        asm volatile("{\n.reg .pred q;\nmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\nselp.u32 %0, 1, 0, q;\n}"
-                     : "=r"(ok) : "r"(mb), "r"(parity) : "memory");
+        asm volatile("{\n.reg .pred q;\nmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2, %3;\n"
+                     "selp.u32 %0, 1, 0, q;\n}"
+                     : "=r"(ok) : "r"(mb), "r"(parity), "r"(1000u) : "memory");
         if (ok) return true;
     }
     return false;
@@ -339,23 +343,23 @@ track_kernel(const EvalArgs a0, const EvalArgs *__restrict__ args, const long lo
         auto issue = [&](int cc, const ChanConst &chc, const Box &bx, int bb) {
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic writes before async-proxy writes
             __syncwarp();
-            if (lane == 0) {
-                const int W = box_width(bx);
-                const int ncp = (bx.y1 - bx.y0 + 1 + kBoxRows - 1) / kBoxRows;
-                const bool fits = W > 0 && W * kBoxRows * ncp <= a.trk_cap;
-                const int n_tab = min(a.trk_stride, (chc.tab_len + a.trk_pad + 1) & ~1);
-                const uint32_t tab_bytes = (uint32_t)n_tab * 8u;
-                const uint32_t box_bytes = fits ? (uint32_t)(W * kBoxRows * ncp) * 8u : 0u;
-                const uint32_t mb = bb ? mb1 : mb0;
-                const uint32_t tile = tile0 + (uint32_t)bb * buf_bytes;
-                mbar_expect(mb, tab_bytes + box_bytes);
-                if (fits) {
-                    const char *map = reinterpret_cast<const char *>(a.tmap) + (W == 8 ? 0 : W == 16 ? 128 : 256);
-                    for (int k = 0; k < ncp; ++k)
-                        tma_box(tile + (uint32_t)(k * kBoxRows * W * 8), map, bx.x0, bx.y0 + k * kBoxRows, mb);
-                }
-                bulk_copy(tile + (uint32_t)cap * 8u, a.tabs_cs + (size_t)cc * a.trk_stride, tab_bytes, mb);
+            // lane 0 arrives with the expected bytes; lanes 0..ncp-1 copy one
+            // 8-row box each and lane 31 the table (a phase completes once the
+            // arrival and all bytes are in, in whatever order)
+            const int W = box_width(bx);
+            const int ncp = (bx.y1 - bx.y0 + 1 + kBoxRows - 1) / kBoxRows;
+            const bool fits = W > 0 && W * kBoxRows * ncp <= a.trk_cap;
+            const int n_tab = min(a.trk_stride, (chc.tab_len + a.trk_pad + 1) & ~1);
+            const uint32_t tab_bytes = (uint32_t)n_tab * 8u;
+            const uint32_t mb = bb ? mb1 : mb0;
+            const uint32_t tile = tile0 + (uint32_t)bb * buf_bytes;
+            if (lane == 0) mbar_expect(mb, tab_bytes + (fits ? (uint32_t)(W * kBoxRows * ncp) * 8u : 0u));
+            __syncwarp();
+            if (fits && lane < ncp) {
+                const char *map = reinterpret_cast<const char *>(a.tmap) + (W == 8 ? 0 : W == 16 ? 128 : 256);
+                tma_box(tile + (uint32_t)(lane * kBoxRows * W * 8), map, bx.x0, bx.y0 + lane * kBoxRows, mb);
             }
+            if (lane == 31) bulk_copy(tile + (uint32_t)cap * 8u, a.tabs_cs + (size_t)cc * a.trk_stride, tab_bytes, mb);
             pending |= 1u << bb;
         };
         issue(0, ch, box, 0);
@@ -529,7 +533,15 @@ track_kernel(const EvalArgs a0, const EvalArgs *__restrict__ args, const long lo
                 }
             }
 
-            // ---- epilogue: visibility half of the ramp, decorrelation, derivatives ----
+            // ---- epilogue: visibility half of the ramp, residuals, sums ----
+            // With T = T0, Px = i pi Tu, Py = i pi Tv (Tu, Tv in wavelengths) the
+            // derivatives are dV/dl_i = D (el T + Px), dV/dl_j = D (-el T + Px),
+            // dV/dm_i = D (em T + Py), dV/dm_j = D (-em T + Py), with D, el, em
+            // fixed for the baseline and channel.  So every chi^2, gradient and
+            // normal sum of the channel follows from the weighted inner
+            // products <X, Y> = Re(conj(X) Y) of R, T, Px, Py summed over the
+            // lane's visibilities: <R,R>, <R,T>, <R,Px>, <R,Py>, <T,T>, <T,Px>,
+            // <T,Py>, <Px,Px>, <Px,Py>, <Py,Py>.
             const float al2 = ch.alpha2;
             float D = 1.f, el = 0.f, em = 0.f;
             if (a.decorrelation) {
@@ -537,45 +549,57 @@ track_kernel(const EvalArgs a0, const EvalArgs *__restrict__ args, const long lo
                 el = -dL * al2;                      // (l_j - l_i) alpha^2
                 em = -dM * al2;
             }
-            const float su = du / ov;                // Q was accumulated with dx * ov; taps in wavelengths
-            float cs[5] = {0.f, 0.f, 0.f, 0.f, 0.f};   // this channel's chi^2 and gradient terms
+            const float su = pi_f * du / ov;         // Q was accumulated with dx ov; Px = i pi Tu
+            const float sv = pi_f * du;
+            float rr = 0.f, rt = 0.f, rx = 0.f, ry = 0.f, tt = 0.f, tx = 0.f, ty = 0.f, xx = 0.f, xy = 0.f, yy = 0.f;
 #pragma unroll
             for (int v = 0; v < kV; ++v) {
                 float s, co;
                 __sincosf(pi_f * du * (hx[v] * L + hy[v] * M), &s, &co);
                 const float2 ph = make_float2(co, s);
-                const float2 T0 = cmul(ph, S0[v]);
-                float2 Tu = cmul(ph, Su[v]), Tv = cmul(ph, Sv[v]);
-                Tu.x *= su; Tu.y *= su;
-                Tv.x *= du; Tv.y *= du;
-                const float2 V = make_float2(D * T0.x, D * T0.y);
-                const float2 dli = make_float2(D * (el * T0.x - pi_f * Tu.y), D * (el * T0.y + pi_f * Tu.x));
-                const float2 dmi = make_float2(D * (em * T0.x - pi_f * Tv.y), D * (em * T0.y + pi_f * Tv.x));
-                const float2 dlj = make_float2(D * (-el * T0.x - pi_f * Tu.y), D * (-el * T0.y + pi_f * Tu.x));
-                const float2 dmj = make_float2(D * (-em * T0.x - pi_f * Tv.y), D * (-em * T0.y + pi_f * Tv.x));
+                const float2 T = cmul(ph, S0[v]);
+                const float2 U = cmul(ph, Su[v]), W2 = cmul(ph, Sv[v]);
+                const float2 Px = make_float2(-su * U.y, su * U.x);
+                const float2 Py = make_float2(-sv * W2.y, sv * W2.x);
                 const size_t k = kb[v] + c;
                 const float2 vo = vis_obs[k];
                 const float w = wv[v] * (wgt != nullptr ? wgt[k] : 1.f);
-                const float2 R = make_float2(vo.x - V.x, vo.y - V.y);
-                const float w2 = 2.f * w;
-                cs[0] += w * (R.x * R.x + R.y * R.y);
-                cs[1] -= w2 * (R.x * dli.x + R.y * dli.y);
-                cs[2] -= w2 * (R.x * dmi.x + R.y * dmi.y);
-                cs[3] -= w2 * (R.x * dlj.x + R.y * dlj.y);
-                cs[4] -= w2 * (R.x * dmj.x + R.y * dmj.y);
-                S[5] += w2 * (dli.x * dli.x + dli.y * dli.y);
-                S[6] += w2 * (dli.x * dmi.x + dli.y * dmi.y);
-                S[7] += w2 * (dmi.x * dmi.x + dmi.y * dmi.y);
-                S[8] += w2 * (dlj.x * dlj.x + dlj.y * dlj.y);
-                S[9] += w2 * (dlj.x * dmj.x + dlj.y * dmj.y);
-                S[10] += w2 * (dmj.x * dmj.x + dmj.y * dmj.y);
-                S[11] += w2 * (dli.x * dlj.x + dli.y * dlj.y);
-                S[12] += w2 * (dli.x * dmj.x + dli.y * dmj.y);
-                S[13] += w2 * (dmi.x * dlj.x + dmi.y * dlj.y);
-                S[14] += w2 * (dmi.x * dmj.x + dmi.y * dmj.y);
+                const float2 R = make_float2(fmaf(-D, T.x, vo.x), fmaf(-D, T.y, vo.y));
+                const float2 wR = make_float2(w * R.x, w * R.y);
+                const float2 wT = make_float2(w * T.x, w * T.y);
+                const float2 wX = make_float2(w * Px.x, w * Px.y);
+                rr = fmaf(wR.x, R.x, fmaf(wR.y, R.y, rr));
+                rt = fmaf(wR.x, T.x, fmaf(wR.y, T.y, rt));
+                rx = fmaf(wR.x, Px.x, fmaf(wR.y, Px.y, rx));
+                ry = fmaf(wR.x, Py.x, fmaf(wR.y, Py.y, ry));
+                tt = fmaf(wT.x, T.x, fmaf(wT.y, T.y, tt));
+                tx = fmaf(wT.x, Px.x, fmaf(wT.y, Px.y, tx));
+                ty = fmaf(wT.x, Py.x, fmaf(wT.y, Py.y, ty));
+                xx = fmaf(wX.x, Px.x, fmaf(wX.y, Px.y, xx));
+                xy = fmaf(wX.x, Py.x, fmaf(wX.y, Py.y, xy));
+                yy = fmaf(w * Py.x, Py.x, fmaf(w * Py.y, Py.y, yy));
             }
-#pragma unroll
-            for (int k = 0; k < 5; ++k) two_sum_acc(S[k], Cc[k], cs[k]);
+            // chi^2 and the gradient (compensated), the normal blocks (plain)
+            const float g2 = -2.f * D, h2 = 2.f * D * D;
+            two_sum_acc(S[0], Cc[0], rr);
+            two_sum_acc(S[1], Cc[1], g2 * fmaf(el, rt, rx));
+            two_sum_acc(S[2], Cc[2], g2 * fmaf(em, rt, ry));
+            two_sum_acc(S[3], Cc[3], g2 * fmaf(-el, rt, rx));
+            two_sum_acc(S[4], Cc[4], g2 * fmaf(-em, rt, ry));
+            const float ett = el * el * tt, mtt = em * em * tt, emt = el * em * tt;
+            const float etx = 2.f * el * tx, mty = 2.f * em * ty;
+            const float cxy = fmaf(el, ty, em * tx);
+            const float dxy = fmaf(el, ty, -em * tx);
+            S[5] += h2 * (ett + etx + xx);           // l_i l_i
+            S[6] += h2 * (emt + cxy + xy);           // l_i m_i
+            S[7] += h2 * (mtt + mty + yy);           // m_i m_i
+            S[8] += h2 * (ett - etx + xx);           // l_j l_j
+            S[9] += h2 * (emt - cxy + xy);           // l_j m_j
+            S[10] += h2 * (mtt - mty + yy);          // m_j m_j
+            S[11] += h2 * (xx - ett);                // l_i l_j
+            S[12] += h2 * (dxy - emt + xy);          // l_i m_j
+            S[13] += h2 * (-dxy - emt + xy);         // m_i l_j
+            S[14] += h2 * (yy - mtt);                // m_i m_j
             if (c + 1 < nc) {
                 ch = chn;
                 box = boxn;
