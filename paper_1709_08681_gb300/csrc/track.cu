@@ -116,28 +116,24 @@ __device__ __forceinline__ void two_sum_acc(float &s, float &c, float x) {
 
 struct Box {
     int x0, x1, y0, y1;   // inclusive cell range of the warp's footprint; x0 rounded down to even
-    bool empty;
 };
 
-// Positions of the lane's visibilities in channel ch, and the warp's
-// footprint: the union over lanes of each lane's tap pattern, the cells
-// (n0 + a, m0 + b) with a, b in [1 - R, R] around the base cell (n0, m0) of
-// its first visibility (R = ceil of the pattern radius rp, see tap_pattern).
-template <int kV>
-__device__ __forceinline__ void chan_pos(const float4 (&q)[kV], const ChanConst &ch, int half, float rp,
-                                         int (&nx)[kV], float (&fx)[kV], int (&ny)[kV], float (&fy)[kV], Box &b) {
-#pragma unroll
-    for (int v = 0; v < kV; ++v) {
-        trk_pos(q[v].x, q[v].y, ch.sc_hi, ch.sc_lo, half, nx[v], fx[v]);
-        trk_pos(q[v].z, q[v].w, ch.sc_hi, ch.sc_lo, half, ny[v], fy[v]);
-    }
+// The warp's footprint in a channel of scale (sh, sl): the union over lanes
+// of each lane's tap pattern, the cells (n0 + a, m0 + b), a, b in [1 - R, R],
+// around the base cell (n0, m0) of its first visibility (u, v split q0; R the
+// ceiling of the pattern radius rp, see the tap pattern below).
+__device__ __forceinline__ Box chan_box(const float4 &q0, float sh, float sl, int half, float rp) {
+    int n0, m0;
+    float f0, g0;
+    trk_pos(q0.x, q0.y, sh, sl, half, n0, f0);
+    trk_pos(q0.z, q0.w, sh, sl, half, m0, g0);
     const int R = (int)ceilf(rp);
-    const int x0 = __reduce_min_sync(kFull, nx[0] + 1 - R);
-    b.x1 = __reduce_max_sync(kFull, nx[0] + R);
-    b.y0 = __reduce_min_sync(kFull, ny[0] + 1 - R);
-    b.y1 = __reduce_max_sync(kFull, ny[0] + R);
-    b.empty = false;
-    b.x0 = x0 & ~1;                           // TMA: the box's first column at a 16-byte boundary
+    Box b;
+    b.x0 = __reduce_min_sync(kFull, n0 + 1 - R) & ~1;     // TMA: the first column at a 16-byte boundary
+    b.x1 = __reduce_max_sync(kFull, n0 + R);
+    b.y0 = __reduce_min_sync(kFull, m0 + 1 - R);
+    b.y1 = __reduce_max_sync(kFull, m0 + R);
+    return b;
 }
 
 // Box width class (8, 16 or 32 cells; 0 = does not fit) and its TMA copies.
@@ -307,40 +303,30 @@ track_kernel(const EvalArgs a0, const EvalArgs *__restrict__ args, const long lo
         const float dL = (float)(li - lj), dM = (float)(mi - mj);     // decorrelation
         const int nt = a.nt, nc = a.nc, n_bl = a.n_bl, half = a.ng / 2;
         const float du = a.du, ov = (float)a.ov;
-        const float2 *vis_obs = a.vis_obs;
-        const float *wgt = a.w;
-        const float2 step2 = make_float2(-ov, -ov);
         const int tb = chunk * 32 * kV + lane * kV;
-        float4 q[kV];
-        float wv[kV];                  // weight scale of each visibility: 0 past the interval's end
-        size_t kb[kV];                 // its first channel in [nt][n_bl][nc]
-#pragma unroll
-        for (int v = 0; v < kV; ++v) {
-            const int t = min(tb + v, nt - 1);         // past the end: repeat the last step, weight 0
-            wv[v] = tb + v < nt ? a.w_scale : 0.f;
-            q[v] = a.uvs[(size_t)t * n_bl + bl];
-            kb[v] = ((size_t)t * n_bl + bl) * nc;
-        }
-        float S[kRed], Cc[5];
-#pragma unroll
-        for (int k = 0; k < kRed; ++k) S[k] = 0.f;
-#pragma unroll
-        for (int k = 0; k < 5; ++k) Cc[k] = 0.f;
-        float zxs, zxc;                // per-tap ramp step of the global-memory fallback
-        __sincosf(-pi_f * du * L, &zxs, &zxc);
-        const float dsq = dL * dL + dM * dM;
+        // rows of the lane's visibilities in uvs (past the interval's end: the
+        // last step again, with weight 0) and of their first channel in vis_obs
+        const int t0 = min(tb, nt - 1);
+        const int tstep = kV == 2 && tb + 1 < nt ? 1 : 0;
+        const float4 *uvs0 = a.uvs + (size_t)t0 * n_bl + bl;
+        const size_t uvs_step = (size_t)tstep * n_bl;
+        const size_t kb0 = ((size_t)t0 * n_bl + bl) * nc;
+        const size_t kstep = uvs_step * nc;
+        const float wv0 = tb < nt ? a.w_scale : 0.f;
+        const float wv1 = tb + 1 < nt ? a.w_scale : 0.f;
+        // the lane's running sums (see the epilogue): chi^2 and the gradient
+        // moments compensated (TwoSum), the normal-equation moments plain
+        float chi_s = 0.f, chi_c = 0.f, e0s = 0.f, e0c = 0.f, e1s = 0.f, e1c = 0.f, e2s = 0.f, e2c = 0.f;
+        float hA0 = 0.f, hA1 = 0.f, hA2 = 0.f, hB1 = 0.f, hB2 = 0.f, hC = 0.f;
         // pattern radius: the aperture's reach plus the largest distance between
         // a lane's visibilities (consecutive time steps), plus a margin
         const float spread = (float)(kV - 1) * a.trk_spread + 1e-3f;
 
-        int nx[kV], ny[kV];
-        float fx[kV], fy[kV];
-        Box box;
         ChanConst ch = a.chan[0];
-        chan_pos<kV>(q, ch, half, ch.rho_max + spread, nx, fx, ny, fy, box);
+        Box box = chan_box(uvs0[0], ch.sc_hi, ch.sc_lo, half, ch.rho_max + spread);
         bool ok = true;
-        // issues the copies of channel cc (box bx) into buffer bb
-        auto issue = [&](int cc, const ChanConst &chc, const Box &bx, int bb) {
+        // issues the copies of channel cc (box bx, table length tl) into buffer bb
+        auto issue = [&](int cc, int tl, const Box &bx, int bb) {
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic writes before async-proxy writes
             __syncwarp();
             // lane 0 arrives with the expected bytes; lanes 0..ncp-1 copy one
@@ -349,7 +335,7 @@ track_kernel(const EvalArgs a0, const EvalArgs *__restrict__ args, const long lo
             const int W = box_width(bx);
             const int ncp = (bx.y1 - bx.y0 + 1 + kBoxRows - 1) / kBoxRows;
             const bool fits = W > 0 && W * kBoxRows * ncp <= a.trk_cap;
-            const int n_tab = min(a.trk_stride, (chc.tab_len + a.trk_pad + 1) & ~1);
+            const int n_tab = min(a.trk_stride, (tl + a.trk_pad + 1) & ~1);
             const uint32_t tab_bytes = (uint32_t)n_tab * 8u;
             const uint32_t mb = bb ? mb1 : mb0;
             const uint32_t tile = tile0 + (uint32_t)bb * buf_bytes;
@@ -362,25 +348,32 @@ track_kernel(const EvalArgs a0, const EvalArgs *__restrict__ args, const long lo
             if (lane == 31) bulk_copy(tile + (uint32_t)cap * 8u, a.tabs_cs + (size_t)cc * a.trk_stride, tab_bytes, mb);
             pending |= 1u << bb;
         };
-        issue(0, ch, box, 0);
+        issue(0, ch.tab_len, box, 0);
 
         for (int c = 0; c < nc; ++c) {
             const int b = c & 1;
             // prefetch channel c + 1 into the other buffer (its last reader was channel c - 1)
-            int nxn[kV], nyn[kV];
-            float fxn[kV], fyn[kV];
             Box boxn = box;
             ChanConst chn = ch;
             if (c + 1 < nc) {
                 chn = a.chan[c + 1];
-                chan_pos<kV>(q, chn, half, chn.rho_max + spread, nxn, fxn, nyn, fyn, boxn);
-                issue(c + 1, chn, boxn, b ^ 1);
+                boxn = chan_box(uvs0[0], chn.sc_hi, chn.sc_lo, half, chn.rho_max + spread);
+                issue(c + 1, chn.tab_len, boxn, b ^ 1);
             }
             const bool got = mbar_wait(b ? mb1 : mb0, (par >> b) & 1u, a.wait_limit);
             if (__any_sync(kFull, !got)) { ok = false; break; }
             par ^= 1u << b;
             pending &= ~(1u << b);
 
+            // positions of the lane's visibilities in this channel
+            int nx[kV], ny[kV];
+            float fx[kV], fy[kV];
+#pragma unroll
+            for (int v = 0; v < kV; ++v) {
+                const float4 q = uvs0[v * uvs_step];
+                trk_pos(q.x, q.y, ch.sc_hi, ch.sc_lo, half, nx[v], fx[v]);
+                trk_pos(q.z, q.w, ch.sc_hi, ch.sc_lo, half, ny[v], fy[v]);
+            }
             const float rmax = ch.rho_max, rmax2 = rmax * rmax;
             const int W = box_width(box);
             const int ncp = (box.y1 - box.y0 + 1 + kBoxRows - 1) / kBoxRows;
@@ -432,7 +425,7 @@ track_kernel(const EvalArgs a0, const EvalArgs *__restrict__ args, const long lo
                 if constexpr (kV == 2) {
                     const float2 ux = make_float2(fx[0], (float)(nx[1] - nx[0]) + fx[1]);
                     const float2 uy = make_float2(fy[0], (float)(ny[1] - ny[0]) + fy[1]);
-                    const float2 ov2 = make_float2(ov, ov);
+                    const float2 ov2 = make_float2(ov, ov), step2 = make_float2(-ov, -ov);
                     float2 su0 = make_float2(0.f, 0.f), su1 = su0, s00 = su0, s01 = su0, sv0 = su0, sv1 = su0;
                     for (int rb = 1 - R; rb <= R; ++rb) {
                         const float d = (float)(rb <= 0 ? -rb : rb - 1);
@@ -489,6 +482,9 @@ track_kernel(const EvalArgs a0, const EvalArgs *__restrict__ args, const long lo
             } else {
                 // fallback: taps read the grid (L1/L2), ramp per tap from each
                 // visibility's own cell (nx, ny)
+                float zxs, zxc;
+                __sincosf(-pi_f * du * L, &zxs, &zxc);
+                const float2 zx = make_float2(zxc, zxs);
 #pragma unroll
                 for (int v = 0; v < kV; ++v) {
                     hx[v] = fx[v];
@@ -508,7 +504,6 @@ track_kernel(const EvalArgs a0, const EvalArgs *__restrict__ args, const long lo
                         float zs, zc;
                         __sincosf(-pi_f * du * ((float)a_lo * L + (float)bb * M), &zs, &zc);
                         float2 z = make_float2(zc, zs);
-                        const float2 zx = make_float2(zxc, zxs);
                         float pr = 0.f, pi = 0.f, qr = 0.f, qi = 0.f;
                         const float2 *rowp = a.grid + (size_t)(ny[v] + bb) * a.ng + nx[v];
                         float dd = (fx[v] - (float)a_lo) * ov;
@@ -534,20 +529,24 @@ track_kernel(const EvalArgs a0, const EvalArgs *__restrict__ args, const long lo
             }
 
             // ---- epilogue: visibility half of the ramp, residuals, sums ----
-            // With T = T0, Px = i pi Tu, Py = i pi Tv (Tu, Tv in wavelengths) the
-            // derivatives are dV/dl_i = D (el T + Px), dV/dl_j = D (-el T + Px),
-            // dV/dm_i = D (em T + Py), dV/dm_j = D (-em T + Py), with D, el, em
-            // fixed for the baseline and channel.  So every chi^2, gradient and
-            // normal sum of the channel follows from the weighted inner
-            // products <X, Y> = Re(conj(X) Y) of R, T, Px, Py summed over the
-            // lane's visibilities: <R,R>, <R,T>, <R,Px>, <R,Py>, <T,T>, <T,Px>,
-            // <T,Py>, <Px,Px>, <Px,Py>, <Py,Py>.
-            const float al2 = ch.alpha2;
-            float D = 1.f, el = 0.f, em = 0.f;
+            // With T = T0, Px = i pi Tu, Py = i pi Tv (Tu, Tv in wavelengths),
+            // el = -dL alpha^2, em = -dM alpha^2, the derivatives are
+            // dV/dl_i = D (el T + Px), dV/dl_j = D (-el T + Px),
+            // dV/dm_i = D (em T + Py), dV/dm_j = D (-em T + Py).  Every chi^2,
+            // gradient and normal sum then follows from the weighted inner
+            // products <X, Y> = Re(conj(X) Y) of R, T, Px, Py over the lane's
+            // visibilities of the channel, and the channel's D and alpha^2
+            // enter only as factors of moments summed over channels:
+            //   chi^2 = sum <R,R>,  E0 = sum 2 D a2 <R,T>,  E1 = -sum 2 D <R,Px>,
+            //   E2 = -sum 2 D <R,Py>,  A0 = sum 2 D^2 <Px,Px>,  A1 = .. <Py,Py>,
+            //   A2 = .. <Px,Py>,  B1 = sum 2 D^2 a2 <T,Px>,  B2 = .. <T,Py>,
+            //   C = sum 2 D^2 a2^2 <T,T>
+            // (a2 = alpha^2 with decorrelation, else 0 and D = 1); the item's
+            // fifteen sums are formed from them and (dL, dM) once per item.
+            float D = 1.f, a2 = 0.f;
             if (a.decorrelation) {
-                D = __expf(-0.5f * al2 * dsq);
-                el = -dL * al2;                      // (l_j - l_i) alpha^2
-                em = -dM * al2;
+                a2 = ch.alpha2;
+                D = __expf(-0.5f * a2 * (dL * dL + dM * dM));
             }
             const float su = pi_f * du / ov;         // Q was accumulated with dx ov; Px = i pi Tu
             const float sv = pi_f * du;
@@ -561,9 +560,9 @@ track_kernel(const EvalArgs a0, const EvalArgs *__restrict__ args, const long lo
                 const float2 U = cmul(ph, Su[v]), W2 = cmul(ph, Sv[v]);
                 const float2 Px = make_float2(-su * U.y, su * U.x);
                 const float2 Py = make_float2(-sv * W2.y, sv * W2.x);
-                const size_t k = kb[v] + c;
-                const float2 vo = vis_obs[k];
-                const float w = wv[v] * (wgt != nullptr ? wgt[k] : 1.f);
+                const size_t k = kb0 + (size_t)v * kstep + c;
+                const float2 vo = a.vis_obs[k];
+                const float w = (v == 0 ? wv0 : wv1) * (a.w != nullptr ? a.w[k] : 1.f);
                 const float2 R = make_float2(fmaf(-D, T.x, vo.x), fmaf(-D, T.y, vo.y));
                 const float2 wR = make_float2(w * R.x, w * R.y);
                 const float2 wT = make_float2(w * T.x, w * T.y);
@@ -579,35 +578,19 @@ track_kernel(const EvalArgs a0, const EvalArgs *__restrict__ args, const long lo
                 xy = fmaf(wX.x, Py.x, fmaf(wX.y, Py.y, xy));
                 yy = fmaf(w * Py.x, Py.x, fmaf(w * Py.y, Py.y, yy));
             }
-            // chi^2 and the gradient (compensated), the normal blocks (plain)
-            const float g2 = -2.f * D, h2 = 2.f * D * D;
-            two_sum_acc(S[0], Cc[0], rr);
-            two_sum_acc(S[1], Cc[1], g2 * fmaf(el, rt, rx));
-            two_sum_acc(S[2], Cc[2], g2 * fmaf(em, rt, ry));
-            two_sum_acc(S[3], Cc[3], g2 * fmaf(-el, rt, rx));
-            two_sum_acc(S[4], Cc[4], g2 * fmaf(-em, rt, ry));
-            const float ett = el * el * tt, mtt = em * em * tt, emt = el * em * tt;
-            const float etx = 2.f * el * tx, mty = 2.f * em * ty;
-            const float cxy = fmaf(el, ty, em * tx);
-            const float dxy = fmaf(el, ty, -em * tx);
-            S[5] += h2 * (ett + etx + xx);           // l_i l_i
-            S[6] += h2 * (emt + cxy + xy);           // l_i m_i
-            S[7] += h2 * (mtt + mty + yy);           // m_i m_i
-            S[8] += h2 * (ett - etx + xx);           // l_j l_j
-            S[9] += h2 * (emt - cxy + xy);           // l_j m_j
-            S[10] += h2 * (mtt - mty + yy);          // m_j m_j
-            S[11] += h2 * (xx - ett);                // l_i l_j
-            S[12] += h2 * (dxy - emt + xy);          // l_i m_j
-            S[13] += h2 * (-dxy - emt + xy);         // m_i l_j
-            S[14] += h2 * (yy - mtt);                // m_i m_j
-            if (c + 1 < nc) {
-                ch = chn;
-                box = boxn;
-#pragma unroll
-                for (int v = 0; v < kV; ++v) {
-                    nx[v] = nxn[v]; ny[v] = nyn[v]; fx[v] = fxn[v]; fy[v] = fyn[v];
-                }
-            }
+            const float d2 = 2.f * D, dd2 = d2 * D;
+            two_sum_acc(chi_s, chi_c, rr);
+            two_sum_acc(e0s, e0c, d2 * a2 * rt);
+            two_sum_acc(e1s, e1c, -d2 * rx);
+            two_sum_acc(e2s, e2c, -d2 * ry);
+            hA0 = fmaf(dd2, xx, hA0);
+            hA1 = fmaf(dd2, yy, hA1);
+            hA2 = fmaf(dd2, xy, hA2);
+            hB1 = fmaf(dd2 * a2, tx, hB1);
+            hB2 = fmaf(dd2 * a2, ty, hB2);
+            hC = fmaf(dd2 * a2 * a2, tt, hC);
+            ch = chn;
+            box = boxn;
         }
         if (!ok) {
             // a wait ran out: report it, wait (longer bound) for this warp's own
@@ -618,24 +601,47 @@ track_kernel(const EvalArgs a0, const EvalArgs *__restrict__ args, const long lo
             __syncwarp();
             return;
         }
-        // ---- the item's record: butterfly over the warp ----
+        // ---- the item's record: butterfly over the warp, then the fifteen sums in FP64 ----
+        float cmp[4][2] = {{chi_s, chi_c}, {e0s, e0c}, {e1s, e1c}, {e2s, e2c}};
+        float pln[6] = {hA0, hA1, hA2, hB1, hB2, hC};
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
-            for (int k = 0; k < 5; ++k) {
-                const float so = __shfl_xor_sync(kFull, S[k], o);
-                const float co = __shfl_xor_sync(kFull, Cc[k], o);
+            for (int k = 0; k < 4; ++k) {
+                const float so = __shfl_xor_sync(kFull, cmp[k][0], o);
+                const float co = __shfl_xor_sync(kFull, cmp[k][1], o);
                 float cs = 0.f;
-                two_sum_acc(S[k], cs, so);
-                Cc[k] = __fadd_rn(__fadd_rn(Cc[k], co), cs);
+                two_sum_acc(cmp[k][0], cs, so);
+                cmp[k][1] = __fadd_rn(__fadd_rn(cmp[k][1], co), cs);
             }
 #pragma unroll
-            for (int k = 5; k < kRed; ++k) S[k] += __shfl_xor_sync(kFull, S[k], o);
+            for (int k = 0; k < 6; ++k) pln[k] += __shfl_xor_sync(kFull, pln[k], o);
         }
-        double out = 0.0;
-#pragma unroll
-        for (int k = 0; k < kRed; ++k)
-            if (lane == k) out = k < 5 ? (double)S[k] + (double)Cc[k] : (double)S[k];
+        const double chi2 = (double)cmp[0][0] + (double)cmp[0][1];
+        const double E0 = (double)cmp[1][0] + (double)cmp[1][1];
+        const double E1 = (double)cmp[2][0] + (double)cmp[2][1];
+        const double E2 = (double)cmp[3][0] + (double)cmp[3][1];
+        const double A0 = pln[0], A1 = pln[1], A2 = pln[2], B1 = pln[3], B2 = pln[4], C = pln[5];
+        const double xl = dL, xm = dM;
+        double out;
+        switch (lane) {
+            case 0: out = chi2; break;
+            case 1: out = xl * E0 + E1; break;                                  // g l_i
+            case 2: out = xm * E0 + E2; break;                                  // g m_i
+            case 3: out = -xl * E0 + E1; break;                                 // g l_j
+            case 4: out = -xm * E0 + E2; break;                                 // g m_j
+            case 5: out = xl * xl * C - 2.0 * xl * B1 + A0; break;              // l_i l_i
+            case 6: out = xl * xm * C - xl * B2 - xm * B1 + A2; break;          // l_i m_i
+            case 7: out = xm * xm * C - 2.0 * xm * B2 + A1; break;              // m_i m_i
+            case 8: out = xl * xl * C + 2.0 * xl * B1 + A0; break;              // l_j l_j
+            case 9: out = xl * xm * C + xl * B2 + xm * B1 + A2; break;          // l_j m_j
+            case 10: out = xm * xm * C + 2.0 * xm * B2 + A1; break;             // m_j m_j
+            case 11: out = A0 - xl * xl * C; break;                             // l_i l_j
+            case 12: out = -xl * B2 + xm * B1 - xl * xm * C + A2; break;        // l_i m_j
+            case 13: out = xl * B2 - xm * B1 - xl * xm * C + A2; break;         // m_i l_j
+            case 14: out = A1 - xm * xm * C; break;                             // m_i m_j
+            default: out = 0.0;
+        }
         if (lane < kRed) a.partials[(size_t)lane * a.n_bricks + brick] = out;
     }
 }
