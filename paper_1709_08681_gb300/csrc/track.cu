@@ -374,6 +374,16 @@ track_kernel(const EvalArgs a0, const EvalArgs *__restrict__ args, const long lo
                 trk_pos(q.x, q.y, ch.sc_hi, ch.sc_lo, half, nx[v], fx[v]);
                 trk_pos(q.z, q.w, ch.sc_hi, ch.sc_lo, half, ny[v], fy[v]);
             }
+            // the channel's observed visibilities and weights, loaded now so that
+            // their latency hides behind the taps
+            float2 vo[kV];
+            float wk[kV];
+#pragma unroll
+            for (int v = 0; v < kV; ++v) {
+                const size_t k = kb0 + (size_t)v * kstep + c;
+                vo[v] = a.vis_obs[k];
+                wk[v] = (v == 0 ? wv0 : wv1) * (a.w != nullptr ? a.w[k] : 1.f);
+            }
             const float rmax = ch.rho_max, rmax2 = rmax * rmax;
             const int W = box_width(box);
             const int ncp = (box.y1 - box.y0 + 1 + kBoxRows - 1) / kBoxRows;
@@ -560,10 +570,8 @@ track_kernel(const EvalArgs a0, const EvalArgs *__restrict__ args, const long lo
                 const float2 U = cmul(ph, Su[v]), W2 = cmul(ph, Sv[v]);
                 const float2 Px = make_float2(-su * U.y, su * U.x);
                 const float2 Py = make_float2(-sv * W2.y, sv * W2.x);
-                const size_t k = kb0 + (size_t)v * kstep + c;
-                const float2 vo = a.vis_obs[k];
-                const float w = (v == 0 ? wv0 : wv1) * (a.w != nullptr ? a.w[k] : 1.f);
-                const float2 R = make_float2(fmaf(-D, T.x, vo.x), fmaf(-D, T.y, vo.y));
+                const float w = wk[v];
+                const float2 R = make_float2(fmaf(-D, T.x, vo[v].x), fmaf(-D, T.y, vo[v].y));
                 const float2 wR = make_float2(w * R.x, w * R.y);
                 const float2 wT = make_float2(w * T.x, w * T.y);
                 const float2 wX = make_float2(w * Px.x, w * Px.y);
