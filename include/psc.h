@@ -349,15 +349,18 @@ psc_status psc_set_flat_tiling(psc_ctx *ctx, int items, int vis_per_thread);
  * Results equal the brick kernel's up to FP32 summation order. */
 psc_status psc_set_track_tiling(psc_ctx *ctx, int vis_per_lane);
 
-/* Polls of one bounded mbarrier wait in the library's kernels (the TMA and
- * tensor-core pipelines of the track kernel, the model-grid DFT and the
- * network).  A wait that runs out makes the kernel record a flag, wait with a
- * fixed larger bound for its own copies and MMAs still in flight, release its
- * tensor memory and return; the next synchronising call on the object
- * reports PSC_ERR_TIMEOUT and the object stays usable.  0 restores the default
- * (2^24 polls, far beyond any wait that completes).  A tiny limit is for
- * testing that error path.  psc_get_wait_limit returns the current value.
- * Errors: PSC_ERR_ARG for polls < 0. */
+/* Polls of one bounded mbarrier wait of the track kernel (psc_set_track_tiling),
+ * each poll suspending the warp for up to about a microsecond.  A wait that
+ * runs out makes the warp record a flag, wait with a fixed larger bound for
+ * its own copies still in flight and stop; the synchronising call that
+ * consumes the evaluation (psc_residual_grad, psc_lm_end, psc_solve_offsets,
+ * psc_batch_end, psc_solve_batch) then reports PSC_ERR_TIMEOUT, and the
+ * context stays usable.  polls < 0 restores the default (2^24, far beyond any
+ * wait that completes); 0 makes every wait give up at once, which exercises
+ * that error path.  The limit is process-wide and read when a launch is
+ * enqueued (batches capture it in their graph: recreate the batch after a
+ * change).  The model-grid and network kernels keep their own fixed bound.
+ * psc_get_wait_limit returns the current value.  Never fails. */
 psc_status psc_set_wait_limit(long long polls);
 long long psc_get_wait_limit(void);
 

@@ -191,7 +191,8 @@ def _stream(stream):
 
 
 def psc_set_wait_limit(polls):
-    """Polls of one bounded mbarrier wait in the library's kernels (0: default)."""
+    """Polls of one bounded mbarrier wait of the track kernel (< 0: default;
+    0: every wait gives up at once, for testing the error path)."""
     _check(lib().psc_set_wait_limit(int(polls)))
 
 

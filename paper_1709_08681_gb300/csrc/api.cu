@@ -375,8 +375,7 @@ psc_status check_err_flag(psc_ctx *c) {
 extern "C" {
 
 psc_status psc_set_wait_limit(long long polls) {
-    if (polls < 0) return fail(nullptr, PSC_ERR_ARG, "polls must be >= 0");
-    g_wait_polls = polls == 0 ? kDefaultWaitPolls : polls;
+    g_wait_polls = polls < 0 ? kDefaultWaitPolls : polls;
     return PSC_OK;
 }
 

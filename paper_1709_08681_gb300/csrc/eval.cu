@@ -63,6 +63,7 @@ struct BlockSharedT {
     float2 tile[kTiled ? kTile * kTile : 1];
     float2 phx[kTile], phy[kTile];
     float red[kMaxThreads / 32][kRed];
+    float red_c[kMaxThreads / 32][5];      // rounding errors of the compensated warp sums
     float bl[4];
     int box[4];
     int taps;          // taps of the brick's visibilities (pi rho_max^2 each, rounded up)
@@ -484,25 +485,41 @@ __global__ void __launch_bounds__(kMaxThreads, kW ? 4 : 0) eval_kernel(const Eva
     if (a.kv == 2) eval_brick<kPredict, 2, kW>(a, brick, s_tab, sh, acc);
     else eval_brick<kPredict, 1, kW>(a, brick, s_tab, sh, acc);
     if constexpr (!kPredict) {
-        // ---- block reduction: FP32 within a warp, FP64 across warps ----
+        // ---- block reduction: a butterfly within each warp -- compensated
+        // (Knuth's TwoSum, the rounding errors summed beside) for chi^2 and the
+        // gradient, plain FP32 for the normal blocks -- then FP64 across warps ----
+        float comp[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-        for (int k = 0; k < kRed; ++k) {
-            float v = acc[k];
+        for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            acc[k] = v;
+            for (int k = 0; k < 5; ++k) {
+                const float so = __shfl_xor_sync(0xffffffffu, acc[k], o);
+                const float co = __shfl_xor_sync(0xffffffffu, comp[k], o);
+                const float t = __fadd_rn(acc[k], so);
+                const float bp = __fsub_rn(t, acc[k]);
+                const float err = __fadd_rn(__fsub_rn(acc[k], __fsub_rn(t, bp)), __fsub_rn(so, bp));
+                acc[k] = t;
+                comp[k] = __fadd_rn(__fadd_rn(comp[k], co), err);
+            }
+#pragma unroll
+            for (int k = 5; k < kRed; ++k) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
         }
         const int warp = tid >> 5, lane = tid & 31;
         if (lane == 0) {
 #pragma unroll
             for (int k = 0; k < kRed; ++k) sh.red[warp][k] = acc[k];
+#pragma unroll
+            for (int k = 0; k < 5; ++k) sh.red_c[warp][k] = comp[k];
         }
         __syncthreads();
         if (tid < kRed) {
-            float s = 0.f;
+            double s = 0.0;
             const int nw = (blockDim.x + 31) >> 5;
-            for (int wi = 0; wi < nw; ++wi) s += sh.red[wi][tid];
-            a.partials[(size_t)tid * a.n_bricks + brick] = (double)s;      // [kRed][n_bricks]
+            for (int wi = 0; wi < nw; ++wi) {
+                s += (double)sh.red[wi][tid];
+                if (tid < 5) s += (double)sh.red_c[wi][tid];
+            }
+            a.partials[(size_t)tid * a.n_bricks + brick] = s;      // [kRed][n_bricks]
         }
     }
     }                                                 // not skipped

@@ -225,3 +225,33 @@ def test_full_scale_interval_in_the_benchmark_configuration():
         scale = 2 * w_scale * np.sum(np.abs(dV[0]) ** 2 + np.abs(dV[1]) ** 2)
         assert np.max(np.abs(got[3][bl] - np.asarray(X))) < TOL * scale, bl
     s.close()
+
+
+def test_a_wait_that_runs_out_reports_a_timeout_and_the_context_recovers():
+    """Fault path without a fault: with a wait limit of 0 polls every mbarrier
+    wait of the track kernel gives up at once.  Each warp then records the
+    flag, waits (with its fixed larger bound) for its own TMA copies still in
+    flight and stops; the call reports PSC_ERR_TIMEOUT.  With the default
+    limit back, the same context gives the earlier results bit for bit."""
+    m, _, lmt, img = cases.problem(SMALL_AP, n_ant=6, n_time=40, freqs=(1.3e9, 1.4e9), sigma_arcsec=30.0)
+    vobs, w = _obs(m, lmt)
+    gp = GpuProblem(m, img)
+    gp.ctx.psc_set_track_tiling(2)
+    dv, dw = gp.upload(vobs), gp.upload(w, torch.float32)
+    ref = gp.ctx.psc_residual_grad(0.5 * lmt, dv, dw, 1.0, cross=True)
+    try:
+        _abi.psc_set_wait_limit(0)
+        assert _abi.psc_get_wait_limit() == 0
+        with pytest.raises(_abi.PscError) as e:
+            gp.ctx.psc_residual_grad(0.5 * lmt, dv, dw, 1.0, cross=True)
+        assert e.value.status == _abi.PSC_ERR_TIMEOUT
+        with pytest.raises(_abi.PscError) as e:
+            gp.ctx.psc_solve_offsets(dv, dw, 1.0)
+        assert e.value.status == _abi.PSC_ERR_TIMEOUT
+    finally:
+        _abi.psc_set_wait_limit(-1)
+    assert _abi.psc_get_wait_limit() == 1 << 24
+    again = gp.ctx.psc_residual_grad(0.5 * lmt, dv, dw, 1.0, cross=True)
+    assert again[0] == ref[0] and all(np.array_equal(x, y) for x, y in zip(again[1:], ref[1:]))
+    sol, rep = gp.ctx.psc_solve_offsets(dv, dw, 1.0)
+    assert _abi.STOP_REASONS[rep.reason] in ("step", "chi2")
