@@ -71,8 +71,9 @@ def parse():
     p.add_argument("--no-squint", action="store_true", help="skip the two-polarisation section")
     p.add_argument("--mixed-intervals", type=int, default=256,
                    help="intervals of the mixed-array batched-solve section (0 skips it)")
-    p.add_argument("--learned-train", type=int, default=20000, help="training intervals of the learned initialiser")
-    p.add_argument("--learned-eval", type=int, default=512, help="held-out intervals of the comparison")
+    p.add_argument("--learned-train", type=int, default=100_000, help="training intervals of the learned initialiser")
+    p.add_argument("--learned-eval", type=int, default=10_000, help="held-out intervals of the comparison")
+    p.add_argument("--learned-steps", type=int, default=20_000, help="AdamW steps of the network's training")
     return p.parse_args()
 
 
@@ -372,69 +373,45 @@ def measure_iteration(wl, sess, vis, w, stream, steps, warmup, ws=1, sample_cloc
 def measure_e2e(wl, sess, vis, w, w_scale, stream, k_steps):
     """The same step through the public batch API with its inputs copied from
     pinned host memory every step and the offsets plus chi^2 read back (a
-    synchronising call).  The copies run on a second stream into two
-    alternating device buffers (one batch per buffer over the same contexts):
-    step k+1's copy overlaps step k's evaluation, and an event keeps a buffer
-    from being overwritten before the step that reads it has finished.  The
-    resident input buffer serves as one of the two."""
+    synchronising call).  The copy precedes the iteration on the same stream:
+    on this machine a host-to-device copy makes little progress while the
+    fused kernel streams the grid and the visibilities through L2 (it runs at
+    the full rate only beside compute-only work), so overlapping the next
+    step's copy with this step's evaluation only lengthens the step."""
     import torch
     from paper_1709_08681_gb300 import _abi, dist as D
     n_ctx = len(sess.ctxs)
     lm0 = np.zeros((wl.n_ant, 2))
-    opts = _abi.psc_solve_opts_default()
     vis_h = torch.empty(vis.shape, dtype=vis.dtype, pin_memory=True)
     vis_h.copy_(vis)
     w_h = None
     if w is not None:
         w_h = torch.empty(w.shape, dtype=w.dtype, pin_memory=True)
         w_h.copy_(w)
-    bufs = [(vis, w), (torch.empty_like(vis), torch.empty_like(w) if w is not None else None)]
-    batches = [_abi.Batch(sess.ctxs, [sess.vis_slice(vd, k) for k in range(n_ctx)],
-                          [sess.vis_slice(wd, k) for k in range(n_ctx)] if wd is not None else None,
-                          w_scale=w_scale, stream=stream) for vd, wd in bufs]
-    for b_ in batches:
-        b_.psc_batch_begin([lm0] * n_ctx, opts)
-    copy_stream = torch.cuda.Stream(device=vis.device)
-    ev_copied = [torch.cuda.Event() for _ in range(2)]
-    ev_done = [torch.cuda.Event() for _ in range(2)]
-
-    def issue_copy(slot):
-        with torch.cuda.stream(copy_stream):
-            copy_stream.wait_event(ev_done[slot])              # the step that last read this buffer is done
-            bufs[slot][0].copy_(vis_h, non_blocking=True)
-            if w_h is not None:
-                bufs[slot][1].copy_(w_h, non_blocking=True)
-            ev_copied[slot].record(copy_stream)
-
-    for slot, b_ in enumerate(batches):                        # untimed: graph capture of both batches
-        bufs[slot][0].copy_(vis)
-        if w is not None:
-            bufs[slot][1].copy_(w)
-        b_.psc_batch_restart()
-        b_.psc_batch_iterate(1)
-        b_.psc_batch_end()
+    batch = _abi.Batch(sess.ctxs, [sess.vis_slice(vis, k) for k in range(n_ctx)],
+                       [sess.vis_slice(w, k) for k in range(n_ctx)] if w is not None else None,
+                       w_scale=w_scale, stream=stream)
+    batch.psc_batch_begin([lm0] * n_ctx, _abi.psc_solve_opts_default())
+    batch.psc_batch_restart()                                  # untimed: graph capture
+    batch.psc_batch_iterate(1)
+    batch.psc_batch_end()
     d2h = 0
     torch.cuda.synchronize()
     t = time.perf_counter()
-    issue_copy(0)
-    for step_i in range(k_steps):
-        slot = step_i % 2
-        stream.wait_event(ev_copied[slot])
-        batches[slot].psc_batch_restart()
-        batches[slot].psc_batch_iterate(1)
-        ev_done[slot].record(stream)
-        if step_i + 1 < k_steps:
-            issue_copy(1 - slot)
-        lm_out, reps = batches[slot].psc_batch_end()           # synchronises; offsets + chi^2 to the host
+    for _ in range(k_steps):
+        with torch.cuda.stream(stream):
+            vis.copy_(vis_h, non_blocking=True)
+            if w_h is not None:
+                w.copy_(w_h, non_blocking=True)
+        batch.psc_batch_restart()
+        batch.psc_batch_iterate(1)
+        lm_out, reps = batch.psc_batch_end()                   # synchronises; offsets + chi^2 to the host
         d2h = sum(x.nbytes for x in lm_out) + 8 * 5 * len(reps)
     dt = D.max_over_ranks(time.perf_counter() - t, device="cuda")
-    for b_ in batches:
-        b_.close()
-    del bufs
+    batch.close()
     h2d = vis.numel() * 8 + (w.numel() * 4 if w is not None else 0)
     return {"value": wl.n_vis * k_steps / dt / 1e9, "unit": "Gvis/s", "h2d_bytes_per_step": int(h2d),
-            "d2h_bytes_per_step": int(d2h), "steps": k_steps,
-            "h2d_gb_per_s": h2d * k_steps / dt / 1e9}
+            "d2h_bytes_per_step": int(d2h), "steps": k_steps, "h2d_gb_per_s": h2d * k_steps / dt / 1e9}
 
 
 def setup_workload(wl, stream):
@@ -566,8 +543,8 @@ def secondary(args, line, local):
         # 64-antenna 16-channel workload (network trained here on GPU-simulated
         # intervals with the library's kernels)
         from paper_1709_08681_gb300 import learned_init as LI
-        rep, _ = LI.run(n_train=3000, n_eval=20, steps=3000, batch=1024, n_geom=8, seed=args.seed, log=None,
-                        n_eval_batched=64)
+        rep = LI.run_at_scale(n_train=args.learned_train, n_eval=args.learned_eval, steps=args.learned_steps,
+                              seed=args.seed)
         line["learned_init"] = {"workload": "disk64_l16ch", **rep}
     if args.mixed_intervals > 0:
         from paper_1709_08681_gb300 import mixed as MX

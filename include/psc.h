@@ -446,6 +446,25 @@ psc_status psc_set_grid_precision(psc_ctx *ctx, int precision);
 psc_status psc_features(psc_ctx *ctx, const void *vis_obs, const float *w, double w_scale, double sigma_prior_rad,
                         int time_stride, float *feat_dev);
 
+/* The features of psc_features for n (context, data) pairs in three launches
+ * (one stencil pass over all pairs' bricks, the per-baseline sums, the
+ * per-antenna features).  A context may appear in several pairs (for example
+ * one context per observation geometry serving many simulated intervals).
+ * vis_obs[j] / w[j] (NULL for all ones; w itself may be NULL) / w_scale[j]
+ * (NULL for 1) are pair j's data as for psc_features; the features of pair j
+ * go to feat_dev (device) from row sum_{i<j} n_ant_i, [n_ant_j][52] each.
+ * Every pair needs the same brick shape: contexts of the same number of time
+ * steps and channels.  work is caller-owned device scratch of at least the
+ * bytes psc_features_batch_work reports for the same contexts and stride
+ * (the argument tables, then per pair 56 * 8 bytes per brick and per
+ * baseline).  Runs on `stream` and synchronises it (the argument tables are
+ * copied from host memory).  Errors: PSC_ERR_ARG (NULL pointers, a workspace
+ * that is too small, mixed brick shapes), PSC_ERR_CUDA. */
+psc_status psc_features_batch(psc_ctx *const *ctxs, int n, const void *const *vis_obs, const float *const *w,
+                              const double *w_scale, double sigma_prior_rad, int time_stride, void *work,
+                              size_t work_bytes, float *feat_dev, void *stream);
+psc_status psc_features_batch_work(psc_ctx *const *ctxs, int n, int time_stride, size_t *bytes);
+
 /* ---- The learned initial estimate's network (an addition to the method) ----
  * MLP 52 -> 256 -> 256 -> 256 -> 2 with GELU after the hidden layers, input
  * standardised by fixed (mu, s), output the offsets in units of sigma_prior.

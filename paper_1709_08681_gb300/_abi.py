@@ -32,7 +32,7 @@ EXPORTS = ("psc_solve_opts_default", "psc_model_grid", "psc_model_grid_component
            "psc_predict", "psc_residual_grad", "psc_solve_offsets", "psc_lm_begin", "psc_lm_iterate",
            "psc_lm_end", "psc_lm_restart", "psc_set_tiling", "psc_set_grid_precision", "psc_set_staging",
            "psc_set_kernel_model", "psc_set_flat_tiling", "psc_set_track_tiling", "psc_set_wait_limit",
-           "psc_get_wait_limit", "psc_set_brick_order", "psc_fp32_fma_rate", "psc_profile", "psc_profile_read",
+           "psc_get_wait_limit", "psc_features_batch", "psc_features_batch_work", "psc_set_brick_order", "psc_fp32_fma_rate", "psc_profile", "psc_profile_read",
            "psc_residual_grad_noalloc", "psc_batch_create", "psc_batch_destroy", "psc_batch_last_error",
            "psc_batch_autotune", "psc_batch_begin", "psc_batch_restart", "psc_batch_kernel", "psc_batch_iterate", "psc_batch_end",
            "psc_solve_batch", "psc_batch_profile", "psc_batch_profile_read", "psc_features",
@@ -136,6 +136,11 @@ def lib():
             "psc_set_track_tiling": (ctypes.c_int, [_V, ctypes.c_int]),
             "psc_set_wait_limit": (ctypes.c_int, [ctypes.c_longlong]),
             "psc_get_wait_limit": (ctypes.c_longlong, []),
+            "psc_features_batch": (ctypes.c_int, [ctypes.POINTER(_V), ctypes.c_int, ctypes.POINTER(_V),
+                                                  ctypes.POINTER(_V), _D, ctypes.c_double, ctypes.c_int, _V,
+                                                  ctypes.c_size_t, _V, _V]),
+            "psc_features_batch_work": (ctypes.c_int, [ctypes.POINTER(_V), ctypes.c_int, ctypes.c_int,
+                                                       ctypes.POINTER(ctypes.c_size_t)]),
             "psc_batch_iterate": (ctypes.c_int, [_V, ctypes.c_int]),
             "psc_batch_end": (ctypes.c_int, [_V, _D, ctypes.POINTER(psc_solve_report)]),
             "psc_mlp_n_params": (ctypes.c_int, []),
@@ -520,6 +525,35 @@ def psc_fp32_fma_rate(stream=None):
     out = np.zeros(1)
     _check(lib().psc_fp32_fma_rate(_dp(out), _stream(stream)))
     return float(out[0])
+
+
+def psc_features_batch_work(contexts, time_stride):
+    """Workspace bytes of psc_features_batch for these contexts (one per pair)."""
+    n = len(contexts)
+    hs = (_V * n)(*[c.h.value for c in contexts])
+    b = ctypes.c_size_t(0)
+    _check(lib().psc_features_batch_work(hs, n, int(time_stride), ctypes.byref(b)))
+    return int(b.value)
+
+
+def psc_features_batch(contexts, vis_obs, w_scale, sigma_prior, time_stride, work, out, w=None, stream=None):
+    """Features of every (context, data) pair into out (device float32
+    [sum n_ant][52]); work: device scratch of psc_features_batch_work bytes."""
+    n = len(contexts)
+    hs = (_V * n)(*[c.h.value for c in contexts])
+    ws = np.ascontiguousarray(np.broadcast_to(np.asarray(w_scale, dtype=np.float64), (n,)))
+    need = sum(c.n_ant for c in contexts) * 52
+    if out.numel() < need or out.dtype != torch_float32():
+        raise ValueError("out must be float32 with at least %d elements" % need)
+    _check(lib().psc_features_batch(hs, n, _ptr_array(vis_obs), _ptr_array(w) if w is not None else None, _dp(ws),
+                                    float(sigma_prior), int(time_stride), _ptr(work), int(work.numel() * work.element_size()),
+                                    _ptr(out), _stream(stream)))
+    return out
+
+
+def torch_float32():
+    import torch
+    return torch.float32
 
 
 def psc_solve_batch(contexts, vis_obs, w=None, w_scale=None, lm0_list=None, opts=None):

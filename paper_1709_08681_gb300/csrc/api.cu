@@ -285,6 +285,7 @@ LMArgs lm_args(const psc_ctx *c) {
     a.pairs = c->d_pairs;
     a.n_ant = c->n_ant;
     a.n_bl = c->n_bl;
+    a.err = c->d_err;
     return a;
 }
 
@@ -322,6 +323,44 @@ psc_status eval_reduce(psc_ctx *c, const double *lm_dev, const void *vis_obs, co
     }
     PSC_CUDA(c, launch_reduce(red_args(c, ev_out, skip), c->stream));
     return PSC_OK;
+}
+
+// Stencil-feature arguments of one context and its data: every kept time
+// step of up to 32 in one tile, and as many channels as fill 128 threads (few
+// kept steps would otherwise leave most lanes of a 32-step tile idle).
+StencilArgs stencil_args(const psc_ctx *ctx, const void *vis_obs, const float *w, double w_scale, double sigma,
+                         int time_stride) {
+    const int nts = (ctx->nt + time_stride - 1) / time_stride;
+    const int t_tile = std::min(32, nts);
+    const int c_group = std::min(std::min(8, ctx->nc), std::max(1, 128 / t_tile));
+    StencilArgs a{};
+    a.uvw = ctx->uvw;
+    a.grid = ctx->grid;
+    a.chan = ctx->d_chan;
+    a.tabs = ctx->d_tabs;
+    a.vis_obs = (const float2 *)vis_obs;
+    a.w = w;
+    a.w_scale = (float)w_scale;
+    a.n_bl = ctx->n_bl;
+    a.nt = ctx->nt;
+    a.nc = ctx->nc;
+    a.ng = ctx->gd.n_grid;
+    a.support = ctx->gd.support;
+    a.ov = ctx->gd.oversample;
+    a.du = (float)ctx->du;
+    a.t_tile = t_tile;
+    a.c_group = c_group;
+    a.n_tt = (nts + t_tile - 1) / t_tile;
+    a.n_cg = (ctx->nc + c_group - 1) / c_group;
+    a.time_stride = time_stride;
+    a.decorrelation = ctx->ap.decorrelation;
+    a.max_tab_len = ctx->max_tab_len;
+    // a 64 x 64 staged tile pays only for bricks of many visibilities; small
+    // bricks read the grid directly and keep shared memory (and occupancy) free
+    a.stage = t_tile * c_group >= 64;
+    a.n_bricks = (long long)ctx->n_bl * a.n_cg * a.n_tt;
+    a.sigma = (float)sigma;
+    return a;
 }
 
 // Track kernel set-up of a context: the per-channel (intercept, slope)
@@ -978,7 +1017,13 @@ psc_status lm_fetch(psc_ctx *ctx, double *lm_out, psc_solve_report *rep, cudaStr
     if (lm_out)
         PSC_CUDA(ctx, cudaMemcpyAsync(lm_out, ctx->d_lm_cur, sizeof(double) * 2 * ctx->n_ant, cudaMemcpyDeviceToHost, s));
     PSC_CUDA(ctx, cudaMemcpyAsync(&ctx->h_state, ctx->d_state, sizeof(LMState), cudaMemcpyDeviceToHost, s));
+    int flag = 0;
+    PSC_CUDA(ctx, cudaMemcpyAsync(&flag, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
     PSC_CUDA(ctx, cudaStreamSynchronize(s));
+    if (flag) {
+        PSC_CUDA(ctx, cudaMemsetAsync(ctx->d_err, 0, sizeof(int), s));
+        return fail(ctx, PSC_ERR_TIMEOUT, "a bounded wait of the fused evaluation ran out; its results were discarded");
+    }
     if (rep) {
         rep->n_iter = ctx->h_state.n_iter;
         rep->n_eval = ctx->h_state.n_eval;
@@ -986,8 +1031,6 @@ psc_status lm_fetch(psc_ctx *ctx, double *lm_out, psc_solve_report *rep, cudaStr
         rep->chi2 = ctx->h_state.chi2;
         rep->lam = ctx->h_state.lam;
     }
-    psc_status st = check_err_flag(ctx);
-    if (st != PSC_OK) return st;
     if (ctx->h_state.done && ctx->h_state.reason == PSC_STOP_NUMERIC)
         return fail(ctx, PSC_ERR_NUMERIC, "solver stopped on a non-finite chi^2 or step");
     return PSC_OK;
@@ -1065,39 +1108,7 @@ psc_status psc_features(psc_ctx *ctx, const void *vis_obs, const float *w, doubl
     if (!(w_scale > 0.0) || !std::isfinite(w_scale)) return fail(ctx, PSC_ERR_ARG, "w_scale must be > 0");
     if (!(sigma_prior_rad > 0.0) || !std::isfinite(sigma_prior_rad)) return fail(ctx, PSC_ERR_ARG, "sigma_prior must be > 0");
     if (time_stride < 1) return fail(ctx, PSC_ERR_ARG, "time_stride must be >= 1");
-    // brick shape: every kept time step of up to 32 in one tile, and as many
-    // channels as fill 128 threads (few kept steps would otherwise leave most
-    // lanes of a 32-step tile idle)
-    const int nts = (ctx->nt + time_stride - 1) / time_stride;
-    const int t_tile = std::min(32, nts);
-    const int c_group = std::min(std::min(8, ctx->nc), std::max(1, 128 / t_tile));
-    StencilArgs a{};
-    a.uvw = ctx->uvw;
-    a.grid = ctx->grid;
-    a.chan = ctx->d_chan;
-    a.tabs = ctx->d_tabs;
-    a.vis_obs = (const float2 *)vis_obs;
-    a.w = w;
-    a.w_scale = (float)w_scale;
-    a.n_bl = ctx->n_bl;
-    a.nt = ctx->nt;
-    a.nc = ctx->nc;
-    a.ng = ctx->gd.n_grid;
-    a.support = ctx->gd.support;
-    a.ov = ctx->gd.oversample;
-    a.du = (float)ctx->du;
-    a.t_tile = t_tile;
-    a.c_group = c_group;
-    a.n_tt = (nts + t_tile - 1) / t_tile;
-    a.n_cg = (ctx->nc + c_group - 1) / c_group;
-    a.time_stride = time_stride;
-    a.decorrelation = ctx->ap.decorrelation;
-    a.max_tab_len = ctx->max_tab_len;
-    // a 64 x 64 staged tile pays only for bricks of many visibilities; small
-    // bricks read the grid directly and keep shared memory (and occupancy) free
-    a.stage = t_tile * c_group >= 64;
-    a.n_bricks = (long long)ctx->n_bl * a.n_cg * a.n_tt;
-    a.sigma = (float)sigma_prior_rad;
+    StencilArgs a = stencil_args(ctx, vis_obs, w, w_scale, sigma_prior_rad, time_stride);
     const size_t need = (size_t)a.n_bricks * 56;
     if (need > ctx->spart_cap) {
         cudaFree(ctx->d_spart);
@@ -1109,6 +1120,101 @@ psc_status psc_features(psc_ctx *ctx, const void *vis_obs, const float *w, doubl
     if (!ctx->d_sblsum) PSC_CUDA(ctx, dalloc(&ctx->d_sblsum, (size_t)ctx->n_bl * 56));
     a.partials = ctx->d_spart;
     PSC_CUDA(ctx, launch_features(a, ctx->d_sblsum, ctx->n_ant, feat_dev, ctx->stream));
+    return PSC_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+size_t al256b(size_t x) { return (x + 255) / 256 * 256; }
+
+// Workspace layout of psc_features_batch: the argument tables, then per pair
+// its partials and per-baseline sums.
+size_t features_batch_layout(psc_ctx *const *ctxs, int n, int time_stride, std::vector<size_t> *off_part,
+                             std::vector<size_t> *off_bl) {
+    size_t o = al256b(sizeof(StencilArgs) * n) + al256b(sizeof(long long) * (n + 1)) + al256b(sizeof(FeatPair) * n);
+    for (int j = 0; j < n; ++j) {
+        const StencilArgs a = stencil_args(ctxs[j], nullptr, nullptr, 1.0, 1.0, time_stride);
+        if (off_part) off_part->push_back(o);
+        o = al256b(o + sizeof(double) * 56 * (size_t)a.n_bricks);
+        if (off_bl) off_bl->push_back(o);
+        o = al256b(o + sizeof(double) * 56 * (size_t)ctxs[j]->n_bl);
+    }
+    return o;
+}
+
+}  // namespace
+
+extern "C" {
+
+psc_status psc_features_batch_work(psc_ctx *const *ctxs, int n, int time_stride, size_t *bytes) {
+    if (!ctxs || n < 1 || !bytes) return fail(nullptr, PSC_ERR_ARG, "ctxs and bytes must be non-NULL, n >= 1");
+    if (time_stride < 1) return fail(nullptr, PSC_ERR_ARG, "time_stride must be >= 1");
+    for (int j = 0; j < n; ++j)
+        if (!ctxs[j]) return fail(nullptr, PSC_ERR_ARG, "a context is NULL");
+    *bytes = features_batch_layout(ctxs, n, time_stride, nullptr, nullptr);
+    return PSC_OK;
+}
+
+psc_status psc_features_batch(psc_ctx *const *ctxs, int n, const void *const *vis_obs, const float *const *w,
+                              const double *w_scale, double sigma_prior_rad, int time_stride, void *work,
+                              size_t work_bytes, float *feat_dev, void *stream) {
+    if (!ctxs || n < 1 || !vis_obs || !feat_dev || !work) return fail(nullptr, PSC_ERR_ARG, "ctxs, vis_obs, work and feat must be non-NULL, n >= 1");
+    if (!(sigma_prior_rad > 0.0) || !std::isfinite(sigma_prior_rad)) return fail(nullptr, PSC_ERR_ARG, "sigma_prior must be > 0");
+    if (time_stride < 1) return fail(nullptr, PSC_ERR_ARG, "time_stride must be >= 1");
+    for (int j = 0; j < n; ++j) {
+        if (!ctxs[j] || !vis_obs[j]) return fail(nullptr, PSC_ERR_ARG, "a context or its vis_obs is NULL");
+        const double ws = w_scale ? w_scale[j] : 1.0;
+        if (!(ws > 0.0) || !std::isfinite(ws)) return fail(nullptr, PSC_ERR_ARG, "w_scale must be > 0");
+    }
+    std::vector<size_t> off_part, off_bl;
+    const size_t need = features_batch_layout(ctxs, n, time_stride, &off_part, &off_bl);
+    if (work_bytes < need) {
+        char msg[160];
+        std::snprintf(msg, sizeof msg, "psc_features_batch: the workspace holds %zu bytes, %zu needed", work_bytes, need);
+        return fail(nullptr, PSC_ERR_ARG, msg);
+    }
+    unsigned char *base = (unsigned char *)work;
+    std::vector<StencilArgs> args(n);
+    std::vector<long long> prefix(n + 1, 0);
+    std::vector<FeatPair> pairs(n);
+    size_t feat_off = 0;
+    int threads = 0, max_bl = 0, max_ant = 0;
+    size_t dyn = 0;
+    for (int j = 0; j < n; ++j) {
+        psc_ctx *c = ctxs[j];
+        args[j] = stencil_args(c, vis_obs[j], w ? w[j] : nullptr, w_scale ? w_scale[j] : 1.0, sigma_prior_rad, time_stride);
+        args[j].partials = (double *)(base + off_part[j]);
+        const int th = (args[j].t_tile * args[j].c_group + 31) / 32 * 32;
+        if (j > 0 && (th != threads || args[j].stage != args[0].stage))
+            return fail(nullptr, PSC_ERR_ARG, "psc_features_batch: every pair needs the same brick shape (time steps and channels)");
+        threads = th;
+        dyn = std::max(dyn, stencil_dyn_smem(args[j].c_group, args[j].max_tab_len, args[j].stage));
+        prefix[j + 1] = prefix[j] + args[j].n_bricks;
+        pairs[j].partials = args[j].partials;
+        pairs[j].blsum = (double *)(base + off_bl[j]);
+        pairs[j].feat = feat_dev + feat_off;
+        pairs[j].n_bl = c->n_bl;
+        pairs[j].bpb = args[j].n_cg * args[j].n_tt;
+        pairs[j].n_ant = c->n_ant;
+        feat_off += (size_t)c->n_ant * 52;
+        max_bl = std::max(max_bl, c->n_bl);
+        max_ant = std::max(max_ant, c->n_ant);
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    StencilArgs *d_args = (StencilArgs *)base;
+    long long *d_prefix = (long long *)(base + al256b(sizeof(StencilArgs) * n));
+    FeatPair *d_pairs = (FeatPair *)(base + al256b(sizeof(StencilArgs) * n) + al256b(sizeof(long long) * (n + 1)));
+    cudaError_t e = cudaMemcpyAsync(d_args, args.data(), sizeof(StencilArgs) * n, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_prefix, prefix.data(), sizeof(long long) * (n + 1), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_pairs, pairs.data(), sizeof(FeatPair) * n, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = launch_features_batch(d_args, d_prefix, d_pairs, n, prefix[n], threads, dyn, max_bl, max_ant,
+                                  (float)sigma_prior_rad, s);
+    // the argument tables live in pageable host memory: they must be copied before returning
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "psc_features_batch");
     return PSC_OK;
 }
 
@@ -1167,6 +1273,12 @@ struct psc_batch {
     const double **d_lm0 = nullptr;
     unsigned long long *d_queue = nullptr;
     int *d_active = nullptr;
+    // psc_batch_end: every context's offsets, solver state and wait flag
+    // gathered on the device ([lm 2n_ant...][state...][flag...]) and copied
+    // to pinned host memory in one transfer
+    unsigned char *d_gather = nullptr, *h_gather = nullptr;
+    size_t gather_bytes = 0;
+    std::vector<size_t> lm_off;
     int total_bl = 0;
     int grid = 0;
     int threads = 128;           // fused-kernel block size: the widest context's shape
@@ -1211,6 +1323,8 @@ void free_batch(psc_batch *b) {
     for (cudaEvent_t e : b->ev_pool) cudaEventDestroy(e);
     cudaFree(b->d_eval); cudaFree(b->d_prefix); cudaFree(b->d_red); cudaFree(b->d_bl_prefix);
     cudaFree(b->d_lm); cudaFree(b->d_st0); cudaFree(b->d_lm0); cudaFree(b->d_queue); cudaFree(b->d_active);
+    cudaFree(b->d_gather);
+    cudaFreeHost(b->h_gather);
     delete b;
 }
 
@@ -1344,6 +1458,21 @@ psc_status ensure_graph(psc_batch *b) {
         return bfail(b, PSC_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
     }
     return PSC_OK;
+}
+
+// psc_batch_end's gather: context k's accepted offsets to lm + lm_off[k],
+// its solver state to st[k] and its wait flag to flag[k] (then cleared).
+__global__ void batch_gather_kernel(const LMArgs *la, int n, const long long *lm_off, double *lm, LMState *st,
+                                    int *flag) {
+    for (int k = blockIdx.x; k < n; k += gridDim.x) {
+        const LMArgs a = la[k];
+        for (int i = threadIdx.x; i < 2 * a.n_ant; i += blockDim.x) lm[lm_off[k] + i] = a.lm_cur[i];
+        if (threadIdx.x == 0) {
+            st[k] = *a.st;
+            flag[k] = *a.err;
+            *a.err = 0;
+        }
+    }
 }
 
 __global__ void count_active_kernel(const LMArgs *la, int n, int *out) {
@@ -1662,13 +1791,55 @@ psc_status psc_batch_iterate(psc_batch *b, int n_iter) {
 
 psc_status psc_batch_end(psc_batch *b, double *lm_out, psc_solve_report *reps) {
     if (!b) return fail(nullptr, PSC_ERR_ARG, "batch is NULL");
-    size_t off = 0;
+    const int n = (int)b->ctxs.size();
+    if (!b->d_gather) {
+        std::vector<long long> off(n);
+        size_t tot = 0;
+        for (int k = 0; k < n; ++k) {
+            off[k] = (long long)tot;
+            tot += 2 * (size_t)b->ctxs[k]->n_ant;
+        }
+        b->lm_off.assign(off.begin(), off.end());
+        const size_t o_off = 0, o_lm = (sizeof(long long) * n + 255) / 256 * 256;
+        const size_t o_st = (o_lm + sizeof(double) * tot + 255) / 256 * 256;
+        const size_t o_fl = (o_st + sizeof(LMState) * n + 255) / 256 * 256;
+        b->gather_bytes = o_fl + sizeof(int) * n;
+        PSC_BCUDA(b, cudaMalloc(&b->d_gather, b->gather_bytes));
+        PSC_BCUDA(b, cudaMallocHost(&b->h_gather, b->gather_bytes));
+        PSC_BCUDA(b, cudaMemcpy(b->d_gather + o_off, off.data(), sizeof(long long) * n, cudaMemcpyHostToDevice));
+    }
+    const size_t o_lm = (sizeof(long long) * n + 255) / 256 * 256;
+    const size_t tot = b->lm_off.back() + 2 * (size_t)b->ctxs[n - 1]->n_ant;
+    const size_t o_st = (o_lm + sizeof(double) * tot + 255) / 256 * 256;
+    const size_t o_fl = (o_st + sizeof(LMState) * n + 255) / 256 * 256;
+    batch_gather_kernel<<<std::min(n, 1024), 64, 0, b->stream>>>(b->d_lm, n, (const long long *)b->d_gather,
+                                                                  (double *)(b->d_gather + o_lm),
+                                                                  (LMState *)(b->d_gather + o_st),
+                                                                  (int *)(b->d_gather + o_fl));
+    PSC_BCUDA(b, cudaGetLastError());
+    PSC_BCUDA(b, cudaMemcpyAsync(b->h_gather + o_lm, b->d_gather + o_lm, b->gather_bytes - o_lm,
+                                 cudaMemcpyDeviceToHost, b->stream));
+    PSC_BCUDA(b, cudaStreamSynchronize(b->stream));
+    const double *lm = (const double *)(b->h_gather + o_lm);
+    const LMState *st = (const LMState *)(b->h_gather + o_st);
+    const int *flag = (const int *)(b->h_gather + o_fl);
+    if (lm_out) std::memcpy(lm_out, lm, sizeof(double) * tot);
     psc_status worst = PSC_OK;
-    for (size_t k = 0; k < b->ctxs.size(); ++k) {
+    for (int k = 0; k < n; ++k) {
         psc_ctx *c = b->ctxs[k];
-        psc_status st = lm_fetch(c, lm_out ? lm_out + off : nullptr, reps ? reps + k : nullptr, b->stream);
-        if (st != PSC_OK && worst == PSC_OK) { worst = st; b->err = c->err; fail(nullptr, st, c->err); }
-        off += 2 * (size_t)c->n_ant;
+        c->h_state = st[k];
+        if (reps) {
+            reps[k].n_iter = st[k].n_iter;
+            reps[k].n_eval = st[k].n_eval;
+            reps[k].reason = st[k].done ? st[k].reason : PSC_STOP_NONE;
+            reps[k].chi2 = st[k].chi2;
+            reps[k].lam = st[k].lam;
+        }
+        psc_status s_k = PSC_OK;
+        if (flag[k]) s_k = fail(c, PSC_ERR_TIMEOUT, "a bounded wait of the fused evaluation ran out; its results were discarded");
+        else if (st[k].done && st[k].reason == PSC_STOP_NUMERIC)
+            s_k = fail(c, PSC_ERR_NUMERIC, "solver stopped on a non-finite chi^2 or step");
+        if (s_k != PSC_OK && worst == PSC_OK) { worst = s_k; b->err = c->err; fail(nullptr, s_k, c->err); }
     }
     return worst;
 }

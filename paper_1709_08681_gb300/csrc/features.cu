@@ -42,14 +42,13 @@ __device__ __forceinline__ float2 lds_f2(unsigned addr) {
     return v;
 }
 
-__global__ void __launch_bounds__(128) stencil_kernel(const StencilArgs a) {
-    extern __shared__ float2 s_tab[];                 // tables, then the staged tile when a.stage
+// One brick of the stencil pass (s_tab: dynamic shared memory).
+__device__ __forceinline__ void stencil_brick(const StencilArgs &a, int brick, float2 *s_tab) {
     float2 *s_tile = s_tab + a.c_group * (a.max_tab_len + kTabPad);
     __shared__ int s_box[4];
     __shared__ double s_red[4][kSRed];
 
     const int tid = threadIdx.x;
-    const int brick = blockIdx.x;
     const int tt = brick % a.n_tt;
     const int cgi = (brick / a.n_tt) % a.n_cg;
     const int bl = brick / (a.n_tt * a.n_cg);
@@ -257,10 +256,37 @@ __global__ void __launch_bounds__(128) stencil_kernel(const StencilArgs a) {
     }
 }
 
+__global__ void __launch_bounds__(128) stencil_kernel(const StencilArgs a) {
+    extern __shared__ float2 s_tab[];                 // tables, then the staged tile when a.stage
+    stencil_brick(a, blockIdx.x, s_tab);
+}
+
+// Many (context, data) pairs in one launch: block b runs brick b - prefix[p]
+// of pair p, the last pair with prefix[p] <= b.  Every pair has the same
+// block shape (t_tile, c_group) and staging.
+__global__ void __launch_bounds__(128) stencil_batch_kernel(const StencilArgs *__restrict__ args,
+                                                            const long long *__restrict__ prefix, int n) {
+    extern __shared__ float2 s_tab[];
+    __shared__ StencilArgs s_a;
+    __shared__ int s_brick;
+    if (threadIdx.x == 0) {
+        const long long b = blockIdx.x;
+        int lo = 0, hi = n - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (prefix[mid] <= b) lo = mid; else hi = mid - 1;
+        }
+        s_a = args[lo];
+        s_brick = (int)(b - prefix[lo]);
+    }
+    __syncthreads();
+    stencil_brick(s_a, s_brick, s_tab);
+}
+
 // Per-baseline sums of the stencil partials: one thread per (sum, baseline),
 // bricks added in order (deterministic).
-__global__ void stencil_bl_kernel(const double *__restrict__ partials, int n_bl, int bpb, double *__restrict__ blsum) {
-    const long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+__device__ __forceinline__ void stencil_bl(const double *__restrict__ partials, int n_bl, int bpb,
+                                           double *__restrict__ blsum, long long id) {
     if (id >= (long long)n_bl * kSRed) return;
     const int k = (int)(id / n_bl), bl = (int)(id % n_bl);
     const size_t nb = (size_t)n_bl * bpb;
@@ -270,12 +296,22 @@ __global__ void stencil_bl_kernel(const double *__restrict__ partials, int n_bl,
     blsum[(size_t)bl * kSRed + k] = sum;
 }
 
+__global__ void stencil_bl_kernel(const double *__restrict__ partials, int n_bl, int bpb, double *__restrict__ blsum) {
+    stencil_bl(partials, n_bl, bpb, blsum, blockIdx.x * (long long)blockDim.x + threadIdx.x);
+}
+
+// Batched: blockIdx.y is the pair.
+__global__ void stencil_bl_batch_kernel(const FeatPair *__restrict__ pairs) {
+    const FeatPair p = pairs[blockIdx.y];
+    stencil_bl(p.partials, p.n_bl, p.bpb, p.blsum, blockIdx.x * (long long)blockDim.x + threadIdx.x);
+}
+
 // Features of one antenna per block: thread k < kSRed sums value k over the
 // antenna's baselines (partners in increasing order), then the block Newton
 // step and the 25 stencil ratios and chi^2 changes.
-__global__ void features_kernel(const double *__restrict__ blsum, int n_ant, float sigma, float *__restrict__ feat) {
+__device__ __forceinline__ void antenna_features(const double *__restrict__ blsum, int n_ant, float sigma,
+                                                 float *__restrict__ feat, int an) {
     __shared__ double v[kSRed];
-    const int an = blockIdx.x;
     const int k = threadIdx.x;
     if (k < kSRed) {
         double sum = 0.0;
@@ -308,10 +344,40 @@ __global__ void features_kernel(const double *__restrict__ blsum, int n_ant, flo
     }
 }
 
+__global__ void features_kernel(const double *__restrict__ blsum, int n_ant, float sigma, float *__restrict__ feat) {
+    antenna_features(blsum, n_ant, sigma, feat, blockIdx.x);
+}
+
+// Batched: blockIdx.y is the pair, blockIdx.x the antenna (blocks past the
+// pair's antennas return).
+__global__ void features_batch_kernel(const FeatPair *__restrict__ pairs, float sigma) {
+    const FeatPair p = pairs[blockIdx.y];
+    if ((int)blockIdx.x >= p.n_ant) return;
+    antenna_features(p.blsum, p.n_ant, sigma, p.feat, blockIdx.x);
+}
+
 }  // namespace
 
 size_t stencil_dyn_smem(int c_group, int max_tab_len, int stage) {
     return sizeof(float2) * ((size_t)c_group * (max_tab_len + kTabPad) + (stage ? (size_t)kTile * kTile : 0));
+}
+
+cudaError_t launch_features_batch(const StencilArgs *args_dev, const long long *prefix_dev, const FeatPair *pairs_dev,
+                                  int n, long long total_bricks, int threads, size_t dyn, int max_bl, int max_ant,
+                                  float sigma, cudaStream_t s) {
+    cudaError_t e = cudaFuncSetAttribute(stencil_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(dyn > 48 * 1024 ? dyn : 48 * 1024));
+    if (e != cudaSuccess) return e;
+    if (total_bricks > 0x7fffffffLL) return cudaErrorInvalidValue;
+    stencil_batch_kernel<<<(unsigned)total_bricks, threads, dyn, s>>>(args_dev, prefix_dev, n);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const long long n_sum = (long long)max_bl * kSRed;
+    stencil_bl_batch_kernel<<<dim3((unsigned)((n_sum + 255) / 256), n), 256, 0, s>>>(pairs_dev);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    features_batch_kernel<<<dim3(max_ant, n), 64, 0, s>>>(pairs_dev, sigma);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_features(const StencilArgs &a, double *blsum, int n_ant, float *feat, cudaStream_t s) {

@@ -103,6 +103,14 @@ struct StencilArgs {
     float sigma;               // stencil spacing (rad)
 };
 
+// Per-pair outputs of a batched feature pass (psc_features_batch).
+struct FeatPair {
+    const double *partials;    // [56][n_bl * bpb]
+    double *blsum;             // [n_bl][56]
+    float *feat;               // [n_ant][52]
+    int n_bl, bpb, n_ant;
+};
+
 // Arguments of the second-stage reductions of one context.
 struct RedArgs {
     const double *partials;    // [kRed][n_bl * bpb]
@@ -133,6 +141,7 @@ struct LMArgs {
     double *rhs;               // [2n] scratch
     const int2 *pairs;
     int n_ant, n_bl;
+    int *err;                  // the context's bounded-wait flag (read and cleared by psc_batch_end)
 };
 
 __host__ __device__ inline size_t ev_len(int n_ant, int n_bl) { return 1 + 2 * (size_t)n_ant + 3 * (size_t)n_ant + 4 * (size_t)n_bl; }
@@ -197,6 +206,13 @@ cudaError_t launch_step_max(const double *uvw, int nt, int n_bl, unsigned *out_b
 // Records msg as the context-free last error (psc_last_error(NULL)); returns st.
 psc_status set_global_error(psc_status st, const char *msg);
 cudaError_t launch_features(const StencilArgs &a, double *blsum, int n_ant, float *feat, cudaStream_t s);
+// Dynamic shared memory of one stencil block.
+size_t stencil_dyn_smem(int c_group, int max_tab_len, int stage);
+// The stencil pass, per-baseline sums and features of n pairs in three launches
+// (device tables of StencilArgs, first-brick prefixes [n + 1] and FeatPair).
+cudaError_t launch_features_batch(const StencilArgs *args_dev, const long long *prefix_dev, const FeatPair *pairs_dev,
+                                  int n, long long total_bricks, int threads, size_t dyn, int max_bl, int max_ant,
+                                  float sigma, cudaStream_t s);
 // Workspace (bytes) of launch_model_grid; the model grid goes to grid_out
 // and *err_dev points (inside ws) at a flag set if a tensor-core wait ran out.
 size_t model_grid_ws_bytes(int n_img, int n_grid);
