@@ -262,6 +262,13 @@ const char *psc_last_error(const psc_ctx *ctx);
  * dV/dl_i, dV/dm_i, dV/dl_j, dV/dm_j of each baseline (i, j).  Synchronises. */
 psc_status psc_predict(psc_ctx *ctx, const double *lm, void *vis_out, void *dvis_out);
 
+/* psc_predict with the offsets in device memory (lm_dev, [n_ant][2] radians,
+ * read by the kernel) and without synchronising: the launch is only
+ * enqueued on the context's stream, so that a caller simulating many
+ * intervals (one set of offsets each) pays no host round trip per interval.
+ * lm_dev must stay valid until the launch has run. */
+psc_status psc_predict_dev(psc_ctx *ctx, const double *lm_dev, void *vis_out, void *dvis_out);
+
 /* One fused evaluation at offsets lm (host [n_ant][2]) of the residuals
  * R = V^Obs - V^M, chi^2 (Eq. Chisq), the gradient (Eq. DCHIDD) and the
  * Gauss-Newton normal blocks.  vis_obs: device complex64 [n_time][n_bl][n_chan];

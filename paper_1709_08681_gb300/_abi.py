@@ -32,7 +32,7 @@ EXPORTS = ("psc_solve_opts_default", "psc_model_grid", "psc_model_grid_component
            "psc_predict", "psc_residual_grad", "psc_solve_offsets", "psc_lm_begin", "psc_lm_iterate",
            "psc_lm_end", "psc_lm_restart", "psc_set_tiling", "psc_set_grid_precision", "psc_set_staging",
            "psc_set_kernel_model", "psc_set_flat_tiling", "psc_set_track_tiling", "psc_set_wait_limit",
-           "psc_get_wait_limit", "psc_features_batch", "psc_features_batch_work", "psc_set_brick_order", "psc_fp32_fma_rate", "psc_profile", "psc_profile_read",
+           "psc_get_wait_limit", "psc_features_batch", "psc_features_batch_work", "psc_predict_dev", "psc_set_brick_order", "psc_fp32_fma_rate", "psc_profile", "psc_profile_read",
            "psc_residual_grad_noalloc", "psc_batch_create", "psc_batch_destroy", "psc_batch_last_error",
            "psc_batch_autotune", "psc_batch_begin", "psc_batch_restart", "psc_batch_kernel", "psc_batch_iterate", "psc_batch_end",
            "psc_solve_batch", "psc_batch_profile", "psc_batch_profile_read", "psc_features",
@@ -139,6 +139,7 @@ def lib():
             "psc_features_batch": (ctypes.c_int, [ctypes.POINTER(_V), ctypes.c_int, ctypes.POINTER(_V),
                                                   ctypes.POINTER(_V), _D, ctypes.c_double, ctypes.c_int, _V,
                                                   ctypes.c_size_t, _V, _V]),
+            "psc_predict_dev": (ctypes.c_int, [_V, _V, _V, _V]),
             "psc_features_batch_work": (ctypes.c_int, [ctypes.POINTER(_V), ctypes.c_int, ctypes.c_int,
                                                        ctypes.POINTER(ctypes.c_size_t)]),
             "psc_batch_iterate": (ctypes.c_int, [_V, ctypes.c_int]),
@@ -369,6 +370,10 @@ class Context:
     def psc_predict(self, lm, vis_out, dvis_out=None):
         lm = self._lm(lm)
         _check(lib().psc_predict(self.h, _dp(lm), _ptr(vis_out), _ptr(dvis_out)), self.h)
+
+    def psc_predict_dev(self, lm_dev, vis_out, dvis_out=None):
+        """psc_predict with device offsets (float64 [n_ant][2]); enqueued, no synchronisation."""
+        _check(lib().psc_predict_dev(self.h, _ptr(lm_dev), _ptr(vis_out), _ptr(dvis_out)), self.h)
 
     def psc_residual_grad(self, lm, vis_obs, w=None, w_scale=1.0, cross=False):
         lm = self._lm(lm)

@@ -955,6 +955,19 @@ psc_status psc_predict(psc_ctx *ctx, const double *lm, void *vis_out, void *dvis
     return PSC_OK;
 }
 
+psc_status psc_predict_dev(psc_ctx *ctx, const double *lm_dev, void *vis_out, void *dvis_out) {
+    if (!ctx) return fail(nullptr, PSC_ERR_ARG, "ctx is NULL");
+    if (!lm_dev || !vis_out) return fail(ctx, PSC_ERR_ARG, "lm_dev and vis_out must be non-NULL");
+    const int trk = ctx->trk_kv;                  // predictions always run the brick kernel
+    ctx->trk_kv = 0;
+    EvalArgs a = eval_args(ctx, lm_dev);
+    ctx->trk_kv = trk;
+    a.vis_out = (float2 *)vis_out;
+    a.dvis_out = (float2 *)dvis_out;
+    PSC_CUDA(ctx, launch_eval(a, true, ctx->stream));
+    return PSC_OK;
+}
+
 psc_status psc_residual_grad(psc_ctx *ctx, const double *lm, const void *vis_obs, const float *w, double w_scale,
                              double *chi2, double *grad, double *normal, double *cross) {
     if (!ctx) return fail(nullptr, PSC_ERR_ARG, "ctx is NULL");

@@ -171,11 +171,14 @@ class GeometryPool:
 
     def simulate(self, ctxs, lms, out, gen):
         """Observed data of each interval: the predictor at its true offsets
-        plus thermal noise from the seeded device generator."""
-        for c, lm, o in zip(ctxs, lms, out):
-            c.psc_predict(lm, o)
+        (all offsets uploaded at once, the launches enqueued without a host
+        round trip) plus thermal noise from the seeded device generator."""
+        lm_dev = torch.from_numpy(np.ascontiguousarray(np.stack(lms))).to(out.device)
+        for j, c in enumerate(ctxs):
+            c.psc_predict_dev(lm_dev[j], out[j])
         out += torch.view_as_complex(torch.randn(tuple(out.shape) + (2,), generator=gen, device=out.device)
                                      * self.wl.sigma_noise)
+        torch.cuda.current_stream().synchronize()      # lm_dev is read by the launches
 
     def close(self):
         for c in self.full + self.kept:
@@ -247,11 +250,15 @@ def evaluate_at_scale(pool: GeometryPool, net: "_abi.Mlp", n_eval: int, batch: i
         yh = y.double().cpu().numpy() * SIGMA_PRIOR
         return [yh[j * n_ant:(j + 1) * n_ant] for j in range(batch)]
 
-    def trace(lm0, truth):
-        """RMS error of every interval after 0..max_iter iterations: [max_iter + 1][batch]."""
+    def trace(lm0, truth, n_used):
+        """RMS error of every interval after 0, 1, ... iterations (at most
+        max_iter, stopping once the first n_used intervals all meet the target):
+        [iterations + 1][batch]."""
         bt.psc_batch_begin(lm0)
         rows = [[_rms_arcsec(a, b) for a, b in zip(lm0, truth)]]
         for _ in range(max_iter):
+            if max(rows[-1][:n_used]) <= target_arcsec:
+                break
             bt.psc_batch_iterate(1)
             lm, _ = bt.psc_batch_end()
             rows.append([_rms_arcsec(a, b) for a, b in zip(lm, truth)])
@@ -280,7 +287,7 @@ def evaluate_at_scale(pool: GeometryPool, net: "_abi.Mlp", n_eval: int, batch: i
         est_rms += [_rms_arcsec(a, b) for a, b in zip(lm_est[:n_used], truth[:n_used])]
         for arm, start in (("plain", lambda: zeros), ("learned", estimate)):
             lm0 = zeros if arm == "plain" else lm_est
-            tr = trace(lm0, truth)[:, :n_used]
+            tr = trace(lm0, truth, n_used)[:, :n_used]
             ok = np.all(tr <= target_arcsec, axis=1)
             k_all = int(np.argmax(ok)) if ok.any() else None
             each = [int(np.argmax(tr[:, j] <= target_arcsec)) if (tr[:, j] <= target_arcsec).any() else None
