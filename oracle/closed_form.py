@@ -26,16 +26,18 @@ from . import aperture
 from .psc import uv_lambda
 
 
-def efp(kind: str, rho, freq_hz: float, diam_m: float, alpha_per_dlambda: float):
+def efp(kind: str, rho, freq_hz: float, diam_m: float, alpha_per_dlambda: float, blockage: float = 0.0):
     dl = float(aperture.d_lambda(diam_m, freq_hz))
     if kind == "disk":
         return aperture.efp_disk(rho, dl)
     if kind == "gauss":
         return aperture.efp_gauss(rho, alpha_per_dlambda * dl)
+    if kind == "annulus":
+        return aperture.efp_annulus(rho, dl, blockage)
     raise ValueError(kind)
 
 
-def visibilities(uvw_m, freq_hz, n_ant, src, lm, kind, diam_m, alpha_per_dlambda, w_term=False):
+def visibilities(uvw_m, freq_hz, n_ant, src, lm, kind, diam_m, alpha_per_dlambda, w_term=False, blockage=0.0):
     """complex128 [nt][nbl][nc] direct-sum visibilities (see module docstring)."""
     lm = np.asarray(lm, dtype=np.float64)
     uvw_m = np.asarray(uvw_m, dtype=np.float64)
@@ -46,7 +48,7 @@ def visibilities(uvw_m, freq_hz, n_ant, src, lm, kind, diam_m, alpha_per_dlambda
     for c, f in enumerate(np.asarray(freq_hz, dtype=np.float64)):
         for lk, mk, sk in np.asarray(src, dtype=np.float64):
             rho = np.hypot(lk - lm[:, 0], mk - lm[:, 1])           # per antenna
-            e = efp(kind, rho, f, diam_m, alpha_per_dlambda)
+            e = efp(kind, rho, f, diam_m, alpha_per_dlambda, blockage)
             amp = sk * e[ij[:, 0]] * e[ij[:, 1]]                    # [nbl]
             ph = u[:, :, c] * lk + v[:, :, c] * mk
             if w_term:

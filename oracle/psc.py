@@ -54,6 +54,7 @@ class Model:
     alpha_per_dlambda: float
     decorrelation: int
     kernel: str = "gauss"      # "gauss": Eq. AIJPOINTING; "exact": the disks' exact kernel
+    ap_table: object = None    # ap_kind "table": dish-scale samples of A° (oracle.aperture)
 
     @property
     def du(self) -> float:
@@ -65,7 +66,8 @@ class Model:
     def tables(self):
         dl = aperture.d_lambda(self.diam_m, self.freq_hz)
         al = self.alpha()
-        return [aperture.radial_table(self.ap_kind, dl[c], al[c], self.du, self.oversample, self.support)
+        return [aperture.radial_table(self.ap_kind, dl[c], al[c], self.du, self.oversample, self.support,
+                                      self.ap_table)
                 for c in range(len(self.freq_hz))]
 
     def antenna_pairs(self):
