@@ -57,7 +57,7 @@ typedef enum {
     PSC_ERR_DEVICE = 7          /* a device-side consistency check failed */
 } psc_status;
 
-enum { PSC_AP_DISK = 0, PSC_AP_GAUSS = 1 };
+enum { PSC_AP_DISK = 0, PSC_AP_GAUSS = 1, PSC_AP_TABLE = 2 };
 enum { PSC_GRID_F32 = 0, PSC_GRID_BF16 = 1 };
 enum { PSC_STAGE_AUTO = 0, PSC_STAGE_NEVER = 1 };
 enum { PSC_KERNEL_GAUSS = 0, PSC_KERNEL_EXACT_DISK = 1 };
@@ -87,18 +87,31 @@ typedef struct {
  *                 Airy power beam, integral 1).
  *   PSC_AP_GAUSS: Gaussian voltage pattern exp(-alpha^2 rho^2) (Sec. 3);
  *                 A°(q) = (pi / 2 alpha^2) exp(-pi^2 q^2 / (2 alpha^2)).
+ *   PSC_AP_TABLE: a caller's radial A° (Sec. 3 and Alg. 1's second
+ *                 pre-compute: A° may carry a-priori primary-beam effects,
+ *                 such as a tapered illumination or blockage), given on the
+ *                 scale of the dish: table[k] = A°(q) D_lambda^2 at
+ *                 q / D_lambda = k / (table_len - 1), k = 0 .. table_len - 1,
+ *                 linear between samples, A° = 0 from q = D_lambda on (an
+ *                 aperture's autocorrelation ends at one diameter).  The
+ *                 samples are used as given: 2 pi int_0^1 T(x) x dx is the
+ *                 beam's PB(0) (1 for a normalised beam).  For the uniform
+ *                 disk T(x) = (8 / pi^2) (acos x - x sqrt(1 - x^2)).
  * alpha = alpha_per_dlambda * diam_m * nu / c at every channel.  For the disk,
  * alpha only enters the decorrelation factor (1.1442341... matches the Airy
  * half-power width).  A° is applied through a radial table at `oversample`
  * samples per cell, linearly interpolated:
  *   t = rho*ov, n = floor(t), f = t - n, A° = (1-f) tab[n] + f tab[n+1]
  *   if n + 1 < len, else 0;  tab[n] = A°(n du / ov) du^2,
- *   len = floor(ov * rho_max) + 2, rho_max = D_lambda/du (disk), (S/2)sqrt(2) (Gaussian). */
+ *   len = floor(ov * rho_max) + 2, rho_max = D_lambda/du (disk, table), (S/2)sqrt(2) (Gaussian).
+ * psc_create copies the table (the caller's array may be freed after it). */
 typedef struct {
-    int    kind;               /* PSC_AP_DISK or PSC_AP_GAUSS */
+    int    kind;               /* PSC_AP_DISK, PSC_AP_GAUSS or PSC_AP_TABLE */
     double diam_m;             /* aperture diameter (m), > 0 */
     double alpha_per_dlambda;  /* alpha / D_lambda, > 0 */
     int    decorrelation;      /* 1: keep exp(-alpha^2 |p_i - p_j|^2 / 2) of Eq. AIJPOINTING; 0: drop it */
+    const double *table;       /* PSC_AP_TABLE: host [table_len], finite; otherwise unused (NULL) */
+    int    table_len;          /* PSC_AP_TABLE: 2 .. 65536 */
 } psc_aperture;
 
 /* One block of observation (normally one solution interval, Algorithm 1's
@@ -142,6 +155,18 @@ typedef struct {
 
 /* Fills *opts with the defaults listed above. */
 void psc_solve_opts_default(psc_solve_opts *opts);
+
+/* Observation geometry: the baseline coordinates (u, v, w) of Eq. ME, in
+ * metres, from antenna positions.  ant_enu_m: host [n_ant][3] (east, north,
+ * up, metres) in the horizon frame at latitude lat_rad; the phase centre at
+ * declination dec_rad; ha_rad: host [n_time] hour angles (local sidereal time
+ * minus right ascension).  Writes uvw_out (device, caller-owned,
+ * [n_time][n_bl][3] float64) with b_ij = x_j - x_i for the baselines in the
+ * order (0,1), (0,2), ..., (1,2), ..., u east, v north, w towards the phase
+ * centre -- the layout psc_obs.uvw_dev takes.  FP64.  Synchronises.  Errors:
+ * PSC_ERR_ARG (sizes, NULL or non-finite inputs), PSC_ERR_CUDA. */
+psc_status psc_uvw(int n_ant, const double *ant_enu_m, double lat_rad, double dec_rad, int n_time, const double *ha_rad,
+                   void *uvw_out, void *stream);
 
 /* V° = F[I^M] (Algorithm 1, first pre-compute): the unnormalised DFT of the
  * image zero-padded to Ng x Ng, G[gy][gx] = sum I[row][col]

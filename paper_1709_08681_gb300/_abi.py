@@ -18,7 +18,7 @@ from . import build as _build
 
 PSC_OK, PSC_ERR_ARG, PSC_ERR_CUDA, PSC_ERR_OOM = 0, 1, 2, 3
 PSC_ERR_NOT_CONVERGED, PSC_ERR_TIMEOUT, PSC_ERR_NUMERIC, PSC_ERR_DEVICE = 4, 5, 6, 7
-PSC_AP_DISK, PSC_AP_GAUSS = 0, 1
+PSC_AP_DISK, PSC_AP_GAUSS, PSC_AP_TABLE = 0, 1, 2
 PSC_GRID_F32, PSC_GRID_BF16 = 0, 1
 PSC_STAGE_AUTO, PSC_STAGE_NEVER = 0, 1
 PSC_KERNEL_GAUSS, PSC_KERNEL_EXACT_DISK = 0, 1
@@ -32,7 +32,7 @@ EXPORTS = ("psc_solve_opts_default", "psc_model_grid", "psc_model_grid_component
            "psc_predict", "psc_residual_grad", "psc_solve_offsets", "psc_lm_begin", "psc_lm_iterate",
            "psc_lm_end", "psc_lm_restart", "psc_set_tiling", "psc_set_grid_precision", "psc_set_staging",
            "psc_set_kernel_model", "psc_set_flat_tiling", "psc_set_track_tiling", "psc_set_wait_limit",
-           "psc_get_wait_limit", "psc_features_batch", "psc_features_batch_work", "psc_predict_dev", "psc_set_brick_order", "psc_fp32_fma_rate", "psc_profile", "psc_profile_read",
+           "psc_get_wait_limit", "psc_features_batch", "psc_features_batch_work", "psc_predict_dev", "psc_uvw", "psc_set_brick_order", "psc_fp32_fma_rate", "psc_profile", "psc_profile_read",
            "psc_residual_grad_noalloc", "psc_batch_create", "psc_batch_destroy", "psc_batch_last_error",
            "psc_batch_autotune", "psc_batch_begin", "psc_batch_restart", "psc_batch_kernel", "psc_batch_iterate", "psc_batch_end",
            "psc_solve_batch", "psc_batch_profile", "psc_batch_profile_read", "psc_features",
@@ -53,7 +53,21 @@ class psc_grid_desc(ctypes.Structure):
 
 class psc_aperture(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("diam_m", ctypes.c_double), ("alpha_per_dlambda", ctypes.c_double),
-                ("decorrelation", ctypes.c_int)]
+                ("decorrelation", ctypes.c_int), ("table", ctypes.POINTER(ctypes.c_double)),
+                ("table_len", ctypes.c_int)]
+
+
+def make_aperture(ap_kind, diam_m, alpha_per_dlambda, decorrelation=1, table=None):
+    """psc_aperture for "disk", "gauss" or "table" (table: the caller's radial
+    A° samples, see PSC_AP_TABLE); returns (struct, the array it points at)."""
+    kind = {"disk": PSC_AP_DISK, "gauss": PSC_AP_GAUSS, "table": PSC_AP_TABLE}.get(ap_kind, ap_kind)
+    tab = None
+    ap = psc_aperture(int(kind), float(diam_m), float(alpha_per_dlambda), int(decorrelation), None, 0)
+    if table is not None:
+        tab = np.ascontiguousarray(table, dtype=np.float64)
+        ap.table = tab.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        ap.table_len = int(tab.size)
+    return ap, tab
 
 
 class psc_obs(ctypes.Structure):
@@ -140,6 +154,7 @@ def lib():
                                                   ctypes.POINTER(_V), _D, ctypes.c_double, ctypes.c_int, _V,
                                                   ctypes.c_size_t, _V, _V]),
             "psc_predict_dev": (ctypes.c_int, [_V, _V, _V, _V]),
+            "psc_uvw": (ctypes.c_int, [ctypes.c_int, _D, ctypes.c_double, ctypes.c_double, ctypes.c_int, _D, _V, _V]),
             "psc_features_batch_work": (ctypes.c_int, [ctypes.POINTER(_V), ctypes.c_int, ctypes.c_int,
                                                        ctypes.POINTER(ctypes.c_size_t)]),
             "psc_batch_iterate": (ctypes.c_int, [_V, ctypes.c_int]),
@@ -206,6 +221,21 @@ def psc_get_wait_limit():
     return int(lib().psc_get_wait_limit())
 
 
+def psc_uvw(ant_enu_m, lat_rad, dec_rad, ha_rad, uvw_out, stream=None):
+    """Baseline coordinates into uvw_out (device float64 [n_time][n_bl][3])."""
+    enu = np.ascontiguousarray(ant_enu_m, dtype=np.float64)
+    ha = np.ascontiguousarray(np.atleast_1d(ha_rad), dtype=np.float64)
+    n_ant = enu.shape[0]
+    if enu.shape != (n_ant, 3):
+        raise ValueError("ant_enu_m must be [n_ant][3]")
+    need = ha.size * (n_ant * (n_ant - 1) // 2) * 3
+    if uvw_out.numel() < need:
+        raise ValueError("uvw_out holds %d values; %d needed" % (uvw_out.numel(), need))
+    _check(lib().psc_uvw(int(n_ant), _dp(enu), float(lat_rad), float(dec_rad), int(ha.size), _dp(ha), _ptr(uvw_out),
+                         _stream(stream)))
+    return uvw_out
+
+
 def psc_solve_opts_default() -> psc_solve_opts:
     o = psc_solve_opts()
     lib().psc_solve_opts_default(ctypes.byref(o))
@@ -237,8 +267,7 @@ def psc_snapshot_components(comp_lmS, a, b, ap_kind, diam_m, alpha_per_dlambda, 
     by the beam ratio at freq_hz (host [n][3] in, new array out)."""
     comp = np.ascontiguousarray(comp_lmS, dtype=np.float64).reshape(-1, 3)
     out = np.empty_like(comp)
-    kind = {"disk": PSC_AP_DISK, "gauss": PSC_AP_GAUSS}.get(ap_kind, ap_kind)
-    ap = psc_aperture(int(kind), float(diam_m), float(alpha_per_dlambda), 1)
+    ap, _tab = make_aperture(ap_kind, diam_m, alpha_per_dlambda, 1)
     _check(lib().psc_snapshot_components(comp.shape[0], _dp(comp), float(a), float(b), ctypes.byref(ap),
                                          float(freq_hz), _dp(out)))
     return out
@@ -248,8 +277,7 @@ def psc_wstack_components(comp_lmS, a, b, ap_kind, diam_m, alpha_per_dlambda, fr
     """(l', m', S', n - 1) per component (host [n][3] true l, m, S in, [n][4] out)."""
     comp = np.ascontiguousarray(comp_lmS, dtype=np.float64).reshape(-1, 3)
     out = np.empty((comp.shape[0], 4))
-    kind = {"disk": PSC_AP_DISK, "gauss": PSC_AP_GAUSS}.get(ap_kind, ap_kind)
-    ap = psc_aperture(int(kind), float(diam_m), float(alpha_per_dlambda), 1)
+    ap, _tab = make_aperture(ap_kind, diam_m, alpha_per_dlambda, 1)
     _check(lib().psc_wstack_components(comp.shape[0], _dp(comp), float(a), float(b), ctypes.byref(ap),
                                        float(freq_hz), _dp(out)))
     return out
@@ -272,7 +300,7 @@ def psc_model_grid_wstack(comp_lmSn, n_grid, cell_rad, n_planes, w0, dw, grids_o
 
 def psc_residual_grad_noalloc(n_ant, n_time, n_chan, uvw_dev, freq_hz, ap_kind, diam_m, alpha_per_dlambda,
                               decorrelation, n_img, n_grid, cell_rad, support, oversample, grid_dev, lm, vis_obs,
-                              w=None, w_scale=1.0, cross=False, stream=None):
+                              w=None, w_scale=1.0, cross=False, stream=None, ap_table=None):
     """Allocation-free fused evaluation (no psc_ctx; scratch in the
     library's static device array).  Returns (chi2, g, H[, X]).
 
@@ -290,8 +318,7 @@ def psc_residual_grad_noalloc(n_ant, n_time, n_chan, uvw_dev, freq_hz, ap_kind, 
         if x is not None and not isinstance(x, int) and x.numel() < need:
             raise ValueError("%s holds %d elements; the problem needs %d" % (name, x.numel(), need))
     obs = psc_obs(int(n_ant), int(n_time), int(n_chan), _ptr(uvw_dev), _dp(freq))
-    kind = {"disk": PSC_AP_DISK, "gauss": PSC_AP_GAUSS}.get(ap_kind, ap_kind)
-    ap = psc_aperture(int(kind), float(diam_m), float(alpha_per_dlambda), int(decorrelation))
+    ap, _tab = make_aperture(ap_kind, diam_m, alpha_per_dlambda, decorrelation, ap_table)
     gd = psc_grid_desc(int(n_img), int(n_grid), float(cell_rad), int(support), int(oversample))
     lm = np.ascontiguousarray(lm, dtype=np.float64)
     n_bl = int(n_ant) * (int(n_ant) - 1) // 2
@@ -309,14 +336,13 @@ class Context:
     """Owns one ``psc_ctx``; ``uvw_dev`` and ``grid_dev`` must outlive it."""
 
     def __init__(self, n_ant, n_time, n_chan, uvw_dev, freq_hz, ap_kind, diam_m, alpha_per_dlambda,
-                 decorrelation, n_img, n_grid, cell_rad, support, oversample, grid_dev, stream=None):
+                 decorrelation, n_img, n_grid, cell_rad, support, oversample, grid_dev, stream=None, ap_table=None):
         self._keep = (uvw_dev, grid_dev)
         self.n_ant, self.n_time, self.n_chan = int(n_ant), int(n_time), int(n_chan)
         self.n_bl = self.n_ant * (self.n_ant - 1) // 2
         self._freq = np.ascontiguousarray(freq_hz, dtype=np.float64)
         obs = psc_obs(self.n_ant, self.n_time, self.n_chan, _ptr(uvw_dev), _dp(self._freq))
-        kind = {"disk": PSC_AP_DISK, "gauss": PSC_AP_GAUSS}.get(ap_kind, ap_kind)
-        ap = psc_aperture(int(kind), float(diam_m), float(alpha_per_dlambda), int(decorrelation))
+        ap, _tab = make_aperture(ap_kind, diam_m, alpha_per_dlambda, decorrelation, ap_table)
         gd = psc_grid_desc(int(n_img), int(n_grid), float(cell_rad), int(support), int(oversample))
         h = _V()
         _check(lib().psc_create(ctypes.byref(h), ctypes.byref(obs), ctypes.byref(ap), ctypes.byref(gd),

@@ -58,6 +58,7 @@ struct psc_ctx {
     int brick_order = PSC_ORDER_BASELINE;
     int *d_bl_order = nullptr;   // baselines in Morton order of their mid-interval (u, v)
     float *d_kmom = nullptr;     // exact disk kernel: lens-moment combinations (psc_set_kernel_model)
+    double *d_aptab = nullptr;   // PSC_AP_TABLE: the caller's table, copied
     // residual-w stack (psc_set_wstack): borrowed planes [wp_n][ng][ng], plane
     // w_p = wp_w0 + p wp_dw (wavelengths), residual w of the plane w = wp_a u + wp_b v
     const float2 *wp_grid = nullptr;
@@ -98,6 +99,25 @@ psc_status fail(psc_ctx *ctx, psc_status st, const std::string &msg) {
 
 long long psc::wait_limit() { return g_wait_polls; }
 
+bool psc::aperture_ok(const psc_aperture *ap, const char **why) {
+    if (!ap) { *why = "aperture is NULL"; return false; }
+    if (ap->kind != PSC_AP_DISK && ap->kind != PSC_AP_GAUSS && ap->kind != PSC_AP_TABLE) { *why = "unknown aperture kind"; return false; }
+    if (!(ap->diam_m > 0.0) || !(ap->alpha_per_dlambda > 0.0) || !std::isfinite(ap->diam_m) ||
+        !std::isfinite(ap->alpha_per_dlambda)) {
+        *why = "diam_m and alpha_per_dlambda must be finite and > 0";
+        return false;
+    }
+    if (ap->kind == PSC_AP_TABLE) {
+        if (!ap->table || ap->table_len < 2 || ap->table_len > 65536) {
+            *why = "PSC_AP_TABLE needs a table of 2 .. 65536 samples";
+            return false;
+        }
+        for (int k = 0; k < ap->table_len; ++k)
+            if (!std::isfinite(ap->table[k])) { *why = "the aperture table must be finite"; return false; }
+    }
+    return true;
+}
+
 psc_status psc::set_global_error(psc_status st, const char *msg) {
     g_err = msg;
     return st;
@@ -128,6 +148,7 @@ void free_ctx(psc_ctx *c) {
     cudaFree(c->d_kmom);
     cudaFree(c->d_tabcs);
     cudaFree(c->d_tmap);
+    cudaFree(c->d_aptab);
     cudaFree(c->d_err);
     cudaFree(c->d_bl_order);
     cudaFree(c->d_uvs);
@@ -326,13 +347,14 @@ psc_status eval_reduce(psc_ctx *c, const double *lm_dev, const void *vis_obs, co
 }
 
 // Stencil-feature arguments of one context and its data: every kept time
-// step of up to 32 in one tile, and as many channels as fill 128 threads (few
-// kept steps would otherwise leave most lanes of a 32-step tile idle).
+// step of up to 32 in one tile, and as many channels (at most 16) as fill 128
+// threads (few kept steps would otherwise leave most lanes of a 32-step tile
+// idle).
 StencilArgs stencil_args(const psc_ctx *ctx, const void *vis_obs, const float *w, double w_scale, double sigma,
                          int time_stride) {
     const int nts = (ctx->nt + time_stride - 1) / time_stride;
     const int t_tile = std::min(32, nts);
-    const int c_group = std::min(std::min(8, ctx->nc), std::max(1, 128 / t_tile));
+    const int c_group = std::min(std::min(16, ctx->nc), std::max(1, 128 / t_tile));
     StencilArgs a{};
     a.uvw = ctx->uvw;
     a.grid = ctx->grid;
@@ -436,6 +458,31 @@ const char *psc_last_error(const psc_ctx *ctx) {
     return ctx ? ctx->err.c_str() : g_err.c_str();
 }
 
+psc_status psc_uvw(int n_ant, const double *ant_enu_m, double lat_rad, double dec_rad, int n_time, const double *ha_rad,
+                   void *uvw_out, void *stream) {
+    if (n_ant < 2 || n_ant > 512) return fail(nullptr, PSC_ERR_ARG, "n_ant must be in [2, 512]");
+    if (n_time < 1) return fail(nullptr, PSC_ERR_ARG, "n_time must be >= 1");
+    if (!ant_enu_m || !ha_rad || !uvw_out) return fail(nullptr, PSC_ERR_ARG, "ant_enu_m, ha_rad and uvw_out must be non-NULL");
+    if (!std::isfinite(lat_rad) || !std::isfinite(dec_rad) || std::fabs(lat_rad) > M_PI / 2 || std::fabs(dec_rad) > M_PI / 2)
+        return fail(nullptr, PSC_ERR_ARG, "latitude and declination must be in [-pi/2, pi/2]");
+    for (int k = 0; k < 3 * n_ant; ++k)
+        if (!std::isfinite(ant_enu_m[k])) return fail(nullptr, PSC_ERR_ARG, "antenna positions must be finite");
+    for (int t = 0; t < n_time; ++t)
+        if (!std::isfinite(ha_rad[t])) return fail(nullptr, PSC_ERR_ARG, "hour angles must be finite");
+    cudaStream_t s = (cudaStream_t)stream;
+    double *d_enu = nullptr, *d_ha = nullptr;
+    cudaError_t e = dalloc(&d_enu, 3 * (size_t)n_ant);
+    if (e == cudaSuccess) e = dalloc(&d_ha, n_time);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_enu, ant_enu_m, sizeof(double) * 3 * n_ant, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_ha, ha_rad, sizeof(double) * n_time, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = launch_uvw(d_enu, n_ant, lat_rad, dec_rad, d_ha, n_time, (double *)uvw_out, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(d_enu);
+    cudaFree(d_ha);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "psc_uvw");
+    return PSC_OK;
+}
+
 psc_status psc_model_grid(const psc_grid_desc *gd, const float *image_dev, void *grid_out, void *stream) {
     std::string why;
     if (!check_grid_desc(gd, &why)) return fail(nullptr, PSC_ERR_ARG, why);
@@ -502,7 +549,8 @@ psc_status psc_snapshot_plane(const double *uvw_dev, long long n_rows, double *a
 psc_status psc_snapshot_components(int n_comp, const double *comp_in, double a, double b, const psc_aperture *ap,
                                    double freq_hz, double *comp_out) {
     if (n_comp < 0 || (n_comp > 0 && (!comp_in || !comp_out))) return fail(nullptr, PSC_ERR_ARG, "component arrays must be non-NULL");
-    if (!ap || (ap->kind != PSC_AP_DISK && ap->kind != PSC_AP_GAUSS)) return fail(nullptr, PSC_ERR_ARG, "unknown aperture");
+    if (!ap || (ap->kind != PSC_AP_DISK && ap->kind != PSC_AP_GAUSS))
+        return fail(nullptr, PSC_ERR_ARG, "the source move needs a disk or Gaussian aperture (its beam in closed form)");
     if (!(ap->diam_m > 0.0) || !(freq_hz > 0.0) || !std::isfinite(a) || !std::isfinite(b))
         return fail(nullptr, PSC_ERR_ARG, "diam_m, freq_hz must be > 0 and a, b finite");
     const double dl = ap->diam_m * freq_hz / kC;
@@ -621,8 +669,8 @@ psc_status psc_create(psc_ctx **out, const psc_obs *obs, const psc_aperture *ap,
     if (obs->n_time < 1) return fail(nullptr, PSC_ERR_ARG, "n_time must be >= 1");
     if (obs->n_chan < 1 || obs->n_chan > 4096) return fail(nullptr, PSC_ERR_ARG, "n_chan must be in [1, 4096]");
     if (!obs->uvw_dev || !obs->freq_hz || !grid_dev) return fail(nullptr, PSC_ERR_ARG, "uvw, freq and grid must be non-NULL");
-    if (ap->kind != PSC_AP_DISK && ap->kind != PSC_AP_GAUSS) return fail(nullptr, PSC_ERR_ARG, "unknown aperture kind");
-    if (!(ap->diam_m > 0.0) || !(ap->alpha_per_dlambda > 0.0)) return fail(nullptr, PSC_ERR_ARG, "diam_m and alpha_per_dlambda must be > 0");
+    const char *ap_why = nullptr;
+    if (!aperture_ok(ap, &ap_why)) return fail(nullptr, PSC_ERR_ARG, ap_why);
     for (int c = 0; c < obs->n_chan; ++c)
         if (!(obs->freq_hz[c] > 0.0) || !std::isfinite(obs->freq_hz[c])) return fail(nullptr, PSC_ERR_ARG, "frequencies must be > 0");
 
@@ -634,6 +682,7 @@ psc_status psc_create(psc_ctx **out, const psc_obs *obs, const psc_aperture *ap,
     c->nc = obs->n_chan;
     c->gd = *gd;
     c->ap = *ap;
+    c->ap.table = nullptr;                            // the copy on the device replaces the caller's array
     c->du = 1.0 / (gd->n_grid * gd->cell_rad);
     c->uvw = obs->uvw_dev;
     c->grid = (const float2 *)grid_dev;
@@ -646,7 +695,7 @@ psc_status psc_create(psc_ctx **out, const psc_obs *obs, const psc_aperture *ap,
     for (int k = 0; k < c->nc; ++k) {
         const double dl = ap->diam_m * obs->freq_hz[k] / kC;
         const double alpha = ap->alpha_per_dlambda * dl;
-        const double rho_max = ap->kind == PSC_AP_DISK ? dl / c->du : 0.5 * gd->support * std::sqrt(2.0);
+        const double rho_max = aperture_reach(ap->kind, dl, c->du, gd->support);
         const int L = (int)std::floor(ov * rho_max) + 2;
         if (L > (1 << 20)) { free_ctx(c); return fail(nullptr, PSC_ERR_ARG, "aperture table too long: aperture much wider than the grid cell"); }
         ch[k].uv_scale = obs->freq_hz[k] / (kC * c->du);
@@ -706,7 +755,13 @@ psc_status psc_create(psc_ctx **out, const psc_obs *obs, const psc_aperture *ap,
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_freq, obs->freq_hz, sizeof(double) * c->nc, cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_off, off.data(), sizeof(int) * c->nc, cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_len, len.data(), sizeof(int) * c->nc, cudaMemcpyHostToDevice, c->stream);
-    if (e == cudaSuccess) e = launch_tables(*ap, d_freq, c->nc, c->du, ov, gd->support, d_off, d_len, c->d_tabs, c->stream);
+    if (e == cudaSuccess && ap->kind == PSC_AP_TABLE) {
+        e = dalloc(&c->d_aptab, ap->table_len);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(c->d_aptab, ap->table, sizeof(double) * ap->table_len, cudaMemcpyHostToDevice, c->stream);
+    }
+    if (e == cudaSuccess)
+        e = launch_tables(*ap, c->d_aptab, d_freq, c->nc, c->du, ov, gd->support, d_off, d_len, c->d_tabs, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_state, 0, sizeof(LMState), c->stream);
     // baselines in Morton (Z) order of their (u, v) at the middle time step, for
     // PSC_ORDER_UV: bricks launched together then read nearby grid cells

@@ -8,9 +8,9 @@
 // point needs no psc_ctx and allocates nothing.  All of its working memory
 // lives in one file-scope device array of kScratchBytes (16 MiB), which every
 // GPU that loads the library holds until the process exits: channel
-// constants, A° tables, antenna pairs, the FP32 split of the baseline
-// coordinates, per-brick partial sums, per-baseline sums and the packed
-// result.  The caller still passes every input and output.
+// constants, A° tables (and a caller's aperture table), antenna pairs, the
+// FP32 split of the baseline coordinates, per-brick partial sums,
+// per-baseline sums and the packed result.  The caller still passes every input and output.
 //
 // The host cannot use the array's name as a device address (in host code it
 // names a host-side stand-in), so the address is looked up with
@@ -50,7 +50,7 @@ __global__ void noalloc_setup_kernel(const double *freq, int nc, double du, int 
         for (int c = 0; c < nc; ++c) {
             const double dl = diam_m * freq[c] / kC;
             const double alpha = alpha_per_dl * dl;
-            const double rho_max = kind == PSC_AP_DISK ? dl / du : 0.5 * support * sqrt(2.0);
+            const double rho_max = kind == PSC_AP_GAUSS ? 0.5 * support * sqrt(2.0) : dl / du;
             const int L = (int)floor(ov * rho_max) + 2;
             ChanConst ch;
             ch.uv_scale = freq[c] / (kC * du);
@@ -100,8 +100,8 @@ extern "C" psc_status psc_residual_grad_noalloc(const psc_obs *obs, const psc_ap
         return fail_arg("psc_residual_grad_noalloc: invalid grid descriptor");
     if (obs->n_ant < 2 || obs->n_ant > 512 || obs->n_time < 1 || obs->n_chan < 1 || obs->n_chan > 4096)
         return fail_arg("psc_residual_grad_noalloc: n_ant, n_time or n_chan out of range");
-    if ((ap->kind != PSC_AP_DISK && ap->kind != PSC_AP_GAUSS) || !(ap->diam_m > 0.0) || !(ap->alpha_per_dlambda > 0.0))
-        return fail_arg("psc_residual_grad_noalloc: invalid aperture");
+    const char *ap_why = nullptr;
+    if (!aperture_ok(ap, &ap_why)) return fail_arg("psc_residual_grad_noalloc: invalid aperture");
     if (!(w_scale > 0.0) || !std::isfinite(w_scale)) return fail_arg("psc_residual_grad_noalloc: w_scale must be > 0");
 
     const int n_ant = obs->n_ant, nc = obs->n_chan, nt = obs->n_time;
@@ -113,7 +113,7 @@ extern "C" psc_status psc_residual_grad_noalloc(const psc_obs *obs, const psc_ap
         const double f = obs->freq_hz[c];
         if (!(f > 0.0) || !std::isfinite(f)) return fail_arg("psc_residual_grad_noalloc: frequencies must be > 0");
         const double dl = ap->diam_m * f / kC;
-        const double rho_max = ap->kind == PSC_AP_DISK ? dl / du : 0.5 * gd->support * std::sqrt(2.0);
+        const double rho_max = aperture_reach(ap->kind, dl, du, gd->support);
         const double Ld = std::floor(ov * rho_max) + 2;
         if (Ld > (1 << 20)) return fail_arg("psc_residual_grad_noalloc: aperture table too long");
         const int L = (int)Ld;
@@ -132,6 +132,7 @@ extern "C" psc_status psc_residual_grad_noalloc(const psc_obs *obs, const psc_ap
     const size_t o_toff = off;  off = align256(off + sizeof(int) * nc);
     const size_t o_tlen = off;  off = align256(off + sizeof(int) * nc);
     const size_t o_tabs = off;  off = align256(off + sizeof(float2) * (size_t)total_tab);
+    const size_t o_aptb = off;  off = align256(off + (ap->kind == PSC_AP_TABLE ? sizeof(double) * ap->table_len : 0));
     const size_t o_pair = off;  off = align256(off + sizeof(int2) * (size_t)n_bl);
     const size_t o_uvs = off;   off = align256(off + sizeof(float4) * (size_t)nt * n_bl);
     const size_t o_part = off;  off = align256(off + sizeof(double) * kRed * n_bricks);
@@ -198,7 +199,10 @@ extern "C" psc_status psc_residual_grad_noalloc(const psc_obs *obs, const psc_ap
     noalloc_setup_kernel<<<1, 256, 0, s>>>(d_freq, nc, du, ap->kind, ap->diam_m, ap->alpha_per_dlambda, ov,
                                            gd->support, d_chan, d_toff, d_tlen, n_ant, d_pairs);
     NA_CUDA(cudaGetLastError());
-    NA_CUDA(launch_tables(*ap, d_freq, nc, du, ov, gd->support, d_toff, d_tlen, d_tabs, s));
+    double *d_aptb = (double *)(base + o_aptb);
+    if (ap->kind == PSC_AP_TABLE)
+        NA_CUDA(cudaMemcpyAsync(d_aptb, ap->table, sizeof(double) * ap->table_len, cudaMemcpyHostToDevice, s));
+    NA_CUDA(launch_tables(*ap, d_aptb, d_freq, nc, du, ov, gd->support, d_toff, d_tlen, d_tabs, s));
     NA_CUDA(launch_split_uv(obs->uvw_dev, (size_t)nt * n_bl, d_uvs, s));
 
     EvalArgs a{};

@@ -163,6 +163,11 @@ cudaError_t make_grid_maps(const float2 *grid, int ng, void *maps_dev, cudaStrea
 // Polls of a bounded mbarrier wait (the default unless psc_set_wait_limit changed it).
 long long wait_limit();
 
+// Baseline coordinates [n_time][n_bl][3] (m) from antenna positions (device
+// [n_ant][3] east, north, up) and hour angles (device [n_time]).
+cudaError_t launch_uvw(const double *enu_dev, int n_ant, double lat, double dec, const double *ha_dev, int n_time,
+                       double *uvw_dev, cudaStream_t s);
+
 // Launchers (defined in the .cu files).
 cudaError_t launch_eval(const EvalArgs &a, bool predict, cudaStream_t s);
 // Persistent fused launch over several contexts (device arrays of EvalArgs and
@@ -175,9 +180,17 @@ cudaError_t eval_batch_occupancy(int threads, size_t dyn, bool stacked, int *blo
 cudaError_t launch_reduce(const RedArgs &r, cudaStream_t s);
 cudaError_t launch_reduce_batch(const RedArgs *ra_dev, const int *bl_prefix_dev, int n_ctx, int total_bl,
                                 cudaStream_t s);
-cudaError_t launch_tables(const psc_aperture &ap, const double *freq_dev, int nc, double du, int ov,
-                          int support, const int *tab_off_dev, const int *tab_len_dev, float2 *tabs,
-                          cudaStream_t s);
+// A° tables of every channel (ap_table_dev: the caller's table on the device
+// for PSC_AP_TABLE, else unused).
+cudaError_t launch_tables(const psc_aperture &ap, const double *ap_table_dev, const double *freq_dev, int nc,
+                          double du, int ov, int support, const int *tab_off_dev, const int *tab_len_dev,
+                          float2 *tabs, cudaStream_t s);
+// Reach of the A° table in grid cells: D_lambda / du (disk, caller table), (S/2) sqrt(2) (Gaussian).
+inline double aperture_reach(int kind, double dl, double du, int support) {
+    return kind == PSC_AP_GAUSS ? 0.5 * support * 1.4142135623730951 : dl / du;
+}
+// Argument check of an aperture description (message in *why).
+bool aperture_ok(const psc_aperture *ap, const char **why);
 cudaError_t launch_lm_update(const LMArgs &a, cudaStream_t s);
 // Batched forms: one block per context (device arrays of LMArgs).
 cudaError_t launch_lm_update_batch(const LMArgs *la_dev, int n_ctx, size_t dyn, cudaStream_t s);

@@ -321,7 +321,7 @@ def evaluate_at_scale(pool: GeometryPool, net: "_abi.Mlp", n_eval: int, batch: i
     return out
 
 
-def run_at_scale(n_train=100_000, n_eval=10_000, n_geom_train=64, n_geom_eval=16, train_batch=1024,
+def run_at_scale(n_train=100_000, n_eval=10_000, n_geom_train=64, n_geom_eval=16, train_batch=4096,
                  eval_batch=256, steps=20_000, batch=1024, lr=1e-3, seed=0, time_stride=15, log=None):
     """The learned initialiser on the 64-antenna workload: a pool of
     training geometries (hour-angle windows over -3 h..+3 h) and a disjoint

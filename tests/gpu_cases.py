@@ -25,7 +25,7 @@ class GpuProblem:
         self.shape = (nt, nbl, len(m.freq_hz))
         self.ctx = _abi.Context(m.n_ant, nt, len(m.freq_hz), self.uvw, m.freq_hz, m.ap_kind, m.diam_m,
                                 m.alpha_per_dlambda, m.decorrelation, n_img, ng, m.cell_rad, m.support,
-                                m.oversample, self.grid)
+                                m.oversample, self.grid, ap_table=getattr(m, "ap_table", None))
         if t_tile or c_group or kv:
             self.ctx.psc_set_tiling(t_tile or 0, c_group or 0, kv or 0)
 
