@@ -19,6 +19,14 @@
 // FP64 solution for any matrix whose condition number is well below 1e7.  If
 // the FP32 factorisation meets a non-positive pivot or the refinement does
 // not converge, the system is factored in FP64 instead.
+//
+// Small systems live in shared memory and are factored column by column.
+// Large ones (2 n_ant above 90, e.g. 394 x 394 for 197 antennas) live in
+// global memory, where a column-by-column update would wait on one L2 round
+// trip per element: they are factored in panels of 32 columns (diagonal block
+// in shared memory, rows below solved from registers, trailing update in
+// 64 x 64 tiles staged in shared memory), solved in blocks of 32 rows, and the
+// FP64 residual is formed one warp per row with coalesced loads.
 #include <math.h>
 
 #include "psc_internal.cuh"
@@ -30,6 +38,21 @@ constexpr int kLmThreads = 256;
 constexpr int kSmallN2 = 90;            // 2 n_ant up to this: matrices in shared memory
 constexpr int kRefineMax = 6;
 constexpr double kRefineTol = 1e-12;
+constexpr int kPan = 32;                // panel width of the blocked factorisation
+constexpr int kTile = 64;               // trailing-update tile, 4 x 4 elements per thread
+constexpr int kLd = kPan + 1;           // padded row of the shared tiles
+constexpr int kWsFloats = 2 * kTile * kLd;
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ float warp_sum(float v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
 
 __device__ double block_max(double v, double *s) {
     const int tid = threadIdx.x;
@@ -84,6 +107,170 @@ __device__ void solve32_warp(const float *L, int n, float *y) {
         if (lane == 0) y[k] = xk;
         for (int i = lane; i < k; i += 32) y[i] -= L[(size_t)k * n + i] * xk;
         __syncwarp();
+    }
+}
+
+// Blocked FP32 Cholesky A = L L^T of the row-major n x n matrix in global
+// memory (lower triangle read and written; the upper one is left as it was),
+// all threads of the block (256).  ws: kWsFloats floats of shared memory.
+// Returns nonzero (uniformly) if a pivot is not positive.
+__device__ int chol32_blocked(float *A, int n, float *ws) {
+    __shared__ int s_bad;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tx = tid & 15, ty = tid >> 4;            // 16 x 16 threads, 4 x 4 elements each
+    float *D = ws;                                     // diagonal block; column kPan holds 1 / L_cc
+    float *Li = ws, *Lj = ws + kTile * kLd;            // trailing-update tiles (D is dead by then)
+    if (tid == 0) s_bad = 0;
+    for (int k0 = 0; k0 < n; k0 += kPan) {
+        const int kb = min(kPan, n - k0), m0 = k0 + kb;
+        for (int e = tid; e < kPan * kPan; e += blockDim.x) {
+            const int r = e / kPan, c = e % kPan;
+            D[r * kLd + c] = (r < kb && c <= r) ? A[(size_t)(k0 + r) * n + k0 + c] : 0.f;
+        }
+        __syncthreads();
+        if (warp == 0) {                               // factor the diagonal block, lane r owns row r
+            for (int c = 0; c < kb; ++c) {
+                const float d = D[c * kLd + c];
+                const bool nonpos = !(d > 0.f);
+                const float lcc = nonpos ? 1.f : sqrtf(d), inv = 1.f / lcc;
+                __syncwarp();
+                if (lane == c) { D[c * kLd + c] = lcc; D[c * kLd + kPan] = inv; }
+                if (lane > c && lane < kb) D[lane * kLd + c] *= inv;
+                __syncwarp();
+                if (lane > c && lane < kb) {
+                    const float lrc = D[lane * kLd + c];
+                    for (int t = c + 1; t <= lane; ++t) D[lane * kLd + t] -= lrc * D[t * kLd + c];
+                }
+                __syncwarp();
+                if (nonpos && lane == 0) s_bad = 1;
+            }
+        }
+        __syncthreads();
+        for (int e = tid; e < kb * kb; e += blockDim.x) {
+            const int r = e / kb, c = e % kb;
+            if (c <= r) A[(size_t)(k0 + r) * n + k0 + c] = D[r * kLd + c];
+        }
+        // rows below: L21 = A21 L11^-T, one thread per row (a panel with rows
+        // below is always full, kb = kPan)
+        for (int i = m0 + tid; i < n; i += blockDim.x) {
+            float *row = A + (size_t)i * n + k0;
+            float x[kPan];
+#pragma unroll
+            for (int c = 0; c < kPan; ++c) x[c] = row[c];
+#pragma unroll
+            for (int c = 0; c < kPan; ++c) {
+                float v = x[c];
+#pragma unroll
+                for (int t = 0; t < c; ++t) v = fmaf(-x[t], D[c * kLd + t], v);
+                x[c] = v * D[c * kLd + kPan];
+            }
+#pragma unroll
+            for (int c = 0; c < kPan; ++c) row[c] = x[c];
+        }
+        __syncthreads();
+        // trailing update: A22 -= L21 L21^T on the lower triangle, tile by tile
+        const int nt = (n - m0 + kTile - 1) / kTile;
+        for (int ti = 0; ti < nt; ++ti) {
+            for (int tj = 0; tj <= ti; ++tj) {
+                const int i0 = m0 + ti * kTile, j0 = m0 + tj * kTile;
+                for (int e = tid; e < kTile * kPan; e += blockDim.x) {
+                    const int r = e / kPan, c = e % kPan;
+                    Li[r * kLd + c] = i0 + r < n ? A[(size_t)(i0 + r) * n + k0 + c] : 0.f;
+                    Lj[r * kLd + c] = j0 + r < n ? A[(size_t)(j0 + r) * n + k0 + c] : 0.f;
+                }
+                __syncthreads();
+                float acc[4][4] = {};
+#pragma unroll 8
+                for (int t = 0; t < kPan; ++t) {
+                    float li[4], lj[4];
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) li[r] = Li[(ty + 16 * r) * kLd + t];
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) lj[c] = Lj[(tx + 16 * c) * kLd + t];
+#pragma unroll
+                    for (int r = 0; r < 4; ++r)
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) acc[r][c] = fmaf(li[r], lj[c], acc[r][c]);
+                }
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    const int i = i0 + ty + 16 * r;
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const int j = j0 + tx + 16 * c;
+                        if (i < n && j <= i) A[(size_t)i * n + j] -= acc[r][c];
+                    }
+                }
+                __syncthreads();
+            }
+        }
+    }
+    __syncthreads();
+    return s_bad;
+}
+
+// Solves L L^T y = y in place (y in shared memory) with the factor of
+// chol32_blocked, all threads of the block, in blocks of kPan rows: the
+// off-diagonal part of each block as warp dot products over rows of L (forward)
+// or columns of L (backward), the diagonal block by warp 0 from registers.
+// red: 8 x 32 floats of shared memory.
+__device__ void solve32_blocked(const float *L, int n, float *y, float *red) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    for (int k0 = 0; k0 < n; k0 += kPan) {             // L z = y
+        const int kb = min(kPan, n - k0);
+        for (int r = warp; r < kb; r += nw) {
+            const float *row = L + (size_t)(k0 + r) * n;
+            float p = 0.f;
+            for (int j = lane; j < k0; j += 32) p = fmaf(row[j], y[j], p);
+            p = warp_sum(p);
+            if (lane == 0) y[k0 + r] -= p;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            const float *row = L + (size_t)(k0 + lane) * n + k0;
+            float l[kPan], d = 1.f;
+#pragma unroll
+            for (int c = 0; c < kPan; ++c) {
+                l[c] = (lane < kb && c <= lane) ? row[c] : 0.f;
+                if (c == lane && lane < kb) d = l[c];
+            }
+            const float inv = 1.f / d;
+            float s = lane < kb ? y[k0 + lane] : 0.f;
+#pragma unroll
+            for (int c = 0; c < kPan; ++c) {
+                const float zc = __shfl_sync(kFull, s * inv, c);
+                if (lane > c) s = fmaf(-l[c], zc, s);
+            }
+            if (lane < kb) y[k0 + lane] = s * inv;
+        }
+        __syncthreads();
+    }
+    for (int k0 = ((n - 1) / kPan) * kPan; k0 >= 0; k0 -= kPan) {     // L^T x = z
+        const int kb = min(kPan, n - k0), m0 = k0 + kb;
+        float p = 0.f;
+        if (lane < kb)
+            for (int j = m0 + warp; j < n; j += nw) p = fmaf(L[(size_t)j * n + k0 + lane], y[j], p);
+        red[warp * 32 + lane] = p;
+        __syncthreads();
+        if (warp == 0) {
+            float s = 0.f;
+            for (int w = 0; w < nw; ++w) s += red[w * 32 + lane];
+            float col[kPan], d = 1.f;                  // lane r: column r of the diagonal block
+#pragma unroll
+            for (int j = 0; j < kPan; ++j) {
+                col[j] = (lane < kb && j >= lane && j < kb) ? L[(size_t)(k0 + j) * n + k0 + lane] : 0.f;
+                if (j == lane && lane < kb) d = col[j];
+            }
+            const float inv = 1.f / d;
+            s = lane < kb ? y[k0 + lane] - s : 0.f;
+#pragma unroll
+            for (int c = kPan - 1; c >= 0; --c) {
+                const float xc = __shfl_sync(kFull, s * inv, c);
+                if (lane < c) s = fmaf(-col[c], xc, s);
+            }
+            if (lane < kb) y[k0 + lane] = s * inv;
+        }
+        __syncthreads();
     }
 }
 
@@ -198,12 +385,14 @@ __global__ void __launch_bounds__(kLmThreads) lm_update_kernel(const LMArgs a0, 
         }
         __syncthreads();
     } else {
-        // dynamic shared memory: [A64 | A32] (small systems only) then b, r (FP64), y32
+        // dynamic shared memory: [A64 | A32] (small systems only) then b, r (FP64),
+        // y32, and the blocked factorisation's tiles (large systems only)
         double *A = small ? s_dyn : a.mat;
         float *A32 = small ? (float *)(s_dyn + (size_t)n2 * n2) : a.mat32;
         double *vb = small ? s_dyn + (size_t)n2 * n2 + ((size_t)n2 * n2 + 1) / 2 : s_dyn;
         double *vr = vb + n2;
         float *y32 = (float *)(vr + n2);
+        float *ws = y32 + n2;
 
         // assemble H + lam diag(H) (FP64, both triangles) and b = -g
         for (size_t k = tid; k < (size_t)n2 * n2; k += blockDim.x) A[k] = 0.0;
@@ -243,7 +432,7 @@ __global__ void __launch_bounds__(kLmThreads) lm_update_kernel(const LMArgs a0, 
         for (size_t k = tid; k < (size_t)n2 * n2; k += blockDim.x) A32[k] = (float)A[k];
         __syncthreads();
 
-        const int bad = chol32(A32, n2);
+        const int bad = small ? chol32(A32, n2) : chol32_blocked(A32, n2, ws);
         double bmax = 0.0;
         for (int p = tid; p < n2; p += blockDim.x) { bmax = fmax(bmax, fabs(vb[p])); vr[p] = vb[p]; }
         bmax = block_max(bmax, s_tmp);
@@ -251,17 +440,33 @@ __global__ void __launch_bounds__(kLmThreads) lm_update_kernel(const LMArgs a0, 
         for (int it = 0; it < kRefineMax && !bad && !converged; ++it) {
             for (int p = tid; p < n2; p += blockDim.x) y32[p] = (float)vr[p];
             __syncthreads();
-            if (tid < 32) solve32_warp(A32, n2, y32);
+            if (small) {
+                if (tid < 32) solve32_warp(A32, n2, y32);
+            } else {
+                solve32_blocked(A32, n2, y32, ws);
+            }
             __syncthreads();
             for (int p = tid; p < n2; p += blockDim.x) delta[p] += (double)y32[p];
             __syncthreads();
             double rmax = 0.0;
-            for (int p = tid; p < n2; p += blockDim.x) {         // r = b - A x in FP64
-                double acc = vb[p];
-                const double *row = A + (size_t)p * n2;
-                for (int q = 0; q < n2; ++q) acc = fma(-row[q], delta[q], acc);
-                vr[p] = acc;
-                rmax = fmax(rmax, fabs(acc));
+            if (small) {
+                for (int p = tid; p < n2; p += blockDim.x) {     // r = b - A x in FP64
+                    double acc = vb[p];
+                    const double *row = A + (size_t)p * n2;
+                    for (int q = 0; q < n2; ++q) acc = fma(-row[q], delta[q], acc);
+                    vr[p] = acc;
+                    rmax = fmax(rmax, fabs(acc));
+                }
+            } else {
+                const int lane = tid & 31, nw = blockDim.x >> 5;
+                for (int p = tid >> 5; p < n2; p += nw) {       // one warp per row
+                    const double *row = A + (size_t)p * n2;
+                    double acc = 0.0;
+                    for (int q = lane; q < n2; q += 32) acc = fma(row[q], delta[q], acc);
+                    const double r = vb[p] - warp_sum(acc);
+                    if (lane == 0) vr[p] = r;
+                    rmax = fmax(rmax, fabs(r));
+                }
             }
             rmax = block_max(rmax, s_tmp);
             converged = rmax <= kRefineTol * bmax;
@@ -307,12 +512,13 @@ __global__ void lm_restart_kernel(const LMArgs a0, const LMState *st00, const do
 }
 
 // Dynamic shared memory of the LM kernel: the FP64 matrix and its FP32 copy
-// for small systems, then b, r (FP64) and y (FP32), 2 n_ant each.
+// for small systems, then b, r (FP64) and y (FP32), 2 n_ant each, then the
+// blocked factorisation's tiles for large systems.
 size_t lm_dyn_smem(int n_ant) {
     const size_t n2 = 2 * (size_t)n_ant;
     const size_t vec = sizeof(double) * 2 * n2 + sizeof(float) * n2;
     if ((int)n2 <= kSmallN2) return sizeof(double) * (n2 * n2 + (n2 * n2 + 1) / 2) + vec;
-    return vec;
+    return vec + sizeof(float) * kWsFloats;
 }
 
 }  // namespace
