@@ -527,37 +527,34 @@ __global__ void __launch_bounds__(kMaxThreads, kW ? 4 : 0) eval_kernel(const Eva
     }                                                 // brick loop
 }
 
-// Second stage (a): per-baseline sums over its bricks, one warp per baseline,
-// a fixed butterfly order (deterministic).  partials is [kRed][n_bricks] with
-// the bricks of baseline bl at [bl * bpb, (bl + 1) * bpb).  Batched form: the
-// global warp number runs over the baselines of all contexts (bl_prefix).
+// Second stage (a): per-baseline sums over its bricks, one thread per
+// (baseline, sum), the bricks added in order (deterministic).  partials is
+// [kRed][n_bricks] with the bricks of baseline bl at [bl * bpb, (bl + 1) * bpb).
+// Batched form: the global baseline number runs over the baselines of all
+// contexts (bl_prefix).
 __global__ void bl_reduce_kernel(const RedArgs r0, const RedArgs *__restrict__ ra,
                                  const int *__restrict__ bl_prefix, int n_ctx) {
-    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
+    const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int gb = (int)(gt / kRed), k = (int)(gt - (long long)gb * kRed);
     RedArgs r = r0;
-    int bl = gw;
+    int bl = gb;
     if (ra != nullptr) {
-        if (gw >= bl_prefix[n_ctx]) return;
+        if (gb >= bl_prefix[n_ctx]) return;
         int lo = 0, hi = n_ctx - 1;
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
-            if (bl_prefix[mid] <= gw) lo = mid; else hi = mid - 1;
+            if (bl_prefix[mid] <= gb) lo = mid; else hi = mid - 1;
         }
         r = ra[lo];
-        bl = gw - bl_prefix[lo];
+        bl = gb - bl_prefix[lo];
     }
     if (bl >= r.n_bl) return;
     if (r.skip != nullptr && *r.skip) return;
     const size_t nb = (size_t)r.n_bl * r.bpb;
-    for (int k = 0; k < kRed; ++k) {
-        const double *p = r.partials + (size_t)k * nb + (size_t)bl * r.bpb;
-        double sum = 0.0;
-        for (int b = lane; b < r.bpb; b += 32) sum += p[b];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-        if (lane == 0) r.blsum[(size_t)bl * kRed + k] = sum;
-    }
+    const double *p = r.partials + (size_t)k * nb + (size_t)bl * r.bpb;
+    double sum = 0.0;
+    for (int b = 0; b < r.bpb; ++b) sum += p[b];
+    r.blsum[(size_t)bl * kRed + k] = sum;
 }
 
 // Second stage (b): chi^2, per-antenna gradient and diagonal blocks, cross
@@ -723,9 +720,8 @@ cudaError_t set_eval_smem(size_t dyn) {
 }
 
 cudaError_t launch_reduce(const RedArgs &r, cudaStream_t s) {
-    const int warps_per_block = 8;
-    bl_reduce_kernel<<<(r.n_bl + warps_per_block - 1) / warps_per_block, 32 * warps_per_block, 0, s>>>(
-        r, nullptr, nullptr, 0);
+    const long long threads = (long long)r.n_bl * kRed;
+    bl_reduce_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(r, nullptr, nullptr, 0);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     ev_kernel<<<1, kMaxThreads, 0, s>>>(r, nullptr);
@@ -734,10 +730,9 @@ cudaError_t launch_reduce(const RedArgs &r, cudaStream_t s) {
 
 cudaError_t launch_reduce_batch(const RedArgs *ra_dev, const int *bl_prefix_dev, int n_ctx, int total_bl,
                                 cudaStream_t s) {
-    const int warps_per_block = 8;
+    const long long threads = (long long)total_bl * kRed;
     RedArgs none{};
-    bl_reduce_kernel<<<(total_bl + warps_per_block - 1) / warps_per_block, 32 * warps_per_block, 0, s>>>(
-        none, ra_dev, bl_prefix_dev, n_ctx);
+    bl_reduce_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(none, ra_dev, bl_prefix_dev, n_ctx);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     ev_kernel<<<n_ctx, kMaxThreads, 0, s>>>(none, ra_dev);

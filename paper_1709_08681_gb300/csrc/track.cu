@@ -24,12 +24,15 @@
 // block barrier.  Boxes wider than 32 cells or taller than the tile fall back
 // to taps read from global memory with the ramp applied per tap.
 //
-// Sums.  Each lane accumulates its visibilities' chi^2 and gradient terms with
-// Knuth's TwoSum (compensated FP32: a running sum and its rounding error), and
-// the normal-equation terms in plain FP32.  One butterfly over the warp per
-// item (TwoSum again for the five compensated sums) gives the item's record;
-// records are summed per baseline in FP64 in a fixed order (bl_reduce_kernel),
-// so the results do not depend on which warp ran which item.
+// Sums.  Over the channels, each lane keeps ten moments from which the
+// item's fifteen sums follow (see the epilogue): chi^2 and the three gradient
+// moments with Knuth's TwoSum (compensated FP32: a running sum and its
+// rounding error), the six normal-equation moments in plain FP32.  One
+// butterfly over the warp per item (TwoSum again for the compensated four)
+// gives the item's moments; the fifteen sums are formed from them in FP64 and
+// written as the item's record.  Records are summed per baseline in FP64 in a
+// fixed order (bl_reduce_kernel), so the results do not depend on which warp
+// ran which item.
 //
 // Waits.  Every mbarrier wait is bounded (wait_limit polls).  A wait that runs
 // out sets *err; the warp then waits, with a fixed larger bound, for its own
