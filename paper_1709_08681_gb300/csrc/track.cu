@@ -184,6 +184,54 @@ __device__ __forceinline__ void pat_row2(uint32_t row, float2 dxo, float2 dyo2, 
     }
 }
 
+// Two rows of the pattern at once, for a lane's two visibilities: rows b and
+// 1 - b have the same width (the pattern is symmetric about the unit cell),
+// so they share the column offsets dxo; their row offsets differ (dyo2a,
+// dyo2b).  Returns each row's sums P (pa0, pa1; pb0, pb1) and adds both
+// rows' sum A dxo G' to su0, su1.  Twice the independent work per unrolled
+// body, half the row set-ups and dispatches.
+template <int kCW>
+__device__ __forceinline__ void pat_pair2(uint32_t row_a, uint32_t row_b, float2 dxo, float2 dyo2a, float2 dyo2b,
+                                          float2 step, uint32_t tab_adj, float2 &pa0, float2 &pa1, float2 &pb0,
+                                          float2 &pb1, float2 &su0, float2 &su1) {
+    const float2 magic = make_float2(8388608.0f, 8388608.0f);
+#pragma unroll
+    for (int k = 0; k < 2 * kCW; ++k) {
+        const float2 ga = lds_f2(row_a + 8u * k);
+        const float2 gb = lds_f2(row_b + 8u * k);
+        const float2 sa = ffma2(dxo, dxo, dyo2a);
+        const float2 sb = ffma2(dxo, dxo, dyo2b);
+        const float2 ta = make_float2(sqrt_fast(sa.x), sqrt_fast(sa.y));
+        const float2 tb = make_float2(sqrt_fast(sb.x), sqrt_fast(sb.y));
+        const float2 fa = fadd2_rz(ta, magic);
+        const float2 fb = fadd2_rz(tb, magic);
+        const float2 ea0 = lds_f2(tab_addr(tab_adj, fa.x));
+        const float2 ea1 = lds_f2(tab_addr(tab_adj, fa.y));
+        const float2 eb0 = lds_f2(tab_addr(tab_adj, fb.x));
+        const float2 eb1 = lds_f2(tab_addr(tab_adj, fb.y));
+        const float2 Aa = make_float2(fmaf(ta.x, ea0.y, ea0.x), fmaf(ta.y, ea1.y, ea1.x));
+        const float2 Ab = make_float2(fmaf(tb.x, eb0.y, eb0.x), fmaf(tb.y, eb1.y, eb1.x));
+        const float2 Ada = fmul2(Aa, dxo);
+        const float2 Adb = fmul2(Ab, dxo);
+        if (k == 0) {
+            pa0 = fmul2(make_float2(Aa.x, Aa.x), ga);
+            pa1 = fmul2(make_float2(Aa.y, Aa.y), ga);
+            pb0 = fmul2(make_float2(Ab.x, Ab.x), gb);
+            pb1 = fmul2(make_float2(Ab.y, Ab.y), gb);
+        } else {
+            fma2_acc(pa0.x, pa0.y, Aa.x, ga.x, ga.y);
+            fma2_acc(pa1.x, pa1.y, Aa.y, ga.x, ga.y);
+            fma2_acc(pb0.x, pb0.y, Ab.x, gb.x, gb.y);
+            fma2_acc(pb1.x, pb1.y, Ab.y, gb.x, gb.y);
+        }
+        fma2_acc(su0.x, su0.y, Ada.x, ga.x, ga.y);
+        fma2_acc(su1.x, su1.y, Ada.y, ga.x, ga.y);
+        fma2_acc(su0.x, su0.y, Adb.x, gb.x, gb.y);
+        fma2_acc(su1.x, su1.y, Adb.y, gb.x, gb.y);
+        dxo = fadd2(dxo, step);
+    }
+}
+
 // The same for one visibility per lane.
 template <int kCW>
 __device__ __forceinline__ void pat_row1(uint32_t row, float dxo, float dyo2, float ov, uint32_t tab_adj, float2 &p,
@@ -440,30 +488,38 @@ track_kernel(const EvalArgs a0, const EvalArgs *__restrict__ args, const long lo
                     const float2 uy = make_float2(fy[0], (float)(ny[1] - ny[0]) + fy[1]);
                     const float2 ov2 = make_float2(ov, ov), step2 = make_float2(-ov, -ov);
                     float2 su0 = make_float2(0.f, 0.f), su1 = su0, s00 = su0, s01 = su0, sv0 = su0, sv1 = su0;
-                    for (int rb = 1 - R; rb <= R; ++rb) {
-                        const float d = (float)(rb <= 0 ? -rb : rb - 1);
+                    const float2 eps2 = make_float2(1e-20f, 1e-20f);
+                    // rows b = -j and b = j + 1 (distance j from the unit cell) together
+                    for (int j = 0; j < R; ++j) {
+                        const float d = (float)j;
                         const float rem = fmaf(-d, d, rp2);
                         const int cw = (int)ceilf(rem * rsqrt_fast(rem));
-                        const float fb = (float)rb, fa = (float)(1 - cw);
-                        const float2 dy = fadd2(uy, make_float2(-fb, -fb));
-                        const float2 dyo = fmul2(dy, ov2);
-                        const float2 dyo2 = ffma2(dyo, dyo, make_float2(1e-20f, 1e-20f));
+                        const float fa = (float)(1 - cw);
+                        const float2 dya = fadd2(uy, make_float2(d, d));
+                        const float2 dyb = fadd2(uy, make_float2(-d - 1.f, -d - 1.f));
+                        const float2 dyoa = fmul2(dya, ov2), dyob = fmul2(dyb, ov2);
+                        const float2 dyo2a = ffma2(dyoa, dyoa, eps2), dyo2b = ffma2(dyob, dyob, eps2);
                         const float2 dxo = fmul2(fadd2(ux, make_float2(-fa, -fa)), ov2);
-                        const uint32_t row = base + (uint32_t)(rb * W + 1 - cw) * 8u;
-                        float2 p0, p1;
+                        const uint32_t row_a = base + (uint32_t)(1 - cw - j * W) * 8u;
+                        const uint32_t row_b = base + (uint32_t)((j + 1) * W + 1 - cw) * 8u;
+                        float2 pa0, pa1, pb0, pb1;
                         switch (cw) {
-                            case 1: pat_row2<1>(row, dxo, dyo2, step2, tab_adj, p0, p1, su0, su1); break;
-                            case 2: pat_row2<2>(row, dxo, dyo2, step2, tab_adj, p0, p1, su0, su1); break;
-                            case 3: pat_row2<3>(row, dxo, dyo2, step2, tab_adj, p0, p1, su0, su1); break;
-                            case 4: pat_row2<4>(row, dxo, dyo2, step2, tab_adj, p0, p1, su0, su1); break;
-                            case 5: pat_row2<5>(row, dxo, dyo2, step2, tab_adj, p0, p1, su0, su1); break;
-                            case 6: pat_row2<6>(row, dxo, dyo2, step2, tab_adj, p0, p1, su0, su1); break;
-                            default: pat_row2_n(row, 2 * cw, dxo, dyo2, step2, tab_adj, p0, p1, su0, su1);
+                            case 1: pat_pair2<1>(row_a, row_b, dxo, dyo2a, dyo2b, step2, tab_adj, pa0, pa1, pb0, pb1, su0, su1); break;
+                            case 2: pat_pair2<2>(row_a, row_b, dxo, dyo2a, dyo2b, step2, tab_adj, pa0, pa1, pb0, pb1, su0, su1); break;
+                            case 3: pat_pair2<3>(row_a, row_b, dxo, dyo2a, dyo2b, step2, tab_adj, pa0, pa1, pb0, pb1, su0, su1); break;
+                            case 4: pat_pair2<4>(row_a, row_b, dxo, dyo2a, dyo2b, step2, tab_adj, pa0, pa1, pb0, pb1, su0, su1); break;
+                            case 5: pat_pair2<5>(row_a, row_b, dxo, dyo2a, dyo2b, step2, tab_adj, pa0, pa1, pb0, pb1, su0, su1); break;
+                            case 6: pat_pair2<6>(row_a, row_b, dxo, dyo2a, dyo2b, step2, tab_adj, pa0, pa1, pb0, pb1, su0, su1); break;
+                            default:
+                                pat_row2_n(row_a, 2 * cw, dxo, dyo2a, step2, tab_adj, pa0, pa1, su0, su1);
+                                pat_row2_n(row_b, 2 * cw, dxo, dyo2b, step2, tab_adj, pb0, pb1, su0, su1);
                         }
-                        s00 = fadd2(s00, p0);
-                        s01 = fadd2(s01, p1);
-                        sv0 = ffma2(make_float2(dy.x, dy.x), p0, sv0);
-                        sv1 = ffma2(make_float2(dy.y, dy.y), p1, sv1);
+                        s00 = fadd2(s00, fadd2(pa0, pb0));
+                        s01 = fadd2(s01, fadd2(pa1, pb1));
+                        sv0 = ffma2(make_float2(dya.x, dya.x), pa0, sv0);
+                        sv0 = ffma2(make_float2(dyb.x, dyb.x), pb0, sv0);
+                        sv1 = ffma2(make_float2(dya.y, dya.y), pa1, sv1);
+                        sv1 = ffma2(make_float2(dyb.y, dyb.y), pb1, sv1);
                     }
                     S0[0] = s00; S0[1] = s01; Su[0] = su0; Su[1] = su1; Sv[0] = sv0; Sv[1] = sv1;
                 } else {
