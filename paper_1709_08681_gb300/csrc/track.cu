@@ -63,10 +63,6 @@ __device__ __forceinline__ void mbar_init(uint32_t mb) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(mb));
 }
 
-__device__ __forceinline__ void mbar_expect(uint32_t mb, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(mb), "r"(bytes) : "memory");
-}
-
 // Bounded wait for a phase of mbarrier mb: at most `limit` polls, each of
 // which may suspend the warp for up to a microsecond (a hint to the
 // hardware) instead of spinning.
@@ -81,16 +77,26 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mb, uint32_t parity, long lon
     return false;
 }
 
-// One 2-D TMA copy of a W x 8 box of the grid (x = column, y = row) to dst.
-__device__ __forceinline__ void tma_box(uint32_t dst, const void *map, int x, int y, uint32_t mb) {
-    asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
-                 :: "r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(mb) : "memory");
+// The asynchronous copies, each issued by the lanes whose p is nonzero (no
+// branch around it): the arrival that sets a phase's expected bytes; one 2-D
+// TMA copy of a W x 8 box of the grid (x = column, y = row) to dst; one
+// contiguous bulk copy (16-byte aligned addresses, size a multiple of 16).
+// All complete on mbarrier mb.
+__device__ __forceinline__ void mbar_expect_if(int p, uint32_t mb, uint32_t bytes) {
+    asm volatile("{\n.reg .pred q;\nsetp.ne.s32 q, %2, 0;\n@q mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n}"
+                 :: "r"(mb), "r"(bytes), "r"(p) : "memory");
 }
 
-// Contiguous bulk copy (16-byte aligned addresses, size a multiple of 16).
-__device__ __forceinline__ void bulk_copy(uint32_t dst, const void *src, uint32_t bytes, uint32_t mb) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                 :: "r"(dst), "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(mb) : "memory");
+__device__ __forceinline__ void tma_box_if(int p, uint32_t dst, const void *map, int x, int y, uint32_t mb) {
+    asm volatile("{\n.reg .pred q;\nsetp.ne.s32 q, %5, 0;\n"
+                 "@q cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n}"
+                 :: "r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(mb), "r"(p) : "memory");
+}
+
+__device__ __forceinline__ void bulk_copy_if(int p, uint32_t dst, const void *src, uint32_t bytes, uint32_t mb) {
+    asm volatile("{\n.reg .pred q;\nsetp.ne.s32 q, %4, 0;\n"
+                 "@q cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n}"
+                 :: "r"(dst), "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(mb), "r"(p) : "memory");
 }
 
 // Grid position x = u sc + Ng/2 from the FP32 split u = uh + ul and
@@ -119,6 +125,8 @@ __device__ __forceinline__ void two_sum_acc(float &s, float &c, float x) {
 
 struct Box {
     int x0, x1, y0, y1;   // inclusive cell range of the warp's footprint; x0 rounded down to even
+    int n0, m0;           // this lane's first visibility: base cell and fraction in the channel
+    float f0, g0;
 };
 
 // The warp's footprint in a channel of scale (sh, sl): the union over lanes
@@ -132,6 +140,10 @@ __device__ __forceinline__ Box chan_box(const float4 &q0, float sh, float sl, in
     trk_pos(q0.z, q0.w, sh, sl, half, m0, g0);
     const int R = (int)ceilf(rp);
     Box b;
+    b.n0 = n0;
+    b.m0 = m0;
+    b.f0 = f0;
+    b.g0 = g0;
     b.x0 = __reduce_min_sync(kFull, n0 + 1 - R) & ~1;     // TMA: the first column at a 16-byte boundary
     b.x1 = __reduce_max_sync(kFull, n0 + R);
     b.y0 = __reduce_min_sync(kFull, m0 + 1 - R);
@@ -363,6 +375,14 @@ track_kernel(const EvalArgs a0, const EvalArgs *__restrict__ args, const long lo
         const size_t uvs_step = (size_t)tstep * n_bl;
         const size_t kb0 = ((size_t)t0 * n_bl + bl) * nc;
         const size_t kstep = uvs_step * nc;
+        // (u, v) of the second visibility minus the first, metres: the split
+        // parts' differences are exact (neighbouring time steps)
+        float du1 = 0.f, dv1 = 0.f;
+        if (kV == 2 && tstep) {
+            const float4 q0 = uvs0[0], q1 = uvs0[uvs_step];
+            du1 = __fadd_rn(__fsub_rn(q1.x, q0.x), __fsub_rn(q1.y, q0.y));
+            dv1 = __fadd_rn(__fsub_rn(q1.z, q0.z), __fsub_rn(q1.w, q0.w));
+        }
         const float wv0 = tb < nt ? a.w_scale : 0.f;
         const float wv1 = tb + 1 < nt ? a.w_scale : 0.f;
         // the lane's running sums (see the epilogue): chi^2 and the gradient
@@ -390,13 +410,14 @@ track_kernel(const EvalArgs a0, const EvalArgs *__restrict__ args, const long lo
             const uint32_t tab_bytes = (uint32_t)n_tab * 8u;
             const uint32_t mb = bb ? mb1 : mb0;
             const uint32_t tile = tile0 + (uint32_t)bb * buf_bytes;
-            if (lane == 0) mbar_expect(mb, tab_bytes + (fits ? (uint32_t)(W * kBoxRows * ncp) * 8u : 0u));
+            mbar_expect_if(lane == 0, mb, tab_bytes + (fits ? (uint32_t)(W * kBoxRows * ncp) * 8u : 0u));
             __syncwarp();
-            if (fits && lane < ncp) {
+            {
                 const char *map = reinterpret_cast<const char *>(a.tmap) + (W == 8 ? 0 : W == 16 ? 128 : 256);
-                tma_box(tile + (uint32_t)(lane * kBoxRows * W * 8), map, bx.x0, bx.y0 + lane * kBoxRows, mb);
+                tma_box_if(fits && lane < ncp, tile + (uint32_t)(lane * kBoxRows * W * 8), map, bx.x0,
+                           bx.y0 + lane * kBoxRows, mb);
             }
-            if (lane == 31) bulk_copy(tile + (uint32_t)cap * 8u, a.tabs_cs + (size_t)cc * a.trk_stride, tab_bytes, mb);
+            bulk_copy_if(lane == 31, tile + (uint32_t)cap * 8u, a.tabs_cs + (size_t)cc * a.trk_stride, tab_bytes, mb);
             pending |= 1u << bb;
         };
         issue(0, ch.tab_len, box, 0);
@@ -419,11 +440,18 @@ track_kernel(const EvalArgs a0, const EvalArgs *__restrict__ args, const long lo
             // positions of the lane's visibilities in this channel
             int nx[kV], ny[kV];
             float fx[kV], fy[kV];
-#pragma unroll
-            for (int v = 0; v < kV; ++v) {
-                const float4 q = uvs0[v * uvs_step];
-                trk_pos(q.x, q.y, ch.sc_hi, ch.sc_lo, half, nx[v], fx[v]);
-                trk_pos(q.z, q.w, ch.sc_hi, ch.sc_lo, half, ny[v], fy[v]);
+            nx[0] = box.n0;                            // computed with the channel's box
+            ny[0] = box.m0;
+            fx[0] = box.f0;
+            fy[0] = box.g0;
+            if constexpr (kV == 2) {
+                // the second visibility moved by (du1, dv1) metres: a fraction of a cell
+                float gx = fmaf(du1, ch.sc_hi, fx[0]), gy = fmaf(dv1, ch.sc_hi, fy[0]);
+                const float flx = floorf(gx), fly = floorf(gy);
+                nx[1] = nx[0] + (int)flx;
+                ny[1] = ny[0] + (int)fly;
+                fx[1] = gx - flx;
+                fy[1] = gy - fly;
             }
             // the channel's observed visibilities and weights, loaded now so that
             // their latency hides behind the taps
@@ -634,16 +662,20 @@ track_kernel(const EvalArgs a0, const EvalArgs *__restrict__ args, const long lo
                 const float2 wR = make_float2(w * R.x, w * R.y);
                 const float2 wT = make_float2(w * T.x, w * T.y);
                 const float2 wX = make_float2(w * Px.x, w * Px.y);
-                rr = fmaf(wR.x, R.x, fmaf(wR.y, R.y, rr));
-                rt = fmaf(wR.x, T.x, fmaf(wR.y, T.y, rt));
-                rx = fmaf(wR.x, Px.x, fmaf(wR.y, Px.y, rx));
-                ry = fmaf(wR.x, Py.x, fmaf(wR.y, Py.y, ry));
-                tt = fmaf(wT.x, T.x, fmaf(wT.y, T.y, tt));
-                tx = fmaf(wT.x, Px.x, fmaf(wT.y, Px.y, tx));
-                ty = fmaf(wT.x, Py.x, fmaf(wT.y, Py.y, ty));
-                xx = fmaf(wX.x, Px.x, fmaf(wX.y, Px.y, xx));
-                xy = fmaf(wX.x, Py.x, fmaf(wX.y, Py.y, xy));
-                yy = fmaf(w * Py.x, Py.x, fmaf(w * Py.y, Py.y, yy));
+                // the ten inner products as five packed pairs
+                {
+                    float2 p;
+                    p = ffma2(make_float2(wR.y, wR.y), make_float2(R.y, T.y), ffma2(make_float2(wR.x, wR.x), make_float2(R.x, T.x), make_float2(rr, rt)));
+                    rr = p.x; rt = p.y;
+                    p = ffma2(make_float2(wR.y, wR.y), make_float2(Px.y, Py.y), ffma2(make_float2(wR.x, wR.x), make_float2(Px.x, Py.x), make_float2(rx, ry)));
+                    rx = p.x; ry = p.y;
+                    p = ffma2(make_float2(wT.y, wT.y), make_float2(T.y, Px.y), ffma2(make_float2(wT.x, wT.x), make_float2(T.x, Px.x), make_float2(tt, tx)));
+                    tt = p.x; tx = p.y;
+                    p = ffma2(make_float2(wT.y, wX.y), make_float2(Py.y, Py.y), ffma2(make_float2(wT.x, wX.x), make_float2(Py.x, Py.x), make_float2(ty, xy)));
+                    ty = p.x; xy = p.y;
+                    p = ffma2(make_float2(wX.y, w * Py.y), make_float2(Px.y, Py.y), ffma2(make_float2(wX.x, w * Py.x), make_float2(Px.x, Py.x), make_float2(xx, yy)));
+                    xx = p.x; yy = p.y;
+                }
             }
             const float d2 = 2.f * D, dd2 = d2 * D;
             two_sum_acc(chi_s, chi_c, rr);
