@@ -25,7 +25,8 @@
 // to taps read from global memory with the ramp applied per tap.
 //
 // Sums.  Over the channels, each lane keeps ten moments from which the
-// item's fifteen sums follow (see the epilogue): chi^2 and the three gradient
+// item's fifteen sums follow (see the epilogue), in shared memory rather than
+// registers, which the tap loops need: chi^2 and the three gradient
 // moments with Knuth's TwoSum (compensated FP32: a running sum and its
 // rounding error), the six normal-equation moments in plain FP32.  One
 // butterfly over the warp per item (TwoSum again for the compensated four)
@@ -304,6 +305,8 @@ track_kernel(const EvalArgs a0, const EvalArgs *__restrict__ args, const long lo
     extern __shared__ __align__(128) unsigned char trk_raw[];
     __shared__ EvalArgs s_args[kTrkWarps];
     __shared__ __align__(8) unsigned long long s_mbar[kTrkWarps][2];
+    __shared__ float s_mom[kTrkWarps][14][32];      // the lanes' running channel moments
+    __shared__ float4 s_q[kTrkWarps][2][32];         // per lane: first (u, v) split; (du1, dv1, wv0, wv1)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const bool persistent = queue != nullptr;
     EvalArgs &a = s_args[warp];
@@ -387,14 +390,22 @@ track_kernel(const EvalArgs a0, const EvalArgs *__restrict__ args, const long lo
         const float wv1 = tb + 1 < nt ? a.w_scale : 0.f;
         // the lane's running sums (see the epilogue): chi^2 and the gradient
         // moments compensated (TwoSum), the normal-equation moments plain
-        float chi_s = 0.f, chi_c = 0.f, e0s = 0.f, e0c = 0.f, e1s = 0.f, e1c = 0.f, e2s = 0.f, e2c = 0.f;
-        float hA0 = 0.f, hA1 = 0.f, hA2 = 0.f, hB1 = 0.f, hB2 = 0.f, hC = 0.f;
+        float (*mom)[32] = s_mom[warp];
+#pragma unroll
+        for (int k = 0; k < 14; ++k) mom[k][lane] = 0.f;
         // pattern radius: the aperture's reach plus the largest distance between
         // a lane's visibilities (consecutive time steps), plus a margin
         const float spread = (float)(kV - 1) * a.trk_spread + 1e-3f;
 
         ChanConst ch = a.chan[0];
-        Box box = chan_box(uvs0[0], ch.sc_hi, ch.sc_lo, half, ch.rho_max + spread);
+        // per-lane item constants live in shared memory, not registers (the tap
+        // loops need every register): the first visibility's (u, v) split,
+        // read for every channel's box, and (du1, dv1, weight 0, weight 1)
+        const float4 &q00 = s_q[warp][0][lane];
+        const float4 &qd = s_q[warp][1][lane];
+        s_q[warp][0][lane] = uvs0[0];
+        s_q[warp][1][lane] = make_float4(du1, dv1, wv0, wv1);
+        Box box = chan_box(q00, ch.sc_hi, ch.sc_lo, half, ch.rho_max + spread);
         bool ok = true;
         // issues the copies of channel cc (box bx, table length tl) into buffer bb
         auto issue = [&](int cc, int tl, const Box &bx, int bb) {
@@ -429,7 +440,7 @@ track_kernel(const EvalArgs a0, const EvalArgs *__restrict__ args, const long lo
             ChanConst chn = ch;
             if (c + 1 < nc) {
                 chn = a.chan[c + 1];
-                boxn = chan_box(uvs0[0], chn.sc_hi, chn.sc_lo, half, chn.rho_max + spread);
+                boxn = chan_box(q00, chn.sc_hi, chn.sc_lo, half, chn.rho_max + spread);
                 issue(c + 1, chn.tab_len, boxn, b ^ 1);
             }
             const bool got = mbar_wait(b ? mb1 : mb0, (par >> b) & 1u, a.wait_limit);
@@ -446,7 +457,7 @@ track_kernel(const EvalArgs a0, const EvalArgs *__restrict__ args, const long lo
             fy[0] = box.g0;
             if constexpr (kV == 2) {
                 // the second visibility moved by (du1, dv1) metres: a fraction of a cell
-                float gx = fmaf(du1, ch.sc_hi, fx[0]), gy = fmaf(dv1, ch.sc_hi, fy[0]);
+                float gx = fmaf(qd.x, ch.sc_hi, fx[0]), gy = fmaf(qd.y, ch.sc_hi, fy[0]);
                 const float flx = floorf(gx), fly = floorf(gy);
                 nx[1] = nx[0] + (int)flx;
                 ny[1] = ny[0] + (int)fly;
@@ -461,7 +472,7 @@ track_kernel(const EvalArgs a0, const EvalArgs *__restrict__ args, const long lo
             for (int v = 0; v < kV; ++v) {
                 const size_t k = kb0 + (size_t)v * kstep + c;
                 vo[v] = a.vis_obs[k];
-                wk[v] = (v == 0 ? wv0 : wv1) * (a.w != nullptr ? a.w[k] : 1.f);
+                wk[v] = (v == 0 ? qd.z : qd.w) * (a.w != nullptr ? a.w[k] : 1.f);
             }
             const float rmax = ch.rho_max, rmax2 = rmax * rmax;
             const int W = box_width(box);
@@ -472,7 +483,7 @@ track_kernel(const EvalArgs a0, const EvalArgs *__restrict__ args, const long lo
             float2 S0[kV], Su[kV], Sv[kV];
 #pragma unroll
             for (int v = 0; v < kV; ++v) S0[v] = Su[v] = Sv[v] = make_float2(0.f, 0.f);
-            float hx[kV], hy[kV];                      // positions relative to the ramp origin
+            float parg[kV];                            // the visibility half of the ramp: its phase
             if (staged) {
                 // cell half of the ramp, in place: cell (col, r) *= exp(-i pi du (col L + r M))
                 const int lw = W == 8 ? 3 : W == 16 ? 4 : 5;
@@ -496,8 +507,7 @@ track_kernel(const EvalArgs a0, const EvalArgs *__restrict__ args, const long lo
                 __syncwarp();
 #pragma unroll
                 for (int v = 0; v < kV; ++v) {
-                    hx[v] = (float)(nx[v] - box.x0) + fx[v];
-                    hy[v] = (float)(ny[v] - box.y0) + fy[v];
+                    parg[v] = pi_f * du * (((float)(nx[v] - box.x0) + fx[v]) * L + ((float)(ny[v] - box.y0) + fy[v]) * M);
                 }
                 // The tap pattern, the same for every lane of the warp (no
                 // divergence, no per-lane spans): relative to the lane's base
@@ -584,8 +594,7 @@ track_kernel(const EvalArgs a0, const EvalArgs *__restrict__ args, const long lo
                 const float2 zx = make_float2(zxc, zxs);
 #pragma unroll
                 for (int v = 0; v < kV; ++v) {
-                    hx[v] = fx[v];
-                    hy[v] = fy[v];
+                    parg[v] = pi_f * du * (fx[v] * L + fy[v] * M);
                     const int b_lo = max((int)floorf(fy[v] - rmax) + 1, -ny[v]);
                     const int b_hi = min((int)ceilf(fy[v] + rmax) - 1, a.ng - 1 - ny[v]);
                     for (int bb = b_lo; bb <= b_hi; ++bb) {
@@ -651,7 +660,7 @@ track_kernel(const EvalArgs a0, const EvalArgs *__restrict__ args, const long lo
 #pragma unroll
             for (int v = 0; v < kV; ++v) {
                 float s, co;
-                __sincosf(pi_f * du * (hx[v] * L + hy[v] * M), &s, &co);
+                __sincosf(parg[v], &s, &co);
                 const float2 ph = make_float2(co, s);
                 const float2 T = cmul(ph, S0[v]);
                 const float2 U = cmul(ph, Su[v]), W2 = cmul(ph, Sv[v]);
@@ -678,16 +687,19 @@ track_kernel(const EvalArgs a0, const EvalArgs *__restrict__ args, const long lo
                 }
             }
             const float d2 = 2.f * D, dd2 = d2 * D;
-            two_sum_acc(chi_s, chi_c, rr);
-            two_sum_acc(e0s, e0c, d2 * a2 * rt);
-            two_sum_acc(e1s, e1c, -d2 * rx);
-            two_sum_acc(e2s, e2c, -d2 * ry);
-            hA0 = fmaf(dd2, xx, hA0);
-            hA1 = fmaf(dd2, yy, hA1);
-            hA2 = fmaf(dd2, xy, hA2);
-            hB1 = fmaf(dd2 * a2, tx, hB1);
-            hB2 = fmaf(dd2 * a2, ty, hB2);
-            hC = fmaf(dd2 * a2 * a2, tt, hC);
+            {
+                float ms, mc;
+                ms = mom[0][lane]; mc = mom[1][lane]; two_sum_acc(ms, mc, rr); mom[0][lane] = ms; mom[1][lane] = mc;
+                ms = mom[2][lane]; mc = mom[3][lane]; two_sum_acc(ms, mc, d2 * a2 * rt); mom[2][lane] = ms; mom[3][lane] = mc;
+                ms = mom[4][lane]; mc = mom[5][lane]; two_sum_acc(ms, mc, -d2 * rx); mom[4][lane] = ms; mom[5][lane] = mc;
+                ms = mom[6][lane]; mc = mom[7][lane]; two_sum_acc(ms, mc, -d2 * ry); mom[6][lane] = ms; mom[7][lane] = mc;
+                mom[8][lane] = fmaf(dd2, xx, mom[8][lane]);
+                mom[9][lane] = fmaf(dd2, yy, mom[9][lane]);
+                mom[10][lane] = fmaf(dd2, xy, mom[10][lane]);
+                mom[11][lane] = fmaf(dd2 * a2, tx, mom[11][lane]);
+                mom[12][lane] = fmaf(dd2 * a2, ty, mom[12][lane]);
+                mom[13][lane] = fmaf(dd2 * a2 * a2, tt, mom[13][lane]);
+            }
             ch = chn;
             box = boxn;
         }
@@ -701,8 +713,9 @@ track_kernel(const EvalArgs a0, const EvalArgs *__restrict__ args, const long lo
             return;
         }
         // ---- the item's record: butterfly over the warp, then the fifteen sums in FP64 ----
-        float cmp[4][2] = {{chi_s, chi_c}, {e0s, e0c}, {e1s, e1c}, {e2s, e2c}};
-        float pln[6] = {hA0, hA1, hA2, hB1, hB2, hC};
+        float cmp[4][2] = {{mom[0][lane], mom[1][lane]}, {mom[2][lane], mom[3][lane]}, {mom[4][lane], mom[5][lane]},
+                           {mom[6][lane], mom[7][lane]}};
+        float pln[6] = {mom[8][lane], mom[9][lane], mom[10][lane], mom[11][lane], mom[12][lane], mom[13][lane]};
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
