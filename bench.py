@@ -396,22 +396,32 @@ def measure_e2e(wl, sess, vis, w, w_scale, stream, k_steps):
     batch.psc_batch_iterate(1)
     batch.psc_batch_end()
     d2h = 0
+    # events on the stream split each step into its copy and its iteration
+    # (recording them adds no synchronisation)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(k_steps)]
     torch.cuda.synchronize()
     t = time.perf_counter()
-    for _ in range(k_steps):
+    for k in range(k_steps):
+        ev[k][0].record(stream)
         with torch.cuda.stream(stream):
             vis.copy_(vis_h, non_blocking=True)
             if w_h is not None:
                 w.copy_(w_h, non_blocking=True)
+        ev[k][1].record(stream)
         batch.psc_batch_restart()
         batch.psc_batch_iterate(1)
+        ev[k][2].record(stream)
         lm_out, reps = batch.psc_batch_end()                   # synchronises; offsets + chi^2 to the host
         d2h = sum(x.nbytes for x in lm_out) + 8 * 5 * len(reps)
     dt = D.max_over_ranks(time.perf_counter() - t, device="cuda")
+    copy_ms = float(np.median([a.elapsed_time(b) for a, b, _ in ev]))
+    iter_ms = float(np.median([b.elapsed_time(c) for _, b, c in ev]))
     batch.close()
     h2d = vis.numel() * 8 + (w.numel() * 4 if w is not None else 0)
     return {"value": wl.n_vis * k_steps / dt / 1e9, "unit": "Gvis/s", "h2d_bytes_per_step": int(h2d),
-            "d2h_bytes_per_step": int(d2h), "steps": k_steps, "h2d_gb_per_s": h2d * k_steps / dt / 1e9}
+            "d2h_bytes_per_step": int(d2h), "steps": k_steps, "h2d_gb_per_s": h2d * k_steps / dt / 1e9,
+            "copy_ms_per_step": copy_ms, "copy_gb_per_s": h2d / copy_ms / 1e6, "iterate_ms_per_step": iter_ms}
 
 
 def setup_workload(wl, stream):
