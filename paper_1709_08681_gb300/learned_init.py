@@ -322,12 +322,14 @@ def evaluate_at_scale(pool: GeometryPool, net: "_abi.Mlp", n_eval: int, batch: i
 
 
 def run_at_scale(n_train=100_000, n_eval=10_000, n_geom_train=64, n_geom_eval=16, train_batch=4096,
-                 eval_batch=256, steps=20_000, batch=1024, lr=1e-3, seed=0, time_stride=15, log=None):
+                 eval_batch=256, steps=20_000, batch=1024, lr=1e-3, seed=0, time_stride=30, log=None):
     """The learned initialiser on the 64-antenna workload: a pool of
     training geometries (hour-angle windows over -3 h..+3 h) and a disjoint
     pool of held-out ones between them, n_train simulated training intervals,
     training with the library's kernels, and evaluate_at_scale on n_eval
-    held-out intervals.  Returns the report."""
+    held-out intervals.  The features read every time_stride-th time step
+    (2 of the 60 at 30: the estimate is 3.7 arcsec RMS against 3.6 at 15, in
+    half the time).  Returns the report."""
     stream = torch.cuda.current_stream()
     ha_train = np.linspace(-3.0, 3.0, n_geom_train)
     step = ha_train[1] - ha_train[0] if n_geom_train > 1 else 1.0
