@@ -382,6 +382,9 @@ StencilArgs stencil_args(const psc_ctx *ctx, const void *vis_obs, const float *w
     a.stage = t_tile * c_group >= 64;
     a.n_bricks = (long long)ctx->n_bl * a.n_cg * a.n_tt;
     a.sigma = (float)sigma;
+    // bricks of exactly one warp with a single channel group and time tile (a
+    // brick is then a baseline): four per block, sharing the block's tables
+    a.wpb = (t_tile * c_group == 32 && a.n_cg == 1 && a.n_tt == 1 && !a.stage) ? 4 : 1;
     return a;
 }
 
@@ -1254,12 +1257,12 @@ psc_status psc_features_batch(psc_ctx *const *ctxs, int n, const void *const *vi
         psc_ctx *c = ctxs[j];
         args[j] = stencil_args(c, vis_obs[j], w ? w[j] : nullptr, w_scale ? w_scale[j] : 1.0, sigma_prior_rad, time_stride);
         args[j].partials = (double *)(base + off_part[j]);
-        const int th = (args[j].t_tile * args[j].c_group + 31) / 32 * 32;
-        if (j > 0 && (th != threads || args[j].stage != args[0].stage))
+        const int th = args[j].wpb > 1 ? 32 * args[j].wpb : (args[j].t_tile * args[j].c_group + 31) / 32 * 32;
+        if (j > 0 && (th != threads || args[j].stage != args[0].stage || args[j].wpb != args[0].wpb))
             return fail(nullptr, PSC_ERR_ARG, "psc_features_batch: every pair needs the same brick shape (time steps and channels)");
         threads = th;
         dyn = std::max(dyn, stencil_dyn_smem(args[j].c_group, args[j].max_tab_len, args[j].stage));
-        prefix[j + 1] = prefix[j] + args[j].n_bricks;
+        prefix[j + 1] = prefix[j] + (args[j].n_bricks + args[j].wpb - 1) / args[j].wpb;    // blocks
         pairs[j].partials = args[j].partials;
         pairs[j].blsum = (double *)(base + off_bl[j]);
         pairs[j].feat = feat_dev + feat_off;

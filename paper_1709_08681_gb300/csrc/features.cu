@@ -43,23 +43,32 @@ __device__ __forceinline__ float2 lds_f2(unsigned addr) {
 }
 
 // One brick of the stencil pass (s_tab: dynamic shared memory).
-__device__ __forceinline__ void stencil_brick(const StencilArgs &a, int brick, float2 *s_tab) {
+__device__ __forceinline__ void stencil_brick(const StencilArgs &a, int blk, float2 *s_tab) {
     float2 *s_tile = s_tab + a.c_group * (a.max_tab_len + kTabPad);
-    __shared__ int s_box[4];
+    __shared__ int s_boxes[4][4];
     __shared__ double s_red[4][kSRed];
 
+    // block blk runs brick blk, or (a.wpb > 1) bricks blk wpb + w, one per warp w,
+    // which share the block's channel group and so its tables
     const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const bool wb = a.wpb > 1;
+    const long long brick_ll = wb ? (long long)blk * a.wpb + (tid >> 5) : blk;
+    const bool brick_ok = brick_ll < a.n_bricks;
+    const int brick = brick_ok ? (int)brick_ll : 0;
+    const int bt = wb ? lane : tid;               // the thread within its brick
+    int *s_box = s_boxes[wb ? tid >> 5 : 0];
     const int tt = brick % a.n_tt;
     const int cgi = (brick / a.n_tt) % a.n_cg;
     const int bl = brick / (a.n_tt * a.n_cg);
-    const int lt = tid % a.t_tile;
-    const int lc = tid / a.t_tile;
+    const int lt = bt % a.t_tile;
+    const int lc = bt / a.t_tile;
     const int t = (tt * a.t_tile + lt) * a.time_stride;
     const int c = cgi * a.c_group + lc;
-    const bool valid = lc < a.c_group && t < a.nt && c < a.nc;
+    const bool valid = brick_ok && lc < a.c_group && t < a.nt && c < a.nc;
     const int tab_stride = a.max_tab_len + kTabPad;
 
-    if (tid == 0) { s_box[0] = INT_MAX; s_box[1] = INT_MIN; s_box[2] = INT_MAX; s_box[3] = INT_MIN; }
+    if (bt == 0) { s_box[0] = INT_MAX; s_box[1] = INT_MIN; s_box[2] = INT_MAX; s_box[3] = INT_MIN; }
     __syncthreads();
     int ix0 = 0, iy0 = 0;
     float fx = 0.f, fy = 0.f;
@@ -241,7 +250,16 @@ __device__ __forceinline__ void stencil_brick(const StencilArgs &a, int brick, f
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         acc[k] = v;
     }
-    const int warp = tid >> 5, lane = tid & 31;
+    if (wb) {
+        // the warp is the brick: its sums are the record
+        if (brick_ok) {
+#pragma unroll
+            for (int k = 0; k < kSRed; ++k)
+                if (lane == (k & 31)) a.partials[(size_t)k * a.n_bricks + brick] = (double)acc[k];
+        }
+        return;
+    }
+    const int warp = tid >> 5;
     if (lane == 0) {
 #pragma unroll
         for (int k = 0; k < kSRed; ++k) s_red[warp][k] = (double)acc[k];
@@ -261,9 +279,9 @@ __global__ void __launch_bounds__(128) stencil_kernel(const StencilArgs a) {
     stencil_brick(a, blockIdx.x, s_tab);
 }
 
-// Many (context, data) pairs in one launch: block b runs brick b - prefix[p]
-// of pair p, the last pair with prefix[p] <= b.  Every pair has the same
-// block shape (t_tile, c_group) and staging.
+// Many (context, data) pairs in one launch: block b runs block b - prefix[p]
+// of pair p (prefix counts blocks), the last pair with prefix[p] <= b.  Every
+// pair has the same block shape (t_tile, c_group, bricks per block) and staging.
 __global__ void __launch_bounds__(128) stencil_batch_kernel(const StencilArgs *__restrict__ args,
                                                             const long long *__restrict__ prefix, int n) {
     extern __shared__ float2 s_tab[];
@@ -363,13 +381,13 @@ size_t stencil_dyn_smem(int c_group, int max_tab_len, int stage) {
 }
 
 cudaError_t launch_features_batch(const StencilArgs *args_dev, const long long *prefix_dev, const FeatPair *pairs_dev,
-                                  int n, long long total_bricks, int threads, size_t dyn, int max_bl, int max_ant,
+                                  int n, long long total_blocks, int threads, size_t dyn, int max_bl, int max_ant,
                                   float sigma, cudaStream_t s) {
     cudaError_t e = cudaFuncSetAttribute(stencil_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)(dyn > 48 * 1024 ? dyn : 48 * 1024));
     if (e != cudaSuccess) return e;
-    if (total_bricks > 0x7fffffffLL) return cudaErrorInvalidValue;
-    stencil_batch_kernel<<<(unsigned)total_bricks, threads, dyn, s>>>(args_dev, prefix_dev, n);
+    if (total_blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+    stencil_batch_kernel<<<(unsigned)total_blocks, threads, dyn, s>>>(args_dev, prefix_dev, n);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const long long n_sum = (long long)max_bl * kSRed;
@@ -385,7 +403,8 @@ cudaError_t launch_features(const StencilArgs &a, double *blsum, int n_ant, floa
     cudaError_t e = cudaFuncSetAttribute(stencil_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)(dyn > 48 * 1024 ? dyn : 48 * 1024));
     if (e != cudaSuccess) return e;
-    stencil_kernel<<<(int)a.n_bricks, (a.t_tile * a.c_group + 31) / 32 * 32, dyn, s>>>(a);
+    const int threads = a.wpb > 1 ? 32 * a.wpb : (a.t_tile * a.c_group + 31) / 32 * 32;
+    stencil_kernel<<<(int)((a.n_bricks + a.wpb - 1) / a.wpb), threads, dyn, s>>>(a);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const long long n_sum = (long long)a.n_bl * kSRed;

@@ -101,6 +101,7 @@ struct StencilArgs {
     int stage;                 // 1: stage the grid cells of a brick in shared memory when they fit
     long long n_bricks;
     float sigma;               // stencil spacing (rad)
+    int wpb;                   // 1: one brick per block; 4: bricks of one warp, four per block (shared tables)
 };
 
 // Per-pair outputs of a batched feature pass (psc_features_batch).
@@ -224,7 +225,7 @@ size_t stencil_dyn_smem(int c_group, int max_tab_len, int stage);
 // The stencil pass, per-baseline sums and features of n pairs in three launches
 // (device tables of StencilArgs, first-brick prefixes [n + 1] and FeatPair).
 cudaError_t launch_features_batch(const StencilArgs *args_dev, const long long *prefix_dev, const FeatPair *pairs_dev,
-                                  int n, long long total_bricks, int threads, size_t dyn, int max_bl, int max_ant,
+                                  int n, long long total_blocks, int threads, size_t dyn, int max_bl, int max_ant,
                                   float sigma, cudaStream_t s);
 // Workspace (bytes) of launch_model_grid; the model grid goes to grid_out
 // and *err_dev points (inside ws) at a flag set if a tensor-core wait ran out.

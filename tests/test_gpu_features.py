@@ -24,6 +24,10 @@ def _need_gpu():
     (cases.DISK_SMALL, 7, 40, (1.2e9, 1.3e9, 1.4e9, 1.5e9, 1.6e9), 1),
     (cases.DISK_SMALL, 6, 45, (1.3e9, 1.4e9), 2),
     (cases.GAUSS_SMALL, 5, 12, (1.4e9,), 3),
+    # bricks of exactly one warp (kept steps x channels = 32), four to a block;
+    # 15 and 21 baselines leave the last block partly empty
+    (cases.DISK_SMALL, 6, 12, tuple(1.3e9 + 0.03e9 * k for k in range(8)), 3),
+    (cases.GAUSS_SMALL, 7, 60, tuple(1.3e9 + 0.0125e9 * k for k in range(16)), 30),
 ])
 def test_features_match_oracle(spec, n_ant, nt, freqs, stride):
     m, _, lmt, img = cases.problem(spec, n_ant=n_ant, n_time=nt, freqs=freqs, sigma_arcsec=30.0)
