@@ -166,41 +166,12 @@ __device__ __forceinline__ unsigned tab_addr(unsigned tab_adj, float tf) {
     return tab_adj + ((unsigned)__float_as_int(tf) << 3);
 }
 
-// One row of the tap pattern for a lane's two visibilities, unrolled: the
-// 2 kCW cells from shared address `row` (the row's first column a = 1 - kCW),
-// visibility v's first column at dxo.v = (x_v - a) ov.  Returns the row sums
-// P_v = sum A G' in p0, p1 and adds sum A dxo G' to su0, su1.
-template <int kCW>
-__device__ __forceinline__ void pat_row2(uint32_t row, float2 dxo, float2 dyo2, float2 step, uint32_t tab_adj,
-                                         float2 &p0, float2 &p1, float2 &su0, float2 &su1) {
-    const float2 magic = make_float2(8388608.0f, 8388608.0f);
-#pragma unroll
-    for (int k = 0; k < 2 * kCW; ++k) {
-        const float2 g = lds_f2(row + 8u * k);
-        const float2 s2 = ffma2(dxo, dxo, dyo2);
-        const float2 t = make_float2(sqrt_fast(s2.x), sqrt_fast(s2.y));
-        const float2 tf = fadd2_rz(t, magic);                       // floor(t) + 2^23, both
-        const float2 e0 = lds_f2(tab_addr(tab_adj, tf.x));
-        const float2 e1 = lds_f2(tab_addr(tab_adj, tf.y));
-        const float2 A = make_float2(fmaf(t.x, e0.y, e0.x), fmaf(t.y, e1.y, e1.x));
-        const float2 Ad = fmul2(A, dxo);
-        if (k == 0) {
-            p0 = fmul2(make_float2(A.x, A.x), g);
-            p1 = fmul2(make_float2(A.y, A.y), g);
-        } else {
-            fma2_acc(p0.x, p0.y, A.x, g.x, g.y);
-            fma2_acc(p1.x, p1.y, A.y, g.x, g.y);
-        }
-        fma2_acc(su0.x, su0.y, Ad.x, g.x, g.y);
-        fma2_acc(su1.x, su1.y, Ad.y, g.x, g.y);
-        dxo = fadd2(dxo, step);
-    }
-}
-
-// Two rows of the pattern at once, for a lane's two visibilities: rows b and
-// 1 - b have the same width (the pattern is symmetric about the unit cell),
-// so they share the column offsets dxo; their row offsets differ (dyo2a,
-// dyo2b).  Returns each row's sums P (pa0, pa1; pb0, pb1) and adds both
+// Two rows of the tap pattern at once, for a lane's two visibilities,
+// unrolled.  Rows b and 1 - b have the same width (the pattern is symmetric
+// about the unit cell): 2 kCW cells each from shared addresses row_a and
+// row_b (the rows' first column a = 1 - kCW), so they share the column offsets
+// dxo.v = (x_v - a) ov; their squared row offsets differ (dyo2a, dyo2b).
+// Returns each row's sums P_v = sum A G' (pa0, pa1; pb0, pb1) and adds both
 // rows' sum A dxo G' to su0, su1.  Twice the independent work per unrolled
 // body, half the row set-ups and dispatches.
 template <int kCW>
@@ -245,7 +216,9 @@ __device__ __forceinline__ void pat_pair2(uint32_t row_a, uint32_t row_b, float2
     }
 }
 
-// The same for one visibility per lane.
+// One row of the pattern for one visibility per lane, unrolled: 2 kCW cells
+// from `row`, the first at dxo = (x - a) ov.  Returns P = sum A G' in p and
+// adds sum A dxo G' to su.
 template <int kCW>
 __device__ __forceinline__ void pat_row1(uint32_t row, float dxo, float dyo2, float ov, uint32_t tab_adj, float2 &p,
                                          float2 &su) {
@@ -394,8 +367,10 @@ track_kernel(const EvalArgs a0, const EvalArgs *__restrict__ args, const long lo
 #pragma unroll
         for (int k = 0; k < 14; ++k) mom[k][lane] = 0.f;
         // pattern radius: the aperture's reach plus the largest distance between
-        // a lane's visibilities (consecutive time steps), plus a margin
-        const float spread = (float)(kV - 1) * a.trk_spread + 1e-3f;
+        // a lane's visibilities in this item (metres here; times the channel's
+        // scale, cells), plus a margin
+        const float sp_m = kV == 2 ? __uint_as_float(__reduce_max_sync(kFull, __float_as_uint(sqrtf(du1 * du1 + dv1 * dv1))))
+                                   : 0.f;
 
         ChanConst ch = a.chan[0];
         // per-lane item constants live in shared memory, not registers (the tap
@@ -405,7 +380,7 @@ track_kernel(const EvalArgs a0, const EvalArgs *__restrict__ args, const long lo
         const float4 &qd = s_q[warp][1][lane];
         s_q[warp][0][lane] = uvs0[0];
         s_q[warp][1][lane] = make_float4(du1, dv1, wv0, wv1);
-        Box box = chan_box(q00, ch.sc_hi, ch.sc_lo, half, ch.rho_max + spread);
+        Box box = chan_box(q00, ch.sc_hi, ch.sc_lo, half, ch.rho_max + fmaf(sp_m, ch.sc_hi, 1e-3f));
         bool ok = true;
         // issues the copies of channel cc (box bx, table length tl) into buffer bb
         auto issue = [&](int cc, int tl, const Box &bx, int bb) {
@@ -440,7 +415,7 @@ track_kernel(const EvalArgs a0, const EvalArgs *__restrict__ args, const long lo
             ChanConst chn = ch;
             if (c + 1 < nc) {
                 chn = a.chan[c + 1];
-                boxn = chan_box(q00, chn.sc_hi, chn.sc_lo, half, chn.rho_max + spread);
+                boxn = chan_box(q00, chn.sc_hi, chn.sc_lo, half, chn.rho_max + fmaf(sp_m, chn.sc_hi, 1e-3f));
                 issue(c + 1, chn.tab_len, boxn, b ^ 1);
             }
             const bool got = mbar_wait(b ? mb1 : mb0, (par >> b) & 1u, a.wait_limit);
@@ -517,8 +492,8 @@ track_kernel(const EvalArgs a0, const EvalArgs *__restrict__ args, const long lo
                 // with d_b the row's distance from the unit cell.  Every cell
                 // within rho_max of any of the lane's visibilities is in it;
                 // the others read zero table entries (the tables are padded
-                // past rp + sqrt(2) + spread).
-                const float rp = rmax + spread, rp2 = rp * rp;
+                // past the aperture's reach + sqrt(2) + the context's largest step).
+                const float rp = rmax + fmaf(sp_m, ch.sc_hi, 1e-3f), rp2 = rp * rp;
                 const int R = (int)ceilf(rp);
                 const uint32_t base = tile + (uint32_t)((ny[0] - box.y0) * W + (nx[0] - box.x0)) * 8u;
                 if constexpr (kV == 2) {
