@@ -577,13 +577,14 @@ const char *psc_batch_kernel(const psc_batch *b);
  * block size serves the persistent launch); the winner is also timed with
  * PSC_STAGE_NEVER and the faster grid access kept.  Contexts of the same
  * array, channels and grid reuse the first one's choice, with the time tile
- * refitted to their own length (flat bricks need no refit).  Each
- * representative is also timed with the track kernel (psc_set_track_tiling,
- * 1 and 2 visibilities per lane, where allowed); if the track kernel's total
- * over the batch (each representative weighted by the time steps of the
- * contexts that reuse it) beats the brick kernel's, every context takes the
- * faster track tiling.  Writes the chosen (t_tile, c_group, vis_per_thread,
- * staging mode) of context k to tiling_out[4k..4k+3] (NULL to skip); flat
+ * refitted to their own length (flat bricks need no refit).  The fused
+ * kernel is then chosen on the whole batch: one persistent launch with these
+ * brick shapes, and one with the track kernel (psc_set_track_tiling) for each
+ * of 1 and 2 visibilities per lane that every context allows, each timed; the
+ * fastest is kept.  Each context's trial offsets and solver state are saved
+ * before those launches and restored after them.  Writes the chosen (t_tile,
+ * c_group, vis_per_thread, staging mode) of context k to tiling_out[4k..4k+3]
+ * (NULL to skip); flat
  * bricks are written as (items, 0, vis_per_thread, staging mode) and the
  * track tiling as (-1, 0, vis_per_lane, PSC_STAGE_AUTO).  Synchronises. */
 psc_status psc_batch_autotune(psc_batch *b, int *tiling_out);

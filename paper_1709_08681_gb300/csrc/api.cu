@@ -1485,6 +1485,18 @@ psc_status build_tables(psc_batch *b) {
     return PSC_OK;
 }
 
+// The batch's persistent fused launch (its work queue already reset).
+psc_status launch_fused(psc_batch *b) {
+    const int n = (int)b->ctxs.size();
+    cudaStream_t s = b->stream;
+    if (b->track)
+        PSC_BCUDA(b, launch_track_batch(b->d_eval, b->d_prefix, n, b->d_queue, b->track, kTrkCap, b->trk_tabc, b->grid, s));
+    else
+        PSC_BCUDA(b, launch_eval_batch(b->d_eval, b->d_prefix, n, b->d_queue, b->threads, b->eval_dyn, b->grid,
+                                       b->stacked, s));
+    return PSC_OK;
+}
+
 // One LM iteration of every context: fused persistent launch, reductions, update.
 psc_status enqueue_iteration(psc_batch *b) {
     const int n = (int)b->ctxs.size();
@@ -1498,11 +1510,8 @@ psc_status enqueue_iteration(psc_batch *b) {
         }
         PSC_BCUDA(b, cudaEventRecord(b->ev_pool[b->ev_used], s));
     }
-    if (b->track)
-        PSC_BCUDA(b, launch_track_batch(b->d_eval, b->d_prefix, n, b->d_queue, b->track, kTrkCap, b->trk_tabc, b->grid, s));
-    else
-        PSC_BCUDA(b, launch_eval_batch(b->d_eval, b->d_prefix, n, b->d_queue, b->threads, b->eval_dyn, b->grid,
-                                       b->stacked, s));
+    psc_status fst = launch_fused(b);
+    if (fst != PSC_OK) return fst;
     if (b->prof) {
         PSC_BCUDA(b, cudaEventRecord(b->ev_pool[b->ev_used + 1], s));
         b->ev_used += 2;
@@ -1670,10 +1679,6 @@ psc_status psc_batch_autotune(psc_batch *b, int *tiling_out) {
     std::vector<double> zeros;
     std::vector<std::vector<std::pair<float, Tiling>>> timed(n);
     std::vector<int> reused(n, -1);
-    // per representative context: best brick-kernel time, track-kernel time per
-    // visibilities per lane (1, 2; infinite where not allowed)
-    std::vector<float> t_brick(n, 1e30f);
-    std::vector<std::array<float, 3>> t_trk(n, {1e30f, 1e30f, 1e30f});
     auto time_eval = [&](psc_ctx *c, int k, float *ms) -> psc_status {
         psc_status st = ensure_partials(c);
         if (st != PSC_OK) return bfail(b, st, c->err);
@@ -1726,56 +1731,7 @@ psc_status psc_batch_autotune(psc_batch *b, int *tiling_out) {
             psc_status st = time_eval(c, k, &ms);
             if (st != PSC_OK) return st;
             c->no_stage = ms < best ? 1 : 0;
-            t_brick[k] = std::min(best, ms);
-            // the track kernel, where the context allows it
-            for (int kv = 1; kv <= 2; ++kv) {
-                if (!trk_refusal(c, kv).empty()) continue;
-                st = trk_prepare(c);
-                if (st != PSC_OK) return bfail(b, st, c->err);
-                c->trk_kv = kv;
-                st = time_eval(c, k, &ms);
-                c->trk_kv = 0;
-                if (st != PSC_OK) return st;
-                t_trk[k][kv] = ms;
-            }
         }
-    }
-    // batch-wide choice of the fused kernel: the total time of the
-    // representatives, each weighted by the time steps of the contexts that
-    // reuse its choice
-    std::vector<double> weight(n, 0.0);
-    for (int k = 0; k < n; ++k) {
-        const int r = reused[k] < 0 ? k : reused[k];
-        weight[r] += (double)b->ctxs[k]->nt / b->ctxs[r]->nt;
-    }
-    double tot_brick = 0.0, tot_trk[3] = {0.0, 0.0, 0.0};
-    for (int k = 0; k < n; ++k) {
-        if (reused[k] >= 0) continue;
-        tot_brick += weight[k] * t_brick[k];
-        for (int kv = 1; kv <= 2; ++kv) tot_trk[kv] += weight[k] * t_trk[k][kv];
-    }
-    int use_trk = 0;
-    for (int kv = 1; kv <= 2; ++kv)
-        if (tot_trk[kv] < 1e29 && tot_trk[kv] < tot_brick && (use_trk == 0 || tot_trk[kv] < tot_trk[use_trk]))
-            use_trk = kv;
-    for (int k = 0; k < n && use_trk; ++k)               // every context must take that tiling
-        if (!trk_refusal(b->ctxs[k], use_trk).empty()) use_trk = 0;
-    if (use_trk) {
-        for (int k = 0; k < n; ++k) {
-            psc_ctx *c = b->ctxs[k];
-            psc_status st = trk_prepare(c);
-            if (st != PSC_OK) return bfail(b, st, c->err);
-            c->trk_kv = use_trk;
-            if (tiling_out) {
-                tiling_out[4 * k] = -1;
-                tiling_out[4 * k + 1] = 0;
-                tiling_out[4 * k + 2] = use_trk;
-                tiling_out[4 * k + 3] = PSC_STAGE_AUTO;
-            }
-        }
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
-        return build_tables(b);
     }
     // one block size serves the whole persistent launch: contexts whose best
     // shape is narrower take their fastest timed shape of the widest size
@@ -1813,6 +1769,85 @@ psc_status psc_batch_autotune(psc_batch *b, int *tiling_out) {
             tiling_out[4 * k + 1] = c->flat > 0 ? 0 : c->c_group;
             tiling_out[4 * k + 2] = c->kv;
             tiling_out[4 * k + 3] = c->no_stage ? PSC_STAGE_NEVER : PSC_STAGE_AUTO;
+        }
+    }
+    // the fused kernel, chosen on the whole batch: one persistent launch of the
+    // brick kernel (the shapes above) and of the track kernel with each
+    // visibilities-per-lane that every context allows.  (Single contexts, timed
+    // alone, misjudge it: short intervals leave most of the GPU idle.)
+    std::vector<int> cands{0};
+    for (int kv = 1; kv <= 2; ++kv) {
+        bool all = true;
+        for (psc_ctx *c : b->ctxs) all = all && trk_refusal(c, kv).empty();
+        if (all) cands.push_back(kv);
+    }
+    int use_trk = 0;
+    if (cands.size() > 1) {
+        // the timing evaluates every context at zero offsets with its solver
+        // running: save each context's trial offsets and state, restore them after
+        size_t lm_len = 0;
+        for (psc_ctx *c : b->ctxs) lm_len += 2 * (size_t)c->n_ant;
+        double *d_lm_save = nullptr;
+        LMState *d_st_save = nullptr;
+        cudaError_t e = dalloc(&d_lm_save, lm_len);
+        if (e == cudaSuccess) e = dalloc(&d_st_save, (size_t)n);
+        size_t off = 0;
+        for (int k = 0; k < n && e == cudaSuccess; ++k) {
+            psc_ctx *c = b->ctxs[k];
+            e = cudaMemcpyAsync(d_lm_save + off, c->d_lm_trial, sizeof(double) * 2 * c->n_ant, cudaMemcpyDeviceToDevice, b->stream);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(d_st_save + k, c->d_state, sizeof(LMState), cudaMemcpyDeviceToDevice, b->stream);
+            if (e == cudaSuccess) e = cudaMemsetAsync(c->d_lm_trial, 0, sizeof(double) * 2 * c->n_ant, b->stream);
+            if (e == cudaSuccess) e = cudaMemsetAsync(c->d_done, 0, sizeof(int), b->stream);
+            off += 2 * (size_t)c->n_ant;
+        }
+        float best = 1e30f;
+        psc_status st = PSC_OK;
+        for (size_t q = 0; q < cands.size() && e == cudaSuccess && st == PSC_OK; ++q) {
+            const int kv = cands[q];
+            for (psc_ctx *c : b->ctxs) {
+                if (kv > 0) {
+                    st = trk_prepare(c);
+                    if (st != PSC_OK) break;
+                }
+                c->trk_kv = kv;
+            }
+            if (st == PSC_OK) st = build_tables(b);
+            if (st != PSC_OK) break;
+            float ms = 0.f;
+            for (int r = 0; r < 2 && st == PSC_OK; ++r) {             // warm, then timed
+                if (r == 1) e = cudaEventRecord(e0, b->stream);
+                if (e == cudaSuccess) e = cudaMemsetAsync(b->d_queue, 0, sizeof(unsigned long long), b->stream);
+                if (e == cudaSuccess) st = launch_fused(b);
+                if (r == 1 && e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
+            }
+            if (e == cudaSuccess && st == PSC_OK) e = cudaEventSynchronize(e1);
+            if (e == cudaSuccess && st == PSC_OK) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e == cudaSuccess && st == PSC_OK && ms < best) {
+                best = ms;
+                use_trk = kv;
+            }
+        }
+        off = 0;
+        for (int k = 0; k < n && d_lm_save && d_st_save; ++k) {
+            psc_ctx *c = b->ctxs[k];
+            cudaMemcpyAsync(c->d_lm_trial, d_lm_save + off, sizeof(double) * 2 * c->n_ant, cudaMemcpyDeviceToDevice, b->stream);
+            cudaMemcpyAsync(c->d_state, d_st_save + k, sizeof(LMState), cudaMemcpyDeviceToDevice, b->stream);
+            off += 2 * (size_t)c->n_ant;
+        }
+        cudaStreamSynchronize(b->stream);
+        cudaFree(d_lm_save);
+        cudaFree(d_st_save);
+        if (st != PSC_OK) return st;
+        if (e != cudaSuccess) return bfail(b, PSC_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
+    }
+    for (int k = 0; k < n; ++k) {
+        psc_ctx *c = b->ctxs[k];
+        c->trk_kv = use_trk;
+        if (use_trk && tiling_out) {
+            tiling_out[4 * k] = -1;
+            tiling_out[4 * k + 1] = 0;
+            tiling_out[4 * k + 2] = use_trk;
+            tiling_out[4 * k + 3] = PSC_STAGE_AUTO;
         }
     }
     cudaEventDestroy(e0);

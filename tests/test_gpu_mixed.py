@@ -74,8 +74,11 @@ def test_mixed_batch_equals_individual_solves_and_recovers_offsets(mixed):
     b = _abi.Batch(s.ctxs, vis, None, w_scale=w_scale)
     tiling = b.psc_batch_autotune()
     # refitted shapes may be narrower than the batch's block (the widest one);
-    # c_group 0 marks flat bricks of tt items
-    assert all((1 <= tt * cg <= 256 or (cg == 0 and tt in (64, 128, 192, 256))) and kv in (1, 2) and st in (0, 1)
+    # c_group 0 marks flat bricks of tt items, (-1, 0) the track kernel, which
+    # then serves every context
+    track = [tt == -1 and cg == 0 for tt, cg, kv, st in tiling]
+    assert all(track) or not any(track)
+    assert all((1 <= tt * cg <= 256 or (cg == 0 and tt in (-1, 64, 128, 192, 256))) and kv in (1, 2) and st in (0, 1)
                for tt, cg, kv, st in tiling)
     b.close()
     sols, reps = _abi.psc_solve_batch(s.ctxs, vis, None, w_scale=w_scale)
