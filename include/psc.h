@@ -132,8 +132,11 @@ typedef struct {
  * (H + lam diag(H)) delta = -g over all 2 n_ant parameters (PSC_LM_FULL) or
  * per antenna with step scaled by block_gain (PSC_LM_BLOCK).  A trial that
  * lowers chi^2 is accepted (lam /= 10, floored at lam_min), else rejected
- * (lam *= 10).  Stops: max |delta| < step_tol_rad; an accepted relative chi^2
- * decrease < chi2_rtol; lam > lam_max; max_iter iterations. */
+ * (lam *= 10).  Stops: max |delta| < step_tol_rad; a rejected trial whose
+ * step max |delta| was below 10 step_tol_rad (reason PSC_STOP_STEP: the minimum
+ * is found to within that, and raising lam would only shrink the step to the
+ * tolerance); an accepted relative chi^2 decrease < chi2_rtol; lam > lam_max;
+ * max_iter iterations. */
 typedef struct {
     int    max_iter;       /* 50 */
     int    mode;           /* PSC_LM_FULL */

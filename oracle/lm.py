@@ -20,8 +20,11 @@ needs the paper's loop gain (Eq. SelfCal's gamma): its step is scaled by
 far more slowly than the full solve and is kept as an option.  A trial is accepted when it lowers chi^2
 (lam /= 10), else rejected (lam *= 10).  Stop when the largest step is below
 ``step_tol`` (rad), when an accepted step lowers chi^2 by a relative amount
-below ``chi2_rtol``, when lam exceeds ``lam_max``, or after ``max_iter``
-iterations.  Every iteration costs exactly one evaluation at the trial point.
+below ``chi2_rtol``, when lam exceeds ``lam_max``, when a rejected step was
+already below 10 ``step_tol`` (the minimum is then found to within that, and
+raising lam would only shrink the step to the tolerance), or after
+``max_iter`` iterations.  Every iteration costs exactly one evaluation at the
+trial point.
 """
 from __future__ import annotations
 
@@ -101,6 +104,11 @@ def _solve(evaluate, step, lm0, opts: Options):
             lam *= 10.0
             if lam > opts.lam_max:
                 reason = "lambda"
+                break
+            # a rejected step already below ten times the tolerance ends the
+            # solve: raising lam would only shrink it to the tolerance
+            if math.isfinite(chi2_t) and np.max(np.abs(delta)) < 10.0 * opts.step_tol:
+                reason = "step"
                 break
     return lm, Report(n_iter=it, n_eval=n_eval, reason=reason, chi2=chi2, lam=lam, chi2_history=hist)
 

@@ -328,6 +328,11 @@ __global__ void __launch_bounds__(kLmThreads) lm_update_kernel(const LMArgs a0, 
     const int n = a.n_ant, n2 = 2 * n;
     const size_t len = ev_len(n, a.n_bl);
 
+    // the step that produced this trial (its largest component)
+    double tstep = 0.0;
+    for (int p = tid; p < n2; p += blockDim.x) tstep = fmax(tstep, fabs(a.lm_trial[p] - a.lm_cur[p]));
+    tstep = block_max(tstep, s_tmp);
+
     if (tid == 0) {
         const double chi2_t = a.ev[0];
         int accept = 0, stop = PSC_STOP_NONE;
@@ -343,6 +348,10 @@ __global__ void __launch_bounds__(kLmThreads) lm_update_kernel(const LMArgs a0, 
         } else {
             lam *= 10.0;
             if (lam > st->lam_max) stop = PSC_STOP_LAMBDA;
+            // a rejected step already below ten times the step tolerance: the
+            // minimum is found to within the evaluation's own noise, and a
+            // rising lam would only shrink the step to the tolerance
+            else if (isfinite(chi2_t) && tstep < 10.0 * st->step_tol) stop = PSC_STOP_STEP;
         }
         st->n_eval += 1;
         if (accept) st->chi2 = chi2_t;
