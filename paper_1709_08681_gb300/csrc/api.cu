@@ -384,7 +384,7 @@ StencilArgs stencil_args(const psc_ctx *ctx, const void *vis_obs, const float *w
     a.sigma = (float)sigma;
     // bricks of exactly one warp with a single channel group and time tile (a
     // brick is then a baseline): four per block, sharing the block's tables
-    a.wpb = (t_tile * c_group == 32 && a.n_cg == 1 && a.n_tt == 1 && !a.stage) ? 4 : 1;
+    a.wpb = (t_tile * c_group == 32 && a.n_cg == 1 && a.n_tt == 1 && !a.stage) ? 4 : 1;   // at most 4: one box per warp
     return a;
 }
 
@@ -1837,8 +1837,13 @@ psc_status psc_batch_autotune(psc_batch *b, int *tiling_out) {
         cudaStreamSynchronize(b->stream);
         cudaFree(d_lm_save);
         cudaFree(d_st_save);
-        if (st != PSC_OK) return st;
-        if (e != cudaSuccess) return bfail(b, PSC_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
+        if (st != PSC_OK || e != cudaSuccess) {
+            for (psc_ctx *c : b->ctxs) c->trk_kv = 0;       // no context left half-switched
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            if (st != PSC_OK) return st;
+            return bfail(b, PSC_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
+        }
     }
     for (int k = 0; k < n; ++k) {
         psc_ctx *c = b->ctxs[k];

@@ -45,7 +45,7 @@ __device__ __forceinline__ float2 lds_f2(unsigned addr) {
 // One brick of the stencil pass (s_tab: dynamic shared memory).
 __device__ __forceinline__ void stencil_brick(const StencilArgs &a, int blk, float2 *s_tab) {
     float2 *s_tile = s_tab + a.c_group * (a.max_tab_len + kTabPad);
-    __shared__ int s_boxes[4][4];
+    __shared__ int s_boxes[4][4];                 // one box per warp: wpb <= 4 (128 threads)
     __shared__ double s_red[4][kSRed];
 
     // block blk runs brick blk, or (a.wpb > 1) bricks blk wpb + w, one per warp w,
