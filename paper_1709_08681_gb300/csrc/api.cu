@@ -265,6 +265,9 @@ EvalArgs eval_args(const psc_ctx *c, const double *lm_dev) {
         a.trk_cap = kTrkCap;
         a.trk_stride = c->trk_stride;
         a.trk_pad = trk_pad(c, c->trk_kv);
+        // the longest table a channel copies with this tiling's pad (the stride
+        // is sized for two visibilities per lane)
+        a.trk_tabc = (std::min(c->trk_stride, (c->max_tab_len + a.trk_pad + 1) & ~1) + 15) / 16 * 16;
         a.trk_spread = (float)c->step_cells;
         a.tabs_cs = c->d_tabcs;
         a.tmap = c->d_tmap;
@@ -1437,12 +1440,13 @@ psc_status build_tables(psc_batch *b) {
     // one fused kernel per persistent launch: the track kernel for all
     // contexts (same visibilities per lane) or for none
     int n_trk = 0, kv_trk = 0, tabc = 0;
-    for (psc_ctx *c : b->ctxs) {
+    for (int k = 0; k < n; ++k) {
+        const psc_ctx *c = b->ctxs[k];
         if (c->trk_kv <= 0) continue;
         ++n_trk;
         if (kv_trk && kv_trk != c->trk_kv) kv_trk = -1;
         else if (kv_trk == 0) kv_trk = c->trk_kv;
-        tabc = std::max(tabc, (c->trk_stride + 15) / 16 * 16);
+        tabc = std::max(tabc, ev[k].trk_tabc);
     }
     if (n_trk != 0 && (n_trk != n || kv_trk < 0))
         return bfail(b, PSC_ERR_ARG, "a batch runs one fused kernel: give every context the same track tiling, or none");

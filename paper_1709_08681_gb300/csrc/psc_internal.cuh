@@ -76,6 +76,7 @@ struct EvalArgs {
     int trk_cap;               // staged tile capacity of one buffer (cells)
     int trk_stride;            // entries per channel in tabs_cs (even)
     int trk_pad;               // zero entries past a channel's table that a lane can reach
+    int trk_tabc;              // table capacity of a warp buffer (entries, multiple of 16): the longest copy
     float trk_spread;          // largest move of a baseline between consecutive time steps (cells, top channel)
     const float2 *tabs_cs;     // [nc][trk_stride]: (A°(n) - n s_n, s_n), s_n = A°(n+1) - A°(n), zero padded
     const void *tmap;          // 3 CUtensorMaps over the grid (8-byte cells), boxes 8, 16, 32 wide x 8 rows

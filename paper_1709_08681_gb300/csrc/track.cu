@@ -770,7 +770,7 @@ cudaError_t track_occupancy(int kv, size_t dyn, int *blocks_per_sm) {
 }
 
 cudaError_t launch_track(const EvalArgs &a, cudaStream_t s) {
-    const int cap = a.trk_cap, tabc = (a.trk_stride + 15) / 16 * 16;
+    const int cap = a.trk_cap, tabc = a.trk_tabc;
     const size_t dyn = track_dyn_smem(cap, tabc);
     cudaError_t e = set_track_smem(dyn);
     if (e != cudaSuccess) return e;
