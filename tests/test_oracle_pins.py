@@ -322,3 +322,35 @@ def test_predict_points_equals_predict():
     Vp, dVp = psc.predict_points(m, lm, t, b, c)
     assert np.allclose(Vp, V[t, b, c], rtol=1e-13, atol=1e-15)
     assert np.allclose(dVp, dV[:, t, b, c], rtol=1e-13, atol=1e-12)
+
+
+def test_lm_stops_on_a_rejected_step_below_ten_tolerances():
+    """The rejected-step stop rule of the LM (Terminate() is left to the
+    minimiser, Sec. 2.2).  chi^2 is a quadratic plus a bump within 1.5 step
+    tolerances of its minimum (standing in for rounding noise there).  From a
+    start 2 tolerances away, the Gauss-Newton trial lands next to the minimum,
+    inside the bump, and is rejected; its step (about 2 tolerances) is above
+    the plain step rule, so only the rejected-step rule can stop the solve:
+    after one iteration, at the start, within 10 tolerances of the minimum.
+    Without the bump the trial is accepted and the solve converges."""
+    tol = LM.Options().step_tol
+    H = np.array([[4.0, 1.0], [1.0, 3.0]])
+    x_min = np.array([3e-5, -2e-5])
+
+    def evaluate(bump):
+        def f(p):
+            d = np.ravel(p) - x_min
+            chi2 = 0.5 * d @ H @ d               # about 8 tol^2 = 2e-18 at the start
+            if bump and 0.0 < np.max(np.abs(d)) < 1.5 * tol:
+                chi2 += 1e-15
+            return chi2, H @ d, H
+        return f
+
+    start = x_min + np.array([2.0 * tol, 0.0])
+    p, rep = LM.solve_full(evaluate(True), start)
+    assert rep.reason == "step" and rep.n_iter == 1 and rep.n_eval == 2, rep
+    assert np.array_equal(np.ravel(p), start)
+    assert np.max(np.abs(np.ravel(p) - x_min)) < 10 * tol
+    p0, rep0 = LM.solve_full(evaluate(False), start)
+    assert rep0.reason in ("step", "chi2"), rep0
+    assert np.max(np.abs(np.ravel(p0) - x_min)) < tol
