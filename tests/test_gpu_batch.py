@@ -93,6 +93,43 @@ def test_batch_autotune_keeps_results():
     b.close()
 
 
+def test_autotune_in_the_middle_of_a_solve_leaves_it_undisturbed():
+    """psc_batch_autotune times whole-batch launches at zero offsets; it saves
+    and restores every context's trial offsets and solver state around them.
+    Small apertures, so that the track kernel is among the candidates."""
+    small_ap = ("disk", 512, 5.0, 1024)
+    ivs = []
+    for n_ant, nt, freqs, seed in ((5, 40, (1.3e9, 1.4e9), 4), (6, 64, (1.3e9, 1.4e9, 1.5e9), 5)):
+        m, _, lmt, img = cases.problem(small_ap, n_ant=n_ant, n_time=nt, freqs=freqs, sigma_arcsec=30.0, seed=seed)
+        V, _ = psc.predict(m, lmt, False)
+        vobs = (V + I.complex_noise(V.shape, 1e-3, seed + 10)).astype(np.complex64)
+        gp = GpuProblem(m, img)
+        ivs.append(dict(m=m, gp=gp, dv=gp.upload(vobs)))
+    ctxs = [iv["gp"].ctx for iv in ivs]
+    zeros = [np.zeros((iv["m"].n_ant, 2)) for iv in ivs]
+    b = _abi.Batch(ctxs, [iv["dv"] for iv in ivs], None, w_scale=[1e6, 1e6])
+    b.psc_batch_autotune()
+    b.psc_batch_begin(zeros)
+    b.psc_batch_iterate(2)
+    lm_a, rep_a = b.psc_batch_end()
+    b.psc_batch_autotune()                             # mid-solve (its choice may differ: timing)
+    lm_b, rep_b = b.psc_batch_end()
+    for x, y in zip(lm_a, lm_b):
+        assert np.array_equal(x, y)
+    for x, y in zip(rep_a, rep_b):
+        assert (x.n_iter, x.n_eval, x.reason, x.chi2, x.lam) == (y.n_iter, y.n_eval, y.reason, y.chi2, y.lam)
+    b.psc_batch_iterate(40)
+    got, reps = b.psc_batch_end()
+    b.close()
+    # the same minimum as a solve without the interruption: each may stop up to
+    # ten step tolerances (1e-3 arcsec) from it, along a different path (the
+    # kernel chosen mid-solve may differ from the first choice)
+    for k, iv in enumerate(ivs):
+        assert _abi.STOP_REASONS[reps[k].reason] in ("step", "chi2"), k
+        ref, _ = iv["gp"].ctx.psc_solve_offsets(iv["dv"], None, 1e6)
+        assert np.max(np.abs(got[k] - ref)) < 5e-3 * I.ARCSEC, k
+
+
 def test_batch_rejects_duplicates():
     ivs = _intervals()[:1]
     c = ivs[0]["gp"].ctx
